@@ -1,0 +1,107 @@
+/*
+ * neb_oracle.h -- plain, single-threaded CPU oracle of the Next Event
+ * Backtracking (NEB) iteration (Jendersie, "Next Event Backtracking").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code
+ * with the CUDA path: it has its own BVH, its own intersection routines, its
+ * own octree and computes every MIS weight explicitly from the full vertex
+ * list of the path (Eq. misweight .. Eq. misw), where the GPU uses a
+ * recursive form.
+ *
+ * Precision: geometry, sampling decisions and the density octree are FP32
+ * (the octree follows the listing of Appendix B, which uses float); all
+ * radiometric quantities, MIS products and the accumulation are FP64.
+ * Build with -ffp-contract=off so the FP32 parts round the same way on
+ * every host.
+ */
+#ifndef NEB_ORACLE_H
+#define NEB_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Scene arrays; layouts are documented in paper_1909_00573_gb300/scenes.py. */
+typedef struct {
+  const float* tri;       /* [nt][3][3] */
+  const uint32_t* tri_mat;/* [nt] */
+  int nt;
+  const float* sph;       /* [ns][4] centre, radius */
+  const uint32_t* sph_mat;/* [ns] */
+  int ns;
+  const float* mats;      /* [nm][12] */
+  int nm;
+  const float* cam;       /* [10] */
+} orc_scene;
+
+typedef struct {
+  int width, height, max_depth;
+  float merge_radius;
+  int octree_capacity, split_factor;
+  uint64_t seed;
+  int density_mode;        /* 0 robust (median of 5), 1 single query */
+  uint32_t strategy_mask;  /* 1 random hit, 2 NEE, 4 NEB photon merge */
+  int first_iteration;     /* 1-based index of the first iteration rendered */
+  int pixel_begin, pixel_end; /* camera paths traced: [begin, end) (row-major), end<=0: all */
+} orc_config;
+
+/* stats[] slots filled by orc_render (summed over iterations) */
+enum {
+  ORC_ST_CAMERA_RAYS = 0, ORC_ST_NEE_VERTICES, ORC_ST_SHADOW_RAYS, ORC_ST_PHOTONS,
+  ORC_ST_PHOTON_HITS, ORC_ST_MERGES, ORC_ST_RANDOM_HITS, ORC_ST_OCTREE_NODES,
+  ORC_ST_OCTREE_DEPTH, ORC_ST_COUNT
+};
+
+/* Render n_iter iterations.  accum: [H*W*3] FP64 sums over the iterations
+ * (not divided).  last_split (may be NULL): [3][H*W*3] contributions of the
+ * last iteration split by event type (0 random hit, 1 NEE, 2 photon merge).
+ * nee_rho (may be NULL): [H*W*(D-1)] density at every NEE vertex of the last
+ * iteration, indexed pixel*(D-1) + (k-1), -1 where no NEE vertex exists.
+ * Returns 0 on success. */
+int orc_render(const orc_scene* scene, const orc_config* cfg, int n_iter,
+               double* accum, double* last_split, float* nee_rho, int64_t* stats);
+
+/* ---- unit entry points used by the pin tests ---- */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+float orc_intersection_area(const float bmin[3], const float bmax[3],
+                            const float pos[3], const float normal[3]);
+
+typedef struct orc_octree orc_octree;
+orc_octree* orc_octree_new(const float scene_min[3], const float scene_max[3],
+                           int capacity, int split_factor);
+void orc_octree_free(orc_octree* o);
+void orc_octree_set_iteration(orc_octree* o, int iter);
+void orc_octree_increment(orc_octree* o, const float pos[3]);
+float orc_octree_density(orc_octree* o, const float pos[3], const float normal[3], int robust);
+/* Copies min(n, capacity) nodes; returns capacity.  meta: alloc, depth, capacity. */
+int orc_octree_dump(const orc_octree* o, int32_t* nodes, int n, int32_t meta[3]);
+
+/* BVH parity helpers: closest hit for n rays ([n][6] origin, direction);
+ * out_prim -1 on miss, out_t the hit distance.  brute != 0 tests every
+ * primitive instead of walking the BVH. */
+int orc_trace(const orc_scene* scene, const float* rays, int n, int brute,
+              int32_t* out_prim, float* out_t);
+
+/* Merge candidate enumeration helper: for every query point, the number of
+ * points within radius r (d^2 <= r^2 in FP32).  brute != 0 uses the O(N*M)
+ * scan, otherwise the sorted-window search used by orc_render. */
+void orc_count_neighbours(const float* pts, int n, const float* queries, int m,
+                          float r, int brute, int32_t* out_count);
+
+/* Balance-heuristic weights of every strategy for one explicit path (used by
+ * the MIS pin tests).  See the definition of orc_path in the source. */
+int orc_mis_weights(const float* verts, int n_verts, const float* light,
+                    float merge_radius, double rho, uint32_t mask, double* w_out);
+
+/* BSDF probes for the pin tests (material row in the scenes layout). */
+int orc_bsdf_probe(const float* mrow, const float* n, const float* wo, const float* u, int camera, float* wi,
+                   double* weight, double* pdf_out, double* f_out);
+void orc_bsdf_eval_probe(const float* mrow, const float* n, const float* wo, const float* wi, double* f_out,
+                         double* pdf_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

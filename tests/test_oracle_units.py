@@ -1,0 +1,505 @@
+"""Pins of the oracle's building blocks against things other than itself:
+published known-answer vectors, exact geometry computed a different way,
+brute force, textbook formulas and hand-worked examples."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10 (random numbers, keyed by (iteration, pixel, bounce, dim))
+# --------------------------------------------------------------------------
+def load_kat():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        v = [int(x, 16) for x in line.split()]
+        rows.append((v[0:4], v[4:6], v[6:10]))
+    return rows
+
+
+def test_philox_known_answers(oracle):
+    for ctr, key, out in load_kat():
+        assert oracle.philox4x32_10(ctr, key).tolist() == out
+
+
+# --------------------------------------------------------------------------
+# plane/box intersection area (Eq. area, Appendix A and the listing)
+# --------------------------------------------------------------------------
+def exact_area(bmin, bmax, p, n):
+    """Area of {x in box : n.x = n.p} by clipping: plane/edge crossings,
+    ordered by angle around their centroid, then the 3D shoelace formula."""
+    bmin = np.asarray(bmin, np.float64)
+    bmax = np.asarray(bmax, np.float64)
+    n = np.asarray(n, np.float64)
+    n = n / np.linalg.norm(n)
+    h = float(n @ np.asarray(p, np.float64))
+    corners = np.array([[bmax[0] if i & 1 else bmin[0], bmax[1] if i & 2 else bmin[1],
+                         bmax[2] if i & 4 else bmin[2]] for i in range(8)])
+    pts = []
+    for i in range(8):
+        for bit in (1, 2, 4):
+            j = i | bit
+            if j == i:
+                continue
+            a, b = corners[i], corners[j]
+            da, db = a @ n - h, b @ n - h
+            if da == 0.0:
+                pts.append(a)
+            if db == 0.0:
+                pts.append(b)
+            if da * db < 0:
+                t = da / (da - db)
+                pts.append(a + t * (b - a))
+    if len(pts) < 3:
+        return 0.0
+    P = np.unique(np.round(np.array(pts), 14), axis=0)
+    if len(P) < 3:
+        return 0.0
+    c = P.mean(0)
+    u = np.cross(n, [1.0, 0, 0]) if abs(n[0]) < 0.9 else np.cross(n, [0, 1.0, 0])
+    u /= np.linalg.norm(u)
+    w = np.cross(n, u)
+    ang = np.arctan2((P - c) @ w, (P - c) @ u)
+    P = P[np.argsort(ang)]
+    s = np.zeros(3)
+    for i in range(len(P)):
+        s += np.cross(P[i], P[(i + 1) % len(P)])
+    return 0.5 * abs(s @ n)
+
+
+def test_area_closed_forms(oracle):
+    unit = ([0, 0, 0], [1, 1, 1])
+    # axis-aligned planes cut a face-sized square
+    assert oracle.intersection_area(*unit, [0.3, 0.4, 0.5], [0, 0, 1]) == pytest.approx(1.0, rel=1e-7)
+    assert oracle.intersection_area([0, 0, 0], [2, 3, 5], [1, 1, 1], [1, 0, 0]) == pytest.approx(15.0, rel=1e-7)
+    # plane x + y = 1 (one zero component) cuts a sqrt(2) x 1 rectangle
+    n = np.array([1, 1, 0]) / math.sqrt(2)
+    assert oracle.intersection_area(*unit, [0.5, 0.5, 0.5], n) == pytest.approx(math.sqrt(2), rel=1e-6)
+    # plane through the cube centre with normal (1,1,1)/sqrt(3): regular hexagon of side sqrt(2)/2
+    n = np.ones(3) / math.sqrt(3)
+    hexagon = 3 * math.sqrt(3) / 2 * 0.5
+    assert oracle.intersection_area(*unit, [0.5, 0.5, 0.5], n) == pytest.approx(hexagon, rel=1e-5)
+    # corner triangle: plane x+y+z = 0.5 cuts a triangle with legs 0.5
+    tri = math.sqrt(3) / 4 * (0.5 * math.sqrt(2)) ** 2
+    assert oracle.intersection_area(*unit, [0.5, 0, 0], n) == pytest.approx(tri, rel=1e-5)
+    # plane beyond the box: mathematically 0; the FP32 alternating sum of eight
+    # squares of size ~12 cancels to a few 1e-6 (the float issue noted in Sec. 5.3)
+    assert oracle.intersection_area(*unit, [2.0, 2.0, 2.0], n) == pytest.approx(0.0, abs=1e-4)
+
+
+def test_area_matches_polygon_clipping(oracle):
+    rng = np.random.default_rng(1)
+    errs = []
+    for _ in range(3000):
+        bmin = rng.uniform(-2, 2, 3).astype(np.float32)
+        bmax = (bmin + rng.uniform(0.1, 2.0, 3)).astype(np.float32)
+        p = (bmin + rng.uniform(0, 1, 3) * (bmax - bmin)).astype(np.float32)
+        while True:
+            n = rng.normal(size=3)
+            n /= np.linalg.norm(n)
+            if np.all(np.abs(n) > 0.05):
+                break
+        n = n.astype(np.float32)
+        a = oracle.intersection_area(bmin, bmax, p, n)
+        e = exact_area(bmin, bmax, p, n)
+        scale = max(e, 1e-3 * float(np.prod(bmax - bmin)) ** (2 / 3))
+        errs.append(abs(a - e) / scale)
+    # FP32 evaluation of the alternating sum of squares; components >= 0.05
+    assert np.quantile(errs, 0.99) < 2e-3 and max(errs) < 2e-2, (np.quantile(errs, 0.99), max(errs))
+
+
+def test_area_near_listing_thresholds_is_bounded(oracle):
+    """The listing switches to the 1D / 2D formulas when a component is within
+    1e-3 of 1 or below 1e-4; the error there stays small (documented reading)."""
+    rng = np.random.default_rng(2)
+    for _ in range(500):
+        bmin = np.zeros(3, np.float32)
+        bmax = rng.uniform(0.5, 1.5, 3).astype(np.float32)
+        p = (rng.uniform(0.2, 0.8, 3) * bmax).astype(np.float32)
+        eps = rng.uniform(0, 2e-3)
+        n = np.array([math.sqrt(max(0.0, 1 - eps * eps)), eps * 0.6, eps * 0.8], np.float64)
+        n = rng.permutation(n).astype(np.float32)
+        a = oracle.intersection_area(bmin, bmax, p, n)
+        e = exact_area(bmin, bmax, p, n)
+        assert abs(a - e) <= 5e-3 * e + 1e-6
+
+
+# --------------------------------------------------------------------------
+# density octree (Sec. 5, Appendix B)
+# --------------------------------------------------------------------------
+def test_octree_capacity_rounding_and_root(oracle):
+    o = oracle.Octree([0, 0, 0], [1, 1, 1], 10, 4)
+    nodes, alloc, depth = o.dump()
+    assert len(nodes) == 17          # 1 + round_up(10, 8)
+    assert alloc == 1 and depth == 0 and nodes[0] == 0
+
+
+def test_octree_split_hand_worked(oracle):
+    """split factor 8, iteration 1: threshold 8, children start at ceil(8/4 * 1) = 2."""
+    o = oracle.Octree([0, 0, 0], [1, 1, 1], 64, 8)
+    o.set_iteration(1)
+    nodes, alloc, depth = o.dump()
+    assert alloc == 1 and np.all(nodes[1:] == 2)
+    p = [0.2, 0.2, 0.2]                      # lower octant 0 at every level
+    o.insert([p] * 7)
+    nodes, alloc, depth = o.dump()
+    assert nodes[0] == 7 and alloc == 1
+    o.insert([p])                            # 8th vertex reaches the threshold: split
+    nodes, alloc, depth = o.dump()
+    assert nodes[0] == -1 and alloc == 9 and depth == 1
+    assert np.all(nodes[1:9] == 2)           # children untouched by the splitting insert
+    o.insert([p])                            # descends into child 0 (octant of p)
+    nodes, alloc, depth = o.dump()
+    assert nodes[1] == 3 and np.all(nodes[2:9] == 2)
+    q = [0.8, 0.2, 0.8]                      # octant x=1, y=0, z=1 -> index 1 + 4 = 5
+    o.insert([q])
+    nodes, _, _ = o.dump()
+    assert nodes[1 + 5] == 3
+    # iteration 2: threshold 16, unused nodes re-armed to ceil(8/4*2) = 4
+    o.set_iteration(2)
+    nodes, alloc, _ = o.dump()
+    assert alloc == 9 and np.all(nodes[9:] == 4) and nodes[1] == 3
+
+
+def test_octree_allocation_overflow(oracle):
+    o = oracle.Octree([0, 0, 0], [1, 1, 1], 8, 4)   # capacity 9: one split only
+    o.set_iteration(1)
+    o.insert([[0.1, 0.1, 0.1]] * 4)                  # root split
+    nodes, alloc, depth = o.dump()
+    assert nodes[0] == -1 and alloc == 9 and depth == 1
+    o.insert([[0.1, 0.1, 0.1]] * 3)                  # child 0: 1 + 3 = 4 -> split wanted, overflow
+    nodes, alloc, depth = o.dump()
+    assert nodes[1] == 4 and alloc == 10 and depth == 1
+    # the listing increments before it checks for a split, so the full leaf
+    # keeps counting; no further allocation is attempted
+    o.insert([[0.1, 0.1, 0.1]] * 5)
+    nodes2, alloc2, _ = o.dump()
+    assert nodes2[1] == 9 and np.array_equal(nodes[2:], nodes2[2:]) and alloc2 == 10
+
+
+def test_octree_out_of_box_is_dropped(oracle):
+    o = oracle.Octree([0, 0, 0], [1, 1, 1], 64, 4)
+    o.set_iteration(1)
+    o.insert([[1.5, 0.5, 0.5], [-0.5, 0.5, 0.5]])
+    nodes, alloc, _ = o.dump()
+    assert nodes[0] == 0
+    assert o.density([[1.5, 0.5, 0.5]], [[0, 1, 0]], robust=False)[0] == 0.0
+
+
+def _descend(nodes, mn, size, q):
+    """Brute-force walk of the node array using only the encoding of Sec. 5.4:
+    a negative value is the negated index of the first of eight children."""
+    lo = np.zeros(3)
+    hi = np.ones(3)
+    nq = (np.asarray(q, np.float64) - mn) / size
+    idx = 0
+    while nodes[idx] < 0:
+        base = -int(nodes[idx])
+        mid = 0.5 * (lo + hi)
+        bits = (nq >= mid).astype(int)
+        idx = base + bits[0] + 2 * bits[1] + 4 * bits[2]
+        lo = np.where(bits, mid, lo)
+        hi = np.where(bits, hi, mid)
+    return int(nodes[idx]), mn + lo * size, mn + hi * size, hi[0] - lo[0]
+
+
+def test_octree_density_matches_descent_and_exact_area(oracle):
+    rng = np.random.default_rng(3)
+    smin = np.array([0, 0, 0], np.float32)
+    smax = np.array([1, 1, 1], np.float32)
+    o = oracle.Octree(smin, smax, 1 << 14, 4)
+    o.set_iteration(1)
+    # points on a tilted plane through the box
+    n = np.array([0.3, 0.8, 0.52])
+    n /= np.linalg.norm(n)
+    pts = []
+    while len(pts) < 4000:
+        x = rng.uniform(0, 1, 3)
+        x = x - ((x - 0.5) @ n) * n
+        if np.all((x > 0) & (x < 1)):
+            pts.append(x)
+    pts = np.array(pts, np.float32)
+    o.insert(pts)
+    nodes, alloc, depth = o.dump()
+    # listing's initialise(): enlarge the box by 1.002 around its minimum corner
+    size = ((smax - smin) * np.float32(1.002)).astype(np.float32)
+    mn = (smin - size * np.float32(0.001 / 1.002)).astype(np.float32)
+    scale = float(np.sqrt(np.sum(size.astype(np.float64) ** 2)))
+    q = pts[:400]
+    rho = o.density(q, np.tile(n.astype(np.float32), (len(q), 1)), robust=False)
+    checked = 0
+    for i in range(len(q)):
+        c, lo, hi, frac = _descend(nodes, mn.astype(np.float64), size.astype(np.float64), q[i])
+        res = round(1.0 / frac)
+        # skip points within float noise of a cell face
+        nq = (q[i].astype(np.float64) - mn) / size * res
+        if np.min(np.abs(nq - np.round(nq))) < 1e-4:
+            continue
+        area = exact_area(lo, hi, q[i], n)
+        diag = scale / res
+        expect = 0.0 if c <= 0 else c / max(0.01 * diag * diag, area)
+        assert rho[i] == pytest.approx(expect, rel=3e-3), (i, c, area)
+        checked += 1
+    assert checked > 300
+
+
+def test_octree_density_of_uniform_plane(oracle):
+    """N vertices spread uniformly over a unit square give rho ~ N per unit area."""
+    rng = np.random.default_rng(4)
+    o = oracle.Octree([0, 0, 0], [1, 1, 1], 1 << 16, 4)
+    N = 20000
+    o.set_iteration(1)
+    pts = np.stack([rng.uniform(0, 1, N), np.full(N, 0.37), rng.uniform(0, 1, N)], 1).astype(np.float32)
+    o.insert(pts)
+    q = np.stack([rng.uniform(0.05, 0.95, 2000), np.full(2000, 0.37), rng.uniform(0.05, 0.95, 2000)], 1)
+    rho = o.density(q, np.tile([0, 1, 0], (2000, 1)), robust=True)
+    # the estimate is biased by the child initialisation guess (Sec. 5.2) and
+    # the leaf counts are small; the mean must still land close to N
+    assert 0.7 * N < float(np.mean(rho)) < 1.3 * N
+
+
+# --------------------------------------------------------------------------
+# BVH closest hit versus brute force and versus an independent FP64 test
+# --------------------------------------------------------------------------
+def _random_rays(rng, n, lo, hi):
+    o = rng.uniform(lo, hi, (n, 3))
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return np.concatenate([o, d], 1).astype(np.float32)
+
+
+def test_bvh_equals_brute_force(oracle):
+    from paper_1909_00573_gb300 import scenes
+    s = scenes.tiny_room()
+    rng = np.random.default_rng(5)
+    rays = _random_rays(rng, 4000, 0.02, 0.98)
+    p1, t1 = oracle.trace(s, rays, brute=False)
+    p2, t2 = oracle.trace(s, rays, brute=True)
+    assert np.array_equal(p1, p2)
+    assert np.array_equal(t1[p1 >= 0], t2[p2 >= 0])
+    assert np.mean(p1 >= 0) > 0.75          # the room is open at z = 0
+
+
+def _mt_double(o, d, tri):
+    """Moeller-Trumbore in FP64 over all triangles: (prim, t)."""
+    v0, v1, v2 = tri[:, 0].astype(np.float64), tri[:, 1].astype(np.float64), tri[:, 2].astype(np.float64)
+    e1, e2 = v1 - v0, v2 - v0
+    pv = np.cross(d, e2)
+    det = np.einsum("ij,ij->i", e1, pv)
+    ok = np.abs(det) > 1e-14
+    inv = np.where(ok, 1.0 / np.where(ok, det, 1), 0)
+    tv = o - v0
+    u = np.einsum("ij,ij->i", tv, pv) * inv
+    qv = np.cross(tv, e1)
+    v = (qv @ d) * inv
+    t = np.einsum("ij,ij->i", e2, qv) * inv
+    hit = ok & (u >= 0) & (v >= 0) & (u + v <= 1) & (t > 1e-9)
+    if not hit.any():
+        return -1, np.inf
+    t = np.where(hit, t, np.inf)
+    i = int(np.argmin(t))
+    return i, float(t[i])
+
+
+def test_watertight_triangle_test_vs_fp64(oracle):
+    from paper_1909_00573_gb300 import scenes
+    rng = np.random.default_rng(6)
+    tri = rng.uniform(-1, 1, (60, 3, 3)).astype(np.float32)
+    s = scenes.Scene(tri, np.zeros(60), np.zeros((0, 4)), np.zeros(0), scenes.material(0, (0.5,) * 3)[None],
+                     np.zeros(10))
+    rays = _random_rays(rng, 1500, -0.5, 0.5)
+    prim, t = oracle.trace(s, rays, brute=True)
+    agree = 0
+    for i in range(len(rays)):
+        j, tt = _mt_double(rays[i, :3].astype(np.float64), rays[i, 3:].astype(np.float64), tri)
+        if j == prim[i]:
+            agree += 1
+            if j >= 0:
+                assert t[i] == pytest.approx(tt, rel=1e-4, abs=1e-5)
+    assert agree >= len(rays) - 3      # edge / near-tie cases only
+
+
+def test_sphere_intersection(oracle):
+    from paper_1909_00573_gb300 import scenes
+    s = scenes.Scene(np.zeros((0, 3, 3)), np.zeros(0), np.array([[0, 0, 5, 1.0], [100, 0, 0, 0.05]]),
+                     np.array([0, 0]), scenes.material(0, emission=(1, 1, 1))[None], np.zeros(10))
+    rays = np.array([[0, 0, 0, 0, 0, 1], [0, 0.5, 0, 0, 0, 1], [0, 0, 5, 1, 0, 0], [0, 0, 0, 1, 0, 0],
+                     [0, 0.06, 0, 1, 0, 0]], np.float32)
+    prim, t = oracle.trace(s, rays)
+    assert prim.tolist() == [0, 0, 0, 1, -1]
+    assert t[0] == pytest.approx(4.0, rel=1e-6)
+    assert t[1] == pytest.approx(5 - math.sqrt(0.75), rel=1e-6)
+    assert t[2] == pytest.approx(1.0, rel=1e-6)     # from the centre: far root
+    assert t[3] == pytest.approx(99.95, rel=1e-6)   # distant small sphere (cancellation-free form)
+
+
+# --------------------------------------------------------------------------
+# merge candidate search (range search around photons)
+# --------------------------------------------------------------------------
+def test_neighbour_search_equals_brute_force(oracle):
+    rng = np.random.default_rng(7)
+    pts = rng.uniform(0, 1, (3000, 3)).astype(np.float32)
+    q = rng.uniform(0, 1, (500, 3)).astype(np.float32)
+    r = 0.05
+    a = oracle.count_neighbours(pts, q, r, brute=False)
+    b = oracle.count_neighbours(pts, q, r, brute=True)
+    d2 = ((pts[None, :, :] - q[:, None, :]) ** 2)
+    d2 = (d2[..., 0] + d2[..., 1]) + d2[..., 2]          # FP32, same order
+    c = (d2 <= np.float32(r) * np.float32(r)).sum(1)
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+    assert c.sum() > 0
+
+
+# --------------------------------------------------------------------------
+# BSDFs: textbook Fresnel, Snell, cosine sampling, sampler/pdf consistency
+# --------------------------------------------------------------------------
+def fresnel_textbook(cos_i, n1, n2):
+    sin_t = n1 / n2 * math.sqrt(max(0.0, 1 - cos_i ** 2))
+    if sin_t >= 1:
+        return 1.0
+    cos_t = math.sqrt(1 - sin_t ** 2)
+    rs = (n1 * cos_i - n2 * cos_t) / (n1 * cos_i + n2 * cos_t)
+    rp = (n2 * cos_i - n1 * cos_t) / (n2 * cos_i + n1 * cos_t)
+    return 0.5 * (rs * rs + rp * rp)
+
+
+@pytest.mark.parametrize("theta_deg,entering", [(0, True), (30, True), (56.31, True), (80, True),
+                                                 (20, False), (41, False), (45, False)])
+def test_dielectric_fresnel_snell_and_scaling(oracle, theta_deg, entering):
+    from paper_1909_00573_gb300 import scenes
+    glass = scenes.material(scenes.MAT_DIELECTRIC, ior=1.5)
+    th = math.radians(theta_deg)
+    n = np.array([0, 0, 1.0], np.float32)
+    wo = np.array([math.sin(th), 0, math.cos(th) if entering else -math.cos(th)], np.float32)
+    n1, n2 = (1.0, 1.5) if entering else (1.5, 1.0)
+    F = fresnel_textbook(math.cos(th), n1, n2)
+    # bisection on the lobe random number locates the reflect/refract switch
+    lo, hi = 0.0, 1.0
+    for _ in range(40):
+        mid = 0.5 * (lo + hi)
+        ok, wi, w, pdf, f = oracle.bsdf_sample(glass, n, wo, [mid, 0.5, 0.5])
+        reflected = (wi[2] > 0) == (wo[2] > 0)
+        lo, hi = (mid, hi) if reflected else (lo, mid)
+    assert lo == pytest.approx(F, abs=2e-6)
+    ok, wi, w, pdf, f = oracle.bsdf_sample(glass, n, wo, [0.0, 0.5, 0.5])   # reflection
+    assert np.allclose(wi, [-wo[0], -wo[1], wo[2]], atol=1e-6) and np.allclose(w, 1)
+    if F < 1:
+        ok, wi, w, pdf, f = oracle.bsdf_sample(glass, n, wo, [0.999999, 0.5, 0.5], camera=True)
+        sin_t = math.hypot(wi[0], wi[1])
+        assert n1 * math.sin(th) == pytest.approx(n2 * sin_t, abs=1e-5)       # Snell
+        assert (wi[2] > 0) != (wo[2] > 0)
+        assert w[0] == pytest.approx((n1 / n2) ** 2, rel=1e-6)                 # radiance scaling
+        ok, wi, w, pdf, f = oracle.bsdf_sample(glass, n, wo, [0.999999, 0.5, 0.5], camera=False)
+        assert w[0] == pytest.approx(1.0)
+
+
+def test_lambert_sampling_is_cosine_weighted(oracle):
+    from paper_1909_00573_gb300 import scenes
+    m = scenes.material(0, (0.6, 0.5, 0.4))
+    rng = np.random.default_rng(8)
+    n = np.array([0.0, 0.6, 0.8], np.float32)
+    wo = np.array([0.0, 0.0, 1.0], np.float32)
+    cos = []
+    for u in rng.uniform(0, 1, (4000, 3)):
+        ok, wi, w, pdf, f = oracle.bsdf_sample(m, n, wo, u)
+        c = float(wi @ n)
+        assert ok and c > 0 and np.allclose(w, [0.6, 0.5, 0.4], rtol=1e-6)
+        assert pdf == pytest.approx(c / math.pi, rel=1e-5) and f[0] == pytest.approx(0.6 / math.pi)
+        cos.append(c)
+    assert np.mean(cos) == pytest.approx(2 / 3, abs=0.015)                  # E[cos] under cos/pi
+    assert np.mean(np.square(cos)) == pytest.approx(0.5, abs=0.015)         # E[cos^2] = 1/2
+
+
+def test_ggx_sampler_matches_its_pdf_and_brdf(oracle):
+    """E[f cos / pdf] over the sampler equals the quadrature of f cos over the
+    hemisphere, and f is reciprocal."""
+    from paper_1909_00573_gb300 import scenes
+    m = scenes.material(scenes.MAT_GGX, (0.9, 0.9, 0.9), alpha=0.3)
+    n = np.array([0, 0, 1.0], np.float32)
+    th = math.radians(35)
+    wo = np.array([math.sin(th), 0, math.cos(th)], np.float32)
+    rng = np.random.default_rng(9)
+    acc = []
+    for u in rng.uniform(0, 1, (20000, 3)):
+        ok, wi, w, pdf, f = oracle.bsdf_sample(m, n, wo, u)
+        acc.append(w[0] if ok else 0.0)
+    mc = float(np.mean(acc))
+    # midpoint quadrature in (cos theta, phi)
+    N = 200
+    tot = 0.0
+    for i in range(N):
+        ct = (i + 0.5) / N
+        st = math.sqrt(1 - ct * ct)
+        for j in range(2 * N):
+            ph = (j + 0.5) / (2 * N) * 2 * math.pi
+            wi = np.array([st * math.cos(ph), st * math.sin(ph), ct], np.float32)
+            f, _ = oracle.bsdf_eval(m, n, wo, wi)
+            tot += f[0] * ct
+    quad = tot * (1.0 / N) * (2 * math.pi / (2 * N))
+    assert mc == pytest.approx(quad, rel=0.03)
+    wi = np.array([-0.3, 0.2, 0.93], np.float32)
+    wi /= np.linalg.norm(wi)
+    f1, p1 = oracle.bsdf_eval(m, n, wo, wi)
+    f2, p2 = oracle.bsdf_eval(m, n, wi, wo)
+    assert f1[0] == pytest.approx(f2[0], rel=1e-5) and p1 == pytest.approx(p2, rel=1e-5)
+
+
+# --------------------------------------------------------------------------
+# MIS weights (Eq. rhpdf, Eq. neepdf, Eq. photonpdf, Eq. misw): hand-worked
+# --------------------------------------------------------------------------
+def test_mis_length_two_hand_worked(oracle):
+    # camera (0,1,0) -> floor point (0,0,0), normal +y -> light point (0,2,0)
+    # facing down, NEE area pdf p_l = 0.25.
+    # p_e = p_{0->1} p_{1->2} = 1 * (cos/pi = 1/pi) * cos_y / d^2 = 1/(4 pi)
+    # p_E = p_l * p_{0->1} = 0.25
+    verts = [[0, 1, 0, 0, 0, 0, 0], [0, 0, 0, 0, 1, 0, 0]]
+    light = [0, 2, 0, 0, -1, 0, 0.25]
+    w = oracle.mis_weights(verts, light, 0.01, 50.0)
+    pe, pE = 1 / (4 * math.pi), 0.25
+    assert w[0] == pytest.approx(pe / (pe + pE), rel=1e-6)
+    assert w[1] == pytest.approx(pE / (pe + pE), rel=1e-6)
+    assert w.sum() == pytest.approx(1.0)
+
+
+def test_mis_length_three_hand_worked(oracle):
+    """Path x0=(0,1,0) camera, x1=(0,0,0) floor (n=+y), x2=(0,1,1) wall (n=-z),
+    light x3=(0,1,0) facing +z, p_l=0.5, rho=100, r=0.05.
+      F2 = p_{1->2} = (cos_1/pi)(cos_2)/d^2 = (1/sqrt2/pi)(1/sqrt2)/2 = 1/(4 pi)
+      F3 = p_{2->3} = (1/pi)(1)/1 = 1/pi
+      R1 = p_{2->1} = (1/sqrt2/pi)(1/sqrt2)/2 = 1/(4 pi)
+      p_e = F2 F3 = 1/(4 pi^2);  p_E = p_l F2 = 1/(8 pi)
+      n_P p_P1 = p_l rho pi r^2 R1 = 0.5*100*pi*0.0025/(4 pi) = 1/32"""
+    verts = [[0, 1, 0, 0, 0, 0, 0], [0, 0, 0, 0, 1, 0, 0], [0, 1, 1, 0, 0, -1, 0]]
+    light = [0, 1, 0, 0, 0, 1, 0.5]
+    pe, pE, pP = 1 / (4 * math.pi ** 2), 1 / (8 * math.pi), 1 / 32
+    s = pe + pE + pP
+    w = oracle.mis_weights(verts, light, 0.05, 100.0)
+    assert w.tolist() == pytest.approx([pe / s, pE / s, pP / s], rel=1e-5)
+    # strategy mask: without photons the same path is weighted between e and E only
+    w = oracle.mis_weights(verts, light, 0.05, 100.0, mask=3)
+    assert w.tolist() == pytest.approx([pe / (pe + pE), pE / (pe + pE), 0.0], rel=1e-5)
+    # rho = 0 (no density) removes the photon strategy
+    w = oracle.mis_weights(verts, light, 0.05, 0.0)
+    assert w[2] == 0.0
+
+
+def test_mis_delta_vertices(oracle):
+    verts = [[0, 1, 0, 0, 0, 0, 0], [0, 0, 0, 0, 1, 0, 0], [0, 1, 1, 0, 0, -1, 1]]
+    light = [0, 1, 0, 0, 0, 1, 0.5]
+    w = oracle.mis_weights(verts, light, 0.05, 100.0)
+    assert w[1] == 0.0                      # no NEE at a delta vertex
+    # pdf at the delta vertex x2 is 1: F3 = 1 * 1 / 1, R1 = 1 * (1/sqrt2) / 2
+    pe = 1 / (4 * math.pi) * 1.0
+    pP = 0.5 * 100 * math.pi * 0.0025 * (1 / (2 * math.sqrt(2)))
+    assert w[0] == pytest.approx(pe / (pe + pP), rel=1e-5)
+    verts[1][6] = 1                         # merge vertex on glass: no merge strategy
+    verts[2][6] = 0
+    w = oracle.mis_weights(verts, light, 0.05, 100.0)
+    assert w[2] == 0.0 and w[0] + w[1] == pytest.approx(1.0)
