@@ -1,0 +1,174 @@
+/*
+ * neb.h -- C ABI of the GB300 (sm_103a) Next Event Backtracking library,
+ * libneb.so.  Jendersie, "Next Event Backtracking" (arXiv 1909.00573).
+ *
+ * One iteration (neb_iterate) runs the three passes of the method's outline
+ * (Sec. 3, Fig. 2) entirely in CUDA kernels on one GPU:
+ *   pass 1  view paths; every view vertex where NEE is attempted is stored
+ *           and counted in the density octree (Sec. 3.1, Sec. 5.1);
+ *   pass 2  density rho at each NEE vertex (Eq. octdensity), NEE
+ *           contributions (Sec. 3.2), photons Phi = dE / rho (Eq. flux)
+ *           walked from the NEE vertices and merged at view vertices (Sec. 3.2);
+ *   pass 3  self emission of stored random hits (Sec. 3.3),
+ * weighted by the balance heuristic over all strategies (Sec. 4, Eq. misw).
+ *
+ * Conventions for every entry point:
+ *  - Return value: NEB_OK (0) or a negative NEB_ERR_* code; the message of the
+ *    last failure on a context is returned by neb_last_error().
+ *  - Host pointers are borrowed for the duration of the call only (data is
+ *    copied); the library never keeps or frees caller memory.
+ *  - A context owns all of its device memory and its work runs in order on
+ *    the CUDA stream given to neb_create (the caller's stream, e.g. the
+ *    current PyTorch stream, or NULL for a stream the library creates).
+ *    Entry points that return host data synchronise that stream.
+ *  - Contexts are not thread-safe; use one context per host thread.
+ *  - Layouts of scene arrays are those of paper_1909_00573_gb300/scenes.py:
+ *    tri [nt][3][3] float, tri_mat [nt] uint32, sph [ns][4] float (centre,
+ *    radius), sph_mat [ns] uint32, mats [nm][12] float (type, albedo rgb,
+ *    emission rgb, ior, alpha, pad), cam [10] float (eye, target, up, vfov).
+ */
+#ifndef NEB_H
+#define NEB_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  NEB_OK = 0,
+  NEB_ERR_ARG = -1,            /* invalid argument or call order */
+  NEB_ERR_OOM = -2,            /* device allocation failed */
+  NEB_ERR_CUDA = -3,           /* a CUDA runtime call failed */
+  NEB_ERR_DEVICE_TIMEOUT = -4, /* a bounded device spin-wait expired (octree split) */
+  NEB_ERR_QUEUE_OVERFLOW = -5, /* a device work queue or stack overflowed */
+  NEB_ERR_NO_DEVICE = -6       /* no CUDA device */
+};
+
+/* device status word bits, reported by neb_get_stats() */
+enum {
+  NEB_STATUS_SPIN_TIMEOUT = 1u,   /* an octree insert gave up waiting for a child pointer */
+  NEB_STATUS_QUEUE_OVERFLOW = 2u, /* an append found its queue full */
+  NEB_STATUS_STACK_OVERFLOW = 4u, /* a BVH traversal stack overflowed */
+  NEB_STATUS_OCTREE_FULL = 8u     /* octree allocation overflow (not an error: Appendix B) */
+};
+
+typedef struct {
+  int width, height;     /* image size; one camera path per pixel per iteration */
+  int max_depth;         /* D: maximum path length in segments, 1 <= D <= 64 */
+  float merge_radius;    /* r of the uniform kernel 1/(pi r^2) (Sec. 3.2) */
+  int octree_capacity;   /* nodes; rounded up to 8n+1 (Appendix B initialize) */
+  int split_factor;      /* SPLIT_FACTOR of Appendix B (paper: 4) */
+  uint64_t seed;         /* Philox4x32-10 key */
+  int octree_mode;       /* 0 concurrent lock-free inserts, 1 sequential in (pixel, k) order */
+  int density_mode;      /* 0 robust median of five (get_density_robust), 1 single query */
+  uint32_t strategy_mask;/* bit 0 random hit (e), bit 1 NEE (E), bit 2 NEB photon merge (P) */
+  int keep_split;        /* nonzero: keep the last iteration's contributions split by strategy */
+} neb_config;
+
+typedef struct {
+  int64_t iterations;
+  int64_t camera_rays, nee_vertices, shadow_rays, photons, photon_hits;
+  int64_t merge_tests, merges, random_hits;
+  int64_t octree_inserts, octree_queries;  /* queries count each of the five robust lookups */
+  int64_t bvh_node_visits, prim_tests;
+  int32_t octree_nodes, octree_depth;
+  uint32_t status;                         /* NEB_STATUS_* bits, sticky */
+  int32_t pad;
+} neb_stats;
+
+typedef struct neb_ctx neb_ctx;
+
+/* Creates a context bound to `cuda_stream` (cudaStream_t or NULL) and sizes
+ * its per-iteration device buffers for cfg (all allocations happen here and
+ * in neb_scene_upload / neb_build_bvh, never in neb_iterate). */
+int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** out);
+void neb_destroy(neb_ctx* ctx);
+const char* neb_last_error(const neb_ctx* ctx);
+
+/* Copies the scene to the device (SoA triangles as float4 v0, v1, v2; spheres;
+ * materials), builds the light list (emissive triangles in index order, then
+ * spheres) with power-proportional selection through an alias table (Vose
+ * 1991), and derives the octree box from the scene bounds (Appendix B
+ * initialize: enlarged by 1.002).  Resets the accumulation. */
+int neb_scene_upload(neb_ctx* ctx, const float* tri, const uint32_t* tri_mat, int nt,
+                     const float* sph, const uint32_t* sph_mat, int ns,
+                     const float* mats, int nm, const float* cam);
+
+/* Builds the BVH on the device: 30-bit Morton codes of primitive centroids,
+ * stable 4-bit LSD radix sort, Karras (HPG 2012) hierarchy, bottom-up bounds. */
+int neb_build_bvh(neb_ctx* ctx);
+
+/* Enqueues n_iterations NEB iterations on the context stream (asynchronous).
+ * Iteration indices continue from the previous call (1-based). */
+int neb_iterate(neb_ctx* ctx, int n_iterations);
+
+/* Progressive result: FP64 per-pixel sums divided by the iteration count,
+ * written as [H][W][3] float.  out_is_device: nonzero if rgb_out is device
+ * memory (written on the context stream), zero for host memory (synchronises). */
+int neb_resolve(neb_ctx* ctx, float* rgb_out, int out_is_device);
+
+/* Raw FP64 sums [H][W][3] (host memory; synchronises). */
+int neb_read_accum(neb_ctx* ctx, double* out);
+
+/* Last iteration's contributions split by strategy [3][H][W][3] (0 random hit,
+ * 1 NEE, 2 photon merge); requires cfg.keep_split.  Host memory. */
+int neb_read_split(neb_ctx* ctx, double* out);
+
+/* Density rho at every NEE vertex of the last iteration, [H*W][D-1] indexed
+ * pixel*(D-1) + (k-1); -1 where the path has no NEE vertex k.  Host memory. */
+int neb_read_nee_rho(neb_ctx* ctx, float* out);
+
+/* Counters accumulated since the scene upload, plus the device status word.
+ * Synchronises.  Returns NEB_ERR_DEVICE_TIMEOUT / NEB_ERR_QUEUE_OVERFLOW if the
+ * corresponding status bit is set (the stats are filled in either case). */
+int neb_get_stats(neb_ctx* ctx, neb_stats* out);
+
+/* Per-stage device times in milliseconds, accumulated over iterations since
+ * profiling was enabled (CUDA events on the context stream around each
+ * stage).  names receives up to max_stages NUL-terminated names of <= 31
+ * chars (32 bytes each); returns the number of stages. */
+int neb_set_profiling(neb_ctx* ctx, int enable);
+int neb_get_stage_times(neb_ctx* ctx, double* ms, int64_t* launches, char* names, int max_stages);
+
+/* ---------------- component entry points (tests and tools) --------------- */
+
+/* Closest hit of n rays [n][6] (origin, unit direction) through the BVH:
+ * prim index (-1 on a miss; triangles first, then spheres) and distance. */
+int neb_trace_closest(neb_ctx* ctx, const float* rays, int n, int32_t* out_prim, float* out_t);
+
+/* Philox4x32-10 on the device: n counters [n][4] under one key -> [n][4]. */
+int neb_philox(const uint32_t* ctr, int n, const uint32_t key[2], uint32_t* out);
+
+/* Plane/box intersection area of Eq. area with the listing's 1D/2D
+ * thresholds (Appendix B intersection_area), evaluated on the device for n
+ * cases: boxes [n][6] (min, max), positions [n][3], normals [n][3]. */
+int neb_plane_box_area(const float* boxes, const float* pos, const float* nrm, int n, float* out);
+
+/* Stand-alone density octree (Sec. 5, Appendix B) on the device. */
+typedef struct neb_octree neb_octree;
+int neb_octree_create(const float scene_min[3], const float scene_max[3], int capacity,
+                      int split_factor, void* cuda_stream, neb_octree** out);
+void neb_octree_destroy(neb_octree* o);
+/* set_iteration of the listing: scales, threshold, re-arm of unused nodes */
+int neb_octree_set_iteration(neb_octree* o, int iter);
+/* Inserts n positions [n][3]: mode 0 concurrent (one thread per position,
+ * lock-free CAS counting and splitting with a bounded spin), mode 1 one
+ * device thread in array order (identical to the sequential listing). */
+int neb_octree_insert(neb_octree* o, const float* pos, int n, int mode);
+/* get_density (robust = 0) or get_density_robust (robust = 1), FP64
+ * normalisation, for n positions / geometric normals [n][3]. */
+int neb_octree_density(neb_octree* o, const float* pos, const float* nrm, int n, int robust, float* out);
+/* Copies the node array (capacity entries) and meta = {alloc, depth, capacity, status}. */
+int neb_octree_read(neb_octree* o, int32_t* nodes, int n_nodes, int32_t meta[4]);
+
+/* Merge candidate search through the device hashed grid (cell size 2r, the
+ * structure used by the photon merge): for each query, the number of points
+ * with |p - q|^2 <= r^2 evaluated in FP32. */
+int neb_count_neighbours(const float* pts, int n, const float* queries, int m, float r, int32_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,525 @@
+// neb_api.cu -- the C ABI of libneb.so: context lifetime, scene upload
+// (materials, light list and alias table), iteration, readback, statistics.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "neb_device.cuh"
+#include "neb_internal.h"
+
+using namespace neb;
+
+namespace neb {
+SceneView scene_view(const neb_ctx* c) {
+  SceneView s;
+  s.tv0 = c->tv0;
+  s.tv1 = c->tv1;
+  s.tv2 = c->tv2;
+  s.sph = c->sph;
+  s.sph_mat = c->sph_mat;
+  s.mats = c->mats;
+  s.nodes = c->nodes;
+  s.prim_light = c->prim_light;
+  s.light_prim = c->light_prim;
+  s.light_psel = c->light_psel;
+  s.light_inv_area = c->light_inv_area;
+  s.alias_prob = c->alias_prob;
+  s.alias_idx = c->alias_idx;
+  s.nt = c->nt;
+  s.ns = c->ns;
+  s.nl = c->nl;
+  return s;
+}
+}  // namespace neb
+
+static int fail(neb_ctx* c, int code, const char* what, cudaError_t e = cudaSuccess) {
+  if (c) {
+    char buf[512];
+    if (e != cudaSuccess)
+      snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    else
+      snprintf(buf, sizeof(buf), "%s", what);
+    c->err = buf;
+  }
+  return code;
+}
+
+template <typename T>
+static cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, sizeof(T) * count);
+}
+
+static void free_scene(neb_ctx* c) {
+  cudaFree(c->tv0); cudaFree(c->tv1); cudaFree(c->tv2); cudaFree(c->sph); cudaFree(c->mats); cudaFree(c->sph_mat);
+  cudaFree(c->prim_light); cudaFree(c->light_prim); cudaFree(c->alias_idx); cudaFree(c->light_psel);
+  cudaFree(c->light_inv_area); cudaFree(c->alias_prob); cudaFree(c->nodes); cudaFree(c->oct_nodes);
+  cudaFree(c->oct_state);
+  c->tv0 = c->tv1 = c->tv2 = c->sph = c->mats = nullptr;
+  c->sph_mat = c->prim_light = c->light_prim = c->alias_idx = nullptr;
+  c->light_psel = c->light_inv_area = c->alias_prob = nullptr;
+  c->nodes = nullptr;
+  c->oct_nodes = nullptr;
+  c->oct_state = nullptr;
+  c->scene_ready = c->bvh_ready = false;
+}
+
+extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** out) {
+  if (!cfg || !out) return NEB_ERR_ARG;
+  *out = nullptr;
+  if (cfg->width < 1 || cfg->height < 1 || cfg->max_depth < 1 || cfg->max_depth > kMaxDepth ||
+      !(cfg->merge_radius > 0.0f) || cfg->octree_capacity < 1 || cfg->split_factor < 1 ||
+      (cfg->octree_mode != 0 && cfg->octree_mode != 1) || (cfg->density_mode != 0 && cfg->density_mode != 1) ||
+      (cfg->strategy_mask & ~7u) || (long long)cfg->width * cfg->height > (1ll << 28))
+    return NEB_ERR_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return NEB_ERR_NO_DEVICE;
+  neb_ctx* c = new (std::nothrow) neb_ctx();
+  if (!c) return NEB_ERR_OOM;
+  c->cfg = *cfg;
+  c->W = cfg->width;
+  c->H = cfg->height;
+  c->D = cfg->max_depth;
+  c->P = c->W * c->H;
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return NEB_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  size_t P = (size_t)c->P, D = (size_t)c->D;
+  c->cap_cam = c->P;
+  c->cap_nee = (int)(P * (D > 1 ? D - 1 : 1));
+  c->cap_rh = (int)(P * D);
+  c->cap_ph = c->cap_nee;
+  uint32_t t = 1024;
+  while (t < (uint32_t)c->cap_nee) t <<= 1;
+  c->table_size = t;
+  c->scan_scratch.n = scan_scratch_ints((size_t)t + 1);
+  bool ok = dalloc(&c->camq[0], P) == cudaSuccess && dalloc(&c->camq[1], P) == cudaSuccess &&
+            dalloc(&c->nv.pos, c->cap_nee) == cudaSuccess && dalloc(&c->nv.nrm, c->cap_nee) == cudaSuccess &&
+            dalloc(&c->nv.wo, c->cap_nee) == cudaSuccess && dalloc(&c->nv.tau, c->cap_nee) == cudaSuccess &&
+            dalloc(&c->nv.err, c->cap_nee) == cudaSuccess && dalloc(&c->nv.ldir, c->cap_nee) == cudaSuccess &&
+            dalloc(&c->nv.dE, c->cap_nee) == cudaSuccess && dalloc(&c->rh, c->cap_rh) == cudaSuccess &&
+            dalloc(&c->phq[0], c->cap_ph) == cudaSuccess && dalloc(&c->phq[1], c->cap_ph) == cudaSuccess &&
+            dalloc(&c->mrec, c->cap_nee) == cudaSuccess && dalloc(&c->vert_bucket, c->cap_nee) == cudaSuccess &&
+            dalloc(&c->bucket_count, (size_t)t + 1) == cudaSuccess &&
+            dalloc(&c->bucket_start, (size_t)t + 1) == cudaSuccess &&
+            dalloc(&c->scan_scratch.data, c->scan_scratch.n) == cudaSuccess &&
+            dalloc(&c->accum, P * 3) == cudaSuccess && dalloc(&c->counters, 1) == cudaSuccess &&
+            (!cfg->keep_split || dalloc(&c->split, P * 9) == cudaSuccess) &&
+            (cfg->octree_mode != 1 || dalloc(&c->slot_map, P * (D > 1 ? D - 1 : 1)) == cudaSuccess);
+  if (!ok) {
+    neb_destroy(c);
+    return NEB_ERR_OOM;
+  }
+  cudaMemsetAsync(c->bucket_count, 0, sizeof(int) * ((size_t)t + 1), c->stream);
+  cudaMemsetAsync(c->accum, 0, sizeof(double) * P * 3, c->stream);
+  cudaMemsetAsync(c->counters, 0, sizeof(DevCounters), c->stream);
+  if (c->split) cudaMemsetAsync(c->split, 0, sizeof(double) * P * 9, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    neb_destroy(c);
+    return NEB_ERR_CUDA;
+  }
+  *out = c;
+  return NEB_OK;
+}
+
+extern "C" void neb_destroy(neb_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_scene(c);
+  cudaFree(c->camq[0]); cudaFree(c->camq[1]);
+  cudaFree(c->nv.pos); cudaFree(c->nv.nrm); cudaFree(c->nv.wo); cudaFree(c->nv.tau); cudaFree(c->nv.err);
+  cudaFree(c->nv.ldir); cudaFree(c->nv.dE);
+  cudaFree(c->rh); cudaFree(c->phq[0]); cudaFree(c->phq[1]); cudaFree(c->mrec); cudaFree(c->vert_bucket);
+  cudaFree(c->bucket_count); cudaFree(c->bucket_start); cudaFree(c->scan_scratch.data); cudaFree(c->accum);
+  cudaFree(c->split); cudaFree(c->counters); cudaFree(c->slot_map);
+  for (auto& ev : c->ev)
+    if (ev) cudaEventDestroy(ev);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+extern "C" const char* neb_last_error(const neb_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+static float i2f(int i) {
+  float f;
+  memcpy(&f, &i, sizeof(f));
+  return f;
+}
+
+static float3 hnorm(float3 a) {
+  float l = sqrtf(a.x * a.x + a.y * a.y + a.z * a.z);
+  float inv = 1.0f / l;
+  return make_float3(a.x * inv, a.y * inv, a.z * inv);
+}
+static float3 hcross(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+static float3 hsub(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+
+extern "C" int neb_scene_upload(neb_ctx* c, const float* tri, const uint32_t* tri_mat, int nt, const float* sph,
+                                const uint32_t* sph_mat, int ns, const float* mats, int nm, const float* cam) {
+  if (!c) return NEB_ERR_ARG;
+  if (nt < 0 || ns < 0 || nm < 1 || !mats || !cam || (nt > 0 && (!tri || !tri_mat)) ||
+      (ns > 0 && (!sph || !sph_mat)) || nt + ns < 1)
+    return fail(c, NEB_ERR_ARG, "neb_scene_upload: bad arguments");
+  for (int i = 0; i < nt; ++i)
+    if (tri_mat[i] >= (uint32_t)nm) return fail(c, NEB_ERR_ARG, "neb_scene_upload: triangle material out of range");
+  for (int i = 0; i < ns; ++i)
+    if (sph_mat[i] >= (uint32_t)nm) return fail(c, NEB_ERR_ARG, "neb_scene_upload: sphere material out of range");
+  cudaStreamSynchronize(c->stream);
+  free_scene(c);
+  c->nt = nt;
+  c->ns = ns;
+  c->nm = nm;
+  // ---- host-side repacking into the device layouts
+  std::vector<float4> v0(nt), v1(nt), v2(nt), sp(ns), mt(3 * (size_t)nm);
+  std::vector<int> smat(ns);
+  for (int i = 0; i < nt; ++i) {
+    const float* t = tri + 9 * (size_t)i;
+    v0[i] = make_float4(t[0], t[1], t[2], i2f((int)tri_mat[i]));
+    v1[i] = make_float4(t[3], t[4], t[5], 0.0f);
+    v2[i] = make_float4(t[6], t[7], t[8], 0.0f);
+  }
+  for (int i = 0; i < ns; ++i) {
+    sp[i] = make_float4(sph[4 * i], sph[4 * i + 1], sph[4 * i + 2], sph[4 * i + 3]);
+    smat[i] = (int)sph_mat[i];
+  }
+  for (int m = 0; m < nm; ++m) {
+    const float* r = mats + 12 * (size_t)m;
+    mt[3 * m] = make_float4(i2f((int)r[0]), r[1], r[2], r[3]);
+    mt[3 * m + 1] = make_float4(r[4], r[5], r[6], r[7]);
+    mt[3 * m + 2] = make_float4(r[8], 0.0f, 0.0f, 0.0f);
+  }
+  // ---- light list: emissive triangles in index order, then emissive spheres
+  int np = nt + ns;
+  std::vector<int> prim_light(np, -1), light_prim;
+  std::vector<double> power;
+  std::vector<float> inv_area;
+  const double PI = 3.14159265358979323846;
+  for (int p = 0; p < np; ++p) {
+    int m = p < nt ? (int)tri_mat[p] : (int)sph_mat[p - nt];
+    const float* e = mats + 12 * (size_t)m + 4;
+    double le = ((double)e[0] + (double)e[1] + (double)e[2]) / 3.0;
+    if (le <= 0.0) continue;
+    if (p < nt) {
+      const float* t = tri + 9 * (size_t)p;
+      float3 a = make_float3(t[0], t[1], t[2]), b = make_float3(t[3], t[4], t[5]), cc = make_float3(t[6], t[7], t[8]);
+      float3 cr = hcross(hsub(b, a), hsub(cc, a));
+      double area = 0.5 * sqrt((double)cr.x * cr.x + (double)cr.y * cr.y + (double)cr.z * cr.z);
+      float fa = (float)area;
+      power.push_back(PI * area * le);
+      inv_area.push_back(1.0f / fa);
+    } else {
+      double R = sph[4 * (size_t)(p - nt) + 3];
+      power.push_back(4.0 * PI * PI * R * R * le);
+      inv_area.push_back((float)(1.0 / (2.0 * PI * R * R)));
+    }
+    prim_light[p] = (int)light_prim.size();
+    light_prim.push_back(p);
+  }
+  int nl = (int)light_prim.size();
+  c->nl = nl;
+  // alias table, Vose (1991): worklists used as stacks filled in index order
+  std::vector<float> psel(nl), aprob(nl);
+  std::vector<int> aidx(nl);
+  if (nl > 0) {
+    double total = 0.0;
+    for (int i = 0; i < nl; ++i) total += power[i];
+    std::vector<double> pp(nl);
+    std::vector<int> small, large;
+    for (int i = 0; i < nl; ++i) {
+      psel[i] = (float)(power[i] / total);
+      pp[i] = power[i] * (double)nl / total;
+      aidx[i] = i;
+      if (pp[i] < 1.0) small.push_back(i); else large.push_back(i);
+    }
+    while (!small.empty() && !large.empty()) {
+      int l = small.back(); small.pop_back();
+      int g = large.back(); large.pop_back();
+      aprob[l] = (float)pp[l];
+      aidx[l] = g;
+      pp[g] = (pp[g] + pp[l]) - 1.0;
+      if (pp[g] < 1.0) small.push_back(g); else large.push_back(g);
+    }
+    while (!large.empty()) { aprob[large.back()] = 1.0f; large.pop_back(); }
+    while (!small.empty()) { aprob[small.back()] = 1.0f; small.pop_back(); }
+  }
+  // scene bounds
+  for (int k = 0; k < 3; ++k) { c->bmin[k] = 3.402823466e+38f; c->bmax[k] = -3.402823466e+38f; }
+  for (size_t i = 0; i < (size_t)nt * 3; ++i)
+    for (int k = 0; k < 3; ++k) {
+      float v = tri[i * 3 + k];
+      if (v < c->bmin[k]) c->bmin[k] = v;
+      if (v > c->bmax[k]) c->bmax[k] = v;
+    }
+  for (int i = 0; i < ns; ++i)
+    for (int k = 0; k < 3; ++k) {
+      float ce = sph[4 * (size_t)i + k], r = sph[4 * (size_t)i + 3];
+      if (ce - r < c->bmin[k]) c->bmin[k] = ce - r;
+      if (ce + r > c->bmax[k]) c->bmax[k] = ce + r;
+    }
+  // camera basis (pinhole)
+  {
+    float3 eye = make_float3(cam[0], cam[1], cam[2]), target = make_float3(cam[3], cam[4], cam[5]),
+           up = make_float3(cam[6], cam[7], cam[8]);
+    c->cam.eye = eye;
+    c->cam.fwd = hnorm(hsub(target, eye));
+    c->cam.right = hnorm(hcross(c->cam.fwd, up));
+    c->cam.up = hcross(c->cam.right, c->cam.fwd);
+    c->cam.tanh_ = tanf(cam[9] * 3.14159265358979323846f / 360.0f);
+    c->cam.aspect = (float)c->W / (float)c->H;
+  }
+  // ---- device copies
+  cudaStream_t st = c->stream;
+  bool ok = dalloc(&c->tv0, nt) == cudaSuccess && dalloc(&c->tv1, nt) == cudaSuccess &&
+            dalloc(&c->tv2, nt) == cudaSuccess && dalloc(&c->sph, ns) == cudaSuccess &&
+            dalloc(&c->sph_mat, ns) == cudaSuccess && dalloc(&c->mats, 3 * (size_t)nm) == cudaSuccess &&
+            dalloc(&c->prim_light, np) == cudaSuccess && dalloc(&c->light_prim, nl) == cudaSuccess &&
+            dalloc(&c->light_psel, nl) == cudaSuccess && dalloc(&c->light_inv_area, nl) == cudaSuccess &&
+            dalloc(&c->alias_prob, nl) == cudaSuccess && dalloc(&c->alias_idx, nl) == cudaSuccess;
+  c->oct = octree_params(c->bmin, c->bmax, c->cfg.octree_capacity, c->cfg.split_factor);
+  c->oct_cap = c->oct.capacity;
+  ok = ok && dalloc(&c->oct_nodes, (size_t)c->oct_cap) == cudaSuccess && dalloc(&c->oct_state, 1) == cudaSuccess;
+  if (!ok) {
+    free_scene(c);
+    return fail(c, NEB_ERR_OOM, "neb_scene_upload: device allocation failed");
+  }
+  if (nt) {
+    cudaMemcpyAsync(c->tv0, v0.data(), sizeof(float4) * nt, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->tv1, v1.data(), sizeof(float4) * nt, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->tv2, v2.data(), sizeof(float4) * nt, cudaMemcpyHostToDevice, st);
+  }
+  if (ns) {
+    cudaMemcpyAsync(c->sph, sp.data(), sizeof(float4) * ns, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->sph_mat, smat.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st);
+  }
+  cudaMemcpyAsync(c->mats, mt.data(), sizeof(float4) * 3 * nm, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(c->prim_light, prim_light.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st);
+  if (nl) {
+    cudaMemcpyAsync(c->light_prim, light_prim.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->light_psel, psel.data(), sizeof(float) * nl, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->light_inv_area, inv_area.data(), sizeof(float) * nl, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->alias_prob, aprob.data(), sizeof(float) * nl, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(c->alias_idx, aidx.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, st);
+  }
+  OctreeState s0{1, 0, 0, 0};
+  cudaMemsetAsync(c->oct_nodes, 0, sizeof(int) * (size_t)c->oct_cap, st);
+  cudaMemcpyAsync(c->oct_state, &s0, sizeof(s0), cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(c->accum, 0, sizeof(double) * 3 * (size_t)c->P, st);
+  cudaMemsetAsync(c->counters, 0, sizeof(DevCounters), st);
+  c->iteration = 0;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(c, NEB_ERR_CUDA, "neb_scene_upload", e);
+  c->scene_ready = true;
+  return NEB_OK;
+}
+
+extern "C" int neb_build_bvh(neb_ctx* c) {
+  if (!c) return NEB_ERR_ARG;
+  if (!c->scene_ready) return fail(c, NEB_ERR_ARG, "neb_build_bvh: no scene uploaded");
+  cudaError_t e = build_bvh(c);
+  if (e != cudaSuccess) return fail(c, e == cudaErrorMemoryAllocation ? NEB_ERR_OOM : NEB_ERR_CUDA, "neb_build_bvh", e);
+  c->bvh_ready = true;
+  return NEB_OK;
+}
+
+extern "C" int neb_iterate(neb_ctx* c, int n_iterations) {
+  if (!c || n_iterations < 0) return NEB_ERR_ARG;
+  if (!c->bvh_ready) return fail(c, NEB_ERR_ARG, "neb_iterate: call neb_scene_upload and neb_build_bvh first");
+  for (int i = 0; i < n_iterations; ++i) {
+    cudaError_t e = run_iteration(c, c->iteration + 1);
+    if (e != cudaSuccess) return fail(c, NEB_ERR_CUDA, "neb_iterate", e);
+    c->iteration += 1;
+  }
+  return NEB_OK;
+}
+
+extern "C" int neb_resolve(neb_ctx* c, float* rgb_out, int out_is_device) {
+  if (!c || !rgb_out) return NEB_ERR_ARG;
+  size_t n = (size_t)c->P * 3;
+  if (out_is_device) {
+    cudaError_t e = launch_resolve(c->accum, c->P, c->iteration, rgb_out, c->stream);
+    return e == cudaSuccess ? NEB_OK : fail(c, NEB_ERR_CUDA, "neb_resolve", e);
+  }
+  float* d = nullptr;
+  cudaError_t e = cudaMallocAsync(&d, sizeof(float) * n, c->stream);
+  if (e != cudaSuccess) return fail(c, NEB_ERR_OOM, "neb_resolve", e);
+  launch_resolve(c->accum, c->P, c->iteration, d, c->stream);
+  cudaMemcpyAsync(rgb_out, d, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream);
+  cudaFreeAsync(d, c->stream);
+  e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? NEB_OK : fail(c, NEB_ERR_CUDA, "neb_resolve", e);
+}
+
+extern "C" int neb_read_accum(neb_ctx* c, double* out) {
+  if (!c || !out) return NEB_ERR_ARG;
+  cudaMemcpyAsync(out, c->accum, sizeof(double) * 3 * (size_t)c->P, cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? NEB_OK : fail(c, NEB_ERR_CUDA, "neb_read_accum", e);
+}
+
+extern "C" int neb_read_split(neb_ctx* c, double* out) {
+  if (!c || !out) return NEB_ERR_ARG;
+  if (!c->split) return fail(c, NEB_ERR_ARG, "neb_read_split: context created without keep_split");
+  cudaMemcpyAsync(out, c->split, sizeof(double) * 9 * (size_t)c->P, cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? NEB_OK : fail(c, NEB_ERR_CUDA, "neb_read_split", e);
+}
+
+extern "C" int neb_read_nee_rho(neb_ctx* c, float* out) {
+  if (!c || !out) return NEB_ERR_ARG;
+  if (c->D < 2) return fail(c, NEB_ERR_ARG, "neb_read_nee_rho: max_depth < 2 has no NEE vertices");
+  size_t n = (size_t)c->P * (c->D - 1);
+  float* d = nullptr;
+  cudaError_t e = cudaMallocAsync(&d, sizeof(float) * n, c->stream);
+  if (e != cudaSuccess) return fail(c, NEB_ERR_OOM, "neb_read_nee_rho", e);
+  launch_read_rho(c, d);
+  cudaMemcpyAsync(out, d, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream);
+  cudaFreeAsync(d, c->stream);
+  e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? NEB_OK : fail(c, NEB_ERR_CUDA, "neb_read_nee_rho", e);
+}
+
+extern "C" int neb_get_stats(neb_ctx* c, neb_stats* out) {
+  if (!c || !out) return NEB_ERR_ARG;
+  DevCounters h;
+  OctreeState os{};
+  cudaMemcpyAsync(&h, c->counters, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+  if (c->oct_state) cudaMemcpyAsync(&os, c->oct_state, sizeof(os), cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(c, NEB_ERR_CUDA, "neb_get_stats", e);
+  memset(out, 0, sizeof(*out));
+  out->iterations = c->iteration;
+  out->camera_rays = (int64_t)h.camera_rays;
+  out->nee_vertices = (int64_t)h.nee_vertices;
+  out->shadow_rays = (int64_t)h.shadow_rays;
+  out->photons = (int64_t)h.photons;
+  out->photon_hits = (int64_t)h.photon_hits;
+  out->merge_tests = (int64_t)h.merge_tests;
+  out->merges = (int64_t)h.merges;
+  out->random_hits = (int64_t)h.random_hits;
+  out->octree_inserts = (int64_t)h.octree_inserts;
+  out->octree_queries = (int64_t)h.octree_queries;
+  out->bvh_node_visits = (int64_t)h.node_visits;
+  out->prim_tests = (int64_t)h.prim_tests;
+  out->octree_nodes = os.alloc < c->oct_cap ? os.alloc : c->oct_cap;
+  out->octree_depth = os.depth;
+  out->status = h.status | os.status;
+  if (out->status & NEB_STATUS_SPIN_TIMEOUT) return fail(c, NEB_ERR_DEVICE_TIMEOUT, "octree insert spin timed out");
+  if (out->status & (NEB_STATUS_QUEUE_OVERFLOW | NEB_STATUS_STACK_OVERFLOW))
+    return fail(c, NEB_ERR_QUEUE_OVERFLOW, "device queue or traversal stack overflowed");
+  return NEB_OK;
+}
+
+static const char* kStageNames[STAGE_COUNT] = {"rearm",   "camera",  "extend",   "shadow", "octree_insert",
+                                               "density", "nee_emit", "grid_build", "emission", "photon"};
+
+extern "C" int neb_set_profiling(neb_ctx* c, int enable) {
+  if (!c) return NEB_ERR_ARG;
+  if (enable && !c->ev[0]) {
+    for (int i = 0; i < 128; ++i)
+      if (cudaEventCreate(&c->ev[i]) != cudaSuccess) return fail(c, NEB_ERR_CUDA, "neb_set_profiling");
+  }
+  c->profiling = enable != 0;
+  for (int i = 0; i < STAGE_COUNT; ++i) {
+    c->stage_ms[i] = 0.0;
+    c->stage_launches[i] = 0;
+  }
+  return NEB_OK;
+}
+
+extern "C" int neb_get_stage_times(neb_ctx* c, double* ms, int64_t* launches, char* names, int max_stages) {
+  if (!c) return NEB_ERR_ARG;
+  int n = max_stages < STAGE_COUNT ? max_stages : STAGE_COUNT;
+  for (int i = 0; i < n; ++i) {
+    if (ms) ms[i] = c->stage_ms[i];
+    if (launches) launches[i] = c->stage_launches[i];
+    if (names) {
+      strncpy(names + 32 * i, kStageNames[i], 31);
+      names[32 * i + 31] = 0;
+    }
+  }
+  return STAGE_COUNT;
+}
+
+extern "C" int neb_trace_closest(neb_ctx* c, const float* rays, int n, int32_t* out_prim, float* out_t) {
+  if (!c || n < 0 || (n > 0 && (!rays || !out_prim || !out_t))) return NEB_ERR_ARG;
+  if (!c->bvh_ready) return fail(c, NEB_ERR_ARG, "neb_trace_closest: no BVH");
+  if (n == 0) return NEB_OK;
+  float* d = nullptr;
+  size_t bytes = sizeof(float) * 6 * (size_t)n + sizeof(int) * (size_t)n + sizeof(float) * (size_t)n;
+  cudaError_t e = cudaMallocAsync(&d, bytes, c->stream);
+  if (e != cudaSuccess) return fail(c, NEB_ERR_OOM, "neb_trace_closest", e);
+  int* dp = reinterpret_cast<int*>(d + 6 * (size_t)n);
+  float* dt = reinterpret_cast<float*>(dp + n);
+  cudaMemcpyAsync(d, rays, sizeof(float) * 6 * (size_t)n, cudaMemcpyHostToDevice, c->stream);
+  launch_trace_debug(scene_view(c), d, n, dp, dt, &c->counters->status, c->stream);
+  cudaMemcpyAsync(out_prim, dp, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+  cudaMemcpyAsync(out_t, dt, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+  cudaFreeAsync(d, c->stream);
+  e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? NEB_OK : fail(c, NEB_ERR_CUDA, "neb_trace_closest", e);
+}
+
+extern "C" int neb_philox(const uint32_t* ctr, int n, const uint32_t key[2], uint32_t* out) {
+  if (n < 0 || (n > 0 && (!ctr || !out || !key))) return NEB_ERR_ARG;
+  if (n == 0) return NEB_OK;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return NEB_ERR_NO_DEVICE;
+  uint32_t* d = nullptr;
+  if (cudaMalloc(&d, sizeof(uint32_t) * 8 * (size_t)n) != cudaSuccess) return NEB_ERR_OOM;
+  cudaMemcpy(d, ctr, sizeof(uint32_t) * 4 * (size_t)n, cudaMemcpyHostToDevice);
+  launch_philox(d, n, make_uint2(key[0], key[1]), d + 4 * (size_t)n, 0);
+  cudaError_t e = cudaMemcpy(out, d + 4 * (size_t)n, sizeof(uint32_t) * 4 * (size_t)n, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess ? NEB_OK : NEB_ERR_CUDA;
+}
+
+extern "C" int neb_plane_box_area(const float* boxes, const float* pos, const float* nrm, int n, float* out) {
+  if (n < 0 || (n > 0 && (!boxes || !pos || !nrm || !out))) return NEB_ERR_ARG;
+  if (n == 0) return NEB_OK;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return NEB_ERR_NO_DEVICE;
+  float* d = nullptr;
+  if (cudaMalloc(&d, sizeof(float) * 13 * (size_t)n) != cudaSuccess) return NEB_ERR_OOM;
+  cudaMemcpy(d, boxes, sizeof(float) * 6 * (size_t)n, cudaMemcpyHostToDevice);
+  cudaMemcpy(d + 6 * (size_t)n, pos, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice);
+  cudaMemcpy(d + 9 * (size_t)n, nrm, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice);
+  launch_area(d, d + 6 * (size_t)n, d + 9 * (size_t)n, n, d + 12 * (size_t)n, 0);
+  cudaError_t e = cudaMemcpy(out, d + 12 * (size_t)n, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess ? NEB_OK : NEB_ERR_CUDA;
+}
+
+extern "C" int neb_count_neighbours(const float* pts, int n, const float* queries, int m, float r, int32_t* out) {
+  if (n < 0 || m < 0 || !(r > 0.0f) || (n > 0 && !pts) || (m > 0 && (!queries || !out))) return NEB_ERR_ARG;
+  if (m == 0) return NEB_OK;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return NEB_ERR_NO_DEVICE;
+  float *dp = nullptr, *dq = nullptr;
+  int* dout = nullptr;
+  if (cudaMalloc(&dp, sizeof(float) * 3 * (size_t)(n > 0 ? n : 1)) != cudaSuccess ||
+      cudaMalloc(&dq, sizeof(float) * 3 * (size_t)m) != cudaSuccess ||
+      cudaMalloc(&dout, sizeof(int) * (size_t)m) != cudaSuccess) {
+    cudaFree(dp); cudaFree(dq); cudaFree(dout);
+    return NEB_ERR_OOM;
+  }
+  if (n > 0) cudaMemcpy(dp, pts, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice);
+  cudaMemcpy(dq, queries, sizeof(float) * 3 * (size_t)m, cudaMemcpyHostToDevice);
+  cudaError_t e = count_neighbours_device(dp, n, dq, m, r, dout, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(out, dout, sizeof(int) * (size_t)m, cudaMemcpyDeviceToHost);
+  cudaFree(dp); cudaFree(dq); cudaFree(dout);
+  return e == cudaSuccess ? NEB_OK : NEB_ERR_CUDA;
+}

@@ -1,0 +1,351 @@
+// neb_bvh.cu -- BVH construction on the device (linear BVH: Morton codes,
+// radix sort, Karras' parallel hierarchy, bottom-up bounds) and the small
+// component kernels used by the tests (closest hit, Philox, plane/box area).
+//
+// Karras, "Maximizing Parallelism in the Construction of BVHs, Octrees, and
+// k-d Trees", HPG 2012.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+
+#include "neb_device.cuh"
+#include "neb_internal.h"
+#include "neb_octree.cuh"
+
+namespace neb {
+
+__device__ __forceinline__ int float_to_ordered(float f) {
+  int i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ordered_to_float(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+__device__ __forceinline__ void prim_bounds(const SceneView& s, int p, float3& lo, float3& hi) {
+  if (p < s.nt) {
+    float3 a = xyz(__ldg(s.tv0 + p)), b = xyz(__ldg(s.tv1 + p)), c = xyz(__ldg(s.tv2 + p));
+    lo = f3(fminf(a.x, fminf(b.x, c.x)), fminf(a.y, fminf(b.y, c.y)), fminf(a.z, fminf(b.z, c.z)));
+    hi = f3(fmaxf(a.x, fmaxf(b.x, c.x)), fmaxf(a.y, fmaxf(b.y, c.y)), fmaxf(a.z, fmaxf(b.z, c.z)));
+  } else {
+    float4 sp = __ldg(s.sph + (p - s.nt));
+    lo = f3(sp.x - sp.w, sp.y - sp.w, sp.z - sp.w);
+    hi = f3(sp.x + sp.w, sp.y + sp.w, sp.z + sp.w);
+  }
+}
+
+// centroid bounds (ordered-int atomics)
+__global__ void k_centroid_bounds(SceneView s, int n, int* cb) {
+  float3 lo = f3(FLT_MAX, FLT_MAX, FLT_MAX), hi = f3(-FLT_MAX, -FLT_MAX, -FLT_MAX);
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    float3 a, b;
+    prim_bounds(s, p, a, b);
+    float3 c = mul(add(a, b), 0.5f);
+    lo = f3(fminf(lo.x, c.x), fminf(lo.y, c.y), fminf(lo.z, c.z));
+    hi = f3(fmaxf(hi.x, c.x), fmaxf(hi.y, c.y), fmaxf(hi.z, c.z));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
+    lo.y = fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o));
+    lo.z = fminf(lo.z, __shfl_xor_sync(0xffffffffu, lo.z, o));
+    hi.x = fmaxf(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, o));
+    hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
+    hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(cb + 0, float_to_ordered(lo.x));
+    atomicMin(cb + 1, float_to_ordered(lo.y));
+    atomicMin(cb + 2, float_to_ordered(lo.z));
+    atomicMax(cb + 3, float_to_ordered(hi.x));
+    atomicMax(cb + 4, float_to_ordered(hi.y));
+    atomicMax(cb + 5, float_to_ordered(hi.z));
+  }
+}
+
+__device__ __forceinline__ uint32_t expand_bits(uint32_t v) {
+  v = (v * 0x00010001u) & 0xFF0000FFu;
+  v = (v * 0x00000101u) & 0x0F00F00Fu;
+  v = (v * 0x00000011u) & 0xC30C30C3u;
+  v = (v * 0x00000005u) & 0x49249249u;
+  return v;
+}
+
+__global__ void k_morton(SceneView s, int n, const int* cb, uint32_t* keys, int* vals) {
+  float3 lo = f3(ordered_to_float(cb[0]), ordered_to_float(cb[1]), ordered_to_float(cb[2]));
+  float3 hi = f3(ordered_to_float(cb[3]), ordered_to_float(cb[4]), ordered_to_float(cb[5]));
+  float3 ext = sub(hi, lo);
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    float3 a, b;
+    prim_bounds(s, p, a, b);
+    float3 c = mul(add(a, b), 0.5f);
+    float x = ext.x > 0.0f ? (c.x - lo.x) / ext.x : 0.5f;
+    float y = ext.y > 0.0f ? (c.y - lo.y) / ext.y : 0.5f;
+    float z = ext.z > 0.0f ? (c.z - lo.z) / ext.z : 0.5f;
+    uint32_t ix = (uint32_t)fminf(fmaxf(x * 1024.0f, 0.0f), 1023.0f);
+    uint32_t iy = (uint32_t)fminf(fmaxf(y * 1024.0f, 0.0f), 1023.0f);
+    uint32_t iz = (uint32_t)fminf(fmaxf(z * 1024.0f, 0.0f), 1023.0f);
+    keys[p] = (expand_bits(ix) << 2) | (expand_bits(iy) << 1) | expand_bits(iz);
+    vals[p] = p;
+  }
+}
+
+// ---- stable LSD radix sort, 4-bit digits, one element per thread ----------------
+constexpr int kSortThreads = 256;
+
+__global__ void k_digit_hist(const uint32_t* __restrict__ keys, int n, int shift, int nblocks, int* hist) {
+  __shared__ int h[16];
+  if (threadIdx.x < 16) h[threadIdx.x] = 0;
+  __syncthreads();
+  int i = blockIdx.x * kSortThreads + threadIdx.x;
+  if (i < n) atomicAdd(&h[(keys[i] >> shift) & 15u], 1);
+  __syncthreads();
+  if (threadIdx.x < 16) hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void k_digit_scatter(const uint32_t* __restrict__ keys, const int* __restrict__ vals, int n, int shift,
+                                int nblocks, const int* __restrict__ offs, uint32_t* __restrict__ okeys,
+                                int* __restrict__ ovals) {
+  __shared__ int wcount[kSortThreads / 32][16];
+  __shared__ int wpre[kSortThreads / 32][16];
+  int i = blockIdx.x * kSortThreads + threadIdx.x;
+  bool valid = i < n;
+  uint32_t key = valid ? keys[i] : 0u;
+  int digit = valid ? (int)((key >> shift) & 15u) : 16;
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int rank = 0, mycount = 0;
+#pragma unroll
+  for (int v = 0; v < 16; ++v) {
+    unsigned b = __ballot_sync(0xffffffffu, digit == v);
+    if (lane == v) mycount = __popc(b);
+    if (digit == v) rank = __popc(b & ((1u << lane) - 1u));
+  }
+  if (lane < 16) wcount[warp][lane] = mycount;
+  __syncthreads();
+  if (threadIdx.x < 16) {
+    int run = 0;
+    for (int w = 0; w < kSortThreads / 32; ++w) {
+      wpre[w][threadIdx.x] = run;
+      run += wcount[w][threadIdx.x];
+    }
+  }
+  __syncthreads();
+  if (valid) {
+    int dst = offs[digit * nblocks + blockIdx.x] + wpre[warp][digit] + rank;
+    okeys[dst] = key;
+    ovals[dst] = vals[i];
+  }
+}
+
+// ---- Karras hierarchy ------------------------------------------------------------
+__device__ __forceinline__ int karras_delta(const uint32_t* keys, int n, int i, int j) {
+  if (j < 0 || j >= n) return -1;
+  uint32_t a = keys[i], b = keys[j];
+  if (a == b) return 32 + __clz((uint32_t)i ^ (uint32_t)j);
+  return __clz(a ^ b);
+}
+
+// children: >= 0 internal node, < 0 ~(sorted leaf position)
+__global__ void k_karras(const uint32_t* __restrict__ keys, int n, int2* child, int* parent_int, int* parent_leaf) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n - 1; i += gridDim.x * blockDim.x) {
+    int dnext = karras_delta(keys, n, i, i + 1), dprev = karras_delta(keys, n, i, i - 1);
+    int d = dnext > dprev ? 1 : -1;
+    int dmin = karras_delta(keys, n, i, i - d);
+    int lmax = 2;
+    while (karras_delta(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+      if (karras_delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    int j = i + l * d;
+    int dnode = karras_delta(keys, n, i, j);
+    int s = 0, t = l;
+    do {
+      t = (t + 1) >> 1;
+      if (karras_delta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    int gamma = i + s * d + (d < 0 ? -1 : 0);
+    int lo = min(i, j), hi = max(i, j);
+    int left = (lo == gamma) ? ~gamma : gamma;
+    int right = (hi == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+    child[i] = make_int2(left, right);
+    if (left >= 0) parent_int[left] = i; else parent_leaf[~left] = i;
+    if (right >= 0) parent_int[right] = i; else parent_leaf[~right] = i;
+  }
+}
+
+struct Box6 {
+  float lo[3], hi[3];
+};
+
+__device__ __forceinline__ void child_box(const SceneView& s, int c, const int* sorted_prim, const Box6* boxes,
+                                          float3& lo, float3& hi) {
+  if (c < 0) {
+    prim_bounds(s, sorted_prim[~c], lo, hi);
+  } else {
+    const float* b = reinterpret_cast<const float*>(boxes + c);
+    lo = f3(__ldcg(b + 0), __ldcg(b + 1), __ldcg(b + 2));
+    hi = f3(__ldcg(b + 3), __ldcg(b + 4), __ldcg(b + 5));
+  }
+}
+
+__global__ void k_bounds(SceneView s, int n, const int* __restrict__ sorted_prim, const int2* __restrict__ child,
+                         const int* __restrict__ parent_int, const int* __restrict__ parent_leaf, int* flags,
+                         Box6* boxes) {
+  for (int leaf = blockIdx.x * blockDim.x + threadIdx.x; leaf < n; leaf += gridDim.x * blockDim.x) {
+    int p = parent_leaf[leaf];
+    while (p >= 0) {
+      __threadfence();
+      if (atomicAdd(flags + p, 1) == 0) break;  // the sibling finishes this node
+      __threadfence();
+      int2 ch = child[p];
+      float3 a0, a1, b0, b1;
+      child_box(s, ch.x, sorted_prim, boxes, a0, a1);
+      child_box(s, ch.y, sorted_prim, boxes, b0, b1);
+      float* out = reinterpret_cast<float*>(boxes + p);
+      __stcg(out + 0, fminf(a0.x, b0.x));
+      __stcg(out + 1, fminf(a0.y, b0.y));
+      __stcg(out + 2, fminf(a0.z, b0.z));
+      __stcg(out + 3, fmaxf(a1.x, b1.x));
+      __stcg(out + 4, fmaxf(a1.y, b1.y));
+      __stcg(out + 5, fmaxf(a1.z, b1.z));
+      p = p == 0 ? -1 : parent_int[p];
+    }
+  }
+}
+
+__global__ void k_write_nodes(SceneView s, int n, const int* __restrict__ sorted_prim, const int2* __restrict__ child,
+                              const Box6* boxes, BVHNode* nodes) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n - 1; i += gridDim.x * blockDim.x) {
+    int2 ch = child[i];
+    float3 a0, a1, b0, b1;
+    child_box(s, ch.x, sorted_prim, boxes, a0, a1);
+    child_box(s, ch.y, sorted_prim, boxes, b0, b1);
+    BVHNode nd;
+    nd.a = make_float4(a0.x, a1.x, a0.y, a1.y);
+    nd.b = make_float4(b0.x, b1.x, b0.y, b1.y);
+    nd.c = make_float4(a0.z, a1.z, b0.z, b1.z);
+    int l = ch.x < 0 ? ~sorted_prim[~ch.x] : ch.x;
+    int r = ch.y < 0 ? ~sorted_prim[~ch.y] : ch.y;
+    nd.ch = make_int4(l, r, 0, 0);
+    nodes[i] = nd;
+  }
+}
+
+__global__ void k_single_leaf(SceneView s, BVHNode* nodes) {
+  float3 lo, hi;
+  prim_bounds(s, 0, lo, hi);
+  BVHNode nd;
+  nd.a = make_float4(lo.x, hi.x, lo.y, hi.y);
+  nd.b = nd.a;
+  nd.c = make_float4(lo.z, hi.z, lo.z, hi.z);
+  nd.ch = make_int4(~0, ~0, 0, 0);
+  nodes[0] = nd;
+}
+
+cudaError_t build_bvh(neb_ctx* c) {
+  int n = c->nt + c->ns;
+  cudaStream_t st = c->stream;
+  if (c->nodes) { cudaFree(c->nodes); c->nodes = nullptr; }
+  if (n == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&c->nodes, sizeof(BVHNode) * (size_t)(n > 1 ? n - 1 : 1));
+  if (e != cudaSuccess) return e;
+  SceneView s = scene_view(c);
+  if (n == 1) {
+    k_single_leaf<<<1, 1, 0, st>>>(s, c->nodes);
+    return cudaGetLastError();
+  }
+  int nblocks = (n + kSortThreads - 1) / kSortThreads;
+  size_t hist_n = (size_t)16 * nblocks;
+  uint32_t *k0 = nullptr, *k1 = nullptr;
+  int *v0 = nullptr, *v1 = nullptr, *hist = nullptr, *offs = nullptr, *cb = nullptr;
+  int2* child = nullptr;
+  int *pint = nullptr, *pleaf = nullptr, *flags = nullptr;
+  Box6* boxes = nullptr;
+  Scratch sc;
+  sc.n = scan_scratch_ints(hist_n);
+  bool ok = cudaMalloc(&k0, 4ull * n) == cudaSuccess && cudaMalloc(&k1, 4ull * n) == cudaSuccess &&
+            cudaMalloc(&v0, 4ull * n) == cudaSuccess && cudaMalloc(&v1, 4ull * n) == cudaSuccess &&
+            cudaMalloc(&hist, 4ull * hist_n) == cudaSuccess && cudaMalloc(&offs, 4ull * hist_n) == cudaSuccess &&
+            cudaMalloc(&cb, 4ull * 6) == cudaSuccess && cudaMalloc(&child, 8ull * (n - 1)) == cudaSuccess &&
+            cudaMalloc(&pint, 4ull * (n - 1)) == cudaSuccess && cudaMalloc(&pleaf, 4ull * n) == cudaSuccess &&
+            cudaMalloc(&flags, 4ull * (n - 1)) == cudaSuccess &&
+            cudaMalloc(&boxes, sizeof(Box6) * (size_t)(n - 1)) == cudaSuccess &&
+            cudaMalloc(&sc.data, 4ull * sc.n) == cudaSuccess;
+  if (ok) {
+    int init[6] = {0x7fffffff, 0x7fffffff, 0x7fffffff, (int)0x80000000, (int)0x80000000, (int)0x80000000};
+    cudaMemcpyAsync(cb, init, sizeof(init), cudaMemcpyHostToDevice, st);
+    int gb = (n + 255) / 256;
+    if (gb > 152 * 16) gb = 152 * 16;
+    k_centroid_bounds<<<gb, 256, 0, st>>>(s, n, cb);
+    k_morton<<<gb, 256, 0, st>>>(s, n, cb, k0, v0);
+    for (int shift = 0; shift < 30; shift += 4) {
+      k_digit_hist<<<nblocks, kSortThreads, 0, st>>>(k0, n, shift, nblocks, hist);
+      scan_exclusive(hist, offs, hist_n, sc, st);
+      k_digit_scatter<<<nblocks, kSortThreads, 0, st>>>(k0, v0, n, shift, nblocks, offs, k1, v1);
+      uint32_t* tk = k0; k0 = k1; k1 = tk;
+      int* tv = v0; v0 = v1; v1 = tv;
+    }
+    cudaMemsetAsync(pint, 0xff, 4ull * (n - 1), st);
+    cudaMemsetAsync(flags, 0, 4ull * (n - 1), st);
+    k_karras<<<gb, 256, 0, st>>>(k0, n, child, pint, pleaf);
+    k_bounds<<<gb, 256, 0, st>>>(s, n, v0, child, pint, pleaf, flags, boxes);
+    k_write_nodes<<<gb, 256, 0, st>>>(s, n, v0, child, boxes, c->nodes);
+    e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+  } else {
+    e = cudaErrorMemoryAllocation;
+  }
+  cudaFree(k0); cudaFree(k1); cudaFree(v0); cudaFree(v1); cudaFree(hist); cudaFree(offs); cudaFree(cb);
+  cudaFree(child); cudaFree(pint); cudaFree(pleaf); cudaFree(flags); cudaFree(boxes); cudaFree(sc.data);
+  return e;
+}
+
+// ---- component kernels -------------------------------------------------------------
+__global__ void k_trace_debug(SceneView s, const float* __restrict__ rays, int n, int* prim, float* tout,
+                              uint32_t* status) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    RayPre r = make_ray(f3(rays[6 * i], rays[6 * i + 1], rays[6 * i + 2]),
+                        f3(rays[6 * i + 3], rays[6 * i + 4], rays[6 * i + 5]));
+    float t;
+    uint32_t visits = 0;
+    int p = trace_closest(s, r, FLT_MAX, t, status, visits);
+    prim[i] = p;
+    tout[i] = p >= 0 ? t : __int_as_float(0x7f800000);
+  }
+}
+
+cudaError_t launch_trace_debug(const SceneView& s, const float* d_rays, int n, int* d_prim, float* d_t,
+                               uint32_t* d_status, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_trace_debug<<<(n + 127) / 128, 128, 0, st>>>(s, d_rays, n, d_prim, d_t, d_status);
+  return cudaGetLastError();
+}
+
+__global__ void k_philox(const uint4* __restrict__ ctr, int n, uint2 key, uint4* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = philox4x32_10(ctr[i], key);
+}
+
+cudaError_t launch_philox(const uint32_t* d_ctr, int n, uint2 key, uint32_t* d_out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_philox<<<(n + 255) / 256, 256, 0, st>>>(reinterpret_cast<const uint4*>(d_ctr), n, key,
+                                            reinterpret_cast<uint4*>(d_out));
+  return cudaGetLastError();
+}
+
+__global__ void k_area(const float* __restrict__ boxes, const float* __restrict__ pos, const float* __restrict__ nrm,
+                       int n, float* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float lo[3] = {boxes[6 * i], boxes[6 * i + 1], boxes[6 * i + 2]};
+    float hi[3] = {boxes[6 * i + 3], boxes[6 * i + 4], boxes[6 * i + 5]};
+    float p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+    float q[3] = {nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]};
+    out[i] = intersection_area(lo, hi, p, q);
+  }
+}
+
+cudaError_t launch_area(const float* d_boxes, const float* d_pos, const float* d_nrm, int n, float* d_out,
+                        cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_area<<<(n + 255) / 256, 256, 0, st>>>(d_boxes, d_pos, d_nrm, n, d_out);
+  return cudaGetLastError();
+}
+
+}  // namespace neb

@@ -1,0 +1,193 @@
+// neb_internal.h -- host-side context and the launchers shared between the
+// translation units of libneb.so.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "neb_device.cuh"
+#include "neb_types.h"
+
+namespace neb {
+
+// ---- wavefront records -------------------------------------------------------
+
+// Camera ray in flight from x_{k-1} to x_k (64 bytes).
+struct __align__(16) CamRay {
+  float4 o;    // origin xyz, w: pixel (int bits)
+  float4 d;    // direction xyz, w: pdf_fwd = solid-angle pdf of d at x_{k-1} (1: camera or delta)
+  float4 tau;  // throughput up to x_k (rgb), w: cos_prev = |n_{k-1} . d|
+  float4 mis;  // x: C'_k = C_{k-1} + [x_{k-1} non-delta], y: C_{k-1},
+               // z: NEE id of x_{k-1} (int bits, -1 none), w: flags (int bits)
+};
+enum { RAY_FROM_CAMERA = 1, RAY_PREV_DELTA = 2 };
+
+// Random hit of an emitter at x_l = y, finished in pass 3 (48 bytes).
+struct __align__(16) RHEvent {
+  float4 L;     // rgb tau * Le, w: F_l = pdf_fwd |cos_y| / t^2 (0 when l == 1)
+  float4 y;     // hit point, w: light index (int bits)
+  int4 info;    // x pixel, y NEE id of x_{l-1} (-1 when l == 1), z flags, w C_{l-1} (float bits)
+};
+
+// Photon ray leaving a photon vertex (64 bytes).
+struct __align__(16) PhotonRay {
+  float4 o;    // origin, w: pixel of the path that owns the NEE vertex (int bits)
+  float4 d;    // direction, w: pdf_dir (solid angle, 1 for delta)
+  float4 phi;  // flux rgb, w: cos_orig = |n_origin . d|
+  float4 mis;  // x E0, y pA, z pB, w: k_nee | (j << 8), j = index of the next hit
+};
+
+// Grid-ordered copy of a mergeable view vertex (64 bytes).
+struct __align__(16) MergeRec {
+  float4 pos;  // xyz, w: Cfac
+  float4 nrm;  // geometric normal, w: mat | (k << 20) (int bits)
+  float4 wo;   // direction to x_{k-1}, w: pixel (int bits)
+  float4 tau;  // throughput, w unused
+};
+
+// NEE vertex store, structure of arrays (one float4 per field).
+struct NeeStore {
+  float4* pos;   // xyz, w: Cfac_k = C'_k cos_prev / (pdf_fwd |cos_k|)
+  float4* nrm;   // geometric normal (unflipped), w: mat | k << 20 | flags << 26 (int bits)
+  float4* wo;    // xyz, w: pixel (int bits)
+  float4* tau;   // rgb, w: g_y = cos_y / (dist^2 p_l)
+  float4* err;   // hit point error bound, w: ldist
+  float4* ldir;  // direction to the light point, w: rho (after the density pass)
+  float4* dE;    // irradiance rgb (zero if back-facing or occluded), w unused
+};
+enum { NV_DELTA = 1, NV_MERGEABLE = 2, NV_SHADOW = 4 };
+enum { NV_MAT_MASK = (1 << 20) - 1, NV_K_SHIFT = 20, NV_FLAG_SHIFT = 26 };
+
+// Per-iteration queue sizes and accumulated counters (device memory).
+struct DevCounters {
+  int cam_count[2];
+  int nee_count;
+  int rh_count;
+  int ph_count[2];
+  int merge_count;
+  uint32_t status;
+  unsigned long long camera_rays, nee_vertices, shadow_rays, photons, photon_hits;
+  unsigned long long merge_tests, merges, random_hits, octree_inserts, octree_queries;
+  unsigned long long node_visits, prim_tests;
+};
+
+struct CameraParams {
+  float3 eye, fwd, right, up;
+  float tanh_, aspect;
+};
+
+struct IterParams {
+  int W, H, D;
+  int iteration;
+  uint2 key;
+  float r, r2, kernel;  // merge radius, r^2, 1/(pi r^2)
+  uint32_t mask;
+  int keep_split;
+  int cap_cam, cap_nee, cap_rh, cap_ph;
+  float3 gmin;          // hashed grid origin
+  float cell_inv;       // 1 / (2 r)
+  uint32_t table_mask;  // hash table size - 1
+};
+
+enum { STAGE_REARM = 0, STAGE_CAMERA, STAGE_EXTEND, STAGE_SHADOW, STAGE_INSERT, STAGE_DENSITY, STAGE_NEE,
+       STAGE_GRID, STAGE_EMISSION, STAGE_PHOTON, STAGE_COUNT };
+
+struct Scratch {
+  int* data = nullptr;
+  size_t n = 0;
+};
+
+}  // namespace neb
+
+struct neb_ctx {
+  neb_config cfg{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  int W = 0, H = 0, D = 0, P = 0;
+
+  // scene
+  int nt = 0, ns = 0, nm = 0, nl = 0;
+  float bmin[3]{}, bmax[3]{};
+  float4 *tv0 = nullptr, *tv1 = nullptr, *tv2 = nullptr, *sph = nullptr, *mats = nullptr;
+  int* sph_mat = nullptr;
+  int *prim_light = nullptr, *light_prim = nullptr, *alias_idx = nullptr;
+  float *light_psel = nullptr, *light_inv_area = nullptr, *alias_prob = nullptr;
+  neb::CameraParams cam{};
+  bool scene_ready = false;
+
+  // BVH
+  neb::BVHNode* nodes = nullptr;
+  bool bvh_ready = false;
+
+  // density octree
+  int* oct_nodes = nullptr;
+  neb::OctreeState* oct_state = nullptr;
+  neb::OctreeParams oct{};
+  int oct_cap = 0;
+
+  // per-iteration buffers
+  neb::CamRay* camq[2] = {nullptr, nullptr};
+  neb::NeeStore nv{};
+  neb::RHEvent* rh = nullptr;
+  neb::PhotonRay* phq[2] = {nullptr, nullptr};
+  neb::MergeRec* mrec = nullptr;
+  int* vert_bucket = nullptr;
+  int* bucket_count = nullptr;
+  int* bucket_start = nullptr;
+  int* slot_map = nullptr;
+  int cap_cam = 0, cap_nee = 0, cap_rh = 0, cap_ph = 0;
+  uint32_t table_size = 0;
+  neb::Scratch scan_scratch;
+  double* accum = nullptr;
+  double* split = nullptr;
+  neb::DevCounters* counters = nullptr;
+  int iteration = 0;  // iterations completed (enqueued)
+
+  // profiling
+  bool profiling = false;
+  cudaEvent_t ev[2 * neb::STAGE_COUNT * 16] = {};
+  double stage_ms[neb::STAGE_COUNT] = {};
+  long long stage_launches[neb::STAGE_COUNT] = {};
+};
+
+namespace neb {
+
+// ---- launchers implemented in the .cu files -----------------------------------
+SceneView scene_view(const neb_ctx* c);
+
+// neb_bvh.cu
+cudaError_t build_bvh(neb_ctx* c);
+cudaError_t launch_trace_debug(const SceneView& s, const float* d_rays, int n, int* d_prim, float* d_t,
+                               uint32_t* d_status, cudaStream_t st);
+cudaError_t launch_philox(const uint32_t* d_ctr, int n, uint2 key, uint32_t* d_out, cudaStream_t st);
+cudaError_t launch_area(const float* d_boxes, const float* d_pos, const float* d_nrm, int n, float* d_out,
+                        cudaStream_t st);
+
+// neb_grid.cu
+size_t scan_scratch_ints(size_t n);
+cudaError_t scan_exclusive(const int* d_in, int* d_out, size_t n, Scratch& scratch, cudaStream_t st);
+cudaError_t grid_build(neb_ctx* c, const IterParams& ip);
+cudaError_t count_neighbours_device(const float* d_pts, int n, const float* d_q, int m, float r, int* d_out,
+                                    cudaStream_t st);
+
+// neb_octree.cu
+OctreeParams octree_params(const float smin[3], const float smax[3], int capacity, int split_factor);
+void octree_set_iteration_params(OctreeParams& P, int split_factor, int iter);
+cudaError_t launch_oct_rearm(int* nodes, const OctreeState* st, const OctreeParams& P, cudaStream_t s);
+cudaError_t launch_oct_insert_points(int* nodes, OctreeState* st, const OctreeParams& P, const float* d_pos, int n,
+                                     int mode, cudaStream_t s);
+cudaError_t launch_oct_density_points(const int* nodes, const OctreeState* st, const OctreeParams& P,
+                                      const float* d_pos, const float* d_nrm, int n, int robust, float* d_out,
+                                      cudaStream_t s);
+cudaError_t launch_oct_insert_nee(neb_ctx* c);
+cudaError_t launch_oct_density_nee(neb_ctx* c);
+
+// neb_pass.cu
+cudaError_t run_iteration(neb_ctx* c, int iteration);
+cudaError_t launch_resolve(const double* accum, int P, int iterations, float* out, cudaStream_t st);
+cudaError_t launch_read_rho(neb_ctx* c, float* d_out);
+
+}  // namespace neb

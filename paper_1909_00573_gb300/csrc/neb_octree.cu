@@ -1,0 +1,275 @@
+// neb_octree.cu -- density octree kernels (Sec. 5, Appendix B) and the
+// stand-alone octree entry points of the C ABI.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "neb_internal.h"
+#include "neb_octree.cuh"
+
+namespace neb {
+
+// initialize() of the listing: scene box enlarged by 1.002 around its
+// minimum corner, capacity rounded up to 8n + 1.
+OctreeParams octree_params(const float smin[3], const float smax[3], int capacity, int split_factor) {
+  OctreeParams P;
+  float size[3];
+  for (int c = 0; c < 3; ++c) size[c] = (smax[c] - smin[c]) * 1.002f;
+  for (int c = 0; c < 3; ++c) P.size_inv[c] = 1.0f / size[c];
+  P.scene_scale = sqrtf(size[0] * size[0] + size[1] * size[1] + size[2] * size[2]);
+  for (int c = 0; c < 3; ++c) P.minb[c] = smin[c] - size[c] * (0.001f / 1.002f);
+  P.capacity = 1 + ((capacity + 7) & ~7);
+  P.split_count = split_factor;
+  P.iter_clamp = 1;
+  P.stop_filling = 0;
+  P.init_value = 0;
+  return P;
+}
+
+// set_iteration() of the listing (the re-arm of unused nodes is the kernel below)
+void octree_set_iteration_params(OctreeParams& P, int split_factor, int iter) {
+  int ic = iter < kFillIterations ? iter : kFillIterations;
+  P.iter_clamp = ic;
+  P.stop_filling = iter > kFillIterations;
+  P.split_count = split_factor * ic;
+  P.init_value = (int)ceilf((float)split_factor / 4.0f * (float)iter);
+}
+
+// every node in [alloc, capacity) starts at ceil(SPLIT/4 * iter): a surface
+// meets about four of the eight children of a split cell (Sec. 5.2)
+__global__ void k_oct_rearm(int* nodes, const OctreeState* st, OctreeParams P) {
+  if (P.stop_filling) return;
+  int a = *((const volatile int*)&st->alloc);
+  for (long long i = a + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P.capacity;
+       i += (long long)gridDim.x * blockDim.x)
+    nodes[i] = P.init_value;
+}
+
+__global__ void k_oct_insert_points(int* nodes, OctreeState* st, OctreeParams P, const float* __restrict__ pos, int n,
+                                    int spin_limit) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+    oct_insert_atomic(nodes, st, P, p, spin_limit);
+  }
+}
+
+__global__ void k_oct_insert_points_seq(int* nodes, OctreeState* st, OctreeParams P, const float* __restrict__ pos,
+                                        int n) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  for (int i = 0; i < n; ++i) {
+    float p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+    oct_insert_seq(nodes, st, P, p);
+  }
+}
+
+__global__ void k_oct_density_points(const int* __restrict__ nodes, const OctreeState* st, OctreeParams P,
+                                     const float* __restrict__ pos, const float* __restrict__ nrm, int n, int robust,
+                                     float* out) {
+  int depth = st->depth;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+    float q[3] = {nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]};
+    int nq = 0;
+    out[i] = robust ? oct_density_robust(nodes, P, depth, p, q, &nq) : oct_density(nodes, P, depth, p, q, nullptr);
+  }
+}
+
+// NEB pass: inserts of this iteration's NEE vertices
+__global__ void k_oct_insert_nee(int* nodes, OctreeState* st, OctreeParams P, const float4* __restrict__ vpos,
+                                 DevCounters* cnt, int cap, int spin_limit) {
+  int count = min(cnt->nee_count, cap);
+  uint32_t done = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    float4 v = vpos[i];
+    float p[3] = {v.x, v.y, v.z};
+    oct_insert_atomic(nodes, st, P, p, spin_limit);
+    ++done;
+  }
+  if (done) atomicAdd(&cnt->octree_inserts, (unsigned long long)done);
+}
+
+// deterministic mode: one thread inserts in (pixel, k) order
+__global__ void k_oct_insert_nee_seq(int* nodes, OctreeState* st, OctreeParams P, const float4* __restrict__ vpos,
+                                     const int* __restrict__ slot_map, int n_slots, DevCounters* cnt) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  unsigned long long done = 0;
+  for (int s = 0; s < n_slots; ++s) {
+    int id = slot_map[s];
+    if (id < 0) continue;
+    float4 v = vpos[id];
+    float p[3] = {v.x, v.y, v.z};
+    oct_insert_seq(nodes, st, P, p);
+    ++done;
+  }
+  cnt->octree_inserts += done;
+}
+
+__global__ void k_oct_density_nee(const int* __restrict__ nodes, const OctreeState* st, OctreeParams P,
+                                  const float4* __restrict__ vpos, const float4* __restrict__ vnrm, float4* vldir,
+                                  DevCounters* cnt, int cap, int robust) {
+  int count = min(cnt->nee_count, cap);
+  int depth = st->depth;
+  int queries = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    float4 v = vpos[i], nn = vnrm[i];
+    float p[3] = {v.x, v.y, v.z};
+    float q[3] = {nn.x, nn.y, nn.z};
+    float rho;
+    if (robust) {
+      rho = oct_density_robust(nodes, P, depth, p, q, &queries);
+    } else {
+      rho = oct_density(nodes, P, depth, p, q, nullptr);
+      ++queries;
+    }
+    vldir[i].w = rho;
+  }
+  if (queries) atomicAdd(&cnt->octree_queries, (unsigned long long)queries);
+}
+
+static int blocks_for(int n, int threads) {
+  int b = (n + threads - 1) / threads;
+  return b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b);
+}
+
+cudaError_t launch_oct_rearm(int* nodes, const OctreeState* st, const OctreeParams& P, cudaStream_t s) {
+  k_oct_rearm<<<blocks_for(P.capacity, 256), 256, 0, s>>>(nodes, st, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oct_insert_points(int* nodes, OctreeState* st, const OctreeParams& P, const float* d_pos, int n,
+                                     int mode, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (mode == 1)
+    k_oct_insert_points_seq<<<1, 1, 0, s>>>(nodes, st, P, d_pos, n);
+  else
+    k_oct_insert_points<<<blocks_for(n, 256), 256, 0, s>>>(nodes, st, P, d_pos, n, kSpinLimit);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oct_density_points(const int* nodes, const OctreeState* st, const OctreeParams& P,
+                                      const float* d_pos, const float* d_nrm, int n, int robust, float* d_out,
+                                      cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_oct_density_points<<<blocks_for(n, 256), 256, 0, s>>>(nodes, st, P, d_pos, d_nrm, n, robust, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oct_insert_nee(neb_ctx* c) {
+  if (c->cfg.octree_mode == 1)
+    k_oct_insert_nee_seq<<<1, 1, 0, c->stream>>>(c->oct_nodes, c->oct_state, c->oct, c->nv.pos, c->slot_map,
+                                                 c->P * (c->D - 1), c->counters);
+  else
+    k_oct_insert_nee<<<152 * 8, 256, 0, c->stream>>>(c->oct_nodes, c->oct_state, c->oct, c->nv.pos, c->counters,
+                                                     c->cap_nee, kSpinLimit);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oct_density_nee(neb_ctx* c) {
+  k_oct_density_nee<<<152 * 8, 256, 0, c->stream>>>(c->oct_nodes, c->oct_state, c->oct, c->nv.pos, c->nv.nrm,
+                                                    c->nv.ldir, c->counters, c->cap_nee,
+                                                    c->cfg.density_mode == 0);
+  return cudaGetLastError();
+}
+
+}  // namespace neb
+
+// ---------------------------------------------------------------------------
+// stand-alone octree (C ABI)
+// ---------------------------------------------------------------------------
+struct neb_octree {
+  neb::OctreeParams P{};
+  int split_factor = 4;
+  int* nodes = nullptr;
+  neb::OctreeState* st = nullptr;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+};
+
+extern "C" int neb_octree_create(const float scene_min[3], const float scene_max[3], int capacity, int split_factor,
+                                 void* cuda_stream, neb_octree** out) {
+  if (!scene_min || !scene_max || !out || capacity < 1 || split_factor < 1) return NEB_ERR_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return NEB_ERR_NO_DEVICE;
+  neb_octree* o = new (std::nothrow) neb_octree();
+  if (!o) return NEB_ERR_OOM;
+  o->P = neb::octree_params(scene_min, scene_max, capacity, split_factor);
+  o->split_factor = split_factor;
+  if (cuda_stream) {
+    o->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&o->stream, cudaStreamNonBlocking) != cudaSuccess) { delete o; return NEB_ERR_CUDA; }
+    o->own_stream = true;
+  }
+  if (cudaMalloc(&o->nodes, sizeof(int) * (size_t)o->P.capacity) != cudaSuccess ||
+      cudaMalloc(&o->st, sizeof(neb::OctreeState)) != cudaSuccess) {
+    neb_octree_destroy(o);
+    return NEB_ERR_OOM;
+  }
+  neb::OctreeState s0{1, 0, 0, 0};
+  cudaMemsetAsync(o->nodes, 0, sizeof(int) * (size_t)o->P.capacity, o->stream);
+  cudaMemcpyAsync(o->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, o->stream);
+  if (cudaStreamSynchronize(o->stream) != cudaSuccess) { neb_octree_destroy(o); return NEB_ERR_CUDA; }
+  *out = o;
+  return NEB_OK;
+}
+
+extern "C" void neb_octree_destroy(neb_octree* o) {
+  if (!o) return;
+  if (o->nodes) cudaFree(o->nodes);
+  if (o->st) cudaFree(o->st);
+  if (o->own_stream && o->stream) cudaStreamDestroy(o->stream);
+  delete o;
+}
+
+extern "C" int neb_octree_set_iteration(neb_octree* o, int iter) {
+  if (!o || iter < 1) return NEB_ERR_ARG;
+  neb::octree_set_iteration_params(o->P, o->split_factor, iter);
+  if (neb::launch_oct_rearm(o->nodes, o->st, o->P, o->stream) != cudaSuccess) return NEB_ERR_CUDA;
+  return cudaStreamSynchronize(o->stream) == cudaSuccess ? NEB_OK : NEB_ERR_CUDA;
+}
+
+extern "C" int neb_octree_insert(neb_octree* o, const float* pos, int n, int mode) {
+  if (!o || (n > 0 && !pos) || n < 0 || (mode != 0 && mode != 1)) return NEB_ERR_ARG;
+  if (n == 0) return NEB_OK;
+  float* d = nullptr;
+  if (cudaMallocAsync(&d, sizeof(float) * 3 * (size_t)n, o->stream) != cudaSuccess) return NEB_ERR_OOM;
+  cudaMemcpyAsync(d, pos, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, o->stream);
+  cudaError_t e = neb::launch_oct_insert_points(o->nodes, o->st, o->P, d, n, mode, o->stream);
+  cudaFreeAsync(d, o->stream);
+  if (e != cudaSuccess || cudaStreamSynchronize(o->stream) != cudaSuccess) return NEB_ERR_CUDA;
+  neb::OctreeState s;
+  cudaMemcpy(&s, o->st, sizeof(s), cudaMemcpyDeviceToHost);
+  if (s.status & NEB_STATUS_SPIN_TIMEOUT) return NEB_ERR_DEVICE_TIMEOUT;
+  return NEB_OK;
+}
+
+extern "C" int neb_octree_density(neb_octree* o, const float* pos, const float* nrm, int n, int robust, float* out) {
+  if (!o || n < 0 || (n > 0 && (!pos || !nrm || !out))) return NEB_ERR_ARG;
+  if (n == 0) return NEB_OK;
+  float* d = nullptr;
+  size_t bytes = sizeof(float) * 3 * (size_t)n;
+  if (cudaMallocAsync(&d, bytes * 2 + sizeof(float) * (size_t)n, o->stream) != cudaSuccess) return NEB_ERR_OOM;
+  cudaMemcpyAsync(d, pos, bytes, cudaMemcpyHostToDevice, o->stream);
+  cudaMemcpyAsync(d + 3 * (size_t)n, nrm, bytes, cudaMemcpyHostToDevice, o->stream);
+  float* dout = d + 6 * (size_t)n;
+  cudaError_t e = neb::launch_oct_density_points(o->nodes, o->st, o->P, d, d + 3 * (size_t)n, n, robust, dout,
+                                                 o->stream);
+  cudaMemcpyAsync(out, dout, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, o->stream);
+  cudaFreeAsync(d, o->stream);
+  if (e != cudaSuccess || cudaStreamSynchronize(o->stream) != cudaSuccess) return NEB_ERR_CUDA;
+  return NEB_OK;
+}
+
+extern "C" int neb_octree_read(neb_octree* o, int32_t* nodes, int n_nodes, int32_t meta[4]) {
+  if (!o || !meta) return NEB_ERR_ARG;
+  neb::OctreeState s;
+  if (cudaMemcpyAsync(&s, o->st, sizeof(s), cudaMemcpyDeviceToHost, o->stream) != cudaSuccess) return NEB_ERR_CUDA;
+  int m = n_nodes < o->P.capacity ? n_nodes : o->P.capacity;
+  if (nodes && m > 0) cudaMemcpyAsync(nodes, o->nodes, sizeof(int) * (size_t)m, cudaMemcpyDeviceToHost, o->stream);
+  if (cudaStreamSynchronize(o->stream) != cudaSuccess) return NEB_ERR_CUDA;
+  meta[0] = s.alloc;
+  meta[1] = s.depth;
+  meta[2] = o->P.capacity;
+  meta[3] = (int32_t)s.status;
+  return NEB_OK;
+}

@@ -1,0 +1,232 @@
+// neb_octree.cuh -- device side of the density octree (Sec. 5 and the
+// listing of Appendix B): plane/box area (Eq. area), count-and-split insert
+// (lock-free, and sequential for the deterministic mode), and the density
+// query with its robust median-of-five variant.
+#pragma once
+#include "neb_device.cuh"
+
+namespace neb {
+
+// Eq. area with the listing's 1D (|n_d| within 1e-3 of 1) and 2D (|n_d| <
+// 1e-4) cases; corners enter the alternating sum in the listing's order.
+__host__ __device__ __forceinline__ float intersection_area(const float bmin[3], const float bmax[3],
+                                                            const float pos[3], const float n[3]) {
+  float cs[3] = {bmax[0] - bmin[0], bmax[1] - bmin[1], bmax[2] - bmin[2]};
+  float an[3] = {fabsf(n[0]), fabsf(n[1]), fabsf(n[2])};
+  if (fabsf(an[0] - 1.0f) < 1e-3f) return cs[1] * cs[2];
+  if (fabsf(an[1] - 1.0f) < 1e-3f) return cs[0] * cs[2];
+  if (fabsf(an[2] - 1.0f) < 1e-3f) return cs[0] * cs[1];
+  for (int d = 0; d < 3; ++d) {
+    if (an[d] < 1e-4f) {
+      int x = d == 2 ? 0 : d + 1;
+      int y = x == 2 ? 0 : x + 1;
+      float h = n[x] * pos[x] + n[y] * pos[y];
+      float s = 0.0f;
+      s += fmaxf(0.0f, h - (n[x] * bmin[x] + n[y] * bmin[y]));
+      s -= fmaxf(0.0f, h - (n[x] * bmin[x] + n[y] * bmax[y]));
+      s -= fmaxf(0.0f, h - (n[x] * bmax[x] + n[y] * bmin[y]));
+      s += fmaxf(0.0f, h - (n[x] * bmax[x] + n[y] * bmax[y]));
+      return cs[d] * fabsf(s / (n[x] * n[y]));
+    }
+  }
+  float h = n[0] * pos[0] + n[1] * pos[1] + n[2] * pos[2];
+  float s = 0.0f, t;
+  t = fmaxf(0.0f, h - (n[0] * bmin[0] + n[1] * bmin[1] + n[2] * bmin[2])); s += t * t;
+  t = fmaxf(0.0f, h - (n[0] * bmin[0] + n[1] * bmin[1] + n[2] * bmax[2])); s -= t * t;
+  t = fmaxf(0.0f, h - (n[0] * bmin[0] + n[1] * bmax[1] + n[2] * bmax[2])); s += t * t;
+  t = fmaxf(0.0f, h - (n[0] * bmin[0] + n[1] * bmax[1] + n[2] * bmin[2])); s -= t * t;
+  t = fmaxf(0.0f, h - (n[0] * bmax[0] + n[1] * bmax[1] + n[2] * bmin[2])); s += t * t;
+  t = fmaxf(0.0f, h - (n[0] * bmax[0] + n[1] * bmin[1] + n[2] * bmin[2])); s -= t * t;
+  t = fmaxf(0.0f, h - (n[0] * bmax[0] + n[1] * bmin[1] + n[2] * bmax[2])); s += t * t;
+  t = fmaxf(0.0f, h - (n[0] * bmax[0] + n[1] * bmax[1] + n[2] * bmax[2])); s -= t * t;
+  return fabsf(s / (2.0f * n[0] * n[1] * n[2]));
+}
+
+__device__ __forceinline__ bool oct_norm_pos(const OctreeParams& P, const float pos[3], float np[3]) {
+  for (int c = 0; c < 3; ++c) np[c] = (pos[c] - P.minb[c]) * P.size_inv[c];
+  for (int c = 0; c < 3; ++c)
+    if (!(np[c] >= 0.0f && np[c] < 1.0f)) return false;
+  return true;
+}
+
+// ---- insert ---------------------------------------------------------------
+// Sequential form (one device thread): identical to the listing run by one
+// CPU thread.
+__device__ __forceinline__ int oct_split_seq(int* nodes, OctreeState* st, const OctreeParams& P, int idx, int count,
+                                             int depth) {
+  if (count >= P.split_count) {
+    if (depth + 1 > kOctMaxDepth) return 0;
+    if (count == P.split_count) {
+      int child = st->alloc;
+      st->alloc += 8;
+      if (child >= P.capacity) {
+        st->alloc = P.capacity + 1;
+        st->status |= NEB_STATUS_OCTREE_FULL;
+        return 0;
+      }
+      nodes[idx] = -child;
+      if (depth + 1 > st->depth) st->depth = depth + 1;
+      return 0;
+    }
+    return nodes[idx] < 0 ? nodes[idx] : 0;
+  }
+  return count;
+}
+
+__device__ __forceinline__ void oct_insert_seq(int* nodes, OctreeState* st, const OctreeParams& P,
+                                               const float pos[3]) {
+  if (P.stop_filling) return;
+  float np[3];
+  if (!oct_norm_pos(P, pos, np)) return;
+  int v = nodes[0];
+  if (v >= 0) nodes[0] = ++v;
+  v = oct_split_seq(nodes, st, P, 0, v, 0);
+  int edge = 1, depth = 0;
+  while (v < 0) {
+    edge *= 2;
+    ++depth;
+    int ix = ((int)(np[0] * (float)edge)) & 1;
+    int iy = ((int)(np[1] * (float)edge)) & 1;
+    int iz = ((int)(np[2] * (float)edge)) & 1;
+    int idx = ix + 2 * (iy + 2 * iz) - v;
+    v = nodes[idx];
+    if (v >= 0) nodes[idx] = ++v;
+    v = oct_split_seq(nodes, st, P, idx, v, depth);
+  }
+}
+
+// Lock-free form: CAS increment of a non-negative counter
+// (increment_if_positive), one thread per split (the one that reaches the
+// threshold exactly), the others wait for the child pointer with a bounded
+// spin and then count in the child.  A spin that runs out sets
+// NEB_STATUS_SPIN_TIMEOUT and drops the insert; it never traps.
+__device__ __forceinline__ int oct_inc_atomic(int* nodes, int idx) {
+  int old = *((volatile int*)(nodes + idx));
+  while (true) {
+    if (old < 0) return old;
+    int prev = atomicCAS(nodes + idx, old, old + 1);
+    if (prev == old) return old + 1;
+    old = prev;
+  }
+}
+
+__device__ __forceinline__ int oct_split_atomic(int* nodes, OctreeState* st, const OctreeParams& P, int idx,
+                                                int count, int depth, int spin_limit) {
+  if (count >= P.split_count) {
+    if (depth + 1 > kOctMaxDepth) return 0;
+    if (count == P.split_count) {
+      int child = atomicAdd(&st->alloc, 8);
+      if (child >= P.capacity) {
+        atomicExch(&st->alloc, P.capacity + 1);
+        atomicOr(&st->status, NEB_STATUS_OCTREE_FULL);
+        return 0;
+      }
+      atomicExch(nodes + idx, -child);
+      atomicMax(&st->depth, depth + 1);
+      return 0;
+    }
+    for (int it = 0; it < spin_limit; ++it) {
+      int c = *((volatile int*)(nodes + idx));
+      if (c < 0) return c;
+      if (*((volatile int*)&st->alloc) > P.capacity) return 0;
+      __nanosleep(64);
+    }
+    atomicOr(&st->status, NEB_STATUS_SPIN_TIMEOUT);
+    return 0;
+  }
+  return count;
+}
+
+__device__ __forceinline__ void oct_insert_atomic(int* nodes, OctreeState* st, const OctreeParams& P,
+                                                  const float pos[3], int spin_limit) {
+  if (P.stop_filling) return;
+  float np[3];
+  if (!oct_norm_pos(P, pos, np)) return;
+  int v = oct_inc_atomic(nodes, 0);
+  v = oct_split_atomic(nodes, st, P, 0, v, 0, spin_limit);
+  int edge = 1, depth = 0;
+  while (v < 0) {
+    edge *= 2;
+    ++depth;
+    int ix = ((int)(np[0] * (float)edge)) & 1;
+    int iy = ((int)(np[1] * (float)edge)) & 1;
+    int iz = ((int)(np[2] * (float)edge)) & 1;
+    int idx = ix + 2 * (iy + 2 * iz) - v;
+    v = oct_inc_atomic(nodes, idx);
+    v = oct_split_atomic(nodes, st, P, idx, v, depth, spin_limit);
+  }
+}
+
+// ---- query -----------------------------------------------------------------
+// get_density of the listing with the final normalisation in FP64:
+// rho = c / (min(iter, 1000) * max(minArea, A)).  *size receives the cell
+// diagonal when non-null (robust centre query: minArea uses 0.1 instead of 0.01).
+__device__ __forceinline__ float oct_density(const int* __restrict__ nodes, const OctreeParams& P, int depth,
+                                             const float pos[3], const float n[3], float* size) {
+  float off[3], np[3];
+  for (int c = 0; c < 3; ++c) {
+    off[c] = pos[c] - P.minb[c];
+    np[c] = off[c] * P.size_inv[c];
+  }
+  for (int c = 0; c < 3; ++c)
+    if (!(np[c] >= 0.0f && np[c] < 1.0f)) return 0.0f;
+  int grid = 1 << depth;
+  int ip[3];
+  for (int c = 0; c < 3; ++c) ip[c] = (int)(np[c] * (float)grid);
+  int v = __ldg(nodes);
+  int mask = grid;
+  while (v < 0) {
+    mask >>= 1;
+    int idx = ((ip[0] & mask) ? 1 : 0) + ((ip[1] & mask) ? 2 : 0) + ((ip[2] & mask) ? 4 : 0);
+    idx -= v;
+    v = __ldg(nodes + idx);
+  }
+  if (v > 0) {
+    int cur = grid / mask;
+    float cmin[3], cmax[3];
+    for (int c = 0; c < 3; ++c) {
+      float csz = 1.0f / ((float)cur * P.size_inv[c]);
+      int cp = ip[c] / mask;
+      cmin[c] = (float)cp * csz;
+      cmax[c] = cmin[c] + csz;
+    }
+    float area = intersection_area(cmin, cmax, off, n);
+    float diag = P.scene_scale / (float)cur;
+    float min_area = diag * diag;
+    if (size) { *size = diag; min_area *= 0.1f; } else min_area *= 0.01f;
+    double rho = (double)v / ((double)P.iter_clamp * (double)fmaxf(min_area, area));
+    return (float)rho;
+  }
+  return 0.0f;
+}
+
+// get_density_robust of the listing: median of the centre query and four
+// queries displaced by 1.1 cell diagonals along the tangents of the Duff et
+// al. basis of the geometric normal; ties go to the greater value.
+__device__ __forceinline__ float oct_density_robust(const int* __restrict__ nodes, const OctreeParams& P, int depth,
+                                                    const float pos[3], const float n[3], int* queries) {
+  float d[5];
+  float diag = 1e-3f;
+  int count = 0;
+  d[0] = oct_density(nodes, P, depth, pos, n, &diag);
+  diag *= 1.1f;
+  if (d[0] > 0.0f) ++count;
+  float3 t, b;
+  onb(f3(n[0], n[1], n[2]), t, b);
+  float3 p = f3(pos[0], pos[1], pos[2]);
+  float3 q[4] = {add(p, mul(t, diag)), sub(p, mul(t, diag)), add(p, mul(b, diag)), sub(p, mul(b, diag))};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float qq[3] = {q[i].x, q[i].y, q[i].z};
+    d[count] = oct_density(nodes, P, depth, qq, n, nullptr);
+    if (d[count] > 0.0f) ++count;
+  }
+  *queries += 5;
+  int m = count / 2;
+  for (int i = 0; i <= m; ++i)
+    for (int j = i + 1; j < count; ++j)
+      if (d[j] < d[i]) { float tmp = d[i]; d[i] = d[j]; d[j] = tmp; }
+  return d[m];
+}
+
+}  // namespace neb

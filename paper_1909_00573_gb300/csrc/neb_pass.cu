@@ -1,0 +1,636 @@
+// neb_pass.cu -- the wavefront kernels of one NEB iteration and their
+// orchestration (Sec. 3 outline: pass 1 view paths, pass 2 density / NEE /
+// photons, pass 3 self emission).
+//
+// MIS (Sec. 4): the balance heuristic over the random hit (e), the NEE (E)
+// and the NEB photon merges P_k (Eq. rhpdf, Eq. neepdf, Eq. photonpdf,
+// Eq. misw) is evaluated recursively.  With F_i = p_{i-1->i}, R_i = p_{i+1->i}
+// and ok(k) = [x_k non-delta]:
+//   C_m   = sum_{k<m} ok(k) prod_{i=k}^{m-1} R_i / F_{i+1}        (view side)
+//   random hit at x_l: p_sum/p_e = 1 + [E] nd(x_{l-1}) q + [P] q rho_{l-1} pi r^2 C_{l-1}, q = p_l / F_l
+//   NEE at x_m:        p_sum/p_E = 1 + [e] F_l / p_l + [P] rho_m pi r^2 C_m
+//   merge at x_k with a photon from NEE vertex x_m:
+//                      p_sum/(n_P p_Pk) = 1 + E0 A_k + B_k + C_k, where the photon
+//   carries E0 = ([e] F_l/p_l + [E] nd(x_m)) / (rho_m pi r^2), A_k = prod F_{i+1}/R_i
+//   and B_k = sum over photon vertices of ok(k') prod F_{i+1}/R_i.
+// n_T cancels (n_P = n_T).  Squared distances cancel between F and R, so only
+// cosines and directional pdfs are carried.
+#include <cfloat>
+#include <cstdio>
+
+#include "neb_device.cuh"
+#include "neb_internal.h"
+#include "neb_octree.cuh"
+
+namespace neb {
+
+constexpr int kThreads = 256;
+
+static int grid_blocks() {
+  static int blocks = 0;
+  if (blocks == 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    blocks = (sms > 0 ? sms : 152) * 8;
+  }
+  return blocks;
+}
+
+__device__ __forceinline__ void warp_count(unsigned long long* dst, uint32_t v) {
+  uint32_t s = __reduce_add_sync(0xffffffffu, v);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(dst, (unsigned long long)s);
+}
+
+__device__ __forceinline__ void add_pixel(double* accum, double* split, int which, int pixel, float3 L, int P) {
+  double* a = accum + (size_t)pixel * 3;
+  atomicAdd(a, (double)L.x);
+  atomicAdd(a + 1, (double)L.y);
+  atomicAdd(a + 2, (double)L.z);
+  if (split) {
+    double* sp = split + ((size_t)which * P + pixel) * 3;
+    atomicAdd(sp, (double)L.x);
+    atomicAdd(sp + 1, (double)L.y);
+    atomicAdd(sp + 2, (double)L.z);
+  }
+}
+
+// NEE area pdf p_l of point y on light li seen from x (power-proportional
+// selection times uniform area on triangles / on the hemisphere of a sphere
+// that faces x).
+__device__ __forceinline__ float light_pdf(const SceneView& s, int li, float3 y, float3 x) {
+  int prim = __ldg(s.light_prim + li);
+  float psel = __ldg(s.light_psel + li), ia = __ldg(s.light_inv_area + li);
+  if (prim < s.nt) return psel * ia;
+  float3 c = xyz(__ldg(s.sph + (prim - s.nt)));
+  if (!(dot(sub(y, c), sub(x, c)) > 0.0f)) return 0.0f;
+  return psel * ia;
+}
+
+__device__ __forceinline__ uint32_t grid_hash(int x, int y, int z, uint32_t mask) {
+  // Teschner et al., "Optimized Spatial Hashing for Collision Detection of Deformable Objects" (VMV 2003)
+  return (((uint32_t)x * 73856093u) ^ ((uint32_t)y * 19349663u) ^ ((uint32_t)z * 83492791u)) & mask;
+}
+
+// ---------------------------------------------------------------------------
+// pass 1
+// ---------------------------------------------------------------------------
+__global__ void k_begin(DevCounters* cnt) {
+  cnt->cam_count[1] = 0;
+  cnt->nee_count = 0;
+  cnt->rh_count = 0;
+  cnt->ph_count[0] = 0;
+  cnt->ph_count[1] = 0;
+  cnt->merge_count = 0;
+}
+
+__global__ void k_camera(IterParams ip, CameraParams cam, CamRay* q, DevCounters* cnt) {
+  int P = ip.W * ip.H;
+  for (int pixel = blockIdx.x * blockDim.x + threadIdx.x; pixel < P; pixel += gridDim.x * blockDim.x) {
+    uint4 rb = rng_block(ip.key, ip.iteration, pixel, 0, 0);
+    float ju = u01(rb.x), jv = u01(rb.y);
+    int px = pixel % ip.W, py = pixel / ip.W;
+    float sx = (((float)px + ju) / (float)ip.W) * 2.0f - 1.0f;
+    float sy = 1.0f - (((float)py + jv) / (float)ip.H) * 2.0f;
+    float a = sx * cam.tanh_ * cam.aspect;
+    float b = sy * cam.tanh_;
+    float3 d = normalize(f3(cam.fwd.x + cam.right.x * a + cam.up.x * b, cam.fwd.y + cam.right.y * a + cam.up.y * b,
+                            cam.fwd.z + cam.right.z * a + cam.up.z * b));
+    CamRay r;
+    r.o = make_float4(cam.eye.x, cam.eye.y, cam.eye.z, __int_as_float(pixel));
+    r.d = make_float4(d.x, d.y, d.z, 1.0f);
+    r.tau = make_float4(1.0f, 1.0f, 1.0f, 0.0f);
+    r.mis = make_float4(0.0f, 0.0f, __int_as_float(-1), __int_as_float(RAY_FROM_CAMERA));
+    q[pixel] = r;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    cnt->cam_count[0] = P;
+    atomicAdd(&cnt->camera_rays, 0ull);
+  }
+}
+
+// Camera path extension: closest hit, random-hit event, NEE vertex (light
+// sample, octree-bound record), BSDF sample and the next ray.  Queues are
+// compacted with warp ballots.
+__global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip, int k, const CamRay* __restrict__ in,
+                                                     int in_slot, CamRay* __restrict__ out, int out_slot,
+                                                     NeeStore nv, RHEvent* __restrict__ rh, DevCounters* cnt,
+                                                     int* __restrict__ slot_map) {
+  const int count = min(cnt->cam_count[in_slot], ip.cap_cam);
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
+    const int i = base + threadIdx.x;
+    const bool valid = i < count;
+    uint32_t visits = 0, rays = 0, nee_new = 0, rhits = 0;
+    bool store_nee = false, alive = false;
+    CamRay ry;
+    float3 p = f3(0, 0, 0), n = f3(0, 0, 0), err = f3(0, 0, 0), d = f3(0, 0, 0), tau = f3(0, 0, 0);
+    Mat m;
+    m.type = 0;
+    int pixel = 0, mat = 0, flags = 0;
+    float Cfac = 0.0f, cos_k = 0.0f;
+    // NEE sample
+    float3 ldir = f3(0, 0, 0), dE = f3(0, 0, 0);
+    float ldist = 0.0f, g_y = 0.0f;
+    bool shadow = false;
+    if (valid) {
+      ry = in[i];
+      rays = 1;
+      d = xyz(ry.d);
+      pixel = __float_as_int(ry.o.w);
+      flags = __float_as_int(ry.mis.w);
+      RayPre r = make_ray(xyz(ry.o), d);
+      float t;
+      int prim = trace_closest(s, r, FLT_MAX, t, &cnt->status, visits);
+      if (prim >= 0) {
+        hit_point(s, r, prim, t, p, err, n);
+        mat = prim_mat(s, prim);
+        m = load_mat(s.mats, mat);
+        float3 wo = neg(d);
+        tau = xyz(ry.tau);
+        cos_k = fabsf(dot(n, d));
+        int li = __ldg(s.prim_light + prim);
+        if ((ip.mask & 1u) && li >= 0 && (prim >= s.nt || dot(n, wo) > 0.0f)) {
+          float F_l = (flags & RAY_FROM_CAMERA) ? 0.0f : ry.d.w * cos_k / (t * t);
+          int slot = atomicAdd(&cnt->rh_count, 1);
+          if (slot < ip.cap_rh) {
+            RHEvent e;
+            float3 L = cmul(tau, m.emission);
+            e.L = make_float4(L.x, L.y, L.z, F_l);
+            e.y = make_float4(p.x, p.y, p.z, __int_as_float(li));
+            e.info = make_int4(pixel, __float_as_int(ry.mis.z), flags, __float_as_int(ry.mis.y));
+            rh[slot] = e;
+          } else {
+            atomicOr(&cnt->status, NEB_STATUS_QUEUE_OVERFLOW);
+          }
+          rhits = 1;
+        }
+        if (!mat_black(m)) {
+          alive = k < ip.D;
+          Cfac = (flags & RAY_FROM_CAMERA) ? 0.0f : ry.mis.x * ry.tau.w / (ry.d.w * cos_k);
+          if (k <= ip.D - 1 && s.nl > 0) {
+            store_nee = true;
+            nee_new = 1;
+            uint4 rb = rng_block(ip.key, ip.iteration, pixel, 256u * k, 0);
+            int lidx = (int)(((uint64_t)(rb.x >> 8) * (uint64_t)s.nl) >> 24);
+            if (!(u01(rb.y) < __ldg(s.alias_prob + lidx))) lidx = __ldg(s.alias_idx + lidx);
+            float u2 = u01(rb.z), u3 = u01(rb.w);
+            int lprim = __ldg(s.light_prim + lidx);
+            float3 y, ny;
+            if (lprim < s.nt) {
+              float b1 = u2, b2 = u3;
+              if (b1 + b2 > 1.0f) { b1 = 1.0f - b1; b2 = 1.0f - b2; }
+              float3 a0 = xyz(__ldg(s.tv0 + lprim)), a1 = xyz(__ldg(s.tv1 + lprim)), a2 = xyz(__ldg(s.tv2 + lprim));
+              float3 e1 = sub(a1, a0), e2 = sub(a2, a0);
+              y = add(add(a0, mul(e1, b1)), mul(e2, b2));
+              ny = normalize(cross(e1, e2));
+            } else {
+              float4 sp = __ldg(s.sph + (lprim - s.nt));
+              float3 ce = xyz(sp);
+              float3 w = normalize(sub(p, ce));
+              float z = u2;
+              float rr = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+              float phi = kTwoPi * u3;
+              float3 dir = from_local(w, rr * cosf(phi), rr * sinf(phi), z);
+              y = add(ce, mul(dir, sp.w));
+              ny = dir;
+            }
+            float p_l = light_pdf(s, lidx, y, p);
+            float3 dd = sub(y, p);
+            float dist2 = dot(dd, dd);
+            float dist = sqrtf(dist2);
+            ldir = mul(dd, 1.0f / dist);
+            ldist = dist;
+            float cos_y = -dot(ny, ldir);
+            if (cos_y > 0.0f && p_l > 0.0f) {
+              float cos_x = fabsf(dot(n, ldir));
+              float g = cos_x * cos_y / (dist2 * p_l);
+              Mat lm = load_mat(s.mats, prim_mat(s, lprim));
+              dE = mul(lm.emission, g);
+              g_y = cos_y / (dist2 * p_l);
+              shadow = true;
+            }
+          }
+        }
+      }
+    }
+    // NEE vertex slot (all lanes)
+    int nid = warp_append(&cnt->nee_count, store_nee, ip.cap_nee, &cnt->status);
+    bool emit = false;
+    CamRay nr;
+    if (valid && store_nee && nid >= 0) {
+      bool delta = mat_delta(m);
+      int vflags = (delta ? NV_DELTA : 0) | ((!delta && k <= ip.D - 2) ? NV_MERGEABLE : 0) | (shadow ? NV_SHADOW : 0);
+      nv.pos[nid] = make_float4(p.x, p.y, p.z, Cfac);
+      nv.nrm[nid] = make_float4(n.x, n.y, n.z, __int_as_float(mat | (k << NV_K_SHIFT) | (vflags << NV_FLAG_SHIFT)));
+      nv.wo[nid] = make_float4(-d.x, -d.y, -d.z, __int_as_float(pixel));
+      nv.tau[nid] = make_float4(tau.x, tau.y, tau.z, g_y);
+      nv.err[nid] = make_float4(err.x, err.y, err.z, ldist);
+      nv.ldir[nid] = make_float4(ldir.x, ldir.y, ldir.z, 0.0f);
+      nv.dE[nid] = make_float4(dE.x, dE.y, dE.z, 0.0f);
+      if (slot_map) slot_map[(size_t)pixel * (ip.D - 1) + (k - 1)] = nid;
+    }
+    if (valid && alive) {
+      float3 wo = neg(d);
+      uint4 rb = rng_block(ip.key, ip.iteration, pixel, 256u * k, 1);
+      float3 wi, w;
+      float pdf_f, pdf_r;
+      if (bsdf_sample(m, n, wo, u01(rb.x), u01(rb.y), u01(rb.z), true, wi, w, pdf_f, pdf_r)) {
+        float3 nt = cmul(tau, w);
+        if (maxc(nt) > 0.0f) {
+          float C_k = pdf_r * Cfac;
+          bool delta = mat_delta(m);
+          float3 o = offset_origin(p, n, err, wi);
+          nr.o = make_float4(o.x, o.y, o.z, __int_as_float(pixel));
+          nr.d = make_float4(wi.x, wi.y, wi.z, pdf_f);
+          nr.tau = make_float4(nt.x, nt.y, nt.z, fabsf(dot(n, wi)));
+          nr.mis = make_float4(C_k + (delta ? 0.0f : 1.0f), C_k, __int_as_float(store_nee ? nid : -1),
+                               __int_as_float(delta ? RAY_PREV_DELTA : 0));
+          emit = true;
+        }
+      }
+    }
+    int slot = warp_append(&cnt->cam_count[out_slot], emit, ip.cap_cam, &cnt->status);
+    if (emit && slot >= 0) out[slot] = nr;
+    warp_count(&cnt->camera_rays, rays);
+    warp_count(&cnt->node_visits, visits);
+    warp_count(&cnt->nee_vertices, nee_new);
+    warp_count(&cnt->random_hits, rhits);
+  }
+}
+
+// Shadow rays of the NEE vertices (any hit, tmax = (1 - 1e-4) dist).
+__global__ void __launch_bounds__(kThreads) k_shadow(SceneView s, NeeStore nv, DevCounters* cnt, int cap_nee) {
+  const int count = min(cnt->nee_count, cap_nee);
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
+    const int i = base + threadIdx.x;
+    uint32_t visits = 0, rays = 0;
+    if (i < count) {
+      int bits = __float_as_int(nv.nrm[i].w);
+      if ((bits >> NV_FLAG_SHIFT) & NV_SHADOW) {
+        float4 pp = nv.pos[i], nn = nv.nrm[i], ee = nv.err[i], ld = nv.ldir[i];
+        float3 ldir = xyz(ld);
+        float3 o = offset_origin(xyz(pp), xyz(nn), xyz(ee), ldir);
+        RayPre r = make_ray(o, ldir);
+        rays = 1;
+        if (trace_any(s, r, ee.w * (1.0f - 1e-4f), &cnt->status, visits)) nv.dE[i] = make_float4(0, 0, 0, 0);
+      }
+    }
+    warp_count(&cnt->shadow_rays, rays);
+    warp_count(&cnt->node_visits, visits);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pass 2: NEE contributions and photon emission from the NEE vertices
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_nee(SceneView s, IterParams ip, NeeStore nv, DevCounters* cnt,
+                                                  double* accum, double* split, PhotonRay* __restrict__ phq) {
+  const int count = min(cnt->nee_count, ip.cap_nee);
+  const int stride = gridDim.x * blockDim.x;
+  const int P = ip.W * ip.H;
+  const float pir2 = kPi * ip.r * ip.r;
+  for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
+    const int i = base + threadIdx.x;
+    bool emit = false;
+    PhotonRay ph;
+    uint32_t nphot = 0;
+    if (i < count) {
+      float4 pp = nv.pos[i], nn = nv.nrm[i], ww = nv.wo[i], tt = nv.tau[i], ee = nv.err[i], ld = nv.ldir[i],
+             de = nv.dE[i];
+      int bits = __float_as_int(nn.w);
+      int mat = bits & NV_MAT_MASK, k = (bits >> NV_K_SHIFT) & 63, vflags = (bits >> NV_FLAG_SHIFT) & 7;
+      bool delta = vflags & NV_DELTA;
+      int pixel = __float_as_int(ww.w);
+      float3 p = xyz(pp), n = xyz(nn), wo = xyz(ww), tau = xyz(tt), ldir = xyz(ld), dE = xyz(de);
+      float rho = ld.w, Cfac = pp.w, g_y = tt.w;
+      Mat m = load_mat(s.mats, mat);
+      bool visible = maxc(dE) > 0.0f;
+      if ((ip.mask & 2u) && !delta && visible) {
+        float3 f = bsdf_eval(m, n, wo, ldir);
+        if (maxc(f) > 0.0f) {
+          float pdfF = bsdf_pdf(m, n, wo, ldir), pdfC = bsdf_pdf(m, n, ldir, wo);
+          float inv_w = 1.0f + ((ip.mask & 1u) ? pdfF * g_y : 0.0f) + ((ip.mask & 4u) ? rho * pir2 * pdfC * Cfac : 0.0f);
+          float3 L = mul(cmul(cmul(tau, f), dE), 1.0f / inv_w);
+          add_pixel(accum, split, 1, pixel, L, P);
+        }
+      }
+      if ((ip.mask & 4u) && ip.D >= 3 && visible && rho > 0.0f) {
+        float3 phi0 = mul(dE, 1.0f / rho);
+        uint4 rb = rng_block(ip.key, ip.iteration, pixel, 256u * k + 1u, 1);
+        float3 w1, wt;
+        float pdf1, pdfr1;
+        if (bsdf_sample(m, n, ldir, u01(rb.x), u01(rb.y), u01(rb.z), false, w1, wt, pdf1, pdfr1)) {
+          float3 phi = cmul(phi0, wt);
+          if (maxc(phi) > 0.0f) {
+            float E0 = (((ip.mask & 1u) ? pdfr1 * g_y : 0.0f) + (((ip.mask & 2u) && !delta) ? 1.0f : 0.0f)) /
+                       (rho * pir2);
+            float3 o = offset_origin(p, n, xyz(ee), w1);
+            ph.o = make_float4(o.x, o.y, o.z, __int_as_float(pixel));
+            ph.d = make_float4(w1.x, w1.y, w1.z, pdf1);
+            ph.phi = make_float4(phi.x, phi.y, phi.z, fabsf(dot(n, w1)));
+            ph.mis = make_float4(E0, 1.0f, 0.0f, __int_as_float(k | (1 << 8)));
+            emit = true;
+            nphot = 1;
+          }
+        }
+      }
+    }
+    int slot = warp_append(&cnt->ph_count[0], emit, ip.cap_ph, &cnt->status);
+    if (emit && slot >= 0) phq[slot] = ph;
+    warp_count(&cnt->photons, nphot);
+  }
+}
+
+// pass 3: self emission of the stored random hits (Sec. 3.3)
+__global__ void __launch_bounds__(kThreads) k_emission(SceneView s, IterParams ip, NeeStore nv, const RHEvent* rh,
+                                                       DevCounters* cnt, double* accum, double* split) {
+  const int count = min(cnt->rh_count, ip.cap_rh);
+  const int P = ip.W * ip.H;
+  const float pir2 = kPi * ip.r * ip.r;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+    RHEvent ev = rh[e];
+    int pixel = ev.info.x, prev = ev.info.y, flags = ev.info.z;
+    float C_prev = __int_as_float(ev.info.w);
+    float inv_w = 1.0f;
+    if (!(flags & RAY_FROM_CAMERA)) {
+      float rho = 0.0f;
+      float3 xp;
+      if (prev >= 0) {
+        xp = xyz(nv.pos[prev]);
+        rho = nv.ldir[prev].w;
+      } else {
+        continue;  // the NEE store overflowed; the event cannot be weighted
+      }
+      float p_l = light_pdf(s, __float_as_int(ev.y.w), xyz(ev.y), xp);
+      float q = p_l / ev.L.w;
+      inv_w = 1.0f + (((ip.mask & 2u) && !(flags & RAY_PREV_DELTA)) ? q : 0.0f) +
+              ((ip.mask & 4u) ? q * rho * pir2 * C_prev : 0.0f);
+    }
+    float3 L = mul(xyz(ev.L), 1.0f / inv_w);
+    add_pixel(accum, split, 0, pixel, L, P);
+  }
+}
+
+// Photon walk: closest hit, merge with the view vertices of the hashed grid
+// (inverted search of Sec. 3.2), then the next scattering.
+__global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip, int j, const PhotonRay* __restrict__ in,
+                                                     int in_slot, PhotonRay* __restrict__ out, int out_slot,
+                                                     const MergeRec* __restrict__ mrec,
+                                                     const int* __restrict__ bucket_start, DevCounters* cnt,
+                                                     double* accum, double* split) {
+  const int count = min(cnt->ph_count[in_slot], ip.cap_ph);
+  const int stride = gridDim.x * blockDim.x;
+  const int P = ip.W * ip.H;
+  for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
+    const int i = base + threadIdx.x;
+    bool emit = false;
+    PhotonRay nph;
+    uint32_t visits = 0, hits = 0, tests = 0, merges = 0;
+    if (i < count) {
+      PhotonRay ph = in[i];
+      float3 d = xyz(ph.d);
+      RayPre r = make_ray(xyz(ph.o), d);
+      float t;
+      int prim = trace_closest(s, r, FLT_MAX, t, &cnt->status, visits);
+      if (prim >= 0) {
+        float3 hp, herr, hn;
+        hit_point(s, r, prim, t, hp, herr, hn);
+        Mat hm = load_mat(s.mats, prim_mat(s, prim));
+        if (!mat_black(hm)) {
+          hits = 1;
+          int knee = __float_as_int(ph.mis.w) & 0xff;
+          int pixel = __float_as_int(ph.o.w);
+          float cos_hit = fabsf(dot(hn, d));
+          float cos_orig = ph.phi.w, pdf_dir = ph.d.w;
+          float E0 = ph.mis.x, pA = ph.mis.y, pB = ph.mis.z;
+          float3 phi = xyz(ph.phi);
+          bool hdelta = mat_delta(hm);
+          if (!hdelta) {
+            float s1 = (E0 * pA + pB) * cos_orig / (pdf_dir * cos_hit);
+            float3 md = neg(d);
+            float gx = (hp.x - ip.gmin.x) * ip.cell_inv, gy = (hp.y - ip.gmin.y) * ip.cell_inv,
+                  gz = (hp.z - ip.gmin.z) * ip.cell_inv;
+            int cx = (int)floorf(gx), cy = (int)floorf(gy), cz = (int)floorf(gz);
+            int ox = (gx - (float)cx >= 0.5f) ? 1 : -1, oy = (gy - (float)cy >= 0.5f) ? 1 : -1,
+                oz = (gz - (float)cz >= 0.5f) ? 1 : -1;
+            uint32_t bk[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              bk[c] = grid_hash(cx + ((c & 1) ? ox : 0), cy + ((c & 2) ? oy : 0), cz + ((c & 4) ? oz : 0),
+                                ip.table_mask);
+            for (int c = 0; c < 8; ++c) {
+              bool dup = false;
+              for (int c2 = 0; c2 < c; ++c2) dup |= bk[c2] == bk[c];
+              if (dup) continue;
+              int b0 = __ldg(bucket_start + bk[c]), b1 = __ldg(bucket_start + bk[c] + 1);
+              for (int e = b0; e < b1; ++e) {
+                float4 mp = __ldg(&mrec[e].pos);
+                float dx = mp.x - hp.x, dy = mp.y - hp.y, dz = mp.z - hp.z;
+                float d2 = dx * dx + dy * dy + dz * dz;
+                ++tests;
+                if (!(d2 <= ip.r2)) continue;
+                float4 mn = __ldg(&mrec[e].nrm);
+                int mb = __float_as_int(mn.w);
+                int kk = (mb >> NV_K_SHIFT) & 63;
+                if (kk + j + 1 > ip.D) continue;
+                Mat cm = load_mat(s.mats, mb & NV_MAT_MASK);
+                float4 mw = __ldg(&mrec[e].wo);
+                float3 cn = xyz(mn), cwo = xyz(mw);
+                float3 f = bsdf_eval(cm, cn, cwo, md);
+                if (!(maxc(f) > 0.0f)) continue;
+                float pdfF = bsdf_pdf(cm, cn, cwo, md), pdfC = bsdf_pdf(cm, cn, md, cwo);
+                float inv_w = 1.0f + pdfF * s1 + pdfC * mp.w;
+                float3 ctau = xyz(__ldg(&mrec[e].tau));
+                float3 L = mul(cmul(cmul(ctau, f), phi), ip.kernel / inv_w);
+                add_pixel(accum, split, 2, __float_as_int(mw.w), L, P);
+                ++merges;
+              }
+            }
+          }
+          if (j + 1 <= ip.D - 2) {
+            uint4 rb = rng_block(ip.key, ip.iteration, pixel, 256u * knee + 1u + (uint32_t)j, 1);
+            float3 w, wt;
+            float pdf_f, pdf_r;
+            if (bsdf_sample(hm, hn, neg(d), u01(rb.x), u01(rb.y), u01(rb.z), false, w, wt, pdf_f, pdf_r)) {
+              float3 phi2 = cmul(phi, wt);
+              if (maxc(phi2) > 0.0f) {
+                float ratio = pdf_r * cos_orig / (pdf_dir * cos_hit);
+                float3 o = offset_origin(hp, hn, herr, w);
+                nph.o = make_float4(o.x, o.y, o.z, __int_as_float(pixel));
+                nph.d = make_float4(w.x, w.y, w.z, pdf_f);
+                nph.phi = make_float4(phi2.x, phi2.y, phi2.z, fabsf(dot(hn, w)));
+                nph.mis = make_float4(E0, ratio * pA, (hdelta ? 0.0f : 1.0f) + ratio * pB,
+                                      __int_as_float(knee | ((j + 1) << 8)));
+                emit = true;
+              }
+            }
+          }
+        }
+      }
+    }
+    int slot = warp_append(&cnt->ph_count[out_slot], emit, ip.cap_ph, &cnt->status);
+    if (emit && slot >= 0) out[slot] = nph;
+    warp_count(&cnt->node_visits, visits);
+    warp_count(&cnt->photon_hits, hits);
+    warp_count(&cnt->merge_tests, tests);
+    warp_count(&cnt->merges, merges);
+  }
+}
+
+__global__ void k_reset_photon_slot(DevCounters* cnt, int slot) { cnt->ph_count[slot] = 0; }
+__global__ void k_reset_cam_slot(DevCounters* cnt, int slot) { cnt->cam_count[slot] = 0; }
+
+__global__ void k_resolve(const double* __restrict__ accum, int n, double inv, float* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = (float)(accum[i] * inv);
+}
+
+__global__ void k_fill(float* out, size_t n, float v) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) out[i] = v;
+}
+
+__global__ void k_read_rho(NeeStore nv, const DevCounters* cnt, int D, int cap_nee, float* out) {
+  int count = min(cnt->nee_count, cap_nee);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    int bits = __float_as_int(nv.nrm[i].w);
+    int k = (bits >> NV_K_SHIFT) & 63;
+    int pixel = __float_as_int(nv.wo[i].w);
+    out[(size_t)pixel * (D - 1) + (k - 1)] = nv.ldir[i].w;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// orchestration
+// ---------------------------------------------------------------------------
+struct StageTimer {
+  neb_ctx* c;
+  int idx = 0;
+  cudaEvent_t ev[2 * 64];
+  int stage[64];
+  explicit StageTimer(neb_ctx* ctx) : c(ctx) {}
+  void begin(int s) {
+    if (!c->profiling || idx >= 64) return;
+    stage[idx] = s;
+    cudaEventRecord(c->ev[2 * idx], c->stream);
+  }
+  void end() {
+    if (!c->profiling || idx >= 64) return;
+    cudaEventRecord(c->ev[2 * idx + 1], c->stream);
+    ++idx;
+  }
+  void collect() {
+    if (!c->profiling) return;
+    cudaEventSynchronize(c->ev[2 * idx - 1]);
+    for (int i = 0; i < idx; ++i) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]);
+      c->stage_ms[stage[i]] += ms;
+      c->stage_launches[stage[i]] += 1;
+    }
+  }
+};
+
+IterParams iter_params(const neb_ctx* c, int iteration) {
+  IterParams ip;
+  ip.W = c->W;
+  ip.H = c->H;
+  ip.D = c->D;
+  ip.iteration = iteration;
+  ip.key = make_uint2((uint32_t)(c->cfg.seed & 0xffffffffu), (uint32_t)(c->cfg.seed >> 32));
+  ip.r = c->cfg.merge_radius;
+  ip.r2 = ip.r * ip.r;
+  ip.kernel = (float)(1.0 / (3.14159265358979323846 * (double)ip.r * (double)ip.r));
+  ip.mask = c->cfg.strategy_mask;
+  ip.keep_split = c->cfg.keep_split;
+  ip.cap_cam = c->cap_cam;
+  ip.cap_nee = c->cap_nee;
+  ip.cap_rh = c->cap_rh;
+  ip.cap_ph = c->cap_ph;
+  float cs = 2.0f * ip.r;
+  ip.gmin = f3(c->bmin[0] - cs, c->bmin[1] - cs, c->bmin[2] - cs);
+  ip.cell_inv = 1.0f / cs;
+  ip.table_mask = c->table_size - 1;
+  return ip;
+}
+
+cudaError_t run_iteration(neb_ctx* c, int iteration) {
+  const int B = grid_blocks();
+  SceneView s = scene_view(c);
+  IterParams ip = iter_params(c, iteration);
+  cudaStream_t st = c->stream;
+  StageTimer tm(c);
+  double* split = c->cfg.keep_split ? c->split : nullptr;
+
+  // octree set_iteration (Appendix B): host-side scalars, device re-arm
+  octree_set_iteration_params(c->oct, c->cfg.split_factor, iteration);
+  tm.begin(STAGE_REARM);
+  k_begin<<<1, 1, 0, st>>>(c->counters);
+  if (split) cudaMemsetAsync(c->split, 0, sizeof(double) * 9 * (size_t)c->P, st);
+  if (c->slot_map) cudaMemsetAsync(c->slot_map, 0xff, sizeof(int) * (size_t)c->P * (c->D - 1), st);
+  launch_oct_rearm(c->oct_nodes, c->oct_state, c->oct, st);
+  tm.end();
+
+  // pass 1
+  tm.begin(STAGE_CAMERA);
+  k_camera<<<B, kThreads, 0, st>>>(ip, c->cam, c->camq[0], c->counters);
+  tm.end();
+  for (int k = 1; k <= c->D; ++k) {
+    int in = (k - 1) & 1, out = k & 1;
+    k_reset_cam_slot<<<1, 1, 0, st>>>(c->counters, out);
+    tm.begin(STAGE_EXTEND);
+    k_extend<<<B, kThreads, 0, st>>>(s, ip, k, c->camq[in], in, c->camq[out], out, c->nv, c->rh, c->counters,
+                                     c->slot_map);
+    tm.end();
+  }
+  tm.begin(STAGE_SHADOW);
+  k_shadow<<<B, kThreads, 0, st>>>(s, c->nv, c->counters, c->cap_nee);
+  tm.end();
+  tm.begin(STAGE_INSERT);
+  launch_oct_insert_nee(c);
+  tm.end();
+  // pass 2
+  tm.begin(STAGE_DENSITY);
+  launch_oct_density_nee(c);
+  tm.end();
+  tm.begin(STAGE_NEE);
+  k_nee<<<B, kThreads, 0, st>>>(s, ip, c->nv, c->counters, c->accum, split, c->phq[0]);
+  tm.end();
+  if ((ip.mask & 4u) && c->D >= 3) {
+    tm.begin(STAGE_GRID);
+    grid_build(c, ip);
+    tm.end();
+  }
+  // pass 3 (independent of the photons; enqueued here)
+  tm.begin(STAGE_EMISSION);
+  k_emission<<<B, kThreads, 0, st>>>(s, ip, c->nv, c->rh, c->counters, c->accum, split);
+  tm.end();
+  if ((ip.mask & 4u) && c->D >= 3) {
+    for (int j = 1; j <= c->D - 2; ++j) {
+      int in = (j - 1) & 1, out = j & 1;
+      k_reset_photon_slot<<<1, 1, 0, st>>>(c->counters, out);
+      tm.begin(STAGE_PHOTON);
+      k_photon<<<B, kThreads, 0, st>>>(s, ip, j, c->phq[in], in, c->phq[out], out, c->mrec, c->bucket_start,
+                                       c->counters, c->accum, split);
+      tm.end();
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  tm.collect();
+  return e;
+}
+
+cudaError_t launch_resolve(const double* accum, int P, int iterations, float* out, cudaStream_t st) {
+  int n = P * 3;
+  double inv = iterations > 0 ? 1.0 / iterations : 0.0;
+  k_resolve<<<(n + 255) / 256, 256, 0, st>>>(accum, n, inv, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_read_rho(neb_ctx* c, float* d_out) {
+  k_fill<<<grid_blocks(), 256, 0, c->stream>>>(d_out, (size_t)c->P * (c->D - 1), -1.0f);  // no NEE vertex
+  k_read_rho<<<grid_blocks(), 256, 0, c->stream>>>(c->nv, c->counters, c->D, c->cap_nee, d_out);
+  return cudaGetLastError();
+}
+
+}  // namespace neb

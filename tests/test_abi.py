@@ -1,0 +1,59 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every
+function that include/neb.h declares (no compute calls without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "neb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(neb_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libneb():
+    from paper_1909_00573_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_library_exports_every_declared_function(libneb):
+    names = declared_functions()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(libneb, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header():
+    from paper_1909_00573_gb300 import neb
+    assert sorted(neb.EXPORTS) == declared_functions()
+
+
+def test_argument_errors_without_gpu(libneb):
+    """Invalid arguments are rejected before any device call."""
+    from paper_1909_00573_gb300 import neb
+    L = neb.lib()
+    h = ctypes.c_void_p()
+    cfg = neb.Config(0, 8, 4, 0.01, 64, 4, 0, 0, 0, 7, 0)          # width 0
+    assert L.neb_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
+    cfg = neb.Config(8, 8, 99, 0.01, 64, 4, 0, 0, 0, 7, 0)         # depth above 64
+    assert L.neb_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
+    cfg = neb.Config(8, 8, 4, 0.01, 64, 4, 0, 0, 0, 9, 0)          # unknown strategy bit
+    assert L.neb_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
+    assert L.neb_iterate(None, 1) == -1
+    assert L.neb_philox(None, -1, None, None) == -1
+
+
+def test_product_path_does_not_import_the_oracle():
+    """The package never reaches into oracle/ (the oracle is test infrastructure)."""
+    pkg = os.path.join(ROOT, "paper_1909_00573_gb300")
+    for dp, _, fs in os.walk(pkg):
+        for f in fs:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dp, f)).read()
+                assert not re.search(r"(from\s+oracle|import\s+oracle|liboracle|neb_oracle)", txt), f

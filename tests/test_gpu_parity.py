@@ -1,0 +1,312 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on
+the same seeded inputs.
+
+Tolerances: integer / index work (Philox, octree nodes, neighbour counts,
+closest-hit primitive ids) is compared bit-exactly; FP32 arithmetic that both
+sides perform in the same order without contraction (plane/box area, octree
+density, hit distances) is compared bit-exactly too; per-path radiometric
+contributions (FP32 on the GPU, FP64 in the oracle) within 1e-4 relative on at
+least 99.9 % of paths, the rest only where a discrete decision flips (grazing
+hit, merge radius, octree cell boundary)."""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def neb():
+    from paper_1909_00573_gb300 import build
+    build.build()
+    from paper_1909_00573_gb300 import neb as N
+    return N
+
+
+# --------------------------------------------------------------------------
+def test_philox_device_known_answers(neb):
+    from test_oracle_units import load_kat
+    for ctr, key, out in load_kat():
+        assert neb.philox([ctr], key)[0].tolist() == out
+
+
+def test_philox_device_equals_oracle(neb, oracle):
+    rng = np.random.default_rng(11)
+    ctr = rng.integers(0, 2 ** 32, (512, 4), dtype=np.uint64).astype(np.uint32)
+    key = [0x12345678, 0x9abcdef0]
+    g = neb.philox(ctr, key)
+    for i in range(0, 512, 37):
+        assert g[i].tolist() == oracle.philox4x32_10(ctr[i], key).tolist()
+
+
+def test_plane_box_area_bit_exact(neb, oracle):
+    rng = np.random.default_rng(12)
+    n = 4000
+    lo = rng.uniform(-2, 2, (n, 3)).astype(np.float32)
+    hi = (lo + rng.uniform(0.01, 2, (n, 3))).astype(np.float32)
+    pos = (lo + rng.uniform(-0.2, 1.2, (n, 3)) * (hi - lo)).astype(np.float32)
+    nrm = rng.normal(size=(n, 3))
+    nrm[: n // 4, 0] = 0.0                      # the 2D cases
+    nrm[n // 4: n // 2] = [0.0004, 0.9999999, 0.0002]   # the 1D cases
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    nrm = nrm.astype(np.float32)
+    g = neb.plane_box_area(np.concatenate([lo, hi], 1), pos, nrm)
+    o = np.array([oracle.intersection_area(lo[i], hi[i], pos[i], nrm[i]) for i in range(n)], np.float32)
+    assert np.array_equal(g.view(np.int32), o.view(np.int32))
+
+
+# --------------------------------------------------------------------------
+# density octree
+# --------------------------------------------------------------------------
+def _octree_inputs(seed, n_iter=3, n=6000):
+    """Seeded vertex streams: clustered points on two planes (shared by both sides)."""
+    rng = np.random.default_rng(seed)
+    its = []
+    for _ in range(n_iter):
+        a = np.stack([rng.uniform(0, 1, n), np.full(n, 0.31), rng.uniform(0, 1, n)], 1)
+        b = np.stack([rng.normal(0.7, 0.05, n), rng.uniform(0, 1, n), np.full(n, 0.83)], 1)
+        its.append(np.clip(np.concatenate([a, b]), 0, 1).astype(np.float32))
+    return its
+
+
+@pytest.mark.parametrize("split", [4, 8])
+def test_octree_sequential_bit_exact(neb, oracle, split):
+    its = _octree_inputs(13 + split)
+    g = neb.Octree([0, 0, 0], [1, 1, 1], 1 << 14, split)
+    o = oracle.Octree([0, 0, 0], [1, 1, 1], 1 << 14, split)
+    for i, pts in enumerate(its, start=1):
+        g.set_iteration(i)
+        o.set_iteration(i)
+        g.insert(pts, mode=1)
+        o.insert(pts)
+        gn, ga, gd, gs = g.read()
+        on, oa, od = o.dump()
+        assert (ga, gd) == (oa, od)
+        assert np.array_equal(gn, on)
+    rng = np.random.default_rng(14)
+    q = np.concatenate([its[-1][:500], rng.uniform(0, 1, (500, 3))]).astype(np.float32)
+    nq = rng.normal(size=(1000, 3))
+    nq[:250] = [0, 1, 0]
+    nq /= np.linalg.norm(nq, axis=1, keepdims=True)
+    nq = nq.astype(np.float32)
+    for robust in (False, True):
+        gr = g.density(q, nq, robust)
+        orr = o.density(q, nq, robust)
+        assert np.array_equal(gr.view(np.int32), orr.view(np.int32)), robust
+
+
+def test_octree_concurrent_conserves_counts(neb):
+    """Every insert is accounted for: sum over leaves of (final - initial) plus,
+    for cells split in this iteration, (threshold - initial) equals the number
+    of inserted vertices (the splitting vertex stays counted in the parent,
+    racing vertices are re-counted in the children: Appendix B)."""
+    its = _octree_inputs(21, n_iter=3, n=40000)
+    split = 4
+    g = neb.Octree([0, 0, 0], [1, 1, 1], 1 << 20, split)
+    for i, pts in enumerate(its, start=1):
+        g.set_iteration(i)
+        before, a0, _, _ = g.read()
+        g.insert(pts, mode=0)
+        after, a1, depth, status = g.read()
+        assert status & neb.STATUS_SPIN_TIMEOUT == 0
+        T = split * i
+        total = 0
+        for idx in range(a1):
+            b, a = int(before[idx]), int(after[idx])
+            if b < 0:
+                continue           # split in an earlier iteration
+            total += (a - b) if a >= 0 else (T - b)
+        assert total == len(pts)
+        assert a1 > a0
+
+
+def test_octree_concurrent_close_to_sequential(neb, oracle):
+    its = _octree_inputs(31, n_iter=2, n=20000)
+    g = neb.Octree([0, 0, 0], [1, 1, 1], 1 << 18, 4)
+    o = oracle.Octree([0, 0, 0], [1, 1, 1], 1 << 18, 4)
+    for i, pts in enumerate(its, start=1):
+        g.set_iteration(i)
+        o.set_iteration(i)
+        g.insert(pts, mode=0)
+        o.insert(pts)
+    q = its[-1][::10]
+    nq = np.tile(np.array([0, 1, 0], np.float32), (len(q), 1))
+    gr = g.density(q, nq, True)
+    orr = o.density(q, nq, True)
+    ok = (orr > 0) & (gr > 0)
+    assert ok.mean() > 0.95
+    # split order differs between runs; the estimate stays close on average
+    ratio = np.median(gr[ok] / orr[ok])
+    assert 0.9 < ratio < 1.1
+    _, ga, _, _ = g.read()
+    _, oa, _ = o.dump()
+    assert abs(ga - oa) <= 0.05 * oa
+
+
+# --------------------------------------------------------------------------
+# BVH closest hit, merge grid
+# --------------------------------------------------------------------------
+def _rays(rng, n, lo, hi):
+    o = rng.uniform(lo, hi, (n, 3))
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return np.concatenate([o, d], 1).astype(np.float32)
+
+
+@pytest.mark.parametrize("name", ["tiny_room", "soup", "spheres"])
+def test_bvh_closest_hit_equals_oracle(neb, oracle, name):
+    from paper_1909_00573_gb300 import scenes
+    rng = np.random.default_rng(41)
+    if name == "tiny_room":
+        s = scenes.tiny_room()
+        rays = _rays(rng, 20000, 0.02, 0.98)
+    elif name == "soup":
+        tri = rng.uniform(-1, 1, (3000, 3, 3)).astype(np.float32)
+        tri[:, 1:] = tri[:, :1] + 0.1 * (tri[:, 1:] - tri[:, :1])
+        s = scenes.Scene(tri, np.zeros(3000), np.zeros((0, 4)), np.zeros(0),
+                         scenes.material(0, (0.5,) * 3)[None], np.zeros(10))
+        rays = _rays(rng, 20000, -1.2, 1.2)
+    else:
+        sph = np.concatenate([rng.uniform(-1, 1, (500, 3)), rng.uniform(0.01, 0.1, (500, 1))], 1)
+        s = scenes.Scene(np.zeros((0, 3, 3)), np.zeros(0), sph, np.zeros(500),
+                         scenes.material(0, emission=(1, 1, 1))[None], np.zeros(10))
+        rays = _rays(rng, 20000, -1.2, 1.2)
+    rc = scenes.RenderConfig(8, 8, 4, 0.01, 1024, 4, 1)
+    ctx = neb.Context(neb.make_config(rc))
+    ctx.scene_upload(s)
+    ctx.build_bvh()
+    gp, gt = ctx.trace_closest(rays)
+    assert ctx.stats()["status"] == 0
+    op, ot = oracle.trace(s, rays)
+    same = gp == op
+    assert same.mean() >= 0.9999, same.mean()
+    hit = same & (gp >= 0)
+    assert np.array_equal(gt[hit].view(np.int32), ot[hit].view(np.int32))
+    assert (gp >= 0).mean() > 0.3
+
+
+def test_neighbour_counts_equal_brute_force(neb, oracle):
+    rng = np.random.default_rng(51)
+    pts = rng.uniform(0, 1, (30000, 3)).astype(np.float32)
+    q = np.concatenate([rng.uniform(0, 1, (3000, 3)), pts[:1000]]).astype(np.float32)
+    for r in (0.01, 0.037):
+        g = neb.count_neighbours(pts, q, r)
+        o = oracle.count_neighbours(pts, q, r, brute=True)
+        assert np.array_equal(g, o)
+    assert neb.count_neighbours(np.zeros((0, 3), np.float32), q[:5], 0.1).tolist() == [0] * 5
+
+
+# --------------------------------------------------------------------------
+# whole iterations
+# --------------------------------------------------------------------------
+def _compare(g, o, rel=1e-4, floor_frac=1e-6):
+    """Fraction of entries with |g - o| <= rel |o| + floor (floor from the image scale)."""
+    floor = floor_frac * max(float(np.abs(o).max()), 1e-30)
+    return np.abs(g - o) <= rel * np.abs(o) + floor
+
+
+def test_tiny_room_per_path_parity(neb, oracle):
+    """Config tiny room (64x64, D = 8, r = 0.01, 2^16 nodes, split 8, 4
+    iterations), deterministic octree: every camera path's contribution in the
+    last iteration, split by strategy, matches the oracle."""
+    from paper_1909_00573_gb300 import scenes
+    s, rc = scenes.workload("tiny_room")
+    rc.octree_mode = 1
+    ctx = neb.render(s, rc)
+    gsplit, grho, gacc, st = ctx.read_split(), ctx.read_nee_rho(), ctx.read_accum(), ctx.stats()
+    ctx.close()
+    ref = oracle.render(s, rc, want_rho=True)
+    osplit, orho, oacc = ref["split"], ref["rho"], ref["accum"]
+    assert st["status"] & ~neb.STATUS_OCTREE_FULL == 0
+    # per path (pixel of the last iteration), all strategies together
+    tot_ok = _compare(gsplit.sum(0).sum(-1), osplit.sum(0).sum(-1))
+    assert tot_ok.mean() >= 0.999, tot_ok.mean()
+    for k in range(3):
+        ok = _compare(gsplit[k].sum(-1), osplit[k].sum(-1))
+        assert ok.mean() >= 0.995, (k, ok.mean())
+    # the density at every NEE vertex
+    both = (grho >= 0) & (orho >= 0)
+    assert np.array_equal(grho >= 0, orho >= 0) or ((grho >= 0) != (orho >= 0)).mean() < 1e-3
+    assert np.mean(grho[both] == orho[both]) >= 0.999
+    # the progressive sums over all iterations
+    assert _compare(gacc.sum(-1), oacc.sum(-1)).mean() >= 0.995
+    # counters agree with the oracle's
+    assert st["nee_vertices"] == ref["stats"]["nee_vertices"] or \
+        abs(st["nee_vertices"] - ref["stats"]["nee_vertices"]) <= 2
+
+
+def test_ragged_small_image_parity(neb, oracle):
+    """Odd image size (a ragged last block), D = 3 (one photon bounce)."""
+    from paper_1909_00573_gb300 import scenes
+    s = scenes.tiny_room()
+    rc = scenes.RenderConfig(37, 23, 3, 0.02, 4096, 4, 2, octree_mode=1)
+    ctx = neb.render(s, rc)
+    g = ctx.read_split()
+    ctx.close()
+    o = oracle.render(s, rc)["split"]
+    assert _compare(g.sum(0).sum(-1), o.sum(0).sum(-1)).mean() >= 0.995
+
+
+def test_glass_sphere_energy_gpu(neb):
+    from paper_1909_00573_gb300 import scenes
+    s = scenes.glass_in_emitting_box()
+    rc = scenes.RenderConfig(64, 64, 24, 0.01, 1 << 16, 8, 1)
+    ctx = neb.render(s, rc, keep_split=False)
+    v = ctx.read_accum()[..., 0]
+    ctx.close()
+    ones = np.abs(v - 1.0) < 2e-5
+    assert np.all(ones | (v == 0.0)) and ones.mean() > 0.97
+
+
+def test_white_furnace_gpu(neb):
+    import math
+    from paper_1909_00573_gb300 import scenes
+    s = scenes.white_furnace(0.5, 1.0)
+    D = 5
+    expect = sum(0.5 ** j for j in range(D))
+    for mask in (1, 3):
+        rc = scenes.RenderConfig(64, 64, D, 0.02, 1 << 16, 8, 1, strategy_mask=mask)
+        vals = []
+        ctx = neb.Context(neb.make_config(rc, keep_split=True))
+        ctx.scene_upload(s)
+        ctx.build_bvh()
+        for _ in range(4):
+            ctx.iterate(1)
+            vals.append(ctx.read_split().sum(0)[..., 0])
+        ctx.close()
+        v = np.stack(vals).ravel()
+        se = v.std(ddof=1) / math.sqrt(v.size)
+        assert abs(v.mean() - expect) < 3 * se, (mask, v.mean(), expect, se)
+    rc = scenes.RenderConfig(64, 64, D, 0.02, 1 << 16, 8, 4)
+    ctx = neb.render(s, rc)
+    img = ctx.resolve()[..., 0]
+    ctx.close()
+    assert abs(img.mean() / expect - 1) < 0.05
+
+
+def test_zero_and_degenerate_inputs(neb):
+    from paper_1909_00573_gb300 import scenes
+    s = scenes.tiny_room()
+    # D = 1: only directly visible emitters, no NEE vertices
+    rc = scenes.RenderConfig(16, 16, 1, 0.01, 64, 4, 2)
+    ctx = neb.render(s, rc)
+    st = ctx.stats()
+    assert st["nee_vertices"] == 0 and st["photons"] == 0
+    ctx.close()
+    # a scene without lights renders black
+    dark = scenes.Scene(s.tri[:10], s.tri_mat[:10], np.zeros((0, 4)), np.zeros(0), s.mats, s.cam)
+    ctx = neb.render(dark, scenes.RenderConfig(16, 16, 4, 0.01, 64, 4, 1))
+    assert np.all(ctx.resolve() == 0)
+    ctx.close()
+    # a tiny octree overflows gracefully (status bit, no error)
+    rc = scenes.RenderConfig(32, 32, 6, 0.01, 8, 4, 2)          # 1 + 8 nodes
+    ctx = neb.render(s, rc)
+    st = ctx.stats()
+    assert st["status"] == neb.STATUS_OCTREE_FULL and st["octree_nodes"] == 9
+    ctx.close()
+    # argument errors surface as exceptions
+    with pytest.raises(neb.NebError):
+        neb.Context(neb.make_config(scenes.RenderConfig(0, 4, 4, 0.01, 64, 4, 1)))
