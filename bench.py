@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark of the NEB iteration on one or more GB300s.
+
+Workload: the large-city scene (400 x 400 seeded boxes, ~1.95M triangles, a
+glass torus of extent diag/1000, 16 sphere lights), 1280 x 720 camera paths
+per iteration, maximum path length 10, merge radius 1e-3 of the torus extent,
+4M-node density octree, split factor 4.  A step is one NEB iteration (all
+passes) over the 921,600 paths of one image.
+
+Prints one JSON line (rank 0).  value = camera paths per second over all GPUs
+(Mpaths/s) with the scene resident in HBM; e2e = the same metric through the
+C ABI from pinned host buffers (scene upload, BVH build, iterations and an
+image read back per step inside the timed region).
+
+--impl reference times the CPU oracle (the plain single-threaded C
+implementation used by the parity tests) on a band of the same image.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpaths/s"
+WORKLOAD = "large_city"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=32)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+def load_peaks():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def stage_bytes(stage, d, P, iters):
+    """Algorithmic bytes of one stage over the profiled iterations (per-unit
+    figures: 64 B per ray record read or written, 112 B per NEE record, 48 B
+    per random-hit event, 64 B per BVH node visit, 48 B per triangle test,
+    16 B per merge candidate tested plus 48 B and 24 B of FP64 atomics per
+    accepted merge)."""
+    trav = {"extend": 0, "shadow": 1, "photon": 2}
+    if stage == "extend":
+        rec = 64 * d["camera_rays"] + 64 * max(d["camera_rays"] - P * iters, 0) + 112 * d["nee_vertices"] + \
+            48 * d["random_hits"]
+    elif stage == "shadow":
+        rec = 64 * d["nee_vertices"] + 16 * d["shadow_rays"]
+    elif stage == "photon":
+        rec = 64 * 2 * d["photon_hits"] + 16 * d["merge_tests"] + (48 + 24) * d["merges"]
+    else:
+        return None, None
+    k = trav[stage]
+    tr = 64 * d["stage_node_visits"][k] + 48 * d["stage_prim_tests"][k]
+    return rec + tr, rec
+
+
+def stats_delta(a, b):
+    out = {}
+    for k, v in b.items():
+        if isinstance(v, list):
+            out[k] = [x - y for x, y in zip(v, a[k])]
+        elif isinstance(v, int):
+            out[k] = v - a.get(k, 0)
+    return out
+
+
+def cpu_baseline_sample(scene, rc, rows, n_iter=1):
+    from oracle import oracle as O
+    W, H = rc.width, rc.height
+    r0 = max(0, H // 2 - rows // 2)
+    res = O.render(scene, rc, n_iter=n_iter, pixel_range=(r0 * W, (r0 + rows) * W), want_split=False)
+    t = float(sum(res["iter_seconds"]))
+    paths = rows * W * n_iter
+    return paths, t, f"{rows} rows x {W} px (rows {r0}..{r0 + rows - 1}) of the {W}x{H} image, " \
+                     f"{n_iter} iteration(s), single thread"
+
+
+# ----------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_1909_00573_gb300 import scenes
+    O.build()
+    scene, rc = scenes.workload(args.workload)
+    steps, warm = max(args.steps, 1), max(args.warmup, 0)
+    # size one step so the whole run takes ~90 s of oracle time (~5k paths/s)
+    t_step = 90.0 / (steps + warm)
+    rows = max(1, int(t_step * 5000 / rc.width))
+    W = rc.width
+    r0 = max(0, rc.height // 2 - rows // 2)
+    res = O.render(scene, rc, n_iter=steps + warm, pixel_range=(r0 * W, (r0 + rows) * W), want_split=False)
+    it = res["iter_seconds"][warm:]
+    paths = rows * W
+    sec = float(sum(it))
+    value = paths * len(it) / sec / 1e6
+    sample = f"{rows} rows x {W} px (rows {r0}..{r0 + rows - 1}) of the {W}x{rc.height} image per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": steps, "warmup": warm, "ms_per_step": 1000 * sec / len(it), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(rc, scene),
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def config_dict(rc, scene):
+    return {"workload": f"{scene.name}: {scene.n_tri} triangles, {scene.n_sph} sphere lights, "
+                        f"{rc.width}x{rc.height}, 1 spp per iteration, D={rc.max_depth}, "
+                        f"r={rc.merge_radius:.3g}, octree {rc.octree_capacity} nodes, split {rc.split_factor}",
+            "paths_per_step": rc.width * rc.height, "max_depth": rc.max_depth,
+            "octree_mode": "concurrent" if rc.octree_mode == 0 else "sequential",
+            "l2": "inputs larger than L2 (scene + BVH + per-iteration records > 129 MB)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1909_00573_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    if dist:
+        dist.barrier()
+    from paper_1909_00573_gb300 import neb, scenes
+
+    scene, rc = scenes.workload(args.workload)
+    rc.seed = rank                      # replicas render independent sample streams
+    P = rc.width * rc.height
+    stream = torch.cuda.current_stream()
+    ctx = neb.Context(neb.make_config(rc), stream.cuda_stream)
+    ctx.scene_upload(scene)
+    ctx.build_bvh()
+    ctx.iterate(args.warmup)
+    torch.cuda.synchronize()
+    s0 = ctx.stats(check=False)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    ctx.iterate(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    s1 = ctx.stats(check=False)
+    d = stats_delta(s0, s1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * P * args.steps / (ms / 1000.0) / 1e6
+
+    # ---- per-stage times (CUDA events on the context stream), roofline of the dominant kernel
+    ctx.set_profiling(True)
+    p0 = ctx.stats(check=False)
+    ctx.iterate(args.profile_steps)
+    torch.cuda.synchronize()
+    p1 = ctx.stats(check=False)
+    stages = ctx.stage_times()
+    ctx.set_profiling(False)
+    pd = stats_delta(p0, p1)
+    peak, peak_kind = load_peaks()
+    dom = max(stages, key=lambda k: stages[k][0])
+    dom_ms, dom_launches = stages[dom]
+    byt, byt_nt = stage_bytes(dom, pd, P, args.profile_steps)
+    roof = None
+    if byt is not None and dom_ms > 0:
+        per_launch = byt / dom_launches
+        avg_ms = dom_ms / dom_launches
+        achieved = per_launch / (avg_ms / 1000.0) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                "bytes_per_launch": per_launch, "avg_launch_ms": avg_ms,
+                "achieved_without_traversal": (byt_nt / dom_launches) / (avg_ms / 1000.0) / 1e9}
+    total_stage_ms = sum(v[0] for v in stages.values())
+    ctx.close()
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+        hs = scenes.Scene(pin(scene.tri), pin(scene.tri_mat), pin(scene.sph), pin(scene.sph_mat),
+                          pin(scene.mats), pin(scene.cam), scene.name)
+        img = torch.empty((rc.height, rc.width, 3), dtype=torch.float32).pin_memory()
+        h2d = hs.tri.nbytes + hs.tri_mat.nbytes + hs.sph.nbytes + hs.sph_mat.nbytes + hs.mats.nbytes + hs.cam.nbytes
+        ctx2 = neb.Context(neb.make_config(rc), stream.cuda_stream)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx2.scene_upload(hs)
+        ctx2.build_bvh()
+        for _ in range(args.steps):
+            ctx2.iterate(1)
+            neb.lib().neb_resolve(ctx2.h, neb.vp(img.data_ptr()), 0)
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([t_e2e], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        ctx2.close()
+        e2e = {"value": world * P * args.steps / t_e2e / 1e6, "unit": METRIC,
+               "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(img.numel() * 4),
+               "note": "scene upload + BVH build once per job (h2d amortised over the steps), image read back "
+                       "to pinned host memory every step"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        paths, sec, sample = cpu_baseline_sample(scene, rc, rows=64)
+        cpu = {"value": paths / sec / 1e6, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_dict(rc, scene), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(d.get("kernel_launches", 0)), "clocks": clk,
+                "stages_ms_per_step": {k: v[0] / args.profile_steps for k, v in stages.items()},
+                "stage_sum_ms_per_step": total_stage_ms / args.profile_steps,
+                "counters_per_step": {k: (v / args.steps if not isinstance(v, list) else [x / args.steps for x in v])
+                                      for k, v in d.items() if k not in ("iterations",)},
+                "status": s1["status"]}
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

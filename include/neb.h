@@ -73,6 +73,9 @@ typedef struct {
   int64_t merge_tests, merges, random_hits;
   int64_t octree_inserts, octree_queries;  /* queries count each of the five robust lookups */
   int64_t bvh_node_visits, prim_tests;
+  int64_t kernel_launches;                 /* kernels enqueued by neb_iterate */
+  int64_t stage_node_visits[3];            /* BVH node visits of the extend, shadow and photon kernels */
+  int64_t stage_prim_tests[3];             /* primitive tests of the same kernels */
   int32_t octree_nodes, octree_depth;
   uint32_t status;                         /* NEB_STATUS_* bits, sticky */
   int32_t pad;

@@ -37,12 +37,20 @@
  *    dim/4, iteration); stream = 256*k for view vertex k, 256*k + 1 + s for
  *    the s-th scattering of the photon leaving NEE vertex k.
  */
+#define _POSIX_C_SOURCE 199309L
 #include "neb_oracle.h"
 
 #include <float.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
+
+static double now_seconds(void) {
+  struct timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
 
 #define PI_D 3.14159265358979323846
 #define TWO_PI_F 6.28318530717958647692f
@@ -1271,6 +1279,7 @@ int orc_render(const orc_scene* scene_in, const orc_config* cfg, int n_iter, dou
   int first = cfg->first_iteration > 0 ? cfg->first_iteration : 1;
 
   for (int it = 0; it < n_iter; ++it) {
+    double t_start = now_seconds();
     int iter = first + it;
     int last = it == n_iter - 1;
     c.rng.iter = (uint32_t)iter;
@@ -1468,6 +1477,7 @@ int orc_render(const orc_scene* scene_in, const orc_config* cfg, int n_iter, dou
         }
       }
     }
+    if (cfg->iter_seconds) cfg->iter_seconds[it] = now_seconds() - t_start;
   }
   st[ORC_ST_OCTREE_NODES] = oct->alloc < oct->capacity ? oct->alloc : oct->capacity;
   st[ORC_ST_OCTREE_DEPTH] = oct->depth;

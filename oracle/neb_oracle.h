@@ -45,6 +45,7 @@ typedef struct {
   uint32_t strategy_mask;  /* 1 random hit, 2 NEE, 4 NEB photon merge */
   int first_iteration;     /* 1-based index of the first iteration rendered */
   int pixel_begin, pixel_end; /* camera paths traced: [begin, end) (row-major), end<=0: all */
+  double* iter_seconds;       /* optional [n_iter]: wall time of each iteration (BVH build excluded) */
 } orc_config;
 
 /* stats[] slots filled by orc_render (summed over iterations) */

@@ -46,7 +46,8 @@ class _Config(C.Structure):
     _fields_ = [("width", C.c_int), ("height", C.c_int), ("max_depth", C.c_int),
                 ("merge_radius", C.c_float), ("octree_capacity", C.c_int), ("split_factor", C.c_int),
                 ("seed", C.c_uint64), ("density_mode", C.c_int), ("strategy_mask", C.c_uint32),
-                ("first_iteration", C.c_int), ("pixel_begin", C.c_int), ("pixel_end", C.c_int)]
+                ("first_iteration", C.c_int), ("pixel_begin", C.c_int), ("pixel_end", C.c_int),
+                ("iter_seconds", C.c_void_p)]
 
 
 _lib = None
@@ -182,8 +183,9 @@ def render(scene, cfg, n_iter=None, first_iteration=1, pixel_range=None, want_sp
     n_iter = cfg.iterations if n_iter is None else n_iter
     s, keep = _scene_struct(scene)
     pb, pe = (0, 0) if pixel_range is None else pixel_range
+    iter_sec = np.zeros(max(int(n_iter), 1), np.float64)
     c = _Config(cfg.width, cfg.height, cfg.max_depth, cfg.merge_radius, cfg.octree_capacity, cfg.split_factor,
-                cfg.seed, cfg.density_mode, cfg.strategy_mask, first_iteration, pb, pe)
+                cfg.seed, cfg.density_mode, cfg.strategy_mask, first_iteration, pb, pe, _ptr(iter_sec))
     P = cfg.width * cfg.height
     accum = np.zeros((P, 3), np.float64)
     split = np.zeros((3, P, 3), np.float64) if want_split else None
@@ -193,7 +195,8 @@ def render(scene, cfg, n_iter=None, first_iteration=1, pixel_range=None, want_sp
     if rc != 0:
         raise RuntimeError(f"orc_render failed: {rc}")
     out = {"accum": accum.reshape(cfg.height, cfg.width, 3),
-           "stats": dict(zip(ST_NAMES, stats.tolist()))}
+           "stats": dict(zip(ST_NAMES, stats.tolist())),
+           "iter_seconds": iter_sec[:n_iter]}
     if want_split:
         out["split"] = split.reshape(3, cfg.height, cfg.width, 3)
     if want_rho:

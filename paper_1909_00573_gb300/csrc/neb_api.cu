@@ -320,6 +320,7 @@ extern "C" int neb_scene_upload(neb_ctx* c, const float* tri, const uint32_t* tr
   cudaMemsetAsync(c->accum, 0, sizeof(double) * 3 * (size_t)c->P, st);
   cudaMemsetAsync(c->counters, 0, sizeof(DevCounters), st);
   c->iteration = 0;
+  c->launches = 0;
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(c, NEB_ERR_CUDA, "neb_scene_upload", e);
   c->scene_ready = true;
@@ -414,6 +415,11 @@ extern "C" int neb_get_stats(neb_ctx* c, neb_stats* out) {
   out->octree_queries = (int64_t)h.octree_queries;
   out->bvh_node_visits = (int64_t)h.node_visits;
   out->prim_tests = (int64_t)h.prim_tests;
+  out->kernel_launches = c->launches;
+  for (int i = 0; i < 3; ++i) {
+    out->stage_node_visits[i] = (int64_t)h.visits_by[i];
+    out->stage_prim_tests[i] = (int64_t)h.ptests_by[i];
+  }
   out->octree_nodes = os.alloc < c->oct_cap ? os.alloc : c->oct_cap;
   out->octree_depth = os.depth;
   out->status = h.status | os.status;

@@ -304,8 +304,8 @@ __global__ void k_trace_debug(SceneView s, const float* __restrict__ rays, int n
     RayPre r = make_ray(f3(rays[6 * i], rays[6 * i + 1], rays[6 * i + 2]),
                         f3(rays[6 * i + 3], rays[6 * i + 4], rays[6 * i + 5]));
     float t;
-    uint32_t visits = 0;
-    int p = trace_closest(s, r, FLT_MAX, t, status, visits);
+    uint32_t visits = 0, ptests = 0;
+    int p = trace_closest(s, r, FLT_MAX, t, status, visits, ptests);
     prim[i] = p;
     tout[i] = p >= 0 ? t : __int_as_float(0x7f800000);
   }

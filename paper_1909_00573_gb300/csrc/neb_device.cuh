@@ -380,7 +380,7 @@ __device__ __forceinline__ float isect_prim(const SceneView& s, const RayPre& r,
 // Closest hit with t in (deltaT, tmax); equal distances go to the lower
 // primitive index.  Children are visited near-first; leaves hold one primitive.
 __device__ __forceinline__ int trace_closest(const SceneView& s, const RayPre& r, float tmax, float& t_out,
-                                             uint32_t* status, uint32_t& visits) {
+                                             uint32_t* status, uint32_t& visits, uint32_t& ptests) {
   int best = -1;
   float best_t = tmax;
   if (s.nt + s.ns == 0) { t_out = tmax; return -1; }
@@ -397,12 +397,14 @@ __device__ __forceinline__ int trace_closest(const SceneView& s, const RayPre& r
     bool hr = box_hit(f3(b.x, b.z, c.z), f3(b.y, b.w, c.w), r, best_t, tr);
     if (hl && ch.x < 0) {
       int p = ~ch.x;
+      ++ptests;
       float t = isect_prim(s, r, p);
       if (t > 0.0f && t < tmax && (t < best_t || (t == best_t && best >= 0 && p < best))) { best_t = t; best = p; }
       hl = false;
     }
     if (hr && ch.y < 0) {
       int p = ~ch.y;
+      ++ptests;
       float t = isect_prim(s, r, p);
       if (t > 0.0f && t < tmax && (t < best_t || (t == best_t && best >= 0 && p < best))) { best_t = t; best = p; }
       hr = false;
@@ -428,7 +430,7 @@ __device__ __forceinline__ int trace_closest(const SceneView& s, const RayPre& r
 
 // Any hit with t in (deltaT, tmax).
 __device__ __forceinline__ bool trace_any(const SceneView& s, const RayPre& r, float tmax, uint32_t* status,
-                                          uint32_t& visits) {
+                                          uint32_t& visits, uint32_t& ptests) {
   if (s.nt + s.ns == 0) return false;
   int stack[64];
   int sp = 0;
@@ -442,11 +444,13 @@ __device__ __forceinline__ bool trace_any(const SceneView& s, const RayPre& r, f
     bool hl = box_hit(f3(a.x, a.z, c.x), f3(a.y, a.w, c.y), r, tmax, tl);
     bool hr = box_hit(f3(b.x, b.z, c.z), f3(b.y, b.w, c.w), r, tmax, tr);
     if (hl && ch.x < 0) {
+      ++ptests;
       float t = isect_prim(s, r, ~ch.x);
       if (t > 0.0f && t < tmax) return true;
       hl = false;
     }
     if (hr && ch.y < 0) {
+      ++ptests;
       float t = isect_prim(s, r, ~ch.y);
       if (t > 0.0f && t < tmax) return true;
       hr = false;

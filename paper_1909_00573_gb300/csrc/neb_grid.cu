@@ -60,6 +60,11 @@ __global__ void k_scan_add(int* __restrict__ out, size_t n, const int* __restric
     if (base + j < n) out[base + j] += o;
 }
 
+int scan_launch_count(size_t n) {
+  size_t nb = (n + kScanTile - 1) / kScanTile;
+  return nb <= 1 ? 1 : 2 + scan_launch_count(nb);
+}
+
 size_t scan_scratch_ints(size_t n) {
   size_t total = 0;
   while (n > (size_t)kScanTile) {

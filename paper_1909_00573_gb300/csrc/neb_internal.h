@@ -71,6 +71,7 @@ struct DevCounters {
   unsigned long long camera_rays, nee_vertices, shadow_rays, photons, photon_hits;
   unsigned long long merge_tests, merges, random_hits, octree_inserts, octree_queries;
   unsigned long long node_visits, prim_tests;
+  unsigned long long visits_by[3], ptests_by[3];  // extend, shadow, photon kernels
 };
 
 struct CameraParams {
@@ -145,6 +146,7 @@ struct neb_ctx {
   double* split = nullptr;
   neb::DevCounters* counters = nullptr;
   int iteration = 0;  // iterations completed (enqueued)
+  long long launches = 0;  // kernels enqueued by neb_iterate
 
   // profiling
   bool profiling = false;
@@ -168,6 +170,7 @@ cudaError_t launch_area(const float* d_boxes, const float* d_pos, const float* d
 
 // neb_grid.cu
 size_t scan_scratch_ints(size_t n);
+int scan_launch_count(size_t n);
 cudaError_t scan_exclusive(const int* d_in, int* d_out, size_t n, Scratch& scratch, cudaStream_t st);
 cudaError_t grid_build(neb_ctx* c, const IterParams& ip);
 cudaError_t count_neighbours_device(const float* d_pts, int n, const float* d_q, int m, float r, int* d_out,

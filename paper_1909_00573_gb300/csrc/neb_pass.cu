@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
   for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
     const int i = base + threadIdx.x;
     const bool valid = i < count;
-    uint32_t visits = 0, rays = 0, nee_new = 0, rhits = 0;
+    uint32_t visits = 0, ptests = 0, rays = 0, nee_new = 0, rhits = 0;
     bool store_nee = false, alive = false;
     CamRay ry;
     float3 p = f3(0, 0, 0), n = f3(0, 0, 0), err = f3(0, 0, 0), d = f3(0, 0, 0), tau = f3(0, 0, 0);
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
       flags = __float_as_int(ry.mis.w);
       RayPre r = make_ray(xyz(ry.o), d);
       float t;
-      int prim = trace_closest(s, r, FLT_MAX, t, &cnt->status, visits);
+      int prim = trace_closest(s, r, FLT_MAX, t, &cnt->status, visits, ptests);
       if (prim >= 0) {
         hit_point(s, r, prim, t, p, err, n);
         mat = prim_mat(s, prim);
@@ -254,6 +254,9 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
     if (emit && slot >= 0) out[slot] = nr;
     warp_count(&cnt->camera_rays, rays);
     warp_count(&cnt->node_visits, visits);
+    warp_count(&cnt->prim_tests, ptests);
+    warp_count(&cnt->visits_by[0], visits);
+    warp_count(&cnt->ptests_by[0], ptests);
     warp_count(&cnt->nee_vertices, nee_new);
     warp_count(&cnt->random_hits, rhits);
   }
@@ -265,7 +268,7 @@ __global__ void __launch_bounds__(kThreads) k_shadow(SceneView s, NeeStore nv, D
   const int stride = gridDim.x * blockDim.x;
   for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
     const int i = base + threadIdx.x;
-    uint32_t visits = 0, rays = 0;
+    uint32_t visits = 0, ptests = 0, rays = 0;
     if (i < count) {
       int bits = __float_as_int(nv.nrm[i].w);
       if ((bits >> NV_FLAG_SHIFT) & NV_SHADOW) {
@@ -274,11 +277,14 @@ __global__ void __launch_bounds__(kThreads) k_shadow(SceneView s, NeeStore nv, D
         float3 o = offset_origin(xyz(pp), xyz(nn), xyz(ee), ldir);
         RayPre r = make_ray(o, ldir);
         rays = 1;
-        if (trace_any(s, r, ee.w * (1.0f - 1e-4f), &cnt->status, visits)) nv.dE[i] = make_float4(0, 0, 0, 0);
+        if (trace_any(s, r, ee.w * (1.0f - 1e-4f), &cnt->status, visits, ptests)) nv.dE[i] = make_float4(0, 0, 0, 0);
       }
     }
     warp_count(&cnt->shadow_rays, rays);
     warp_count(&cnt->node_visits, visits);
+    warp_count(&cnt->prim_tests, ptests);
+    warp_count(&cnt->visits_by[1], visits);
+    warp_count(&cnt->ptests_by[1], ptests);
   }
 }
 
@@ -387,13 +393,13 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
     const int i = base + threadIdx.x;
     bool emit = false;
     PhotonRay nph;
-    uint32_t visits = 0, hits = 0, tests = 0, merges = 0;
+    uint32_t visits = 0, ptests = 0, hits = 0, tests = 0, merges = 0;
     if (i < count) {
       PhotonRay ph = in[i];
       float3 d = xyz(ph.d);
       RayPre r = make_ray(xyz(ph.o), d);
       float t;
-      int prim = trace_closest(s, r, FLT_MAX, t, &cnt->status, visits);
+      int prim = trace_closest(s, r, FLT_MAX, t, &cnt->status, visits, ptests);
       if (prim >= 0) {
         float3 hp, herr, hn;
         hit_point(s, r, prim, t, hp, herr, hn);
@@ -473,6 +479,9 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
     int slot = warp_append(&cnt->ph_count[out_slot], emit, ip.cap_ph, &cnt->status);
     if (emit && slot >= 0) out[slot] = nph;
     warp_count(&cnt->node_visits, visits);
+    warp_count(&cnt->prim_tests, ptests);
+    warp_count(&cnt->visits_by[2], visits);
+    warp_count(&cnt->ptests_by[2], ptests);
     warp_count(&cnt->photon_hits, hits);
     warp_count(&cnt->merge_tests, tests);
     warp_count(&cnt->merges, merges);
@@ -564,16 +573,19 @@ cudaError_t run_iteration(neb_ctx* c, int iteration) {
 
   // octree set_iteration (Appendix B): host-side scalars, device re-arm
   octree_set_iteration_params(c->oct, c->cfg.split_factor, iteration);
+  long long launches = 0;
   tm.begin(STAGE_REARM);
   k_begin<<<1, 1, 0, st>>>(c->counters);
   if (split) cudaMemsetAsync(c->split, 0, sizeof(double) * 9 * (size_t)c->P, st);
   if (c->slot_map) cudaMemsetAsync(c->slot_map, 0xff, sizeof(int) * (size_t)c->P * (c->D - 1), st);
   launch_oct_rearm(c->oct_nodes, c->oct_state, c->oct, st);
+  launches += 2;
   tm.end();
 
   // pass 1
   tm.begin(STAGE_CAMERA);
   k_camera<<<B, kThreads, 0, st>>>(ip, c->cam, c->camq[0], c->counters);
+  launches += 1;
   tm.end();
   for (int k = 1; k <= c->D; ++k) {
     int in = (k - 1) & 1, out = k & 1;
@@ -581,6 +593,7 @@ cudaError_t run_iteration(neb_ctx* c, int iteration) {
     tm.begin(STAGE_EXTEND);
     k_extend<<<B, kThreads, 0, st>>>(s, ip, k, c->camq[in], in, c->camq[out], out, c->nv, c->rh, c->counters,
                                      c->slot_map);
+    launches += 2;
     tm.end();
   }
   tm.begin(STAGE_SHADOW);
@@ -596,14 +609,17 @@ cudaError_t run_iteration(neb_ctx* c, int iteration) {
   tm.begin(STAGE_NEE);
   k_nee<<<B, kThreads, 0, st>>>(s, ip, c->nv, c->counters, c->accum, split, c->phq[0]);
   tm.end();
+  launches += 4;
   if ((ip.mask & 4u) && c->D >= 3) {
     tm.begin(STAGE_GRID);
     grid_build(c, ip);
+    launches += 2 + scan_launch_count((size_t)c->table_size + 1);
     tm.end();
   }
   // pass 3 (independent of the photons; enqueued here)
   tm.begin(STAGE_EMISSION);
   k_emission<<<B, kThreads, 0, st>>>(s, ip, c->nv, c->rh, c->counters, c->accum, split);
+  launches += 1;
   tm.end();
   if ((ip.mask & 4u) && c->D >= 3) {
     for (int j = 1; j <= c->D - 2; ++j) {
@@ -612,9 +628,11 @@ cudaError_t run_iteration(neb_ctx* c, int iteration) {
       tm.begin(STAGE_PHOTON);
       k_photon<<<B, kThreads, 0, st>>>(s, ip, j, c->phq[in], in, c->phq[out], out, c->mrec, c->bucket_start,
                                        c->counters, c->accum, split);
+      launches += 2;
       tm.end();
     }
   }
+  c->launches += launches;
   cudaError_t e = cudaGetLastError();
   tm.collect();
   return e;

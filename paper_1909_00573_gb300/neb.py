@@ -45,11 +45,19 @@ class Stats(C.Structure):
                 ("shadow_rays", C.c_int64), ("photons", C.c_int64), ("photon_hits", C.c_int64),
                 ("merge_tests", C.c_int64), ("merges", C.c_int64), ("random_hits", C.c_int64),
                 ("octree_inserts", C.c_int64), ("octree_queries", C.c_int64), ("bvh_node_visits", C.c_int64),
-                ("prim_tests", C.c_int64), ("octree_nodes", C.c_int32), ("octree_depth", C.c_int32),
+                ("prim_tests", C.c_int64), ("kernel_launches", C.c_int64),
+                ("stage_node_visits", C.c_int64 * 3), ("stage_prim_tests", C.c_int64 * 3),
+                ("octree_nodes", C.c_int32), ("octree_depth", C.c_int32),
                 ("status", C.c_uint32), ("pad", C.c_int32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+        d = {}
+        for k, _ in self._fields_:
+            if k == "pad":
+                continue
+            v = getattr(self, k)
+            d[k] = list(v) if k.startswith("stage_") else v
+        return d
 
 
 _lib = None
