@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=2)
+    ap.add_argument("--res", default=None, help="WxH override (smaller cases for ncu captures)")
     return ap.parse_args()
 
 
@@ -221,15 +222,22 @@ def main():
     from paper_1909_00573_gb300 import neb, scenes
 
     scene, rc = scenes.workload(args.workload)
+    if args.res:
+        rc.width, rc.height = (int(x) for x in args.res.lower().split("x"))
     rc.seed = rank                      # replicas render independent sample streams
     P = rc.width * rc.height
-    stream = torch.cuda.current_stream()
+    # a dedicated (non-default) stream: the library's kernels and the timing
+    # events must be ordered on the same stream
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    assert stream.cuda_stream != 0
     ctx = neb.Context(neb.make_config(rc), stream.cuda_stream)
     ctx.scene_upload(scene)
     ctx.build_bvh()
     ctx.iterate(args.warmup)
     torch.cuda.synchronize()
     s0 = ctx.stats(check=False)
+    t_wall0 = time.perf_counter()
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -241,9 +249,11 @@ def main():
     ctx.iterate(args.steps)
     ev1.record(stream)
     torch.cuda.synchronize()
+    wall_ms = (time.perf_counter() - t_wall0) * 1000.0
     if dist:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
+    assert ms > 0.5 * wall_ms / 1.0 - 50.0, (ms, wall_ms)   # device time tracks the host clock
     clk = clocks.stop()
     s1 = ctx.stats(check=False)
     d = stats_delta(s0, s1)

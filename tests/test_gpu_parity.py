@@ -283,7 +283,8 @@ def test_white_furnace_gpu(neb):
         ctx.close()
         v = np.stack(vals).ravel()
         se = v.std(ddof=1) / math.sqrt(v.size)
-        assert abs(v.mean() - expect) < 3 * se, (mask, v.mean(), expect, se)
+        # random hits alone are exact here (every bounce carries weight a): se may be 0
+        assert abs(v.mean() - expect) <= 3 * se + 1e-6 * expect, (mask, v.mean(), expect, se)
     rc = scenes.RenderConfig(64, 64, D, 0.02, 1 << 16, 8, 4)
     ctx = neb.render(s, rc)
     img = ctx.resolve()[..., 0]
