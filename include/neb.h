@@ -171,6 +171,28 @@ int neb_octree_read(neb_octree* o, int32_t* nodes, int n_nodes, int32_t meta[4])
  * with |p - q|^2 <= r^2 evaluated in FP32. */
 int neb_count_neighbours(const float* pts, int n, const float* queries, int m, float r, int32_t* out);
 
+/* The same neighbour count for callers that cannot allocate device memory:
+ * for example a host application whose device memory is entirely reserved by
+ * its own pooling allocator, or a latency-critical loop that must not hit the
+ * device-wide synchronisation cudaMalloc and cudaFree can cause.  The paper
+ * has no counterpart; this is a library service.
+ *
+ * d_pts [n][3], d_queries [m][3] and d_out [m] are DEVICE pointers owned by
+ * the caller; cuda_stream is a cudaStream_t (NULL: the default stream).  The
+ * call only enqueues work (memset + kernels) on that stream and returns;
+ * synchronise before reading d_out.  It allocates nothing: its scratch is a
+ * fixed ~9 MiB array inside the library image (held by every GPU that loads
+ * the library until the process exits), so n may not exceed
+ * NEB_NOALLOC_MAX_POINTS (larger n returns NEB_ERR_ARG; m is unlimited).
+ * The first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress; make that first call before any stream capture.
+ * Every call on a device shares the one array: calls whose work overlaps on
+ * the GPU (other streams, other host threads) race and corrupt each other's
+ * results; serialise them.  Results equal those of neb_count_neighbours. */
+#define NEB_NOALLOC_MAX_POINTS (1 << 18)
+int neb_count_neighbours_noalloc(const float* d_pts, int n, const float* d_queries, int m, float r,
+                                 int32_t* d_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

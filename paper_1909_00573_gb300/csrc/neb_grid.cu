@@ -235,3 +235,81 @@ cudaError_t count_neighbours_device(const float* d_pts, int n, const float* d_q,
 }
 
 }  // namespace neb
+
+// ---------------------------------------------------------------------------
+// Neighbour counting without any device allocation.
+//
+// Same grid and kernels as count_neighbours_device, but every scratch buffer
+// (bucket counts and starts, per-point buckets, the bucket-sorted points and
+// the scan's block sums) lives in one file-scope __device__ array of fixed
+// size.  The array is part of the module image, so every GPU that loads the
+// library holds it until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+constexpr uint32_t kNaTable = 1u << 19;                       // hash buckets
+constexpr size_t kNaCountsOff = 0;                            // int[kNaTable + 1]
+constexpr size_t kNaStartsOff = (2u << 20) + 256;             // int[kNaTable + 1]
+constexpr size_t kNaBucketOff = (4u << 20) + 512;             // int[NEB_NOALLOC_MAX_POINTS]
+constexpr size_t kNaSortedOff = (5u << 20) + 512;             // float4[NEB_NOALLOC_MAX_POINTS]
+constexpr size_t kNaScanOff = (9u << 20) + 512;               // int[kNaScanInts]
+constexpr size_t kNaScanInts = 4096;
+constexpr size_t kNaBytes = kNaScanOff + kNaScanInts * sizeof(int);
+static_assert((kNaTable + 1) * sizeof(int) <= kNaStartsOff - kNaCountsOff, "counts");
+static_assert((kNaTable + 1) * sizeof(int) <= kNaBucketOff - kNaStartsOff, "starts");
+static_assert(NEB_NOALLOC_MAX_POINTS * sizeof(int) <= kNaSortedOff - kNaBucketOff, "buckets");
+static_assert(NEB_NOALLOC_MAX_POINTS * sizeof(float4) <= kNaScanOff - kNaSortedOff, "sorted points");
+static_assert(kNaScanInts >= 2 * ((kNaTable + 1 + 1023) / 1024) + 2 + 16, "scan block sums");
+
+constexpr int kNaMaxDevices = 64;
+std::mutex g_na_mutex;
+unsigned char* g_na_addr[kNaMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+// Device address of the scratch array on the current device, looked up once
+// per device (host code cannot use the symbol's host-side name as a pointer).
+static int noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return NEB_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  if (!g_na_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return NEB_ERR_CUDA;
+    g_na_addr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_na_addr[dev];
+  return NEB_OK;
+}
+
+extern "C" int neb_count_neighbours_noalloc(const float* d_pts, int n, const float* d_queries, int m, float r,
+                                            int32_t* d_out, void* cuda_stream) {
+  if (n < 0 || m < 0 || !(r > 0.0f) || (n > 0 && !d_pts) || (m > 0 && (!d_queries || !d_out)))
+    return NEB_ERR_ARG;
+  if (n > NEB_NOALLOC_MAX_POINTS) return NEB_ERR_ARG;
+  if (m == 0) return NEB_OK;
+  unsigned char* base = nullptr;
+  int rc = noalloc_scratch(&base);
+  if (rc != NEB_OK) return rc;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int* counts = reinterpret_cast<int*>(base + kNaCountsOff);
+  int* starts = reinterpret_cast<int*>(base + kNaStartsOff);
+  int* vb = reinterpret_cast<int*>(base + kNaBucketOff);
+  float4* sorted = reinterpret_cast<float4*>(base + kNaSortedOff);
+  neb::Scratch sc;
+  sc.data = reinterpret_cast<int*>(base + kNaScanOff);
+  sc.n = kNaScanInts;
+  const float cs = 2.0f * r;
+  const float3 gmin = neb::f3(0.0f, 0.0f, 0.0f);
+  // the previous call's bucket counts are consumed to zero by its scatter, but
+  // a call that failed half-way could leave them dirty: clear them every time
+  if (cudaMemsetAsync(counts, 0, sizeof(int) * (kNaTable + 1), st) != cudaSuccess) return NEB_ERR_CUDA;
+  if (n > 0) neb::k_pts_count<<<(n + 255) / 256, 256, 0, st>>>(d_pts, n, gmin, 1.0f / cs, kNaTable - 1, counts, vb);
+  if (neb::scan_exclusive(counts, starts, kNaTable + 1, sc, st) != cudaSuccess) return NEB_ERR_CUDA;
+  if (n > 0) neb::k_pts_scatter<<<(n + 255) / 256, 256, 0, st>>>(d_pts, n, vb, starts, counts, sorted);
+  neb::k_pts_query<<<(m + 255) / 256, 256, 0, st>>>(sorted, starts, d_queries, m, r * r, gmin, 1.0f / cs,
+                                                    kNaTable - 1, d_out);
+  return cudaGetLastError() == cudaSuccess ? NEB_OK : NEB_ERR_CUDA;
+}

@@ -24,7 +24,8 @@ EXPORTS = ["neb_create", "neb_destroy", "neb_last_error", "neb_scene_upload", "n
            "neb_resolve", "neb_read_accum", "neb_read_split", "neb_read_nee_rho", "neb_get_stats",
            "neb_set_profiling", "neb_get_stage_times", "neb_trace_closest", "neb_philox", "neb_plane_box_area",
            "neb_octree_create", "neb_octree_destroy", "neb_octree_set_iteration", "neb_octree_insert",
-           "neb_octree_density", "neb_octree_read", "neb_count_neighbours"]
+           "neb_octree_density", "neb_octree_read", "neb_count_neighbours", "neb_count_neighbours_noalloc"]
+NOALLOC_MAX_POINTS = 1 << 18
 
 
 class NebError(RuntimeError):
@@ -95,6 +96,7 @@ def lib():
             "neb_octree_density": ([vp, vp, vp, C.c_int, C.c_int, vp], C.c_int),
             "neb_octree_read": ([vp, vp, C.c_int, vp], C.c_int),
             "neb_count_neighbours": ([vp, C.c_int, vp, C.c_int, C.c_float, vp], C.c_int),
+            "neb_count_neighbours_noalloc": ([vp, C.c_int, vp, C.c_int, C.c_float, vp, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -234,6 +236,14 @@ def count_neighbours(points, queries, r):
     out = np.zeros(len(Q), np.int32)
     _check(lib().neb_count_neighbours(_p(P), len(P), _p(Q), len(Q), C.c_float(r), _p(out)))
     return out
+
+
+def count_neighbours_noalloc(d_points: int, n: int, d_queries: int, m: int, r: float, d_out: int,
+                             stream: int = 0):
+    """Allocation-free neighbour count on caller-owned device buffers (raw
+    device pointers); enqueues on `stream` and returns without synchronising."""
+    _check(lib().neb_count_neighbours_noalloc(vp(d_points), int(n), vp(d_queries), int(m), C.c_float(r),
+                                              vp(d_out), vp(stream) if stream else None))
 
 
 class Octree:
