@@ -71,14 +71,19 @@ __device__ __forceinline__ uint32_t expand_bits(uint32_t v) {
 __global__ void k_morton(SceneView s, int n, const int* cb, uint32_t* keys, int* vals) {
   float3 lo = f3(ordered_to_float(cb[0]), ordered_to_float(cb[1]), ordered_to_float(cb[2]));
   float3 hi = f3(ordered_to_float(cb[3]), ordered_to_float(cb[4]), ordered_to_float(cb[5]));
+  // one scale for all axes: Morton cells stay cubes in world space, so flat
+  // scenes (a city is 400 x 20 x 400) are not split along their short axis
+  // as often as along the long ones
   float3 ext = sub(hi, lo);
+  float e = fmaxf(ext.x, fmaxf(ext.y, ext.z));
+  float inv = e > 0.0f ? 1.0f / e : 0.0f;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     float3 a, b;
     prim_bounds(s, p, a, b);
     float3 c = mul(add(a, b), 0.5f);
-    float x = ext.x > 0.0f ? (c.x - lo.x) / ext.x : 0.5f;
-    float y = ext.y > 0.0f ? (c.y - lo.y) / ext.y : 0.5f;
-    float z = ext.z > 0.0f ? (c.z - lo.z) / ext.z : 0.5f;
+    float x = (c.x - lo.x) * inv;
+    float y = (c.y - lo.y) * inv;
+    float z = (c.z - lo.z) * inv;
     uint32_t ix = (uint32_t)fminf(fmaxf(x * 1024.0f, 0.0f), 1023.0f);
     uint32_t iy = (uint32_t)fminf(fmaxf(y * 1024.0f, 0.0f), 1023.0f);
     uint32_t iz = (uint32_t)fminf(fmaxf(z * 1024.0f, 0.0f), 1023.0f);

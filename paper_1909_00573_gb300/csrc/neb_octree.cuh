@@ -101,7 +101,10 @@ __device__ __forceinline__ void oct_insert_seq(int* nodes, OctreeState* st, cons
 // spin and then count in the child.  A spin that runs out sets
 // NEB_STATUS_SPIN_TIMEOUT and drops the insert; it never traps.
 __device__ __forceinline__ int oct_inc_atomic(int* nodes, int idx) {
-  int old = *((volatile int*)(nodes + idx));
+  // A plain (cacheable) first read is enough: a child pointer never changes
+  // once published, and a stale counter only makes the CAS below fail and
+  // return the current value.
+  int old = nodes[idx];
   while (true) {
     if (old < 0) return old;
     int prev = atomicCAS(nodes + idx, old, old + 1);
