@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=2)
     ap.add_argument("--res", default=None, help="WxH override (smaller cases for ncu captures)")
+    ap.add_argument("--bvh", type=int, default=0, help="0 PLOC (default), 1 Karras LBVH")
     return ap.parse_args()
 
 
@@ -231,9 +232,12 @@ def main():
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     assert stream.cuda_stream != 0
-    ctx = neb.Context(neb.make_config(rc), stream.cuda_stream)
+    ctx = neb.Context(neb.make_config(rc, bvh_builder=args.bvh), stream.cuda_stream)
     ctx.scene_upload(scene)
+    torch.cuda.synchronize()
+    t_b0 = time.perf_counter()
     ctx.build_bvh()
+    bvh_build_ms = (time.perf_counter() - t_b0) * 1000.0
     ctx.iterate(args.warmup)
     torch.cuda.synchronize()
     s0 = ctx.stats(check=False)
@@ -296,7 +300,7 @@ def main():
                           pin(scene.mats), pin(scene.cam), scene.name)
         img = torch.empty((rc.height, rc.width, 3), dtype=torch.float32).pin_memory()
         h2d = hs.tri.nbytes + hs.tri_mat.nbytes + hs.sph.nbytes + hs.sph_mat.nbytes + hs.mats.nbytes + hs.cam.nbytes
-        ctx2 = neb.Context(neb.make_config(rc), stream.cuda_stream)
+        ctx2 = neb.Context(neb.make_config(rc, bvh_builder=args.bvh), stream.cuda_stream)
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
@@ -333,7 +337,8 @@ def main():
                 "stage_sum_ms_per_step": total_stage_ms / args.profile_steps,
                 "counters_per_step": {k: (v / args.steps if not isinstance(v, list) else [x / args.steps for x in v])
                                       for k, v in d.items() if k not in ("iterations",)},
-                "status": s1["status"]}
+                "status": s1["status"], "bvh_build_ms": bvh_build_ms,
+                "bvh": "PLOC" if args.bvh == 0 else "LBVH"}
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

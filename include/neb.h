@@ -65,6 +65,7 @@ typedef struct {
   int density_mode;      /* 0 robust median of five (get_density_robust), 1 single query */
   uint32_t strategy_mask;/* bit 0 random hit (e), bit 1 NEE (E), bit 2 NEB photon merge (P) */
   int keep_split;        /* nonzero: keep the last iteration's contributions split by strategy */
+  int bvh_builder;       /* 0 PLOC clustering over the Morton order (default), 1 Karras LBVH */
 } neb_config;
 
 typedef struct {
@@ -99,8 +100,12 @@ int neb_scene_upload(neb_ctx* ctx, const float* tri, const uint32_t* tri_mat, in
                      const float* sph, const uint32_t* sph_mat, int ns,
                      const float* mats, int nm, const float* cam);
 
-/* Builds the BVH on the device: 30-bit Morton codes of primitive centroids,
- * stable 4-bit LSD radix sort, Karras (HPG 2012) hierarchy, bottom-up bounds. */
+/* Builds the BVH on the device: 30-bit Morton codes of primitive centroids
+ * (one scale for all axes), stable 4-bit LSD radix sort, then either PLOC
+ * (Meister and Bittner 2018: rounds of mutual nearest-neighbour merges by
+ * union surface area within +-16 positions of the Morton order; default) or
+ * the Karras (HPG 2012) hierarchy with bottom-up bounds.  Leaves hold one
+ * primitive; the root is node 0. */
 int neb_build_bvh(neb_ctx* ctx);
 
 /* Enqueues n_iterations NEB iterations on the context stream (asynchronous).

@@ -75,7 +75,8 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
   if (cfg->width < 1 || cfg->height < 1 || cfg->max_depth < 1 || cfg->max_depth > kMaxDepth ||
       !(cfg->merge_radius > 0.0f) || cfg->octree_capacity < 1 || cfg->split_factor < 1 ||
       (cfg->octree_mode != 0 && cfg->octree_mode != 1) || (cfg->density_mode != 0 && cfg->density_mode != 1) ||
-      (cfg->strategy_mask & ~7u) || (long long)cfg->width * cfg->height > (1ll << 28))
+      (cfg->strategy_mask & ~7u) || (cfg->bvh_builder != 0 && cfg->bvh_builder != 1) ||
+      (long long)cfg->width * cfg->height > (1ll << 28))
     return NEB_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return NEB_ERR_NO_DEVICE;
@@ -110,6 +111,7 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
             dalloc(&c->nv.err, c->cap_nee) == cudaSuccess && dalloc(&c->nv.ldir, c->cap_nee) == cudaSuccess &&
             dalloc(&c->nv.dE, c->cap_nee) == cudaSuccess && dalloc(&c->rh, c->cap_rh) == cudaSuccess &&
             dalloc(&c->phq[0], c->cap_ph) == cudaSuccess && dalloc(&c->phq[1], c->cap_ph) == cudaSuccess &&
+            dalloc(&c->hits, (size_t)(c->cap_ph > c->cap_cam ? c->cap_ph : c->cap_cam)) == cudaSuccess &&
             dalloc(&c->mrec, c->cap_nee) == cudaSuccess && dalloc(&c->vert_bucket, c->cap_nee) == cudaSuccess &&
             dalloc(&c->bucket_count, (size_t)t + 1) == cudaSuccess &&
             dalloc(&c->bucket_start, (size_t)t + 1) == cudaSuccess &&
@@ -141,7 +143,7 @@ extern "C" void neb_destroy(neb_ctx* c) {
   cudaFree(c->camq[0]); cudaFree(c->camq[1]);
   cudaFree(c->nv.pos); cudaFree(c->nv.nrm); cudaFree(c->nv.wo); cudaFree(c->nv.tau); cudaFree(c->nv.err);
   cudaFree(c->nv.ldir); cudaFree(c->nv.dE);
-  cudaFree(c->rh); cudaFree(c->phq[0]); cudaFree(c->phq[1]); cudaFree(c->mrec); cudaFree(c->vert_bucket);
+  cudaFree(c->rh); cudaFree(c->phq[0]); cudaFree(c->phq[1]); cudaFree(c->hits); cudaFree(c->mrec); cudaFree(c->vert_bucket);
   cudaFree(c->bucket_count); cudaFree(c->bucket_start); cudaFree(c->scan_scratch.data); cudaFree(c->accum);
   cudaFree(c->split); cudaFree(c->counters); cudaFree(c->slot_map);
   for (auto& ev : c->ev)
@@ -429,8 +431,9 @@ extern "C" int neb_get_stats(neb_ctx* c, neb_stats* out) {
   return NEB_OK;
 }
 
-static const char* kStageNames[STAGE_COUNT] = {"rearm",   "camera",  "extend",   "shadow", "octree_insert",
-                                               "density", "nee_emit", "grid_build", "emission", "photon"};
+static const char* kStageNames[STAGE_COUNT] = {"rearm",      "camera",   "trace_camera", "extend",
+                                               "shadow",     "octree_insert", "density", "nee_emit",
+                                               "grid_build", "emission", "trace_photon", "photon"};
 
 extern "C" int neb_set_profiling(neb_ctx* c, int enable) {
   if (!c) return NEB_ERR_ARG;

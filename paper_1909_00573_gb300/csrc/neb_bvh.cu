@@ -244,6 +244,153 @@ __global__ void k_single_leaf(SceneView s, BVHNode* nodes) {
   nodes[0] = nd;
 }
 
+// ---- PLOC: parallel locally-ordered clustering over the Morton order -------------
+// Meister and Bittner, "Parallel Locally-Ordered Clustering for Bounding Volume
+// Hierarchy Construction", IEEE TVCG 2018.  Clusters start as the Morton-sorted
+// primitives; every round each cluster finds the neighbour within +-R positions
+// whose union box has the smallest surface area, mutual nearest neighbours merge
+// into a new internal node, and the survivors are compacted in order.  Internal
+// nodes are numbered from N-2 downwards so the final merge (the root) is node 0.
+constexpr int kPlocR = 16;
+constexpr int kPlocThreads = 256;
+
+__device__ __forceinline__ float half_area(float3 lo, float3 hi) {
+  float3 d = sub(hi, lo);
+  return d.x * d.y + d.y * d.z + d.z * d.x;
+}
+
+__global__ void k_ploc_init(SceneView s, int n, const int* __restrict__ sorted_prim, int* cid, float4* blo,
+                            float4* bhi) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int p = sorted_prim[i];
+    float3 lo, hi;
+    prim_bounds(s, p, lo, hi);
+    cid[i] = ~p;
+    blo[i] = make_float4(lo.x, lo.y, lo.z, 0.0f);
+    bhi[i] = make_float4(hi.x, hi.y, hi.z, 0.0f);
+  }
+}
+
+__global__ void __launch_bounds__(kPlocThreads) k_ploc_nn(int n, const float4* __restrict__ blo,
+                                                          const float4* __restrict__ bhi, int* __restrict__ nn) {
+  __shared__ float4 slo[kPlocThreads + 2 * kPlocR], shi[kPlocThreads + 2 * kPlocR];
+  int b0 = blockIdx.x * kPlocThreads;
+  for (int t = threadIdx.x; t < kPlocThreads + 2 * kPlocR; t += kPlocThreads) {
+    int g = b0 - kPlocR + t;
+    if (g >= 0 && g < n) {
+      slo[t] = blo[g];
+      shi[t] = bhi[g];
+    }
+  }
+  __syncthreads();
+  int i = b0 + threadIdx.x;
+  if (i >= n) return;
+  int me = threadIdx.x + kPlocR;
+  float3 alo = xyz(slo[me]), ahi = xyz(shi[me]);
+  float best = 3.402823466e+38f;
+  int bj = -1;
+  for (int d = -kPlocR; d <= kPlocR; ++d) {
+    int j = i + d;
+    if (d == 0 || j < 0 || j >= n) continue;
+    float3 lo = xyz(slo[me + d]), hi = xyz(shi[me + d]);
+    float a = half_area(f3(fminf(alo.x, lo.x), fminf(alo.y, lo.y), fminf(alo.z, lo.z)),
+                        f3(fmaxf(ahi.x, hi.x), fmaxf(ahi.y, hi.y), fmaxf(ahi.z, hi.z)));
+    if (a < best) {  // ascending j: ties keep the smaller index
+      best = a;
+      bj = j;
+    }
+  }
+  nn[i] = bj;
+}
+
+__global__ void k_ploc_flags(int n, const int* __restrict__ nn, int* merge_flag, int* keep_flag) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int j = nn[i];
+    bool mutual = j >= 0 && nn[j] == i;
+    merge_flag[i] = (mutual && i < j) ? 1 : 0;
+    keep_flag[i] = (!mutual || i < j) ? 1 : 0;
+  }
+}
+
+__global__ void k_ploc_compact(int n, const int* __restrict__ nn, const int* __restrict__ cid,
+                               const float4* __restrict__ blo, const float4* __restrict__ bhi,
+                               const int* __restrict__ merge_rank, const int* __restrict__ keep_pos, int node_base,
+                               BVHNode* nodes, int* cid2, float4* blo2, float4* bhi2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int j = nn[i];
+    bool mutual = j >= 0 && nn[j] == i;
+    if (mutual && i > j) continue;  // absorbed by its partner
+    int pos = keep_pos[i];
+    float4 lo = blo[i], hi = bhi[i];
+    if (!mutual) {
+      cid2[pos] = cid[i];
+      blo2[pos] = lo;
+      bhi2[pos] = hi;
+      continue;
+    }
+    float4 lo2 = blo[j], hi2 = bhi[j];
+    int node = node_base - merge_rank[i];
+    BVHNode nd;
+    nd.a = make_float4(lo.x, hi.x, lo.y, hi.y);
+    nd.b = make_float4(lo2.x, hi2.x, lo2.y, hi2.y);
+    nd.c = make_float4(lo.z, hi.z, lo2.z, hi2.z);
+    nd.ch = make_int4(cid[i], cid[j], 0, 0);
+    nodes[node] = nd;
+    cid2[pos] = node;
+    blo2[pos] = make_float4(fminf(lo.x, lo2.x), fminf(lo.y, lo2.y), fminf(lo.z, lo2.z), 0.0f);
+    bhi2[pos] = make_float4(fmaxf(hi.x, hi2.x), fmaxf(hi.y, hi2.y), fmaxf(hi.z, hi2.z), 0.0f);
+  }
+}
+
+static cudaError_t ploc_build(const SceneView& s, int n, const int* sorted_prim, BVHNode* nodes, Scratch& sc,
+                              cudaStream_t st) {
+  int *cid[2] = {nullptr, nullptr}, *nn = nullptr, *mflag = nullptr, *kflag = nullptr, *mrank = nullptr,
+      *kpos = nullptr, *tail = nullptr;
+  float4 *blo[2] = {nullptr, nullptr}, *bhi[2] = {nullptr, nullptr};
+  cudaError_t e = cudaSuccess;
+  bool ok = cudaMalloc(&cid[0], 4ull * n) == cudaSuccess && cudaMalloc(&cid[1], 4ull * n) == cudaSuccess &&
+            cudaMalloc(&blo[0], 16ull * n) == cudaSuccess && cudaMalloc(&blo[1], 16ull * n) == cudaSuccess &&
+            cudaMalloc(&bhi[0], 16ull * n) == cudaSuccess && cudaMalloc(&bhi[1], 16ull * n) == cudaSuccess &&
+            cudaMalloc(&nn, 4ull * n) == cudaSuccess && cudaMalloc(&mflag, 4ull * n) == cudaSuccess &&
+            cudaMalloc(&kflag, 4ull * n) == cudaSuccess && cudaMalloc(&mrank, 4ull * n) == cudaSuccess &&
+            cudaMalloc(&kpos, 4ull * n) == cudaSuccess && cudaMalloc(&tail, 16) == cudaSuccess;
+  if (!ok) e = cudaErrorMemoryAllocation;
+  if (ok) {
+    int gb = (n + 255) / 256;
+    if (gb > 152 * 16) gb = 152 * 16;
+    k_ploc_init<<<gb, 256, 0, st>>>(s, n, sorted_prim, cid[0], blo[0], bhi[0]);
+    int cur = 0, count = n, base = n - 2;
+    int rounds = 0;
+    while (count > 1 && e == cudaSuccess) {
+      int nb = (count + kPlocThreads - 1) / kPlocThreads;
+      k_ploc_nn<<<nb, kPlocThreads, 0, st>>>(count, blo[cur], bhi[cur], nn);
+      int fb = nb > 152 * 16 ? 152 * 16 : nb;
+      k_ploc_flags<<<fb, 256, 0, st>>>(count, nn, mflag, kflag);
+      scan_exclusive(mflag, mrank, count, sc, st);
+      scan_exclusive(kflag, kpos, count, sc, st);
+      int h[4];
+      cudaMemcpyAsync(&h[0], mrank + count - 1, 4, cudaMemcpyDeviceToHost, st);
+      cudaMemcpyAsync(&h[1], mflag + count - 1, 4, cudaMemcpyDeviceToHost, st);
+      cudaMemcpyAsync(&h[2], kpos + count - 1, 4, cudaMemcpyDeviceToHost, st);
+      cudaMemcpyAsync(&h[3], kflag + count - 1, 4, cudaMemcpyDeviceToHost, st);
+      k_ploc_compact<<<fb, 256, 0, st>>>(count, nn, cid[cur], blo[cur], bhi[cur], mrank, kpos, base, nodes,
+                                         cid[1 - cur], blo[1 - cur], bhi[1 - cur]);
+      e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) break;
+      int merges = h[0] + h[1], next = h[2] + h[3];
+      if (merges <= 0 || next >= count) { e = cudaErrorUnknown; break; }  // no progress: cannot happen
+      base -= merges;
+      count = next;
+      cur = 1 - cur;
+      ++rounds;
+    }
+    if (e == cudaSuccess && base != -1) e = cudaErrorUnknown;
+  }
+  cudaFree(cid[0]); cudaFree(cid[1]); cudaFree(blo[0]); cudaFree(blo[1]); cudaFree(bhi[0]); cudaFree(bhi[1]);
+  cudaFree(nn); cudaFree(mflag); cudaFree(kflag); cudaFree(mrank); cudaFree(kpos); cudaFree(tail);
+  return e;
+}
+
 cudaError_t build_bvh(neb_ctx* c) {
   int n = c->nt + c->ns;
   cudaStream_t st = c->stream;
@@ -287,12 +434,20 @@ cudaError_t build_bvh(neb_ctx* c) {
       uint32_t* tk = k0; k0 = k1; k1 = tk;
       int* tv = v0; v0 = v1; v1 = tv;
     }
-    cudaMemsetAsync(pint, 0xff, 4ull * (n - 1), st);
-    cudaMemsetAsync(flags, 0, 4ull * (n - 1), st);
-    k_karras<<<gb, 256, 0, st>>>(k0, n, child, pint, pleaf);
-    k_bounds<<<gb, 256, 0, st>>>(s, n, v0, child, pint, pleaf, flags, boxes);
-    k_write_nodes<<<gb, 256, 0, st>>>(s, n, v0, child, boxes, c->nodes);
-    e = cudaStreamSynchronize(st);
+    if (c->cfg.bvh_builder == 1) {
+      cudaMemsetAsync(pint, 0xff, 4ull * (n - 1), st);
+      cudaMemsetAsync(flags, 0, 4ull * (n - 1), st);
+      k_karras<<<gb, 256, 0, st>>>(k0, n, child, pint, pleaf);
+      k_bounds<<<gb, 256, 0, st>>>(s, n, v0, child, pint, pleaf, flags, boxes);
+      k_write_nodes<<<gb, 256, 0, st>>>(s, n, v0, child, boxes, c->nodes);
+      e = cudaStreamSynchronize(st);
+    } else {
+      Scratch sc2;
+      sc2.n = scan_scratch_ints(n);
+      e = cudaMalloc(&sc2.data, 4ull * sc2.n);
+      if (e == cudaSuccess) e = ploc_build(s, n, v0, c->nodes, sc2, st);
+      cudaFree(sc2.data);
+    }
     if (e == cudaSuccess) e = cudaGetLastError();
   } else {
     e = cudaErrorMemoryAllocation;

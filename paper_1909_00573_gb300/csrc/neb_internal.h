@@ -71,7 +71,8 @@ struct DevCounters {
   unsigned long long camera_rays, nee_vertices, shadow_rays, photons, photon_hits;
   unsigned long long merge_tests, merges, random_hits, octree_inserts, octree_queries;
   unsigned long long node_visits, prim_tests;
-  unsigned long long visits_by[3], ptests_by[3];  // extend, shadow, photon kernels
+  unsigned long long visits_by[3], ptests_by[3];  // camera, shadow, photon traversal
+  int fetch[4];                                   // dynamic-fetch counters of the traversal kernels
 };
 
 struct CameraParams {
@@ -92,8 +93,8 @@ struct IterParams {
   uint32_t table_mask;  // hash table size - 1
 };
 
-enum { STAGE_REARM = 0, STAGE_CAMERA, STAGE_EXTEND, STAGE_SHADOW, STAGE_INSERT, STAGE_DENSITY, STAGE_NEE,
-       STAGE_GRID, STAGE_EMISSION, STAGE_PHOTON, STAGE_COUNT };
+enum { STAGE_REARM = 0, STAGE_CAMERA, STAGE_TRACE_CAM, STAGE_EXTEND, STAGE_SHADOW, STAGE_INSERT, STAGE_DENSITY,
+       STAGE_NEE, STAGE_GRID, STAGE_EMISSION, STAGE_TRACE_PHOTON, STAGE_PHOTON, STAGE_COUNT };
 
 struct Scratch {
   int* data = nullptr;
@@ -134,6 +135,7 @@ struct neb_ctx {
   neb::NeeStore nv{};
   neb::RHEvent* rh = nullptr;
   neb::PhotonRay* phq[2] = {nullptr, nullptr};
+  int2* hits = nullptr;  // closest hits of the current ray queue
   neb::MergeRec* mrec = nullptr;
   int* vert_bucket = nullptr;
   int* bucket_count = nullptr;
@@ -187,6 +189,11 @@ cudaError_t launch_oct_density_points(const int* nodes, const OctreeState* st, c
                                       cudaStream_t s);
 cudaError_t launch_oct_insert_nee(neb_ctx* c);
 cudaError_t launch_oct_density_nee(neb_ctx* c);
+
+// neb_trace.cu
+cudaError_t launch_trace_closest(neb_ctx* c, const float4* recs, const int* count_ptr, int cap, int2* hits,
+                                 int which);
+cudaError_t launch_trace_shadow(neb_ctx* c);
 
 // neb_pass.cu
 cudaError_t run_iteration(neb_ctx* c, int iteration);

@@ -115,13 +115,13 @@ __global__ void k_camera(IterParams ip, CameraParams cam, CamRay* q, DevCounters
 __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip, int k, const CamRay* __restrict__ in,
                                                      int in_slot, CamRay* __restrict__ out, int out_slot,
                                                      NeeStore nv, RHEvent* __restrict__ rh, DevCounters* cnt,
-                                                     int* __restrict__ slot_map) {
+                                                     int* __restrict__ slot_map, const int2* __restrict__ hits) {
   const int count = min(cnt->cam_count[in_slot], ip.cap_cam);
   const int stride = gridDim.x * blockDim.x;
   for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
     const int i = base + threadIdx.x;
     const bool valid = i < count;
-    uint32_t visits = 0, ptests = 0, rays = 0, nee_new = 0, rhits = 0;
+    uint32_t rays = 0, nee_new = 0, rhits = 0;
     bool store_nee = false, alive = false;
     CamRay ry;
     float3 p = f3(0, 0, 0), n = f3(0, 0, 0), err = f3(0, 0, 0), d = f3(0, 0, 0), tau = f3(0, 0, 0);
@@ -140,8 +140,9 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
       pixel = __float_as_int(ry.o.w);
       flags = __float_as_int(ry.mis.w);
       RayPre r = make_ray(xyz(ry.o), d);
-      float t;
-      int prim = trace_closest(s, r, FLT_MAX, t, &cnt->status, visits, ptests);
+      int2 hh = hits[i];
+      int prim = hh.x;
+      float t = __int_as_float(hh.y);
       if (prim >= 0) {
         hit_point(s, r, prim, t, p, err, n);
         mat = prim_mat(s, prim);
@@ -253,10 +254,6 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
     int slot = warp_append(&cnt->cam_count[out_slot], emit, ip.cap_cam, &cnt->status);
     if (emit && slot >= 0) out[slot] = nr;
     warp_count(&cnt->camera_rays, rays);
-    warp_count(&cnt->node_visits, visits);
-    warp_count(&cnt->prim_tests, ptests);
-    warp_count(&cnt->visits_by[0], visits);
-    warp_count(&cnt->ptests_by[0], ptests);
     warp_count(&cnt->nee_vertices, nee_new);
     warp_count(&cnt->random_hits, rhits);
   }
@@ -385,7 +382,7 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
                                                      int in_slot, PhotonRay* __restrict__ out, int out_slot,
                                                      const MergeRec* __restrict__ mrec,
                                                      const int* __restrict__ bucket_start, DevCounters* cnt,
-                                                     double* accum, double* split) {
+                                                     double* accum, double* split, const int2* __restrict__ hits) {
   const int count = min(cnt->ph_count[in_slot], ip.cap_ph);
   const int stride = gridDim.x * blockDim.x;
   const int P = ip.W * ip.H;
@@ -393,19 +390,20 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
     const int i = base + threadIdx.x;
     bool emit = false;
     PhotonRay nph;
-    uint32_t visits = 0, ptests = 0, hits = 0, tests = 0, merges = 0;
+    uint32_t nhits = 0, tests = 0, merges = 0;
     if (i < count) {
       PhotonRay ph = in[i];
       float3 d = xyz(ph.d);
       RayPre r = make_ray(xyz(ph.o), d);
-      float t;
-      int prim = trace_closest(s, r, FLT_MAX, t, &cnt->status, visits, ptests);
+      int2 hh = hits[i];
+      int prim = hh.x;
+      float t = __int_as_float(hh.y);
       if (prim >= 0) {
         float3 hp, herr, hn;
         hit_point(s, r, prim, t, hp, herr, hn);
         Mat hm = load_mat(s.mats, prim_mat(s, prim));
         if (!mat_black(hm)) {
-          hits = 1;
+          nhits = 1;
           int knee = __float_as_int(ph.mis.w) & 0xff;
           int pixel = __float_as_int(ph.o.w);
           float cos_hit = fabsf(dot(hn, d));
@@ -478,11 +476,7 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
     }
     int slot = warp_append(&cnt->ph_count[out_slot], emit, ip.cap_ph, &cnt->status);
     if (emit && slot >= 0) out[slot] = nph;
-    warp_count(&cnt->node_visits, visits);
-    warp_count(&cnt->prim_tests, ptests);
-    warp_count(&cnt->visits_by[2], visits);
-    warp_count(&cnt->ptests_by[2], ptests);
-    warp_count(&cnt->photon_hits, hits);
+    warp_count(&cnt->photon_hits, nhits);
     warp_count(&cnt->merge_tests, tests);
     warp_count(&cnt->merges, merges);
   }
@@ -590,14 +584,18 @@ cudaError_t run_iteration(neb_ctx* c, int iteration) {
   for (int k = 1; k <= c->D; ++k) {
     int in = (k - 1) & 1, out = k & 1;
     k_reset_cam_slot<<<1, 1, 0, st>>>(c->counters, out);
+    tm.begin(STAGE_TRACE_CAM);
+    launch_trace_closest(c, reinterpret_cast<const float4*>(c->camq[in]), &c->counters->cam_count[in], c->cap_cam,
+                         c->hits, 0);
+    tm.end();
     tm.begin(STAGE_EXTEND);
     k_extend<<<B, kThreads, 0, st>>>(s, ip, k, c->camq[in], in, c->camq[out], out, c->nv, c->rh, c->counters,
-                                     c->slot_map);
-    launches += 2;
+                                     c->slot_map, c->hits);
+    launches += 3;
     tm.end();
   }
   tm.begin(STAGE_SHADOW);
-  k_shadow<<<B, kThreads, 0, st>>>(s, c->nv, c->counters, c->cap_nee);
+  launch_trace_shadow(c);
   tm.end();
   tm.begin(STAGE_INSERT);
   launch_oct_insert_nee(c);
@@ -625,10 +623,14 @@ cudaError_t run_iteration(neb_ctx* c, int iteration) {
     for (int j = 1; j <= c->D - 2; ++j) {
       int in = (j - 1) & 1, out = j & 1;
       k_reset_photon_slot<<<1, 1, 0, st>>>(c->counters, out);
+      tm.begin(STAGE_TRACE_PHOTON);
+      launch_trace_closest(c, reinterpret_cast<const float4*>(c->phq[in]), &c->counters->ph_count[in], c->cap_ph,
+                           c->hits, 2);
+      tm.end();
       tm.begin(STAGE_PHOTON);
       k_photon<<<B, kThreads, 0, st>>>(s, ip, j, c->phq[in], in, c->phq[out], out, c->mrec, c->bucket_start,
-                                       c->counters, c->accum, split);
-      launches += 2;
+                                       c->counters, c->accum, split, c->hits);
+      launches += 3;
       tm.end();
     }
   }

@@ -1,0 +1,249 @@
+// neb_trace.cu -- persistent BVH traversal kernels with dynamic ray fetch.
+//
+// Each warp keeps 32 rays in flight.  A lane that finishes its ray becomes
+// idle; once enough lanes are idle (or none is busy) the warp fetches that
+// many new rays with one atomic on a per-launch counter, so a few long rays
+// no longer hold 31 idle lanes until they finish (Aila and Laine, "Understanding
+// the Efficiency of Ray Traversal on GPUs", HPG 2009: persistent threads with
+// dynamic fetch).  The traversal itself is the stack walk of trace_closest /
+// trace_any cut into single node steps so lanes can be refilled between steps.
+#include <cfloat>
+
+#include "neb_device.cuh"
+#include "neb_internal.h"
+
+namespace neb {
+
+constexpr int kTraceThreads = 256;
+constexpr int kRefill = 8;     // refill when at least this many lanes are idle
+constexpr int kSteps = 16;     // node steps between refill checks
+constexpr int kIdle = -1, kDone = -2;
+
+struct Walk {
+  int node, sp, best;
+  float best_t;
+};
+
+// One node step of the closest-hit walk; returns true when the walk is over.
+__device__ __forceinline__ bool closest_step(const SceneView& s, const RayPre& r, float tmax, Walk& w, int* stack,
+                                             uint32_t* status, uint32_t& visits, uint32_t& ptests) {
+  const float4* np = reinterpret_cast<const float4*>(s.nodes + w.node);
+  float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
+  int4 ch = __ldg(reinterpret_cast<const int4*>(np + 3));
+  ++visits;
+  float tl, tr;
+  bool hl = box_hit(f3(a.x, a.z, c.x), f3(a.y, a.w, c.y), r, w.best_t, tl);
+  bool hr = box_hit(f3(b.x, b.z, c.z), f3(b.y, b.w, c.w), r, w.best_t, tr);
+  if (hl && ch.x < 0) {
+    int p = ~ch.x;
+    ++ptests;
+    float t = isect_prim(s, r, p);
+    if (t > 0.0f && t < tmax && (t < w.best_t || (t == w.best_t && w.best >= 0 && p < w.best))) {
+      w.best_t = t;
+      w.best = p;
+    }
+    hl = false;
+  }
+  if (hr && ch.y < 0) {
+    int p = ~ch.y;
+    ++ptests;
+    float t = isect_prim(s, r, p);
+    if (t > 0.0f && t < tmax && (t < w.best_t || (t == w.best_t && w.best >= 0 && p < w.best))) {
+      w.best_t = t;
+      w.best = p;
+    }
+    hr = false;
+  }
+  if (hl && hr) {
+    int nearc = tl <= tr ? ch.x : ch.y;
+    int farc = tl <= tr ? ch.y : ch.x;
+    if (w.sp < 64) stack[w.sp++] = farc;
+    else atomicOr(status, NEB_STATUS_STACK_OVERFLOW);
+    w.node = nearc;
+  } else if (hl) {
+    w.node = ch.x;
+  } else if (hr) {
+    w.node = ch.y;
+  } else {
+    if (w.sp == 0) return true;
+    w.node = stack[--w.sp];
+  }
+  return false;
+}
+
+// One node step of the any-hit walk; returns 1 on a hit, -1 when the walk is over, 0 otherwise.
+__device__ __forceinline__ int any_step(const SceneView& s, const RayPre& r, float tmax, Walk& w, int* stack,
+                                        uint32_t* status, uint32_t& visits, uint32_t& ptests) {
+  const float4* np = reinterpret_cast<const float4*>(s.nodes + w.node);
+  float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
+  int4 ch = __ldg(reinterpret_cast<const int4*>(np + 3));
+  ++visits;
+  float tl, tr;
+  bool hl = box_hit(f3(a.x, a.z, c.x), f3(a.y, a.w, c.y), r, tmax, tl);
+  bool hr = box_hit(f3(b.x, b.z, c.z), f3(b.y, b.w, c.w), r, tmax, tr);
+  if (hl && ch.x < 0) {
+    ++ptests;
+    float t = isect_prim(s, r, ~ch.x);
+    if (t > 0.0f && t < tmax) return 1;
+    hl = false;
+  }
+  if (hr && ch.y < 0) {
+    ++ptests;
+    float t = isect_prim(s, r, ~ch.y);
+    if (t > 0.0f && t < tmax) return 1;
+    hr = false;
+  }
+  if (hl && hr) {
+    if (w.sp < 64) stack[w.sp++] = ch.y;
+    else atomicOr(status, NEB_STATUS_STACK_OVERFLOW);
+    w.node = ch.x;
+  } else if (hl) {
+    w.node = ch.x;
+  } else if (hr) {
+    w.node = ch.y;
+  } else {
+    if (w.sp == 0) return -1;
+    w.node = stack[--w.sp];
+  }
+  return 0;
+}
+
+__device__ __forceinline__ void warp_total(unsigned long long* dst, uint32_t v) {
+  uint32_t t = __reduce_add_sync(0xffffffffu, v);
+  if ((threadIdx.x & 31) == 0 && t) atomicAdd(dst, (unsigned long long)t);
+}
+
+// Warp-aggregated fetch of new rays for the idle lanes; all lanes call it.
+// Returns the new ray index of an idle lane, kDone when the queue is empty.
+__device__ __forceinline__ int fetch_rays(int cur, int* fetch, int count) {
+  const unsigned FULL = 0xffffffffu;
+  int lane = threadIdx.x & 31;
+  bool idle = cur == kIdle;
+  unsigned im = __ballot_sync(FULL, idle);
+  unsigned bm = __ballot_sync(FULL, cur >= 0);
+  if (im == 0 || (__popc(im) < kRefill && bm != 0)) return cur;
+  int leader = __ffs(im) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(fetch, __popc(im));
+  base = __shfl_sync(FULL, base, leader);
+  if (!idle) return cur;
+  int r = base + __popc(im & ((1u << lane) - 1u));
+  return r < count ? r : kDone;
+}
+
+// Closest hit for a queue of 64-byte records (origin in float4 0, direction in
+// float4 1: CamRay and PhotonRay).  hits[i] = (prim, t bits), prim -1 on a miss.
+__global__ void __launch_bounds__(kTraceThreads) k_trace_closest(SceneView s, const float4* __restrict__ recs,
+                                                                 const int* __restrict__ count_ptr, int cap,
+                                                                 int* __restrict__ fetch, int2* __restrict__ hits,
+                                                                 DevCounters* cnt, int which) {
+  const int count = min(*count_ptr, cap);
+  int ray = kIdle;
+  RayPre r;
+  Walk w;
+  int stack[64];
+  uint32_t visits = 0, ptests = 0;
+  while (true) {
+    int nr = fetch_rays(ray, fetch, count);
+    if (ray == kIdle && nr >= 0) {
+      float4 o = __ldg(recs + 4 * (size_t)nr), d = __ldg(recs + 4 * (size_t)nr + 1);
+      r = make_ray(xyz(o), xyz(d));
+      w.node = 0;
+      w.sp = 0;
+      w.best = -1;
+      w.best_t = FLT_MAX;
+      if (s.nt + s.ns == 0) {
+        hits[nr] = make_int2(-1, __float_as_int(FLT_MAX));
+        nr = kIdle;
+      }
+    }
+    ray = nr;
+    if (__all_sync(0xffffffffu, ray == kDone)) break;
+    for (int step = 0; step < kSteps && ray >= 0; ++step) {
+      if (closest_step(s, r, FLT_MAX, w, stack, &cnt->status, visits, ptests)) {
+        hits[ray] = make_int2(w.best, __float_as_int(w.best_t));
+        ray = kIdle;
+      }
+    }
+  }
+  warp_total(&cnt->node_visits, visits);
+  warp_total(&cnt->prim_tests, ptests);
+  warp_total(&cnt->visits_by[which], visits);
+  warp_total(&cnt->ptests_by[which], ptests);
+}
+
+// Shadow rays of the NEE vertices: any hit with tmax = (1 - 1e-4) dist from
+// the offset origin; an occluded vertex gets dE = 0.
+__global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, NeeStore nv, int cap,
+                                                                int* __restrict__ fetch, DevCounters* cnt) {
+  const int count = min(cnt->nee_count, cap);
+  int ray = kIdle;
+  RayPre r;
+  Walk w;
+  float tmax = 0.0f;
+  int stack[64];
+  uint32_t visits = 0, ptests = 0, rays = 0;
+  while (true) {
+    int nr = fetch_rays(ray, fetch, count);
+    if (ray == kIdle && nr >= 0) {
+      int bits = __float_as_int(nv.nrm[nr].w);
+      if ((bits >> NV_FLAG_SHIFT) & NV_SHADOW) {
+        float4 pp = nv.pos[nr], nn = nv.nrm[nr], ee = nv.err[nr], ld = nv.ldir[nr];
+        float3 ldir = xyz(ld);
+        r = make_ray(offset_origin(xyz(pp), xyz(nn), xyz(ee), ldir), ldir);
+        tmax = ee.w * (1.0f - 1e-4f);
+        w.node = 0;
+        w.sp = 0;
+        ++rays;
+        if (s.nt + s.ns == 0) nr = kIdle;
+      } else {
+        nr = kIdle;  // no shadow ray for this vertex
+      }
+    }
+    ray = nr;
+    if (__all_sync(0xffffffffu, ray == kDone)) break;
+    for (int step = 0; step < kSteps && ray >= 0; ++step) {
+      int res = any_step(s, r, tmax, w, stack, &cnt->status, visits, ptests);
+      if (res != 0) {
+        if (res > 0) nv.dE[ray] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        ray = kIdle;
+      }
+    }
+  }
+  warp_total(&cnt->shadow_rays, rays);
+  warp_total(&cnt->node_visits, visits);
+  warp_total(&cnt->prim_tests, ptests);
+  warp_total(&cnt->visits_by[1], visits);
+  warp_total(&cnt->ptests_by[1], ptests);
+}
+
+static int trace_blocks() {
+  static int blocks = 0;
+  if (blocks == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_closest, kTraceThreads, 0);
+    blocks = (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 4);
+  }
+  return blocks;
+}
+
+cudaError_t launch_trace_closest(neb_ctx* c, const float4* recs, const int* count_ptr, int cap, int2* hits,
+                                 int which) {
+  int* fetch = &c->counters->fetch[which];
+  cudaMemsetAsync(fetch, 0, sizeof(int), c->stream);
+  k_trace_closest<<<trace_blocks(), kTraceThreads, 0, c->stream>>>(scene_view(c), recs, count_ptr, cap, fetch, hits,
+                                                                   c->counters, which);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace_shadow(neb_ctx* c) {
+  int* fetch = &c->counters->fetch[1];
+  cudaMemsetAsync(fetch, 0, sizeof(int), c->stream);
+  k_trace_shadow<<<trace_blocks(), kTraceThreads, 0, c->stream>>>(scene_view(c), c->nv, c->cap_nee, fetch,
+                                                                  c->counters);
+  return cudaGetLastError();
+}
+
+}  // namespace neb

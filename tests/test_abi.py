@@ -39,11 +39,13 @@ def test_argument_errors_without_gpu(libneb):
     from paper_1909_00573_gb300 import neb
     L = neb.lib()
     h = ctypes.c_void_p()
-    cfg = neb.Config(0, 8, 4, 0.01, 64, 4, 0, 0, 0, 7, 0)          # width 0
+    cfg = neb.Config(0, 8, 4, 0.01, 64, 4, 0, 0, 0, 7, 0, 0)       # width 0
     assert L.neb_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
-    cfg = neb.Config(8, 8, 99, 0.01, 64, 4, 0, 0, 0, 7, 0)         # depth above 64
+    cfg = neb.Config(8, 8, 99, 0.01, 64, 4, 0, 0, 0, 7, 0, 0)      # depth above 64
     assert L.neb_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
-    cfg = neb.Config(8, 8, 4, 0.01, 64, 4, 0, 0, 0, 9, 0)          # unknown strategy bit
+    cfg = neb.Config(8, 8, 4, 0.01, 64, 4, 0, 0, 0, 9, 0, 0)       # unknown strategy bit
+    assert L.neb_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
+    cfg = neb.Config(8, 8, 4, 0.01, 64, 4, 0, 0, 0, 7, 0, 5)       # unknown BVH builder
     assert L.neb_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
     assert L.neb_iterate(None, 1) == -1
     assert L.neb_philox(None, -1, None, None) == -1

@@ -156,8 +156,9 @@ def _rays(rng, n, lo, hi):
     return np.concatenate([o, d], 1).astype(np.float32)
 
 
+@pytest.mark.parametrize("builder", [0, 1])
 @pytest.mark.parametrize("name", ["tiny_room", "soup", "spheres"])
-def test_bvh_closest_hit_equals_oracle(neb, oracle, name):
+def test_bvh_closest_hit_equals_oracle(neb, oracle, name, builder):
     from paper_1909_00573_gb300 import scenes
     rng = np.random.default_rng(41)
     if name == "tiny_room":
@@ -175,7 +176,7 @@ def test_bvh_closest_hit_equals_oracle(neb, oracle, name):
                          scenes.material(0, emission=(1, 1, 1))[None], np.zeros(10))
         rays = _rays(rng, 20000, -1.2, 1.2)
     rc = scenes.RenderConfig(8, 8, 4, 0.01, 1024, 4, 1)
-    ctx = neb.Context(neb.make_config(rc))
+    ctx = neb.Context(neb.make_config(rc, bvh_builder=builder))
     ctx.scene_upload(s)
     ctx.build_bvh()
     gp, gt = ctx.trace_closest(rays)
