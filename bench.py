@@ -121,19 +121,24 @@ def load_peaks():
 
 
 def stage_bytes(stage, d, P, iters):
-    """Algorithmic bytes of one stage over the profiled iterations (per-unit
-    figures: 64 B per ray record read or written, 112 B per NEE record, 48 B
-    per random-hit event, 64 B per BVH node visit, 48 B per triangle test,
-    16 B per merge candidate tested plus 48 B and 24 B of FP64 atomics per
-    accepted merge)."""
-    trav = {"extend": 0, "shadow": 1, "photon": 2}
-    if stage == "extend":
-        rec = 64 * d["camera_rays"] + 64 * max(d["camera_rays"] - P * iters, 0) + 112 * d["nee_vertices"] + \
-            48 * d["random_hits"]
+    """Algorithmic bytes of one stage over the profiled iterations, with and
+    without BVH traversal.  Per-unit figures: 64 B per BVH node visit and 48 B
+    per triangle test (traversal); 32 B ray read + 8 B hit written per traced
+    ray; 64 B per ray record read or written; 112 B per NEE record; 48 B per
+    random-hit event; 16 B per merge candidate tested, 48 B + 24 B of FP64
+    atomics per accepted merge."""
+    trav = {"trace_camera": 0, "shadow": 1, "trace_photon": 2}
+    if stage == "trace_camera":
+        rec = 40 * d["camera_rays"]
+    elif stage == "trace_photon":
+        rec = 40 * d["photon_hits"]
     elif stage == "shadow":
         rec = 64 * d["nee_vertices"] + 16 * d["shadow_rays"]
+    elif stage == "extend":
+        return (72 * d["camera_rays"] + 64 * max(d["camera_rays"] - P * iters, 0) + 112 * d["nee_vertices"] +
+                48 * d["random_hits"]), None
     elif stage == "photon":
-        rec = 64 * 2 * d["photon_hits"] + 16 * d["merge_tests"] + (48 + 24) * d["merges"]
+        return 72 * d["photon_hits"] + 64 * d["photon_hits"] + 16 * d["merge_tests"] + 72 * d["merges"], None
     else:
         return None, None
     k = trav[stage]
@@ -288,7 +293,8 @@ def main():
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
                 "bytes_per_launch": per_launch, "avg_launch_ms": avg_ms,
-                "achieved_without_traversal": (byt_nt / dom_launches) / (avg_ms / 1000.0) / 1e9}
+                "achieved_without_traversal": (None if byt_nt is None else
+                                               (byt_nt / dom_launches) / (avg_ms / 1000.0) / 1e9)}
     total_stage_ms = sum(v[0] for v in stages.values())
     ctx.close()
 
