@@ -391,6 +391,9 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
     bool emit = false;
     PhotonRay nph;
     uint32_t nhits = 0, tests = 0, merges = 0;
+    bool want_merge = false;
+    float3 m_p = f3(0, 0, 0), m_d = f3(0, 0, 0), m_phi = f3(0, 0, 0);
+    float m_s1 = 0.0f;
     if (i < count) {
       PhotonRay ph = in[i];
       float3 d = xyz(ph.d);
@@ -412,46 +415,11 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
           float3 phi = xyz(ph.phi);
           bool hdelta = mat_delta(hm);
           if (!hdelta) {
-            float s1 = (E0 * pA + pB) * cos_orig / (pdf_dir * cos_hit);
-            float3 md = neg(d);
-            float gx = (hp.x - ip.gmin.x) * ip.cell_inv, gy = (hp.y - ip.gmin.y) * ip.cell_inv,
-                  gz = (hp.z - ip.gmin.z) * ip.cell_inv;
-            int cx = (int)floorf(gx), cy = (int)floorf(gy), cz = (int)floorf(gz);
-            int ox = (gx - (float)cx >= 0.5f) ? 1 : -1, oy = (gy - (float)cy >= 0.5f) ? 1 : -1,
-                oz = (gz - (float)cz >= 0.5f) ? 1 : -1;
-            uint32_t bk[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c)
-              bk[c] = grid_hash(cx + ((c & 1) ? ox : 0), cy + ((c & 2) ? oy : 0), cz + ((c & 4) ? oz : 0),
-                                ip.table_mask);
-            for (int c = 0; c < 8; ++c) {
-              bool dup = false;
-              for (int c2 = 0; c2 < c; ++c2) dup |= bk[c2] == bk[c];
-              if (dup) continue;
-              int b0 = __ldg(bucket_start + bk[c]), b1 = __ldg(bucket_start + bk[c] + 1);
-              for (int e = b0; e < b1; ++e) {
-                float4 mp = __ldg(&mrec[e].pos);
-                float dx = mp.x - hp.x, dy = mp.y - hp.y, dz = mp.z - hp.z;
-                float d2 = dx * dx + dy * dy + dz * dz;
-                ++tests;
-                if (!(d2 <= ip.r2)) continue;
-                float4 mn = __ldg(&mrec[e].nrm);
-                int mb = __float_as_int(mn.w);
-                int kk = (mb >> NV_K_SHIFT) & 63;
-                if (kk + j + 1 > ip.D) continue;
-                Mat cm = load_mat(s.mats, mb & NV_MAT_MASK);
-                float4 mw = __ldg(&mrec[e].wo);
-                float3 cn = xyz(mn), cwo = xyz(mw);
-                float3 f = bsdf_eval(cm, cn, cwo, md);
-                if (!(maxc(f) > 0.0f)) continue;
-                float pdfF = bsdf_pdf(cm, cn, cwo, md), pdfC = bsdf_pdf(cm, cn, md, cwo);
-                float inv_w = 1.0f + pdfF * s1 + pdfC * mp.w;
-                float3 ctau = xyz(__ldg(&mrec[e].tau));
-                float3 L = mul(cmul(cmul(ctau, f), phi), ip.kernel / inv_w);
-                add_pixel(accum, split, 2, __float_as_int(mw.w), L, P);
-                ++merges;
-              }
-            }
+            want_merge = true;
+            m_p = hp;
+            m_d = d;
+            m_phi = phi;
+            m_s1 = (E0 * pA + pB) * cos_orig / (pdf_dir * cos_hit);
           }
           if (j + 1 <= ip.D - 2) {
             uint4 rb = rng_block(ip.key, ip.iteration, pixel, 256u * knee + 1u + (uint32_t)j, 1);
@@ -471,6 +439,59 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
               }
             }
           }
+        }
+      }
+    }
+    // Merge (inverted range search, Sec. 3.2): the warp handles its photon hits
+    // one after another and splits each hit's candidate lists across its 32
+    // lanes, so a hit in a dense cell does not serialise on one lane.
+    unsigned wm = __ballot_sync(0xffffffffu, want_merge);
+    while (wm) {
+      int src = __ffs(wm) - 1;
+      wm &= wm - 1;
+      float3 hp = f3(__shfl_sync(0xffffffffu, m_p.x, src), __shfl_sync(0xffffffffu, m_p.y, src),
+                     __shfl_sync(0xffffffffu, m_p.z, src));
+      float3 md = f3(-__shfl_sync(0xffffffffu, m_d.x, src), -__shfl_sync(0xffffffffu, m_d.y, src),
+                     -__shfl_sync(0xffffffffu, m_d.z, src));
+      float3 phi = f3(__shfl_sync(0xffffffffu, m_phi.x, src), __shfl_sync(0xffffffffu, m_phi.y, src),
+                      __shfl_sync(0xffffffffu, m_phi.z, src));
+      float s1 = __shfl_sync(0xffffffffu, m_s1, src);
+      float gx = (hp.x - ip.gmin.x) * ip.cell_inv, gy = (hp.y - ip.gmin.y) * ip.cell_inv,
+            gz = (hp.z - ip.gmin.z) * ip.cell_inv;
+      int cx = (int)floorf(gx), cy = (int)floorf(gy), cz = (int)floorf(gz);
+      int ox = (gx - (float)cx >= 0.5f) ? 1 : -1, oy = (gy - (float)cy >= 0.5f) ? 1 : -1,
+          oz = (gz - (float)cz >= 0.5f) ? 1 : -1;
+      uint32_t bk[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        bk[c] = grid_hash(cx + ((c & 1) ? ox : 0), cy + ((c & 2) ? oy : 0), cz + ((c & 4) ? oz : 0),
+                          ip.table_mask);
+      for (int c = 0; c < 8; ++c) {
+        bool dup = false;
+        for (int c2 = 0; c2 < c; ++c2) dup |= bk[c2] == bk[c];
+        if (dup) continue;
+        int b0 = __ldg(bucket_start + bk[c]), b1 = __ldg(bucket_start + bk[c] + 1);
+        for (int e = b0 + (int)(threadIdx.x & 31); e < b1; e += 32) {
+          float4 mp = __ldg(&mrec[e].pos);
+          float dx = mp.x - hp.x, dy = mp.y - hp.y, dz = mp.z - hp.z;
+          float d2 = dx * dx + dy * dy + dz * dz;
+          ++tests;
+          if (!(d2 <= ip.r2)) continue;
+          float4 mn = __ldg(&mrec[e].nrm);
+          int mb = __float_as_int(mn.w);
+          int kk = (mb >> NV_K_SHIFT) & 63;
+          if (kk + j + 1 > ip.D) continue;
+          Mat cm = load_mat(s.mats, mb & NV_MAT_MASK);
+          float4 mw = __ldg(&mrec[e].wo);
+          float3 cn = xyz(mn), cwo = xyz(mw);
+          float3 f = bsdf_eval(cm, cn, cwo, md);
+          if (!(maxc(f) > 0.0f)) continue;
+          float pdfF = bsdf_pdf(cm, cn, cwo, md), pdfC = bsdf_pdf(cm, cn, md, cwo);
+          float inv_w = 1.0f + pdfF * s1 + pdfC * mp.w;
+          float3 ctau = xyz(__ldg(&mrec[e].tau));
+          float3 L = mul(cmul(cmul(ctau, f), phi), ip.kernel / inv_w);
+          add_pixel(accum, split, 2, __float_as_int(mw.w), L, P);
+          ++merges;
         }
       }
     }
