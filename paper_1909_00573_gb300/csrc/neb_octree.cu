@@ -47,9 +47,10 @@ __global__ void k_oct_rearm(int* nodes, const OctreeState* st, OctreeParams P) {
 
 __global__ void k_oct_insert_points(int* nodes, OctreeState* st, OctreeParams P, const float* __restrict__ pos, int n,
                                     int spin_limit) {
+  const bool frozen = st->alloc > P.capacity;  // overflowed in an earlier launch
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     float p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
-    oct_insert_atomic(nodes, st, P, p, spin_limit);
+    oct_insert_atomic(nodes, st, P, p, spin_limit, frozen);
   }
 }
 
@@ -78,11 +79,12 @@ __global__ void k_oct_density_points(const int* __restrict__ nodes, const Octree
 __global__ void k_oct_insert_nee(int* nodes, OctreeState* st, OctreeParams P, const float4* __restrict__ vpos,
                                  DevCounters* cnt, int cap, int spin_limit) {
   int count = min(cnt->nee_count, cap);
+  const bool frozen = st->alloc > P.capacity;  // overflowed in an earlier iteration
   uint32_t done = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
     float4 v = vpos[i];
     float p[3] = {v.x, v.y, v.z};
-    oct_insert_atomic(nodes, st, P, p, spin_limit);
+    oct_insert_atomic(nodes, st, P, p, spin_limit, frozen);
     ++done;
   }
   if (done) atomicAdd(&cnt->octree_inserts, (unsigned long long)done);

@@ -100,11 +100,15 @@ __device__ __forceinline__ void oct_insert_seq(int* nodes, OctreeState* st, cons
 // threshold exactly), the others wait for the child pointer with a bounded
 // spin and then count in the child.  A spin that runs out sets
 // NEB_STATUS_SPIN_TIMEOUT and drops the insert; it never traps.
-__device__ __forceinline__ int oct_inc_atomic(int* nodes, int idx) {
+__device__ __forceinline__ int oct_inc_atomic(int* nodes, int idx, bool frozen) {
   // A plain (cacheable) first read is enough: a child pointer never changes
   // once published, and a stale counter only makes the CAS below fail and
   // return the current value.
   int old = nodes[idx];
+  // frozen: the allocation overflowed before this kernel started, so no
+  // counter can turn into a child pointer any more and a plain atomic add is
+  // the same increment without CAS retries on crowded leaves
+  if (frozen && old >= 0) return atomicAdd(nodes + idx, 1) + 1;
   while (true) {
     if (old < 0) return old;
     int prev = atomicCAS(nodes + idx, old, old + 1);
@@ -141,11 +145,11 @@ __device__ __forceinline__ int oct_split_atomic(int* nodes, OctreeState* st, con
 }
 
 __device__ __forceinline__ void oct_insert_atomic(int* nodes, OctreeState* st, const OctreeParams& P,
-                                                  const float pos[3], int spin_limit) {
+                                                  const float pos[3], int spin_limit, bool frozen) {
   if (P.stop_filling) return;
   float np[3];
   if (!oct_norm_pos(P, pos, np)) return;
-  int v = oct_inc_atomic(nodes, 0);
+  int v = oct_inc_atomic(nodes, 0, frozen);
   v = oct_split_atomic(nodes, st, P, 0, v, 0, spin_limit);
   int edge = 1, depth = 0;
   while (v < 0) {
@@ -155,7 +159,7 @@ __device__ __forceinline__ void oct_insert_atomic(int* nodes, OctreeState* st, c
     int iy = ((int)(np[1] * (float)edge)) & 1;
     int iz = ((int)(np[2] * (float)edge)) & 1;
     int idx = ix + 2 * (iy + 2 * iz) - v;
-    v = oct_inc_atomic(nodes, idx);
+    v = oct_inc_atomic(nodes, idx, frozen);
     v = oct_split_atomic(nodes, st, P, idx, v, depth, spin_limit);
   }
 }

@@ -1,0 +1,80 @@
+"""Parity at the full workload sizes, in the launch configuration bench.py
+times (full image, D = 10, concurrent octree).
+
+With photon merges disabled (strategy mask e|E) every camera path is
+independent of all others, so the oracle can compute sampled bands of pixels
+on its own and each path is compared one by one.  With all strategies on,
+the whole-iteration outputs are checked through properties that hold at any
+size (counters consistent, finite non-negative image, octree accounting)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def neb():
+    from paper_1909_00573_gb300 import build
+    build.build()
+    from paper_1909_00573_gb300 import neb as N
+    return N
+
+
+def _band_parity(neb, oracle, scene, rc, rows):
+    W = rc.width
+    ctx = neb.render(scene, rc, n_iter=1, keep_split=True)
+    g = ctx.read_split()
+    st = ctx.stats(check=False)
+    ctx.close()
+    assert st["status"] & ~neb.STATUS_OCTREE_FULL == 0
+    worst = 1.0
+    for r0 in rows:
+        ref = oracle.render(scene, rc, n_iter=1, pixel_range=(r0 * W, (r0 + 4) * W))
+        o = ref["split"][:, r0:r0 + 4].sum(0).sum(-1)
+        gg = g[:, r0:r0 + 4].sum(0).sum(-1)
+        floor = 1e-6 * max(float(np.abs(o).max()), 1e-30)
+        ok = np.abs(gg - o) <= 1e-4 * np.abs(o) + floor
+        worst = min(worst, ok.mean())
+        assert o.sum() > 0
+    return worst
+
+
+def test_large_city_fullsize_per_path_parity(neb, oracle):
+    from paper_1909_00573_gb300 import scenes
+    s, rc = scenes.workload("large_city")
+    rc.strategy_mask = 3
+    frac = _band_parity(neb, oracle, s, rc, rows=[100, 358, 600])
+    assert frac >= 0.999, frac
+
+
+def test_many_lights_fullsize_per_path_parity(neb, oracle):
+    """65,536 sphere lights through the alias table and the GGX roof patch."""
+    from paper_1909_00573_gb300 import scenes
+    s, rc = scenes.workload("many_lights")
+    rc.strategy_mask = 3
+    frac = _band_parity(neb, oracle, s, rc, rows=[300, 538])
+    assert frac >= 0.999, frac
+
+
+@pytest.mark.parametrize("name", ["large_city", "many_lights"])
+def test_fullsize_all_strategies_properties(neb, name):
+    from paper_1909_00573_gb300 import scenes
+    s, rc = scenes.workload(name)
+    ctx = neb.render(s, rc, n_iter=2, keep_split=True)
+    st = ctx.stats(check=False)
+    split = ctx.read_split()
+    img = ctx.resolve()
+    ctx.close()
+    P = rc.width * rc.height
+    assert st["status"] & ~neb.STATUS_OCTREE_FULL == 0          # no spin timeout, overflow or stack overflow
+    assert st["iterations"] == 2
+    assert st["octree_inserts"] == st["nee_vertices"] <= 2 * P * (rc.max_depth - 1)
+    assert st["octree_queries"] == 5 * st["nee_vertices"]        # robust query: five lookups
+    assert st["shadow_rays"] <= st["nee_vertices"]
+    assert st["photons"] <= st["shadow_rays"]
+    assert st["merges"] <= st["merge_tests"]
+    assert st["camera_rays"] <= 2 * P * rc.max_depth
+    assert np.all(np.isfinite(img)) and img.min() >= 0.0
+    assert split[0].sum() > 0 and split[1].sum() > 0              # random hits and NEE contribute
+    if st["merges"] > 0:
+        assert split[2].sum() > 0

@@ -316,3 +316,20 @@ def test_zero_and_degenerate_inputs(neb):
     # argument errors surface as exceptions
     with pytest.raises(neb.NebError):
         neb.Context(neb.make_config(scenes.RenderConfig(0, 4, 4, 0.01, 64, 4, 1)))
+
+
+def test_octree_full_concurrent_equals_sequential(neb, oracle):
+    """After an allocation overflow no cell can split again; concurrent inserts
+    then only count, so they must give exactly the sequential node array."""
+    its = _octree_inputs(61, n_iter=3, n=8000)
+    g = neb.Octree([0, 0, 0], [1, 1, 1], 256, 4)
+    o = oracle.Octree([0, 0, 0], [1, 1, 1], 256, 4)
+    for i, pts in enumerate(its, start=1):
+        g.set_iteration(i)
+        o.set_iteration(i)
+        g.insert(pts, mode=1 if i == 1 else 0)     # first iteration fills the tree in order
+        o.insert(pts)
+        gn, ga, gd, gs = g.read()
+        on, oa, od = o.dump()
+        assert gs & neb.STATUS_OCTREE_FULL
+        assert (ga, gd) == (oa, od) and np.array_equal(gn, on), i
