@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=2)
     ap.add_argument("--res", default=None, help="WxH override (smaller cases for ncu captures)")
     ap.add_argument("--bvh", type=int, default=0, help="0 PLOC (default), 1 Karras LBVH")
+    ap.add_argument("--octree-cap", type=int, default=None, help="octree capacity override (analysis runs)")
     return ap.parse_args()
 
 
@@ -230,6 +231,8 @@ def main():
     scene, rc = scenes.workload(args.workload)
     if args.res:
         rc.width, rc.height = (int(x) for x in args.res.lower().split("x"))
+    if args.octree_cap:
+        rc.octree_capacity = args.octree_cap
     rc.seed = rank                      # replicas render independent sample streams
     P = rc.width * rc.height
     # a dedicated (non-default) stream: the library's kernels and the timing

@@ -48,9 +48,22 @@ __global__ void k_oct_rearm(int* nodes, const OctreeState* st, OctreeParams P) {
 __global__ void k_oct_insert_points(int* nodes, OctreeState* st, OctreeParams P, const float* __restrict__ pos, int n,
                                     int spin_limit) {
   const bool frozen = st->alloc > P.capacity;  // overflowed in an earlier launch
+  if (frozen) {
+    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+      int i = base + threadIdx.x;
+      int leaf = -1;
+      if (i < n) {
+        float p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+        leaf = oct_frozen_leaf(nodes, P, p);
+      }
+      unsigned same = __match_any_sync(0xffffffffu, leaf);
+      if (leaf >= 0 && (int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(nodes + leaf, __popc(same));
+    }
+    return;
+  }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     float p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
-    oct_insert_atomic(nodes, st, P, p, spin_limit, frozen);
+    oct_insert_atomic(nodes, st, P, p, spin_limit, false);
   }
 }
 
@@ -81,11 +94,30 @@ __global__ void k_oct_insert_nee(int* nodes, OctreeState* st, OctreeParams P, co
   int count = min(cnt->nee_count, cap);
   const bool frozen = st->alloc > P.capacity;  // overflowed in an earlier iteration
   uint32_t done = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
-    float4 v = vpos[i];
-    float p[3] = {v.x, v.y, v.z};
-    oct_insert_atomic(nodes, st, P, p, spin_limit, frozen);
-    ++done;
+  if (frozen) {
+    // No cell can split any more: every insert only counts in its leaf.  Lanes
+    // of a warp that land in the same leaf add their count with one atomic
+    // (neighbouring paths share leaves; crowded leaves would otherwise
+    // serialise thousands of single increments).
+    for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
+      int i = base + threadIdx.x;
+      int leaf = -1;
+      if (i < count) {
+        float4 v = vpos[i];
+        float p[3] = {v.x, v.y, v.z};
+        leaf = oct_frozen_leaf(nodes, P, p);
+        ++done;
+      }
+      unsigned same = __match_any_sync(0xffffffffu, leaf);
+      if (leaf >= 0 && (int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(nodes + leaf, __popc(same));
+    }
+  } else {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+      float4 v = vpos[i];
+      float p[3] = {v.x, v.y, v.z};
+      oct_insert_atomic(nodes, st, P, p, spin_limit, false);
+      ++done;
+    }
   }
   if (done) atomicAdd(&cnt->octree_inserts, (unsigned long long)done);
 }

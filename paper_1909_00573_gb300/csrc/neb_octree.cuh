@@ -164,6 +164,26 @@ __device__ __forceinline__ void oct_insert_atomic(int* nodes, OctreeState* st, c
   }
 }
 
+// Leaf reached by a position once the octree can no longer split (allocation
+// overflowed): a read-only descent; -1 for positions outside the box.
+__device__ __forceinline__ int oct_frozen_leaf(const int* nodes, const OctreeParams& P, const float pos[3]) {
+  if (P.stop_filling) return -1;
+  float np[3];
+  if (!oct_norm_pos(P, pos, np)) return -1;
+  int idx = 0;
+  int v = nodes[0];
+  int edge = 1;
+  while (v < 0) {
+    edge *= 2;
+    int ix = ((int)(np[0] * (float)edge)) & 1;
+    int iy = ((int)(np[1] * (float)edge)) & 1;
+    int iz = ((int)(np[2] * (float)edge)) & 1;
+    idx = ix + 2 * (iy + 2 * iz) - v;
+    v = nodes[idx];
+  }
+  return idx;
+}
+
 // ---- query -----------------------------------------------------------------
 // get_density of the listing with the final normalisation in FP64:
 // rho = c / (min(iter, 1000) * max(minArea, A)).  *size receives the cell
