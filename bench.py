@@ -257,10 +257,12 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()          # ncu --profile-from-start off captures exactly the timed steps
     ev0.record(stream)
     ctx.iterate(args.steps)
     ev1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     wall_ms = (time.perf_counter() - t_wall0) * 1000.0
     if dist:
         dist.barrier()

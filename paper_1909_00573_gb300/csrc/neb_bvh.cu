@@ -233,14 +233,18 @@ __global__ void k_write_nodes(SceneView s, int n, const int* __restrict__ sorted
   }
 }
 
-__global__ void k_single_leaf(SceneView s, BVHNode* nodes) {
+__global__ void k_single_leaf(SceneView s, BVH4Node* nodes) {
   float3 lo, hi;
   prim_bounds(s, 0, lo, hi);
-  BVHNode nd;
-  nd.a = make_float4(lo.x, hi.x, lo.y, hi.y);
-  nd.b = nd.a;
-  nd.c = make_float4(lo.z, hi.z, lo.z, hi.z);
-  nd.ch = make_int4(~0, ~0, 0, 0);
+  BVH4Node nd;
+  nd.lox = make_float4(lo.x, 0, 0, 0);
+  nd.hix = make_float4(hi.x, 0, 0, 0);
+  nd.loy = make_float4(lo.y, 0, 0, 0);
+  nd.hiy = make_float4(hi.y, 0, 0, 0);
+  nd.loz = make_float4(lo.z, 0, 0, 0);
+  nd.hiz = make_float4(hi.z, 0, 0, 0);
+  nd.ch = make_int4(~0, kEmptyChild, kEmptyChild, kEmptyChild);
+  nd.pad = make_float4(0, 0, 0, 0);
   nodes[0] = nd;
 }
 
@@ -391,18 +395,127 @@ static cudaError_t ploc_build(const SceneView& s, int n, const int* sorted_prim,
   return e;
 }
 
+// ---- collapse of the binary tree into a 4-wide BVH ----------------------------------
+// Top down, one tree level of 4-wide nodes per launch: a node starts from the
+// two children of its binary node and repeatedly opens the inner child with
+// the largest surface area until it has four children or only leaves.  The
+// children that stay inner become the next level's work; siblings get
+// consecutive node indices.
+__global__ void k_collapse4(const BVHNode* __restrict__ bin, const int2* __restrict__ work, int n_work,
+                            BVH4Node* out, int2* next_work, int* counters) {
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < n_work; w += gridDim.x * blockDim.x) {
+    int2 it = work[w];
+    BVHNode b = bin[it.x];
+    int ref[4];
+    float3 lo[4], hi[4];
+    ref[0] = b.ch.x;
+    lo[0] = f3(b.a.x, b.a.z, b.c.x);
+    hi[0] = f3(b.a.y, b.a.w, b.c.y);
+    ref[1] = b.ch.y;
+    lo[1] = f3(b.b.x, b.b.z, b.c.z);
+    hi[1] = f3(b.b.y, b.b.w, b.c.w);
+    int cnt = 2;
+    while (cnt < 4) {
+      int best = -1;
+      float barea = -1.0f;
+      for (int i = 0; i < cnt; ++i)
+        if (ref[i] >= 0) {
+          float a = half_area(lo[i], hi[i]);
+          if (a > barea) { barea = a; best = i; }
+        }
+      if (best < 0) break;
+      BVHNode cb = bin[ref[best]];
+      ref[best] = cb.ch.x;
+      lo[best] = f3(cb.a.x, cb.a.z, cb.c.x);
+      hi[best] = f3(cb.a.y, cb.a.w, cb.c.y);
+      ref[cnt] = cb.ch.y;
+      lo[cnt] = f3(cb.b.x, cb.b.z, cb.c.z);
+      hi[cnt] = f3(cb.b.y, cb.b.w, cb.c.w);
+      ++cnt;
+    }
+    int k = 0;
+    for (int i = 0; i < cnt; ++i) k += ref[i] >= 0;
+    int base = k ? atomicAdd(&counters[0], k) : 0;
+    int wb = k ? atomicAdd(&counters[1], k) : 0;
+    float L[3][4], H[3][4];
+    int R[4];
+    int j = 0;
+    for (int i = 0; i < 4; ++i) {
+      if (i < cnt) {
+        L[0][i] = lo[i].x; L[1][i] = lo[i].y; L[2][i] = lo[i].z;
+        H[0][i] = hi[i].x; H[1][i] = hi[i].y; H[2][i] = hi[i].z;
+        if (ref[i] >= 0) {
+          R[i] = base + j;
+          next_work[wb + j] = make_int2(ref[i], base + j);
+          ++j;
+        } else {
+          R[i] = ref[i];
+        }
+      } else {
+        L[0][i] = L[1][i] = L[2][i] = 0.0f;
+        H[0][i] = H[1][i] = H[2][i] = 0.0f;
+        R[i] = kEmptyChild;
+      }
+    }
+    BVH4Node o;
+    o.lox = make_float4(L[0][0], L[0][1], L[0][2], L[0][3]);
+    o.hix = make_float4(H[0][0], H[0][1], H[0][2], H[0][3]);
+    o.loy = make_float4(L[1][0], L[1][1], L[1][2], L[1][3]);
+    o.hiy = make_float4(H[1][0], H[1][1], H[1][2], H[1][3]);
+    o.loz = make_float4(L[2][0], L[2][1], L[2][2], L[2][3]);
+    o.hiz = make_float4(H[2][0], H[2][1], H[2][2], H[2][3]);
+    o.ch = make_int4(R[0], R[1], R[2], R[3]);
+    o.pad = make_float4(0, 0, 0, 0);
+    out[it.y] = o;
+  }
+}
+
+static cudaError_t collapse4(const BVHNode* bin, int n_bin, BVH4Node* out, cudaStream_t st, int* n_out) {
+  int2 *w0 = nullptr, *w1 = nullptr;
+  int* cnt = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (cudaMalloc(&w0, 8ull * (n_bin + 1)) != cudaSuccess || cudaMalloc(&w1, 8ull * (n_bin + 1)) != cudaSuccess ||
+      cudaMalloc(&cnt, 8) != cudaSuccess) {
+    cudaFree(w0); cudaFree(w1); cudaFree(cnt);
+    return cudaErrorMemoryAllocation;
+  }
+  int2 root = make_int2(0, 0);
+  int init[2] = {1, 0};
+  cudaMemcpyAsync(w0, &root, 8, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(cnt, init, 8, cudaMemcpyHostToDevice, st);
+  int n_work = 1;
+  int h[2] = {1, 0};
+  while (n_work > 0) {
+    int blocks = (n_work + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_collapse4<<<blocks, 256, 0, st>>>(bin, w0, n_work, out, w1, cnt);
+    cudaMemcpyAsync(h, cnt, 8, cudaMemcpyDeviceToHost, st);
+    cudaMemsetAsync(cnt + 1, 0, 4, st);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) break;
+    n_work = h[1];
+    int2* t = w0; w0 = w1; w1 = t;
+  }
+  *n_out = h[0];
+  cudaFree(w0); cudaFree(w1); cudaFree(cnt);
+  return e;
+}
+
 cudaError_t build_bvh(neb_ctx* c) {
   int n = c->nt + c->ns;
   cudaStream_t st = c->stream;
   if (c->nodes) { cudaFree(c->nodes); c->nodes = nullptr; }
   if (n == 0) return cudaSuccess;
-  cudaError_t e = cudaMalloc(&c->nodes, sizeof(BVHNode) * (size_t)(n > 1 ? n - 1 : 1));
+  cudaError_t e = cudaMalloc(&c->nodes, sizeof(BVH4Node) * (size_t)(n > 1 ? n - 1 : 1));
   if (e != cudaSuccess) return e;
   SceneView s = scene_view(c);
   if (n == 1) {
     k_single_leaf<<<1, 1, 0, st>>>(s, c->nodes);
     return cudaGetLastError();
   }
+  BVHNode* bin = nullptr;
+  e = cudaMalloc(&bin, sizeof(BVHNode) * (size_t)(n - 1));
+  if (e != cudaSuccess) return e;
   int nblocks = (n + kSortThreads - 1) / kSortThreads;
   size_t hist_n = (size_t)16 * nblocks;
   uint32_t *k0 = nullptr, *k1 = nullptr;
@@ -439,21 +552,25 @@ cudaError_t build_bvh(neb_ctx* c) {
       cudaMemsetAsync(flags, 0, 4ull * (n - 1), st);
       k_karras<<<gb, 256, 0, st>>>(k0, n, child, pint, pleaf);
       k_bounds<<<gb, 256, 0, st>>>(s, n, v0, child, pint, pleaf, flags, boxes);
-      k_write_nodes<<<gb, 256, 0, st>>>(s, n, v0, child, boxes, c->nodes);
+      k_write_nodes<<<gb, 256, 0, st>>>(s, n, v0, child, boxes, bin);
       e = cudaStreamSynchronize(st);
     } else {
       Scratch sc2;
       sc2.n = scan_scratch_ints(n);
       e = cudaMalloc(&sc2.data, 4ull * sc2.n);
-      if (e == cudaSuccess) e = ploc_build(s, n, v0, c->nodes, sc2, st);
+      if (e == cudaSuccess) e = ploc_build(s, n, v0, bin, sc2, st);
       cudaFree(sc2.data);
     }
     if (e == cudaSuccess) e = cudaGetLastError();
+    int n4 = 0;
+    if (e == cudaSuccess) e = collapse4(bin, n - 1, c->nodes, st, &n4);
+    c->n_nodes4 = n4;
   } else {
     e = cudaErrorMemoryAllocation;
   }
   cudaFree(k0); cudaFree(k1); cudaFree(v0); cudaFree(v1); cudaFree(hist); cudaFree(offs); cudaFree(cb);
   cudaFree(child); cudaFree(pint); cudaFree(pleaf); cudaFree(flags); cudaFree(boxes); cudaFree(sc.data);
+  cudaFree(bin);
   return e;
 }
 

@@ -358,7 +358,7 @@ struct SceneView {
   const float4* __restrict__ sph;  // centre, radius
   const int* __restrict__ sph_mat;
   const float4* __restrict__ mats; // 3 float4 per material
-  const BVHNode* __restrict__ nodes;
+  const BVH4Node* __restrict__ nodes;
   const int* __restrict__ prim_light;
   const int* __restrict__ light_prim;
   const float* __restrict__ light_psel;
@@ -377,98 +377,101 @@ __device__ __forceinline__ float isect_prim(const SceneView& s, const RayPre& r,
   return isect_sph(r, __ldg(s.sph + (p - s.nt)));
 }
 
+// ---- BVH4 traversal --------------------------------------------------------------
+struct Node4 {
+  float4 lox, hix, loy, hiy, loz, hiz;
+  int4 ch;
+};
+__device__ __forceinline__ Node4 load_node4(const BVH4Node* __restrict__ nodes, int i) {
+  const float4* p = reinterpret_cast<const float4*>(nodes + i);
+  Node4 n;
+  n.lox = __ldg(p);
+  n.hix = __ldg(p + 1);
+  n.loy = __ldg(p + 2);
+  n.hiy = __ldg(p + 3);
+  n.loz = __ldg(p + 4);
+  n.hiz = __ldg(p + 5);
+  n.ch = __ldg(reinterpret_cast<const int4*>(p + 6));
+  return n;
+}
+__device__ __forceinline__ float comp4(float4 v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w)); }
+__device__ __forceinline__ int comp4i(int4 v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w)); }
+
+__device__ __forceinline__ bool child_hit(const Node4& n, int c, const RayPre& r, float tmax, float& tnear) {
+  return box_hit(f3(comp4(n.lox, c), comp4(n.loy, c), comp4(n.loz, c)),
+                 f3(comp4(n.hix, c), comp4(n.hiy, c), comp4(n.hiz, c)), r, tmax, tnear);
+}
+
+// One node step of the closest-hit walk over the BVH4: leaf children whose
+// box is hit are tested at once, hit inner children are visited near-first
+// (the others pushed far-to-near).  Returns true when the walk is over.
+__device__ __forceinline__ bool closest_step4(const SceneView& s, const RayPre& r, float tmax, int& node, int& sp,
+                                              int* stack, float& best_t, int& best, uint32_t* status,
+                                              uint32_t& visits, uint32_t& ptests) {
+  Node4 n = load_node4(s.nodes, node);
+  ++visits;
+  float td[4];
+  int cr[4];
+  int cnt = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    int ref = comp4i(n.ch, c);
+    if (ref == kEmptyChild) continue;
+    float tn;
+    if (!child_hit(n, c, r, best_t, tn)) continue;
+    if (ref < 0) {
+      int p = ~ref;
+      ++ptests;
+      float t = isect_prim(s, r, p);
+      if (t > 0.0f && t < tmax && (t < best_t || (t == best_t && best >= 0 && p < best))) {
+        best_t = t;
+        best = p;
+      }
+    } else {
+      td[cnt] = tn;
+      cr[cnt] = ref;
+      ++cnt;
+    }
+  }
+  if (cnt == 0) {
+    if (sp == 0) return true;
+    node = stack[--sp];
+    return false;
+  }
+  // sort the (at most four) inner children by entry distance
+  for (int a = 1; a < cnt; ++a) {
+    float tv = td[a];
+    int rv = cr[a];
+    int b = a - 1;
+    while (b >= 0 && td[b] > tv) {
+      td[b + 1] = td[b];
+      cr[b + 1] = cr[b];
+      --b;
+    }
+    td[b + 1] = tv;
+    cr[b + 1] = rv;
+  }
+  for (int a = cnt - 1; a >= 1; --a) {
+    if (sp < 64) stack[sp++] = cr[a];
+    else atomicOr(status, NEB_STATUS_STACK_OVERFLOW);
+  }
+  node = cr[0];
+  return false;
+}
+
 // Closest hit with t in (deltaT, tmax); equal distances go to the lower
-// primitive index.  Children are visited near-first; leaves hold one primitive.
+// primitive index.
 __device__ __forceinline__ int trace_closest(const SceneView& s, const RayPre& r, float tmax, float& t_out,
                                              uint32_t* status, uint32_t& visits, uint32_t& ptests) {
   int best = -1;
   float best_t = tmax;
   if (s.nt + s.ns == 0) { t_out = tmax; return -1; }
   int stack[64];
-  int sp = 0;
-  int node = 0;
-  while (true) {
-    const float4* np = reinterpret_cast<const float4*>(s.nodes + node);
-    float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
-    int4 ch = __ldg(reinterpret_cast<const int4*>(np + 3));
-    ++visits;
-    float tl, tr;
-    bool hl = box_hit(f3(a.x, a.z, c.x), f3(a.y, a.w, c.y), r, best_t, tl);
-    bool hr = box_hit(f3(b.x, b.z, c.z), f3(b.y, b.w, c.w), r, best_t, tr);
-    if (hl && ch.x < 0) {
-      int p = ~ch.x;
-      ++ptests;
-      float t = isect_prim(s, r, p);
-      if (t > 0.0f && t < tmax && (t < best_t || (t == best_t && best >= 0 && p < best))) { best_t = t; best = p; }
-      hl = false;
-    }
-    if (hr && ch.y < 0) {
-      int p = ~ch.y;
-      ++ptests;
-      float t = isect_prim(s, r, p);
-      if (t > 0.0f && t < tmax && (t < best_t || (t == best_t && best >= 0 && p < best))) { best_t = t; best = p; }
-      hr = false;
-    }
-    if (hl && hr) {
-      int nearc = tl <= tr ? ch.x : ch.y;
-      int farc = tl <= tr ? ch.y : ch.x;
-      if (sp < 64) stack[sp++] = farc;
-      else atomicOr(status, NEB_STATUS_STACK_OVERFLOW);
-      node = nearc;
-    } else if (hl) {
-      node = ch.x;
-    } else if (hr) {
-      node = ch.y;
-    } else {
-      if (sp == 0) break;
-      node = stack[--sp];
-    }
+  int sp = 0, node = 0;
+  while (!closest_step4(s, r, tmax, node, sp, stack, best_t, best, status, visits, ptests)) {
   }
   t_out = best_t;
   return best;
-}
-
-// Any hit with t in (deltaT, tmax).
-__device__ __forceinline__ bool trace_any(const SceneView& s, const RayPre& r, float tmax, uint32_t* status,
-                                          uint32_t& visits, uint32_t& ptests) {
-  if (s.nt + s.ns == 0) return false;
-  int stack[64];
-  int sp = 0;
-  int node = 0;
-  while (true) {
-    const float4* np = reinterpret_cast<const float4*>(s.nodes + node);
-    float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
-    int4 ch = __ldg(reinterpret_cast<const int4*>(np + 3));
-    ++visits;
-    float tl, tr;
-    bool hl = box_hit(f3(a.x, a.z, c.x), f3(a.y, a.w, c.y), r, tmax, tl);
-    bool hr = box_hit(f3(b.x, b.z, c.z), f3(b.y, b.w, c.w), r, tmax, tr);
-    if (hl && ch.x < 0) {
-      ++ptests;
-      float t = isect_prim(s, r, ~ch.x);
-      if (t > 0.0f && t < tmax) return true;
-      hl = false;
-    }
-    if (hr && ch.y < 0) {
-      ++ptests;
-      float t = isect_prim(s, r, ~ch.y);
-      if (t > 0.0f && t < tmax) return true;
-      hr = false;
-    }
-    if (hl && hr) {
-      if (sp < 64) stack[sp++] = ch.y;
-      else atomicOr(status, NEB_STATUS_STACK_OVERFLOW);
-      node = ch.x;
-    } else if (hl) {
-      node = ch.x;
-    } else if (hr) {
-      node = ch.y;
-    } else {
-      if (sp == 0) break;
-      node = stack[--sp];
-    }
-  }
-  return false;
 }
 
 // Hit point and its floating-point error bound: triangles are rebuilt from

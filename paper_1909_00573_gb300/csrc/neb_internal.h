@@ -120,8 +120,9 @@ struct neb_ctx {
   neb::CameraParams cam{};
   bool scene_ready = false;
 
-  // BVH
-  neb::BVHNode* nodes = nullptr;
+  // BVH (4-wide)
+  neb::BVH4Node* nodes = nullptr;
+  int n_nodes4 = 0;
   bool bvh_ready = false;
 
   // density octree

@@ -259,32 +259,6 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
   }
 }
 
-// Shadow rays of the NEE vertices (any hit, tmax = (1 - 1e-4) dist).
-__global__ void __launch_bounds__(kThreads) k_shadow(SceneView s, NeeStore nv, DevCounters* cnt, int cap_nee) {
-  const int count = min(cnt->nee_count, cap_nee);
-  const int stride = gridDim.x * blockDim.x;
-  for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
-    const int i = base + threadIdx.x;
-    uint32_t visits = 0, ptests = 0, rays = 0;
-    if (i < count) {
-      int bits = __float_as_int(nv.nrm[i].w);
-      if ((bits >> NV_FLAG_SHIFT) & NV_SHADOW) {
-        float4 pp = nv.pos[i], nn = nv.nrm[i], ee = nv.err[i], ld = nv.ldir[i];
-        float3 ldir = xyz(ld);
-        float3 o = offset_origin(xyz(pp), xyz(nn), xyz(ee), ldir);
-        RayPre r = make_ray(o, ldir);
-        rays = 1;
-        if (trace_any(s, r, ee.w * (1.0f - 1e-4f), &cnt->status, visits, ptests)) nv.dE[i] = make_float4(0, 0, 0, 0);
-      }
-    }
-    warp_count(&cnt->shadow_rays, rays);
-    warp_count(&cnt->node_visits, visits);
-    warp_count(&cnt->prim_tests, ptests);
-    warp_count(&cnt->visits_by[1], visits);
-    warp_count(&cnt->ptests_by[1], ptests);
-  }
-}
-
 // ---------------------------------------------------------------------------
 // pass 2: NEE contributions and photon emission from the NEE vertices
 // ---------------------------------------------------------------------------

@@ -19,6 +19,16 @@ struct __align__(16) BVHNode {
   int4 ch;
 };
 
+// BVH4 node, 128 bytes (eight 128-bit loads): per axis the low and high
+// bounds of the four children, then the four child links (>= 0 node index,
+// < 0 ~primitive, kEmptyChild for an unused slot).
+struct __align__(16) BVH4Node {
+  float4 lox, hix, loy, hiy, loz, hiz;
+  int4 ch;
+  float4 pad;
+};
+constexpr int kEmptyChild = (int)0x80000000;
+
 // Octree globals of Appendix B (initialize / set_iteration), device resident.
 struct OctreeParams {
   float minb[3], size_inv[3], scene_scale;
