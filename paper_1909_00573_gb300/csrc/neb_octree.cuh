@@ -227,17 +227,77 @@ __device__ __forceinline__ float oct_density(const int* __restrict__ nodes, cons
   return 0.0f;
 }
 
+// Cell of the leaf (v, mask) reached by a query with integer position ip,
+// offset position off and normal n: returns the count v (0 when empty) and
+// the area denominator max(minArea, A) of get_density's quotient.
+__device__ __forceinline__ int oct_leaf_terms(const OctreeParams& P, int grid, int mask, int v, const int ip[3],
+                                              const float off[3], const float n[3], float* size, float& denom) {
+  denom = 1.0f;
+  if (v <= 0) return 0;
+  int cur = grid / mask;
+  float cmin[3], cmax[3];
+  for (int c = 0; c < 3; ++c) {
+    float csz = 1.0f / ((float)cur * P.size_inv[c]);
+    int cp = ip[c] / mask;
+    cmin[c] = (float)cp * csz;
+    cmax[c] = cmin[c] + csz;
+  }
+  float area = intersection_area(cmin, cmax, off, n);
+  float diag = P.scene_scale / (float)cur;
+  float min_area = diag * diag;
+  if (size) { *size = diag; min_area *= 0.1f; } else min_area *= 0.01f;
+  denom = fmaxf(min_area, area);
+  return v;
+}
+
+// The listing's quotient with its normalisation in FP64, rounded to FP32.
+__device__ __forceinline__ float oct_rho(int v, int iter_clamp, float denom) {
+  if (v <= 0) return 0.0f;
+  return (float)((double)v / ((double)iter_clamp * (double)denom));
+}
+
 // get_density_robust of the listing: median of the centre query and four
 // queries displaced by 1.1 cell diagonals along the tangents of the Duff et
-// al. basis of the geometric normal; ties go to the greater value.
+// al. basis of the geometric normal; ties go to the greater value.  A
+// displaced query walks the same nodes as the centre one down to the first
+// level where its cell coordinates differ, so it resumes from the centre's
+// recorded path there instead of at the root (same nodes, same result).
 __device__ __forceinline__ float oct_density_robust(const int* __restrict__ nodes, const OctreeParams& P, int depth,
                                                     const float pos[3], const float n[3], int* queries) {
-  float d[5];
+  int cv[5] = {0, 0, 0, 0, 0};     // leaf counts of the five queries
+  float cd[5] = {1, 1, 1, 1, 1};   // their area denominators
   float diag = 1e-3f;
-  int count = 0;
-  d[0] = oct_density(nodes, P, depth, pos, n, &diag);
+  const int grid = 1 << depth;
+  // centre query with its path: vs[L] = node value at level L
+  int vs[kOctMaxDepth + 2];
+  int ipc[3];
+  int Lc = -1;
+  {
+    float off[3], np[3];
+    bool in = true;
+    for (int c = 0; c < 3; ++c) {
+      off[c] = pos[c] - P.minb[c];
+      np[c] = off[c] * P.size_inv[c];
+      in = in && (np[c] >= 0.0f && np[c] < 1.0f);
+    }
+    if (in) {
+      for (int c = 0; c < 3; ++c) ipc[c] = (int)(np[c] * (float)grid);
+      int v = __ldg(nodes);
+      int mask = grid;
+      int L = 0;
+      vs[0] = v;
+      while (v < 0) {
+        mask >>= 1;
+        int idx = ((ipc[0] & mask) ? 1 : 0) + ((ipc[1] & mask) ? 2 : 0) + ((ipc[2] & mask) ? 4 : 0);
+        idx -= v;
+        v = __ldg(nodes + idx);
+        vs[++L] = v;
+      }
+      Lc = L;
+      cv[0] = oct_leaf_terms(P, grid, mask, v, ipc, off, n, &diag, cd[0]);
+    }
+  }
   diag *= 1.1f;
-  if (d[0] > 0.0f) ++count;
   float3 t, b;
   onb(f3(n[0], n[1], n[2]), t, b);
   float3 p = f3(pos[0], pos[1], pos[2]);
@@ -245,11 +305,48 @@ __device__ __forceinline__ float oct_density_robust(const int* __restrict__ node
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     float qq[3] = {q[i].x, q[i].y, q[i].z};
-    d[count] = oct_density(nodes, P, depth, qq, n, nullptr);
-    if (d[count] > 0.0f) ++count;
+    float off[3], np[3];
+    bool in = true;
+    for (int c = 0; c < 3; ++c) {
+      off[c] = qq[c] - P.minb[c];
+      np[c] = off[c] * P.size_inv[c];
+      in = in && (np[c] >= 0.0f && np[c] < 1.0f);
+    }
+    if (in) {
+      int ip[3];
+      for (int c = 0; c < 3; ++c) ip[c] = (int)(np[c] * (float)grid);
+      int v, mask, L;
+      if (Lc >= 0) {
+        unsigned diff = (unsigned)((ip[0] ^ ipc[0]) | (ip[1] ^ ipc[1]) | (ip[2] ^ ipc[2]));
+        // first level whose octant differs: mask (grid >> L) equals the top differing bit
+        int Ld = diff ? depth - (31 - __clz(diff)) : depth + 1;
+        L = Ld - 1 < Lc ? Ld - 1 : Lc;
+        v = vs[L];
+        mask = grid >> L;
+      } else {
+        v = __ldg(nodes);
+        mask = grid;
+        L = 0;
+      }
+      while (v < 0) {
+        mask >>= 1;
+        int idx = ((ip[0] & mask) ? 1 : 0) + ((ip[1] & mask) ? 2 : 0) + ((ip[2] & mask) ? 4 : 0);
+        idx -= v;
+        v = __ldg(nodes + idx);
+      }
+      cv[i + 1] = oct_leaf_terms(P, grid, mask, v, ip, off, n, nullptr, cd[i + 1]);
+    }
   }
   *queries += 5;
-  int m = count / 2;
+  // Median of the positive results, ties to the greater: the listing's partial
+  // selection sort over the FP64 quotients rounded to FP32.
+  float d[5];
+  int count = 0;
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+    if (cv[i] > 0) d[count++] = oct_rho(cv[i], P.iter_clamp, cd[i]);
+  if (count == 0) return 0.0f;
+  const int m = count / 2;
   for (int i = 0; i <= m; ++i)
     for (int j = i + 1; j < count; ++j)
       if (d[j] < d[i]) { float tmp = d[i]; d[i] = d[j]; d[j] = tmp; }
