@@ -416,22 +416,20 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
         }
       }
     }
-    // Merge (inverted range search, Sec. 3.2): the warp handles its photon hits
-    // one after another and splits each hit's candidate lists across its 32
-    // lanes, so a hit in a dense cell does not serialise on one lane.
-    unsigned wm = __ballot_sync(0xffffffffu, want_merge);
-    while (wm) {
-      int src = __ffs(wm) - 1;
-      wm &= wm - 1;
-      float3 hp = f3(__shfl_sync(0xffffffffu, m_p.x, src), __shfl_sync(0xffffffffu, m_p.y, src),
-                     __shfl_sync(0xffffffffu, m_p.z, src));
-      float3 md = f3(-__shfl_sync(0xffffffffu, m_d.x, src), -__shfl_sync(0xffffffffu, m_d.y, src),
-                     -__shfl_sync(0xffffffffu, m_d.z, src));
-      float3 phi = f3(__shfl_sync(0xffffffffu, m_phi.x, src), __shfl_sync(0xffffffffu, m_phi.y, src),
-                      __shfl_sync(0xffffffffu, m_phi.z, src));
-      float s1 = __shfl_sync(0xffffffffu, m_s1, src);
-      float gx = (hp.x - ip.gmin.x) * ip.cell_inv, gy = (hp.y - ip.gmin.y) * ip.cell_inv,
-            gz = (hp.z - ip.gmin.z) * ip.cell_inv;
+    // Merge (inverted range search, Sec. 3.2).  Each lane looks up the bucket
+    // ranges of its own hit's eight cells (all loads in flight at once), a
+    // warp scan lays the candidate lists of the 32 hits end to end, and the
+    // lanes take that combined list 32 entries at a time: lane l handles entry
+    // 32 q + l, whose hit and cell it finds by a binary search over the
+    // scanned counts.  A hit in a dense cell is thus spread over the warp and
+    // no hit waits for the lookups of another.
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    int cb[8], cl[8];  // bucket start and length of each cell (0 for a repeated bucket)
+    int nl = 0;
+    if (want_merge) {
+      float gx = (m_p.x - ip.gmin.x) * ip.cell_inv, gy = (m_p.y - ip.gmin.y) * ip.cell_inv,
+            gz = (m_p.z - ip.gmin.z) * ip.cell_inv;
       int cx = (int)floorf(gx), cy = (int)floorf(gy), cz = (int)floorf(gz);
       int ox = (gx - (float)cx >= 0.5f) ? 1 : -1, oy = (gy - (float)cy >= 0.5f) ? 1 : -1,
           oz = (gz - (float)cz >= 0.5f) ? 1 : -1;
@@ -440,34 +438,72 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
       for (int c = 0; c < 8; ++c)
         bk[c] = grid_hash(cx + ((c & 1) ? ox : 0), cy + ((c & 2) ? oy : 0), cz + ((c & 4) ? oz : 0),
                           ip.table_mask);
+#pragma unroll
       for (int c = 0; c < 8; ++c) {
         bool dup = false;
+#pragma unroll
         for (int c2 = 0; c2 < c; ++c2) dup |= bk[c2] == bk[c];
-        if (dup) continue;
         int b0 = __ldg(bucket_start + bk[c]), b1 = __ldg(bucket_start + bk[c] + 1);
-        for (int e = b0 + (int)(threadIdx.x & 31); e < b1; e += 32) {
-          float4 mp = __ldg(&mrec[e].pos);
-          float dx = mp.x - hp.x, dy = mp.y - hp.y, dz = mp.z - hp.z;
-          float d2 = dx * dx + dy * dy + dz * dz;
-          ++tests;
-          if (!(d2 <= ip.r2)) continue;
-          float4 mn = __ldg(&mrec[e].nrm);
-          int mb = __float_as_int(mn.w);
-          int kk = (mb >> NV_K_SHIFT) & 63;
-          if (kk + j + 1 > ip.D) continue;
-          Mat cm = load_mat(s.mats, mb & NV_MAT_MASK);
-          float4 mw = __ldg(&mrec[e].wo);
-          float3 cn = xyz(mn), cwo = xyz(mw);
-          float3 f = bsdf_eval(cm, cn, cwo, md);
-          if (!(maxc(f) > 0.0f)) continue;
-          float pdfF = bsdf_pdf(cm, cn, cwo, md), pdfC = bsdf_pdf(cm, cn, md, cwo);
-          float inv_w = 1.0f + pdfF * s1 + pdfC * mp.w;
-          float3 ctau = xyz(__ldg(&mrec[e].tau));
-          float3 L = mul(cmul(cmul(ctau, f), phi), ip.kernel / inv_w);
-          add_pixel(accum, split, 2, __float_as_int(mw.w), L, P);
-          ++merges;
+        cb[c] = b0;
+        cl[c] = dup ? 0 : b1 - b0;
+        nl += cl[c];
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) cb[c] = cl[c] = 0;
+    }
+    int incl = nl;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    for (int q0 = 0; q0 < total; q0 += 32) {
+      const int q = q0 + lane;
+      // owner = number of lanes whose inclusive count is <= q
+      int L = 0;
+#pragma unroll
+      for (int st = 16; st > 0; st >>= 1) {
+        int v = __shfl_sync(FULL, incl, L + st - 1);
+        if (v <= q) L += st;
+      }
+      L = L < 31 ? L : 31;
+      int u = q - (__shfl_sync(FULL, incl, L) - __shfl_sync(FULL, nl, L));
+      int e = -1;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        int len = __shfl_sync(FULL, cl[c], L), start = __shfl_sync(FULL, cb[c], L);
+        if (e < 0) {
+          if (u < len) e = start + u;
+          else u -= len;
         }
       }
+      float3 hp = f3(__shfl_sync(FULL, m_p.x, L), __shfl_sync(FULL, m_p.y, L), __shfl_sync(FULL, m_p.z, L));
+      float3 md = f3(-__shfl_sync(FULL, m_d.x, L), -__shfl_sync(FULL, m_d.y, L), -__shfl_sync(FULL, m_d.z, L));
+      float3 phi = f3(__shfl_sync(FULL, m_phi.x, L), __shfl_sync(FULL, m_phi.y, L), __shfl_sync(FULL, m_phi.z, L));
+      float s1 = __shfl_sync(FULL, m_s1, L);
+      if (q >= total || e < 0) continue;
+      float4 mp = __ldg(&mrec[e].pos);
+      float dx = mp.x - hp.x, dy = mp.y - hp.y, dz = mp.z - hp.z;
+      float d2 = dx * dx + dy * dy + dz * dz;
+      ++tests;
+      if (!(d2 <= ip.r2)) continue;
+      float4 mn = __ldg(&mrec[e].nrm);
+      int mb = __float_as_int(mn.w);
+      int kk = (mb >> NV_K_SHIFT) & 63;
+      if (kk + j + 1 > ip.D) continue;
+      Mat cm = load_mat(s.mats, mb & NV_MAT_MASK);
+      float4 mw = __ldg(&mrec[e].wo);
+      float3 cn = xyz(mn), cwo = xyz(mw);
+      float3 f = bsdf_eval(cm, cn, cwo, md);
+      if (!(maxc(f) > 0.0f)) continue;
+      float pdfF = bsdf_pdf(cm, cn, cwo, md), pdfC = bsdf_pdf(cm, cn, md, cwo);
+      float inv_w = 1.0f + pdfF * s1 + pdfC * mp.w;
+      float3 ctau = xyz(__ldg(&mrec[e].tau));
+      float3 L3 = mul(cmul(cmul(ctau, f), phi), ip.kernel / inv_w);
+      add_pixel(accum, split, 2, __float_as_int(mw.w), L3, P);
+      ++merges;
     }
     int slot = warp_append(&cnt->ph_count[out_slot], emit, ip.cap_ph, &cnt->status);
     if (emit && slot >= 0) out[slot] = nph;
