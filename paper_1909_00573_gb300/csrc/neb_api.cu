@@ -109,26 +109,34 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
   c->table_size = t;
   c->scan_scratch.n = scan_scratch_ints((size_t)t + 1);
   bool ok = dalloc(&c->camq[0], P) == cudaSuccess && dalloc(&c->camq[1], P) == cudaSuccess &&
-            dalloc(&c->nv.pos, c->cap_nee) == cudaSuccess && dalloc(&c->nv.nrm, c->cap_nee) == cudaSuccess &&
-            dalloc(&c->nv.wo, c->cap_nee) == cudaSuccess && dalloc(&c->nv.tau, c->cap_nee) == cudaSuccess &&
-            dalloc(&c->nv.err, c->cap_nee) == cudaSuccess && dalloc(&c->nv.ldir, c->cap_nee) == cudaSuccess &&
-            dalloc(&c->nv.dE, c->cap_nee) == cudaSuccess && dalloc(&c->rh, c->cap_rh) == cudaSuccess &&
-            dalloc(&c->phq[0], c->cap_ph) == cudaSuccess && dalloc(&c->phq[1], c->cap_ph) == cudaSuccess &&
-            dalloc(&c->hits, (size_t)(c->cap_ph > c->cap_cam ? c->cap_ph : c->cap_cam)) == cudaSuccess &&
-            dalloc(&c->mrec, c->cap_nee) == cudaSuccess && dalloc(&c->vert_bucket, c->cap_nee) == cudaSuccess &&
-            dalloc(&c->bucket_count, (size_t)t + 1) == cudaSuccess &&
-            dalloc(&c->bucket_start, (size_t)t + 1) == cudaSuccess &&
-            dalloc(&c->scan_scratch.data, c->scan_scratch.n) == cudaSuccess &&
-            dalloc(&c->accum, P * 3) == cudaSuccess && dalloc(&c->counters, 1) == cudaSuccess &&
-            (!cfg->keep_split || dalloc(&c->split, P * 9) == cudaSuccess) &&
-            (cfg->octree_mode != 1 || dalloc(&c->slot_map, P * (D > 1 ? D - 1 : 1)) == cudaSuccess);
+            dalloc(&c->counters, 2) == cudaSuccess;
+  for (int k = 0; k < 2 && ok; ++k) {
+    IterSlot& sl = c->slots[k];
+    sl.cnt = c->counters + k;
+    ok = dalloc(&sl.nv.pos, c->cap_nee) == cudaSuccess && dalloc(&sl.nv.nrm, c->cap_nee) == cudaSuccess &&
+         dalloc(&sl.nv.wo, c->cap_nee) == cudaSuccess && dalloc(&sl.nv.tau, c->cap_nee) == cudaSuccess &&
+         dalloc(&sl.nv.err, c->cap_nee) == cudaSuccess && dalloc(&sl.nv.ldir, c->cap_nee) == cudaSuccess &&
+         dalloc(&sl.nv.dE, c->cap_nee) == cudaSuccess && dalloc(&sl.rh, c->cap_rh) == cudaSuccess &&
+         (cfg->octree_mode != 1 || dalloc(&sl.slot_map, P * (D > 1 ? D - 1 : 1)) == cudaSuccess);
+  }
+  ok = ok && dalloc(&c->phq[0], c->cap_ph) == cudaSuccess && dalloc(&c->phq[1], c->cap_ph) == cudaSuccess &&
+       dalloc(&c->hits, (size_t)c->cap_cam) == cudaSuccess && dalloc(&c->hits_ph, (size_t)c->cap_ph) == cudaSuccess &&
+       dalloc(&c->mrec, c->cap_nee) == cudaSuccess && dalloc(&c->vert_bucket, c->cap_nee) == cudaSuccess &&
+       dalloc(&c->bucket_count, (size_t)t + 1) == cudaSuccess &&
+       dalloc(&c->bucket_start, (size_t)t + 1) == cudaSuccess &&
+       dalloc(&c->scan_scratch.data, c->scan_scratch.n) == cudaSuccess && dalloc(&c->accum, P * 3) == cudaSuccess &&
+       (!cfg->keep_split || dalloc(&c->split, P * 9) == cudaSuccess);
+  ok = ok && cudaStreamCreateWithFlags(&c->stream_b, cudaStreamNonBlocking) == cudaSuccess;
+  for (int k = 0; k < 2 && ok; ++k)
+    ok = cudaEventCreateWithFlags(&c->ev_pass1[k], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_pass23[k], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     neb_destroy(c);
     return NEB_ERR_OOM;
   }
   cudaMemsetAsync(c->bucket_count, 0, sizeof(int) * ((size_t)t + 1), c->stream);
   cudaMemsetAsync(c->accum, 0, sizeof(double) * P * 3, c->stream);
-  cudaMemsetAsync(c->counters, 0, sizeof(DevCounters), c->stream);
+  cudaMemsetAsync(c->counters, 0, 2 * sizeof(DevCounters), c->stream);
   if (c->split) cudaMemsetAsync(c->split, 0, sizeof(double) * P * 9, c->stream);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
@@ -144,13 +152,21 @@ extern "C" void neb_destroy(neb_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   free_scene(c);
   cudaFree(c->camq[0]); cudaFree(c->camq[1]);
-  cudaFree(c->nv.pos); cudaFree(c->nv.nrm); cudaFree(c->nv.wo); cudaFree(c->nv.tau); cudaFree(c->nv.err);
-  cudaFree(c->nv.ldir); cudaFree(c->nv.dE);
-  cudaFree(c->rh); cudaFree(c->phq[0]); cudaFree(c->phq[1]); cudaFree(c->hits); cudaFree(c->mrec); cudaFree(c->vert_bucket);
-  cudaFree(c->bucket_count); cudaFree(c->bucket_start); cudaFree(c->scan_scratch.data); cudaFree(c->accum);
-  cudaFree(c->split); cudaFree(c->counters); cudaFree(c->slot_map);
+  if (c->stream_b) cudaStreamSynchronize(c->stream_b);
+  for (IterSlot& sl : c->slots) {
+    cudaFree(sl.nv.pos); cudaFree(sl.nv.nrm); cudaFree(sl.nv.wo); cudaFree(sl.nv.tau); cudaFree(sl.nv.err);
+    cudaFree(sl.nv.ldir); cudaFree(sl.nv.dE); cudaFree(sl.rh); cudaFree(sl.slot_map);
+  }
+  cudaFree(c->phq[0]); cudaFree(c->phq[1]); cudaFree(c->hits); cudaFree(c->hits_ph); cudaFree(c->mrec);
+  cudaFree(c->vert_bucket); cudaFree(c->bucket_count); cudaFree(c->bucket_start); cudaFree(c->scan_scratch.data);
+  cudaFree(c->accum); cudaFree(c->split); cudaFree(c->counters);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
+  for (int k = 0; k < 2; ++k) {
+    if (c->ev_pass1[k]) cudaEventDestroy(c->ev_pass1[k]);
+    if (c->ev_pass23[k]) cudaEventDestroy(c->ev_pass23[k]);
+  }
+  if (c->stream_b) cudaStreamDestroy(c->stream_b);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -323,7 +339,7 @@ extern "C" int neb_scene_upload(neb_ctx* c, const float* tri, const uint32_t* tr
   cudaMemsetAsync(c->oct_nodes, 0, sizeof(int) * (size_t)c->oct_cap, st);
   cudaMemcpyAsync(c->oct_state, &s0, sizeof(s0), cudaMemcpyHostToDevice, st);
   cudaMemsetAsync(c->accum, 0, sizeof(double) * 3 * (size_t)c->P, st);
-  cudaMemsetAsync(c->counters, 0, sizeof(DevCounters), st);
+  cudaMemsetAsync(c->counters, 0, 2 * sizeof(DevCounters), st);
   c->iteration = 0;
   c->launches = 0;
   cudaError_t e = cudaStreamSynchronize(st);
@@ -344,10 +360,19 @@ extern "C" int neb_build_bvh(neb_ctx* c) {
 extern "C" int neb_iterate(neb_ctx* c, int n_iterations) {
   if (!c || n_iterations < 0) return NEB_ERR_ARG;
   if (!c->bvh_ready) return fail(c, NEB_ERR_ARG, "neb_iterate: call neb_scene_upload and neb_build_bvh first");
+  // Passes 2-3 of an iteration overlap pass 1 of the next one (two streams,
+  // two buffer slots); stage timing keeps everything on one stream.  The
+  // caller's stream waits for the last iteration before the call returns, so
+  // work enqueued on it afterwards sees every result.
+  const bool overlap = !c->profiling;
   for (int i = 0; i < n_iterations; ++i) {
-    cudaError_t e = run_iteration(c, c->iteration + 1);
+    cudaError_t e = run_iteration(c, c->iteration + 1, overlap);
     if (e != cudaSuccess) return fail(c, NEB_ERR_CUDA, "neb_iterate", e);
     c->iteration += 1;
+  }
+  if (overlap && n_iterations > 0) {
+    cudaError_t e = cudaStreamWaitEvent(c->stream, c->ev_pass23[c->iteration & 1], 0);
+    if (e != cudaSuccess) return fail(c, NEB_ERR_CUDA, "neb_iterate", e);
   }
   return NEB_OK;
 }
@@ -400,12 +425,32 @@ extern "C" int neb_read_nee_rho(neb_ctx* c, float* out) {
 
 extern "C" int neb_get_stats(neb_ctx* c, neb_stats* out) {
   if (!c || !out) return NEB_ERR_ARG;
-  DevCounters h;
+  DevCounters hs[2];
   OctreeState os{};
-  cudaMemcpyAsync(&h, c->counters, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+  cudaMemcpyAsync(hs, c->counters, sizeof(hs), cudaMemcpyDeviceToHost, c->stream);
   if (c->oct_state) cudaMemcpyAsync(&os, c->oct_state, sizeof(os), cudaMemcpyDeviceToHost, c->stream);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return fail(c, NEB_ERR_CUDA, "neb_get_stats", e);
+  // the two slots' counters together cover every iteration
+  DevCounters h = hs[0];
+  const DevCounters& h1 = hs[1];
+  h.status |= h1.status;
+  h.camera_rays += h1.camera_rays;
+  h.nee_vertices += h1.nee_vertices;
+  h.shadow_rays += h1.shadow_rays;
+  h.photons += h1.photons;
+  h.photon_hits += h1.photon_hits;
+  h.merge_tests += h1.merge_tests;
+  h.merges += h1.merges;
+  h.random_hits += h1.random_hits;
+  h.octree_inserts += h1.octree_inserts;
+  h.octree_queries += h1.octree_queries;
+  h.node_visits += h1.node_visits;
+  h.prim_tests += h1.prim_tests;
+  for (int i = 0; i < 3; ++i) {
+    h.visits_by[i] += h1.visits_by[i];
+    h.ptests_by[i] += h1.ptests_by[i];
+  }
   memset(out, 0, sizeof(*out));
   out->iterations = c->iteration;
   out->camera_rays = (int64_t)h.camera_rays;

@@ -75,6 +75,16 @@ struct DevCounters {
   int fetch[4];                                   // dynamic-fetch counters of the traversal kernels
 };
 
+// Buffers that pass 1 of an iteration fills and passes 2 and 3 read.  There
+// are two sets, used by odd and even iterations, so pass 1 of iteration i + 1
+// can run on one stream while passes 2 and 3 of iteration i finish on another.
+struct IterSlot {
+  NeeStore nv{};
+  RHEvent* rh = nullptr;
+  int* slot_map = nullptr;   // deterministic octree mode: NEE id per (pixel, k)
+  DevCounters* cnt = nullptr;
+};
+
 struct CameraParams {
   float3 eye, fwd, right, up;
   float tanh_, aspect;
@@ -134,21 +144,24 @@ struct neb_ctx {
 
   // per-iteration buffers
   neb::CamRay* camq[2] = {nullptr, nullptr};
-  neb::NeeStore nv{};
-  neb::RHEvent* rh = nullptr;
+  neb::IterSlot slots[2];
   neb::PhotonRay* phq[2] = {nullptr, nullptr};
-  int2* hits = nullptr;  // closest hits of the current ray queue
+  int2* hits = nullptr;     // closest hits of the camera ray queue (pass 1)
+  int2* hits_ph = nullptr;  // closest hits of the photon ray queue (pass 3)
   neb::MergeRec* mrec = nullptr;
   int* vert_bucket = nullptr;
   int* bucket_count = nullptr;
   int* bucket_start = nullptr;
-  int* slot_map = nullptr;
   int cap_cam = 0, cap_nee = 0, cap_rh = 0, cap_ph = 0;
   uint32_t table_size = 0;
   neb::Scratch scan_scratch;
   double* accum = nullptr;
   double* split = nullptr;
-  neb::DevCounters* counters = nullptr;
+  neb::DevCounters* counters = nullptr;  // two sets, one per slot
+  // passes 2-3 run on stream_b, overlapped with the next iteration's pass 1
+  // on `stream`; ev_pass1[s] / ev_pass23[s] mark the end of each half for slot s
+  cudaStream_t stream_b = nullptr;
+  cudaEvent_t ev_pass1[2] = {nullptr, nullptr}, ev_pass23[2] = {nullptr, nullptr};
   int iteration = 0;  // iterations completed (enqueued)
   long long launches = 0;  // kernels enqueued by neb_iterate
 
@@ -176,7 +189,7 @@ cudaError_t launch_area(const float* d_boxes, const float* d_pos, const float* d
 size_t scan_scratch_ints(size_t n);
 int scan_launch_count(size_t n);
 cudaError_t scan_exclusive(const int* d_in, int* d_out, size_t n, Scratch& scratch, cudaStream_t st);
-cudaError_t grid_build(neb_ctx* c, const IterParams& ip);
+cudaError_t grid_build(neb_ctx* c, const IterParams& ip, const IterSlot& sl, cudaStream_t st);
 cudaError_t count_neighbours_device(const float* d_pts, int n, const float* d_q, int m, float r, int* d_out,
                                     cudaStream_t st);
 
@@ -189,16 +202,17 @@ cudaError_t launch_oct_insert_points(int* nodes, OctreeState* st, const OctreePa
 cudaError_t launch_oct_density_points(const int* nodes, const OctreeState* st, const OctreeParams& P,
                                       const float* d_pos, const float* d_nrm, int n, int robust, float* d_out,
                                       cudaStream_t s);
-cudaError_t launch_oct_insert_nee(neb_ctx* c);
-cudaError_t launch_oct_density_nee(neb_ctx* c);
+cudaError_t launch_oct_insert_nee(neb_ctx* c, const IterSlot& sl, cudaStream_t st);
+cudaError_t launch_oct_density_nee(neb_ctx* c, const IterSlot& sl, cudaStream_t st);
 
 // neb_trace.cu
 cudaError_t launch_trace_closest(neb_ctx* c, const float4* recs, const int* count_ptr, int cap, int2* hits,
-                                 int which);
-cudaError_t launch_trace_shadow(neb_ctx* c);
+                                 int which, DevCounters* cnt, cudaStream_t st);
+cudaError_t launch_trace_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st);
 
 // neb_pass.cu
-cudaError_t run_iteration(neb_ctx* c, int iteration);
+// overlap: passes 2-3 go to stream_b (ordered by the slot events), else all on c->stream
+cudaError_t run_iteration(neb_ctx* c, int iteration, bool overlap);
 cudaError_t launch_resolve(const double* accum, int P, int iterations, float* out, cudaStream_t st);
 cudaError_t launch_read_rho(neb_ctx* c, float* d_out);
 

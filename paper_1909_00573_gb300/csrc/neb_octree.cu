@@ -188,20 +188,19 @@ cudaError_t launch_oct_density_points(const int* nodes, const OctreeState* st, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_oct_insert_nee(neb_ctx* c) {
+cudaError_t launch_oct_insert_nee(neb_ctx* c, const IterSlot& sl, cudaStream_t st) {
   if (c->cfg.octree_mode == 1)
-    k_oct_insert_nee_seq<<<1, 1, 0, c->stream>>>(c->oct_nodes, c->oct_state, c->oct, c->nv.pos, c->slot_map,
-                                                 c->P * (c->D - 1), c->counters);
+    k_oct_insert_nee_seq<<<1, 1, 0, st>>>(c->oct_nodes, c->oct_state, c->oct, sl.nv.pos, sl.slot_map,
+                                          c->P * (c->D - 1), sl.cnt);
   else
-    k_oct_insert_nee<<<152 * 8, 256, 0, c->stream>>>(c->oct_nodes, c->oct_state, c->oct, c->nv.pos, c->counters,
-                                                     c->cap_nee, kSpinLimit);
+    k_oct_insert_nee<<<152 * 8, 256, 0, st>>>(c->oct_nodes, c->oct_state, c->oct, sl.nv.pos, sl.cnt, c->cap_nee,
+                                              kSpinLimit);
   return cudaGetLastError();
 }
 
-cudaError_t launch_oct_density_nee(neb_ctx* c) {
-  k_oct_density_nee<<<152 * 8, 256, 0, c->stream>>>(c->oct_nodes, c->oct_state, c->oct, c->nv.pos, c->nv.nrm,
-                                                    c->nv.ldir, c->counters, c->cap_nee,
-                                                    c->cfg.density_mode == 0);
+cudaError_t launch_oct_density_nee(neb_ctx* c, const IterSlot& sl, cudaStream_t st) {
+  k_oct_density_nee<<<152 * 8, 256, 0, st>>>(c->oct_nodes, c->oct_state, c->oct, sl.nv.pos, sl.nv.nrm, sl.nv.ldir,
+                                             sl.cnt, c->cap_nee, c->cfg.density_mode == 0);
   return cudaGetLastError();
 }
 

@@ -588,83 +588,98 @@ IterParams iter_params(const neb_ctx* c, int iteration) {
   return ip;
 }
 
-cudaError_t run_iteration(neb_ctx* c, int iteration) {
+cudaError_t run_iteration(neb_ctx* c, int iteration, bool overlap) {
   const int B = grid_blocks();
   SceneView s = scene_view(c);
   IterParams ip = iter_params(c, iteration);
+  const int slot = iteration & 1;
+  IterSlot& sl = c->slots[slot];
+  DevCounters* cnt = sl.cnt;
+  // pass 1 on the caller's stream; passes 2-3 on stream_b when overlapped
   cudaStream_t st = c->stream;
-  StageTimer tm(c);
+  cudaStream_t st2 = overlap ? c->stream_b : c->stream;
+  StageTimer tm(c);  // profiling runs never overlap, so every stage is on c->stream
   double* split = c->cfg.keep_split ? c->split : nullptr;
-
-  // octree set_iteration (Appendix B): host-side scalars, device re-arm
-  octree_set_iteration_params(c->oct, c->cfg.split_factor, iteration);
   long long launches = 0;
-  tm.begin(STAGE_REARM);
-  k_begin<<<1, 1, 0, st>>>(c->counters);
-  if (split) cudaMemsetAsync(c->split, 0, sizeof(double) * 9 * (size_t)c->P, st);
-  if (c->slot_map) cudaMemsetAsync(c->slot_map, 0xff, sizeof(int) * (size_t)c->P * (c->D - 1), st);
-  launch_oct_rearm(c->oct_nodes, c->oct_state, c->oct, st);
-  launches += 2;
-  tm.end();
 
-  // pass 1
+  // ---- pass 1: view paths, NEE samples and shadow rays into slot `slot`
+  // (its previous user, iteration - 2, must have finished passes 2-3)
+  if (overlap) cudaStreamWaitEvent(st, c->ev_pass23[slot], 0);
+  tm.begin(STAGE_REARM);
+  k_begin<<<1, 1, 0, st>>>(cnt);
+  if (sl.slot_map) cudaMemsetAsync(sl.slot_map, 0xff, sizeof(int) * (size_t)c->P * (c->D - 1), st);
+  launches += 1;
+  tm.end();
   tm.begin(STAGE_CAMERA);
-  k_camera<<<B, kThreads, 0, st>>>(ip, c->cam, c->camq[0], c->counters);
+  k_camera<<<B, kThreads, 0, st>>>(ip, c->cam, c->camq[0], cnt);
   launches += 1;
   tm.end();
   for (int k = 1; k <= c->D; ++k) {
     int in = (k - 1) & 1, out = k & 1;
-    k_reset_cam_slot<<<1, 1, 0, st>>>(c->counters, out);
+    k_reset_cam_slot<<<1, 1, 0, st>>>(cnt, out);
     tm.begin(STAGE_TRACE_CAM);
-    launch_trace_closest(c, reinterpret_cast<const float4*>(c->camq[in]), &c->counters->cam_count[in], c->cap_cam,
-                         c->hits, 0);
+    launch_trace_closest(c, reinterpret_cast<const float4*>(c->camq[in]), &cnt->cam_count[in], c->cap_cam, c->hits,
+                         0, cnt, st);
     tm.end();
     tm.begin(STAGE_EXTEND);
-    k_extend<<<B, kThreads, 0, st>>>(s, ip, k, c->camq[in], in, c->camq[out], out, c->nv, c->rh, c->counters,
-                                     c->slot_map, c->hits);
+    k_extend<<<B, kThreads, 0, st>>>(s, ip, k, c->camq[in], in, c->camq[out], out, sl.nv, sl.rh, cnt, sl.slot_map,
+                                     c->hits);
     launches += 3;
     tm.end();
   }
   tm.begin(STAGE_SHADOW);
-  launch_trace_shadow(c);
+  launch_trace_shadow(c, sl, st);
+  launches += 1;
   tm.end();
+  if (overlap) {
+    cudaEventRecord(c->ev_pass1[slot], st);
+    cudaStreamWaitEvent(st2, c->ev_pass1[slot], 0);
+  }
+
+  // ---- pass 2: octree set_iteration (Appendix B: host-side scalars, device
+  // re-arm), inserts of this iteration's NEE vertices, densities, NEE
+  // contributions and photon emission
+  octree_set_iteration_params(c->oct, c->cfg.split_factor, iteration);
   tm.begin(STAGE_INSERT);
-  launch_oct_insert_nee(c);
+  if (split) cudaMemsetAsync(c->split, 0, sizeof(double) * 9 * (size_t)c->P, st2);
+  launch_oct_rearm(c->oct_nodes, c->oct_state, c->oct, st2);
+  launch_oct_insert_nee(c, sl, st2);
+  launches += 2;
   tm.end();
-  // pass 2
   tm.begin(STAGE_DENSITY);
-  launch_oct_density_nee(c);
+  launch_oct_density_nee(c, sl, st2);
   tm.end();
   tm.begin(STAGE_NEE);
-  k_nee<<<B, kThreads, 0, st>>>(s, ip, c->nv, c->counters, c->accum, split, c->phq[0]);
+  k_nee<<<B, kThreads, 0, st2>>>(s, ip, sl.nv, cnt, c->accum, split, c->phq[0]);
   tm.end();
-  launches += 4;
+  launches += 2;
   if ((ip.mask & 4u) && c->D >= 3) {
     tm.begin(STAGE_GRID);
-    grid_build(c, ip);
+    grid_build(c, ip, sl, st2);
     launches += 2 + scan_launch_count((size_t)c->table_size + 1);
     tm.end();
   }
-  // pass 3 (independent of the photons; enqueued here)
+  // ---- pass 3: deferred random hits, photon walks and merges
   tm.begin(STAGE_EMISSION);
-  k_emission<<<B, kThreads, 0, st>>>(s, ip, c->nv, c->rh, c->counters, c->accum, split);
+  k_emission<<<B, kThreads, 0, st2>>>(s, ip, sl.nv, sl.rh, cnt, c->accum, split);
   launches += 1;
   tm.end();
   if ((ip.mask & 4u) && c->D >= 3) {
     for (int j = 1; j <= c->D - 2; ++j) {
       int in = (j - 1) & 1, out = j & 1;
-      k_reset_photon_slot<<<1, 1, 0, st>>>(c->counters, out);
+      k_reset_photon_slot<<<1, 1, 0, st2>>>(cnt, out);
       tm.begin(STAGE_TRACE_PHOTON);
-      launch_trace_closest(c, reinterpret_cast<const float4*>(c->phq[in]), &c->counters->ph_count[in], c->cap_ph,
-                           c->hits, 2);
+      launch_trace_closest(c, reinterpret_cast<const float4*>(c->phq[in]), &cnt->ph_count[in], c->cap_ph,
+                           c->hits_ph, 2, cnt, st2);
       tm.end();
       tm.begin(STAGE_PHOTON);
-      k_photon<<<B, kThreads, 0, st>>>(s, ip, j, c->phq[in], in, c->phq[out], out, c->mrec, c->bucket_start,
-                                       c->counters, c->accum, split, c->hits);
+      k_photon<<<B, kThreads, 0, st2>>>(s, ip, j, c->phq[in], in, c->phq[out], out, c->mrec, c->bucket_start, cnt,
+                                        c->accum, split, c->hits_ph);
       launches += 3;
       tm.end();
     }
   }
+  if (overlap) cudaEventRecord(c->ev_pass23[slot], st2);
   c->launches += launches;
   cudaError_t e = cudaGetLastError();
   tm.collect();
@@ -679,8 +694,9 @@ cudaError_t launch_resolve(const double* accum, int P, int iterations, float* ou
 }
 
 cudaError_t launch_read_rho(neb_ctx* c, float* d_out) {
+  const IterSlot& sl = c->slots[c->iteration & 1];  // slot of the last iteration
   k_fill<<<grid_blocks(), 256, 0, c->stream>>>(d_out, (size_t)c->P * (c->D - 1), -1.0f);  // no NEE vertex
-  k_read_rho<<<grid_blocks(), 256, 0, c->stream>>>(c->nv, c->counters, c->D, c->cap_nee, d_out);
+  k_read_rho<<<grid_blocks(), 256, 0, c->stream>>>(sl.nv, sl.cnt, c->D, c->cap_nee, d_out);
   return cudaGetLastError();
 }
 

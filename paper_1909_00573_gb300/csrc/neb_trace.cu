@@ -204,19 +204,18 @@ static int trace_blocks() {
 }
 
 cudaError_t launch_trace_closest(neb_ctx* c, const float4* recs, const int* count_ptr, int cap, int2* hits,
-                                 int which) {
-  int* fetch = &c->counters->fetch[which];
-  cudaMemsetAsync(fetch, 0, sizeof(int), c->stream);
-  k_trace_closest<<<trace_blocks(), kTraceThreads, 0, c->stream>>>(scene_view(c), recs, count_ptr, cap, fetch, hits,
-                                                                   c->counters, which);
+                                 int which, DevCounters* cnt, cudaStream_t st) {
+  int* fetch = &cnt->fetch[which];
+  cudaMemsetAsync(fetch, 0, sizeof(int), st);
+  k_trace_closest<<<trace_blocks(), kTraceThreads, 0, st>>>(scene_view(c), recs, count_ptr, cap, fetch, hits, cnt,
+                                                            which);
   return cudaGetLastError();
 }
 
-cudaError_t launch_trace_shadow(neb_ctx* c) {
-  int* fetch = &c->counters->fetch[1];
-  cudaMemsetAsync(fetch, 0, sizeof(int), c->stream);
-  k_trace_shadow<<<trace_blocks(), kTraceThreads, 0, c->stream>>>(scene_view(c), c->nv, c->cap_nee, fetch,
-                                                                  c->counters);
+cudaError_t launch_trace_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st) {
+  int* fetch = &sl.cnt->fetch[1];
+  cudaMemsetAsync(fetch, 0, sizeof(int), st);
+  k_trace_shadow<<<trace_blocks(), kTraceThreads, 0, st>>>(scene_view(c), sl.nv, c->cap_nee, fetch, sl.cnt);
   return cudaGetLastError();
 }
 

@@ -243,6 +243,34 @@ def test_tiny_room_per_path_parity(neb, oracle):
         abs(st["nee_vertices"] - ref["stats"]["nee_vertices"]) <= 2
 
 
+def test_overlapped_iterations_equal_sequential(neb):
+    """Passes 2-3 of iteration i overlap pass 1 of iteration i + 1 on a second
+    stream (two buffer slots).  With the deterministic octree, that schedule
+    must give the same results as running every stage in order on one stream
+    (stage timing forces the latter): identical densities and counters, and
+    FP64 sums equal up to the order of the atomic additions."""
+    from paper_1909_00573_gb300 import scenes
+    s, rc = scenes.workload("tiny_room")
+    rc.octree_mode = 1
+    out = []
+    for sequential in (False, True):
+        ctx = neb.Context(neb.make_config(rc, keep_split=True))
+        ctx.scene_upload(s)
+        ctx.build_bvh()
+        ctx.set_profiling(sequential)
+        ctx.iterate(rc.iterations)
+        out.append((ctx.read_nee_rho(), ctx.read_split(), ctx.read_accum(), ctx.stats()))
+        ctx.close()
+    (r0, sp0, a0, st0), (r1, sp1, a1, st1) = out
+    assert np.array_equal(r0, r1)
+    for key in ("camera_rays", "nee_vertices", "shadow_rays", "photons", "photon_hits", "merge_tests", "merges",
+                "random_hits", "octree_inserts", "octree_queries", "octree_nodes", "iterations"):
+        assert st0[key] == st1[key], key
+    np.testing.assert_allclose(sp0, sp1, rtol=1e-12, atol=1e-12 * float(np.abs(sp1).max()))
+    np.testing.assert_allclose(a0, a1, rtol=1e-12, atol=1e-12 * float(np.abs(a1).max()))
+    assert a0.sum() > 0
+
+
 def test_ragged_small_image_parity(neb, oracle):
     """Odd image size (a ragged last block), D = 3 (one photon bounce)."""
     from paper_1909_00573_gb300 import scenes
