@@ -235,6 +235,7 @@ struct RayPre {
   float3 o, d, inv;
   int kx, ky, kz;
   float Sx, Sy, Sz;
+  int oct;  // bit a set when direction component a has its sign bit set
 };
 
 __device__ __forceinline__ RayPre make_ray(float3 o, float3 d) {
@@ -242,6 +243,7 @@ __device__ __forceinline__ RayPre make_ray(float3 o, float3 d) {
   r.o = o;
   r.d = d;
   r.inv = f3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+  r.oct = (signbit(d.x) ? 1 : 0) | (signbit(d.y) ? 2 : 0) | (signbit(d.z) ? 4 : 0);
   float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
   int kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
   int kx = kz == 2 ? 0 : kz + 1;
@@ -379,28 +381,44 @@ __device__ __forceinline__ float isect_prim(const SceneView& s, const RayPre& r,
 }
 
 // ---- BVH4 traversal --------------------------------------------------------------
-struct Node4 {
-  float4 lox, hix, loy, hiy, loz, hiz;
+// A 4-wide node keeps, per axis, the low and the high bounds of its four
+// children in one float4 each.  On axis a the entry plane of every child is
+// its low bound when the ray's direction component is positive and its high
+// bound when it is negative, so the walk loads the entry and exit planes
+// directly by the ray's octant and needs no per-child compare and swap.  The
+// slab distances are those of box_hit: the decisions are the same for every
+// non-zero direction component (a zero component gives NaN planes, which
+// both forms ignore).
+struct Node4Oct {
+  float4 nx, fx, ny, fy, nz, fz;  // entry / exit planes per axis, children 0-3
   int4 ch;
 };
-__device__ __forceinline__ Node4 load_node4(const BVH4Node* __restrict__ nodes, int i) {
+__device__ __forceinline__ Node4Oct load_node4_oct(const BVH4Node* __restrict__ nodes, int i, int oct) {
   const float4* p = reinterpret_cast<const float4*>(nodes + i);
-  Node4 n;
-  n.lox = __ldg(p);
-  n.hix = __ldg(p + 1);
-  n.loy = __ldg(p + 2);
-  n.hiy = __ldg(p + 3);
-  n.loz = __ldg(p + 4);
-  n.hiz = __ldg(p + 5);
+  const int ox = oct & 1, oy = (oct >> 1) & 1, oz = (oct >> 2) & 1;
+  Node4Oct n;
+  n.nx = __ldg(p + ox);
+  n.fx = __ldg(p + (1 - ox));
+  n.ny = __ldg(p + 2 + oy);
+  n.fy = __ldg(p + 3 - oy);
+  n.nz = __ldg(p + 4 + oz);
+  n.fz = __ldg(p + 5 - oz);
   n.ch = __ldg(reinterpret_cast<const int4*>(p + 6));
   return n;
 }
 __device__ __forceinline__ float comp4(float4 v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w)); }
 __device__ __forceinline__ int comp4i(int4 v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w)); }
 
-__device__ __forceinline__ bool child_hit(const Node4& n, int c, const RayPre& r, float tmax, float& tnear) {
-  return box_hit(f3(comp4(n.lox, c), comp4(n.loy, c), comp4(n.loz, c)),
-                 f3(comp4(n.hix, c), comp4(n.hiy, c), comp4(n.hiz, c)), r, tmax, tnear);
+// Slab test of child c: entry = max(0, entry planes), exit = min(tmax, exit
+// planes widened by 1 + 2 gamma_3); NaN distances drop out of fmaxf / fminf.
+__device__ __forceinline__ bool child_hit(const Node4Oct& n, int c, const RayPre& r, float tmax, float& tnear) {
+  float t0 = fmaxf(fmaxf((comp4(n.nx, c) - r.o.x) * r.inv.x, (comp4(n.ny, c) - r.o.y) * r.inv.y),
+                   fmaxf((comp4(n.nz, c) - r.o.z) * r.inv.z, 0.0f));
+  float t1 = fminf(fminf((comp4(n.fx, c) - r.o.x) * r.inv.x, (comp4(n.fy, c) - r.o.y) * r.inv.y),
+                   (comp4(n.fz, c) - r.o.z) * r.inv.z) * 1.0000004f;
+  t1 = fminf(t1, tmax);
+  tnear = t0;
+  return t0 <= t1;
 }
 
 // One node step of the closest-hit walk over the BVH4: leaf children whose
@@ -409,7 +427,7 @@ __device__ __forceinline__ bool child_hit(const Node4& n, int c, const RayPre& r
 __device__ __forceinline__ bool closest_step4(const SceneView& s, const RayPre& r, float tmax, int& node, int& sp,
                                               int* stack, float& best_t, int& best, uint32_t* status,
                                               uint32_t& visits, uint32_t& ptests) {
-  Node4 n = load_node4(s.nodes, node);
+  Node4Oct n = load_node4_oct(s.nodes, node, r.oct);
   ++visits;
   float td[4];
   int cr[4];
