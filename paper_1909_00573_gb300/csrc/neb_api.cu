@@ -23,7 +23,6 @@ SceneView scene_view(const neb_ctx* c) {
   s.sph_mat = c->sph_mat;
   s.mats = c->mats;
   s.nodes = c->nodes;
-  s.nodes2 = c->nodes2;
   s.prim_light = c->prim_light;
   s.light_prim = c->light_prim;
   s.light_psel = c->light_psel;
@@ -59,14 +58,13 @@ static cudaError_t dalloc(T** p, size_t count) {
 static void free_scene(neb_ctx* c) {
   cudaFree(c->tv0); cudaFree(c->tv1); cudaFree(c->tv2); cudaFree(c->sph); cudaFree(c->mats); cudaFree(c->sph_mat);
   cudaFree(c->prim_light); cudaFree(c->light_prim); cudaFree(c->alias_idx); cudaFree(c->light_psel);
-  cudaFree(c->light_inv_area); cudaFree(c->alias_prob); cudaFree(c->nodes); cudaFree(c->nodes2);
+  cudaFree(c->light_inv_area); cudaFree(c->alias_prob); cudaFree(c->nodes);
   cudaFree(c->oct_nodes);
   cudaFree(c->oct_state);
   c->tv0 = c->tv1 = c->tv2 = c->sph = c->mats = nullptr;
   c->sph_mat = c->prim_light = c->light_prim = c->alias_idx = nullptr;
   c->light_psel = c->light_inv_area = c->alias_prob = nullptr;
   c->nodes = nullptr;
-  c->nodes2 = nullptr;
   c->oct_nodes = nullptr;
   c->oct_state = nullptr;
   c->scene_ready = c->bvh_ready = false;

@@ -233,15 +233,9 @@ __global__ void k_write_nodes(SceneView s, int n, const int* __restrict__ sorted
   }
 }
 
-__global__ void k_single_leaf(SceneView s, BVH4Node* nodes, BVHNode* bin) {
+__global__ void k_single_leaf(SceneView s, BVH4Node* nodes) {
   float3 lo, hi;
   prim_bounds(s, 0, lo, hi);
-  BVHNode b;
-  b.a = make_float4(lo.x, hi.x, lo.y, hi.y);
-  b.b = b.a;
-  b.c = make_float4(lo.z, hi.z, lo.z, hi.z);
-  b.ch = make_int4(~0, ~0, 0, 0);
-  bin[0] = b;
   BVH4Node nd;
   nd.lox = make_float4(lo.x, 0, 0, 0);
   nd.hix = make_float4(hi.x, 0, 0, 0);
@@ -511,20 +505,18 @@ cudaError_t build_bvh(neb_ctx* c) {
   int n = c->nt + c->ns;
   cudaStream_t st = c->stream;
   if (c->nodes) { cudaFree(c->nodes); c->nodes = nullptr; }
-  if (c->nodes2) { cudaFree(c->nodes2); c->nodes2 = nullptr; }
   if (n == 0) return cudaSuccess;
   cudaError_t e = cudaMalloc(&c->nodes, sizeof(BVH4Node) * (size_t)(n > 1 ? n - 1 : 1));
   if (e != cudaSuccess) return e;
   SceneView s = scene_view(c);
-  BVHNode* bin = nullptr;
-  e = cudaMalloc(&bin, sizeof(BVHNode) * (size_t)(n > 1 ? n - 1 : 1));
-  if (e != cudaSuccess) return e;
-  c->nodes2 = bin;
-  s.nodes2 = bin;
   if (n == 1) {
-    k_single_leaf<<<1, 1, 0, st>>>(s, c->nodes, bin);
+    k_single_leaf<<<1, 1, 0, st>>>(s, c->nodes);
     return cudaGetLastError();
   }
+  // the binary tree (LBVH or PLOC) is built first and collapsed into the 4-wide one
+  BVHNode* bin = nullptr;
+  e = cudaMalloc(&bin, sizeof(BVHNode) * (size_t)(n - 1));
+  if (e != cudaSuccess) return e;
   int nblocks = (n + kSortThreads - 1) / kSortThreads;
   size_t hist_n = (size_t)16 * nblocks;
   uint32_t *k0 = nullptr, *k1 = nullptr;
@@ -579,6 +571,8 @@ cudaError_t build_bvh(neb_ctx* c) {
   }
   cudaFree(k0); cudaFree(k1); cudaFree(v0); cudaFree(v1); cudaFree(hist); cudaFree(offs); cudaFree(cb);
   cudaFree(child); cudaFree(pint); cudaFree(pleaf); cudaFree(flags); cudaFree(boxes); cudaFree(sc.data);
+  cudaStreamSynchronize(st);
+  cudaFree(bin);
   return e;
 }
 

@@ -361,7 +361,6 @@ struct SceneView {
   const int* __restrict__ sph_mat;
   const float4* __restrict__ mats; // 3 float4 per material
   const BVH4Node* __restrict__ nodes;
-  const BVHNode* __restrict__ nodes2;
   const int* __restrict__ prim_light;
   const int* __restrict__ light_prim;
   const float* __restrict__ light_psel;

@@ -132,7 +132,6 @@ struct neb_ctx {
 
   // BVH (4-wide)
   neb::BVH4Node* nodes = nullptr;
-  neb::BVHNode* nodes2 = nullptr;  // the binary tree (shadow rays)
   int n_nodes4 = 0;
   bool bvh_ready = false;
 

@@ -19,13 +19,12 @@ constexpr int kRefill = 8;     // refill when at least this many lanes are idle
 constexpr int kSteps = 24;     // node steps between refill checks
 constexpr int kIdle = -1, kDone = -2;
 
-// Traversal state.  Closest-hit walks run over the 4-wide BVH and test a leaf
-// primitive as soon as its box is hit.  Shadow (any-hit) walks run over the
-// binary tree the 4-wide one was collapsed from: they queue leaf primitives
-// and the warp tests its queued primitives together once every lane has two
-// queued or nothing left to walk, so the long triangle test runs with most
-// lanes active ("while-while" with speculative traversal, Aila and Laine
-// 2009).  Measured on the city scene, each kind of walk is fastest this way.
+// Traversal state.  Both walks run over the 4-wide BVH.  Closest-hit walks
+// test a leaf primitive as soon as its box is hit.  Shadow (any-hit) walks
+// queue leaf primitives, and the warp tests its queued primitives together
+// once every lane has two queued or nothing left to walk, so the long
+// triangle test runs with most lanes active ("while-while" with speculative
+// traversal, Aila and Laine 2009).
 struct Walk {
   int node;  // next inner node, -1 when the stack is exhausted
   int sp, best;
@@ -42,37 +41,32 @@ __device__ __forceinline__ void walk_init(Walk& w) {
   w.npend = 0;
 }
 
-// One inner-node step of the any-hit walk over the binary tree.
-__device__ __forceinline__ void inner_step2(const SceneView& s, const RayPre& r, float tbound, Walk& w, int* stack,
+// One inner-node step of the any-hit walk over the 4-wide tree: leaf children
+// whose box is hit are queued (at most four, so a walk steps with at most one
+// queued primitive), the first hit inner child is visited next and the others
+// are pushed.
+__device__ __forceinline__ void inner_step4(const SceneView& s, const RayPre& r, float tbound, Walk& w, int* stack,
                                            uint32_t* status, uint32_t& visits) {
-  const float4* np = reinterpret_cast<const float4*>(s.nodes2 + w.node);
-  float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
-  int4 ch = __ldg(reinterpret_cast<const int4*>(np + 3));
+  Node4Oct n = load_node4_oct(s.nodes, w.node, r.oct);
   ++visits;
-  float tl, tr;
-  bool hl = box_hit(f3(a.x, a.z, c.x), f3(a.y, a.w, c.y), r, tbound, tl);
-  bool hr = box_hit(f3(b.x, b.z, c.z), f3(b.y, b.w, c.w), r, tbound, tr);
-  if (hl && ch.x < 0) {
-    w.pend[w.npend++] = ~ch.x;
-    hl = false;
+  int next = -1;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    int ref = comp4i(n.ch, c);
+    if (ref == kEmptyChild) continue;
+    float tn;
+    if (!child_hit(n, c, r, tbound, tn)) continue;
+    if (ref < 0) {
+      w.pend[w.npend++] = ~ref;
+    } else if (next < 0) {
+      next = ref;
+    } else if (w.sp < 64) {
+      stack[w.sp++] = ref;
+    } else {
+      atomicOr(status, NEB_STATUS_STACK_OVERFLOW);
+    }
   }
-  if (hr && ch.y < 0) {
-    w.pend[w.npend++] = ~ch.y;
-    hr = false;
-  }
-  if (hl && hr) {
-    int nearc = tl <= tr ? ch.x : ch.y;
-    int farc = tl <= tr ? ch.y : ch.x;
-    if (w.sp < 64) stack[w.sp++] = farc;
-    else atomicOr(status, NEB_STATUS_STACK_OVERFLOW);
-    w.node = nearc;
-  } else if (hl) {
-    w.node = ch.x;
-  } else if (hr) {
-    w.node = ch.y;
-  } else {
-    w.node = w.sp > 0 ? stack[--w.sp] : -1;
-  }
+  w.node = next >= 0 ? next : (w.sp > 0 ? stack[--w.sp] : -1);
 }
 
 __device__ __forceinline__ void warp_total(unsigned long long* dst, uint32_t v) {
@@ -166,7 +160,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, Nee
     ray = nr;
     if (__all_sync(0xffffffffu, ray == kDone)) break;
     for (int step = 0; step < kSteps; ++step) {
-      if (ray >= 0 && w.node >= 0 && w.npend <= 1) inner_step2(s, r, tmax, w, stack, &cnt->status, visits);
+      if (ray >= 0 && w.node >= 0 && w.npend <= 1) inner_step4(s, r, tmax, w, stack, &cnt->status, visits);
       bool ready = ray < 0 || w.npend >= 2 || w.node < 0;
       if (__all_sync(0xffffffffu, ready)) {
         if (ray >= 0) {
