@@ -124,6 +124,11 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
        dalloc(&c->bucket_start, (size_t)t + 1) == cudaSuccess &&
        dalloc(&c->scan_scratch.data, c->scan_scratch.n) == cudaSuccess && dalloc(&c->accum, P * 3) == cudaSuccess &&
        (!cfg->keep_split || dalloc(&c->split, P * 9) == cudaSuccess);
+  c->shadow_scratch.n = scan_scratch_ints(shadow_hist_ints());
+  ok = ok && dalloc(&c->shadow_order, c->cap_nee) == cudaSuccess &&
+       dalloc(&c->shadow_hist, shadow_hist_ints()) == cudaSuccess &&
+       dalloc(&c->shadow_offs, shadow_hist_ints()) == cudaSuccess &&
+       dalloc(&c->shadow_scratch.data, c->shadow_scratch.n) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&c->stream_b, cudaStreamNonBlocking) == cudaSuccess;
   for (int k = 0; k < 2 && ok; ++k)
     ok = cudaEventCreateWithFlags(&c->ev_pass1[k], cudaEventDisableTiming) == cudaSuccess &&
@@ -135,6 +140,7 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
   cudaMemsetAsync(c->bucket_count, 0, sizeof(int) * ((size_t)t + 1), c->stream);
   cudaMemsetAsync(c->accum, 0, sizeof(double) * P * 3, c->stream);
   cudaMemsetAsync(c->counters, 0, 2 * sizeof(DevCounters), c->stream);
+  cudaMemsetAsync(c->shadow_hist, 0, sizeof(int) * shadow_hist_ints(), c->stream);
   if (c->split) cudaMemsetAsync(c->split, 0, sizeof(double) * P * 9, c->stream);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
@@ -158,6 +164,7 @@ extern "C" void neb_destroy(neb_ctx* c) {
   cudaFree(c->phq[0]); cudaFree(c->phq[1]); cudaFree(c->hits); cudaFree(c->hits_ph); cudaFree(c->mrec);
   cudaFree(c->vert_bucket); cudaFree(c->bucket_count); cudaFree(c->bucket_start); cudaFree(c->scan_scratch.data);
   cudaFree(c->accum); cudaFree(c->split); cudaFree(c->counters);
+  cudaFree(c->shadow_order); cudaFree(c->shadow_hist); cudaFree(c->shadow_offs); cudaFree(c->shadow_scratch.data);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
   for (int k = 0; k < 2; ++k) {

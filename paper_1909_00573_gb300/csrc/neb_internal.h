@@ -55,7 +55,7 @@ struct NeeStore {
   float4* tau;   // rgb, w: g_y = cos_y / (dist^2 p_l)
   float4* err;   // hit point error bound, w: ldist
   float4* ldir;  // direction to the light point, w: rho (after the density pass)
-  float4* dE;    // irradiance rgb (zero if back-facing or occluded), w unused
+  float4* dE;    // irradiance rgb (zero if back-facing or occluded), w: sampled light (int bits, -1 none)
 };
 enum { NV_DELTA = 1, NV_MERGEABLE = 2, NV_SHADOW = 4 };
 enum { NV_MAT_MASK = (1 << 20) - 1, NV_K_SHIFT = 20, NV_FLAG_SHIFT = 26 };
@@ -64,6 +64,7 @@ enum { NV_MAT_MASK = (1 << 20) - 1, NV_K_SHIFT = 20, NV_FLAG_SHIFT = 26 };
 struct DevCounters {
   int cam_count[2];
   int nee_count;
+  int shadow_count;  // NEE vertices with a shadow ray (length of the light-grouped order)
   int rh_count;
   int ph_count[2];
   int merge_count;
@@ -147,6 +148,10 @@ struct neb_ctx {
   neb::PhotonRay* phq[2] = {nullptr, nullptr};
   int2* hits = nullptr;     // closest hits of the camera ray queue (pass 1)
   int2* hits_ph = nullptr;  // closest hits of the photon ray queue (pass 3)
+  int* shadow_order = nullptr;  // NEE ids of the shadow rays, grouped by light
+  int* shadow_hist = nullptr;   // per light group and block counts, then offsets
+  int* shadow_offs = nullptr;
+  neb::Scratch shadow_scratch;  // scan scratch of pass 1 (the grid's is used by pass 2 concurrently)
   neb::MergeRec* mrec = nullptr;
   int* vert_bucket = nullptr;
   int* bucket_count = nullptr;
@@ -186,6 +191,7 @@ cudaError_t launch_area(const float* d_boxes, const float* d_pos, const float* d
 
 // neb_grid.cu
 size_t scan_scratch_ints(size_t n);
+size_t shadow_hist_ints();
 int scan_launch_count(size_t n);
 cudaError_t scan_exclusive(const int* d_in, int* d_out, size_t n, Scratch& scratch, cudaStream_t st);
 cudaError_t grid_build(neb_ctx* c, const IterParams& ip, const IterSlot& sl, cudaStream_t st);

@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
     float3 ldir = f3(0, 0, 0), dE = f3(0, 0, 0);
     float ldist = 0.0f, g_y = 0.0f;
     bool shadow = false;
+    int nee_light = -1;
     if (valid) {
       ry = in[i];
       rays = 1;
@@ -210,6 +211,7 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
               dE = mul(lm.emission, g);
               g_y = cos_y / (dist2 * p_l);
               shadow = true;
+              nee_light = lidx;
             }
           }
         }
@@ -228,7 +230,7 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
       nv.tau[nid] = make_float4(tau.x, tau.y, tau.z, g_y);
       nv.err[nid] = make_float4(err.x, err.y, err.z, ldist);
       nv.ldir[nid] = make_float4(ldir.x, ldir.y, ldir.z, 0.0f);
-      nv.dE[nid] = make_float4(dE.x, dE.y, dE.z, 0.0f);
+      nv.dE[nid] = make_float4(dE.x, dE.y, dE.z, __int_as_float(nee_light));
       if (slot_map) slot_map[(size_t)pixel * (ip.D - 1) + (k - 1)] = nid;
     }
     if (valid && alive) {
@@ -629,7 +631,7 @@ cudaError_t run_iteration(neb_ctx* c, int iteration, bool overlap) {
   }
   tm.begin(STAGE_SHADOW);
   launch_trace_shadow(c, sl, st);
-  launches += 1;
+  launches += 3 + scan_launch_count(shadow_hist_ints());  // grouping by light, then the walk
   tm.end();
   if (overlap) {
     cudaEventRecord(c->ev_pass1[slot], st);

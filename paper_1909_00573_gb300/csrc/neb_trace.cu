@@ -130,12 +130,65 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_closest(SceneView s, co
   warp_total(&cnt->ptests_by[which], ptests);
 }
 
-// Shadow rays of the NEE vertices: any hit with tmax = (1 - 1e-4) dist from
-// the offset origin; an occluded vertex gets dE = 0.
-__global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, NeeStore nv, int cap,
-                                                                int* __restrict__ fetch, DevCounters* cnt) {
+// ---- shadow rays, grouped by the sampled light ----------------------------------
+// Shadow rays leave in the order of their NEE vertices (pixel order within a
+// bounce), so the 32 rays of a warp usually aim at different lights and
+// their walks diverge.  A counting sort by light group first (lights beyond
+// kShBins share groups) gives warps of rays that start close together and
+// aim at the same light; within a group the vertex order is kept block by
+// block.  It also drops the vertices without a shadow ray.
+constexpr int kShBins = 256;
+constexpr int kShBlocks = 304;
+constexpr int kShThreads = 512;
+
+size_t shadow_hist_ints() { return (size_t)kShBins * kShBlocks + 1; }
+
+__device__ __forceinline__ int shadow_bin(int light, int nl) {
+  return nl <= kShBins ? light : (int)(((long long)light * kShBins) / nl);
+}
+
+// Block b counts, per light group, the shadow rays of its contiguous chunk of
+// NEE ids into hist[bin * kShBlocks + b], so one exclusive scan gives each
+// block its output offset per group (groups in order, blocks in order within
+// a group).  The entry after the matrix stays 0: its scanned value is the
+// number of shadow rays.
+__global__ void __launch_bounds__(kShThreads) k_shadow_count(NeeStore nv, const DevCounters* cnt, int cap, int nl,
+                                                             int* __restrict__ hist) {
+  __shared__ int h[kShBins];
+  for (int i = threadIdx.x; i < kShBins; i += blockDim.x) h[i] = 0;
+  __syncthreads();
   const int count = min(cnt->nee_count, cap);
-  int ray = kIdle;
+  const int chunk = (count + gridDim.x - 1) / gridDim.x;
+  const int lo = blockIdx.x * chunk, hi = min(count, lo + chunk);
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    int bits = __float_as_int(nv.nrm[i].w);
+    if ((bits >> NV_FLAG_SHIFT) & NV_SHADOW) atomicAdd(&h[shadow_bin(__float_as_int(nv.dE[i].w), nl)], 1);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kShBins; i += blockDim.x) hist[i * gridDim.x + blockIdx.x] = h[i];
+}
+
+__global__ void __launch_bounds__(kShThreads) k_shadow_scatter(NeeStore nv, DevCounters* cnt, int cap, int nl,
+                                                               const int* __restrict__ offs, int* __restrict__ order) {
+  __shared__ int h[kShBins];
+  for (int i = threadIdx.x; i < kShBins; i += blockDim.x) h[i] = offs[i * gridDim.x + blockIdx.x];
+  __syncthreads();
+  const int count = min(cnt->nee_count, cap);
+  const int chunk = (count + gridDim.x - 1) / gridDim.x;
+  const int lo = blockIdx.x * chunk, hi = min(count, lo + chunk);
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    int bits = __float_as_int(nv.nrm[i].w);
+    if ((bits >> NV_FLAG_SHIFT) & NV_SHADOW) order[atomicAdd(&h[shadow_bin(__float_as_int(nv.dE[i].w), nl)], 1)] = i;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) cnt->shadow_count = offs[kShBins * gridDim.x];
+}
+
+// Shadow rays of the NEE vertices listed in `order`: any hit with tmax =
+// (1 - 1e-4) dist from the offset origin; an occluded vertex gets dE = 0.
+__global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, NeeStore nv, const int* __restrict__ order,
+                                                                int cap, int* __restrict__ fetch, DevCounters* cnt) {
+  const int count = min(cnt->shadow_count, cap);
+  int ray = kIdle;  // NEE id of the lane's shadow ray
   RayPre r;
   Walk w;
   float tmax = 0.0f;
@@ -144,18 +197,14 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, Nee
   while (true) {
     int nr = fetch_rays(ray, fetch, count);
     if (ray == kIdle && nr >= 0) {
-      int bits = __float_as_int(nv.nrm[nr].w);
-      if ((bits >> NV_FLAG_SHIFT) & NV_SHADOW) {
-        float4 pp = nv.pos[nr], nn = nv.nrm[nr], ee = nv.err[nr], ld = nv.ldir[nr];
-        float3 ldir = xyz(ld);
-        r = make_ray(offset_origin(xyz(pp), xyz(nn), xyz(ee), ldir), ldir);
-        tmax = ee.w * (1.0f - 1e-4f);
-        walk_init(w);
-        ++rays;
-        if (s.nt + s.ns == 0) nr = kIdle;
-      } else {
-        nr = kIdle;  // no shadow ray for this vertex
-      }
+      nr = __ldg(order + nr);
+      float4 pp = nv.pos[nr], nn = nv.nrm[nr], ee = nv.err[nr], ld = nv.ldir[nr];
+      float3 ldir = xyz(ld);
+      r = make_ray(offset_origin(xyz(pp), xyz(nn), xyz(ee), ldir), ldir);
+      tmax = ee.w * (1.0f - 1e-4f);
+      walk_init(w);
+      ++rays;
+      if (s.nt + s.ns == 0) nr = kIdle;
     }
     ray = nr;
     if (__all_sync(0xffffffffu, ray == kDone)) break;
@@ -207,9 +256,16 @@ cudaError_t launch_trace_closest(neb_ctx* c, const float4* recs, const int* coun
 }
 
 cudaError_t launch_trace_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st) {
+  const int nl = c->nl > 0 ? c->nl : 1;
+  k_shadow_count<<<kShBlocks, kShThreads, 0, st>>>(sl.nv, sl.cnt, c->cap_nee, nl, c->shadow_hist);
+  cudaError_t e = scan_exclusive(c->shadow_hist, c->shadow_offs, shadow_hist_ints(), c->shadow_scratch, st);
+  if (e != cudaSuccess) return e;
+  k_shadow_scatter<<<kShBlocks, kShThreads, 0, st>>>(sl.nv, sl.cnt, c->cap_nee, nl, c->shadow_offs,
+                                                     c->shadow_order);
   int* fetch = &sl.cnt->fetch[1];
   cudaMemsetAsync(fetch, 0, sizeof(int), st);
-  k_trace_shadow<<<trace_blocks(), kTraceThreads, 0, st>>>(scene_view(c), sl.nv, c->cap_nee, fetch, sl.cnt);
+  k_trace_shadow<<<trace_blocks(), kTraceThreads, 0, st>>>(scene_view(c), sl.nv, c->shadow_order, c->cap_nee, fetch,
+                                                           sl.cnt);
   return cudaGetLastError();
 }
 
