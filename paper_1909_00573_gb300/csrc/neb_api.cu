@@ -125,7 +125,7 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
        dalloc(&c->scan_scratch.data, c->scan_scratch.n) == cudaSuccess && dalloc(&c->accum, P * 3) == cudaSuccess &&
        (!cfg->keep_split || dalloc(&c->split, P * 9) == cudaSuccess);
   c->shadow_scratch.n = scan_scratch_ints(shadow_hist_ints());
-  ok = ok && dalloc(&c->shadow_order, c->cap_nee) == cudaSuccess &&
+  ok = ok && dalloc(&c->shadow_rays, c->cap_nee) == cudaSuccess &&
        dalloc(&c->shadow_hist, shadow_hist_ints()) == cudaSuccess &&
        dalloc(&c->shadow_offs, shadow_hist_ints()) == cudaSuccess &&
        dalloc(&c->shadow_scratch.data, c->shadow_scratch.n) == cudaSuccess;
@@ -164,7 +164,7 @@ extern "C" void neb_destroy(neb_ctx* c) {
   cudaFree(c->phq[0]); cudaFree(c->phq[1]); cudaFree(c->hits); cudaFree(c->hits_ph); cudaFree(c->mrec);
   cudaFree(c->vert_bucket); cudaFree(c->bucket_count); cudaFree(c->bucket_start); cudaFree(c->scan_scratch.data);
   cudaFree(c->accum); cudaFree(c->split); cudaFree(c->counters);
-  cudaFree(c->shadow_order); cudaFree(c->shadow_hist); cudaFree(c->shadow_offs); cudaFree(c->shadow_scratch.data);
+  cudaFree(c->shadow_rays); cudaFree(c->shadow_hist); cudaFree(c->shadow_offs); cudaFree(c->shadow_scratch.data);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
   for (int k = 0; k < 2; ++k) {

@@ -39,6 +39,12 @@ struct __align__(16) PhotonRay {
   float4 mis;  // x E0, y pA, z pB, w: k_nee | (j << 8), j = index of the next hit
 };
 
+// Shadow ray of an NEE vertex in light-grouped order (32 bytes).
+struct __align__(16) ShadowRay {
+  float4 o;  // offset origin, w: tmax = (1 - 1e-4) distance to the light point
+  float4 d;  // direction to the light point, w: NEE id (int bits)
+};
+
 // Grid-ordered copy of a mergeable view vertex (64 bytes).
 struct __align__(16) MergeRec {
   float4 pos;  // xyz, w: Cfac
@@ -55,7 +61,7 @@ struct NeeStore {
   float4* tau;   // rgb, w: g_y = cos_y / (dist^2 p_l)
   float4* err;   // hit point error bound, w: ldist
   float4* ldir;  // direction to the light point, w: rho (after the density pass)
-  float4* dE;    // irradiance rgb (zero if back-facing or occluded), w: sampled light (int bits, -1 none)
+  float4* dE;    // irradiance rgb (zero if back-facing or occluded), w unused
 };
 enum { NV_DELTA = 1, NV_MERGEABLE = 2, NV_SHADOW = 4 };
 enum { NV_MAT_MASK = (1 << 20) - 1, NV_K_SHIFT = 20, NV_FLAG_SHIFT = 26 };
@@ -148,7 +154,7 @@ struct neb_ctx {
   neb::PhotonRay* phq[2] = {nullptr, nullptr};
   int2* hits = nullptr;     // closest hits of the camera ray queue (pass 1)
   int2* hits_ph = nullptr;  // closest hits of the photon ray queue (pass 3)
-  int* shadow_order = nullptr;  // NEE ids of the shadow rays, grouped by light
+  neb::ShadowRay* shadow_rays = nullptr;  // shadow rays grouped by light
   int* shadow_hist = nullptr;   // per light group and block counts, then offsets
   int* shadow_offs = nullptr;
   neb::Scratch shadow_scratch;  // scan scratch of pass 1 (the grid's is used by pass 2 concurrently)

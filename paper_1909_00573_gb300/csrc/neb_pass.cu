@@ -133,7 +133,6 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
     float3 ldir = f3(0, 0, 0), dE = f3(0, 0, 0);
     float ldist = 0.0f, g_y = 0.0f;
     bool shadow = false;
-    int nee_light = -1;
     if (valid) {
       ry = in[i];
       rays = 1;
@@ -211,7 +210,6 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
               dE = mul(lm.emission, g);
               g_y = cos_y / (dist2 * p_l);
               shadow = true;
-              nee_light = lidx;
             }
           }
         }
@@ -230,7 +228,7 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
       nv.tau[nid] = make_float4(tau.x, tau.y, tau.z, g_y);
       nv.err[nid] = make_float4(err.x, err.y, err.z, ldist);
       nv.ldir[nid] = make_float4(ldir.x, ldir.y, ldir.z, 0.0f);
-      nv.dE[nid] = make_float4(dE.x, dE.y, dE.z, __int_as_float(nee_light));
+      nv.dE[nid] = make_float4(dE.x, dE.y, dE.z, 0.0f);
       if (slot_map) slot_map[(size_t)pixel * (ip.D - 1) + (k - 1)] = nid;
     }
     if (valid && alive) {

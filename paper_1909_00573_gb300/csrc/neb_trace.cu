@@ -130,31 +130,61 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_closest(SceneView s, co
   warp_total(&cnt->ptests_by[which], ptests);
 }
 
-// ---- shadow rays, grouped by the sampled light ----------------------------------
+// ---- shadow rays, grouped by where they start and end --------------------------
 // Shadow rays leave in the order of their NEE vertices (pixel order within a
 // bounce), so the 32 rays of a warp usually aim at different lights and
-// their walks diverge.  A counting sort by light group first (lights beyond
-// kShBins share groups) gives warps of rays that start close together and
-// aim at the same light; within a group the vertex order is kept block by
-// block.  It also drops the vertices without a shadow ray.
-constexpr int kShBins = 256;
+// their walks diverge.  A counting sort first groups them by the cell of
+// their origin and the cell of their light point in a 4 x 4 x 4 grid over the
+// scene box (4096 groups, origin-major): rays of a group start close together
+// and run in about the same direction, so a warp walks the same nodes and
+// consecutive warps reuse them in cache.  Within a group the vertex order is
+// kept block by block.  The scatter writes each ray as a 32-byte record, so
+// the walk reads its rays coalesced, and vertices without a shadow ray are
+// dropped.
+constexpr int kShBitsO = 2;  // log2 of the origin grid's cells per axis
+constexpr int kShBitsL = 2;  // log2 of the light-point grid's cells per axis
+constexpr int kShBins = 1 << (3 * (kShBitsO + kShBitsL));
 constexpr int kShBlocks = 304;
 constexpr int kShThreads = 512;
+constexpr size_t kShSmem = sizeof(int) * kShBins;
+static_assert(kShSmem <= 48 * 1024, "grouping histogram must fit the default shared-memory limit");
 
 size_t shadow_hist_ints() { return (size_t)kShBins * kShBlocks + 1; }
 
-__device__ __forceinline__ int shadow_bin(int light, int nl) {
-  return nl <= kShBins ? light : (int)(((long long)light * kShBins) / nl);
+struct ShadowGrid {
+  float3 lo, unit;  // scene box minimum, box extent per axis normalised to 1 (1 / extent)
+};
+
+// Morton index of p's cell in a grid of 2^bits cells per axis over the box
+template <int bits>
+__device__ __forceinline__ int shadow_cell(const ShadowGrid& g, float3 p) {
+  const float n = (float)(1 << bits);
+  int ix = min(max((int)((p.x - g.lo.x) * g.unit.x * n), 0), (1 << bits) - 1);
+  int iy = min(max((int)((p.y - g.lo.y) * g.unit.y * n), 0), (1 << bits) - 1);
+  int iz = min(max((int)((p.z - g.lo.z) * g.unit.z * n), 0), (1 << bits) - 1);
+  int m = 0;
+#pragma unroll
+  for (int b = 0; b < bits; ++b)
+    m |= (((ix >> b) & 1) << (3 * b)) | (((iy >> b) & 1) << (3 * b + 1)) | (((iz >> b) & 1) << (3 * b + 2));
+  return m;
 }
 
-// Block b counts, per light group, the shadow rays of its contiguous chunk of
-// NEE ids into hist[bin * kShBlocks + b], so one exclusive scan gives each
-// block its output offset per group (groups in order, blocks in order within
-// a group).  The entry after the matrix stays 0: its scanned value is the
-// number of shadow rays.
-__global__ void __launch_bounds__(kShThreads) k_shadow_count(NeeStore nv, const DevCounters* cnt, int cap, int nl,
-                                                             int* __restrict__ hist) {
-  __shared__ int h[kShBins];
+__device__ __forceinline__ int shadow_bin(const ShadowGrid& g, const NeeStore& nv, int i) {
+  float3 p = xyz(nv.pos[i]);
+  float4 ld = nv.ldir[i];
+  float dist = nv.err[i].w;
+  float3 y = f3(p.x + ld.x * dist, p.y + ld.y * dist, p.z + ld.z * dist);
+  return (shadow_cell<kShBitsO>(g, p) << (3 * kShBitsL)) + shadow_cell<kShBitsL>(g, y);
+}
+
+// Block b counts, per group, the shadow rays of its contiguous chunk of NEE
+// ids into hist[bin * kShBlocks + b], so one exclusive scan gives each block
+// its output offset per group (groups in order, blocks in order within a
+// group).  The entry after the matrix stays 0: its scanned value is the number
+// of shadow rays.
+__global__ void __launch_bounds__(kShThreads) k_shadow_count(NeeStore nv, const DevCounters* cnt, int cap,
+                                                             ShadowGrid g, int* __restrict__ hist) {
+  extern __shared__ int h[];  // kShBins counters
   for (int i = threadIdx.x; i < kShBins; i += blockDim.x) h[i] = 0;
   __syncthreads();
   const int count = min(cnt->nee_count, cap);
@@ -162,15 +192,16 @@ __global__ void __launch_bounds__(kShThreads) k_shadow_count(NeeStore nv, const 
   const int lo = blockIdx.x * chunk, hi = min(count, lo + chunk);
   for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     int bits = __float_as_int(nv.nrm[i].w);
-    if ((bits >> NV_FLAG_SHIFT) & NV_SHADOW) atomicAdd(&h[shadow_bin(__float_as_int(nv.dE[i].w), nl)], 1);
+    if ((bits >> NV_FLAG_SHIFT) & NV_SHADOW) atomicAdd(&h[shadow_bin(g, nv, i)], 1);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < kShBins; i += blockDim.x) hist[i * gridDim.x + blockIdx.x] = h[i];
 }
 
-__global__ void __launch_bounds__(kShThreads) k_shadow_scatter(NeeStore nv, DevCounters* cnt, int cap, int nl,
-                                                               const int* __restrict__ offs, int* __restrict__ order) {
-  __shared__ int h[kShBins];
+__global__ void __launch_bounds__(kShThreads) k_shadow_scatter(NeeStore nv, DevCounters* cnt, int cap, ShadowGrid g,
+                                                               const int* __restrict__ offs,
+                                                               ShadowRay* __restrict__ rays) {
+  extern __shared__ int h[];  // kShBins output cursors
   for (int i = threadIdx.x; i < kShBins; i += blockDim.x) h[i] = offs[i * gridDim.x + blockIdx.x];
   __syncthreads();
   const int count = min(cnt->nee_count, cap);
@@ -178,15 +209,25 @@ __global__ void __launch_bounds__(kShThreads) k_shadow_scatter(NeeStore nv, DevC
   const int lo = blockIdx.x * chunk, hi = min(count, lo + chunk);
   for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     int bits = __float_as_int(nv.nrm[i].w);
-    if ((bits >> NV_FLAG_SHIFT) & NV_SHADOW) order[atomicAdd(&h[shadow_bin(__float_as_int(nv.dE[i].w), nl)], 1)] = i;
+    if ((bits >> NV_FLAG_SHIFT) & NV_SHADOW) {
+      int slot = atomicAdd(&h[shadow_bin(g, nv, i)], 1);
+      float4 pp = nv.pos[i], nn = nv.nrm[i], ee = nv.err[i], ld = nv.ldir[i];
+      float3 ldir = xyz(ld);
+      float3 o = offset_origin(xyz(pp), xyz(nn), xyz(ee), ldir);
+      ShadowRay sr;
+      sr.o = make_float4(o.x, o.y, o.z, ee.w * (1.0f - 1e-4f));
+      sr.d = make_float4(ldir.x, ldir.y, ldir.z, __int_as_float(i));
+      rays[slot] = sr;
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) cnt->shadow_count = offs[kShBins * gridDim.x];
 }
 
-// Shadow rays of the NEE vertices listed in `order`: any hit with tmax =
-// (1 - 1e-4) dist from the offset origin; an occluded vertex gets dE = 0.
-__global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, NeeStore nv, const int* __restrict__ order,
-                                                                int cap, int* __restrict__ fetch, DevCounters* cnt) {
+// Shadow rays (any hit with tmax = (1 - 1e-4) dist from the offset origin);
+// an occluded NEE vertex gets dE = 0.
+__global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, NeeStore nv,
+                                                                const ShadowRay* __restrict__ srays, int cap,
+                                                                int* __restrict__ fetch, DevCounters* cnt) {
   const int count = min(cnt->shadow_count, cap);
   int ray = kIdle;  // NEE id of the lane's shadow ray
   RayPre r;
@@ -197,11 +238,10 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, Nee
   while (true) {
     int nr = fetch_rays(ray, fetch, count);
     if (ray == kIdle && nr >= 0) {
-      nr = __ldg(order + nr);
-      float4 pp = nv.pos[nr], nn = nv.nrm[nr], ee = nv.err[nr], ld = nv.ldir[nr];
-      float3 ldir = xyz(ld);
-      r = make_ray(offset_origin(xyz(pp), xyz(nn), xyz(ee), ldir), ldir);
-      tmax = ee.w * (1.0f - 1e-4f);
+      float4 so = __ldg(&srays[nr].o), sd = __ldg(&srays[nr].d);
+      nr = __float_as_int(sd.w);
+      r = make_ray(xyz(so), xyz(sd));
+      tmax = so.w;
       walk_init(w);
       ++rays;
       if (s.nt + s.ns == 0) nr = kIdle;
@@ -256,15 +296,22 @@ cudaError_t launch_trace_closest(neb_ctx* c, const float4* recs, const int* coun
 }
 
 cudaError_t launch_trace_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st) {
-  const int nl = c->nl > 0 ? c->nl : 1;
-  k_shadow_count<<<kShBlocks, kShThreads, 0, st>>>(sl.nv, sl.cnt, c->cap_nee, nl, c->shadow_hist);
+  ShadowGrid g;
+  g.lo = f3(c->bmin[0], c->bmin[1], c->bmin[2]);
+  float un[3];
+  for (int a = 0; a < 3; ++a) {
+    float ext = c->bmax[a] - c->bmin[a];
+    un[a] = ext > 0.0f ? 1.0f / ext : 0.0f;
+  }
+  g.unit = f3(un[0], un[1], un[2]);
+  k_shadow_count<<<kShBlocks, kShThreads, kShSmem, st>>>(sl.nv, sl.cnt, c->cap_nee, g, c->shadow_hist);
   cudaError_t e = scan_exclusive(c->shadow_hist, c->shadow_offs, shadow_hist_ints(), c->shadow_scratch, st);
   if (e != cudaSuccess) return e;
-  k_shadow_scatter<<<kShBlocks, kShThreads, 0, st>>>(sl.nv, sl.cnt, c->cap_nee, nl, c->shadow_offs,
-                                                     c->shadow_order);
+  k_shadow_scatter<<<kShBlocks, kShThreads, kShSmem, st>>>(sl.nv, sl.cnt, c->cap_nee, g, c->shadow_offs,
+                                                     c->shadow_rays);
   int* fetch = &sl.cnt->fetch[1];
   cudaMemsetAsync(fetch, 0, sizeof(int), st);
-  k_trace_shadow<<<trace_blocks(), kTraceThreads, 0, st>>>(scene_view(c), sl.nv, c->shadow_order, c->cap_nee, fetch,
+  k_trace_shadow<<<trace_blocks(), kTraceThreads, 0, st>>>(scene_view(c), sl.nv, c->shadow_rays, c->cap_nee, fetch,
                                                            sl.cnt);
   return cudaGetLastError();
 }
