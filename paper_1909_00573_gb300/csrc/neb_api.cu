@@ -107,6 +107,7 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
   c->table_size = t;
   c->scan_scratch.n = scan_scratch_ints((size_t)t + 1);
   bool ok = dalloc(&c->camq[0], P) == cudaSuccess && dalloc(&c->camq[1], P) == cudaSuccess &&
+            dalloc(&c->camq_grouped, P) == cudaSuccess &&
             dalloc(&c->counters, 2) == cudaSuccess;
   for (int k = 0; k < 2 && ok; ++k) {
     IterSlot& sl = c->slots[k];
@@ -155,7 +156,7 @@ extern "C" void neb_destroy(neb_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   free_scene(c);
-  cudaFree(c->camq[0]); cudaFree(c->camq[1]);
+  cudaFree(c->camq[0]); cudaFree(c->camq[1]); cudaFree(c->camq_grouped);
   if (c->stream_b) cudaStreamSynchronize(c->stream_b);
   for (IterSlot& sl : c->slots) {
     cudaFree(sl.nv.pos); cudaFree(sl.nv.nrm); cudaFree(sl.nv.wo); cudaFree(sl.nv.tau); cudaFree(sl.nv.err);

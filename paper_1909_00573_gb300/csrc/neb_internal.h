@@ -150,13 +150,14 @@ struct neb_ctx {
 
   // per-iteration buffers
   neb::CamRay* camq[2] = {nullptr, nullptr};
+  neb::CamRay* camq_grouped = nullptr;  // bounce rays regrouped before tracing
   neb::IterSlot slots[2];
   neb::PhotonRay* phq[2] = {nullptr, nullptr};
   int2* hits = nullptr;     // closest hits of the camera ray queue (pass 1)
   int2* hits_ph = nullptr;  // closest hits of the photon ray queue (pass 3)
   neb::ShadowRay* shadow_rays = nullptr;  // shadow rays grouped by light
-  int* shadow_hist = nullptr;   // per light group and block counts, then offsets
-  int* shadow_offs = nullptr;
+  int* shadow_hist = nullptr;   // per group and block counts (camera and shadow grouping, pass 1)
+  int* shadow_offs = nullptr;   // their exclusive scan
   neb::Scratch shadow_scratch;  // scan scratch of pass 1 (the grid's is used by pass 2 concurrently)
   neb::MergeRec* mrec = nullptr;
   int* vert_bucket = nullptr;
@@ -220,6 +221,8 @@ cudaError_t launch_oct_density_nee(neb_ctx* c, const IterSlot& sl, cudaStream_t 
 cudaError_t launch_trace_closest(neb_ctx* c, const float4* recs, const int* count_ptr, int cap, int2* hits,
                                  int which, DevCounters* cnt, cudaStream_t st);
 cudaError_t launch_trace_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st);
+// regroups the camera queue q (count at count_ptr) into out (same count)
+cudaError_t launch_group_camera(neb_ctx* c, const CamRay* q, const int* count_ptr, CamRay* out, cudaStream_t st);
 
 // neb_pass.cu
 // overlap: passes 2-3 go to stream_b (ordered by the slot events), else all on c->stream

@@ -618,12 +618,19 @@ cudaError_t run_iteration(neb_ctx* c, int iteration, bool overlap) {
     int in = (k - 1) & 1, out = k & 1;
     k_reset_cam_slot<<<1, 1, 0, st>>>(cnt, out);
     tm.begin(STAGE_TRACE_CAM);
-    launch_trace_closest(c, reinterpret_cast<const float4*>(c->camq[in]), &cnt->cam_count[in], c->cap_cam, c->hits,
-                         0, cnt, st);
+    // bounce rays are regrouped by origin and direction cell (primary rays
+    // are coherent in pixel order already)
+    const CamRay* qin = c->camq[in];
+    if (k >= 2) {
+      launch_group_camera(c, qin, &cnt->cam_count[in], c->camq_grouped, st);
+      qin = c->camq_grouped;
+      launches += 2 + scan_launch_count(shadow_hist_ints());
+    }
+    launch_trace_closest(c, reinterpret_cast<const float4*>(qin), &cnt->cam_count[in], c->cap_cam, c->hits, 0, cnt,
+                         st);
     tm.end();
     tm.begin(STAGE_EXTEND);
-    k_extend<<<B, kThreads, 0, st>>>(s, ip, k, c->camq[in], in, c->camq[out], out, sl.nv, sl.rh, cnt, sl.slot_map,
-                                     c->hits);
+    k_extend<<<B, kThreads, 0, st>>>(s, ip, k, qin, in, c->camq[out], out, sl.nv, sl.rh, cnt, sl.slot_map, c->hits);
     launches += 3;
     tm.end();
   }

@@ -151,13 +151,13 @@ static_assert(kShSmem <= 48 * 1024, "grouping histogram must fit the default sha
 
 size_t shadow_hist_ints() { return (size_t)kShBins * kShBlocks + 1; }
 
-struct ShadowGrid {
-  float3 lo, unit;  // scene box minimum, box extent per axis normalised to 1 (1 / extent)
+struct CellGrid {
+  float3 lo, unit;  // box minimum, 1 / extent per axis
 };
 
 // Morton index of p's cell in a grid of 2^bits cells per axis over the box
 template <int bits>
-__device__ __forceinline__ int shadow_cell(const ShadowGrid& g, float3 p) {
+__device__ __forceinline__ int grid_cell(const CellGrid& g, float3 p) {
   const float n = (float)(1 << bits);
   int ix = min(max((int)((p.x - g.lo.x) * g.unit.x * n), 0), (1 << bits) - 1);
   int iy = min(max((int)((p.y - g.lo.y) * g.unit.y * n), 0), (1 << bits) - 1);
@@ -169,12 +169,12 @@ __device__ __forceinline__ int shadow_cell(const ShadowGrid& g, float3 p) {
   return m;
 }
 
-__device__ __forceinline__ int shadow_bin(const ShadowGrid& g, const NeeStore& nv, int i) {
+__device__ __forceinline__ int shadow_bin(const CellGrid& g, const NeeStore& nv, int i) {
   float3 p = xyz(nv.pos[i]);
   float4 ld = nv.ldir[i];
   float dist = nv.err[i].w;
   float3 y = f3(p.x + ld.x * dist, p.y + ld.y * dist, p.z + ld.z * dist);
-  return (shadow_cell<kShBitsO>(g, p) << (3 * kShBitsL)) + shadow_cell<kShBitsL>(g, y);
+  return (grid_cell<kShBitsO>(g, p) << (3 * kShBitsL)) + grid_cell<kShBitsL>(g, y);
 }
 
 // Block b counts, per group, the shadow rays of its contiguous chunk of NEE
@@ -183,7 +183,7 @@ __device__ __forceinline__ int shadow_bin(const ShadowGrid& g, const NeeStore& n
 // group).  The entry after the matrix stays 0: its scanned value is the number
 // of shadow rays.
 __global__ void __launch_bounds__(kShThreads) k_shadow_count(NeeStore nv, const DevCounters* cnt, int cap,
-                                                             ShadowGrid g, int* __restrict__ hist) {
+                                                             CellGrid g, int* __restrict__ hist) {
   extern __shared__ int h[];  // kShBins counters
   for (int i = threadIdx.x; i < kShBins; i += blockDim.x) h[i] = 0;
   __syncthreads();
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kShThreads) k_shadow_count(NeeStore nv, const 
   for (int i = threadIdx.x; i < kShBins; i += blockDim.x) hist[i * gridDim.x + blockIdx.x] = h[i];
 }
 
-__global__ void __launch_bounds__(kShThreads) k_shadow_scatter(NeeStore nv, DevCounters* cnt, int cap, ShadowGrid g,
+__global__ void __launch_bounds__(kShThreads) k_shadow_scatter(NeeStore nv, DevCounters* cnt, int cap, CellGrid g,
                                                                const int* __restrict__ offs,
                                                                ShadowRay* __restrict__ rays) {
   extern __shared__ int h[];  // kShBins output cursors
@@ -221,6 +221,54 @@ __global__ void __launch_bounds__(kShThreads) k_shadow_scatter(NeeStore nv, DevC
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) cnt->shadow_count = offs[kShBins * gridDim.x];
+}
+
+// ---- camera rays after a bounce, grouped by where they start and where they go ----
+// Bounce rays leave in the order of the rays they continue, so after the
+// first diffuse bounce a warp's rays start in one area but go in all
+// directions.  The same counting sort as for shadow rays (one histogram per
+// block over a contiguous chunk, a scan, a scatter) regroups them by the 4 x 4
+// x 4 cell of their origin in the scene box and the 4 x 4 x 4 cell of their
+// direction in [-1, 1]^3 before they are traced; the records move, so the
+// walk and the shading kernel read them coalesced.
+__device__ __forceinline__ int camera_bin(const CellGrid& g, const CamRay& q) {
+  const CellGrid dg = {f3(-1.0f, -1.0f, -1.0f), f3(0.5f, 0.5f, 0.5f)};
+  return (grid_cell<kShBitsO>(g, xyz(q.o)) << (3 * kShBitsL)) + grid_cell<kShBitsL>(dg, xyz(q.d));
+}
+
+__global__ void __launch_bounds__(kShThreads) k_cam_group_count(const CamRay* __restrict__ q,
+                                                                const int* __restrict__ count_ptr, int cap,
+                                                                CellGrid g, int* __restrict__ hist) {
+  extern __shared__ int h[];  // kShBins counters
+  for (int i = threadIdx.x; i < kShBins; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  const int count = min(*count_ptr, cap);
+  const int chunk = (count + gridDim.x - 1) / gridDim.x;
+  const int lo = blockIdx.x * chunk, hi = min(count, lo + chunk);
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    CamRay r;
+    r.o = __ldg(&q[i].o);
+    r.d = __ldg(&q[i].d);
+    atomicAdd(&h[camera_bin(g, r)], 1);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kShBins; i += blockDim.x) hist[i * gridDim.x + blockIdx.x] = h[i];
+}
+
+__global__ void __launch_bounds__(kShThreads) k_cam_group_scatter(const CamRay* __restrict__ q,
+                                                                  const int* __restrict__ count_ptr, int cap,
+                                                                  CellGrid g, const int* __restrict__ offs,
+                                                                  CamRay* __restrict__ out) {
+  extern __shared__ int h[];  // kShBins output cursors
+  for (int i = threadIdx.x; i < kShBins; i += blockDim.x) h[i] = offs[i * gridDim.x + blockIdx.x];
+  __syncthreads();
+  const int count = min(*count_ptr, cap);
+  const int chunk = (count + gridDim.x - 1) / gridDim.x;
+  const int lo = blockIdx.x * chunk, hi = min(count, lo + chunk);
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    CamRay r = q[i];
+    out[atomicAdd(&h[camera_bin(g, r)], 1)] = r;
+  }
 }
 
 // Shadow rays (any hit with tmax = (1 - 1e-4) dist from the offset origin);
@@ -295,8 +343,8 @@ cudaError_t launch_trace_closest(neb_ctx* c, const float4* recs, const int* coun
   return cudaGetLastError();
 }
 
-cudaError_t launch_trace_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st) {
-  ShadowGrid g;
+static CellGrid scene_grid(const neb_ctx* c) {
+  CellGrid g;
   g.lo = f3(c->bmin[0], c->bmin[1], c->bmin[2]);
   float un[3];
   for (int a = 0; a < 3; ++a) {
@@ -304,6 +352,20 @@ cudaError_t launch_trace_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st)
     un[a] = ext > 0.0f ? 1.0f / ext : 0.0f;
   }
   g.unit = f3(un[0], un[1], un[2]);
+  return g;
+}
+
+cudaError_t launch_group_camera(neb_ctx* c, const CamRay* q, const int* count_ptr, CamRay* out, cudaStream_t st) {
+  CellGrid g = scene_grid(c);
+  k_cam_group_count<<<kShBlocks, kShThreads, kShSmem, st>>>(q, count_ptr, c->cap_cam, g, c->shadow_hist);
+  cudaError_t e = scan_exclusive(c->shadow_hist, c->shadow_offs, shadow_hist_ints(), c->shadow_scratch, st);
+  if (e != cudaSuccess) return e;
+  k_cam_group_scatter<<<kShBlocks, kShThreads, kShSmem, st>>>(q, count_ptr, c->cap_cam, g, c->shadow_offs, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st) {
+  CellGrid g = scene_grid(c);
   k_shadow_count<<<kShBlocks, kShThreads, kShSmem, st>>>(sl.nv, sl.cnt, c->cap_nee, g, c->shadow_hist);
   cudaError_t e = scan_exclusive(c->shadow_hist, c->shadow_offs, shadow_hist_ints(), c->shadow_scratch, st);
   if (e != cudaSuccess) return e;
