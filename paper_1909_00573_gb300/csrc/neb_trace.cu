@@ -227,13 +227,18 @@ __global__ void __launch_bounds__(kShThreads) k_shadow_scatter(NeeStore nv, DevC
 // Bounce rays leave in the order of the rays they continue, so after the
 // first diffuse bounce a warp's rays start in one area but go in all
 // directions.  The same counting sort as for shadow rays (one histogram per
-// block over a contiguous chunk, a scan, a scatter) regroups them by the 4 x 4
-// x 4 cell of their origin in the scene box and the 4 x 4 x 4 cell of their
-// direction in [-1, 1]^3 before they are traced; the records move, so the
-// walk and the shading kernel read them coalesced.
+// block over a contiguous chunk, a scan, a scatter) regroups them by the 2 x 2
+// x 2 cell of their origin in the scene box and the 8 x 8 x 8 cell of their
+// direction in [-1, 1]^3 before they are traced (on the city scene direction
+// cells matter more than origin cells); the records move, so the walk and the
+// shading kernel read them coalesced.
+constexpr int kCamBitsO = 1;  // log2 of the origin grid's cells per axis
+constexpr int kCamBitsD = 3;  // log2 of the direction grid's cells per axis
+static_assert((1 << (3 * (kCamBitsO + kCamBitsD))) <= kShBins, "camera groups must fit the grouping histogram");
+
 __device__ __forceinline__ int camera_bin(const CellGrid& g, const CamRay& q) {
   const CellGrid dg = {f3(-1.0f, -1.0f, -1.0f), f3(0.5f, 0.5f, 0.5f)};
-  return (grid_cell<kShBitsO>(g, xyz(q.o)) << (3 * kShBitsL)) + grid_cell<kShBitsL>(dg, xyz(q.d));
+  return (grid_cell<kCamBitsO>(g, xyz(q.o)) << (3 * kCamBitsD)) + grid_cell<kCamBitsD>(dg, xyz(q.d));
 }
 
 __global__ void __launch_bounds__(kShThreads) k_cam_group_count(const CamRay* __restrict__ q,
