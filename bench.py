@@ -123,18 +123,18 @@ def load_peaks():
 
 def stage_bytes(stage, d, P, iters):
     """Algorithmic bytes of one stage over the profiled iterations, with and
-    without BVH traversal.  Per-unit figures: 64 B per BVH node visit and 48 B
-    per triangle test (traversal); 32 B ray read + 8 B hit written per traced
-    ray; 64 B per ray record read or written; 112 B per NEE record; 48 B per
-    random-hit event; 16 B per merge candidate tested, 48 B + 24 B of FP64
-    atomics per accepted merge."""
+    without BVH traversal.  Per-unit figures: 128 B per visit of a 4-wide BVH
+    node and 48 B per triangle test (traversal); 32 B ray read + 8 B hit
+    written per traced ray; 64 B per ray record read or written; 112 B per
+    NEE record; 48 B per random-hit event; 16 B per merge candidate tested,
+    48 B + 24 B of FP64 atomics per accepted merge."""
     trav = {"trace_camera": 0, "shadow": 1, "trace_photon": 2}
     if stage == "trace_camera":
         rec = 40 * d["camera_rays"]
     elif stage == "trace_photon":
         rec = 40 * d["photon_hits"]
     elif stage == "shadow":
-        rec = 64 * d["nee_vertices"] + 16 * d["shadow_rays"]
+        rec = 32 * d["shadow_rays"] + 16 * d["shadow_rays"]      # ray record read, dE cleared when occluded
     elif stage == "extend":
         return (72 * d["camera_rays"] + 64 * max(d["camera_rays"] - P * iters, 0) + 112 * d["nee_vertices"] +
                 48 * d["random_hits"]), None
@@ -143,7 +143,7 @@ def stage_bytes(stage, d, P, iters):
     else:
         return None, None
     k = trav[stage]
-    tr = 64 * d["stage_node_visits"][k] + 48 * d["stage_prim_tests"][k]
+    tr = 128 * d["stage_node_visits"][k] + 48 * d["stage_prim_tests"][k]
     return rec + tr, rec
 
 

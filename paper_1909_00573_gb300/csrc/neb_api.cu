@@ -125,11 +125,8 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
        dalloc(&c->bucket_start, (size_t)t + 1) == cudaSuccess &&
        dalloc(&c->scan_scratch.data, c->scan_scratch.n) == cudaSuccess && dalloc(&c->accum, P * 3) == cudaSuccess &&
        (!cfg->keep_split || dalloc(&c->split, P * 9) == cudaSuccess);
-  c->shadow_scratch.n = scan_scratch_ints(shadow_hist_ints());
   ok = ok && dalloc(&c->shadow_rays, c->cap_nee) == cudaSuccess &&
-       dalloc(&c->shadow_hist, shadow_hist_ints()) == cudaSuccess &&
-       dalloc(&c->shadow_offs, shadow_hist_ints()) == cudaSuccess &&
-       dalloc(&c->shadow_scratch.data, c->shadow_scratch.n) == cudaSuccess;
+       dalloc(&c->group_counters, group_counter_ints()) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&c->stream_b, cudaStreamNonBlocking) == cudaSuccess;
   for (int k = 0; k < 2 && ok; ++k)
     ok = cudaEventCreateWithFlags(&c->ev_pass1[k], cudaEventDisableTiming) == cudaSuccess &&
@@ -141,7 +138,7 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
   cudaMemsetAsync(c->bucket_count, 0, sizeof(int) * ((size_t)t + 1), c->stream);
   cudaMemsetAsync(c->accum, 0, sizeof(double) * P * 3, c->stream);
   cudaMemsetAsync(c->counters, 0, 2 * sizeof(DevCounters), c->stream);
-  cudaMemsetAsync(c->shadow_hist, 0, sizeof(int) * shadow_hist_ints(), c->stream);
+  cudaMemsetAsync(c->group_counters, 0, sizeof(int) * group_counter_ints(), c->stream);
   if (c->split) cudaMemsetAsync(c->split, 0, sizeof(double) * P * 9, c->stream);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
@@ -165,7 +162,7 @@ extern "C" void neb_destroy(neb_ctx* c) {
   cudaFree(c->phq[0]); cudaFree(c->phq[1]); cudaFree(c->hits); cudaFree(c->hits_ph); cudaFree(c->mrec);
   cudaFree(c->vert_bucket); cudaFree(c->bucket_count); cudaFree(c->bucket_start); cudaFree(c->scan_scratch.data);
   cudaFree(c->accum); cudaFree(c->split); cudaFree(c->counters);
-  cudaFree(c->shadow_rays); cudaFree(c->shadow_hist); cudaFree(c->shadow_offs); cudaFree(c->shadow_scratch.data);
+  cudaFree(c->shadow_rays); cudaFree(c->group_counters);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
   for (int k = 0; k < 2; ++k) {
@@ -487,13 +484,14 @@ extern "C" int neb_get_stats(neb_ctx* c, neb_stats* out) {
 
 static const char* kStageNames[STAGE_COUNT] = {"rearm",      "camera",   "trace_camera", "extend",
                                                "shadow",     "octree_insert", "density", "nee_emit",
-                                               "grid_build", "emission", "trace_photon", "photon"};
+                                               "grid_build", "emission", "trace_photon", "photon",
+                                               "group"};
 
 extern "C" int neb_set_profiling(neb_ctx* c, int enable) {
   if (!c) return NEB_ERR_ARG;
   if (enable && !c->ev[0]) {
-    for (int i = 0; i < 128; ++i)
-      if (cudaEventCreate(&c->ev[i]) != cudaSuccess) return fail(c, NEB_ERR_CUDA, "neb_set_profiling");
+    for (auto& ev : c->ev)
+      if (cudaEventCreate(&ev) != cudaSuccess) return fail(c, NEB_ERR_CUDA, "neb_set_profiling");
   }
   c->profiling = enable != 0;
   for (int i = 0; i < STAGE_COUNT; ++i) {

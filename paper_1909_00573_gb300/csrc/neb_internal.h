@@ -111,7 +111,9 @@ struct IterParams {
 };
 
 enum { STAGE_REARM = 0, STAGE_CAMERA, STAGE_TRACE_CAM, STAGE_EXTEND, STAGE_SHADOW, STAGE_INSERT, STAGE_DENSITY,
-       STAGE_NEE, STAGE_GRID, STAGE_EMISSION, STAGE_TRACE_PHOTON, STAGE_PHOTON, STAGE_COUNT };
+       STAGE_NEE, STAGE_GRID, STAGE_EMISSION, STAGE_TRACE_PHOTON, STAGE_PHOTON, STAGE_GROUP, STAGE_COUNT };
+// timed stage intervals per iteration: 5 D + 5 for max depth D (up to D = 64)
+constexpr int kMaxStageRecords = 5 * kMaxDepth + 8;
 
 struct Scratch {
   int* data = nullptr;
@@ -156,9 +158,7 @@ struct neb_ctx {
   int2* hits = nullptr;     // closest hits of the camera ray queue (pass 1)
   int2* hits_ph = nullptr;  // closest hits of the photon ray queue (pass 3)
   neb::ShadowRay* shadow_rays = nullptr;  // shadow rays grouped by light
-  int* shadow_hist = nullptr;   // per group and block counts (camera and shadow grouping, pass 1)
-  int* shadow_offs = nullptr;   // their exclusive scan
-  neb::Scratch shadow_scratch;  // scan scratch of pass 1 (the grid's is used by pass 2 concurrently)
+  int* group_counters = nullptr;  // ray grouping of pass 1: group counts, then cursors
   neb::MergeRec* mrec = nullptr;
   int* vert_bucket = nullptr;
   int* bucket_count = nullptr;
@@ -178,7 +178,7 @@ struct neb_ctx {
 
   // profiling
   bool profiling = false;
-  cudaEvent_t ev[2 * neb::STAGE_COUNT * 16] = {};
+  cudaEvent_t ev[2 * neb::kMaxStageRecords] = {};
   double stage_ms[neb::STAGE_COUNT] = {};
   long long stage_launches[neb::STAGE_COUNT] = {};
 };
@@ -198,7 +198,7 @@ cudaError_t launch_area(const float* d_boxes, const float* d_pos, const float* d
 
 // neb_grid.cu
 size_t scan_scratch_ints(size_t n);
-size_t shadow_hist_ints();
+size_t group_counter_ints();
 int scan_launch_count(size_t n);
 cudaError_t scan_exclusive(const int* d_in, int* d_out, size_t n, Scratch& scratch, cudaStream_t st);
 cudaError_t grid_build(neb_ctx* c, const IterParams& ip, const IterSlot& sl, cudaStream_t st);
@@ -220,6 +220,8 @@ cudaError_t launch_oct_density_nee(neb_ctx* c, const IterSlot& sl, cudaStream_t 
 // neb_trace.cu
 cudaError_t launch_trace_closest(neb_ctx* c, const float4* recs, const int* count_ptr, int cap, int2* hits,
                                  int which, DevCounters* cnt, cudaStream_t st);
+// groups the slot's shadow rays into c->shadow_rays, then walks them
+cudaError_t launch_group_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st);
 cudaError_t launch_trace_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st);
 // regroups the camera queue q (count at count_ptr) into out (same count)
 cudaError_t launch_group_camera(neb_ctx* c, const CamRay* q, const int* count_ptr, CamRay* out, cudaStream_t st);

@@ -540,16 +540,15 @@ __global__ void k_read_rho(NeeStore nv, const DevCounters* cnt, int D, int cap_n
 struct StageTimer {
   neb_ctx* c;
   int idx = 0;
-  cudaEvent_t ev[2 * 64];
-  int stage[64];
+  int stage[kMaxStageRecords];
   explicit StageTimer(neb_ctx* ctx) : c(ctx) {}
   void begin(int s) {
-    if (!c->profiling || idx >= 64) return;
+    if (!c->profiling || idx >= kMaxStageRecords) return;
     stage[idx] = s;
     cudaEventRecord(c->ev[2 * idx], c->stream);
   }
   void end() {
-    if (!c->profiling || idx >= 64) return;
+    if (!c->profiling || idx >= kMaxStageRecords) return;
     cudaEventRecord(c->ev[2 * idx + 1], c->stream);
     ++idx;
   }
@@ -617,15 +616,17 @@ cudaError_t run_iteration(neb_ctx* c, int iteration, bool overlap) {
   for (int k = 1; k <= c->D; ++k) {
     int in = (k - 1) & 1, out = k & 1;
     k_reset_cam_slot<<<1, 1, 0, st>>>(cnt, out);
-    tm.begin(STAGE_TRACE_CAM);
     // bounce rays are regrouped by origin and direction cell (primary rays
     // are coherent in pixel order already)
     const CamRay* qin = c->camq[in];
     if (k >= 2) {
+      tm.begin(STAGE_GROUP);
       launch_group_camera(c, qin, &cnt->cam_count[in], c->camq_grouped, st);
       qin = c->camq_grouped;
-      launches += 2 + scan_launch_count(shadow_hist_ints());
+      launches += 3;
+      tm.end();
     }
+    tm.begin(STAGE_TRACE_CAM);
     launch_trace_closest(c, reinterpret_cast<const float4*>(qin), &cnt->cam_count[in], c->cap_cam, c->hits, 0, cnt,
                          st);
     tm.end();
@@ -634,9 +635,13 @@ cudaError_t run_iteration(neb_ctx* c, int iteration, bool overlap) {
     launches += 3;
     tm.end();
   }
+  tm.begin(STAGE_GROUP);
+  launch_group_shadow(c, sl, st);
+  launches += 3;
+  tm.end();
   tm.begin(STAGE_SHADOW);
   launch_trace_shadow(c, sl, st);
-  launches += 3 + scan_launch_count(shadow_hist_ints());  // grouping by light, then the walk
+  launches += 1;
   tm.end();
   if (overlap) {
     cudaEventRecord(c->ev_pass1[slot], st);

@@ -130,26 +130,39 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_closest(SceneView s, co
   warp_total(&cnt->ptests_by[which], ptests);
 }
 
-// ---- shadow rays, grouped by where they start and end --------------------------
-// Shadow rays leave in the order of their NEE vertices (pixel order within a
-// bounce), so the 32 rays of a warp usually aim at different lights and
-// their walks diverge.  A counting sort first groups them by the cell of
-// their origin and the cell of their light point in a 4 x 4 x 4 grid over the
-// scene box (4096 groups, origin-major): rays of a group start close together
-// and run in about the same direction, so a warp walks the same nodes and
-// consecutive warps reuse them in cache.  Within a group the vertex order is
-// kept block by block.  The scatter writes each ray as a 32-byte record, so
-// the walk reads its rays coalesced, and vertices without a shadow ray are
-// dropped.
-constexpr int kShBitsO = 2;  // log2 of the origin grid's cells per axis
-constexpr int kShBitsL = 2;  // log2 of the light-point grid's cells per axis
-constexpr int kShBins = 1 << (3 * (kShBitsO + kShBitsL));
-constexpr int kShBlocks = 304;
-constexpr int kShThreads = 512;
-constexpr size_t kShSmem = sizeof(int) * kShBins;
-static_assert(kShSmem <= 48 * 1024, "grouping histogram must fit the default shared-memory limit");
+// ---- ray grouping ---------------------------------------------------------------
+// Rays are traced faster when the 32 rays of a warp start close together and
+// run in about the same direction: the lanes walk the same nodes and
+// consecutive warps find them in cache.  Two queues are regrouped by a
+// counting sort over kGroups spatial groups before they are traced:
+//  - shadow rays, which leave in the order of their NEE vertices, so that a
+//    warp's rays usually aim at different lights: grouped by the 4 x 4 x 4
+//    cell of the origin and of the light point in the scene box;
+//  - camera rays after the first bounce, which start in one area but go in
+//    all directions: grouped by the 2 x 2 x 2 cell of the origin and the
+//    8 x 8 x 8 cell of the direction in [-1, 1]^3 (on the city scene the
+//    direction matters more than the origin).
+// The sort has three launches.  Count: each block builds a shared-memory
+// histogram of its contiguous chunk of the queue and adds its non-zero
+// groups to global counters (at most one atomic per block and group).  Scan:
+// one block turns the counters into group offsets and re-zeroes them.
+// Scatter: each block histograms its chunk again, reserves one range per
+// non-zero group from the global cursors and ranks its rays inside the range
+// with shared-memory atomics.  The order inside a group is that of the
+// atomics; it changes no result.  The scatter moves the records, so the
+// walks read their rays coalesced; shadow rays are written as 32-byte records
+// and vertices without a shadow ray are dropped.
+constexpr int kGroupBits = 12;
+constexpr int kGroups = 1 << kGroupBits;
+constexpr int kShBitsO = 2, kShBitsL = 2;   // shadow: origin and light-point cells per axis (log2)
+constexpr int kCamBitsO = 1, kCamBitsD = 3;  // camera: origin and direction cells per axis (log2)
+static_assert(3 * (kShBitsO + kShBitsL) <= kGroupBits && 3 * (kCamBitsO + kCamBitsD) <= kGroupBits,
+              "groups must fit the counters");
+constexpr int kGroupBlocks = 152;
+constexpr int kGroupThreads = 1024;
+constexpr int kScanThreads = 1024;
 
-size_t shadow_hist_ints() { return (size_t)kShBins * kShBlocks + 1; }
+size_t group_counter_ints() { return 2 * (size_t)kGroups; }  // counters, then cursors
 
 struct CellGrid {
   float3 lo, unit;  // box minimum, 1 / extent per axis
@@ -169,110 +182,164 @@ __device__ __forceinline__ int grid_cell(const CellGrid& g, float3 p) {
   return m;
 }
 
-__device__ __forceinline__ int shadow_bin(const CellGrid& g, const NeeStore& nv, int i) {
-  float3 p = xyz(nv.pos[i]);
-  float4 ld = nv.ldir[i];
-  float dist = nv.err[i].w;
-  float3 y = f3(p.x + ld.x * dist, p.y + ld.y * dist, p.z + ld.z * dist);
+__device__ __forceinline__ int shadow_group(const CellGrid& g, float3 p, float3 y) {
   return (grid_cell<kShBitsO>(g, p) << (3 * kShBitsL)) + grid_cell<kShBitsL>(g, y);
 }
 
-// Block b counts, per group, the shadow rays of its contiguous chunk of NEE
-// ids into hist[bin * kShBlocks + b], so one exclusive scan gives each block
-// its output offset per group (groups in order, blocks in order within a
-// group).  The entry after the matrix stays 0: its scanned value is the number
-// of shadow rays.
-__global__ void __launch_bounds__(kShThreads) k_shadow_count(NeeStore nv, const DevCounters* cnt, int cap,
-                                                             CellGrid g, int* __restrict__ hist) {
-  extern __shared__ int h[];  // kShBins counters
-  for (int i = threadIdx.x; i < kShBins; i += blockDim.x) h[i] = 0;
-  __syncthreads();
-  const int count = min(cnt->nee_count, cap);
-  const int chunk = (count + gridDim.x - 1) / gridDim.x;
-  const int lo = blockIdx.x * chunk, hi = min(count, lo + chunk);
-  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    int bits = __float_as_int(nv.nrm[i].w);
-    if ((bits >> NV_FLAG_SHIFT) & NV_SHADOW) atomicAdd(&h[shadow_bin(g, nv, i)], 1);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < kShBins; i += blockDim.x) hist[i * gridDim.x + blockIdx.x] = h[i];
-}
-
-__global__ void __launch_bounds__(kShThreads) k_shadow_scatter(NeeStore nv, DevCounters* cnt, int cap, CellGrid g,
-                                                               const int* __restrict__ offs,
-                                                               ShadowRay* __restrict__ rays) {
-  extern __shared__ int h[];  // kShBins output cursors
-  for (int i = threadIdx.x; i < kShBins; i += blockDim.x) h[i] = offs[i * gridDim.x + blockIdx.x];
-  __syncthreads();
-  const int count = min(cnt->nee_count, cap);
-  const int chunk = (count + gridDim.x - 1) / gridDim.x;
-  const int lo = blockIdx.x * chunk, hi = min(count, lo + chunk);
-  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    int bits = __float_as_int(nv.nrm[i].w);
-    if ((bits >> NV_FLAG_SHIFT) & NV_SHADOW) {
-      int slot = atomicAdd(&h[shadow_bin(g, nv, i)], 1);
-      float4 pp = nv.pos[i], nn = nv.nrm[i], ee = nv.err[i], ld = nv.ldir[i];
-      float3 ldir = xyz(ld);
-      float3 o = offset_origin(xyz(pp), xyz(nn), xyz(ee), ldir);
-      ShadowRay sr;
-      sr.o = make_float4(o.x, o.y, o.z, ee.w * (1.0f - 1e-4f));
-      sr.d = make_float4(ldir.x, ldir.y, ldir.z, __int_as_float(i));
-      rays[slot] = sr;
-    }
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) cnt->shadow_count = offs[kShBins * gridDim.x];
-}
-
-// ---- camera rays after a bounce, grouped by where they start and where they go ----
-// Bounce rays leave in the order of the rays they continue, so after the
-// first diffuse bounce a warp's rays start in one area but go in all
-// directions.  The same counting sort as for shadow rays (one histogram per
-// block over a contiguous chunk, a scan, a scatter) regroups them by the 2 x 2
-// x 2 cell of their origin in the scene box and the 8 x 8 x 8 cell of their
-// direction in [-1, 1]^3 before they are traced (on the city scene direction
-// cells matter more than origin cells); the records move, so the walk and the
-// shading kernel read them coalesced.
-constexpr int kCamBitsO = 1;  // log2 of the origin grid's cells per axis
-constexpr int kCamBitsD = 3;  // log2 of the direction grid's cells per axis
-static_assert((1 << (3 * (kCamBitsO + kCamBitsD))) <= kShBins, "camera groups must fit the grouping histogram");
-
-__device__ __forceinline__ int camera_bin(const CellGrid& g, const CamRay& q) {
+__device__ __forceinline__ int camera_group(const CellGrid& g, float3 o, float3 d) {
   const CellGrid dg = {f3(-1.0f, -1.0f, -1.0f), f3(0.5f, 0.5f, 0.5f)};
-  return (grid_cell<kCamBitsO>(g, xyz(q.o)) << (3 * kCamBitsD)) + grid_cell<kCamBitsD>(dg, xyz(q.d));
+  return (grid_cell<kCamBitsO>(g, o) << (3 * kCamBitsD)) + grid_cell<kCamBitsD>(dg, d);
 }
 
-__global__ void __launch_bounds__(kShThreads) k_cam_group_count(const CamRay* __restrict__ q,
-                                                                const int* __restrict__ count_ptr, int cap,
-                                                                CellGrid g, int* __restrict__ hist) {
-  extern __shared__ int h[];  // kShBins counters
-  for (int i = threadIdx.x; i < kShBins; i += blockDim.x) h[i] = 0;
+// Contiguous chunk [lo, hi) of a queue of n entries for this block.
+__device__ __forceinline__ void block_chunk(int n, int& lo, int& hi) {
+  const int chunk = (n + gridDim.x - 1) / gridDim.x;
+  lo = min(n, blockIdx.x * chunk);
+  hi = min(n, lo + chunk);
+}
+
+// h = shared histogram (kGroups ints).  Adds the block's non-zero groups to
+// the global counters.
+__device__ __forceinline__ void flush_counts(const int* h, int* counts) {
+  for (int i = threadIdx.x; i < kGroups; i += blockDim.x)
+    if (h[i]) atomicAdd(counts + i, h[i]);
+}
+
+// Turns the block's histogram h into its first output slot per group by
+// reserving ranges from the global cursors.
+__device__ __forceinline__ void reserve_ranges(int* h, int* cursors) {
+  for (int i = threadIdx.x; i < kGroups; i += blockDim.x)
+    if (h[i]) h[i] = atomicAdd(cursors + i, h[i]);
+}
+
+__device__ __forceinline__ void clear_hist(int* h) {
+  for (int i = threadIdx.x; i < kGroups; i += blockDim.x) h[i] = 0;
+}
+
+// One block: cursors = exclusive scan of counts, counts reset to zero;
+// *total (if non-null) receives the sum.
+__global__ void __launch_bounds__(kScanThreads) k_group_scan(int* __restrict__ counts, int* __restrict__ cursors,
+                                                             int* total) {
+  constexpr int kPer = kGroups / kScanThreads;
+  __shared__ int warp_sums[kScanThreads / 32];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  int v[kPer];
+  int sum = 0;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    v[j] = counts[t * kPer + j];
+    counts[t * kPer + j] = 0;
+    sum += v[j];
+  }
+  int incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int x = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += x;
+  }
+  if (lane == 31) warp_sums[wid] = incl;
   __syncthreads();
-  const int count = min(*count_ptr, cap);
-  const int chunk = (count + gridDim.x - 1) / gridDim.x;
-  const int lo = blockIdx.x * chunk, hi = min(count, lo + chunk);
-  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    CamRay r;
-    r.o = __ldg(&q[i].o);
-    r.d = __ldg(&q[i].d);
-    atomicAdd(&h[camera_bin(g, r)], 1);
+  if (wid == 0) {
+    int w = lane < kScanThreads / 32 ? warp_sums[lane] : 0;
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int x = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += x;
+    }
+    if (lane < kScanThreads / 32) warp_sums[lane] = wi - w;  // exclusive warp offsets
+    if (lane == 31 && total) *total = wi;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < kShBins; i += blockDim.x) hist[i * gridDim.x + blockIdx.x] = h[i];
+  int run = warp_sums[wid] + incl - sum;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    cursors[t * kPer + j] = run;
+    run += v[j];
+  }
+}
+static_assert(kGroups % kScanThreads == 0, "scan covers the groups evenly");
+
+__device__ __forceinline__ bool nee_has_shadow(const NeeStore& nv, int i) {
+  return (__float_as_int(nv.nrm[i].w) >> NV_FLAG_SHIFT) & NV_SHADOW;
+}
+__device__ __forceinline__ float3 nee_light_point(const NeeStore& nv, int i) {
+  float3 p = xyz(nv.pos[i]);
+  float4 ld = nv.ldir[i];
+  float dist = nv.err[i].w;
+  return f3(p.x + ld.x * dist, p.y + ld.y * dist, p.z + ld.z * dist);
 }
 
-__global__ void __launch_bounds__(kShThreads) k_cam_group_scatter(const CamRay* __restrict__ q,
-                                                                  const int* __restrict__ count_ptr, int cap,
-                                                                  CellGrid g, const int* __restrict__ offs,
-                                                                  CamRay* __restrict__ out) {
-  extern __shared__ int h[];  // kShBins output cursors
-  for (int i = threadIdx.x; i < kShBins; i += blockDim.x) h[i] = offs[i * gridDim.x + blockIdx.x];
+__global__ void __launch_bounds__(kGroupThreads) k_shadow_count(NeeStore nv, const DevCounters* cnt, int cap,
+                                                                CellGrid g, int* __restrict__ counts) {
+  __shared__ int h[kGroups];
+  clear_hist(h);
   __syncthreads();
-  const int count = min(*count_ptr, cap);
-  const int chunk = (count + gridDim.x - 1) / gridDim.x;
-  const int lo = blockIdx.x * chunk, hi = min(count, lo + chunk);
+  int lo, hi;
+  block_chunk(min(cnt->nee_count, cap), lo, hi);
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
+    if (nee_has_shadow(nv, i)) atomicAdd(&h[shadow_group(g, xyz(nv.pos[i]), nee_light_point(nv, i))], 1);
+  __syncthreads();
+  flush_counts(h, counts);
+}
+
+__global__ void __launch_bounds__(kGroupThreads) k_shadow_scatter(NeeStore nv, const DevCounters* cnt, int cap,
+                                                                  CellGrid g, int* __restrict__ cursors,
+                                                                  ShadowRay* __restrict__ rays) {
+  __shared__ int h[kGroups];
+  clear_hist(h);
+  __syncthreads();
+  int lo, hi;
+  block_chunk(min(cnt->nee_count, cap), lo, hi);
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
+    if (nee_has_shadow(nv, i)) atomicAdd(&h[shadow_group(g, xyz(nv.pos[i]), nee_light_point(nv, i))], 1);
+  __syncthreads();
+  reserve_ranges(h, cursors);
+  __syncthreads();
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    if (!nee_has_shadow(nv, i)) continue;
+    int slot = atomicAdd(&h[shadow_group(g, xyz(nv.pos[i]), nee_light_point(nv, i))], 1);
+    float4 pp = nv.pos[i], nn = nv.nrm[i], ee = nv.err[i], ld = nv.ldir[i];
+    float3 ldir = xyz(ld);
+    float3 o = offset_origin(xyz(pp), xyz(nn), xyz(ee), ldir);
+    ShadowRay sr;
+    sr.o = make_float4(o.x, o.y, o.z, ee.w * (1.0f - 1e-4f));
+    sr.d = make_float4(ldir.x, ldir.y, ldir.z, __int_as_float(i));
+    rays[slot] = sr;
+  }
+}
+
+__global__ void __launch_bounds__(kGroupThreads) k_cam_group_count(const CamRay* __restrict__ q,
+                                                                   const int* __restrict__ count_ptr, int cap,
+                                                                   CellGrid g, int* __restrict__ counts) {
+  __shared__ int h[kGroups];
+  clear_hist(h);
+  __syncthreads();
+  int lo, hi;
+  block_chunk(min(*count_ptr, cap), lo, hi);
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
+    atomicAdd(&h[camera_group(g, xyz(__ldg(&q[i].o)), xyz(__ldg(&q[i].d)))], 1);
+  __syncthreads();
+  flush_counts(h, counts);
+}
+
+__global__ void __launch_bounds__(kGroupThreads) k_cam_group_scatter(const CamRay* __restrict__ q,
+                                                                     const int* __restrict__ count_ptr, int cap,
+                                                                     CellGrid g, int* __restrict__ cursors,
+                                                                     CamRay* __restrict__ out) {
+  __shared__ int h[kGroups];
+  clear_hist(h);
+  __syncthreads();
+  int lo, hi;
+  block_chunk(min(*count_ptr, cap), lo, hi);
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
+    atomicAdd(&h[camera_group(g, xyz(__ldg(&q[i].o)), xyz(__ldg(&q[i].d)))], 1);
+  __syncthreads();
+  reserve_ranges(h, cursors);
+  __syncthreads();
   for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     CamRay r = q[i];
-    out[atomicAdd(&h[camera_bin(g, r)], 1)] = r;
+    out[atomicAdd(&h[camera_group(g, xyz(r.o), xyz(r.d))], 1)] = r;
   }
 }
 
@@ -360,22 +427,30 @@ static CellGrid scene_grid(const neb_ctx* c) {
   return g;
 }
 
+static int group_blocks() { return kGroupBlocks; }
+
 cudaError_t launch_group_camera(neb_ctx* c, const CamRay* q, const int* count_ptr, CamRay* out, cudaStream_t st) {
   CellGrid g = scene_grid(c);
-  k_cam_group_count<<<kShBlocks, kShThreads, kShSmem, st>>>(q, count_ptr, c->cap_cam, g, c->shadow_hist);
-  cudaError_t e = scan_exclusive(c->shadow_hist, c->shadow_offs, shadow_hist_ints(), c->shadow_scratch, st);
-  if (e != cudaSuccess) return e;
-  k_cam_group_scatter<<<kShBlocks, kShThreads, kShSmem, st>>>(q, count_ptr, c->cap_cam, g, c->shadow_offs, out);
+  int* counts = c->group_counters;
+  int* cursors = c->group_counters + kGroups;
+  k_cam_group_count<<<group_blocks(), kGroupThreads, 0, st>>>(q, count_ptr, c->cap_cam, g, counts);
+  k_group_scan<<<1, kScanThreads, 0, st>>>(counts, cursors, nullptr);
+  k_cam_group_scatter<<<group_blocks(), kGroupThreads, 0, st>>>(q, count_ptr, c->cap_cam, g, cursors, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st) {
+  CellGrid g = scene_grid(c);
+  int* counts = c->group_counters;
+  int* cursors = c->group_counters + kGroups;
+  k_shadow_count<<<group_blocks(), kGroupThreads, 0, st>>>(sl.nv, sl.cnt, c->cap_nee, g, counts);
+  k_group_scan<<<1, kScanThreads, 0, st>>>(counts, cursors, &sl.cnt->shadow_count);
+  k_shadow_scatter<<<group_blocks(), kGroupThreads, 0, st>>>(sl.nv, sl.cnt, c->cap_nee, g, cursors,
+                                                             c->shadow_rays);
   return cudaGetLastError();
 }
 
 cudaError_t launch_trace_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st) {
-  CellGrid g = scene_grid(c);
-  k_shadow_count<<<kShBlocks, kShThreads, kShSmem, st>>>(sl.nv, sl.cnt, c->cap_nee, g, c->shadow_hist);
-  cudaError_t e = scan_exclusive(c->shadow_hist, c->shadow_offs, shadow_hist_ints(), c->shadow_scratch, st);
-  if (e != cudaSuccess) return e;
-  k_shadow_scatter<<<kShBlocks, kShThreads, kShSmem, st>>>(sl.nv, sl.cnt, c->cap_nee, g, c->shadow_offs,
-                                                     c->shadow_rays);
   int* fetch = &sl.cnt->fetch[1];
   cudaMemsetAsync(fetch, 0, sizeof(int), st);
   k_trace_shadow<<<trace_blocks(), kTraceThreads, 0, st>>>(scene_view(c), sl.nv, c->shadow_rays, c->cap_nee, fetch,
