@@ -56,6 +56,27 @@ def dist_env():
     return rank, world, local
 
 
+# ---- replicas: the pass does not shard, so N GPUs run N independent renders
+def replica_seed(rank):
+    """Each replica renders its own sample stream (Philox key = seed)."""
+    return rank
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The job's time is the slowest rank's (all-reduce MAX; identity on one rank)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, paths_per_step, steps, seconds):
+    """Whole-job throughput in Mpaths/s: the paths of all replicas over the job time."""
+    return world * paths_per_step * steps / seconds / 1e6
+
+
 # ----------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ----------------------------------------------------------------------------
@@ -233,7 +254,7 @@ def main():
         rc.width, rc.height = (int(x) for x in args.res.lower().split("x"))
     if args.octree_cap:
         rc.octree_capacity = args.octree_cap
-    rc.seed = rank                      # replicas render independent sample streams
+    rc.seed = replica_seed(rank)        # replicas render independent sample streams
     P = rc.width * rc.height
     # a dedicated (non-default) stream: the library's kernels and the timing
     # events must be ordered on the same stream
@@ -271,11 +292,8 @@ def main():
     clk = clocks.stop()
     s1 = ctx.stats(check=False)
     d = stats_delta(s0, s1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * P * args.steps / (ms / 1000.0) / 1e6
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = job_value(world, P, args.steps, ms / 1000.0)
 
     # ---- per-stage times (CUDA events on the context stream), roofline of the dominant kernel
     ctx.set_profiling(True)
@@ -323,12 +341,9 @@ def main():
             neb.lib().neb_resolve(ctx2.h, neb.vp(img.data_ptr()), 0)
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([t_e2e], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = max_over_ranks(t_e2e, dist, "cuda")
         ctx2.close()
-        e2e = {"value": world * P * args.steps / t_e2e / 1e6, "unit": METRIC,
+        e2e = {"value": job_value(world, P, args.steps, t_e2e), "unit": METRIC,
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(img.numel() * 4),
                "note": "scene upload + BVH build once per job (h2d amortised over the steps), image read back "
                        "to pinned host memory every step"}

@@ -1,0 +1,70 @@
+"""Host logic of the multi-GPU path (replicas only: each GPU renders its own
+sample stream, no data-path collective) with two gloo ranks on the CPU:
+per-rank seeds, the max-over-ranks job time and the whole-job throughput."""
+import os
+import socket
+
+import pytest
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, times, q):
+    import torch.distributed as dist
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        seed = bench.replica_seed(rank)
+        seeds = [None] * world
+        dist.all_gather_object(seeds, seed)
+        t = bench.max_over_ranks(times[rank], dist, "cpu")
+        v = bench.job_value(world, 921600, 8, t)
+        q.put((rank, seeds, t, v))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_replicas_take_the_slowest_rank():
+    torch = pytest.importorskip("torch")
+    mp = torch.multiprocessing.get_context("spawn")
+    q = mp.Queue()
+    port = _free_port()
+    times = [0.25, 0.40]
+    procs = [mp.Process(target=_rank_main, args=(r, 2, port, times, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = dict()
+    for _ in range(2):
+        rank, seeds, t, v = q.get(timeout=120)
+        out[rank] = (seeds, t, v)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank in range(2):
+        seeds, t, v = out[rank]
+        assert seeds == [0, 1]                      # independent sample streams
+        assert t == pytest.approx(0.40)             # every rank sees the slowest rank's time
+        assert v == pytest.approx(2 * 921600 * 8 / 0.40 / 1e6)
+
+
+def test_single_rank_identity():
+    import bench
+    assert bench.max_over_ranks(1.5) == 1.5
+    assert bench.job_value(1, 100, 10, 2.0) == pytest.approx(100 * 10 / 2.0 / 1e6)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    """Under torchrun the oracle arm is timed once: ranks other than 0 exit 0
+    without work and print nothing."""
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    args = type("A", (), {"steps": 2, "warmup": 1, "gpus": 2, "workload": "large_city"})()
+    assert bench.run_reference(args) == 0
+    assert capsys.readouterr().out == ""
