@@ -394,23 +394,22 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, Nee
   warp_total(&cnt->ptests_by[1], ptests);
 }
 
-static int trace_blocks() {
-  static int blocks = 0;
-  if (blocks == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_closest, kTraceThreads, 0);
-    blocks = (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 4);
-  }
-  return blocks;
+// Persistent grid: the SM count times the resident blocks per SM of `kernel`.
+template <typename K>
+static int trace_blocks(K kernel) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kTraceThreads, 0);
+  return (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 4);
 }
 
 cudaError_t launch_trace_closest(neb_ctx* c, const float4* recs, const int* count_ptr, int cap, int2* hits,
                                  int which, DevCounters* cnt, cudaStream_t st) {
+  static const int closest_blocks = trace_blocks(k_trace_closest);
   int* fetch = &cnt->fetch[which];
   cudaMemsetAsync(fetch, 0, sizeof(int), st);
-  k_trace_closest<<<trace_blocks(), kTraceThreads, 0, st>>>(scene_view(c), recs, count_ptr, cap, fetch, hits, cnt,
+  k_trace_closest<<<closest_blocks, kTraceThreads, 0, st>>>(scene_view(c), recs, count_ptr, cap, fetch, hits, cnt,
                                                             which);
   return cudaGetLastError();
 }
@@ -451,9 +450,10 @@ cudaError_t launch_group_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st)
 }
 
 cudaError_t launch_trace_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st) {
+  static const int shadow_blocks = trace_blocks(k_trace_shadow);
   int* fetch = &sl.cnt->fetch[1];
   cudaMemsetAsync(fetch, 0, sizeof(int), st);
-  k_trace_shadow<<<trace_blocks(), kTraceThreads, 0, st>>>(scene_view(c), sl.nv, c->shadow_rays, c->cap_nee, fetch,
+  k_trace_shadow<<<shadow_blocks, kTraceThreads, 0, st>>>(scene_view(c), sl.nv, c->shadow_rays, c->cap_nee, fetch,
                                                            sl.cnt);
   return cudaGetLastError();
 }
