@@ -18,6 +18,7 @@ implementation used by the parity tests) on a band of the same image.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -140,6 +141,34 @@ def load_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
+# stage's kernel, from one ncu capture of the full workload (profiles/ holds
+# the summary and the command).  It is reported only while the kernel's
+# sources hash to the value recorded with the capture, else null.
+TRAFFIC_SOURCES = ("paper_1909_00573_gb300/csrc/neb_trace.cu", "paper_1909_00573_gb300/csrc/neb_device.cuh",
+                   "paper_1909_00573_gb300/csrc/neb_types.h")
+NCU_TRAFFIC = {
+    "trace_camera": {"bytes_per_launch": 66622694,
+                     "sources_sha256": "399e1cad5fdf7f59fefcdc2ceb4a3ce20b84bda99ee4cf82f13fac46f9f3fab1",
+                     "profile": "profiles/k_trace_closest_large_city.md"},
+}
+
+
+def sources_sha256():
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(stage):
+    e = NCU_TRAFFIC.get(stage)
+    if not e or e["bytes_per_launch"] is None or e["sources_sha256"] != sources_sha256():
+        return None, None
+    return e["bytes_per_launch"], e["profile"]
 
 
 def stage_bytes(stage, d, P, iters):
@@ -313,8 +342,9 @@ def main():
         per_launch = byt / dom_launches
         avg_ms = dom_ms / dom_launches
         achieved = per_launch / (avg_ms / 1000.0) / 1e9
+        traffic, traffic_src = measured_traffic(dom)
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src, "peak_kind": peak_kind,
                 "bytes_per_launch": per_launch, "avg_launch_ms": avg_ms,
                 "achieved_without_traversal": (None if byt_nt is None else
                                                (byt_nt / dom_launches) / (avg_ms / 1000.0) / 1e9)}

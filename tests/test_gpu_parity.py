@@ -189,6 +189,37 @@ def test_bvh_closest_hit_equals_oracle(neb, oracle, name, builder):
     assert (gp >= 0).mean() > 0.3
 
 
+def test_bvh_far_origin_rays_hit_their_targets(neb, oracle):
+    """The slab test must stay conservative for origins far from the boxes
+    (large |o|, small boxes): with the camera 15 units from a scene of extent
+    1, rays from 10-15 units away aimed at triangle centroids must all hit,
+    and hit what the oracle hits."""
+    from paper_1909_00573_gb300 import scenes
+    rng = np.random.default_rng(7)
+    tri = rng.uniform(-1, 1, (4000, 3, 3)).astype(np.float32)
+    tri[:, 1:] = tri[:, :1] + 0.05 * (tri[:, 1:] - tri[:, :1])
+    cam = np.zeros(10)
+    cam[:3] = (15.0, 0.0, 0.0)
+    s = scenes.Scene(tri, np.zeros(4000), np.zeros((0, 4)), np.zeros(0),
+                     scenes.material(0, (0.5,) * 3)[None], cam)
+    n = 20000
+    target = tri[rng.integers(0, 4000, n)].mean(axis=1)
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    o = target - d * rng.uniform(10.0, 15.0, (n, 1))
+    rays = np.concatenate([o, d], 1).astype(np.float32)
+    rc = scenes.RenderConfig(8, 8, 4, 0.01, 1024, 4, 1)
+    ctx = neb.Context(neb.make_config(rc))
+    ctx.scene_upload(s)
+    ctx.build_bvh()
+    gp, gt = ctx.trace_closest(rays)
+    ctx.close()
+    op, ot = oracle.trace(s, rays)
+    assert (op >= 0).mean() > 0.999
+    assert np.mean(gp == op) >= 0.9999, np.mean(gp == op)
+    assert np.all(gp[op >= 0] >= 0)
+
+
 def test_neighbour_counts_equal_brute_force(neb, oracle):
     rng = np.random.default_rng(51)
     pts = rng.uniform(0, 1, (30000, 3)).astype(np.float32)
