@@ -170,6 +170,17 @@ int neb_octree_insert(neb_octree* o, const float* pos, int n, int mode);
 int neb_octree_density(neb_octree* o, const float* pos, const float* nrm, int n, int robust, float* out);
 /* Copies the node array (capacity entries) and meta = {alloc, depth, capacity, status}. */
 int neb_octree_read(neb_octree* o, int32_t* nodes, int n_nodes, int32_t meta[4]);
+/* Restores a node array and its allocation state, e.g. one read back by
+ * neb_octree_read, to resume a density estimate (the octree integrates over
+ * iterations, Sec. 5.4).  nodes: n_nodes host entries, 1 <= n_nodes <=
+ * capacity, copied before return; entries past n_nodes become 0.  alloc in
+ * [1, capacity + 1] (capacity + 1: allocation overflowed), depth in
+ * [0, 30]; the status word is cleared.  NEB_ERR_ARG for values out of range.
+ * Node values are taken as given: a non-negative counter above the split
+ * threshold with no child (a state inserts never leave) makes concurrent
+ * inserts through it wait out their bounded spin, drop the position and
+ * return NEB_ERR_DEVICE_TIMEOUT. */
+int neb_octree_load(neb_octree* o, const int32_t* nodes, int n_nodes, int alloc, int depth);
 
 /* Merge candidate search through the device hashed grid (cell size 2r, the
  * structure used by the photon merge): for each query, the number of points

@@ -293,6 +293,17 @@ extern "C" int neb_octree_density(neb_octree* o, const float* pos, const float* 
   return NEB_OK;
 }
 
+extern "C" int neb_octree_load(neb_octree* o, const int32_t* nodes, int n_nodes, int alloc, int depth) {
+  if (!o || !nodes || n_nodes < 1 || n_nodes > o->P.capacity || alloc < 1 || alloc > o->P.capacity + 1 ||
+      depth < 0 || depth > neb::kOctMaxDepth)
+    return NEB_ERR_ARG;
+  neb::OctreeState s{alloc, depth, 0u, 0};
+  cudaMemsetAsync(o->nodes, 0, sizeof(int) * (size_t)o->P.capacity, o->stream);
+  cudaMemcpyAsync(o->nodes, nodes, sizeof(int) * (size_t)n_nodes, cudaMemcpyHostToDevice, o->stream);
+  cudaMemcpyAsync(o->st, &s, sizeof(s), cudaMemcpyHostToDevice, o->stream);
+  return cudaStreamSynchronize(o->stream) == cudaSuccess ? NEB_OK : NEB_ERR_CUDA;
+}
+
 extern "C" int neb_octree_read(neb_octree* o, int32_t* nodes, int n_nodes, int32_t meta[4]) {
   if (!o || !meta) return NEB_ERR_ARG;
   neb::OctreeState s;

@@ -18,13 +18,15 @@ NEB_OK = 0
 ERRORS = {-1: "NEB_ERR_ARG", -2: "NEB_ERR_OOM", -3: "NEB_ERR_CUDA", -4: "NEB_ERR_DEVICE_TIMEOUT",
           -5: "NEB_ERR_QUEUE_OVERFLOW", -6: "NEB_ERR_NO_DEVICE"}
 STATUS_SPIN_TIMEOUT, STATUS_QUEUE_OVERFLOW, STATUS_STACK_OVERFLOW, STATUS_OCTREE_FULL = 1, 2, 4, 8
+ERR_ARG, ERR_OOM, ERR_CUDA, ERR_DEVICE_TIMEOUT, ERR_QUEUE_OVERFLOW, ERR_NO_DEVICE = -1, -2, -3, -4, -5, -6
 
 # every function declared in include/neb.h
 EXPORTS = ["neb_create", "neb_destroy", "neb_last_error", "neb_scene_upload", "neb_build_bvh", "neb_iterate",
            "neb_resolve", "neb_read_accum", "neb_read_split", "neb_read_nee_rho", "neb_get_stats",
            "neb_set_profiling", "neb_get_stage_times", "neb_trace_closest", "neb_philox", "neb_plane_box_area",
            "neb_octree_create", "neb_octree_destroy", "neb_octree_set_iteration", "neb_octree_insert",
-           "neb_octree_density", "neb_octree_read", "neb_count_neighbours", "neb_count_neighbours_noalloc"]
+           "neb_octree_density", "neb_octree_read", "neb_octree_load", "neb_count_neighbours",
+           "neb_count_neighbours_noalloc"]
 NOALLOC_MAX_POINTS = 1 << 18
 
 
@@ -95,6 +97,7 @@ def lib():
             "neb_octree_insert": ([vp, vp, C.c_int, C.c_int], C.c_int),
             "neb_octree_density": ([vp, vp, vp, C.c_int, C.c_int, vp], C.c_int),
             "neb_octree_read": ([vp, vp, C.c_int, vp], C.c_int),
+            "neb_octree_load": ([vp, vp, C.c_int, C.c_int, C.c_int], C.c_int),
             "neb_count_neighbours": ([vp, C.c_int, vp, C.c_int, C.c_float, vp], C.c_int),
             "neb_count_neighbours_noalloc": ([vp, C.c_int, vp, C.c_int, C.c_float, vp, vp], C.c_int),
         }
@@ -286,6 +289,10 @@ class Octree:
         nodes = np.zeros(int(meta[2]), np.int32)
         _check(lib().neb_octree_read(self.h, _p(nodes), len(nodes), _p(meta)))
         return nodes, int(meta[0]), int(meta[1]), int(meta[3])
+
+    def load(self, nodes, alloc, depth):
+        N = np.ascontiguousarray(nodes, np.int32)
+        _check(lib().neb_octree_load(self.h, _p(N), len(N), int(alloc), int(depth)))
 
 
 def render(scene, rc, n_iter=None, keep_split=True, stream=None, **over):

@@ -123,6 +123,58 @@ def test_octree_concurrent_conserves_counts(neb):
         assert a1 > a0
 
 
+def test_octree_load_round_trip(neb):
+    """A node array read back and loaded into a fresh octree (checkpoint and
+    resume) gives the same densities and continues counting identically."""
+    its = _octree_inputs(5, n_iter=3, n=6000)
+    a = neb.Octree([0, 0, 0], [1, 1, 1], 1 << 16, 4)
+    for i, pts in enumerate(its[:2], start=1):
+        a.set_iteration(i)
+        a.insert(pts, mode=1)
+    nodes, alloc, depth, status = a.read()
+    b = neb.Octree([0, 0, 0], [1, 1, 1], 1 << 16, 4)
+    b.load(nodes[:alloc], alloc, depth)
+    for o in (a, b):
+        o.set_iteration(3)
+        o.insert(its[2], mode=1)
+    rng = np.random.default_rng(3)
+    q = rng.uniform(0, 1, (2000, 3)).astype(np.float32)
+    n = rng.normal(size=(2000, 3)).astype(np.float32)
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    assert np.array_equal(a.read()[0], b.read()[0])
+    assert np.array_equal(a.density(q, n), b.density(q, n))
+    with pytest.raises(neb.NebError):
+        b.load(nodes[:alloc], 0, depth)               # alloc out of range
+    a.close()
+    b.close()
+
+
+def test_octree_spin_timeout_is_reported(neb):
+    """A counter above the split threshold with no child pointer (a state
+    inserts never leave, restored here with neb_octree_load) makes concurrent
+    inserts through it wait out their bounded spin: each is dropped after
+    counting in that node, the status bit is set, the call returns
+    NEB_ERR_DEVICE_TIMEOUT, and the octree and the GPU stay usable."""
+    o = neb.Octree([0, 0, 0], [1, 1, 1], 1024, 4)
+    o.set_iteration(1)                                # split threshold 4
+    nodes = np.zeros(1024, np.int32)
+    nodes[0] = 7                                      # above the threshold, never split
+    o.load(nodes, 1, 0)
+    pts = np.random.default_rng(9).uniform(0, 1, (64, 3)).astype(np.float32)
+    with pytest.raises(neb.NebError) as e:
+        o.insert(pts, mode=0)
+    assert e.value.code == neb.ERR_DEVICE_TIMEOUT
+    after, alloc, depth, status = o.read()
+    assert status & neb.STATUS_SPIN_TIMEOUT
+    assert after[0] == 7 + 64 and alloc == 1
+    # a fresh state on the same octree works again
+    o.load(np.zeros(1, np.int32), 1, 0)
+    o.insert(pts, mode=0)
+    after, alloc, depth, status = o.read()
+    assert status == 0 and alloc > 1
+    o.close()
+
+
 def test_octree_concurrent_close_to_sequential(neb, oracle):
     its = _octree_inputs(31, n_iter=2, n=20000)
     g = neb.Octree([0, 0, 0], [1, 1, 1], 1 << 18, 4)
