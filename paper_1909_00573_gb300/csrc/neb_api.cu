@@ -127,7 +127,8 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
        (!cfg->keep_split || dalloc(&c->split, P * 9) == cudaSuccess);
   ok = ok && dalloc(&c->shadow_rays, c->cap_nee) == cudaSuccess &&
        dalloc(&c->group_counters, group_counter_ints()) == cudaSuccess;
-  ok = ok && cudaStreamCreateWithFlags(&c->stream_b, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&c->stream_b, cudaStreamNonBlocking) == cudaSuccess &&
+       cudaStreamCreateWithFlags(&c->stream_cap, cudaStreamNonBlocking) == cudaSuccess;
   for (int k = 0; k < 2 && ok; ++k)
     ok = cudaEventCreateWithFlags(&c->ev_pass1[k], cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&c->ev_pass23[k], cudaEventDisableTiming) == cudaSuccess;
@@ -169,7 +170,12 @@ extern "C" void neb_destroy(neb_ctx* c) {
     if (c->ev_pass1[k]) cudaEventDestroy(c->ev_pass1[k]);
     if (c->ev_pass23[k]) cudaEventDestroy(c->ev_pass23[k]);
   }
+  for (int k = 0; k < 2; ++k) {
+    if (c->graph_pass1[k]) cudaGraphExecDestroy(c->graph_pass1[k]);
+    if (c->graph_pass23[k]) cudaGraphExecDestroy(c->graph_pass23[k]);
+  }
   if (c->stream_b) cudaStreamDestroy(c->stream_b);
+  if (c->stream_cap) cudaStreamDestroy(c->stream_cap);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }

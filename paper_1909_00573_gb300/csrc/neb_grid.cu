@@ -143,7 +143,7 @@ __global__ void k_grid_scatter(NeeStore nv, DevCounters* cnt, int cap, const int
 }
 
 cudaError_t grid_build(neb_ctx* c, const IterParams& ip, const IterSlot& sl, cudaStream_t st) {
-  const int B = 152 * 8;
+  const int B = capped_blocks(c->cap_nee, 256, 152 * 8);
   k_grid_count<<<B, 256, 0, st>>>(sl.nv, sl.cnt, c->cap_nee, ip.gmin, ip.cell_inv, ip.table_mask, c->bucket_count,
                                   c->vert_bucket);
   cudaError_t e = scan_exclusive(c->bucket_count, c->bucket_start, (size_t)c->table_size + 1, c->scan_scratch, st);

@@ -173,6 +173,11 @@ struct neb_ctx {
   // on `stream`; ev_pass1[s] / ev_pass23[s] mark the end of each half for slot s
   cudaStream_t stream_b = nullptr;
   cudaEvent_t ev_pass1[2] = {nullptr, nullptr}, ev_pass23[2] = {nullptr, nullptr};
+  // overlapped iterations launch each half as a CUDA graph, recorded on
+  // stream_cap every iteration and applied to the slot's executable graph
+  bool use_graphs = true;
+  cudaStream_t stream_cap = nullptr;
+  cudaGraphExec_t graph_pass1[2] = {nullptr, nullptr}, graph_pass23[2] = {nullptr, nullptr};
   int iteration = 0;  // iterations completed (enqueued)
   long long launches = 0;  // kernels enqueued by neb_iterate
 
@@ -184,6 +189,14 @@ struct neb_ctx {
 };
 
 namespace neb {
+
+// Grid of a grid-stride kernel over at most `cap` items: enough blocks to give
+// every item a thread, never more than max_blocks (small images launch small
+// grids).
+inline int capped_blocks(long long cap, int threads, int max_blocks) {
+  long long b = (cap + threads - 1) / threads;
+  return b < 1 ? 1 : (b > max_blocks ? max_blocks : (int)b);
+}
 
 // ---- launchers implemented in the .cu files -----------------------------------
 SceneView scene_view(const neb_ctx* c);

@@ -193,13 +193,13 @@ cudaError_t launch_oct_insert_nee(neb_ctx* c, const IterSlot& sl, cudaStream_t s
     k_oct_insert_nee_seq<<<1, 1, 0, st>>>(c->oct_nodes, c->oct_state, c->oct, sl.nv.pos, sl.slot_map,
                                           c->P * (c->D - 1), sl.cnt);
   else
-    k_oct_insert_nee<<<152 * 8, 256, 0, st>>>(c->oct_nodes, c->oct_state, c->oct, sl.nv.pos, sl.cnt, c->cap_nee,
+    k_oct_insert_nee<<<capped_blocks(c->cap_nee, 256, 152 * 8), 256, 0, st>>>(c->oct_nodes, c->oct_state, c->oct, sl.nv.pos, sl.cnt, c->cap_nee,
                                               kSpinLimit);
   return cudaGetLastError();
 }
 
 cudaError_t launch_oct_density_nee(neb_ctx* c, const IterSlot& sl, cudaStream_t st) {
-  k_oct_density_nee<<<152 * 8, 256, 0, st>>>(c->oct_nodes, c->oct_state, c->oct, sl.nv.pos, sl.nv.nrm, sl.nv.ldir,
+  k_oct_density_nee<<<capped_blocks(c->cap_nee, 256, 152 * 8), 256, 0, st>>>(c->oct_nodes, c->oct_state, c->oct, sl.nv.pos, sl.nv.nrm, sl.nv.ldir,
                                              sl.cnt, c->cap_nee, c->cfg.density_mode == 0);
   return cudaGetLastError();
 }

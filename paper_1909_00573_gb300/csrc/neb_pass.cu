@@ -587,30 +587,22 @@ IterParams iter_params(const neb_ctx* c, int iteration) {
   return ip;
 }
 
-cudaError_t run_iteration(neb_ctx* c, int iteration, bool overlap) {
+// Pass 1 of `iteration` on stream st: view paths, NEE samples and shadow rays
+// into slot iteration & 1.  Returns the number of kernels enqueued.
+static long long enqueue_pass1(neb_ctx* c, int iteration, cudaStream_t st, StageTimer& tm) {
   const int B = grid_blocks();
   SceneView s = scene_view(c);
   IterParams ip = iter_params(c, iteration);
-  const int slot = iteration & 1;
-  IterSlot& sl = c->slots[slot];
+  IterSlot& sl = c->slots[iteration & 1];
   DevCounters* cnt = sl.cnt;
-  // pass 1 on the caller's stream; passes 2-3 on stream_b when overlapped
-  cudaStream_t st = c->stream;
-  cudaStream_t st2 = overlap ? c->stream_b : c->stream;
-  StageTimer tm(c);  // profiling runs never overlap, so every stage is on c->stream
-  double* split = c->cfg.keep_split ? c->split : nullptr;
   long long launches = 0;
-
-  // ---- pass 1: view paths, NEE samples and shadow rays into slot `slot`
-  // (its previous user, iteration - 2, must have finished passes 2-3)
-  if (overlap) cudaStreamWaitEvent(st, c->ev_pass23[slot], 0);
   tm.begin(STAGE_REARM);
   k_begin<<<1, 1, 0, st>>>(cnt);
   if (sl.slot_map) cudaMemsetAsync(sl.slot_map, 0xff, sizeof(int) * (size_t)c->P * (c->D - 1), st);
   launches += 1;
   tm.end();
   tm.begin(STAGE_CAMERA);
-  k_camera<<<B, kThreads, 0, st>>>(ip, c->cam, c->camq[0], cnt);
+  k_camera<<<capped_blocks(c->P, kThreads, B), kThreads, 0, st>>>(ip, c->cam, c->camq[0], cnt);
   launches += 1;
   tm.end();
   for (int k = 1; k <= c->D; ++k) {
@@ -631,7 +623,7 @@ cudaError_t run_iteration(neb_ctx* c, int iteration, bool overlap) {
                          st);
     tm.end();
     tm.begin(STAGE_EXTEND);
-    k_extend<<<B, kThreads, 0, st>>>(s, ip, k, qin, in, c->camq[out], out, sl.nv, sl.rh, cnt, sl.slot_map, c->hits);
+    k_extend<<<capped_blocks(c->cap_cam, kThreads, B), kThreads, 0, st>>>(s, ip, k, qin, in, c->camq[out], out, sl.nv, sl.rh, cnt, sl.slot_map, c->hits);
     launches += 3;
     tm.end();
   }
@@ -643,14 +635,21 @@ cudaError_t run_iteration(neb_ctx* c, int iteration, bool overlap) {
   launch_trace_shadow(c, sl, st);
   launches += 1;
   tm.end();
-  if (overlap) {
-    cudaEventRecord(c->ev_pass1[slot], st);
-    cudaStreamWaitEvent(st2, c->ev_pass1[slot], 0);
-  }
+  return launches;
+}
 
-  // ---- pass 2: octree set_iteration (Appendix B: host-side scalars, device
-  // re-arm), inserts of this iteration's NEE vertices, densities, NEE
-  // contributions and photon emission
+// Passes 2-3 of `iteration` on stream st: octree set_iteration (Appendix B:
+// host-side scalars, device re-arm), inserts of the iteration's NEE vertices,
+// densities, NEE contributions and photon emission; then the deferred random
+// hits, photon walks and merges.
+static long long enqueue_pass23(neb_ctx* c, int iteration, cudaStream_t st2, StageTimer& tm) {
+  const int B = grid_blocks();
+  SceneView s = scene_view(c);
+  IterParams ip = iter_params(c, iteration);
+  IterSlot& sl = c->slots[iteration & 1];
+  DevCounters* cnt = sl.cnt;
+  double* split = c->cfg.keep_split ? c->split : nullptr;
+  long long launches = 0;
   octree_set_iteration_params(c->oct, c->cfg.split_factor, iteration);
   tm.begin(STAGE_INSERT);
   if (split) cudaMemsetAsync(c->split, 0, sizeof(double) * 9 * (size_t)c->P, st2);
@@ -662,7 +661,7 @@ cudaError_t run_iteration(neb_ctx* c, int iteration, bool overlap) {
   launch_oct_density_nee(c, sl, st2);
   tm.end();
   tm.begin(STAGE_NEE);
-  k_nee<<<B, kThreads, 0, st2>>>(s, ip, sl.nv, cnt, c->accum, split, c->phq[0]);
+  k_nee<<<capped_blocks(c->cap_nee, kThreads, B), kThreads, 0, st2>>>(s, ip, sl.nv, cnt, c->accum, split, c->phq[0]);
   tm.end();
   launches += 2;
   if ((ip.mask & 4u) && c->D >= 3) {
@@ -671,9 +670,8 @@ cudaError_t run_iteration(neb_ctx* c, int iteration, bool overlap) {
     launches += 2 + scan_launch_count((size_t)c->table_size + 1);
     tm.end();
   }
-  // ---- pass 3: deferred random hits, photon walks and merges
   tm.begin(STAGE_EMISSION);
-  k_emission<<<B, kThreads, 0, st2>>>(s, ip, sl.nv, sl.rh, cnt, c->accum, split);
+  k_emission<<<capped_blocks(c->cap_rh, kThreads, B), kThreads, 0, st2>>>(s, ip, sl.nv, sl.rh, cnt, c->accum, split);
   launches += 1;
   tm.end();
   if ((ip.mask & 4u) && c->D >= 3) {
@@ -685,17 +683,79 @@ cudaError_t run_iteration(neb_ctx* c, int iteration, bool overlap) {
                            c->hits_ph, 2, cnt, st2);
       tm.end();
       tm.begin(STAGE_PHOTON);
-      k_photon<<<B, kThreads, 0, st2>>>(s, ip, j, c->phq[in], in, c->phq[out], out, c->mrec, c->bucket_start, cnt,
+      k_photon<<<capped_blocks(c->cap_ph, kThreads, B), kThreads, 0, st2>>>(s, ip, j, c->phq[in], in, c->phq[out], out, c->mrec, c->bucket_start, cnt,
                                         c->accum, split, c->hits_ph);
       launches += 3;
       tm.end();
     }
   }
-  if (overlap) cudaEventRecord(c->ev_pass23[slot], st2);
+  return launches;
+}
+
+// Records one half of an iteration as a CUDA graph on the private capture
+// stream and refreshes `exec` from it (the topology is the same every
+// iteration; only kernel parameters change), then launches it on `st`.
+// Returns an error, with the capture ended, when any step fails.
+template <typename F>
+static cudaError_t launch_as_graph(neb_ctx* c, cudaGraphExec_t& exec, cudaStream_t st, F&& enqueue) {
+  cudaError_t e = cudaStreamBeginCapture(c->stream_cap, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return e;
+  enqueue(c->stream_cap);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(c->stream_cap, &g);
+  if (e != cudaSuccess) return e;
+  if (exec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(exec, g, &info) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(exec);
+      exec = nullptr;
+    }
+  }
+  if (!exec) e = cudaGraphInstantiate(&exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return e;
+  return cudaGraphLaunch(exec, st);
+}
+
+cudaError_t run_iteration(neb_ctx* c, int iteration, bool overlap) {
+  StageTimer tm(c);  // profiling runs never overlap, so every stage is on c->stream
+  long long launches = 0;
+  if (!overlap) {
+    launches += enqueue_pass1(c, iteration, c->stream, tm);
+    launches += enqueue_pass23(c, iteration, c->stream, tm);
+    c->launches += launches;
+    cudaError_t e = cudaGetLastError();
+    tm.collect();
+    return e;
+  }
+  // Pass 1 on the caller's stream, passes 2-3 on stream_b.  Slot reuse: pass 1
+  // of this iteration waits for passes 2-3 of iteration - 2.
+  const int slot = iteration & 1;
+  cudaStream_t st = c->stream, st2 = c->stream_b;
+  // one half as a graph, or enqueued directly if graphs are off or the
+  // recording fails (then they stay off for this context)
+  auto half = [&](cudaGraphExec_t& exec, cudaStream_t to, auto enqueue) {
+    if (c->use_graphs) {
+      long long n = 0;
+      cudaError_t e = launch_as_graph(c, exec, to, [&](cudaStream_t cs) { n = enqueue(cs); });
+      if (e == cudaSuccess) {
+        launches += n;
+        return;
+      }
+      cudaGetLastError();
+      c->use_graphs = false;
+    }
+    launches += enqueue(to);
+  };
+  cudaStreamWaitEvent(st, c->ev_pass23[slot], 0);
+  half(c->graph_pass1[slot], st, [&](cudaStream_t cs) { return enqueue_pass1(c, iteration, cs, tm); });
+  cudaEventRecord(c->ev_pass1[slot], st);
+  cudaStreamWaitEvent(st2, c->ev_pass1[slot], 0);
+  half(c->graph_pass23[slot], st2, [&](cudaStream_t cs) { return enqueue_pass23(c, iteration, cs, tm); });
+  cudaEventRecord(c->ev_pass23[slot], st2);
   c->launches += launches;
-  cudaError_t e = cudaGetLastError();
-  tm.collect();
-  return e;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_resolve(const double* accum, int P, int iterations, float* out, cudaStream_t st) {

@@ -409,7 +409,7 @@ cudaError_t launch_trace_closest(neb_ctx* c, const float4* recs, const int* coun
   static const int closest_blocks = trace_blocks(k_trace_closest);
   int* fetch = &cnt->fetch[which];
   cudaMemsetAsync(fetch, 0, sizeof(int), st);
-  k_trace_closest<<<closest_blocks, kTraceThreads, 0, st>>>(scene_view(c), recs, count_ptr, cap, fetch, hits, cnt,
+  k_trace_closest<<<capped_blocks(cap, kTraceThreads, closest_blocks), kTraceThreads, 0, st>>>(scene_view(c), recs, count_ptr, cap, fetch, hits, cnt,
                                                             which);
   return cudaGetLastError();
 }
@@ -426,15 +426,15 @@ static CellGrid scene_grid(const neb_ctx* c) {
   return g;
 }
 
-static int group_blocks() { return kGroupBlocks; }
+static int group_blocks(int cap) { return capped_blocks(cap, kGroupThreads, kGroupBlocks); }
 
 cudaError_t launch_group_camera(neb_ctx* c, const CamRay* q, const int* count_ptr, CamRay* out, cudaStream_t st) {
   CellGrid g = scene_grid(c);
   int* counts = c->group_counters;
   int* cursors = c->group_counters + kGroups;
-  k_cam_group_count<<<group_blocks(), kGroupThreads, 0, st>>>(q, count_ptr, c->cap_cam, g, counts);
+  k_cam_group_count<<<group_blocks(c->cap_cam), kGroupThreads, 0, st>>>(q, count_ptr, c->cap_cam, g, counts);
   k_group_scan<<<1, kScanThreads, 0, st>>>(counts, cursors, nullptr);
-  k_cam_group_scatter<<<group_blocks(), kGroupThreads, 0, st>>>(q, count_ptr, c->cap_cam, g, cursors, out);
+  k_cam_group_scatter<<<group_blocks(c->cap_cam), kGroupThreads, 0, st>>>(q, count_ptr, c->cap_cam, g, cursors, out);
   return cudaGetLastError();
 }
 
@@ -442,9 +442,9 @@ cudaError_t launch_group_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st)
   CellGrid g = scene_grid(c);
   int* counts = c->group_counters;
   int* cursors = c->group_counters + kGroups;
-  k_shadow_count<<<group_blocks(), kGroupThreads, 0, st>>>(sl.nv, sl.cnt, c->cap_nee, g, counts);
+  k_shadow_count<<<group_blocks(c->cap_nee), kGroupThreads, 0, st>>>(sl.nv, sl.cnt, c->cap_nee, g, counts);
   k_group_scan<<<1, kScanThreads, 0, st>>>(counts, cursors, &sl.cnt->shadow_count);
-  k_shadow_scatter<<<group_blocks(), kGroupThreads, 0, st>>>(sl.nv, sl.cnt, c->cap_nee, g, cursors,
+  k_shadow_scatter<<<group_blocks(c->cap_nee), kGroupThreads, 0, st>>>(sl.nv, sl.cnt, c->cap_nee, g, cursors,
                                                              c->shadow_rays);
   return cudaGetLastError();
 }
@@ -453,7 +453,7 @@ cudaError_t launch_trace_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st)
   static const int shadow_blocks = trace_blocks(k_trace_shadow);
   int* fetch = &sl.cnt->fetch[1];
   cudaMemsetAsync(fetch, 0, sizeof(int), st);
-  k_trace_shadow<<<shadow_blocks, kTraceThreads, 0, st>>>(scene_view(c), sl.nv, c->shadow_rays, c->cap_nee, fetch,
+  k_trace_shadow<<<capped_blocks(c->cap_nee, kTraceThreads, shadow_blocks), kTraceThreads, 0, st>>>(scene_view(c), sl.nv, c->shadow_rays, c->cap_nee, fetch,
                                                            sl.cnt);
   return cudaGetLastError();
 }
