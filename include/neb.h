@@ -104,13 +104,35 @@ int neb_scene_upload(neb_ctx* ctx, const float* tri, const uint32_t* tri_mat, in
  * (one scale for all axes), stable 4-bit LSD radix sort, then either PLOC
  * (Meister and Bittner 2018: rounds of mutual nearest-neighbour merges by
  * union surface area within +-16 positions of the Morton order; default) or
- * the Karras (HPG 2012) hierarchy with bottom-up bounds.  Leaves hold one
- * primitive; the root is node 0. */
+ * the Karras (HPG 2012) hierarchy with bottom-up bounds; the binary tree is
+ * then collapsed into a 4-wide tree (128-byte nodes, largest-area child
+ * opened first) that all walks use.  Leaves hold one primitive. */
 int neb_build_bvh(neb_ctx* ctx);
 
-/* Enqueues n_iterations NEB iterations on the context stream (asynchronous).
- * Iteration indices continue from the previous call (1-based). */
+/* Enqueues n_iterations NEB iterations (asynchronous).  Iteration indices
+ * continue from the previous call (1-based).  Passes 2-3 of an iteration run
+ * on a second stream owned by the context and overlap pass 1 of the next
+ * iteration; before the call returns, the context stream is made to wait for
+ * the last iteration, so work enqueued on it afterwards sees every result. */
 int neb_iterate(neb_ctx* ctx, int n_iterations);
+
+/* Batched jobs: n_iterations iterations of each of the n contexts, enqueued
+ * round-robin (iteration t of every job before iteration t + 1 of any) so
+ * the jobs' kernels overlap on the GPU.  The contexts must be distinct and on
+ * distinct streams (a NULL stream at neb_create gives each its own); each
+ * job's results are exactly those of neb_iterate on it alone.  Returns after
+ * enqueueing; each context stream waits for its own last iteration.
+ * NEB_ERR_ARG for a null or repeated context, a shared stream, or a context
+ * without its scene and BVH. */
+int neb_iterate_batch(neb_ctx* const* ctxs, int n, int n_iterations);
+
+/* Device bytes a context keeps between iterations for configuration cfg and
+ * a scene of n_tri triangles, n_sph spheres, n_mat materials and n_lights
+ * emissive primitives: the buffers of neb_create, neb_scene_upload and
+ * neb_build_bvh, computed without allocating (the build needs transient
+ * scratch on top).  For admitting many jobs to one GPU.  NEB_ERR_ARG on an
+ * invalid cfg or counts. */
+int neb_job_device_bytes(const neb_config* cfg, int n_tri, int n_sph, int n_mat, int n_lights, uint64_t* out);
 
 /* Progressive result: FP64 per-pixel sums divided by the iteration count,
  * written as [H][W][3] float.  out_is_device: nonzero if rgb_out is device

@@ -70,15 +70,62 @@ static void free_scene(neb_ctx* c) {
   c->scene_ready = c->bvh_ready = false;
 }
 
+static bool config_ok(const neb_config* cfg) {
+  return cfg->width >= 1 && cfg->height >= 1 && cfg->max_depth >= 1 && cfg->max_depth <= kMaxDepth &&
+         cfg->merge_radius > 0.0f && cfg->octree_capacity >= 1 && cfg->split_factor >= 1 &&
+         (cfg->octree_mode == 0 || cfg->octree_mode == 1) && (cfg->density_mode == 0 || cfg->density_mode == 1) &&
+         !(cfg->strategy_mask & ~7u) && (cfg->bvh_builder == 0 || cfg->bvh_builder == 1) &&
+         (long long)cfg->width * cfg->height <= (1ll << 28);
+}
+
+// Queue capacities and hash-table size of a configuration (neb_create).
+struct Capacities {
+  size_t P, cap_cam, cap_nee, cap_rh, cap_ph;
+  uint32_t table;
+};
+static Capacities capacities(const neb_config* cfg) {
+  Capacities k;
+  size_t D = (size_t)cfg->max_depth;
+  k.P = (size_t)cfg->width * cfg->height;
+  k.cap_cam = k.P;
+  k.cap_nee = k.P * (D > 1 ? D - 1 : 1);
+  k.cap_rh = k.P * D;
+  k.cap_ph = k.cap_nee;
+  k.table = 1024;
+  while (k.table < (uint32_t)k.cap_nee) k.table <<= 1;
+  return k;
+}
+
+extern "C" int neb_job_device_bytes(const neb_config* cfg, int n_tri, int n_sph, int n_mat, int n_lights,
+                                    uint64_t* out) {
+  if (!cfg || !out || !config_ok(cfg) || n_tri < 0 || n_sph < 0 || n_mat < 1 || n_lights < 0 ||
+      n_lights > n_tri + n_sph || n_tri + n_sph < 1)
+    return NEB_ERR_ARG;
+  // the buffers of neb_create, neb_scene_upload and neb_build_bvh, in that order
+  const Capacities k = capacities(cfg);
+  const size_t D = (size_t)cfg->max_depth, nee_rows = k.P * (D > 1 ? D - 1 : 1);
+  uint64_t b = 0;
+  b += 3 * k.P * sizeof(CamRay) + 2 * sizeof(DevCounters);
+  b += 2 * (7 * k.cap_nee * sizeof(float4) + k.cap_rh * sizeof(RHEvent) +
+            (cfg->octree_mode == 1 ? nee_rows * sizeof(int) : 0));
+  b += 2 * k.cap_ph * sizeof(PhotonRay) + k.cap_cam * sizeof(int2) + k.cap_ph * sizeof(int2);
+  b += k.cap_nee * (sizeof(MergeRec) + sizeof(int)) + 2 * ((size_t)k.table + 1) * sizeof(int);
+  b += scan_scratch_ints((size_t)k.table + 1) * sizeof(int) + k.P * 3 * sizeof(double);
+  b += cfg->keep_split ? k.P * 9 * sizeof(double) : 0;
+  b += k.cap_nee * sizeof(ShadowRay) + group_counter_ints() * sizeof(int);
+  const size_t nt = (size_t)n_tri, ns = (size_t)n_sph, nl = (size_t)n_lights, np = nt + ns;
+  b += 3 * nt * sizeof(float4) + ns * (sizeof(float4) + sizeof(int)) + 3 * (size_t)n_mat * sizeof(float4);
+  b += np * sizeof(int) + nl * (2 * sizeof(int) + 3 * sizeof(float));
+  b += (1 + (((size_t)cfg->octree_capacity + 7) & ~(size_t)7)) * sizeof(int) + sizeof(OctreeState);
+  b += (np > 1 ? np - 1 : 1) * sizeof(BVH4Node);
+  *out = b;
+  return NEB_OK;
+}
+
 extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** out) {
   if (!cfg || !out) return NEB_ERR_ARG;
   *out = nullptr;
-  if (cfg->width < 1 || cfg->height < 1 || cfg->max_depth < 1 || cfg->max_depth > kMaxDepth ||
-      !(cfg->merge_radius > 0.0f) || cfg->octree_capacity < 1 || cfg->split_factor < 1 ||
-      (cfg->octree_mode != 0 && cfg->octree_mode != 1) || (cfg->density_mode != 0 && cfg->density_mode != 1) ||
-      (cfg->strategy_mask & ~7u) || (cfg->bvh_builder != 0 && cfg->bvh_builder != 1) ||
-      (long long)cfg->width * cfg->height > (1ll << 28))
-    return NEB_ERR_ARG;
+  if (!config_ok(cfg)) return NEB_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return NEB_ERR_NO_DEVICE;
   neb_ctx* c = new (std::nothrow) neb_ctx();
@@ -98,12 +145,12 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
     c->own_stream = true;
   }
   size_t P = (size_t)c->P, D = (size_t)c->D;
-  c->cap_cam = c->P;
-  c->cap_nee = (int)(P * (D > 1 ? D - 1 : 1));
-  c->cap_rh = (int)(P * D);
-  c->cap_ph = c->cap_nee;
-  uint32_t t = 1024;
-  while (t < (uint32_t)c->cap_nee) t <<= 1;
+  const Capacities k = capacities(cfg);
+  c->cap_cam = (int)k.cap_cam;
+  c->cap_nee = (int)k.cap_nee;
+  c->cap_rh = (int)k.cap_rh;
+  c->cap_ph = (int)k.cap_ph;
+  uint32_t t = k.table;
   c->table_size = t;
   c->scan_scratch.n = scan_scratch_ints((size_t)t + 1);
   bool ok = dalloc(&c->camq[0], P) == cudaSuccess && dalloc(&c->camq[1], P) == cudaSuccess &&
@@ -366,22 +413,54 @@ extern "C" int neb_build_bvh(neb_ctx* c) {
   return NEB_OK;
 }
 
+// Passes 2-3 of an iteration overlap pass 1 of the next one (two streams, two
+// buffer slots); stage timing keeps everything on one stream.
+static int iterate_one(neb_ctx* c) {
+  cudaError_t e = run_iteration(c, c->iteration + 1, !c->profiling);
+  if (e != cudaSuccess) return fail(c, NEB_ERR_CUDA, "neb_iterate", e);
+  c->iteration += 1;
+  return NEB_OK;
+}
+
+// The caller's stream waits for the last iteration, so work enqueued on it
+// afterwards sees every result.
+static int join(neb_ctx* c) {
+  if (c->profiling || c->iteration == 0) return NEB_OK;
+  cudaError_t e = cudaStreamWaitEvent(c->stream, c->ev_pass23[c->iteration & 1], 0);
+  return e == cudaSuccess ? NEB_OK : fail(c, NEB_ERR_CUDA, "neb_iterate", e);
+}
+
 extern "C" int neb_iterate(neb_ctx* c, int n_iterations) {
   if (!c || n_iterations < 0) return NEB_ERR_ARG;
   if (!c->bvh_ready) return fail(c, NEB_ERR_ARG, "neb_iterate: call neb_scene_upload and neb_build_bvh first");
-  // Passes 2-3 of an iteration overlap pass 1 of the next one (two streams,
-  // two buffer slots); stage timing keeps everything on one stream.  The
-  // caller's stream waits for the last iteration before the call returns, so
-  // work enqueued on it afterwards sees every result.
-  const bool overlap = !c->profiling;
   for (int i = 0; i < n_iterations; ++i) {
-    cudaError_t e = run_iteration(c, c->iteration + 1, overlap);
-    if (e != cudaSuccess) return fail(c, NEB_ERR_CUDA, "neb_iterate", e);
-    c->iteration += 1;
+    int rc = iterate_one(c);
+    if (rc != NEB_OK) return rc;
   }
-  if (overlap && n_iterations > 0) {
-    cudaError_t e = cudaStreamWaitEvent(c->stream, c->ev_pass23[c->iteration & 1], 0);
-    if (e != cudaSuccess) return fail(c, NEB_ERR_CUDA, "neb_iterate", e);
+  return n_iterations > 0 ? join(c) : NEB_OK;
+}
+
+extern "C" int neb_iterate_batch(neb_ctx* const* ctxs, int n, int n_iterations) {
+  if (n < 0 || n_iterations < 0 || (n > 0 && !ctxs)) return NEB_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return NEB_ERR_ARG;
+    if (!ctxs[i]->bvh_ready)
+      return fail(ctxs[i], NEB_ERR_ARG, "neb_iterate_batch: every job needs its scene and BVH first");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i] || ctxs[j]->stream == ctxs[i]->stream)
+        return fail(ctxs[i], NEB_ERR_ARG, "neb_iterate_batch: jobs must be distinct contexts on distinct streams");
+  }
+  // Round-robin: iteration t of every job is enqueued before iteration t + 1
+  // of any, so the jobs' kernels overlap on the GPU; each job's own order and
+  // results are those of neb_iterate.
+  for (int t = 0; t < n_iterations; ++t)
+    for (int i = 0; i < n; ++i) {
+      int rc = iterate_one(ctxs[i]);
+      if (rc != NEB_OK) return rc;
+    }
+  for (int i = 0; i < n && n_iterations > 0; ++i) {
+    int rc = join(ctxs[i]);
+    if (rc != NEB_OK) return rc;
   }
   return NEB_OK;
 }

@@ -26,7 +26,7 @@ EXPORTS = ["neb_create", "neb_destroy", "neb_last_error", "neb_scene_upload", "n
            "neb_set_profiling", "neb_get_stage_times", "neb_trace_closest", "neb_philox", "neb_plane_box_area",
            "neb_octree_create", "neb_octree_destroy", "neb_octree_set_iteration", "neb_octree_insert",
            "neb_octree_density", "neb_octree_read", "neb_octree_load", "neb_count_neighbours",
-           "neb_count_neighbours_noalloc"]
+           "neb_count_neighbours_noalloc", "neb_iterate_batch", "neb_job_device_bytes"]
 NOALLOC_MAX_POINTS = 1 << 18
 
 
@@ -98,6 +98,8 @@ def lib():
             "neb_octree_density": ([vp, vp, vp, C.c_int, C.c_int, vp], C.c_int),
             "neb_octree_read": ([vp, vp, C.c_int, vp], C.c_int),
             "neb_octree_load": ([vp, vp, C.c_int, C.c_int, C.c_int], C.c_int),
+            "neb_iterate_batch": ([vp, C.c_int, C.c_int], C.c_int),
+            "neb_job_device_bytes": ([vp, C.c_int, C.c_int, C.c_int, C.c_int, vp], C.c_int),
             "neb_count_neighbours": ([vp, C.c_int, vp, C.c_int, C.c_float, vp], C.c_int),
             "neb_count_neighbours_noalloc": ([vp, C.c_int, vp, C.c_int, C.c_float, vp, vp], C.c_int),
         }
@@ -293,6 +295,22 @@ class Octree:
     def load(self, nodes, alloc, depth):
         N = np.ascontiguousarray(nodes, np.int32)
         _check(lib().neb_octree_load(self.h, _p(N), len(N), int(alloc), int(depth)))
+
+
+def iterate_batch(contexts, n_iterations):
+    """Batched jobs (neb_iterate_batch): n_iterations iterations of every
+    context, enqueued round-robin so the jobs overlap on the GPU."""
+    arr = (vp * max(len(contexts), 1))(*[c.h for c in contexts])
+    rc = lib().neb_iterate_batch(arr, len(contexts), int(n_iterations))
+    _check(rc, contexts[0].h if (rc != NEB_OK and contexts) else None)
+
+
+def job_device_bytes(cfg: "Config", n_tri, n_sph, n_mat, n_lights):
+    """Device bytes a job keeps resident (neb_job_device_bytes)."""
+    out = C.c_uint64(0)
+    _check(lib().neb_job_device_bytes(C.byref(cfg), int(n_tri), int(n_sph), int(n_mat), int(n_lights),
+                                      C.byref(out)))
+    return int(out.value)
 
 
 def render(scene, rc, n_iter=None, keep_split=True, stream=None, **over):

@@ -72,6 +72,12 @@ class Scene:
     def n_sph(self):
         return len(self.sph)
 
+    @property
+    def n_emitters(self):
+        """Primitives whose material emits (the light list of neb_scene_upload)."""
+        emits = self.mats[:, 4:7].sum(axis=1) > 0.0
+        return int(emits[self.tri_mat].sum() + emits[self.sph_mat].sum())
+
 
 @dataclasses.dataclass
 class RenderConfig:
@@ -394,6 +400,36 @@ def glass_in_emitting_box(ior=1.5, radius=0.25, subdiv=3) -> Scene:
     tri_mat = np.array([0] * len(walls) + [1] * len(ball), np.uint32)
     cam = _camera((0.5, 0.5, 0.05), (0.5, 0.5, 0.6), (0, 1, 0), 60.0)
     return Scene(tri, tri_mat, np.zeros((0, 4)), np.zeros(0), mats, cam, "glass_in_emitting_box")
+
+
+def batch_jobs(n: int, seed: int = 0, iterations: int = 64):
+    """A seeded mix of n heterogeneous render jobs, [(scene, RenderConfig)].
+
+    A quarter are the room of the tiny-room workload (1,292 triangles, a
+    two-triangle emitter, D = 8, r = 0.01, split 8), the rest cities of the large-city
+    generator with a grid of g x g boxes, g log-uniform in [9, 200] (~26k to
+    ~500k triangles with the torus and ground), 1 to 64 sphere lights
+    (log-uniform), D = 10, r = 1e-3 of the torus extent, split 4.  Image sides
+    are log-uniform in [128, 1024] (multiples of 16, square); octree capacity
+    4 nodes per pixel, within [2^16, 2^22].  Job i renders with Philox seed i.
+    """
+    rng = SplitMix64(0xBA7C4 + 7919 * seed)
+    u = rng.uniform(4 * n).reshape(n, 4)
+    out = []
+    for i in range(n):
+        side = int(round(128.0 * 8.0 ** u[i, 1] / 16.0)) * 16
+        cap = int(min(1 << 22, max(1 << 16, 4 * side * side)))
+        if u[i, 0] < 0.25:
+            sc = tiny_room()
+            rc = RenderConfig(side, side, 8, 0.01, cap, 8, iterations, seed=i)
+        else:
+            grid = int(round(9.0 * (200.0 / 9.0) ** u[i, 3]))
+            n_lights = int(round(64.0 ** u[i, 2]))
+            sc = large_city(seed=i + 1, grid=grid, n_lights=n_lights)
+            torus_extent = math.sqrt(grid * grid * 2 + 400.0) / 1000.0
+            rc = RenderConfig(side, side, 10, 1e-3 * torus_extent, cap, 4, iterations, seed=i)
+        out.append((sc, rc))
+    return out
 
 
 def workload(name: str):

@@ -51,6 +51,33 @@ def test_argument_errors_without_gpu(libneb):
     assert L.neb_philox(None, -1, None, None) == -1
 
 
+def test_batch_and_admission_arguments_without_gpu(libneb):
+    """neb_iterate_batch rejects bad arguments before any device call, an empty
+    batch is a no-op, and neb_job_device_bytes is a pure host computation."""
+    from paper_1909_00573_gb300 import neb, scenes
+    L = neb.lib()
+    assert L.neb_iterate_batch(None, -1, 1) == neb.ERR_ARG
+    assert L.neb_iterate_batch(None, 2, 1) == neb.ERR_ARG
+    assert L.neb_iterate_batch(None, 0, 3) == neb.NEB_OK
+    arr = (ctypes.c_void_p * 2)(None, None)
+    assert L.neb_iterate_batch(arr, 2, 1) == neb.ERR_ARG
+    s, rc = scenes.workload("large_city")
+    cfg = neb.make_config(rc)
+    b = neb.job_device_bytes(cfg, s.n_tri, s.n_sph, len(s.mats), s.n_emitters)
+    # two NEE slots of 112 B per vertex dominate: 2 x 921,600 x 9 x 112 B
+    assert 2 * 921600 * 9 * 112 < b < 6e9
+    split = neb.job_device_bytes(neb.make_config(rc, keep_split=True), s.n_tri, s.n_sph, len(s.mats),
+                                 s.n_emitters)
+    assert split - b == 921600 * 9 * 8                          # the FP64 per-strategy split
+    rc2 = scenes.RenderConfig(2 * rc.width, rc.height, rc.max_depth, rc.merge_radius, rc.octree_capacity,
+                              rc.split_factor, 1)
+    assert neb.job_device_bytes(neb.make_config(rc2), s.n_tri, s.n_sph, len(s.mats), s.n_emitters) > b
+    with pytest.raises(neb.NebError):
+        neb.job_device_bytes(cfg, 0, 0, len(s.mats), 0)        # empty scene
+    with pytest.raises(neb.NebError):
+        neb.job_device_bytes(cfg, 10, 0, 1, 11)                 # more lights than primitives
+
+
 def test_product_path_does_not_import_the_oracle():
     """The package never reaches into oracle/ (the oracle is test infrastructure)."""
     pkg = os.path.join(ROOT, "paper_1909_00573_gb300")

@@ -1,0 +1,77 @@
+"""Batched jobs (neb_iterate_batch) and admission (neb_job_device_bytes) on
+the GPU: every job's result is the same alone and in the batch, and the
+device-memory estimate matches what a job allocates."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def neb():
+    from paper_1909_00573_gb300 import build
+    build.build()
+    from paper_1909_00573_gb300 import neb as N
+    return N
+
+
+def _jobs():
+    from paper_1909_00573_gb300 import scenes
+    room = scenes.tiny_room()
+    out = [(room, scenes.RenderConfig(96, 80, 8, 0.01, 1 << 16, 8, 3, seed=11, octree_mode=1))]
+    for i, (g, nl, side) in enumerate([(12, 3, 128), (20, 9, 144)]):
+        s = scenes.large_city(seed=i + 3, grid=g, n_lights=nl)
+        out.append((s, scenes.RenderConfig(side, side, 10, 2e-3, 1 << 18, 4, 3, seed=20 + i, octree_mode=1)))
+    return out
+
+
+def _start(neb, s, rc):
+    ctx = neb.Context(neb.make_config(rc))
+    ctx.scene_upload(s)
+    ctx.build_bvh()
+    return ctx
+
+
+def test_batch_results_equal_alone(neb):
+    """Three heterogeneous jobs (a room and two cities of different sizes,
+    resolutions, light counts and seeds), deterministic octree: each job's
+    densities are bit-identical and its FP64 sums equal up to the order of the
+    atomic additions whether it runs alone or round-robin with the others."""
+    jobs = _jobs()
+    alone = []
+    for s, rc in jobs:
+        ctx = _start(neb, s, rc)
+        ctx.iterate(rc.iterations)
+        alone.append((ctx.read_nee_rho(), ctx.read_accum(), ctx.stats()))
+        ctx.close()
+    ctxs = [_start(neb, s, rc) for s, rc in jobs]
+    neb.iterate_batch(ctxs, jobs[0][1].iterations)
+    for ctx, (rho, acc, st) in zip(ctxs, alone):
+        r2, a2, st2 = ctx.read_nee_rho(), ctx.read_accum(), ctx.stats()
+        assert np.array_equal(rho, r2)
+        np.testing.assert_allclose(a2, acc, rtol=1e-12, atol=1e-12 * float(np.abs(acc).max()))
+        for key in ("iterations", "camera_rays", "nee_vertices", "shadow_rays", "photons", "merge_tests", "merges",
+                    "octree_inserts", "octree_nodes"):
+            assert st2[key] == st[key], key
+        assert acc.sum() > 0
+        ctx.close()
+
+
+def test_job_device_bytes_matches_allocation(neb):
+    """neb_job_device_bytes predicts the device memory a job holds after
+    neb_create, neb_scene_upload and neb_build_bvh."""
+    torch = pytest.importorskip("torch")
+    from paper_1909_00573_gb300 import scenes
+    s, rc = scenes.workload("large_city")
+    rc.width, rc.height = 640, 360
+    cfg = neb.make_config(rc)
+    expect = neb.job_device_bytes(cfg, s.n_tri, s.n_sph, len(s.mats), s.n_emitters)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    ctx = neb.Context(cfg)
+    ctx.scene_upload(s)
+    ctx.build_bvh()
+    torch.cuda.synchronize()
+    used = free0 - torch.cuda.mem_get_info()[0]
+    ctx.close()
+    assert abs(used - expect) <= 0.05 * expect + (64 << 20), (used, expect)
