@@ -131,14 +131,8 @@ __global__ void k_grid_scatter(NeeStore nv, DevCounters* cnt, int cap, const int
     int b = vert_bucket[i];
     if (b < 0) continue;
     int slot = bucket_start[b] + atomicSub(bucket_count + b, 1) - 1;
-    float4 nn = nv.nrm[i];
-    int bits = __float_as_int(nn.w);
-    MergeRec r;
-    r.pos = nv.pos[i];
-    r.nrm = make_float4(nn.x, nn.y, nn.z, __int_as_float(bits & ((1 << NV_FLAG_SHIFT) - 1)));
-    r.wo = nv.wo[i];
-    r.tau = nv.tau[i];
-    out[slot] = r;
+    float4 p = nv.pos[i];
+    out[slot].pos = make_float4(p.x, p.y, p.z, __int_as_float(i));
   }
 }
 

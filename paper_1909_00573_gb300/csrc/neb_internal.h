@@ -45,12 +45,11 @@ struct __align__(16) ShadowRay {
   float4 d;  // direction to the light point, w: NEE id (int bits)
 };
 
-// Grid-ordered copy of a mergeable view vertex (64 bytes).
+// Grid-ordered entry of a mergeable view vertex (16 bytes): its position and
+// its NEE id; the merge reads the rest of the vertex from the NEE store for
+// the few candidates within the radius.
 struct __align__(16) MergeRec {
-  float4 pos;  // xyz, w: Cfac
-  float4 nrm;  // geometric normal, w: mat | (k << 20) (int bits)
-  float4 wo;   // direction to x_{k-1}, w: pixel (int bits)
-  float4 tau;  // throughput, w unused
+  float4 pos;  // xyz, w: NEE id (int bits)
 };
 
 // NEE vertex store, structure of arrays (one float4 per field).

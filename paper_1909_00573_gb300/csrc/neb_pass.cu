@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(kThreads) k_emission(SceneView s, IterParams i
 // (inverted search of Sec. 3.2), then the next scattering.
 __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip, int j, const PhotonRay* __restrict__ in,
                                                      int in_slot, PhotonRay* __restrict__ out, int out_slot,
-                                                     const MergeRec* __restrict__ mrec,
+                                                     NeeStore nv, const MergeRec* __restrict__ mrec,
                                                      const int* __restrict__ bucket_start, DevCounters* cnt,
                                                      double* accum, double* split, const int2* __restrict__ hits) {
   const int count = min(cnt->ph_count[in_slot], ip.cap_ph);
@@ -489,18 +489,19 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
       float d2 = dx * dx + dy * dy + dz * dz;
       ++tests;
       if (!(d2 <= ip.r2)) continue;
-      float4 mn = __ldg(&mrec[e].nrm);
+      const int id = __float_as_int(mp.w);  // the view vertex, from the NEE store
+      float4 mn = __ldg(&nv.nrm[id]);
       int mb = __float_as_int(mn.w);
       int kk = (mb >> NV_K_SHIFT) & 63;
       if (kk + j + 1 > ip.D) continue;
       Mat cm = load_mat(s.mats, mb & NV_MAT_MASK);
-      float4 mw = __ldg(&mrec[e].wo);
+      float4 mw = __ldg(&nv.wo[id]);
       float3 cn = xyz(mn), cwo = xyz(mw);
       float3 f = bsdf_eval(cm, cn, cwo, md);
       if (!(maxc(f) > 0.0f)) continue;
       float pdfF = bsdf_pdf(cm, cn, cwo, md), pdfC = bsdf_pdf(cm, cn, md, cwo);
-      float inv_w = 1.0f + pdfF * s1 + pdfC * mp.w;
-      float3 ctau = xyz(__ldg(&mrec[e].tau));
+      float inv_w = 1.0f + pdfF * s1 + pdfC * __ldg(&nv.pos[id].w);
+      float3 ctau = xyz(__ldg(&nv.tau[id]));
       float3 L3 = mul(cmul(cmul(ctau, f), phi), ip.kernel / inv_w);
       add_pixel(accum, split, 2, __float_as_int(mw.w), L3, P);
       ++merges;
@@ -683,7 +684,7 @@ static long long enqueue_pass23(neb_ctx* c, int iteration, cudaStream_t st2, Sta
                            c->hits_ph, 2, cnt, st2);
       tm.end();
       tm.begin(STAGE_PHOTON);
-      k_photon<<<capped_blocks(c->cap_ph, kThreads, B), kThreads, 0, st2>>>(s, ip, j, c->phq[in], in, c->phq[out], out, c->mrec, c->bucket_start, cnt,
+      k_photon<<<capped_blocks(c->cap_ph, kThreads, B), kThreads, 0, st2>>>(s, ip, j, c->phq[in], in, c->phq[out], out, sl.nv, c->mrec, c->bucket_start, cnt,
                                         c->accum, split, c->hits_ph);
       launches += 3;
       tm.end();
