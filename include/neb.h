@@ -66,6 +66,9 @@ typedef struct {
   uint32_t strategy_mask;/* bit 0 random hit (e), bit 1 NEE (E), bit 2 NEB photon merge (P) */
   int keep_split;        /* nonzero: keep the last iteration's contributions split by strategy */
   int bvh_builder;       /* 0 PLOC clustering over the Morton order (default), 1 Karras LBVH */
+  int photon_records;    /* photon queue records: 0 FP32 (64 bytes), 1 packed (48 bytes: FP32
+                            origin and MIS factors, RGB flux as three FP16 mantissas of a shared
+                            power-of-two scale, direction octahedral with 16 bits per coordinate) */
 } neb_config;
 
 typedef struct {

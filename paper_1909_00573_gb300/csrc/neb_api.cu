@@ -75,6 +75,7 @@ static bool config_ok(const neb_config* cfg) {
          cfg->merge_radius > 0.0f && cfg->octree_capacity >= 1 && cfg->split_factor >= 1 &&
          (cfg->octree_mode == 0 || cfg->octree_mode == 1) && (cfg->density_mode == 0 || cfg->density_mode == 1) &&
          !(cfg->strategy_mask & ~7u) && (cfg->bvh_builder == 0 || cfg->bvh_builder == 1) &&
+         (cfg->photon_records == 0 || cfg->photon_records == 1) &&
          (long long)cfg->width * cfg->height <= (1ll << 28);
 }
 

@@ -231,6 +231,38 @@ __device__ __forceinline__ bool bsdf_sample(const Mat& m, float3 n, float3 wo, f
 #define NEB_GAMMA5 2.98023313e-07f
 #define NEB_GAMMA7 4.17232688e-07f
 
+// Octahedral unit-vector code with 16 bits per coordinate (Meyer et al.,
+// "On Floating-Point Normal Vectors", EGSR 2010): project onto the octahedron
+// |x| + |y| + |z| = 1, fold the lower half over the diagonals, round each
+// coordinate to a signed 16-bit integer.  Angular error about 3e-5 rad.
+__device__ __forceinline__ float2 oct_fold(float px, float py) {
+  return make_float2((1.0f - fabsf(py)) * (px >= 0.0f ? 1.0f : -1.0f),
+                     (1.0f - fabsf(px)) * (py >= 0.0f ? 1.0f : -1.0f));
+}
+__device__ __forceinline__ uint32_t oct_encode16(float3 n) {
+  float s = fabsf(n.x) + fabsf(n.y) + fabsf(n.z);
+  float px = n.x / s, py = n.y / s;
+  if (n.z < 0.0f) {
+    float2 f = oct_fold(px, py);
+    px = f.x;
+    py = f.y;
+  }
+  int qx = __float2int_rn(fminf(fmaxf(px, -1.0f), 1.0f) * 32767.0f);
+  int qy = __float2int_rn(fminf(fmaxf(py, -1.0f), 1.0f) * 32767.0f);
+  return (uint32_t)(qx & 0xffff) | ((uint32_t)(qy & 0xffff) << 16);
+}
+__device__ __forceinline__ float3 oct_decode16(uint32_t v) {
+  float px = (float)(short)(v & 0xffffu) * (1.0f / 32767.0f), py = (float)(short)(v >> 16) * (1.0f / 32767.0f);
+  float nz = 1.0f - fabsf(px) - fabsf(py);
+  if (nz < 0.0f) {
+    float2 f = oct_fold(px, py);
+    px = f.x;
+    py = f.y;
+  }
+  float l = sqrtf(px * px + py * py + nz * nz);
+  return make_float3(px / l, py / l, nz / l);
+}
+
 struct RayPre {
   float3 o, d, inv;
   int kx, ky, kz;

@@ -39,6 +39,16 @@ struct __align__(16) PhotonRay {
   float4 mis;  // x E0, y pA, z pB, w: k_nee | (j << 8), j = index of the next hit
 };
 
+// Packed photon ray (48 bytes): origin and MIS factors in FP32; the RGB flux
+// as three FP16 mantissas of a shared power-of-two scale; the direction as
+// two 16-bit octahedral coordinates (Meyer et al. 2010).
+struct __align__(16) PackedPhoton {
+  float4 o;    // origin, w: pixel (int bits)
+  float4 mis;  // E0, pA, pB, pdf_dir
+  uint4 q;     // x: direction (u16 x, u16 y); y: flux r, g (FP16); z: flux b, cos_orig (FP16);
+               // w: k_nee | j << 8 | (flux exponent + 128) << 16
+};
+
 // Shadow ray of an NEE vertex in light-grouped order (32 bytes).
 struct __align__(16) ShadowRay {
   float4 o;  // offset origin, w: tmax = (1 - 1e-4) distance to the light point
@@ -230,8 +240,9 @@ cudaError_t launch_oct_insert_nee(neb_ctx* c, const IterSlot& sl, cudaStream_t s
 cudaError_t launch_oct_density_nee(neb_ctx* c, const IterSlot& sl, cudaStream_t st);
 
 // neb_trace.cu
+// packed: recs are PackedPhoton records (direction in octahedral form)
 cudaError_t launch_trace_closest(neb_ctx* c, const float4* recs, const int* count_ptr, int cap, int2* hits,
-                                 int which, DevCounters* cnt, cudaStream_t st);
+                                 int which, DevCounters* cnt, cudaStream_t st, int packed = 0);
 // groups the slot's shadow rays into c->shadow_rays, then walks them
 cudaError_t launch_group_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st);
 cudaError_t launch_trace_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st);

@@ -15,6 +15,8 @@
 //   and B_k = sum over photon vertices of ok(k') prod F_{i+1}/R_i.
 // n_T cancels (n_P = n_T).  Squared distances cancel between F and R, so only
 // cosines and directional pdfs are carried.
+#include <cuda_fp16.h>
+
 #include <cfloat>
 #include <cstdio>
 
@@ -25,6 +27,50 @@
 namespace neb {
 
 constexpr int kThreads = 256;
+
+// ---- photon queue records: PhotonRay (64 bytes) or PackedPhoton (48 bytes)
+union Half2Bits {
+  __half2 h;
+  uint32_t u;
+};
+
+__device__ __forceinline__ void store_photon(void* q, int slot, const PhotonRay& ph, int packed) {
+  if (!packed) {
+    reinterpret_cast<PhotonRay*>(q)[slot] = ph;
+    return;
+  }
+  PackedPhoton pk;
+  pk.o = ph.o;
+  pk.mis = make_float4(ph.mis.x, ph.mis.y, ph.mis.z, ph.d.w);
+  float m = fmaxf(fmaxf(ph.phi.x, ph.phi.y), ph.phi.z);
+  int e = 0;
+  if (m > 0.0f) frexpf(m, &e);  // m = f 2^e with f in [0.5, 1)
+  e = min(max(e, -126), 127);
+  const float sc = ldexpf(1.0f, -e);
+  Half2Bits rg, bc;
+  rg.h = __floats2half2_rn(ph.phi.x * sc, ph.phi.y * sc);
+  bc.h = __floats2half2_rn(ph.phi.z * sc, ph.phi.w);
+  pk.q = make_uint4(oct_encode16(xyz(ph.d)), rg.u, bc.u,
+                    ((uint32_t)__float_as_int(ph.mis.w) & 0xffffu) | ((uint32_t)(e + 128) << 16));
+  reinterpret_cast<PackedPhoton*>(q)[slot] = pk;
+}
+
+__device__ __forceinline__ PhotonRay load_photon(const void* q, int i, int packed) {
+  if (!packed) return reinterpret_cast<const PhotonRay*>(q)[i];
+  const PackedPhoton pk = reinterpret_cast<const PackedPhoton*>(q)[i];
+  PhotonRay ph;
+  float3 d = oct_decode16(pk.q.x);
+  const float sc = ldexpf(1.0f, (int)(pk.q.w >> 16) - 128);
+  Half2Bits rg, bc;
+  rg.u = pk.q.y;
+  bc.u = pk.q.z;
+  float2 frg = __half22float2(rg.h), fbc = __half22float2(bc.h);
+  ph.o = pk.o;
+  ph.d = make_float4(d.x, d.y, d.z, pk.mis.w);
+  ph.phi = make_float4(frg.x * sc, frg.y * sc, fbc.x * sc, fbc.y);
+  ph.mis = make_float4(pk.mis.x, pk.mis.y, pk.mis.z, __int_as_float((int)(pk.q.w & 0xffffu)));
+  return ph;
+}
 
 static int grid_blocks() {
   static int blocks = 0;
@@ -263,7 +309,7 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
 // pass 2: NEE contributions and photon emission from the NEE vertices
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_nee(SceneView s, IterParams ip, NeeStore nv, DevCounters* cnt,
-                                                  double* accum, double* split, PhotonRay* __restrict__ phq) {
+                                                  double* accum, double* split, void* __restrict__ phq, int packed) {
   const int count = min(cnt->nee_count, ip.cap_nee);
   const int stride = gridDim.x * blockDim.x;
   const int P = ip.W * ip.H;
@@ -315,7 +361,7 @@ __global__ void __launch_bounds__(kThreads) k_nee(SceneView s, IterParams ip, Ne
       }
     }
     int slot = warp_append(&cnt->ph_count[0], emit, ip.cap_ph, &cnt->status);
-    if (emit && slot >= 0) phq[slot] = ph;
+    if (emit && slot >= 0) store_photon(phq, slot, ph, packed);
     warp_count(&cnt->photons, nphot);
   }
 }
@@ -352,8 +398,8 @@ __global__ void __launch_bounds__(kThreads) k_emission(SceneView s, IterParams i
 
 // Photon walk: closest hit, merge with the view vertices of the hashed grid
 // (inverted search of Sec. 3.2), then the next scattering.
-__global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip, int j, const PhotonRay* __restrict__ in,
-                                                     int in_slot, PhotonRay* __restrict__ out, int out_slot,
+__global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip, int j, const void* __restrict__ in,
+                                                     int in_slot, void* __restrict__ out, int out_slot, int packed,
                                                      NeeStore nv, const MergeRec* __restrict__ mrec,
                                                      const int* __restrict__ bucket_start, DevCounters* cnt,
                                                      double* accum, double* split, const int2* __restrict__ hits) {
@@ -369,7 +415,7 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
     float3 m_p = f3(0, 0, 0), m_d = f3(0, 0, 0), m_phi = f3(0, 0, 0);
     float m_s1 = 0.0f;
     if (i < count) {
-      PhotonRay ph = in[i];
+      PhotonRay ph = load_photon(in, i, packed);
       float3 d = xyz(ph.d);
       RayPre r = make_ray(xyz(ph.o), d);
       int2 hh = hits[i];
@@ -507,7 +553,7 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
       ++merges;
     }
     int slot = warp_append(&cnt->ph_count[out_slot], emit, ip.cap_ph, &cnt->status);
-    if (emit && slot >= 0) out[slot] = nph;
+    if (emit && slot >= 0) store_photon(out, slot, nph, packed);
     warp_count(&cnt->photon_hits, nhits);
     warp_count(&cnt->merge_tests, tests);
     warp_count(&cnt->merges, merges);
@@ -662,7 +708,8 @@ static long long enqueue_pass23(neb_ctx* c, int iteration, cudaStream_t st2, Sta
   launch_oct_density_nee(c, sl, st2);
   tm.end();
   tm.begin(STAGE_NEE);
-  k_nee<<<capped_blocks(c->cap_nee, kThreads, B), kThreads, 0, st2>>>(s, ip, sl.nv, cnt, c->accum, split, c->phq[0]);
+  k_nee<<<capped_blocks(c->cap_nee, kThreads, B), kThreads, 0, st2>>>(s, ip, sl.nv, cnt, c->accum, split, c->phq[0],
+                                                                        c->cfg.photon_records);
   tm.end();
   launches += 2;
   if ((ip.mask & 4u) && c->D >= 3) {
@@ -681,10 +728,10 @@ static long long enqueue_pass23(neb_ctx* c, int iteration, cudaStream_t st2, Sta
       k_reset_photon_slot<<<1, 1, 0, st2>>>(cnt, out);
       tm.begin(STAGE_TRACE_PHOTON);
       launch_trace_closest(c, reinterpret_cast<const float4*>(c->phq[in]), &cnt->ph_count[in], c->cap_ph,
-                           c->hits_ph, 2, cnt, st2);
+                           c->hits_ph, 2, cnt, st2, c->cfg.photon_records);
       tm.end();
       tm.begin(STAGE_PHOTON);
-      k_photon<<<capped_blocks(c->cap_ph, kThreads, B), kThreads, 0, st2>>>(s, ip, j, c->phq[in], in, c->phq[out], out, sl.nv, c->mrec, c->bucket_start, cnt,
+      k_photon<<<capped_blocks(c->cap_ph, kThreads, B), kThreads, 0, st2>>>(s, ip, j, c->phq[in], in, c->phq[out], out, c->cfg.photon_records, sl.nv, c->mrec, c->bucket_start, cnt,
                                         c->accum, split, c->hits_ph);
       launches += 3;
       tm.end();

@@ -94,10 +94,12 @@ __device__ __forceinline__ int fetch_rays(int cur, int* fetch, int count) {
 
 // Closest hit for a queue of 64-byte records (origin in float4 0, direction in
 // float4 1: CamRay and PhotonRay).  hits[i] = (prim, t bits), prim -1 on a miss.
+// packed: records are PackedPhoton (48 bytes, direction in the octahedral
+// word) instead of 64-byte records with the direction in float4 1.
 __global__ void __launch_bounds__(kTraceThreads) k_trace_closest(SceneView s, const float4* __restrict__ recs,
                                                                  const int* __restrict__ count_ptr, int cap,
                                                                  int* __restrict__ fetch, int2* __restrict__ hits,
-                                                                 DevCounters* cnt, int which) {
+                                                                 DevCounters* cnt, int which, int packed) {
   const int count = min(*count_ptr, cap);
   int ray = kIdle;
   RayPre r;
@@ -107,8 +109,10 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_closest(SceneView s, co
   while (true) {
     int nr = fetch_rays(ray, fetch, count);
     if (ray == kIdle && nr >= 0) {
-      float4 o = __ldg(recs + 4 * (size_t)nr), d = __ldg(recs + 4 * (size_t)nr + 1);
-      r = make_ray(xyz(o), xyz(d));
+      const float4* rec = recs + (packed ? 3 : 4) * (size_t)nr;
+      float4 o = __ldg(rec);
+      float3 d = packed ? oct_decode16(__ldg(reinterpret_cast<const uint4*>(rec + 2)).x) : xyz(__ldg(rec + 1));
+      r = make_ray(xyz(o), d);
       walk_init(w);
       if (s.nt + s.ns == 0) {
         hits[nr] = make_int2(-1, __float_as_int(FLT_MAX));
@@ -405,12 +409,12 @@ static int trace_blocks(K kernel) {
 }
 
 cudaError_t launch_trace_closest(neb_ctx* c, const float4* recs, const int* count_ptr, int cap, int2* hits,
-                                 int which, DevCounters* cnt, cudaStream_t st) {
+                                 int which, DevCounters* cnt, cudaStream_t st, int packed) {
   static const int closest_blocks = trace_blocks(k_trace_closest);
   int* fetch = &cnt->fetch[which];
   cudaMemsetAsync(fetch, 0, sizeof(int), st);
   k_trace_closest<<<capped_blocks(cap, kTraceThreads, closest_blocks), kTraceThreads, 0, st>>>(scene_view(c), recs, count_ptr, cap, fetch, hits, cnt,
-                                                            which);
+                                                            which, packed);
   return cudaGetLastError();
 }
 

@@ -40,7 +40,7 @@ class Config(C.Structure):
     _fields_ = [("width", C.c_int), ("height", C.c_int), ("max_depth", C.c_int), ("merge_radius", C.c_float),
                 ("octree_capacity", C.c_int), ("split_factor", C.c_int), ("seed", C.c_uint64),
                 ("octree_mode", C.c_int), ("density_mode", C.c_int), ("strategy_mask", C.c_uint32),
-                ("keep_split", C.c_int), ("bvh_builder", C.c_int)]
+                ("keep_split", C.c_int), ("bvh_builder", C.c_int), ("photon_records", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -121,12 +121,14 @@ def _check(rc, ctx=None):
         raise NebError(rc, msg)
 
 
-def make_config(rc, keep_split=False, octree_mode=None, density_mode=None, strategy_mask=None, bvh_builder=0):
+def make_config(rc, keep_split=False, octree_mode=None, density_mode=None, strategy_mask=None, bvh_builder=0,
+                photon_records=0):
     """neb_config from a scenes.RenderConfig."""
     return Config(rc.width, rc.height, rc.max_depth, rc.merge_radius, rc.octree_capacity, rc.split_factor,
                   rc.seed, rc.octree_mode if octree_mode is None else octree_mode,
                   rc.density_mode if density_mode is None else density_mode,
-                  rc.strategy_mask if strategy_mask is None else strategy_mask, int(keep_split), int(bvh_builder))
+                  rc.strategy_mask if strategy_mask is None else strategy_mask, int(keep_split), int(bvh_builder),
+                  int(photon_records))
 
 
 class Context:

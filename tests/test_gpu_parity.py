@@ -354,6 +354,37 @@ def test_overlapped_iterations_equal_sequential(neb):
     assert a0.sum() > 0
 
 
+def test_packed_photon_records_error(neb, oracle):
+    """Photon queue records packed to 48 bytes (FP16 flux mantissas, 16-bit
+    octahedral direction) against 64-byte FP32 records and the oracle, on the
+    tiny room (deterministic octree, 4 iterations).  FP32 records reproduce
+    the oracle's image; packed records change photon directions by ~3e-5 rad
+    and fluxes by ~2^-11 relative, which moves only the photon-merge part."""
+    from paper_1909_00573_gb300 import scenes
+    s, rc = scenes.workload("tiny_room")
+    rc.octree_mode = 1
+    ref = oracle.render(s, rc)
+    o = ref["accum"].reshape(-1)
+    out = {}
+    for packed in (0, 1):
+        ctx = neb.Context(neb.make_config(rc, keep_split=True, photon_records=packed))
+        ctx.scene_upload(s)
+        ctx.build_bvh()
+        ctx.iterate(rc.iterations)
+        out[packed] = (ctx.read_accum().reshape(-1), ctx.read_split(), ctx.stats())
+        ctx.close()
+    rel = {k: float(np.linalg.norm(v[0] - o) / np.linalg.norm(o)) for k, v in out.items()}
+    assert rel[0] < 1e-3, rel
+    assert rel[1] < 2e-2, rel
+    # random hits and NEE are untouched by the photon record format
+    for strat in (0, 1):
+        np.testing.assert_allclose(out[1][1][strat], out[0][1][strat], rtol=1e-9, atol=1e-12)
+    pm = float(np.linalg.norm(out[1][1][2] - out[0][1][2]) / np.linalg.norm(out[0][1][2]))
+    assert 0.0 < pm < 5e-2, pm
+    assert out[1][2]["photons"] == out[0][2]["photons"]
+    print(f"relative L2 error vs oracle: fp32 {rel[0]:.2e}, packed {rel[1]:.2e}; photon image packed vs fp32 {pm:.2e}")
+
+
 def test_ragged_small_image_parity(neb, oracle):
     """Odd image size (a ragged last block), D = 3 (one photon bounce)."""
     from paper_1909_00573_gb300 import scenes
