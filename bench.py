@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=0,
                     help="batched-jobs measurement: N heterogeneous jobs, batched vs sequential per-job launches")
     ap.add_argument("--mem-budget-gb", type=float, default=150.0, help="admission cap of the batched jobs")
+    ap.add_argument("--autotune", type=int, default=0,
+                    help="run the autotuner (this many iterations per candidate) before the warm-up")
     return ap.parse_args()
 
 
@@ -380,6 +382,9 @@ def main():
     t_b0 = time.perf_counter()
     ctx.build_bvh()
     bvh_build_ms = (time.perf_counter() - t_b0) * 1000.0
+    if args.autotune > 0:
+        ctx.autotune(args.autotune)
+    tuning = ctx.tuning().as_dict()
     ctx.iterate(args.warmup)
     torch.cuda.synchronize()
     s0 = ctx.stats(check=False)
@@ -478,7 +483,8 @@ def main():
                 "counters_per_step": {k: (v / args.steps if not isinstance(v, list) else [x / args.steps for x in v])
                                       for k, v in d.items() if k not in ("iterations",)},
                 "status": s1["status"], "bvh_build_ms": bvh_build_ms,
-                "bvh": "PLOC" if args.bvh == 0 else "LBVH"}
+                "bvh": "PLOC" if args.bvh == 0 else "LBVH", "tuning": tuning,
+                "tuning_source": "autotuned" if args.autotune > 0 else "defaults"}
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

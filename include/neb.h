@@ -137,6 +137,28 @@ int neb_iterate_batch(neb_ctx* const* ctxs, int n, int n_iterations);
  * invalid cfg or counts. */
 int neb_job_device_bytes(const neb_config* cfg, int n_tri, int n_sph, int n_mat, int n_lights, uint64_t* out);
 
+/* Launch settings of a context; none of them changes any result.  Rays are
+ * regrouped before they are traced by the cell of their origin in the scene
+ * box and the cell of their direction (camera rays after the first bounce)
+ * or of their light point (shadow rays), with 2^bits cells per axis;
+ * 3 (origin_bits + other_bits) <= 12 for each.  shade_blocks_per_sm sizes the
+ * grid of the shading kernels.  Defaults {1, 3, 2, 2, 8}. */
+typedef struct {
+  int cam_origin_bits, cam_dir_bits;         /* each in [0, 4] */
+  int shadow_origin_bits, shadow_light_bits; /* each in [0, 4] */
+  int shade_blocks_per_sm;                   /* [1, 32] */
+} neb_tuning;
+int neb_get_tuning(const neb_ctx* ctx, neb_tuning* out);
+/* NEB_ERR_ARG for values out of range; applies from the next iteration. */
+int neb_set_tuning(neb_ctx* ctx, const neb_tuning* t);
+/* Autotuner: coordinate descent over candidate camera groupings, then
+ * shadow groupings, then shading grid sizes, each candidate timed (CUDA
+ * events on the context stream) over iterations_per_candidate iterations.
+ * These are real iterations: they add to the image like any other.  Keeps
+ * the fastest settings, writes them to *chosen (may be NULL) and returns
+ * after the last candidate has finished. */
+int neb_autotune(neb_ctx* ctx, int iterations_per_candidate, neb_tuning* chosen);
+
 /* Progressive result: FP64 per-pixel sums divided by the iteration count,
  * written as [H][W][3] float.  out_is_device: nonzero if rgb_out is device
  * memory (written on the context stream), zero for host memory (synchronises). */

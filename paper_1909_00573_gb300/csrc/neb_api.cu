@@ -466,6 +466,79 @@ extern "C" int neb_iterate_batch(neb_ctx* const* ctxs, int n, int n_iterations) 
   return NEB_OK;
 }
 
+static bool tuning_ok(const neb_tuning* t) {
+  auto in = [](int v, int lo, int hi) { return v >= lo && v <= hi; };
+  return in(t->cam_origin_bits, 0, 4) && in(t->cam_dir_bits, 0, 4) && in(t->shadow_origin_bits, 0, 4) &&
+         in(t->shadow_light_bits, 0, 4) && 3 * (t->cam_origin_bits + t->cam_dir_bits) <= 12 &&
+         3 * (t->shadow_origin_bits + t->shadow_light_bits) <= 12 && in(t->shade_blocks_per_sm, 1, 32);
+}
+
+extern "C" int neb_get_tuning(const neb_ctx* c, neb_tuning* out) {
+  if (!c || !out) return NEB_ERR_ARG;
+  *out = c->tune;
+  return NEB_OK;
+}
+
+extern "C" int neb_set_tuning(neb_ctx* c, const neb_tuning* t) {
+  if (!c || !t || !tuning_ok(t)) return NEB_ERR_ARG;
+  c->tune = *t;
+  return NEB_OK;
+}
+
+// Milliseconds of n overlapped iterations with the current settings.
+static int time_iterations(neb_ctx* c, int n, float* ms) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return fail(c, NEB_ERR_CUDA, "neb_autotune");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(c, NEB_ERR_CUDA, "neb_autotune");
+  }
+  cudaEventRecord(e0, c->stream);
+  int rc = neb_iterate(c, n);
+  cudaEventRecord(e1, c->stream);
+  cudaError_t e = cudaEventSynchronize(e1);
+  if (rc == NEB_OK && e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != NEB_OK) return rc;
+  return e == cudaSuccess ? NEB_OK : fail(c, NEB_ERR_CUDA, "neb_autotune", e);
+}
+
+extern "C" int neb_autotune(neb_ctx* c, int iterations_per_candidate, neb_tuning* chosen) {
+  if (!c || iterations_per_candidate < 1) return NEB_ERR_ARG;
+  if (!c->bvh_ready) return fail(c, NEB_ERR_ARG, "neb_autotune: call neb_scene_upload and neb_build_bvh first");
+  const int cams[][2] = {{1, 3}, {0, 3}, {1, 2}, {2, 2}, {0, 4}};
+  const int shadows[][2] = {{2, 2}, {1, 2}, {2, 1}, {1, 1}};
+  const int blocks[] = {8, 4, 16};
+  neb_tuning best = c->tune;
+  for (int axis = 0; axis < 3; ++axis) {
+    const int n = axis == 0 ? 5 : (axis == 1 ? 4 : 3);
+    float best_ms = 0.0f;
+    neb_tuning pick = best;
+    for (int i = 0; i < n; ++i) {
+      neb_tuning t = best;
+      if (axis == 0) { t.cam_origin_bits = cams[i][0]; t.cam_dir_bits = cams[i][1]; }
+      if (axis == 1) { t.shadow_origin_bits = shadows[i][0]; t.shadow_light_bits = shadows[i][1]; }
+      if (axis == 2) t.shade_blocks_per_sm = blocks[i];
+      c->tune = t;
+      float ms = 0.0f;
+      int rc = time_iterations(c, iterations_per_candidate, &ms);
+      if (rc != NEB_OK) {
+        c->tune = best;
+        return rc;
+      }
+      if (i == 0 || ms < best_ms) {
+        best_ms = ms;
+        pick = t;
+      }
+    }
+    best = pick;
+  }
+  c->tune = best;
+  if (chosen) *chosen = best;
+  return NEB_OK;
+}
+
 extern "C" int neb_resolve(neb_ctx* c, float* rgb_out, int out_is_device) {
   if (!c || !rgb_out) return NEB_ERR_ARG;
   size_t n = (size_t)c->P * 3;

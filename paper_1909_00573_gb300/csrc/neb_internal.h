@@ -168,6 +168,7 @@ struct neb_ctx {
   int2* hits_ph = nullptr;  // closest hits of the photon ray queue (pass 3)
   neb::ShadowRay* shadow_rays = nullptr;  // shadow rays grouped by light
   int* group_counters = nullptr;  // ray grouping of pass 1: group counts, then cursors
+  neb_tuning tune{1, 3, 2, 2, 8};  // launch settings (neb_set_tuning / neb_autotune)
   neb::MergeRec* mrec = nullptr;
   int* vert_bucket = nullptr;
   int* bucket_count = nullptr;

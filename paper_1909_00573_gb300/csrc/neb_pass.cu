@@ -72,15 +72,16 @@ __device__ __forceinline__ PhotonRay load_photon(const void* q, int i, int packe
   return ph;
 }
 
-static int grid_blocks() {
-  static int blocks = 0;
-  if (blocks == 0) {
-    int dev = 0, sms = 0;
+// Grid of the shading kernels: SMs x the context's blocks per SM.
+static int grid_blocks(const neb_ctx* c) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    blocks = (sms > 0 ? sms : 152) * 8;
+    if (sms <= 0) sms = 152;
   }
-  return blocks;
+  return sms * c->tune.shade_blocks_per_sm;
 }
 
 __device__ __forceinline__ void warp_count(unsigned long long* dst, uint32_t v) {
@@ -637,7 +638,7 @@ IterParams iter_params(const neb_ctx* c, int iteration) {
 // Pass 1 of `iteration` on stream st: view paths, NEE samples and shadow rays
 // into slot iteration & 1.  Returns the number of kernels enqueued.
 static long long enqueue_pass1(neb_ctx* c, int iteration, cudaStream_t st, StageTimer& tm) {
-  const int B = grid_blocks();
+  const int B = grid_blocks(c);
   SceneView s = scene_view(c);
   IterParams ip = iter_params(c, iteration);
   IterSlot& sl = c->slots[iteration & 1];
@@ -690,7 +691,7 @@ static long long enqueue_pass1(neb_ctx* c, int iteration, cudaStream_t st, Stage
 // densities, NEE contributions and photon emission; then the deferred random
 // hits, photon walks and merges.
 static long long enqueue_pass23(neb_ctx* c, int iteration, cudaStream_t st2, StageTimer& tm) {
-  const int B = grid_blocks();
+  const int B = grid_blocks(c);
   SceneView s = scene_view(c);
   IterParams ip = iter_params(c, iteration);
   IterSlot& sl = c->slots[iteration & 1];
@@ -815,8 +816,8 @@ cudaError_t launch_resolve(const double* accum, int P, int iterations, float* ou
 
 cudaError_t launch_read_rho(neb_ctx* c, float* d_out) {
   const IterSlot& sl = c->slots[c->iteration & 1];  // slot of the last iteration
-  k_fill<<<grid_blocks(), 256, 0, c->stream>>>(d_out, (size_t)c->P * (c->D - 1), -1.0f);  // no NEE vertex
-  k_read_rho<<<grid_blocks(), 256, 0, c->stream>>>(sl.nv, sl.cnt, c->D, c->cap_nee, d_out);
+  k_fill<<<grid_blocks(c), 256, 0, c->stream>>>(d_out, (size_t)c->P * (c->D - 1), -1.0f);  // no NEE vertex
+  k_read_rho<<<grid_blocks(c), 256, 0, c->stream>>>(sl.nv, sl.cnt, c->D, c->cap_nee, d_out);
   return cudaGetLastError();
 }
 

@@ -140,12 +140,13 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_closest(SceneView s, co
 // consecutive warps find them in cache.  Two queues are regrouped by a
 // counting sort over kGroups spatial groups before they are traced:
 //  - shadow rays, which leave in the order of their NEE vertices, so that a
-//    warp's rays usually aim at different lights: grouped by the 4 x 4 x 4
-//    cell of the origin and of the light point in the scene box;
+//    warp's rays usually aim at different lights: grouped by the cell of the
+//    origin and of the light point in the scene box (default 4 x 4 x 4 each);
 //  - camera rays after the first bounce, which start in one area but go in
-//    all directions: grouped by the 2 x 2 x 2 cell of the origin and the
-//    8 x 8 x 8 cell of the direction in [-1, 1]^3 (on the city scene the
+//    all directions: grouped by the cell of the origin and of the direction
+//    in [-1, 1]^3 (default 2 x 2 x 2 and 8 x 8 x 8: on the city scene the
 //    direction matters more than the origin).
+// The cell resolutions are launch settings of the context (neb_tuning).
 // The sort has three launches.  Count: each block builds a shared-memory
 // histogram of its contiguous chunk of the queue and adds its non-zero
 // groups to global counters (at most one atomic per block and group).  Scan:
@@ -158,10 +159,6 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_closest(SceneView s, co
 // and vertices without a shadow ray are dropped.
 constexpr int kGroupBits = 12;
 constexpr int kGroups = 1 << kGroupBits;
-constexpr int kShBitsO = 2, kShBitsL = 2;   // shadow: origin and light-point cells per axis (log2)
-constexpr int kCamBitsO = 1, kCamBitsD = 3;  // camera: origin and direction cells per axis (log2)
-static_assert(3 * (kShBitsO + kShBitsL) <= kGroupBits && 3 * (kCamBitsO + kCamBitsD) <= kGroupBits,
-              "groups must fit the counters");
 constexpr int kGroupBlocks = 152;
 constexpr int kGroupThreads = 1024;
 constexpr int kScanThreads = 1024;
@@ -172,27 +169,34 @@ struct CellGrid {
   float3 lo, unit;  // box minimum, 1 / extent per axis
 };
 
-// Morton index of p's cell in a grid of 2^bits cells per axis over the box
-template <int bits>
-__device__ __forceinline__ int grid_cell(const CellGrid& g, float3 p) {
-  const float n = (float)(1 << bits);
-  int ix = min(max((int)((p.x - g.lo.x) * g.unit.x * n), 0), (1 << bits) - 1);
-  int iy = min(max((int)((p.y - g.lo.y) * g.unit.y * n), 0), (1 << bits) - 1);
-  int iz = min(max((int)((p.z - g.lo.z) * g.unit.z * n), 0), (1 << bits) - 1);
+// A grouping key: the scene box and the log2 cells per axis of its two parts
+// (origin, then light point or direction); 3 (a + b) <= kGroupBits.
+struct GroupSpec {
+  CellGrid g;
+  int a, b;
+};
+
+// Morton index of p's cell in a grid of 2^bits (bits <= 4) cells per axis over the box
+__device__ __forceinline__ int grid_cell(const CellGrid& g, float3 p, int bits) {
+  const int n = 1 << bits;
+  int ix = min(max((int)((p.x - g.lo.x) * g.unit.x * (float)n), 0), n - 1);
+  int iy = min(max((int)((p.y - g.lo.y) * g.unit.y * (float)n), 0), n - 1);
+  int iz = min(max((int)((p.z - g.lo.z) * g.unit.z * (float)n), 0), n - 1);
   int m = 0;
 #pragma unroll
-  for (int b = 0; b < bits; ++b)
-    m |= (((ix >> b) & 1) << (3 * b)) | (((iy >> b) & 1) << (3 * b + 1)) | (((iz >> b) & 1) << (3 * b + 2));
+  for (int b = 0; b < 4; ++b)
+    if (b < bits)
+      m |= (((ix >> b) & 1) << (3 * b)) | (((iy >> b) & 1) << (3 * b + 1)) | (((iz >> b) & 1) << (3 * b + 2));
   return m;
 }
 
-__device__ __forceinline__ int shadow_group(const CellGrid& g, float3 p, float3 y) {
-  return (grid_cell<kShBitsO>(g, p) << (3 * kShBitsL)) + grid_cell<kShBitsL>(g, y);
+__device__ __forceinline__ int shadow_group(const GroupSpec& k, float3 p, float3 y) {
+  return (grid_cell(k.g, p, k.a) << (3 * k.b)) + grid_cell(k.g, y, k.b);
 }
 
-__device__ __forceinline__ int camera_group(const CellGrid& g, float3 o, float3 d) {
+__device__ __forceinline__ int camera_group(const GroupSpec& k, float3 o, float3 d) {
   const CellGrid dg = {f3(-1.0f, -1.0f, -1.0f), f3(0.5f, 0.5f, 0.5f)};
-  return (grid_cell<kCamBitsO>(g, o) << (3 * kCamBitsD)) + grid_cell<kCamBitsD>(dg, d);
+  return (grid_cell(k.g, o, k.a) << (3 * k.b)) + grid_cell(dg, d, k.b);
 }
 
 // Contiguous chunk [lo, hi) of a queue of n entries for this block.
@@ -275,7 +279,7 @@ __device__ __forceinline__ float3 nee_light_point(const NeeStore& nv, int i) {
 }
 
 __global__ void __launch_bounds__(kGroupThreads) k_shadow_count(NeeStore nv, const DevCounters* cnt, int cap,
-                                                                CellGrid g, int* __restrict__ counts) {
+                                                                GroupSpec g, int* __restrict__ counts) {
   __shared__ int h[kGroups];
   clear_hist(h);
   __syncthreads();
@@ -288,7 +292,7 @@ __global__ void __launch_bounds__(kGroupThreads) k_shadow_count(NeeStore nv, con
 }
 
 __global__ void __launch_bounds__(kGroupThreads) k_shadow_scatter(NeeStore nv, const DevCounters* cnt, int cap,
-                                                                  CellGrid g, int* __restrict__ cursors,
+                                                                  GroupSpec g, int* __restrict__ cursors,
                                                                   ShadowRay* __restrict__ rays) {
   __shared__ int h[kGroups];
   clear_hist(h);
@@ -315,7 +319,7 @@ __global__ void __launch_bounds__(kGroupThreads) k_shadow_scatter(NeeStore nv, c
 
 __global__ void __launch_bounds__(kGroupThreads) k_cam_group_count(const CamRay* __restrict__ q,
                                                                    const int* __restrict__ count_ptr, int cap,
-                                                                   CellGrid g, int* __restrict__ counts) {
+                                                                   GroupSpec g, int* __restrict__ counts) {
   __shared__ int h[kGroups];
   clear_hist(h);
   __syncthreads();
@@ -329,7 +333,7 @@ __global__ void __launch_bounds__(kGroupThreads) k_cam_group_count(const CamRay*
 
 __global__ void __launch_bounds__(kGroupThreads) k_cam_group_scatter(const CamRay* __restrict__ q,
                                                                      const int* __restrict__ count_ptr, int cap,
-                                                                     CellGrid g, int* __restrict__ cursors,
+                                                                     GroupSpec g, int* __restrict__ cursors,
                                                                      CamRay* __restrict__ out) {
   __shared__ int h[kGroups];
   clear_hist(h);
@@ -433,7 +437,7 @@ static CellGrid scene_grid(const neb_ctx* c) {
 static int group_blocks(int cap) { return capped_blocks(cap, kGroupThreads, kGroupBlocks); }
 
 cudaError_t launch_group_camera(neb_ctx* c, const CamRay* q, const int* count_ptr, CamRay* out, cudaStream_t st) {
-  CellGrid g = scene_grid(c);
+  GroupSpec g = {scene_grid(c), c->tune.cam_origin_bits, c->tune.cam_dir_bits};
   int* counts = c->group_counters;
   int* cursors = c->group_counters + kGroups;
   k_cam_group_count<<<group_blocks(c->cap_cam), kGroupThreads, 0, st>>>(q, count_ptr, c->cap_cam, g, counts);
@@ -443,7 +447,7 @@ cudaError_t launch_group_camera(neb_ctx* c, const CamRay* q, const int* count_pt
 }
 
 cudaError_t launch_group_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st) {
-  CellGrid g = scene_grid(c);
+  GroupSpec g = {scene_grid(c), c->tune.shadow_origin_bits, c->tune.shadow_light_bits};
   int* counts = c->group_counters;
   int* cursors = c->group_counters + kGroups;
   k_shadow_count<<<group_blocks(c->cap_nee), kGroupThreads, 0, st>>>(sl.nv, sl.cnt, c->cap_nee, g, counts);

@@ -26,7 +26,8 @@ EXPORTS = ["neb_create", "neb_destroy", "neb_last_error", "neb_scene_upload", "n
            "neb_set_profiling", "neb_get_stage_times", "neb_trace_closest", "neb_philox", "neb_plane_box_area",
            "neb_octree_create", "neb_octree_destroy", "neb_octree_set_iteration", "neb_octree_insert",
            "neb_octree_density", "neb_octree_read", "neb_octree_load", "neb_count_neighbours",
-           "neb_count_neighbours_noalloc", "neb_iterate_batch", "neb_job_device_bytes"]
+           "neb_count_neighbours_noalloc", "neb_iterate_batch", "neb_job_device_bytes", "neb_get_tuning",
+           "neb_set_tuning", "neb_autotune"]
 NOALLOC_MAX_POINTS = 1 << 18
 
 
@@ -41,6 +42,14 @@ class Config(C.Structure):
                 ("octree_capacity", C.c_int), ("split_factor", C.c_int), ("seed", C.c_uint64),
                 ("octree_mode", C.c_int), ("density_mode", C.c_int), ("strategy_mask", C.c_uint32),
                 ("keep_split", C.c_int), ("bvh_builder", C.c_int), ("photon_records", C.c_int)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("cam_origin_bits", C.c_int), ("cam_dir_bits", C.c_int), ("shadow_origin_bits", C.c_int),
+                ("shadow_light_bits", C.c_int), ("shade_blocks_per_sm", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Stats(C.Structure):
@@ -99,6 +108,9 @@ def lib():
             "neb_octree_read": ([vp, vp, C.c_int, vp], C.c_int),
             "neb_octree_load": ([vp, vp, C.c_int, C.c_int, C.c_int], C.c_int),
             "neb_iterate_batch": ([vp, C.c_int, C.c_int], C.c_int),
+            "neb_get_tuning": ([vp, vp], C.c_int),
+            "neb_set_tuning": ([vp, vp], C.c_int),
+            "neb_autotune": ([vp, C.c_int, vp], C.c_int),
             "neb_job_device_bytes": ([vp, C.c_int, C.c_int, C.c_int, C.c_int, vp], C.c_int),
             "neb_count_neighbours": ([vp, C.c_int, vp, C.c_int, C.c_float, vp], C.c_int),
             "neb_count_neighbours_noalloc": ([vp, C.c_int, vp, C.c_int, C.c_float, vp, vp], C.c_int),
@@ -170,6 +182,19 @@ class Context:
 
     def iterate(self, n=1):
         self._c(lib().neb_iterate(self.h, int(n)))
+
+    def tuning(self):
+        t = Tuning()
+        self._c(lib().neb_get_tuning(self.h, C.byref(t)))
+        return t
+
+    def set_tuning(self, t):
+        self._c(lib().neb_set_tuning(self.h, C.byref(t)))
+
+    def autotune(self, iterations_per_candidate=2):
+        t = Tuning()
+        self._c(lib().neb_autotune(self.h, int(iterations_per_candidate), C.byref(t)))
+        return t
 
     def resolve(self, out_device_ptr: int | None = None):
         if out_device_ptr is not None:

@@ -75,3 +75,33 @@ def test_job_device_bytes_matches_allocation(neb):
     used = free0 - torch.cuda.mem_get_info()[0]
     ctx.close()
     assert abs(used - expect) <= 0.05 * expect + (64 << 20), (used, expect)
+
+
+def test_tuning_changes_no_result(neb):
+    """Launch settings (grouping resolutions, shading grid) leave every result
+    unchanged (deterministic octree: densities identical, FP64 sums equal up to
+    the order of the atomic additions); invalid settings are rejected; the
+    autotuner returns valid settings after running real iterations."""
+    from paper_1909_00573_gb300 import scenes
+    s, rc = scenes.workload("tiny_room")
+    rc.octree_mode = 1
+    out = []
+    for t in (None, neb.Tuning(0, 4, 1, 1, 3)):
+        ctx = _start(neb, s, rc)
+        if t is not None:
+            ctx.set_tuning(t)
+            assert ctx.tuning().as_dict() == t.as_dict()
+        ctx.iterate(3)
+        out.append((ctx.read_nee_rho(), ctx.read_accum()))
+        ctx.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    np.testing.assert_allclose(out[1][1], out[0][1], rtol=1e-12, atol=1e-12 * float(np.abs(out[0][1]).max()))
+    ctx = _start(neb, s, rc)
+    for bad in (neb.Tuning(5, 0, 2, 2, 8), neb.Tuning(2, 3, 2, 2, 8), neb.Tuning(1, 3, 2, 2, 0)):
+        with pytest.raises(neb.NebError):
+            ctx.set_tuning(bad)
+    t = ctx.autotune(1)
+    assert ctx.stats()["iterations"] == 5 + 4 + 3          # one iteration per candidate
+    assert ctx.tuning().as_dict() == t.as_dict()
+    assert 3 * (t.cam_origin_bits + t.cam_dir_bits) <= 12 and 1 <= t.shade_blocks_per_sm <= 32
+    ctx.close()
