@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=0,
                     help="batched-jobs measurement: N heterogeneous jobs, batched vs sequential per-job launches")
     ap.add_argument("--mem-budget-gb", type=float, default=150.0, help="admission cap of the batched jobs")
+    ap.add_argument("--serve", type=int, default=0,
+                    help="served progressive rendering: R requests with Poisson arrivals, vs sequential per-job")
+    ap.add_argument("--rate", type=float, default=200.0, help="mean request arrival rate (per second) for --serve")
     ap.add_argument("--autotune", type=int, default=0,
                     help="run the autotuner (this many iterations per candidate) before the warm-up")
     return ap.parse_args()
@@ -342,12 +345,61 @@ def run_batch(args):
     return 0
 
 
+def run_serve(args):
+    """Served progressive rendering: args.serve requests drawn from the
+    batched-jobs mix, Poisson arrivals at args.rate per second, targets of 16
+    to 256 iterations (log-uniform), admission capped at --mem-budget-gb.
+    The same requests are served by continuous batching and by sequential
+    per-job launches in arrival order."""
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1909_00573_gb300 import build as B
+    B.build()
+    from paper_1909_00573_gb300 import scenes, serve
+    budget = args.mem_budget_gb * 1e9
+    out = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    for mode in ("served", "sequential"):
+        reqs = serve.poisson_requests(scenes.batch_jobs(args.serve, seed=rank), args.rate, seed=rank)
+        t0 = time.perf_counter()
+        if mode == "served":
+            res, rounds, rejected = serve.run_served(reqs, budget, max_jobs=64)
+        else:
+            res, rejected = serve.run_sequential(reqs), []
+        wall = time.perf_counter() - t0
+        out[mode] = serve.summary(res, wall)
+        out[mode]["rejected"] = len(rejected)
+        if mode == "served":
+            out[mode]["rounds"] = len(rounds)
+            out[mode]["max_resident"] = max(n for _, _, n in rounds)
+    clk = clocks.stop()
+    sv, sq = out["served"], out["sequential"]
+    line = {"metric": METRIC, "value": sv["mpaths_per_s"], "unit": METRIC, "n_gpus": 1, "steps": sv["rounds"],
+            "warmup": 0, "ms_per_step": sv["iteration_latency_ms"]["p50"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"served progressive rendering: {args.serve} requests from the batched-jobs mix, "
+                                   f"Poisson arrivals at {args.rate:g}/s, 16..256 iterations each, admission cap "
+                                   f"{args.mem_budget_gb:g} GB, at most 64 resident jobs"},
+            "served": sv, "sequential_per_job": sq,
+            "throughput_ratio": sv["mpaths_per_s"] / sq["mpaths_per_s"],
+            "time_to_target_mean_ratio": sq["time_to_target_s"]["mean"] / sv["time_to_target_s"]["mean"],
+            "timing": "host clock around device synchronisation", "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.batch > 0:
         return run_batch(args)
+    if args.serve > 0:
+        return run_serve(args)
     rank, world, local = dist_env()
     import numpy as np
     import torch
