@@ -1514,6 +1514,40 @@ static int fcmp(const void* a, const void* b) {
   return x < y ? -1 : (x > y ? 1 : 0);
 }
 
+void orc_density_naive(const float* pts, int n, float radius, float* out) {
+  float r2 = radius * radius;
+  double inv_area = 1.0 / (PI_D * (double)radius * (double)radius);
+  for (int i = 0; i < n; ++i) {
+    int cnt = 0;
+    for (int j = 0; j < n; ++j) {
+      float dx = pts[3 * j] - pts[3 * i], dy = pts[3 * j + 1] - pts[3 * i + 1], dz = pts[3 * j + 2] - pts[3 * i + 2];
+      if (dx * dx + dy * dy + dz * dz <= r2) cnt++;
+    }
+    out[i] = (float)((double)cnt * inv_area);
+  }
+}
+
+void orc_density_knn(const float* pts, int n, int k, float* out) {
+  float* best = (float*)malloc(sizeof(float) * (size_t)(k > 0 ? k : 1));
+  for (int i = 0; i < n; ++i) {
+    int have = 0;  /* best[0..have) ascending, the k smallest so far */
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      float dx = pts[3 * j] - pts[3 * i], dy = pts[3 * j + 1] - pts[3 * i + 1], dz = pts[3 * j + 2] - pts[3 * i + 2];
+      float d2 = dx * dx + dy * dy + dz * dz;
+      if (have == k && !(d2 < best[k - 1])) continue;
+      int at = have < k ? have++ : k - 1;
+      while (at > 0 && best[at - 1] > d2) {
+        best[at] = best[at - 1];
+        at--;
+      }
+      best[at] = d2;
+    }
+    out[i] = have == k ? (float)((double)(k - 1) / (PI_D * (double)best[k - 1])) : 0.0f;
+  }
+  free(best);
+}
+
 void orc_count_neighbours(const float* pts, int n, const float* queries, int m, float r, int brute,
                           int32_t* out_count) {
   float r2 = r * r;

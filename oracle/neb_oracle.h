@@ -91,6 +91,16 @@ int orc_trace(const orc_scene* scene, const float* rays, int n, int brute,
 void orc_count_neighbours(const float* pts, int n, const float* queries, int m,
                           float r, int brute, int32_t* out_count);
 
+/* The two density estimators the paper tried before its octree (Sec. 5),
+ * by brute force, each evaluated at every one of the n points [n][3]:
+ * naive: the points within `radius` of the point, itself included, divided
+ * by pi radius^2; k nearest (Loftsgaarden and Quesenberry 1965):
+ * (k - 1) / (pi d_k^2), d_k^2 the k-th smallest squared distance to the other
+ * points (0 when there are fewer than k).  Squared distances in FP32
+ * (other - point, x + y + z order), the quotient in FP64 rounded to FP32. */
+void orc_density_naive(const float* pts, int n, float radius, float* out);
+void orc_density_knn(const float* pts, int n, int k, float* out);
+
 /* Balance-heuristic weights of every strategy for one explicit path (used by
  * the MIS pin tests).  See the definition of orc_path in the source. */
 int orc_mis_weights(const float* verts, int n_verts, const float* light,

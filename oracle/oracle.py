@@ -76,6 +76,8 @@ def lib():
         L.orc_trace.argtypes = [C.POINTER(_Scene), C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
         L.orc_count_neighbours.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_float, C.c_int,
                                            C.c_void_p]
+        L.orc_density_naive.argtypes = [C.c_void_p, C.c_int, C.c_float, C.c_void_p]
+        L.orc_density_knn.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p]
         L.orc_mis_weights.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_float, C.c_double, C.c_uint32,
                                       C.c_void_p]
         L.orc_mis_weights.restype = C.c_int
@@ -164,6 +166,22 @@ def count_neighbours(points, queries, r, brute=False):
     Q = np.ascontiguousarray(queries, np.float32).reshape(-1, 3)
     out = np.zeros(len(Q), np.int32)
     lib().orc_count_neighbours(_ptr(P), len(P), _ptr(Q), len(Q), C.c_float(r), int(brute), _ptr(out))
+    return out
+
+
+def density_naive(points, radius):
+    """Naive estimator (Sec. 5) at every point, brute force."""
+    P = np.ascontiguousarray(points, np.float32).reshape(-1, 3)
+    out = np.zeros(len(P), np.float32)
+    lib().orc_density_naive(_ptr(P), len(P), C.c_float(radius), _ptr(out))
+    return out
+
+
+def density_knn(points, k):
+    """k-nearest-neighbour estimator (Sec. 5) at every point, brute force."""
+    P = np.ascontiguousarray(points, np.float32).reshape(-1, 3)
+    out = np.zeros(len(P), np.float32)
+    lib().orc_density_knn(_ptr(P), len(P), int(k), _ptr(out))
     return out
 
 

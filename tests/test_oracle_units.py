@@ -503,3 +503,37 @@ def test_mis_delta_vertices(oracle):
     verts[2][6] = 0
     w = oracle.mis_weights(verts, light, 0.05, 100.0)
     assert w[2] == 0.0 and w[0] + w[1] == pytest.approx(1.0)
+
+
+def test_density_estimators_closed_forms(oracle):
+    """The naive and k-nearest estimators of Sec. 5 on a unit square lattice
+    in the plane z = 0: within radius 1.5 an interior point sees itself and 8
+    neighbours (9 / (pi 2.25)); its 5th nearest other point is at sqrt(2)
+    ((5 - 1) / (pi 2)); its 4th at distance 1 ((4 - 1) / pi)."""
+    g = np.stack(np.meshgrid(np.arange(9.0), np.arange(9.0), indexing="ij"), -1).reshape(-1, 2)
+    pts = np.concatenate([g, np.zeros((len(g), 1))], 1).astype(np.float32)
+    interior = np.all((g >= 1) & (g <= 7), axis=1)
+    naive = oracle.density_naive(pts, 1.5)
+    assert np.allclose(naive[interior], 9.0 / (np.pi * 2.25), rtol=1e-6)
+    corner = np.all(g == 0, axis=1)
+    assert np.allclose(naive[corner], 4.0 / (np.pi * 2.25), rtol=1e-6)
+    assert np.allclose(oracle.density_knn(pts, 5)[interior], 4.0 / (np.pi * 2.0), rtol=1e-6)
+    assert np.allclose(oracle.density_knn(pts, 4)[interior], 3.0 / np.pi, rtol=1e-6)
+    assert np.all(oracle.density_knn(pts[:3], 4) == 0.0)          # fewer than k other points
+
+
+def test_knn_estimator_unbiased_on_uniform_points(oracle):
+    """(k - 1) / (pi d_k^2) is unbiased for a Poisson process of intensity
+    lambda (Loftsgaarden and Quesenberry 1965): 4000 uniform points in a unit
+    square (lambda = 4000), mean over points away from the border."""
+    rng = np.random.default_rng(12)
+    xy = rng.uniform(0, 1, (4000, 2))
+    pts = np.concatenate([xy, np.zeros((4000, 1))], 1).astype(np.float32)
+    inner = np.all((xy > 0.1) & (xy < 0.9), axis=1)
+    for k in (4, 8):
+        est = oracle.density_knn(pts, k)[inner]
+        assert abs(est.mean() / 4000.0 - 1.0) < 0.05, (k, est.mean())
+    # the naive estimator counts the point itself: E = lambda + 1 / (pi h^2)
+    h = 0.02
+    est = oracle.density_naive(pts, h)[inner]
+    assert abs(est.mean() / (4000.0 + 1.0 / (np.pi * h * h)) - 1.0) < 0.03
