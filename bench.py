@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--serve", type=int, default=0,
                     help="served progressive rendering: R requests with Poisson arrivals, vs sequential per-job")
     ap.add_argument("--rate", type=float, default=200.0, help="mean request arrival rate (per second) for --serve")
+    ap.add_argument("--ablation", action="store_true",
+                    help="density estimators of Sec. 5 (octree, naive, k nearest) on one iteration's NEE vertices")
     ap.add_argument("--autotune", type=int, default=0,
                     help="run the autotuner (this many iterations per candidate) before the warm-up")
     return ap.parse_args()
@@ -392,10 +394,64 @@ def run_serve(args):
     return 0
 
 
+def run_ablation(args):
+    """The density estimators of Sec. 5 on the NEE vertices of one iteration
+    of the workload (after one warm-up iteration): the octree (concurrent
+    insert + robust query, as the pass uses it), the naive estimator (radius 4
+    merge radii) and the k-nearest estimator (k = 4, the paper's smallest),
+    each timed on the device (structure build + one query per vertex)."""
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1909_00573_gb300 import build as B
+    B.build()
+    from paper_1909_00573_gb300 import neb, scenes
+    scene, rc = scenes.workload(args.workload)
+    ctx = neb.Context(neb.make_config(rc))
+    ctx.scene_upload(scene)
+    ctx.build_bvh()
+    ctx.iterate(2)
+    pos, nrm = ctx.read_nee_vertices()
+    ctx.close()
+    v = scene.tri.reshape(-1, 3)
+    lo = v.min(0)
+    hi = v.max(0)
+    if len(scene.sph):
+        lo = np.minimum(lo, (scene.sph[:, :3] - scene.sph[:, 3:]).min(0))
+        hi = np.maximum(hi, (scene.sph[:, :3] + scene.sph[:, 3:]).max(0))
+    radius, k = 4.0 * rc.merge_radius, 4
+    neb.density_estimators(pos[:4096], nrm[:4096], lo, hi, 1 << 16, rc.split_factor, radius, k)   # warm-up
+    rho, ms = neb.density_estimators(pos, nrm, lo, hi, rc.octree_capacity, rc.split_factor, radius, k)
+    n = len(pos)
+    pos_ok = [(r > 0).mean() for r in rho]
+    spread = {}
+    for name, a, b in (("naive_vs_octree", rho[1], rho[0]), ("knn_vs_octree", rho[2], rho[0])):
+        ok = (a > 0) & (b > 0)
+        q = np.log10(a[ok] / b[ok])
+        spread[name] = {"median_log10_ratio": float(np.median(q)), "iqr_log10_ratio": float(np.subtract(*np.percentile(q, [75, 25])))}
+    line = {"metric": "M density estimates/s", "value": n / (ms[0] / 1e3) / 1e6, "unit": "M estimates/s",
+            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": float(ms[0]), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 normalisation)", "data": "synthetic",
+            "config": {"workload": f"density estimators of Sec. 5 on the {n} NEE vertices of one iteration of "
+                                   f"{args.workload} ({rc.width}x{rc.height}, D={rc.max_depth})",
+                       "naive_radius": radius, "k": k, "octree_capacity": rc.octree_capacity,
+                       "split_factor": rc.split_factor},
+            "ms": {"octree": float(ms[0]), "naive": float(ms[1]), "knn": float(ms[2])},
+            "speedup_of_octree": {"vs_knn": float(ms[2] / ms[0]), "vs_naive": float(ms[1] / ms[0])},
+            "fraction_positive": {"octree": float(pos_ok[0]), "naive": float(pos_ok[1]), "knn": float(pos_ok[2])},
+            "agreement": spread}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.ablation:
+        return run_ablation(args)
     if args.batch > 0:
         return run_batch(args)
     if args.serve > 0:

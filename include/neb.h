@@ -174,6 +174,10 @@ int neb_read_split(neb_ctx* ctx, double* out);
 /* Density rho at every NEE vertex of the last iteration, [H*W][D-1] indexed
  * pixel*(D-1) + (k-1); -1 where the path has no NEE vertex k.  Host memory. */
 int neb_read_nee_rho(neb_ctx* ctx, float* out);
+/* The NEE vertices of the last iteration in store order: positions and
+ * geometric normals [cap][3] (host), *count = their number (at most
+ * W*H*(D-1); only the first min(count, cap) are written). */
+int neb_read_nee_vertices(neb_ctx* ctx, float* pos, float* nrm, int cap, int* count);
 
 /* Counters accumulated since the scene upload, plus the device status word.
  * Synchronises.  Returns NEB_ERR_DEVICE_TIMEOUT / NEB_ERR_QUEUE_OVERFLOW if the
@@ -228,6 +232,22 @@ int neb_octree_read(neb_octree* o, int32_t* nodes, int n_nodes, int32_t meta[4])
  * inserts through it wait out their bounded spin, drop the position and
  * return NEB_ERR_DEVICE_TIMEOUT. */
 int neb_octree_load(neb_octree* o, const int32_t* nodes, int n_nodes, int alloc, int depth);
+
+/* The density estimators of Sec. 5 side by side, for n points [n][3] with
+ * geometric normals [n][3] (host) taken as the NEE vertices of one
+ * iteration; every estimate is made at each of the points and written to
+ * rho[3][n]: (0) the density octree as the pass uses it (concurrent insert,
+ * get_density_robust; scene box, capacity and split factor as in
+ * neb_octree_create); (1) the naive estimator: points within `radius` of
+ * the point, itself included, / (pi radius^2), through a hashed grid;
+ * (2) the k-nearest-neighbour estimator (k - 1) / (pi d_k^2), d_k the
+ * distance to the k-th nearest other point (2 <= k <= 16; 0 with fewer than k
+ * other points), through a 4-wide tree built over the points.  ms[3] (may be
+ * NULL) receives each estimator's device time in milliseconds, structure
+ * build plus queries, CUDA events on its stream.  NEB_ERR_ARG for bad sizes. */
+int neb_density_estimators(const float* pos, const float* nrm, int n, const float scene_min[3],
+                           const float scene_max[3], int octree_capacity, int split_factor, float radius, int k,
+                           float* rho, double* ms);
 
 /* Merge candidate search through the device hashed grid (cell size 2r, the
  * structure used by the photon merge): for each query, the number of points

@@ -585,6 +585,29 @@ extern "C" int neb_read_nee_rho(neb_ctx* c, float* out) {
   return e == cudaSuccess ? NEB_OK : fail(c, NEB_ERR_CUDA, "neb_read_nee_rho", e);
 }
 
+extern "C" int neb_read_nee_vertices(neb_ctx* c, float* pos, float* nrm, int cap, int* count) {
+  if (!c || !count || cap < 0 || (cap > 0 && (!pos || !nrm))) return NEB_ERR_ARG;
+  const IterSlot& sl = c->slots[c->iteration & 1];  // slot of the last iteration
+  DevCounters h;
+  cudaMemcpyAsync(&h, sl.cnt, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(c, NEB_ERR_CUDA, "neb_read_nee_vertices", e);
+  const int n = c->iteration > 0 ? (h.nee_count < c->cap_nee ? h.nee_count : c->cap_nee) : 0;
+  *count = n;
+  const int m = n < cap ? n : cap;
+  if (m == 0) return NEB_OK;
+  std::vector<float4> p(m), q(m);
+  cudaMemcpyAsync(p.data(), sl.nv.pos, sizeof(float4) * (size_t)m, cudaMemcpyDeviceToHost, c->stream);
+  cudaMemcpyAsync(q.data(), sl.nv.nrm, sizeof(float4) * (size_t)m, cudaMemcpyDeviceToHost, c->stream);
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(c, NEB_ERR_CUDA, "neb_read_nee_vertices", e);
+  for (int i = 0; i < m; ++i) {
+    pos[3 * i] = p[i].x; pos[3 * i + 1] = p[i].y; pos[3 * i + 2] = p[i].z;
+    nrm[3 * i] = q[i].x; nrm[3 * i + 1] = q[i].y; nrm[3 * i + 2] = q[i].z;
+  }
+  return NEB_OK;
+}
+
 extern "C" int neb_get_stats(neb_ctx* c, neb_stats* out) {
   if (!c || !out) return NEB_ERR_ARG;
   DevCounters hs[2];

@@ -503,14 +503,19 @@ static cudaError_t collapse4(const BVHNode* bin, int n_bin, BVH4Node* out, cudaS
 
 cudaError_t build_bvh(neb_ctx* c) {
   int n = c->nt + c->ns;
-  cudaStream_t st = c->stream;
   if (c->nodes) { cudaFree(c->nodes); c->nodes = nullptr; }
   if (n == 0) return cudaSuccess;
-  cudaError_t e = cudaMalloc(&c->nodes, sizeof(BVH4Node) * (size_t)(n > 1 ? n - 1 : 1));
+  return build_bvh4(scene_view(c), n, c->cfg.bvh_builder, c->stream, &c->nodes, &c->n_nodes4);
+}
+
+cudaError_t build_bvh4(const SceneView& s, int n, int builder, cudaStream_t st, BVH4Node** nodes_out, int* n4_out) {
+  BVH4Node* nodes = nullptr;
+  cudaError_t e = cudaMalloc(&nodes, sizeof(BVH4Node) * (size_t)(n > 1 ? n - 1 : 1));
   if (e != cudaSuccess) return e;
-  SceneView s = scene_view(c);
+  *nodes_out = nodes;
+  *n4_out = 1;
   if (n == 1) {
-    k_single_leaf<<<1, 1, 0, st>>>(s, c->nodes);
+    k_single_leaf<<<1, 1, 0, st>>>(s, nodes);
     return cudaGetLastError();
   }
   // the binary tree (LBVH or PLOC) is built first and collapsed into the 4-wide one
@@ -548,7 +553,7 @@ cudaError_t build_bvh(neb_ctx* c) {
       uint32_t* tk = k0; k0 = k1; k1 = tk;
       int* tv = v0; v0 = v1; v1 = tv;
     }
-    if (c->cfg.bvh_builder == 1) {
+    if (builder == 1) {
       cudaMemsetAsync(pint, 0xff, 4ull * (n - 1), st);
       cudaMemsetAsync(flags, 0, 4ull * (n - 1), st);
       k_karras<<<gb, 256, 0, st>>>(k0, n, child, pint, pleaf);
@@ -564,8 +569,8 @@ cudaError_t build_bvh(neb_ctx* c) {
     }
     if (e == cudaSuccess) e = cudaGetLastError();
     int n4 = 0;
-    if (e == cudaSuccess) e = collapse4(bin, n - 1, c->nodes, st, &n4);
-    c->n_nodes4 = n4;
+    if (e == cudaSuccess) e = collapse4(bin, n - 1, nodes, st, &n4);
+    *n4_out = n4;
   } else {
     e = cudaErrorMemoryAllocation;
   }

@@ -263,6 +263,14 @@ __device__ __forceinline__ float3 oct_decode16(uint32_t v) {
   return make_float3(px / l, py / l, nz / l);
 }
 
+// Bucket of grid cell (x, y, z) in a hash table of mask + 1 buckets (Teschner
+// et al., "Optimized Spatial Hashing for Collision Detection of Deformable
+// Objects", VMV 2003).  The merge grid, its builder and the stand-alone point
+// grids all use this one function.
+__device__ __forceinline__ uint32_t grid_hash(int x, int y, int z, uint32_t mask) {
+  return (((uint32_t)x * 73856093u) ^ ((uint32_t)y * 19349663u) ^ ((uint32_t)z * 83492791u)) & mask;
+}
+
 struct RayPre {
   float3 o, d, inv;
   int kx, ky, kz;

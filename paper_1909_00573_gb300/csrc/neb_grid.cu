@@ -96,16 +96,11 @@ cudaError_t scan_exclusive(const int* d_in, int* d_out, size_t n, Scratch& scrat
 }
 
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t cell_hash(int x, int y, int z, uint32_t mask) {
-  // Teschner et al., "Optimized Spatial Hashing for Collision Detection of Deformable Objects" (VMV 2003)
-  return (((uint32_t)x * 73856093u) ^ ((uint32_t)y * 19349663u) ^ ((uint32_t)z * 83492791u)) & mask;
-}
-
 __device__ __forceinline__ uint32_t point_bucket(float3 p, float3 gmin, float cell_inv, uint32_t mask) {
   int cx = (int)floorf((p.x - gmin.x) * cell_inv);
   int cy = (int)floorf((p.y - gmin.y) * cell_inv);
   int cz = (int)floorf((p.z - gmin.z) * cell_inv);
-  return cell_hash(cx, cy, cz, mask);
+  return grid_hash(cx, cy, cz, mask);
 }
 
 __global__ void k_grid_count(NeeStore nv, DevCounters* cnt, int cap, float3 gmin, float cell_inv, uint32_t mask,
@@ -177,7 +172,7 @@ __global__ void k_pts_query(const float4* __restrict__ sorted, const int* __rest
         oz = (gz - (float)cz >= 0.5f) ? 1 : -1;
     uint32_t bk[8];
     for (int c = 0; c < 8; ++c)
-      bk[c] = cell_hash(cx + ((c & 1) ? ox : 0), cy + ((c & 2) ? oy : 0), cz + ((c & 4) ? oz : 0), mask);
+      bk[c] = grid_hash(cx + ((c & 1) ? ox : 0), cy + ((c & 2) ? oy : 0), cz + ((c & 4) ? oz : 0), mask);
     int cnt = 0;
     for (int c = 0; c < 8; ++c) {
       bool dup = false;
@@ -191,6 +186,16 @@ __global__ void k_pts_query(const float4* __restrict__ sorted, const int* __rest
     }
     out[i] = cnt;
   }
+}
+
+cudaError_t build_point_grid(const float* d_pts, int n, float cell, float3 gmin, uint32_t table, int* bucket_count,
+                             int* bucket_start, int* vert_bucket, float4* sorted, Scratch& sc, cudaStream_t st) {
+  const int nb = capped_blocks(n, 256, 152 * 8);
+  if (n > 0) k_pts_count<<<nb, 256, 0, st>>>(d_pts, n, gmin, 1.0f / cell, table - 1, bucket_count, vert_bucket);
+  cudaError_t e = scan_exclusive(bucket_count, bucket_start, (size_t)table + 1, sc, st);
+  if (e != cudaSuccess) return e;
+  if (n > 0) k_pts_scatter<<<nb, 256, 0, st>>>(d_pts, n, vert_bucket, bucket_start, bucket_count, sorted);
+  return cudaGetLastError();
 }
 
 cudaError_t count_neighbours_device(const float* d_pts, int n, const float* d_q, int m, float r, int* d_out,
@@ -213,9 +218,7 @@ cudaError_t count_neighbours_device(const float* d_pts, int n, const float* d_q,
   cudaMallocAsync(&sorted, sizeof(float4) * (size_t)(n > 0 ? n : 1), st);
   cudaMallocAsync(&sc.data, sizeof(int) * sc.n, st);
   cudaMemsetAsync(bc, 0, sizeof(int) * (table + 1), st);
-  if (n > 0) k_pts_count<<<(n + 255) / 256, 256, 0, st>>>(d_pts, n, gmin, 1.0f / cs, table - 1, bc, vb);
-  scan_exclusive(bc, bs, table + 1, sc, st);
-  if (n > 0) k_pts_scatter<<<(n + 255) / 256, 256, 0, st>>>(d_pts, n, vb, bs, bc, sorted);
+  build_point_grid(d_pts, n, cs, gmin, table, bc, bs, vb, sorted, sc, st);
   if (m > 0)
     k_pts_query<<<(m + 255) / 256, 256, 0, st>>>(sorted, bs, d_q, m, r * r, gmin, 1.0f / cs, table - 1, d_out);
   e = cudaGetLastError();

@@ -213,6 +213,10 @@ SceneView scene_view(const neb_ctx* c);
 
 // neb_bvh.cu
 cudaError_t build_bvh(neb_ctx* c);
+// 4-wide BVH over the n primitives of view s (triangles, then spheres; a
+// sphere of radius 0 is a point) into a new device array *nodes_out;
+// builder 0 PLOC, 1 Karras.  Synchronises st.
+cudaError_t build_bvh4(const SceneView& s, int n, int builder, cudaStream_t st, BVH4Node** nodes_out, int* n4_out);
 cudaError_t launch_trace_debug(const SceneView& s, const float* d_rays, int n, int* d_prim, float* d_t,
                                uint32_t* d_status, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* d_ctr, int n, uint2 key, uint32_t* d_out, cudaStream_t st);
@@ -227,6 +231,12 @@ cudaError_t scan_exclusive(const int* d_in, int* d_out, size_t n, Scratch& scrat
 cudaError_t grid_build(neb_ctx* c, const IterParams& ip, const IterSlot& sl, cudaStream_t st);
 cudaError_t count_neighbours_device(const float* d_pts, int n, const float* d_q, int m, float r, int* d_out,
                                     cudaStream_t st);
+// Hashed grid over n points [n][3] with cubic cells of side `cell` from gmin
+// and `table` buckets (a power of two): counts (zero on entry, consumed back
+// to zero), exclusive-scanned starts (table + 1) and the points in bucket
+// order.
+cudaError_t build_point_grid(const float* d_pts, int n, float cell, float3 gmin, uint32_t table, int* bucket_count,
+                             int* bucket_start, int* vert_bucket, float4* sorted, Scratch& sc, cudaStream_t st);
 
 // neb_octree.cu
 OctreeParams octree_params(const float smin[3], const float smax[3], int capacity, int split_factor);

@@ -114,11 +114,6 @@ __device__ __forceinline__ float light_pdf(const SceneView& s, int li, float3 y,
   return psel * ia;
 }
 
-__device__ __forceinline__ uint32_t grid_hash(int x, int y, int z, uint32_t mask) {
-  // Teschner et al., "Optimized Spatial Hashing for Collision Detection of Deformable Objects" (VMV 2003)
-  return (((uint32_t)x * 73856093u) ^ ((uint32_t)y * 19349663u) ^ ((uint32_t)z * 83492791u)) & mask;
-}
-
 // ---------------------------------------------------------------------------
 // pass 1
 // ---------------------------------------------------------------------------

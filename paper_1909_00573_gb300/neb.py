@@ -27,7 +27,7 @@ EXPORTS = ["neb_create", "neb_destroy", "neb_last_error", "neb_scene_upload", "n
            "neb_octree_create", "neb_octree_destroy", "neb_octree_set_iteration", "neb_octree_insert",
            "neb_octree_density", "neb_octree_read", "neb_octree_load", "neb_count_neighbours",
            "neb_count_neighbours_noalloc", "neb_iterate_batch", "neb_job_device_bytes", "neb_get_tuning",
-           "neb_set_tuning", "neb_autotune"]
+           "neb_set_tuning", "neb_autotune", "neb_density_estimators", "neb_read_nee_vertices"]
 NOALLOC_MAX_POINTS = 1 << 18
 
 
@@ -111,6 +111,9 @@ def lib():
             "neb_get_tuning": ([vp, vp], C.c_int),
             "neb_set_tuning": ([vp, vp], C.c_int),
             "neb_autotune": ([vp, C.c_int, vp], C.c_int),
+            "neb_density_estimators": ([vp, vp, C.c_int, vp, vp, C.c_int, C.c_int, C.c_float, C.c_int, vp, vp],
+                                       C.c_int),
+            "neb_read_nee_vertices": ([vp, vp, vp, C.c_int, vp], C.c_int),
             "neb_job_device_bytes": ([vp, C.c_int, C.c_int, C.c_int, C.c_int, vp], C.c_int),
             "neb_count_neighbours": ([vp, C.c_int, vp, C.c_int, C.c_float, vp], C.c_int),
             "neb_count_neighbours_noalloc": ([vp, C.c_int, vp, C.c_int, C.c_float, vp, vp], C.c_int),
@@ -182,6 +185,14 @@ class Context:
 
     def iterate(self, n=1):
         self._c(lib().neb_iterate(self.h, int(n)))
+
+    def read_nee_vertices(self):
+        n = C.c_int(0)
+        self._c(lib().neb_read_nee_vertices(self.h, None, None, 0, C.byref(n)))
+        pos = np.zeros((n.value, 3), np.float32)
+        nrm = np.zeros((n.value, 3), np.float32)
+        self._c(lib().neb_read_nee_vertices(self.h, _p(pos), _p(nrm), n.value, C.byref(n)))
+        return pos, nrm
 
     def tuning(self):
         t = Tuning()
@@ -322,6 +333,20 @@ class Octree:
     def load(self, nodes, alloc, depth):
         N = np.ascontiguousarray(nodes, np.int32)
         _check(lib().neb_octree_load(self.h, _p(N), len(N), int(alloc), int(depth)))
+
+
+def density_estimators(pos, nrm, scene_min, scene_max, octree_capacity, split_factor, radius, k):
+    """neb_density_estimators: rho[3][n] (octree, naive, k nearest) and the
+    device milliseconds of each (structure build plus queries)."""
+    P = np.ascontiguousarray(pos, np.float32).reshape(-1, 3)
+    N = np.ascontiguousarray(nrm, np.float32).reshape(-1, 3)
+    lo = np.ascontiguousarray(scene_min, np.float32)
+    hi = np.ascontiguousarray(scene_max, np.float32)
+    rho = np.zeros((3, len(P)), np.float32)
+    ms = np.zeros(3, np.float64)
+    _check(lib().neb_density_estimators(_p(P), _p(N), len(P), _p(lo), _p(hi), int(octree_capacity),
+                                        int(split_factor), float(radius), int(k), _p(rho), _p(ms)))
+    return rho, ms
 
 
 def iterate_batch(contexts, n_iterations):
