@@ -53,6 +53,7 @@ static double now_seconds(void) {
 }
 
 #define PI_D 3.14159265358979323846
+#define ORC_LP_STREAM 0x40000000u /* Philox stream of light photon i: + bounce */
 #define TWO_PI_F 6.28318530717958647692f
 #define INV_PI_F 0.318309886183790671538f
 
@@ -941,10 +942,14 @@ typedef struct {
 
 /* Path v_0 .. v_l: v_0 the camera, v_l the light point.  u[i], L[i] are the
  * unit direction and length of segment (v_i, v_{i+1}), i = 0 .. l-1.  p_l is
- * the NEE area pdf of v_l from v_{l-1}; rho the density at v_{l-1}.  Fills
- * p_e, p_E and nP[k] (k = 1 .. l-2, already multiplied by n_P). */
+ * the NEE area pdf of v_l from v_{l-1}; rho the density at v_{l-1}; p_l_lp
+ * the area pdf of v_l under light-photon emission and n_lp their number.
+ * Fills p_e, p_E, nP[k] (k = 1 .. l-2, Eq. photonpdf times n_P) and nLP[k]
+ * (k = 1 .. l-1, Eq. stdphotonpdf times n_LP; the light emits cosine-
+ * weighted about its normal, so p_{l -> l-1} = cos_y / pi |cos_{l-1}| / L^2). */
 static void path_pdfs(const mv_t* v, const v3* u, const float* L, int l, double p_l, double rho, double r,
-                      uint32_t mask, double* p_e, double* p_E, double* nP) {
+                      uint32_t mask, double n_lp, double p_l_lp, double* p_e, double* p_E, double* nP,
+                      double* nLP) {
   double F[64], R[64];
   F[1] = 1.0;
   for (int i = 2; i <= l; ++i) {
@@ -977,23 +982,38 @@ static void path_pdfs(const mv_t* v, const v3* u, const float* L, int l, double 
     }
     nP[k] = x;
   }
+  for (int k = 1; k <= l - 1; ++k) nLP[k] = 0.0;
+  if ((mask & 8u) && n_lp > 0.0 && l >= 2) {
+    double cos_y = (double)vdot(v[l].n_out, vneg(u[l - 1]));
+    double c = fabs((double)vdot(v[l - 1].n_out, u[l - 1]));
+    R[l - 1] = cos_y > 0.0 ? cos_y / PI_D * c / ((double)L[l - 1] * (double)L[l - 1]) : 0.0;
+    for (int k = 1; k <= l - 1; ++k) {
+      if (v[k].delta) continue;
+      double x = n_lp * PI_D * r * r * p_l_lp;
+      for (int i = k; i <= l - 1; ++i) x *= R[i];
+      for (int i = 1; i <= k; ++i) x *= F[i];
+      nLP[k] = x;
+    }
+  }
 }
 
 static double mis_weight(const mv_t* v, const v3* u, const float* L, int l, double p_l, double rho, double r,
-                         uint32_t mask, int strategy /* 0 e, 1 E, 2 P */, int kmerge) {
-  double pe, pE, nP[64];
-  path_pdfs(v, u, L, l, p_l, rho, r, mask, &pe, &pE, nP);
+                         uint32_t mask, double n_lp, double p_l_lp, int strategy /* 0 e, 1 E, 2 P, 3 LP */,
+                         int kmerge) {
+  double pe, pE, nP[64], nLP[64];
+  path_pdfs(v, u, L, l, p_l, rho, r, mask, n_lp, p_l_lp, &pe, &pE, nP, nLP);
   double sum = pe + pE;
   for (int k = 1; k <= l - 2; ++k) sum += nP[k];
-  double own = strategy == 0 ? pe : (strategy == 1 ? pE : nP[kmerge]);
+  for (int k = 1; k <= l - 1; ++k) sum += nLP[k];
+  double own = strategy == 0 ? pe : (strategy == 1 ? pE : (strategy == 2 ? nP[kmerge] : nLP[kmerge]));
   return sum > 0.0 ? own / sum : 0.0;
 }
 
-int orc_mis_weights(const float* verts, int n_verts, const float* light, float merge_radius, double rho,
-                    uint32_t mask, double* w_out) {
+static int mis_weights_impl(const float* verts, int n_verts, const float* light, float merge_radius, double rho,
+                            uint32_t mask, double n_lp, double p_l_lp, int with_lp, double* w_out) {
   /* verts: [n_verts][7] = pos, normal, type (0 Lambertian albedo 1, 1 delta);
-   * v_0 is the camera.  light: pos, normal, p_l.  w_out: [l+1] = w_e, w_E,
-   * w_P1 .. w_P(l-2) with l = n_verts. */
+   * v_0 is the camera.  light: pos, normal, p_l (, p_l^LP).  w_out: [l+1] =
+   * w_e, w_E, w_P1 .. w_P(l-2) with l = n_verts, then w_LP1 .. w_LP(l-1). */
   static mat_t lam = {MT_DIFFUSE, {1, 1, 1}, {0, 0, 0}, 1, 0};
   static mat_t gl = {MT_DIELECTRIC, {0, 0, 0}, {0, 0, 0}, 1.5f, 0};
   int l = n_verts;
@@ -1018,14 +1038,27 @@ int orc_mis_weights(const float* verts, int n_verts, const float* light, float m
     L[i] = sqrtf(vdot(d, d));
     u[i] = vnorm(d);
   }
-  double pe, pE, nP[64];
-  path_pdfs(v, u, L, l, (double)light[6], rho, merge_radius, mask, &pe, &pE, nP);
+  double pe, pE, nP[64], nLP[64];
+  path_pdfs(v, u, L, l, (double)light[6], rho, merge_radius, mask, n_lp, p_l_lp, &pe, &pE, nP, nLP);
   double sum = pe + pE;
   for (int k = 1; k <= l - 2; ++k) sum += nP[k];
+  for (int k = 1; k <= l - 1; ++k) sum += nLP[k];
   w_out[0] = sum > 0 ? pe / sum : 0;
   w_out[1] = sum > 0 ? pE / sum : 0;
   for (int k = 1; k <= l - 2; ++k) w_out[1 + k] = sum > 0 ? nP[k] / sum : 0;
+  if (with_lp)
+    for (int k = 1; k <= l - 1; ++k) w_out[l - 1 + k] = sum > 0 ? nLP[k] / sum : 0;
   return 0;
+}
+
+int orc_mis_weights(const float* verts, int n_verts, const float* light, float merge_radius, double rho,
+                    uint32_t mask, double* w_out) {
+  return mis_weights_impl(verts, n_verts, light, merge_radius, rho, mask & 7u, 0.0, 0.0, 0, w_out);
+}
+
+int orc_mis_weights_lp(const float* verts, int n_verts, const float* light, float merge_radius, double rho,
+                       uint32_t mask, double n_lp, double* w_out) {
+  return mis_weights_impl(verts, n_verts, light, merge_radius, rho, mask, n_lp, (double)light[7], 1, w_out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1089,6 +1122,15 @@ static double light_pdf(const scene_t* s, int li, v3 y, v3 x) {
   const light_t* L = &s->lights[li];
   if (L->kind == 0) return L->psel / (double)L->area;
   return L->psel * sph_pdf_area(s, L->prim, y, x);
+}
+
+/* area pdf of a light point under light-photon emission: the light chosen
+ * as for NEE, the point uniform on the whole light surface */
+static double lp_light_pdf(const scene_t* s, int li) {
+  const light_t* L = &s->lights[li];
+  if (L->kind == 0) return L->psel / (double)L->area;
+  double R = s->sph[(size_t)(L->prim - s->nt) * 4 + 3];
+  return L->psel / (4.0 * PI_D * R * R);
 }
 
 static int sample_light(const ctx_t* c, uint32_t pixel, uint32_t stream, v3 x, int* li, v3* y, v3* ny,
@@ -1277,13 +1319,14 @@ int orc_render(const orc_scene* scene_in, const orc_config* cfg, int n_iter, dou
   double kernel = 1.0 / (PI_D * (double)c.r * (double)c.r);
   float r2 = c.r * c.r;
   int first = cfg->first_iteration > 0 ? cfg->first_iteration : 1;
+  const double n_lp = (cfg->strategy_mask & 8u) ? (double)(cfg->lp_photons > 0 ? cfg->lp_photons : 0) : 0.0;
 
   for (int it = 0; it < n_iter; ++it) {
     double t_start = now_seconds();
     int iter = first + it;
     int last = it == n_iter - 1;
     c.rng.iter = (uint32_t)iter;
-    if (last && last_split) memset(last_split, 0, sizeof(double) * 3 * (size_t)P * 3);
+    if (last && last_split) memset(last_split, 0, sizeof(double) * 4 * (size_t)P * 3);
     orc_octree_set_iteration(oct, iter);
     /* ---- pass 1: view paths, NEE vertices into the octree, random hits ---- */
     int nrh = 0;
@@ -1329,7 +1372,8 @@ int orc_render(const orc_scene* scene_in, const orc_config* cfg, int n_iter, dou
           mv[k + 1].mat = NULL;
           mv[k + 1].n_in = mv[k + 1].n_out = mv[k + 1].n_bsdf = v->ny;
           mv[k + 1].delta = 0;
-          double w = mis_weight(mv, u, L, k + 1, v->p_l, v->rho, c.r, cfg->strategy_mask, 1, 0);
+          double w = mis_weight(mv, u, L, k + 1, v->p_l, v->rho, c.r, cfg->strategy_mask, n_lp,
+                                lp_light_pdf(&s, v->light), 1, 0);
           c3 contrib = cscale(cmul(cmul(v->tau, f), v->dE), w);
           double* a = accum + (size_t)(pb + q) * 3;
           a[0] += contrib.r; a[1] += contrib.g; a[2] += contrib.b;
@@ -1430,7 +1474,8 @@ int orc_render(const orc_scene* scene_in, const orc_config* cfg, int n_iter, dou
                 mv[l].mat = NULL;
                 mv[l].n_in = mv[l].n_out = mv[l].n_bsdf = nv->ny;
                 mv[l].delta = 0;
-                double wgt = mis_weight(mv, u, L, l, nv->p_l, nv->rho, c.r, cfg->strategy_mask, 2, kk);
+                double wgt = mis_weight(mv, u, L, l, nv->p_l, nv->rho, c.r, cfg->strategy_mask, n_lp,
+                                        lp_light_pdf(&s, nv->light), 2, kk);
                 c3 contrib = cscale(cmul(cmul(cvx->tau, f), phi), kernel * wgt);
                 st[ORC_ST_MERGES]++;
                 double* a = accum + (size_t)cpix * 3;
@@ -1451,6 +1496,145 @@ int orc_render(const orc_scene* scene_in, const orc_config* cfg, int n_iter, dou
         }
       }
     }
+    /* ---- pass 2d: conventional light photons (Sec. 6.1), merged at view vertices ---- */
+    if (n_lp > 0.0 && s.nl > 0 && D >= 2) {
+      int nm = 0;  /* view vertices x_k, 1 <= k <= D-1, non-delta */
+      for (int q = 0; q < np; ++q) {
+        cv_t* path = paths + (size_t)q * (D + 1);
+        for (int k = 1; k <= plen[q] && k <= D - 1; ++k) {
+          if (!path[k].is_nee || path[k].delta) continue;
+          mref[nm].x = path[k].pos.x;
+          mref[nm].pixel = pb + q;
+          mref[nm].k = k;
+          nm++;
+        }
+      }
+      qsort(mref, (size_t)nm, sizeof(mref_t), mref_cmp);
+      for (int i = 0; i < cfg->lp_photons; ++i) {
+        const uint32_t lpix = (uint32_t)i, st0 = ORC_LP_STREAM;
+        uint32_t x0 = rng_raw(&c.rng, lpix, st0, 0);
+        int li = (int)(((uint64_t)(x0 >> 8) * (uint64_t)s.nl) >> 24);
+        float ua = rng_u(&c.rng, lpix, st0, 1);
+        if (!(ua < s.alias_prob[li])) li = s.alias_idx[li];
+        float u2 = rng_u(&c.rng, lpix, st0, 2), u3 = rng_u(&c.rng, lpix, st0, 3);
+        const light_t* Lt = &s.lights[li];
+        v3 y, ny, yerr;
+        if (Lt->kind == 0) {
+          float b1 = u2, b2 = u3;
+          if (b1 + b2 > 1.0f) { b1 = 1.0f - b1; b2 = 1.0f - b2; }
+          v3 a = tri_v(&s, Lt->prim, 0), bb = tri_v(&s, Lt->prim, 1), cc = tri_v(&s, Lt->prim, 2);
+          v3 e1 = vsub(bb, a), e2 = vsub(cc, a);
+          y = vadd(vadd(a, vmul(e1, b1)), vmul(e2, b2));
+          ny = vnorm(vcross(e1, e2));
+          yerr = mk3(GAMMA5 * (fabsf(a.x) + fabsf(e1.x * b1) + fabsf(e2.x * b2)),
+                     GAMMA5 * (fabsf(a.y) + fabsf(e1.y * b1) + fabsf(e2.y * b2)),
+                     GAMMA5 * (fabsf(a.z) + fabsf(e1.z * b1) + fabsf(e2.z * b2)));
+        } else {
+          const float* sp = s.sph + (size_t)(Lt->prim - s.nt) * 4;
+          v3 ce = vload(sp);
+          float z = 1.0f - 2.0f * u2;
+          float rr = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+          float ph = TWO_PI_F * u3;
+          ny = mk3(rr * cosf(ph), rr * sinf(ph), z);
+          y = vadd(ce, vmul(ny, sp[3]));
+          yerr = mk3(GAMMA5 * (fabsf(ce.x) + sp[3]), GAMMA5 * (fabsf(ce.y) + sp[3]), GAMMA5 * (fabsf(ce.z) + sp[3]));
+        }
+        const double p_lp = lp_light_pdf(&s, li);
+        float u4 = rng_u(&c.rng, lpix, st0, 4), u5 = rng_u(&c.rng, lpix, st0, 5);
+        float er = sqrtf(u4), eph = TWO_PI_F * u5, ez = sqrtf(fmaxf(0.0f, 1.0f - u4));
+        v3 w = from_local(ny, er * cosf(eph), er * sinf(eph), ez);
+        if (!(ez > 0.0f)) continue;
+        st[ORC_ST_PHOTONS]++;
+        /* flux Le cos / (p_lp cos / pi) / n_LP */
+        c3 phi = cscale(light_le(&s, Lt->prim), PI_D / (p_lp * n_lp));
+        const v3 yl = offset_origin(y, ny, yerr, w);  /* the light vertex of every LP path */
+        v3 o = yl;
+        v3 ph_n[64], ph_dir[64];
+        float ph_t[64];
+        int ph_mat[64];
+        v3 dir = w, hp1 = mk3(0, 0, 0);
+        double rho1 = 0.0, p_l1 = 0.0;
+        for (int j = 1; j <= D - 1; ++j) {
+          float t;
+          int prim = trace_closest(&s, &b, o, dir, INFINITY, &t);
+          if (prim < 0) break;
+          v3 hp, herr;
+          hit_point(&s, o, dir, prim, t, &hp, &herr);
+          v3 hn = prim_normal(&s, prim, hp);
+          int hm = s.prim_mat[prim];
+          const mat_t* hmat = &s.mats[hm];
+          ph_n[j] = hn;
+          ph_mat[j] = hm;
+          ph_dir[j] = dir;
+          ph_t[j] = t;
+          if (mat_black(hmat)) break;
+          st[ORC_ST_PHOTON_HITS]++;
+          if (j == 1) {
+            /* light end of every LP path of this photon: density, NEE pdf
+             * and the light segment at the first hit */
+            float pp[3] = {hp.x, hp.y, hp.z}, nn[3] = {hn.x, hn.y, hn.z};
+            rho1 = orc_octree_density(oct, pp, nn, cfg->density_mode == 0);
+            p_l1 = light_pdf(&s, li, yl, hp);
+            hp1 = hp;
+          }
+          if (!mat_delta(hmat)) {
+            int lo = 0, hi = nm;
+            float xlo = hp.x - c.r;
+            while (lo < hi) { int mid = (lo + hi) / 2; if (mref[mid].x < xlo) lo = mid + 1; else hi = mid; }
+            for (int ci = lo; ci < nm && mref[ci].x <= hp.x + c.r; ++ci) {
+              int cpix = mref[ci].pixel, kk = mref[ci].k;
+              if (kk + j > D) continue;
+              cv_t* cpath = paths + (size_t)(cpix - pb) * (D + 1);
+              cv_t* cvx = &cpath[kk];
+              float dx = cvx->pos.x - hp.x, dy = cvx->pos.y - hp.y, dz = cvx->pos.z - hp.z;
+              float d2 = dx * dx + dy * dy + dz * dz;
+              if (!(d2 <= r2)) continue;
+              const mat_t* cm = &s.mats[cvx->mat];
+              c3 f = bsdf_eval(cm, cvx->n, vneg(cvx->din), vneg(dir));
+              if (!(cmax(f) > 0.0)) continue;
+              /* camera v_0..v_kk, photon hits j-1 .. 1, light vertex o */
+              int l = kk + j;
+              mv_camera(&s, cpath, kk, mv, u, L);
+              mv[kk].n_out = hn;
+              for (int q2 = 1; q2 <= j - 1; ++q2) {
+                int pi = j - q2;
+                mv[kk + q2].mat = &s.mats[ph_mat[pi]];
+                mv[kk + q2].n_bsdf = mv[kk + q2].n_in = mv[kk + q2].n_out = ph_n[pi];
+                mv[kk + q2].delta = mat_delta(&s.mats[ph_mat[pi]]);
+                u[kk + q2 - 1] = vneg(ph_dir[pi + 1]);
+                L[kk + q2 - 1] = ph_t[pi + 1];
+              }
+              v3 ls = vsub(yl, hp1);
+              u[l - 1] = vneg(w);
+              L[l - 1] = sqrtf(vdot(ls, ls));
+              mv[l].mat = NULL;
+              mv[l].n_in = mv[l].n_out = mv[l].n_bsdf = ny;
+              mv[l].delta = 0;
+              double wgt = mis_weight(mv, u, L, l, p_l1, rho1, c.r, cfg->strategy_mask, n_lp, p_lp, 3, kk);
+              c3 contrib = cscale(cmul(cmul(cvx->tau, f), phi), kernel * wgt);
+              st[ORC_ST_MERGES]++;
+              double* a = accum + (size_t)cpix * 3;
+              a[0] += contrib.r; a[1] += contrib.g; a[2] += contrib.b;
+              if (last && last_split) {
+                double* ls3 = last_split + (size_t)3 * P * 3 + (size_t)cpix * 3;
+                ls3[0] += contrib.r; ls3[1] += contrib.g; ls3[2] += contrib.b;
+              }
+            }
+          }
+          if (j == D - 1) break;
+          float ul = rng_u(&c.rng, lpix, st0 + (uint32_t)j, 4);
+          float ub1 = rng_u(&c.rng, lpix, st0 + (uint32_t)j, 5);
+          float ub2 = rng_u(&c.rng, lpix, st0 + (uint32_t)j, 6);
+          v3 wi;
+          c3 wt;
+          if (!bsdf_sample(hmat, hn, vneg(dir), ul, ub1, ub2, 0, &wi, &wt)) break;
+          phi = cmul(phi, wt);
+          if (!(cmax(phi) > 0.0)) break;
+          o = offset_origin(hp, hn, herr, wi);
+          dir = wi;
+        }
+      }
+    }
     /* ---- pass 3: self emission of the stored random hits ---- */
     if (cfg->strategy_mask & 1u) {
       for (int e = 0; e < nrh; ++e) {
@@ -1466,7 +1650,7 @@ int orc_render(const orc_scene* scene_in, const orc_config* cfg, int n_iter, dou
           mv[k].mat = NULL;
           mv[k].n_in = mv[k].n_out = mv[k].n_bsdf = v->n;
           mv[k].delta = 0;
-          w = mis_weight(mv, u, L, k, p_l, prev->rho, c.r, cfg->strategy_mask, 0, 0);
+          w = mis_weight(mv, u, L, k, p_l, prev->rho, c.r, cfg->strategy_mask, n_lp, lp_light_pdf(&s, li), 0, 0);
         }
         c3 contrib = cscale(cmul(v->tau, rh[e].le), w);
         double* a = accum + (size_t)pixel * 3;

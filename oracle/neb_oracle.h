@@ -42,10 +42,11 @@ typedef struct {
   int octree_capacity, split_factor;
   uint64_t seed;
   int density_mode;        /* 0 robust (median of 5), 1 single query */
-  uint32_t strategy_mask;  /* 1 random hit, 2 NEE, 4 NEB photon merge */
+  uint32_t strategy_mask;  /* 1 random hit, 2 NEE, 4 NEB photon merge, 8 conventional light photon merge */
   int first_iteration;     /* 1-based index of the first iteration rendered */
   int pixel_begin, pixel_end; /* camera paths traced: [begin, end) (row-major), end<=0: all */
   double* iter_seconds;       /* optional [n_iter]: wall time of each iteration (BVH build excluded) */
+  int lp_photons;             /* conventional light photons per iteration (n_LP, Sec. 6.1; strategy bit 8) */
 } orc_config;
 
 /* stats[] slots filled by orc_render (summed over iterations) */
@@ -105,6 +106,12 @@ void orc_density_knn(const float* pts, int n, int k, float* out);
  * the MIS pin tests).  See the definition of orc_path in the source. */
 int orc_mis_weights(const float* verts, int n_verts, const float* light,
                     float merge_radius, double rho, uint32_t mask, double* w_out);
+/* The same with conventional light photons (Sec. 6.1): light = pos, normal,
+ * p_l (NEE area pdf of the light point), p_l^LP (its pdf under light-photon
+ * emission); n_lp light photons per iteration; mask bit 8 enables them.
+ * w_out: [l + 1 + (l - 1)] = w_e, w_E, w_P1 .. w_P(l-2), w_LP1 .. w_LP(l-1). */
+int orc_mis_weights_lp(const float* verts, int n_verts, const float* light, float merge_radius, double rho,
+                       uint32_t mask, double n_lp, double* w_out);
 
 /* BSDF probes for the pin tests (material row in the scenes layout). */
 int orc_bsdf_probe(const float* mrow, const float* n, const float* wo, const float* u, int camera, float* wi,

@@ -47,7 +47,7 @@ class _Config(C.Structure):
                 ("merge_radius", C.c_float), ("octree_capacity", C.c_int), ("split_factor", C.c_int),
                 ("seed", C.c_uint64), ("density_mode", C.c_int), ("strategy_mask", C.c_uint32),
                 ("first_iteration", C.c_int), ("pixel_begin", C.c_int), ("pixel_end", C.c_int),
-                ("iter_seconds", C.c_void_p)]
+                ("iter_seconds", C.c_void_p), ("lp_photons", C.c_int)]
 
 
 _lib = None
@@ -81,6 +81,9 @@ def lib():
         L.orc_mis_weights.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_float, C.c_double, C.c_uint32,
                                       C.c_void_p]
         L.orc_mis_weights.restype = C.c_int
+        L.orc_mis_weights_lp.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_float, C.c_double, C.c_uint32,
+                                         C.c_double, C.c_void_p]
+        L.orc_mis_weights_lp.restype = C.c_int
         L.orc_bsdf_probe.argtypes = [C.c_void_p] * 4 + [C.c_int] + [C.c_void_p] * 4
         L.orc_bsdf_probe.restype = C.c_int
         L.orc_bsdf_eval_probe.argtypes = [C.c_void_p] * 6
@@ -195,18 +198,32 @@ def mis_weights(verts, light, merge_radius, rho, mask=7):
     return w[:len(V)]   # w_e, w_E, w_P1 .. w_P(l-2)
 
 
+def mis_weights_lp(verts, light, merge_radius, rho, n_lp, mask=15):
+    """light = pos, normal, p_l, p_l^LP.  Returns w_e, w_E, w_P1 .. w_P(l-2),
+    w_LP1 .. w_LP(l-1) with l = len(verts)."""
+    V = np.ascontiguousarray(verts, np.float32).reshape(-1, 7)
+    Lt = np.ascontiguousarray(light, np.float32).reshape(8)
+    w = np.zeros(2 * len(V) + 1, np.float64)
+    rc = lib().orc_mis_weights_lp(_ptr(V), len(V), _ptr(Lt), C.c_float(merge_radius), C.c_double(rho),
+                                  C.c_uint32(mask), C.c_double(n_lp), _ptr(w))
+    assert rc == 0
+    return w[:2 * len(V) - 1]
+
+
 def render(scene, cfg, n_iter=None, first_iteration=1, pixel_range=None, want_split=True, want_rho=False):
     """Run the oracle.  Returns dict with accum [H,W,3] (sum over iterations),
-    split [3,H,W,3] of the last iteration, rho [H*W, D-1] and stats."""
+    split [4,H,W,3] of the last iteration (random hits, NEE, NEB photon merges,
+    light-photon merges), rho [H*W, D-1] and stats."""
     n_iter = cfg.iterations if n_iter is None else n_iter
     s, keep = _scene_struct(scene)
     pb, pe = (0, 0) if pixel_range is None else pixel_range
     iter_sec = np.zeros(max(int(n_iter), 1), np.float64)
     c = _Config(cfg.width, cfg.height, cfg.max_depth, cfg.merge_radius, cfg.octree_capacity, cfg.split_factor,
-                cfg.seed, cfg.density_mode, cfg.strategy_mask, first_iteration, pb, pe, _ptr(iter_sec))
+                cfg.seed, cfg.density_mode, cfg.strategy_mask, first_iteration, pb, pe, _ptr(iter_sec),
+                getattr(cfg, "lp_photons", 0))
     P = cfg.width * cfg.height
     accum = np.zeros((P, 3), np.float64)
-    split = np.zeros((3, P, 3), np.float64) if want_split else None
+    split = np.zeros((4, P, 3), np.float64) if want_split else None
     rho = np.zeros((P, max(cfg.max_depth - 1, 1)), np.float32) if want_rho else None
     stats = np.zeros(len(ST_NAMES), np.int64)
     rc = lib().orc_render(C.byref(s), C.byref(c), int(n_iter), _ptr(accum), _ptr(split), _ptr(rho), _ptr(stats))
@@ -216,7 +233,7 @@ def render(scene, cfg, n_iter=None, first_iteration=1, pixel_range=None, want_sp
            "stats": dict(zip(ST_NAMES, stats.tolist())),
            "iter_seconds": iter_sec[:n_iter]}
     if want_split:
-        out["split"] = split.reshape(3, cfg.height, cfg.width, 3)
+        out["split"] = split.reshape(4, cfg.height, cfg.width, 3)
     if want_rho:
         out["rho"] = rho
     return out

@@ -92,7 +92,9 @@ class RenderConfig:
     seed: int = 0
     octree_mode: int = 0        # 0 concurrent, 1 deterministic sequential insert
     density_mode: int = 0       # 0 robust median of five, 1 single query
-    strategy_mask: int = 7      # bit 0 random hit (e), bit 1 NEE (E), bit 2 NEB photon merge (P)
+    strategy_mask: int = 7      # bit 0 random hit (e), bit 1 NEE (E), bit 2 NEB photon merge (P),
+                                # bit 3 conventional light-photon merge (LP, Sec. 6.1)
+    lp_photons: int = 0         # light photons per iteration (n_LP) when bit 3 is set
 
 
 class SplitMix64:

@@ -115,6 +115,58 @@ def test_plane_under_sphere_light_closed_form(oracle):
     assert sp[0].sum() > 0 and sp[1].sum() > 0 and sp[2].sum() == 0
 
 
+def _plane_expectation(s, W, H, a, R, h, L):
+    eye, d = _camera_rays(s.cam, W, H, 6)
+    t = -eye[1] / d[..., 1]
+    x = eye + t[..., None] * d
+    dist = np.linalg.norm(x - np.array([0, h, 0]), axis=-1)
+    on_plane = (t > 0) & (np.abs(x[..., 0]) <= 50) & (np.abs(x[..., 2]) <= 50)
+    return np.where(on_plane, a * L * R * R * h / dist ** 3, 0.0).mean(axis=(2, 3))
+
+
+def test_light_photons_alone_reproduce_the_plane_irradiance(oracle):
+    """Conventional light photons only (strategy 8, Sec. 6.1): photon mapping
+    from the sphere light onto the plane converges to (a/pi) E, E = pi L
+    (R/d)^2 cos(theta), up to the kernel's blur (relative curvature of E
+    times r^2 / 8: about 1e-3 here).  Checks the photon flux (L pi / (p_l^LP
+    n_LP), cosine emission, uniform points on the whole sphere)."""
+    a, R, h, L = 0.6, 0.1, 1.0, 5.0
+    s = scenes.plane_under_sphere(a, R, h, L)
+    W = H = 32
+    c = cfg(W, H, 3, mask=8, r=0.05)
+    c.lp_photons = 100000
+    imgs = per_iteration_images(oracle, s, c, 4)[..., 0]
+    expect = _plane_expectation(s, W, H, a, R, h, L)
+    centre = expect > 0.25 * expect.max()
+    got = imgs.mean(0)[centre].sum()
+    assert abs(got / expect[centre].sum() - 1.0) < 0.03, got / expect[centre].sum()
+    r = oracle.render(s, c, n_iter=1)
+    assert r["split"][3].sum() > 0 and r["split"][:3].sum() == 0
+
+
+def test_plane_closed_form_with_light_photons_in_the_mix(oracle):
+    """Random hits, NEE and light photons under the balance heuristic (mask
+    1|2|8): 8x8 block means within 3 standard errors plus the kernel bias.
+    A light photon reaches every view vertex within r, so pixels of one
+    iteration are correlated: the standard error comes from the block means
+    of independent iterations."""
+    a, R, h, L = 0.6, 0.1, 1.0, 5.0
+    s = scenes.plane_under_sphere(a, R, h, L)
+    W = H = 32
+    n_it = 12
+    c = cfg(W, H, 3, mask=11, r=0.05)
+    c.lp_photons = 20000
+    imgs = per_iteration_images(oracle, s, c, n_it)[..., 0]
+    expect = _plane_expectation(s, W, H, a, R, h, L)
+    B = 8
+    for by in range(0, H, B):
+        for bx in range(0, W, B):
+            m = imgs[:, by:by + B, bx:bx + B].mean(axis=(1, 2))
+            e = expect[by:by + B, bx:bx + B].mean()
+            se = m.std(ddof=1) / math.sqrt(n_it)
+            assert abs(m.mean() - e) < 3 * se + 2e-3 * e, (by, bx, m.mean() - e, se)
+
+
 def test_random_hit_weight_split_matches_quadrature(oracle):
     """For one shading point under a sphere light the random-hit share of the
     result is the integral of w_e = p_e / (p_e + p_E) over the light, with

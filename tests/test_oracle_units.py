@@ -505,6 +505,39 @@ def test_mis_delta_vertices(oracle):
     assert w[2] == 0.0 and w[0] + w[1] == pytest.approx(1.0)
 
 
+def test_mis_with_light_photons_hand_worked(oracle):
+    """Eq. stdphotonpdf with n_LP light photons: p_LP,k = p_l^LP pi r^2
+    prod_{i=k}^{l-1} p_{i+1->i} prod_{i<k} p_{i->i+1}, where the light emits
+    cosine-weighted, p_{l->l-1} = (cos_y / pi) |cos_{l-1}| / d^2.
+    Length 2 (x1 floor at the origin, light (0,2,0) facing down): R1 = 1/(4 pi),
+      n_LP p_LP1 = 1000 pi 1e-4 0.125 / (4 pi) = 3.125e-3.
+    Length 3 (the path of the length-three test, light facing +z):
+      R1 = 1/(4 pi), R2 = 1/pi, F2 = 1/(4 pi):
+      n_LP p_LP1 = 500 pi 0.0025 0.25 R1 R2 = n_LP p_LP2 = 500 pi 0.0025 0.25 R2 F2."""
+    verts = [[0, 1, 0, 0, 0, 0, 0], [0, 0, 0, 0, 1, 0, 0]]
+    light = [0, 2, 0, 0, -1, 0, 0.25, 0.125]
+    w = oracle.mis_weights_lp(verts, light, 0.01, 50.0, 1000.0)
+    pe, pE, pLP = 1 / (4 * math.pi), 0.25, 1000 * math.pi * 1e-4 * 0.125 / (4 * math.pi)
+    S = pe + pE + pLP
+    assert w.tolist() == pytest.approx([pe / S, pE / S, pLP / S], rel=1e-5)
+    verts = [[0, 1, 0, 0, 0, 0, 0], [0, 0, 0, 0, 1, 0, 0], [0, 1, 1, 0, 0, -1, 0]]
+    light = [0, 1, 0, 0, 0, 1, 0.5, 0.25]
+    pe, pE, pP = 1 / (4 * math.pi ** 2), 1 / (8 * math.pi), 1 / 32
+    lp = 500 * math.pi * 0.0025 * 0.25 * (1 / (4 * math.pi)) * (1 / math.pi)
+    S = pe + pE + pP + 2 * lp
+    w = oracle.mis_weights_lp(verts, light, 0.05, 100.0, 500.0)
+    assert w.tolist() == pytest.approx([pe / S, pE / S, pP / S, lp / S, lp / S], rel=1e-5)
+    assert w.sum() == pytest.approx(1.0)
+    # no light photons: the weights of the plain combination, LP weights 0
+    w0 = oracle.mis_weights_lp(verts, light, 0.05, 100.0, 0.0)
+    assert w0[:3].tolist() == pytest.approx(oracle.mis_weights(verts, light[:7], 0.05, 100.0).tolist(), rel=1e-9)
+    assert w0[3:].tolist() == [0.0, 0.0]
+    # a delta vertex cannot be a merge vertex: LP weight there is 0
+    verts[2][6] = 1
+    w = oracle.mis_weights_lp(verts, light, 0.05, 100.0, 500.0)
+    assert w[4] == 0.0 and w[1] == 0.0 and w.sum() == pytest.approx(1.0)
+
+
 def test_density_estimators_closed_forms(oracle):
     """The naive and k-nearest estimators of Sec. 5 on a unit square lattice
     in the plane z = 0: within radius 1.5 an interior point sees itself and 8
