@@ -63,12 +63,16 @@ typedef struct {
   uint64_t seed;         /* Philox4x32-10 key */
   int octree_mode;       /* 0 concurrent lock-free inserts, 1 sequential in (pixel, k) order */
   int density_mode;      /* 0 robust median of five (get_density_robust), 1 single query */
-  uint32_t strategy_mask;/* bit 0 random hit (e), bit 1 NEE (E), bit 2 NEB photon merge (P) */
+  uint32_t strategy_mask;/* bit 0 random hit (e), bit 1 NEE (E), bit 2 NEB photon merge (P),
+                            bit 3 conventional light-photon merge (LP, with lp_photons > 0) */
   int keep_split;        /* nonzero: keep the last iteration's contributions split by strategy */
   int bvh_builder;       /* 0 PLOC clustering over the Morton order (default), 1 Karras LBVH */
   int photon_records;    /* photon queue records: 0 FP32 (64 bytes), 1 packed (48 bytes: FP32
                             origin and MIS factors, RGB flux as three FP16 mantissas of a shared
                             power-of-two scale, direction octahedral with 16 bits per coordinate) */
+  int lp_photons;        /* conventional light photons per iteration (n_LP, Sec. 6.1), used when
+                            strategy_mask has bit 8; each is emitted from a light and merged at
+                            view vertices like the NEB photons, under the same balance heuristic */
 } neb_config;
 
 typedef struct {
@@ -167,8 +171,9 @@ int neb_resolve(neb_ctx* ctx, float* rgb_out, int out_is_device);
 /* Raw FP64 sums [H][W][3] (host memory; synchronises). */
 int neb_read_accum(neb_ctx* ctx, double* out);
 
-/* Last iteration's contributions split by strategy [3][H][W][3] (0 random hit,
- * 1 NEE, 2 photon merge); requires cfg.keep_split.  Host memory. */
+/* Last iteration's contributions split by strategy [4][H][W][3] (0 random hit,
+ * 1 NEE, 2 NEB photon merge, 3 light-photon merge); requires cfg.keep_split.
+ * Host memory. */
 int neb_read_split(neb_ctx* ctx, double* out);
 
 /* Density rho at every NEE vertex of the last iteration, [H*W][D-1] indexed

@@ -74,7 +74,8 @@ static bool config_ok(const neb_config* cfg) {
   return cfg->width >= 1 && cfg->height >= 1 && cfg->max_depth >= 1 && cfg->max_depth <= kMaxDepth &&
          cfg->merge_radius > 0.0f && cfg->octree_capacity >= 1 && cfg->split_factor >= 1 &&
          (cfg->octree_mode == 0 || cfg->octree_mode == 1) && (cfg->density_mode == 0 || cfg->density_mode == 1) &&
-         !(cfg->strategy_mask & ~7u) && (cfg->bvh_builder == 0 || cfg->bvh_builder == 1) &&
+         !(cfg->strategy_mask & ~15u) && cfg->lp_photons >= 0 && cfg->lp_photons <= (1 << 26) &&
+         (cfg->bvh_builder == 0 || cfg->bvh_builder == 1) &&
          (cfg->photon_records == 0 || cfg->photon_records == 1) &&
          (long long)cfg->width * cfg->height <= (1ll << 28);
 }
@@ -112,7 +113,7 @@ extern "C" int neb_job_device_bytes(const neb_config* cfg, int n_tri, int n_sph,
   b += 2 * k.cap_ph * sizeof(PhotonRay) + k.cap_cam * sizeof(int2) + k.cap_ph * sizeof(int2);
   b += k.cap_nee * (sizeof(MergeRec) + sizeof(int)) + 2 * ((size_t)k.table + 1) * sizeof(int);
   b += scan_scratch_ints((size_t)k.table + 1) * sizeof(int) + k.P * 3 * sizeof(double);
-  b += cfg->keep_split ? k.P * 9 * sizeof(double) : 0;
+  b += cfg->keep_split ? k.P * 12 * sizeof(double) : 0;
   b += k.cap_nee * sizeof(ShadowRay) + group_counter_ints() * sizeof(int);
   const size_t nt = (size_t)n_tri, ns = (size_t)n_sph, nl = (size_t)n_lights, np = nt + ns;
   b += 3 * nt * sizeof(float4) + ns * (sizeof(float4) + sizeof(int)) + 3 * (size_t)n_mat * sizeof(float4);
@@ -172,7 +173,7 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
        dalloc(&c->bucket_count, (size_t)t + 1) == cudaSuccess &&
        dalloc(&c->bucket_start, (size_t)t + 1) == cudaSuccess &&
        dalloc(&c->scan_scratch.data, c->scan_scratch.n) == cudaSuccess && dalloc(&c->accum, P * 3) == cudaSuccess &&
-       (!cfg->keep_split || dalloc(&c->split, P * 9) == cudaSuccess);
+       (!cfg->keep_split || dalloc(&c->split, P * 12) == cudaSuccess);
   ok = ok && dalloc(&c->shadow_rays, c->cap_nee) == cudaSuccess &&
        dalloc(&c->group_counters, group_counter_ints()) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&c->stream_b, cudaStreamNonBlocking) == cudaSuccess &&
@@ -188,7 +189,7 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
   cudaMemsetAsync(c->accum, 0, sizeof(double) * P * 3, c->stream);
   cudaMemsetAsync(c->counters, 0, 2 * sizeof(DevCounters), c->stream);
   cudaMemsetAsync(c->group_counters, 0, sizeof(int) * group_counter_ints(), c->stream);
-  if (c->split) cudaMemsetAsync(c->split, 0, sizeof(double) * P * 9, c->stream);
+  if (c->split) cudaMemsetAsync(c->split, 0, sizeof(double) * P * 12, c->stream);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     neb_destroy(c);
@@ -566,7 +567,7 @@ extern "C" int neb_read_accum(neb_ctx* c, double* out) {
 extern "C" int neb_read_split(neb_ctx* c, double* out) {
   if (!c || !out) return NEB_ERR_ARG;
   if (!c->split) return fail(c, NEB_ERR_ARG, "neb_read_split: context created without keep_split");
-  cudaMemcpyAsync(out, c->split, sizeof(double) * 9 * (size_t)c->P, cudaMemcpyDeviceToHost, c->stream);
+  cudaMemcpyAsync(out, c->split, sizeof(double) * 12 * (size_t)c->P, cudaMemcpyDeviceToHost, c->stream);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   return e == cudaSuccess ? NEB_OK : fail(c, NEB_ERR_CUDA, "neb_read_split", e);
 }

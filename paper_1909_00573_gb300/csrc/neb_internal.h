@@ -70,7 +70,7 @@ struct NeeStore {
   float4* tau;   // rgb, w: g_y = cos_y / (dist^2 p_l)
   float4* err;   // hit point error bound, w: ldist
   float4* ldir;  // direction to the light point, w: rho (after the density pass)
-  float4* dE;    // irradiance rgb (zero if back-facing or occluded), w unused
+  float4* dE;    // irradiance rgb (zero if back-facing or occluded), w: the light point's light-photon pdf
 };
 enum { NV_DELTA = 1, NV_MERGEABLE = 2, NV_SHADOW = 4 };
 enum { NV_MAT_MASK = (1 << 20) - 1, NV_K_SHIFT = 20, NV_FLAG_SHIFT = 26 };
@@ -112,6 +112,7 @@ struct IterParams {
   uint2 key;
   float r, r2, kernel;  // merge radius, r^2, 1/(pi r^2)
   uint32_t mask;
+  int n_lp;             // conventional light photons this iteration (0 unless mask bit 3)
   int keep_split;
   int cap_cam, cap_nee, cap_rh, cap_ph;
   float3 gmin;          // hashed grid origin

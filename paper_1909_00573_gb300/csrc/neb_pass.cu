@@ -28,6 +28,13 @@ namespace neb {
 
 constexpr int kThreads = 256;
 
+// ---- photon flag word (PhotonRay.mis.w, 16 bits): k of the NEE vertex the
+// photon left (0 for light photons), index j of its next hit, light photon,
+// light photon before its first hit
+constexpr int PH_J_SHIFT = 8, PH_J_MASK = 63;
+constexpr int PH_LP = 1 << 14, PH_FIRST = 1 << 15;
+constexpr uint32_t kLpStream = 0x40000000u;  // Philox stream of light photon i: + hit index
+
 // ---- photon queue records: PhotonRay (64 bytes) or PackedPhoton (48 bytes)
 union Half2Bits {
   __half2 h;
@@ -114,6 +121,25 @@ __device__ __forceinline__ float light_pdf(const SceneView& s, int li, float3 y,
   return psel * ia;
 }
 
+// Area pdf of a light point under conventional light-photon emission (Sec.
+// 6.1): the light chosen as for NEE, the point uniform on its whole surface
+// (a sphere's NEE samples cover the facing hemisphere only: half the pdf).
+__device__ __forceinline__ float lp_light_pdf(const SceneView& s, int li) {
+  int prim = __ldg(s.light_prim + li);
+  float pa = __ldg(s.light_psel + li) * __ldg(s.light_inv_area + li);
+  return prim < s.nt ? pa : 0.5f * pa;
+}
+
+// Outward (emitting) normal of light li at its point y.
+__device__ __forceinline__ float3 light_normal(const SceneView& s, int li, float3 y) {
+  int prim = __ldg(s.light_prim + li);
+  if (prim < s.nt) {
+    float3 v0 = xyz(__ldg(s.tv0 + prim)), v1 = xyz(__ldg(s.tv1 + prim)), v2 = xyz(__ldg(s.tv2 + prim));
+    return normalize(cross(sub(v1, v0), sub(v2, v0)));
+  }
+  return normalize(sub(y, xyz(__ldg(s.sph + (prim - s.nt)))));
+}
+
 // ---------------------------------------------------------------------------
 // pass 1
 // ---------------------------------------------------------------------------
@@ -175,6 +201,7 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
     float3 ldir = f3(0, 0, 0), dE = f3(0, 0, 0);
     float ldist = 0.0f, g_y = 0.0f;
     bool shadow = false;
+    float nee_p_lp = 0.0f;
     if (valid) {
       ry = in[i];
       rays = 1;
@@ -252,6 +279,7 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
               dE = mul(lm.emission, g);
               g_y = cos_y / (dist2 * p_l);
               shadow = true;
+              nee_p_lp = lp_light_pdf(s, lidx);
             }
           }
         }
@@ -263,14 +291,16 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
     CamRay nr;
     if (valid && store_nee && nid >= 0) {
       bool delta = mat_delta(m);
-      int vflags = (delta ? NV_DELTA : 0) | ((!delta && k <= ip.D - 2) ? NV_MERGEABLE : 0) | (shadow ? NV_SHADOW : 0);
+      // mergeable: NEB photons reach x_k for k <= D - 2, light photons for k <= D - 1
+      const int kmerge = ip.n_lp > 0 ? ip.D - 1 : ip.D - 2;
+      int vflags = (delta ? NV_DELTA : 0) | ((!delta && k <= kmerge) ? NV_MERGEABLE : 0) | (shadow ? NV_SHADOW : 0);
       nv.pos[nid] = make_float4(p.x, p.y, p.z, Cfac);
       nv.nrm[nid] = make_float4(n.x, n.y, n.z, __int_as_float(mat | (k << NV_K_SHIFT) | (vflags << NV_FLAG_SHIFT)));
       nv.wo[nid] = make_float4(-d.x, -d.y, -d.z, __int_as_float(pixel));
       nv.tau[nid] = make_float4(tau.x, tau.y, tau.z, g_y);
       nv.err[nid] = make_float4(err.x, err.y, err.z, ldist);
       nv.ldir[nid] = make_float4(ldir.x, ldir.y, ldir.z, 0.0f);
-      nv.dE[nid] = make_float4(dE.x, dE.y, dE.z, 0.0f);
+      nv.dE[nid] = make_float4(dE.x, dE.y, dE.z, nee_p_lp);
       if (slot_map) slot_map[(size_t)pixel * (ip.D - 1) + (k - 1)] = nid;
     }
     if (valid && alive) {
@@ -331,6 +361,9 @@ __global__ void __launch_bounds__(kThreads) k_nee(SceneView s, IterParams ip, Ne
         if (maxc(f) > 0.0f) {
           float pdfF = bsdf_pdf(m, n, wo, ldir), pdfC = bsdf_pdf(m, n, ldir, wo);
           float inv_w = 1.0f + ((ip.mask & 1u) ? pdfF * g_y : 0.0f) + ((ip.mask & 4u) ? rho * pir2 * pdfC * Cfac : 0.0f);
+          // light photons: n_LP pi r^2 p_l^LP R_{l-1} / p_l (C_m + 1), R_{l-1} / p_l = g_y |cos_m| / pi
+          if (ip.n_lp > 0)
+            inv_w += (float)ip.n_lp * pir2 * de.w * g_y * fabsf(dot(n, ldir)) * kInvPi * (pdfC * Cfac + 1.0f);
           float3 L = mul(cmul(cmul(tau, f), dE), 1.0f / inv_w);
           add_pixel(accum, split, 1, pixel, L, P);
         }
@@ -345,6 +378,14 @@ __global__ void __launch_bounds__(kThreads) k_nee(SceneView s, IterParams ip, Ne
           if (maxc(phi) > 0.0f) {
             float E0 = (((ip.mask & 1u) ? pdfr1 * g_y : 0.0f) + (((ip.mask & 2u) && !delta) ? 1.0f : 0.0f)) /
                        (rho * pir2);
+            if (ip.n_lp > 0) {
+              // alpha / (rho pi r^2) = 1 + lp and beta gains lp ok(x_m), lp = n_LP p_l^LP
+              // R_{l-1} / (p_l rho); both are divided out: flux / alpha, E0 = beta / alpha
+              float lp = (float)ip.n_lp * de.w * g_y * fabsf(dot(n, ldir)) * kInvPi / rho;
+              float a = 1.0f + lp;
+              E0 = (E0 + (delta ? 0.0f : lp)) / a;
+              phi = mul(phi, 1.0f / a);
+            }
             float3 o = offset_origin(p, n, xyz(ee), w1);
             ph.o = make_float4(o.x, o.y, o.z, __int_as_float(pixel));
             ph.d = make_float4(w1.x, w1.y, w1.z, pdf1);
@@ -359,6 +400,66 @@ __global__ void __launch_bounds__(kThreads) k_nee(SceneView s, IterParams ip, Ne
     int slot = warp_append(&cnt->ph_count[0], emit, ip.cap_ph, &cnt->status);
     if (emit && slot >= 0) store_photon(phq, slot, ph, packed);
     warp_count(&cnt->photons, nphot);
+  }
+}
+
+// Conventional light photons (Sec. 6.1): n_LP photons per iteration, each
+// from a light chosen as for NEE (alias table, Philox dims 0-1 of stream
+// kLpStream), a point uniform on its whole surface (dims 2-3) and a direction
+// cosine-weighted about its normal (dims 4-5), with flux Le cos / (p_l^LP
+// cos / pi) / n_LP.  They follow the NEB photons in the photon queue; their
+// weights are set up at their first hit (k_photon).
+__global__ void __launch_bounds__(kThreads) k_lp_emit(SceneView s, IterParams ip, DevCounters* cnt,
+                                                      void* __restrict__ phq, int packed) {
+  for (int base = blockIdx.x * blockDim.x; base < ip.n_lp; base += gridDim.x * blockDim.x) {
+    const int i = base + threadIdx.x;
+    bool emit = false;
+    PhotonRay ph;
+    if (i < ip.n_lp && s.nl > 0) {
+      uint4 r0 = rng_block(ip.key, ip.iteration, i, kLpStream, 0);
+      uint4 r1 = rng_block(ip.key, ip.iteration, i, kLpStream, 1);
+      int li = (int)(((uint64_t)(r0.x >> 8) * (uint64_t)s.nl) >> 24);
+      if (!(u01(r0.y) < __ldg(s.alias_prob + li))) li = __ldg(s.alias_idx + li);
+      const int prim = __ldg(s.light_prim + li);
+      const float u2 = u01(r0.z), u3 = u01(r0.w);
+      float3 y, ny, yerr;
+      if (prim < s.nt) {
+        float b1 = u2, b2 = u3;
+        if (b1 + b2 > 1.0f) { b1 = 1.0f - b1; b2 = 1.0f - b2; }
+        float3 a = xyz(__ldg(s.tv0 + prim)), e1 = sub(xyz(__ldg(s.tv1 + prim)), a), e2 = sub(xyz(__ldg(s.tv2 + prim)), a);
+        y = add(add(a, mul(e1, b1)), mul(e2, b2));
+        ny = normalize(cross(e1, e2));
+        yerr = f3(NEB_GAMMA5 * (fabsf(a.x) + fabsf(e1.x * b1) + fabsf(e2.x * b2)),
+                  NEB_GAMMA5 * (fabsf(a.y) + fabsf(e1.y * b1) + fabsf(e2.y * b2)),
+                  NEB_GAMMA5 * (fabsf(a.z) + fabsf(e1.z * b1) + fabsf(e2.z * b2)));
+      } else {
+        float4 sp = __ldg(s.sph + (prim - s.nt));
+        float z = 1.0f - 2.0f * u2;
+        float rr = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+        float phs = kTwoPi * u3;
+        ny = f3(rr * cosf(phs), rr * sinf(phs), z);
+        y = add(xyz(sp), mul(ny, sp.w));
+        yerr = f3(NEB_GAMMA5 * (fabsf(sp.x) + sp.w), NEB_GAMMA5 * (fabsf(sp.y) + sp.w),
+                  NEB_GAMMA5 * (fabsf(sp.z) + sp.w));
+      }
+      const float u4 = u01(r1.x), u5 = u01(r1.y);
+      const float er = sqrtf(u4), eph = kTwoPi * u5, ez = sqrtf(fmaxf(0.0f, 1.0f - u4));
+      float3 w = from_local(ny, er * cosf(eph), er * sinf(eph), ez);
+      if (ez > 0.0f) {
+        const float p_lp = lp_light_pdf(s, li);
+        Mat lm = load_mat(s.mats, prim_mat(s, prim));
+        float3 phi = mul(lm.emission, kPi / (p_lp * (float)ip.n_lp));
+        float3 o = offset_origin(y, ny, yerr, w);
+        ph.o = make_float4(o.x, o.y, o.z, __int_as_float(i));
+        ph.d = make_float4(w.x, w.y, w.z, 1.0f);
+        ph.phi = make_float4(phi.x, phi.y, phi.z, ez);  // w: cos_y
+        ph.mis = make_float4(p_lp, __int_as_float(li), 0.0f, __int_as_float((1 << PH_J_SHIFT) | PH_LP | PH_FIRST));
+        emit = true;
+      }
+    }
+    int slot = warp_append(&cnt->ph_count[0], emit, ip.cap_ph, &cnt->status);
+    if (emit && slot >= 0) store_photon(phq, slot, ph, packed);
+    warp_count(&cnt->photons, emit ? 1u : 0u);
   }
 }
 
@@ -382,10 +483,25 @@ __global__ void __launch_bounds__(kThreads) k_emission(SceneView s, IterParams i
       } else {
         continue;  // the NEE store overflowed; the event cannot be weighted
       }
-      float p_l = light_pdf(s, __float_as_int(ev.y.w), xyz(ev.y), xp);
+      const int li = __float_as_int(ev.y.w);
+      float p_l = light_pdf(s, li, xyz(ev.y), xp);
       float q = p_l / ev.L.w;
       inv_w = 1.0f + (((ip.mask & 2u) && !(flags & RAY_PREV_DELTA)) ? q : 0.0f) +
               ((ip.mask & 4u) ? q * rho * pir2 * C_prev : 0.0f);
+      if (ip.n_lp > 0) {
+        // light photons: n_LP pi r^2 p_l^LP R_{l-1} / F_l (C_{l-1} + ok(x_{l-1})), with
+        // R_{l-1} = (cos_y / pi) |cos_{l-1}| / d^2 the cosine emission toward x_{l-1}
+        float3 y = xyz(ev.y), dd = sub(y, xp);
+        float d2 = dot(dd, dd);
+        float3 u = mul(dd, rsqrtf(d2));
+        float cos_y = -dot(light_normal(s, li, y), u);
+        float cos_p = fabsf(dot(xyz(nv.nrm[prev]), u));
+        if (cos_y > 0.0f) {
+          float R = cos_y * kInvPi * cos_p / d2;
+          inv_w += (float)ip.n_lp * pir2 * lp_light_pdf(s, li) * R / ev.L.w *
+                   (C_prev + ((flags & RAY_PREV_DELTA) ? 0.0f : 1.0f));
+        }
+      }
     }
     float3 L = mul(xyz(ev.L), 1.0f / inv_w);
     add_pixel(accum, split, 0, pixel, L, P);
@@ -398,7 +514,9 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
                                                      int in_slot, void* __restrict__ out, int out_slot, int packed,
                                                      NeeStore nv, const MergeRec* __restrict__ mrec,
                                                      const int* __restrict__ bucket_start, DevCounters* cnt,
-                                                     double* accum, double* split, const int2* __restrict__ hits) {
+                                                     double* accum, double* split, const int2* __restrict__ hits,
+                                                     const int* __restrict__ oct_nodes, const OctreeState* oct_state,
+                                                     OctreeParams oct, int robust) {
   const int count = min(cnt->ph_count[in_slot], ip.cap_ph);
   const int stride = gridDim.x * blockDim.x;
   const int P = ip.W * ip.H;
@@ -409,7 +527,11 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
     uint32_t nhits = 0, tests = 0, merges = 0;
     bool want_merge = false;
     float3 m_p = f3(0, 0, 0), m_d = f3(0, 0, 0), m_phi = f3(0, 0, 0);
-    float m_s1 = 0.0f;
+    // merge weight of this hit: 1 / w = c0 + c1 pdfF + c2 pdfC Cfac, for view
+    // vertices x_k with k <= kmax, contributions to split channel chan
+    float m_c0 = 0.0f, m_c1 = 0.0f, m_c2 = 0.0f;
+    int m_kmax = -1, m_chan = 2;
+    int queries = 0;
     if (i < count) {
       PhotonRay ph = load_photon(in, i, packed);
       float3 d = xyz(ph.d);
@@ -423,35 +545,100 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
         Mat hm = load_mat(s.mats, prim_mat(s, prim));
         if (!mat_black(hm)) {
           nhits = 1;
-          int knee = __float_as_int(ph.mis.w) & 0xff;
+          const int bits = __float_as_int(ph.mis.w);
+          const int knee = bits & 0xff, jph = (bits >> PH_J_SHIFT) & PH_J_MASK;
+          const bool lp = bits & PH_LP;
           int pixel = __float_as_int(ph.o.w);
           float cos_hit = fabsf(dot(hn, d));
-          float cos_orig = ph.phi.w, pdf_dir = ph.d.w;
-          float E0 = ph.mis.x, pA = ph.mis.y, pB = ph.mis.z;
           float3 phi = xyz(ph.phi);
           bool hdelta = mat_delta(hm);
-          if (!hdelta) {
-            want_merge = true;
-            m_p = hp;
-            m_d = d;
-            m_phi = phi;
-            m_s1 = (E0 * pA + pB) * cos_orig / (pdf_dir * cos_hit);
-          }
-          if (j + 1 <= ip.D - 2) {
-            uint4 rb = rng_block(ip.key, ip.iteration, pixel, 256u * knee + 1u + (uint32_t)j, 1);
-            float3 w, wt;
-            float pdf_f, pdf_r;
-            if (bsdf_sample(hm, hn, neg(d), u01(rb.x), u01(rb.y), u01(rb.z), false, w, wt, pdf_f, pdf_r)) {
-              float3 phi2 = cmul(phi, wt);
-              if (maxc(phi2) > 0.0f) {
-                float ratio = pdf_r * cos_orig / (pdf_dir * cos_hit);
-                float3 o = offset_origin(hp, hn, herr, w);
-                nph.o = make_float4(o.x, o.y, o.z, __int_as_float(pixel));
-                nph.d = make_float4(w.x, w.y, w.z, pdf_f);
-                nph.phi = make_float4(phi2.x, phi2.y, phi2.z, fabsf(dot(hn, w)));
-                nph.mis = make_float4(E0, ratio * pA, (hdelta ? 0.0f : 1.0f) + ratio * pB,
-                                      __int_as_float(knee | ((j + 1) << 8)));
-                emit = true;
+          const float pir2 = kPi * ip.r * ip.r;
+          if (bits & PH_FIRST) {
+            // First hit x_{l-1} of a light photon from the light point y (Sec. 6.1).
+            // Every LP path of this photon ends here: with R = p_{l -> l-1} (cosine
+            // emission), p_l the NEE pdf of y from here and rho the density here,
+            // num = n_LP pi r^2 (p_l^LP / p_l) R is the light-photon strategy,
+            // alpha = [P] rho pi r^2 + num the coefficient of the interior merges and
+            // beta = [E] + [e] F_l / p_l + num that of this vertex (Q normalisation).
+            const float3 yl = xyz(ph.o);
+            const float3 dl = sub(hp, yl);
+            const float d2 = dot(dl, dl);
+            const float cos_y = ph.phi.w, p_lp = ph.mis.x;
+            const int li = __float_as_int(ph.mis.y);
+            const float p_l = light_pdf(s, li, yl, hp);
+            float pp[3] = {hp.x, hp.y, hp.z}, nn[3] = {hn.x, hn.y, hn.z};
+            const float rho = robust ? oct_density_robust(oct_nodes, oct, oct_state->depth, pp, nn, &queries)
+                                     : (++queries, oct_density(oct_nodes, oct, oct_state->depth, pp, nn, nullptr));
+            if (p_l > 0.0f) {
+              const float R = cos_y * kInvPi * cos_hit / d2;
+              const float num = (float)ip.n_lp * pir2 * (p_lp / p_l) * R;
+              const float alpha = ((ip.mask & 4u) ? rho * pir2 : 0.0f) + num;
+              const float g = cos_y / (d2 * p_l);  // F_l / p_l = pdfF g
+              if (!hdelta) {
+                // merging here: x_k stands for x_{l-1}; beta per view vertex
+                want_merge = true;
+                m_p = hp;
+                m_d = d;
+                m_phi = phi;
+                m_c0 = ((ip.mask & 2u) ? 1.0f / num : 0.0f) + 1.0f;
+                m_c1 = (ip.mask & 1u) ? g / num : 0.0f;
+                m_c2 = alpha / num;
+                m_kmax = ip.D - 1;
+                m_chan = 3;
+              }
+              if (j + 1 <= ip.D - 1) {
+                // leave x_{l-1} as a photon emitted there, with 1 / alpha folded
+                // into its flux and beta / alpha as its E0
+                uint4 rb = rng_block(ip.key, ip.iteration, pixel, kLpStream + (uint32_t)j, 1);
+                float3 w, wt;
+                float pdf_f, pdf_r;
+                if (bsdf_sample(hm, hn, neg(d), u01(rb.x), u01(rb.y), u01(rb.z), false, w, wt, pdf_f, pdf_r)) {
+                  float3 phi2 = mul(cmul(phi, wt), num / alpha);
+                  if (maxc(phi2) > 0.0f && alpha > 0.0f) {
+                    float beta = (((ip.mask & 2u) && !hdelta) ? 1.0f : 0.0f) + ((ip.mask & 1u) ? pdf_r * g : 0.0f) +
+                                 (hdelta ? 0.0f : num);
+                    float3 o = offset_origin(hp, hn, herr, w);
+                    nph.o = make_float4(o.x, o.y, o.z, __int_as_float(pixel));
+                    nph.d = make_float4(w.x, w.y, w.z, pdf_f);
+                    nph.phi = make_float4(phi2.x, phi2.y, phi2.z, fabsf(dot(hn, w)));
+                    nph.mis = make_float4(beta / alpha, 1.0f, 0.0f, __int_as_float((1 << PH_J_SHIFT) | PH_LP));
+                    emit = true;
+                  }
+                }
+              }
+            }
+          } else {
+            // NEB photons, and light photons after their first hit
+            float cos_orig = ph.phi.w, pdf_dir = ph.d.w;
+            float E0 = ph.mis.x, pA = ph.mis.y, pB = ph.mis.z;
+            if (!hdelta) {
+              want_merge = true;
+              m_p = hp;
+              m_d = d;
+              m_phi = phi;
+              m_c0 = 1.0f;
+              m_c1 = (E0 * pA + pB) * cos_orig / (pdf_dir * cos_hit);
+              m_c2 = 1.0f;
+              m_kmax = ip.D - jph - 1;
+              m_chan = lp ? 3 : 2;
+            }
+            if (jph + 1 <= ip.D - 2) {
+              const uint32_t stream = lp ? kLpStream + (uint32_t)j : 256u * knee + 1u + (uint32_t)j;
+              uint4 rb = rng_block(ip.key, ip.iteration, pixel, stream, 1);
+              float3 w, wt;
+              float pdf_f, pdf_r;
+              if (bsdf_sample(hm, hn, neg(d), u01(rb.x), u01(rb.y), u01(rb.z), false, w, wt, pdf_f, pdf_r)) {
+                float3 phi2 = cmul(phi, wt);
+                if (maxc(phi2) > 0.0f) {
+                  float ratio = pdf_r * cos_orig / (pdf_dir * cos_hit);
+                  float3 o = offset_origin(hp, hn, herr, w);
+                  nph.o = make_float4(o.x, o.y, o.z, __int_as_float(pixel));
+                  nph.d = make_float4(w.x, w.y, w.z, pdf_f);
+                  nph.phi = make_float4(phi2.x, phi2.y, phi2.z, fabsf(dot(hn, w)));
+                  nph.mis = make_float4(E0, ratio * pA, (hdelta ? 0.0f : 1.0f) + ratio * pB,
+                                        __int_as_float(knee | ((jph + 1) << PH_J_SHIFT) | (lp ? PH_LP : 0)));
+                  emit = true;
+                }
               }
             }
           }
@@ -524,7 +711,8 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
       float3 hp = f3(__shfl_sync(FULL, m_p.x, L), __shfl_sync(FULL, m_p.y, L), __shfl_sync(FULL, m_p.z, L));
       float3 md = f3(-__shfl_sync(FULL, m_d.x, L), -__shfl_sync(FULL, m_d.y, L), -__shfl_sync(FULL, m_d.z, L));
       float3 phi = f3(__shfl_sync(FULL, m_phi.x, L), __shfl_sync(FULL, m_phi.y, L), __shfl_sync(FULL, m_phi.z, L));
-      float s1 = __shfl_sync(FULL, m_s1, L);
+      float c0 = __shfl_sync(FULL, m_c0, L), c1 = __shfl_sync(FULL, m_c1, L), c2 = __shfl_sync(FULL, m_c2, L);
+      int kmax = __shfl_sync(FULL, m_kmax, L), chan = __shfl_sync(FULL, m_chan, L);
       if (q >= total || e < 0) continue;
       float4 mp = __ldg(&mrec[e].pos);
       float dx = mp.x - hp.x, dy = mp.y - hp.y, dz = mp.z - hp.z;
@@ -535,22 +723,23 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
       float4 mn = __ldg(&nv.nrm[id]);
       int mb = __float_as_int(mn.w);
       int kk = (mb >> NV_K_SHIFT) & 63;
-      if (kk + j + 1 > ip.D) continue;
+      if (kk > kmax) continue;
       Mat cm = load_mat(s.mats, mb & NV_MAT_MASK);
       float4 mw = __ldg(&nv.wo[id]);
       float3 cn = xyz(mn), cwo = xyz(mw);
       float3 f = bsdf_eval(cm, cn, cwo, md);
       if (!(maxc(f) > 0.0f)) continue;
       float pdfF = bsdf_pdf(cm, cn, cwo, md), pdfC = bsdf_pdf(cm, cn, md, cwo);
-      float inv_w = 1.0f + pdfF * s1 + pdfC * __ldg(&nv.pos[id].w);
+      float inv_w = c0 + c1 * pdfF + c2 * pdfC * __ldg(&nv.pos[id].w);
       float3 ctau = xyz(__ldg(&nv.tau[id]));
       float3 L3 = mul(cmul(cmul(ctau, f), phi), ip.kernel / inv_w);
-      add_pixel(accum, split, 2, __float_as_int(mw.w), L3, P);
+      add_pixel(accum, split, chan, __float_as_int(mw.w), L3, P);
       ++merges;
     }
     int slot = warp_append(&cnt->ph_count[out_slot], emit, ip.cap_ph, &cnt->status);
     if (emit && slot >= 0) store_photon(out, slot, nph, packed);
     warp_count(&cnt->photon_hits, nhits);
+    warp_count(&cnt->octree_queries, (uint32_t)queries);
     warp_count(&cnt->merge_tests, tests);
     warp_count(&cnt->merges, merges);
   }
@@ -618,6 +807,7 @@ IterParams iter_params(const neb_ctx* c, int iteration) {
   ip.r2 = ip.r * ip.r;
   ip.kernel = (float)(1.0 / (3.14159265358979323846 * (double)ip.r * (double)ip.r));
   ip.mask = c->cfg.strategy_mask;
+  ip.n_lp = (ip.mask & 8u) ? c->cfg.lp_photons : 0;
   ip.keep_split = c->cfg.keep_split;
   ip.cap_cam = c->cap_cam;
   ip.cap_nee = c->cap_nee;
@@ -695,7 +885,7 @@ static long long enqueue_pass23(neb_ctx* c, int iteration, cudaStream_t st2, Sta
   long long launches = 0;
   octree_set_iteration_params(c->oct, c->cfg.split_factor, iteration);
   tm.begin(STAGE_INSERT);
-  if (split) cudaMemsetAsync(c->split, 0, sizeof(double) * 9 * (size_t)c->P, st2);
+  if (split) cudaMemsetAsync(c->split, 0, sizeof(double) * 12 * (size_t)c->P, st2);
   launch_oct_rearm(c->oct_nodes, c->oct_state, c->oct, st2);
   launch_oct_insert_nee(c, sl, st2);
   launches += 2;
@@ -706,9 +896,16 @@ static long long enqueue_pass23(neb_ctx* c, int iteration, cudaStream_t st2, Sta
   tm.begin(STAGE_NEE);
   k_nee<<<capped_blocks(c->cap_nee, kThreads, B), kThreads, 0, st2>>>(s, ip, sl.nv, cnt, c->accum, split, c->phq[0],
                                                                         c->cfg.photon_records);
+  if (ip.n_lp > 0 && c->D >= 2) {
+    k_lp_emit<<<capped_blocks(ip.n_lp, kThreads, B), kThreads, 0, st2>>>(s, ip, cnt, c->phq[0], c->cfg.photon_records);
+    launches += 1;
+  }
   tm.end();
   launches += 2;
-  if ((ip.mask & 4u) && c->D >= 3) {
+  // photon walks: NEB photons hit at most D - 2 times, light photons D - 1 times
+  const bool photons = ((ip.mask & 4u) && c->D >= 3) || (ip.n_lp > 0 && c->D >= 2);
+  const int photon_launches = ip.n_lp > 0 ? c->D - 1 : c->D - 2;
+  if (photons) {
     tm.begin(STAGE_GRID);
     grid_build(c, ip, sl, st2);
     launches += 2 + scan_launch_count((size_t)c->table_size + 1);
@@ -718,8 +915,8 @@ static long long enqueue_pass23(neb_ctx* c, int iteration, cudaStream_t st2, Sta
   k_emission<<<capped_blocks(c->cap_rh, kThreads, B), kThreads, 0, st2>>>(s, ip, sl.nv, sl.rh, cnt, c->accum, split);
   launches += 1;
   tm.end();
-  if ((ip.mask & 4u) && c->D >= 3) {
-    for (int j = 1; j <= c->D - 2; ++j) {
+  if (photons) {
+    for (int j = 1; j <= photon_launches; ++j) {
       int in = (j - 1) & 1, out = j & 1;
       k_reset_photon_slot<<<1, 1, 0, st2>>>(cnt, out);
       tm.begin(STAGE_TRACE_PHOTON);
@@ -728,7 +925,8 @@ static long long enqueue_pass23(neb_ctx* c, int iteration, cudaStream_t st2, Sta
       tm.end();
       tm.begin(STAGE_PHOTON);
       k_photon<<<capped_blocks(c->cap_ph, kThreads, B), kThreads, 0, st2>>>(s, ip, j, c->phq[in], in, c->phq[out], out, c->cfg.photon_records, sl.nv, c->mrec, c->bucket_start, cnt,
-                                        c->accum, split, c->hits_ph);
+                                        c->accum, split, c->hits_ph, c->oct_nodes, c->oct_state, c->oct,
+                                        c->cfg.density_mode == 0);
       launches += 3;
       tm.end();
     }

@@ -41,7 +41,8 @@ class Config(C.Structure):
     _fields_ = [("width", C.c_int), ("height", C.c_int), ("max_depth", C.c_int), ("merge_radius", C.c_float),
                 ("octree_capacity", C.c_int), ("split_factor", C.c_int), ("seed", C.c_uint64),
                 ("octree_mode", C.c_int), ("density_mode", C.c_int), ("strategy_mask", C.c_uint32),
-                ("keep_split", C.c_int), ("bvh_builder", C.c_int), ("photon_records", C.c_int)]
+                ("keep_split", C.c_int), ("bvh_builder", C.c_int), ("photon_records", C.c_int),
+                ("lp_photons", C.c_int)]
 
 
 class Tuning(C.Structure):
@@ -143,7 +144,7 @@ def make_config(rc, keep_split=False, octree_mode=None, density_mode=None, strat
                   rc.seed, rc.octree_mode if octree_mode is None else octree_mode,
                   rc.density_mode if density_mode is None else density_mode,
                   rc.strategy_mask if strategy_mask is None else strategy_mask, int(keep_split), int(bvh_builder),
-                  int(photon_records))
+                  int(photon_records), int(getattr(rc, "lp_photons", 0)))
 
 
 class Context:
@@ -221,7 +222,7 @@ class Context:
         return out
 
     def read_split(self):
-        out = np.zeros((3, self.cfg.height, self.cfg.width, 3), np.float64)
+        out = np.zeros((4, self.cfg.height, self.cfg.width, 3), np.float64)
         self._c(lib().neb_read_split(self.h, _p(out)))
         return out
 

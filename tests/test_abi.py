@@ -43,7 +43,9 @@ def test_argument_errors_without_gpu(libneb):
     assert L.neb_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
     cfg = neb.Config(8, 8, 99, 0.01, 64, 4, 0, 0, 0, 7, 0, 0)      # depth above 64
     assert L.neb_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
-    cfg = neb.Config(8, 8, 4, 0.01, 64, 4, 0, 0, 0, 9, 0, 0)       # unknown strategy bit
+    cfg = neb.Config(8, 8, 4, 0.01, 64, 4, 0, 0, 0, 17, 0, 0)      # unknown strategy bit
+    assert L.neb_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
+    cfg = neb.Config(8, 8, 4, 0.01, 64, 4, 0, 0, 0, 15, 0, 0, 0, -1)  # negative light-photon count
     assert L.neb_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
     cfg = neb.Config(8, 8, 4, 0.01, 64, 4, 0, 0, 0, 7, 0, 5)       # unknown BVH builder
     assert L.neb_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
@@ -68,7 +70,7 @@ def test_batch_and_admission_arguments_without_gpu(libneb):
     assert 2 * 921600 * 9 * 112 < b < 6e9
     split = neb.job_device_bytes(neb.make_config(rc, keep_split=True), s.n_tri, s.n_sph, len(s.mats),
                                  s.n_emitters)
-    assert split - b == 921600 * 9 * 8                          # the FP64 per-strategy split
+    assert split - b == 921600 * 12 * 8                         # the FP64 per-strategy split (4 strategies)
     rc2 = scenes.RenderConfig(2 * rc.width, rc.height, rc.max_depth, rc.merge_radius, rc.octree_capacity,
                               rc.split_factor, 1)
     assert neb.job_device_bytes(neb.make_config(rc2), s.n_tri, s.n_sph, len(s.mats), s.n_emitters) > b

@@ -385,6 +385,38 @@ def test_packed_photon_records_error(neb, oracle):
     print(f"relative L2 error vs oracle: fp32 {rel[0]:.2e}, packed {rel[1]:.2e}; photon image packed vs fp32 {pm:.2e}")
 
 
+def test_tiny_room_with_light_photons_parity(neb, oracle):
+    """NEB+LP (Sec. 6.1): all four strategies (random hit, NEE, NEB photons,
+    4096 conventional light photons per iteration) under one balance
+    heuristic, deterministic octree: every camera path's contribution per
+    strategy in the last iteration matches the oracle, as do the densities and
+    the photon counts."""
+    from paper_1909_00573_gb300 import scenes
+    s, rc = scenes.workload("tiny_room")
+    rc.octree_mode = 1
+    rc.strategy_mask = 15
+    rc.lp_photons = 4096
+    ctx = neb.render(s, rc)
+    gsplit, gacc, st = ctx.read_split(), ctx.read_accum(), ctx.stats()
+    ctx.close()
+    ref = oracle.render(s, rc)
+    osplit, oacc = ref["split"], ref["accum"]
+    assert st["status"] & ~neb.STATUS_OCTREE_FULL == 0
+    assert osplit[3].sum() > 0 and gsplit[3].sum() > 0
+    tot_ok = _compare(gsplit.sum(0).sum(-1), osplit.sum(0).sum(-1))
+    assert tot_ok.mean() >= 0.999, tot_ok.mean()
+    for k in range(4):
+        ok = _compare(gsplit[k].sum(-1), osplit[k].sum(-1))
+        assert ok.mean() >= 0.995, (k, ok.mean())
+    assert _compare(gacc.sum(-1), oacc.sum(-1)).mean() >= 0.995
+    assert abs(st["photons"] - ref["stats"]["photons"]) <= 4
+    # light photons change the weights of the other strategies, not their sum of weights
+    ctx = neb.render(s, scenes.RenderConfig(64, 64, 8, 0.01, 1 << 16, 8, 4, octree_mode=1, strategy_mask=7))
+    g7 = ctx.read_split()
+    ctx.close()
+    assert gsplit[:3].sum() < g7.sum()
+
+
 def test_ragged_small_image_parity(neb, oracle):
     """Odd image size (a ragged last block), D = 3 (one photon bounce)."""
     from paper_1909_00573_gb300 import scenes
