@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=200.0, help="mean request arrival rate (per second) for --serve")
     ap.add_argument("--ablation", action="store_true",
                     help="density estimators of Sec. 5 (octree, naive, k nearest) on one iteration's NEE vertices")
+    ap.add_argument("--lp-photons", type=int, default=0,
+                    help="NEB+LP (Sec. 6.1): conventional light photons per iteration in addition to NEB photons")
     ap.add_argument("--autotune", type=int, default=0,
                     help="run the autotuner (this many iterations per candidate) before the warm-up")
     return ap.parse_args()
@@ -265,6 +267,8 @@ def config_dict(rc, scene):
                         f"r={rc.merge_radius:.3g}, octree {rc.octree_capacity} nodes, split {rc.split_factor}",
             "paths_per_step": rc.width * rc.height, "max_depth": rc.max_depth,
             "octree_mode": "concurrent" if rc.octree_mode == 0 else "sequential",
+            "strategies": "e+E+P" + ("+LP" if rc.strategy_mask & 8 else ""),
+            "lp_photons": int(getattr(rc, "lp_photons", 0)) if rc.strategy_mask & 8 else 0,
             "l2": "inputs larger than L2 (scene + BVH + per-iteration records > 129 MB)"}
 
 
@@ -477,6 +481,9 @@ def main():
         rc.width, rc.height = (int(x) for x in args.res.lower().split("x"))
     if args.octree_cap:
         rc.octree_capacity = args.octree_cap
+    if args.lp_photons > 0:
+        rc.strategy_mask |= 8
+        rc.lp_photons = args.lp_photons
     rc.seed = replica_seed(rank)        # replicas render independent sample streams
     P = rc.width * rc.height
     # a dedicated (non-default) stream: the library's kernels and the timing
