@@ -460,17 +460,31 @@ __device__ __forceinline__ bool child_hit(const Node4Oct& n, int c, const RayPre
   return t0 <= t1;
 }
 
-// One node step of the closest-hit walk over the BVH4: leaf children whose
-// box is hit are tested at once, hit inner children are visited near-first
-// (the others pushed far-to-near).  Returns true when the walk is over.
+// Sort key of a hit inner child: its entry distance (>= 0, so the float bits
+// order like the distances) with the two low bits replaced by the child slot.
+// The masked distance is at most the entry distance.
+constexpr uint32_t kNoKey = 0xffffffffu;
+__device__ __forceinline__ uint32_t child_key(float tn, int c) { return (__float_as_uint(tn) & ~3u) | (uint32_t)c; }
+__device__ __forceinline__ float key_dist(uint32_t k) { return __uint_as_float(k & ~3u); }
+__device__ __forceinline__ void key_swap(uint32_t& a, uint32_t& b) {
+  uint32_t lo = min(a, b), hi = max(a, b);
+  a = lo;
+  b = hi;
+}
+
+// One node step of the closest-hit walk over the BVH4.  Leaf children whose
+// box is hit are tested in one loop after the box tests, so the lanes of a
+// warp run their first, second, ... leaf test together; hit inner children
+// that still start before the closest hit are visited near-first (the others
+// pushed far-to-near), ordered by a sorting network over their keys so the
+// step keeps no per-thread array.  Returns true when the walk is over.
 __device__ __forceinline__ bool closest_step4(const SceneView& s, const RayPre& r, float tmax, int& node, int& sp,
-                                              int* stack, float& best_t, int& best, uint32_t* status,
+                                              int* stack, float* stack_t, float& best_t, int& best, uint32_t* status,
                                               uint32_t& visits, uint32_t& ptests) {
   Node4Oct n = load_node4_oct(s.nodes, node, r.oct);
   ++visits;
-  float td[4];
-  int cr[4];
-  int cnt = 0;
+  uint32_t k0 = kNoKey, k1 = kNoKey, k2 = kNoKey, k3 = kNoKey;
+  int leaves = 0;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     int ref = comp4i(n.ch, c);
@@ -478,42 +492,68 @@ __device__ __forceinline__ bool closest_step4(const SceneView& s, const RayPre& 
     float tn;
     if (!child_hit(n, c, r, best_t, tn)) continue;
     if (ref < 0) {
-      int p = ~ref;
-      ++ptests;
-      float t = isect_prim(s, r, p);
-      if (t > 0.0f && t < tmax && (t < best_t || (t == best_t && best >= 0 && p < best))) {
-        best_t = t;
-        best = p;
-      }
+      leaves |= 1 << c;
     } else {
-      td[cnt] = tn;
-      cr[cnt] = ref;
-      ++cnt;
+      uint32_t k = child_key(tn, c);
+      if (c == 0) k0 = k;
+      else if (c == 1) k1 = k;
+      else if (c == 2) k2 = k;
+      else k3 = k;
     }
   }
-  if (cnt == 0) {
-    if (sp == 0) return true;
-    node = stack[--sp];
-    return false;
-  }
-  // sort the (at most four) inner children by entry distance
-  for (int a = 1; a < cnt; ++a) {
-    float tv = td[a];
-    int rv = cr[a];
-    int b = a - 1;
-    while (b >= 0 && td[b] > tv) {
-      td[b + 1] = td[b];
-      cr[b + 1] = cr[b];
-      --b;
+  while (leaves) {
+    int c = __ffs(leaves) - 1;
+    leaves &= leaves - 1;
+    int p = ~comp4i(n.ch, c);
+    ++ptests;
+    float t = isect_prim(s, r, p);
+    if (t > 0.0f && t < tmax && (t < best_t || (t == best_t && best >= 0 && p < best))) {
+      best_t = t;
+      best = p;
     }
-    td[b + 1] = tv;
-    cr[b + 1] = rv;
   }
-  for (int a = cnt - 1; a >= 1; --a) {
-    if (sp < 64) stack[sp++] = cr[a];
+  // a child entered beyond a closer hit found here holds no closer hit
+  if (k0 != kNoKey && key_dist(k0) > best_t) k0 = kNoKey;
+  if (k1 != kNoKey && key_dist(k1) > best_t) k1 = kNoKey;
+  if (k2 != kNoKey && key_dist(k2) > best_t) k2 = kNoKey;
+  if (k3 != kNoKey && key_dist(k3) > best_t) k3 = kNoKey;
+  key_swap(k0, k1);
+  key_swap(k2, k3);
+  key_swap(k0, k2);
+  key_swap(k1, k3);
+  key_swap(k1, k2);
+  if (k0 == kNoKey) {
+    while (sp > 0) {
+      --sp;
+      if (stack_t[sp] <= best_t) {
+        node = stack[sp];
+        return false;
+      }
+    }
+    return true;
+  }
+  if (k3 != kNoKey) {
+    if (sp < 64) {
+      stack_t[sp] = key_dist(k3);
+      stack[sp++] = comp4i(n.ch, k3 & 3);
+    }
     else atomicOr(status, NEB_STATUS_STACK_OVERFLOW);
   }
-  node = cr[0];
+  if (k2 != kNoKey) {
+    if (sp < 64) {
+      stack_t[sp] = key_dist(k2);
+      stack[sp++] = comp4i(n.ch, k2 & 3);
+    }
+    else atomicOr(status, NEB_STATUS_STACK_OVERFLOW);
+  }
+  if (k1 != kNoKey) {
+    if (sp < 64) {
+      stack_t[sp] = key_dist(k1);
+      stack[sp++] = comp4i(n.ch, k1 & 3);
+    }
+    else atomicOr(status, NEB_STATUS_STACK_OVERFLOW);
+  }
+  node = comp4i(n.ch, k0 & 3);
   return false;
 }
 
@@ -525,8 +565,9 @@ __device__ __forceinline__ int trace_closest(const SceneView& s, const RayPre& r
   float best_t = tmax;
   if (s.nt + s.ns == 0) { t_out = tmax; return -1; }
   int stack[64];
+  float stack_t[64];
   int sp = 0, node = 0;
-  while (!closest_step4(s, r, tmax, node, sp, stack, best_t, best, status, visits, ptests)) {
+  while (!closest_step4(s, r, tmax, node, sp, stack, stack_t, best_t, best, status, visits, ptests)) {
   }
   t_out = best_t;
   return best;

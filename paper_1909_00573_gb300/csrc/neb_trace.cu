@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_closest(SceneView s, co
   RayPre r;
   Walk w;
   int stack[64];
+  float stack_t[64];
   uint32_t visits = 0, ptests = 0;
   while (true) {
     int nr = fetch_rays(ray, fetch, count);
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_closest(SceneView s, co
     ray = nr;
     if (__all_sync(0xffffffffu, ray == kDone)) break;
     for (int step = 0; step < kSteps && ray >= 0; ++step) {
-      if (closest_step4(s, r, FLT_MAX, w.node, w.sp, stack, w.best_t, w.best, &cnt->status, visits, ptests)) {
+      if (closest_step4(s, r, FLT_MAX, w.node, w.sp, stack, stack_t, w.best_t, w.best, &cnt->status, visits, ptests)) {
         hits[ray] = make_int2(w.best, __float_as_int(w.best_t));
         ray = kIdle;
       }
