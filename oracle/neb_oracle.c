@@ -498,14 +498,17 @@ static void bvh_build(bvh_t* b, const scene_t* s) {
 static void bvh_free(bvh_t* b) { free(b->nodes); free(b->prims); free(b->pbmin); free(b->pbmax); free(b->cent); }
 
 /* slab test; the far distance is widened by 1 + 2*gamma(3) (Pharr, Jakob,
- * Humphreys, PBRT 3rd ed., Sec. 3.9.2) so that the test stays conservative. */
+ * Humphreys, PBRT 3rd ed., Sec. 3.9.2) so that the test stays conservative.
+ * Near and far planes are chosen by the sign of the direction, so a zero
+ * component of either sign with the origin on a plane gives a NaN distance
+ * that fmaxf / fminf ignore, instead of one that flips the choice. */
 static int box_hit(const float* mn, const float* mx, v3 o, v3 inv, float tmax) {
   float t0 = 0.0f, t1 = tmax;
   for (int a = 0; a < 3; ++a) {
     float oa = vget(o, a), ia = vget(inv, a);
     float tn = (mn[a] - oa) * ia;
     float tf = (mx[a] - oa) * ia;
-    if (tn > tf) { float t = tn; tn = tf; tf = t; }
+    if (signbit(ia)) { float t = tn; tn = tf; tf = t; }
     tf *= 1.0000004f;
     t0 = fmaxf(t0, tn);
     t1 = fminf(t1, tf);

@@ -287,6 +287,29 @@ def test_bvh_equals_brute_force(oracle):
     assert np.mean(p1 >= 0) > 0.75          # the room is open at z = 0
 
 
+def test_bvh_equals_brute_force_axis_aligned_rays(oracle):
+    """Rays parallel to box planes (direction components +0 and -0) from
+    origins on those planes: a slab whose distance is 0 * inf = NaN must not
+    reject the box, whatever the sign of the zero."""
+    from paper_1909_00573_gb300 import scenes
+    rng = np.random.default_rng(13)
+    tri = np.concatenate([scenes.box_faces((2.0 * i, 0.0, 2.0 * j), (2.0 * i + 1.0, 2.0, 2.0 * j + 1.0))
+                          for i in range(4) for j in range(4)], 0).astype(np.float32)
+    s = scenes.Scene(tri, np.zeros(len(tri)), np.zeros((0, 4)), np.zeros(0),
+                     scenes.material(0, (0.5,) * 3)[None], np.zeros(10))
+    n = 6000
+    o = rng.integers(-2, 17, (n, 3)) * 0.5
+    o[:, 1] = rng.integers(0, 5, n) * 0.5
+    d = np.concatenate([np.eye(3), -np.eye(3)])[rng.integers(0, 6, n)]   # -np.eye holds -0.0
+    rays = np.concatenate([o, d], 1).astype(np.float32)
+    assert np.signbit(rays[:, 3:][rays[:, 3:] == 0]).any()
+    p1, t1 = oracle.trace(s, rays, brute=False)
+    p2, t2 = oracle.trace(s, rays, brute=True)
+    assert np.mean(p2 >= 0) > 0.2
+    assert np.array_equal(p1, p2)
+    assert np.array_equal(t1[p1 >= 0], t2[p2 >= 0])
+
+
 def _mt_double(o, d, tri):
     """Moeller-Trumbore in FP64 over all triangles: (prim, t)."""
     v0, v1, v2 = tri[:, 0].astype(np.float64), tri[:, 1].astype(np.float64), tri[:, 2].astype(np.float64)
