@@ -302,39 +302,51 @@ __device__ __forceinline__ float oct_density_robust(const int* __restrict__ node
   onb(f3(n[0], n[1], n[2]), t, b);
   float3 p = f3(pos[0], pos[1], pos[2]);
   float3 q[4] = {add(p, mul(t, diag)), sub(p, mul(t, diag)), add(p, mul(b, diag)), sub(p, mul(b, diag))};
+  // The four displaced walks are independent: they step down together, so
+  // each step issues up to four loads at once instead of one chain at a time.
+  int v4[4], m4[4], ip4[4][3];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     float qq[3] = {q[i].x, q[i].y, q[i].z};
-    float off[3], np[3];
     bool in = true;
     for (int c = 0; c < 3; ++c) {
-      off[c] = qq[c] - P.minb[c];
-      np[c] = off[c] * P.size_inv[c];
-      in = in && (np[c] >= 0.0f && np[c] < 1.0f);
+      float np = (qq[c] - P.minb[c]) * P.size_inv[c];
+      in = in && (np >= 0.0f && np < 1.0f);
+      ip4[i][c] = in ? (int)(np * (float)grid) : 0;
     }
+    v4[i] = 0;  // outside the scene box: no walk, count 0
+    m4[i] = grid;
     if (in) {
-      int ip[3];
-      for (int c = 0; c < 3; ++c) ip[c] = (int)(np[c] * (float)grid);
-      int v, mask, L;
       if (Lc >= 0) {
-        unsigned diff = (unsigned)((ip[0] ^ ipc[0]) | (ip[1] ^ ipc[1]) | (ip[2] ^ ipc[2]));
+        unsigned diff = (unsigned)((ip4[i][0] ^ ipc[0]) | (ip4[i][1] ^ ipc[1]) | (ip4[i][2] ^ ipc[2]));
         // first level whose octant differs: mask (grid >> L) equals the top differing bit
         int Ld = diff ? depth - (31 - __clz(diff)) : depth + 1;
-        L = Ld - 1 < Lc ? Ld - 1 : Lc;
-        v = vs[L];
-        mask = grid >> L;
+        int L = Ld - 1 < Lc ? Ld - 1 : Lc;
+        v4[i] = vs[L];
+        m4[i] = grid >> L;
       } else {
-        v = __ldg(nodes);
-        mask = grid;
-        L = 0;
+        v4[i] = __ldg(nodes);
       }
-      while (v < 0) {
-        mask >>= 1;
-        int idx = ((ip[0] & mask) ? 1 : 0) + ((ip[1] & mask) ? 2 : 0) + ((ip[2] & mask) ? 4 : 0);
-        idx -= v;
-        v = __ldg(nodes + idx);
+    }
+  }
+  while (v4[0] < 0 || v4[1] < 0 || v4[2] < 0 || v4[3] < 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (v4[i] < 0) {
+        m4[i] >>= 1;
+        int mk = m4[i];
+        int idx = ((ip4[i][0] & mk) ? 1 : 0) + ((ip4[i][1] & mk) ? 2 : 0) + ((ip4[i][2] & mk) ? 4 : 0);
+        v4[i] = __ldg(nodes + (idx - v4[i]));
       }
-      cv[i + 1] = oct_leaf_terms(P, grid, mask, v, ip, off, n, nullptr, cd[i + 1]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (v4[i] > 0) {
+      float qq[3] = {q[i].x, q[i].y, q[i].z};
+      float off[3];
+      for (int c = 0; c < 3; ++c) off[c] = qq[c] - P.minb[c];
+      cv[i + 1] = oct_leaf_terms(P, grid, m4[i], v4[i], ip4[i], off, n, nullptr, cd[i + 1]);
     }
   }
   *queries += 5;
