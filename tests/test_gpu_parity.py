@@ -272,6 +272,50 @@ def test_bvh_far_origin_rays_hit_their_targets(neb, oracle):
     assert np.all(gp[op >= 0] >= 0)
 
 
+def test_bvh_axis_aligned_and_tiny_direction_rays(neb, oracle):
+    """Rays with zero or tiny direction components take the slab test's
+    subtract-and-multiply form (infinite slabs); the others the fused form.
+    On a grid of axis-aligned boxes, from origins on half-integer lattice
+    points (many of them exactly on box planes), both must hit what brute
+    force hits."""
+    from paper_1909_00573_gb300 import scenes
+    rng = np.random.default_rng(13)
+    tris = [scenes.box_faces((2.0 * i, 0.0, 2.0 * j), (2.0 * i + 1.0, float(rng.integers(1, 5)), 2.0 * j + 1.0))
+            for i in range(6) for j in range(6)]
+    tri = np.concatenate(tris, 0).astype(np.float32)
+    s = scenes.Scene(tri, np.zeros(len(tri)), np.zeros((0, 4)), np.zeros(0),
+                     scenes.material(0, (0.5,) * 3)[None], np.zeros(10))
+    n = 24000
+    o = rng.integers(-2, 25, (n, 3)) * 0.5
+    o[:, 1] = rng.integers(0, 10, n) * 0.5
+    axes = np.concatenate([np.eye(3), -np.eye(3)])
+    d = axes[rng.integers(0, 6, n)]
+    one_zero = rng.random(n) < 0.3                       # one exact zero component
+    v = rng.normal(size=(n, 3))
+    v[np.arange(n), rng.integers(0, 3, n)] = 0.0
+    d[one_zero] = v[one_zero]
+    tiny = rng.random(n) < 0.1                           # a component below 1e-30
+    w = rng.normal(size=(n, 3))
+    w[np.arange(n), rng.integers(0, 3, n)] = 1e-33
+    d[tiny] = w[tiny]
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    rays = np.concatenate([o, d], 1).astype(np.float32)
+    rc = scenes.RenderConfig(8, 8, 4, 0.01, 1024, 4, 1)
+    ctx = neb.Context(neb.make_config(rc))
+    ctx.scene_upload(s)
+    ctx.build_bvh()
+    gp, gt = ctx.trace_closest(rays)
+    assert ctx.stats()["status"] == 0
+    ctx.close()
+    op, ot = oracle.trace(s, rays, brute=True)
+    assert (op >= 0).mean() > 0.2
+    same = gp == op
+    assert same.mean() >= 0.9999, same.mean()
+    hit = same & (gp >= 0)
+    assert np.array_equal(gt[hit].view(np.int32), ot[hit].view(np.int32))
+    assert np.all(gp[op >= 0] >= 0)
+
+
 def test_neighbour_counts_equal_brute_force(neb, oracle):
     rng = np.random.default_rng(51)
     pts = rng.uniform(0, 1, (30000, 3)).astype(np.float32)
