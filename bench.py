@@ -162,8 +162,8 @@ def load_peaks():
 TRAFFIC_SOURCES = ("paper_1909_00573_gb300/csrc/neb_trace.cu", "paper_1909_00573_gb300/csrc/neb_device.cuh",
                    "paper_1909_00573_gb300/csrc/neb_types.h")
 NCU_TRAFFIC = {
-    "trace_camera": {"bytes_per_launch": 66622694,
-                     "sources_sha256": "399e1cad5fdf7f59fefcdc2ceb4a3ce20b84bda99ee4cf82f13fac46f9f3fab1",
+    "trace_camera": {"bytes_per_launch": 73466496,
+                     "sources_sha256": "8566ef0625fed9f3f4754768a24f8cac270cd6a28a6bd32f44e896627ccfb5bd",
                      "profile": "profiles/k_trace_closest_large_city.md"},
 }
 
