@@ -85,6 +85,20 @@ def max_over_ranks(x, dist=None, device="cpu"):
     return float(t.item())
 
 
+def rates(d, world, ms_total):
+    """Secondary throughputs of the timed steps, whole job (every rank did the
+    same work): rays traced (camera + shadow + photon), merge candidates tested
+    and accepted, octree inserts and queries (a robust query counts 5)."""
+    s = ms_total / 1000.0
+    if s <= 0:
+        return None
+    f = lambda n: world * n / s / 1e6  # noqa: E731
+    rays = d.get("camera_rays", 0) + d.get("shadow_rays", 0) + d.get("photon_hits", 0)
+    return {"Mrays_per_s": f(rays), "Mmerge_tests_per_s": f(d.get("merge_tests", 0)),
+            "Mmerges_per_s": f(d.get("merges", 0)), "Moctree_inserts_per_s": f(d.get("octree_inserts", 0)),
+            "Moctree_queries_per_s": f(d.get("octree_queries", 0))}
+
+
 def job_value(world, paths_per_step, steps, seconds):
     """Whole-job throughput in Mpaths/s: the paths of all replicas over the job time."""
     return world * paths_per_step * steps / seconds / 1e6
@@ -595,6 +609,7 @@ def main():
                 "gpu_launches": int(d.get("kernel_launches", 0)), "clocks": clk,
                 "stages_ms_per_step": {k: v[0] / args.profile_steps for k, v in stages.items()},
                 "stage_sum_ms_per_step": total_stage_ms / args.profile_steps,
+                "rates": rates(d, world, ms),
                 "counters_per_step": {k: (v / args.steps if not isinstance(v, list) else [x / args.steps for x in v])
                                       for k, v in d.items() if k not in ("iterations",)},
                 "status": s1["status"], "bvh_build_ms": bvh_build_ms,
