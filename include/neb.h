@@ -73,6 +73,10 @@ typedef struct {
   int lp_photons;        /* conventional light photons per iteration (n_LP, Sec. 6.1), used when
                             strategy_mask has bit 8; each is emitted from a light and merged at
                             view vertices like the NEB photons, under the same balance heuristic */
+  int density_all;       /* 0: rho is evaluated only where a result uses it (NEE vertices whose
+                            shadow ray reached the light, for w_E and Phi = dE / rho, and the vertex
+                            before each random light hit, for w_e); 1: at every NEE vertex.  The
+                            image is the same either way; 1 only fills neb_read_nee_rho */
 } neb_config;
 
 typedef struct {
@@ -177,7 +181,8 @@ int neb_read_accum(neb_ctx* ctx, double* out);
 int neb_read_split(neb_ctx* ctx, double* out);
 
 /* Density rho at every NEE vertex of the last iteration, [H*W][D-1] indexed
- * pixel*(D-1) + (k-1); -1 where the path has no NEE vertex k.  Host memory. */
+ * pixel*(D-1) + (k-1); -1 where the path has no NEE vertex k, -2 where rho
+ * was not evaluated (cfg.density_all = 0 and no result uses it).  Host memory. */
 int neb_read_nee_rho(neb_ctx* ctx, float* out);
 /* The NEE vertices of the last iteration in store order: positions and
  * geometric normals [cap][3] (host), *count = their number (at most

@@ -77,6 +77,7 @@ static bool config_ok(const neb_config* cfg) {
          !(cfg->strategy_mask & ~15u) && cfg->lp_photons >= 0 && cfg->lp_photons <= (1 << 26) &&
          (cfg->bvh_builder == 0 || cfg->bvh_builder == 1) &&
          (cfg->photon_records == 0 || cfg->photon_records == 1) &&
+         (cfg->density_all == 0 || cfg->density_all == 1) &&
          (long long)cfg->width * cfg->height <= (1ll << 28);
 }
 

@@ -345,9 +345,11 @@ __global__ void __launch_bounds__(kThreads) k_nee(SceneView s, IterParams ip, Ne
     bool emit = false;
     PhotonRay ph;
     uint32_t nphot = 0;
-    if (i < count) {
-      float4 pp = nv.pos[i], nn = nv.nrm[i], ww = nv.wo[i], tt = nv.tau[i], ee = nv.err[i], ld = nv.ldir[i],
-             de = nv.dE[i];
+    // both the NEE contribution and the photon need dE != 0: a vertex whose
+    // shadow ray was blocked is skipped after reading dE alone
+    const float4 de = i < count ? nv.dE[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (i < count && maxc(xyz(de)) > 0.0f) {
+      float4 pp = nv.pos[i], nn = nv.nrm[i], ww = nv.wo[i], tt = nv.tau[i], ee = nv.err[i], ld = nv.ldir[i];
       int bits = __float_as_int(nn.w);
       int mat = bits & NV_MAT_MASK, k = (bits >> NV_K_SHIFT) & 63, vflags = (bits >> NV_FLAG_SHIFT) & 7;
       bool delta = vflags & NV_DELTA;
@@ -355,8 +357,7 @@ __global__ void __launch_bounds__(kThreads) k_nee(SceneView s, IterParams ip, Ne
       float3 p = xyz(pp), n = xyz(nn), wo = xyz(ww), tau = xyz(tt), ldir = xyz(ld), dE = xyz(de);
       float rho = ld.w, Cfac = pp.w, g_y = tt.w;
       Mat m = load_mat(s.mats, mat);
-      bool visible = maxc(dE) > 0.0f;
-      if ((ip.mask & 2u) && !delta && visible) {
+      if ((ip.mask & 2u) && !delta) {
         float3 f = bsdf_eval(m, n, wo, ldir);
         if (maxc(f) > 0.0f) {
           float pdfF = bsdf_pdf(m, n, wo, ldir), pdfC = bsdf_pdf(m, n, ldir, wo);
@@ -368,7 +369,7 @@ __global__ void __launch_bounds__(kThreads) k_nee(SceneView s, IterParams ip, Ne
           add_pixel(accum, split, 1, pixel, L, P);
         }
       }
-      if ((ip.mask & 4u) && ip.D >= 3 && visible && rho > 0.0f) {
+      if ((ip.mask & 4u) && ip.D >= 3 && rho > 0.0f) {
         float3 phi0 = mul(dE, 1.0f / rho);
         uint4 rb = rng_block(ip.key, ip.iteration, pixel, 256u * k + 1u, 1);
         float3 w1, wt;
@@ -465,7 +466,9 @@ __global__ void __launch_bounds__(kThreads) k_lp_emit(SceneView s, IterParams ip
 
 // pass 3: self emission of the stored random hits (Sec. 3.3)
 __global__ void __launch_bounds__(kThreads) k_emission(SceneView s, IterParams ip, NeeStore nv, const RHEvent* rh,
-                                                       DevCounters* cnt, double* accum, double* split) {
+                                                       DevCounters* cnt, double* accum, double* split,
+                                                       const int* __restrict__ oct_nodes, const OctreeState* oct_state,
+                                                       OctreeParams oct, int robust) {
   const int count = min(cnt->rh_count, ip.cap_rh);
   const int P = ip.W * ip.H;
   const float pir2 = kPi * ip.r * ip.r;
@@ -478,8 +481,16 @@ __global__ void __launch_bounds__(kThreads) k_emission(SceneView s, IterParams i
       float rho = 0.0f;
       float3 xp;
       if (prev >= 0) {
-        xp = xyz(nv.pos[prev]);
+        const float4 xp4 = nv.pos[prev];
+        xp = xyz(xp4);
         rho = nv.ldir[prev].w;
+        if (rho < -1.5f) {  // not evaluated by the density pass (its shadow ray was blocked)
+          const float4 nn = nv.nrm[prev];
+          const float pp[3] = {xp4.x, xp4.y, xp4.z}, qq[3] = {nn.x, nn.y, nn.z};
+          int queries = 0;
+          rho = robust ? oct_density_robust(oct_nodes, oct, oct_state->depth, pp, qq, &queries)
+                       : oct_density(oct_nodes, oct, oct_state->depth, pp, qq, nullptr);
+        }
       } else {
         continue;  // the NEE store overflowed; the event cannot be weighted
       }
@@ -912,7 +923,9 @@ static long long enqueue_pass23(neb_ctx* c, int iteration, cudaStream_t st2, Sta
     tm.end();
   }
   tm.begin(STAGE_EMISSION);
-  k_emission<<<capped_blocks(c->cap_rh, kThreads, B), kThreads, 0, st2>>>(s, ip, sl.nv, sl.rh, cnt, c->accum, split);
+  k_emission<<<capped_blocks(c->cap_rh, kThreads, B), kThreads, 0, st2>>>(s, ip, sl.nv, sl.rh, cnt, c->accum, split,
+                                                                           c->oct_nodes, c->oct_state, c->oct,
+                                                                           c->cfg.density_mode == 0);
   launches += 1;
   tm.end();
   if (photons) {

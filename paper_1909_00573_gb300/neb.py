@@ -42,7 +42,7 @@ class Config(C.Structure):
                 ("octree_capacity", C.c_int), ("split_factor", C.c_int), ("seed", C.c_uint64),
                 ("octree_mode", C.c_int), ("density_mode", C.c_int), ("strategy_mask", C.c_uint32),
                 ("keep_split", C.c_int), ("bvh_builder", C.c_int), ("photon_records", C.c_int),
-                ("lp_photons", C.c_int)]
+                ("lp_photons", C.c_int), ("density_all", C.c_int)]
 
 
 class Tuning(C.Structure):
@@ -144,7 +144,7 @@ def make_config(rc, keep_split=False, octree_mode=None, density_mode=None, strat
                   rc.seed, rc.octree_mode if octree_mode is None else octree_mode,
                   rc.density_mode if density_mode is None else density_mode,
                   rc.strategy_mask if strategy_mask is None else strategy_mask, int(keep_split), int(bvh_builder),
-                  int(photon_records), int(getattr(rc, "lp_photons", 0)))
+                  int(photon_records), int(getattr(rc, "lp_photons", 0)), int(getattr(rc, "density_all", 0)))
 
 
 class Context:

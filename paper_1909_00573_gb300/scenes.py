@@ -95,6 +95,7 @@ class RenderConfig:
     strategy_mask: int = 7      # bit 0 random hit (e), bit 1 NEE (E), bit 2 NEB photon merge (P),
                                 # bit 3 conventional light-photon merge (LP, Sec. 6.1)
     lp_photons: int = 0         # light photons per iteration (n_LP) when bit 3 is set
+    density_all: int = 0        # 1: evaluate rho at every NEE vertex, not only where a result uses it
 
 
 class SplitMix64:

@@ -47,6 +47,8 @@ def test_argument_errors_without_gpu(libneb):
     assert L.neb_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
     cfg = neb.Config(8, 8, 4, 0.01, 64, 4, 0, 0, 0, 15, 0, 0, 0, -1)  # negative light-photon count
     assert L.neb_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
+    cfg = neb.Config(8, 8, 4, 0.01, 64, 4, 0, 0, 0, 7, 0, 0, 0, 0, 2)  # density_all not 0 or 1
+    assert L.neb_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
     cfg = neb.Config(8, 8, 4, 0.01, 64, 4, 0, 0, 0, 7, 0, 5)       # unknown BVH builder
     assert L.neb_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
     assert L.neb_iterate(None, 1) == -1

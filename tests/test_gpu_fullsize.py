@@ -69,7 +69,10 @@ def test_fullsize_all_strategies_properties(neb, name):
     assert st["status"] & ~neb.STATUS_OCTREE_FULL == 0          # no spin timeout, overflow or stack overflow
     assert st["iterations"] == 2
     assert st["octree_inserts"] == st["nee_vertices"] <= 2 * P * (rc.max_depth - 1)
-    assert st["octree_queries"] == 5 * st["nee_vertices"]        # robust query: five lookups
+    # robust query: five lookups, at the NEE vertices whose shadow ray reached
+    # the light (every photon comes from one of them)
+    assert st["octree_queries"] % 5 == 0
+    assert 5 * st["photons"] <= st["octree_queries"] <= 5 * st["nee_vertices"]
     assert st["shadow_rays"] <= st["nee_vertices"]
     assert st["photons"] <= st["shadow_rays"]
     assert st["merges"] <= st["merge_tests"]

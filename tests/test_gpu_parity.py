@@ -343,6 +343,7 @@ def test_tiny_room_per_path_parity(neb, oracle):
     from paper_1909_00573_gb300 import scenes
     s, rc = scenes.workload("tiny_room")
     rc.octree_mode = 1
+    rc.density_all = 1           # rho at every NEE vertex, for the comparison below
     ctx = neb.render(s, rc)
     gsplit, grho, gacc, st = ctx.read_split(), ctx.read_nee_rho(), ctx.read_accum(), ctx.stats()
     ctx.close()
@@ -393,6 +394,46 @@ def test_overlapped_iterations_equal_sequential(neb):
     for key in ("camera_rays", "nee_vertices", "shadow_rays", "photons", "photon_hits", "merge_tests", "merges",
                 "random_hits", "octree_inserts", "octree_queries", "octree_nodes", "iterations"):
         assert st0[key] == st1[key], key
+    np.testing.assert_allclose(sp0, sp1, rtol=1e-12, atol=1e-12 * float(np.abs(sp1).max()))
+    np.testing.assert_allclose(a0, a1, rtol=1e-12, atol=1e-12 * float(np.abs(a1).max()))
+    assert a0.sum() > 0
+
+
+@pytest.mark.parametrize("name,lp", [("tiny_room", 0), ("tiny_room", 4096), ("glass_in_emitting_box", 0)])
+def test_density_only_where_used_changes_no_result(neb, name, lp):
+    """By default rho is evaluated only at NEE vertices whose shadow ray
+    reached the light; the random-hit weight evaluates rho at its previous
+    vertex itself.  With the deterministic octree the image and every
+    per-strategy sum equal those of evaluating rho everywhere (up to the
+    order of the FP64 atomic additions), and the densities that are evaluated
+    are identical.  In the glass box every light hit follows a glass vertex,
+    many of whose shadow rays the sphere itself blocks."""
+    from paper_1909_00573_gb300 import scenes
+    if name == "tiny_room":
+        s, rc = scenes.workload("tiny_room")
+    else:
+        s = scenes.glass_in_emitting_box()
+        rc = scenes.RenderConfig(48, 48, 8, 0.01, 1 << 16, 8, 3)
+    rc.octree_mode = 1
+    if lp:
+        rc.strategy_mask |= 8
+        rc.lp_photons = lp
+    out = {}
+    for every in (0, 1):
+        rc.density_all = every
+        ctx = neb.Context(neb.make_config(rc, keep_split=True))
+        ctx.scene_upload(s)
+        ctx.build_bvh()
+        ctx.iterate(rc.iterations)
+        out[every] = (ctx.read_nee_rho(), ctx.read_split(), ctx.read_accum(), ctx.stats())
+        ctx.close()
+    (r0, sp0, a0, st0), (r1, sp1, a1, st1) = out[0], out[1]
+    assert st0["status"] & ~neb.STATUS_OCTREE_FULL == 0
+    assert (r1 == -2).sum() == 0 and (r0 == -2).sum() > 0          # some shadow rays were blocked
+    ev = r0 != -2
+    assert np.array_equal(r0[ev], r1[ev])
+    assert st0["octree_queries"] < st1["octree_queries"]
+    assert st0["random_hits"] == st1["random_hits"] > 0
     np.testing.assert_allclose(sp0, sp1, rtol=1e-12, atol=1e-12 * float(np.abs(sp1).max()))
     np.testing.assert_allclose(a0, a1, rtol=1e-12, atol=1e-12 * float(np.abs(a1).max()))
     assert a0.sum() > 0
