@@ -109,7 +109,7 @@ extern "C" int neb_job_device_bytes(const neb_config* cfg, int n_tri, int n_sph,
   const size_t D = (size_t)cfg->max_depth, nee_rows = k.P * (D > 1 ? D - 1 : 1);
   uint64_t b = 0;
   b += 3 * k.P * sizeof(CamRay) + 2 * sizeof(DevCounters);
-  b += 2 * (7 * k.cap_nee * sizeof(float4) + k.cap_rh * sizeof(RHEvent) +
+  b += 2 * (7 * k.cap_nee * sizeof(float4) + k.cap_nee * sizeof(int) + k.cap_rh * sizeof(RHEvent) +
             (cfg->octree_mode == 1 ? nee_rows * sizeof(int) : 0));
   b += 2 * k.cap_ph * sizeof(PhotonRay) + k.cap_cam * sizeof(int2) + k.cap_ph * sizeof(int2);
   b += k.cap_nee * (sizeof(MergeRec) + sizeof(int)) + 2 * ((size_t)k.table + 1) * sizeof(int);
@@ -165,7 +165,8 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
     ok = dalloc(&sl.nv.pos, c->cap_nee) == cudaSuccess && dalloc(&sl.nv.nrm, c->cap_nee) == cudaSuccess &&
          dalloc(&sl.nv.wo, c->cap_nee) == cudaSuccess && dalloc(&sl.nv.tau, c->cap_nee) == cudaSuccess &&
          dalloc(&sl.nv.err, c->cap_nee) == cudaSuccess && dalloc(&sl.nv.ldir, c->cap_nee) == cudaSuccess &&
-         dalloc(&sl.nv.dE, c->cap_nee) == cudaSuccess && dalloc(&sl.rh, c->cap_rh) == cudaSuccess &&
+         dalloc(&sl.nv.dE, c->cap_nee) == cudaSuccess && dalloc(&sl.nv.lit, c->cap_nee) == cudaSuccess &&
+         dalloc(&sl.rh, c->cap_rh) == cudaSuccess &&
          (cfg->octree_mode != 1 || dalloc(&sl.slot_map, P * (D > 1 ? D - 1 : 1)) == cudaSuccess);
   }
   ok = ok && dalloc(&c->phq[0], c->cap_ph) == cudaSuccess && dalloc(&c->phq[1], c->cap_ph) == cudaSuccess &&
@@ -208,7 +209,7 @@ extern "C" void neb_destroy(neb_ctx* c) {
   if (c->stream_b) cudaStreamSynchronize(c->stream_b);
   for (IterSlot& sl : c->slots) {
     cudaFree(sl.nv.pos); cudaFree(sl.nv.nrm); cudaFree(sl.nv.wo); cudaFree(sl.nv.tau); cudaFree(sl.nv.err);
-    cudaFree(sl.nv.ldir); cudaFree(sl.nv.dE); cudaFree(sl.rh); cudaFree(sl.slot_map);
+    cudaFree(sl.nv.ldir); cudaFree(sl.nv.dE); cudaFree(sl.nv.lit); cudaFree(sl.rh); cudaFree(sl.slot_map);
   }
   cudaFree(c->phq[0]); cudaFree(c->phq[1]); cudaFree(c->hits); cudaFree(c->hits_ph); cudaFree(c->mrec);
   cudaFree(c->vert_bucket); cudaFree(c->bucket_count); cudaFree(c->bucket_start); cudaFree(c->scan_scratch.data);

@@ -69,8 +69,9 @@ struct NeeStore {
   float4* wo;    // xyz, w: pixel (int bits)
   float4* tau;   // rgb, w: g_y = cos_y / (dist^2 p_l)
   float4* err;   // hit point error bound, w: ldist
-  float4* ldir;  // direction to the light point, w: rho (after the density pass)
+  float4* ldir;  // direction to the light point, w: rho after the density pass (-2 where not evaluated)
   float4* dE;    // irradiance rgb (zero if back-facing or occluded), w: the light point's light-photon pdf
+  int* lit;      // ids of the vertices whose shadow ray reached the light (DevCounters::lit_count of them)
 };
 enum { NV_DELTA = 1, NV_MERGEABLE = 2, NV_SHADOW = 4 };
 enum { NV_MAT_MASK = (1 << 20) - 1, NV_K_SHIFT = 20, NV_FLAG_SHIFT = 26 };
@@ -83,6 +84,7 @@ struct DevCounters {
   int rh_count;
   int ph_count[2];
   int merge_count;
+  int lit_count;
   uint32_t status;
   unsigned long long camera_rays, nee_vertices, shadow_rays, photons, photon_hits;
   unsigned long long merge_tests, merges, random_hits, octree_inserts, octree_queries;

@@ -138,24 +138,18 @@ __global__ void k_oct_insert_nee_seq(int* nodes, OctreeState* st, OctreeParams P
   cnt->octree_inserts += done;
 }
 
-// rho at the NEE vertices.  Unless `all`, only where the shadow ray reached
-// the light (dE != 0): there rho enters w_E and the photon flux; elsewhere
-// no result reads it (the random-hit weight evaluates its own, k_emission),
-// and -2 is stored.
+// rho at the NEE vertices.  Unless `all`, only at the vertices of the lit
+// list (their shadow ray reached the light): there rho enters w_E and the
+// photon flux; elsewhere no result reads it (the random-hit weight evaluates
+// its own, k_emission), and the -2 stored at the vertex's creation stays.
 __global__ void k_oct_density_nee(const int* __restrict__ nodes, const OctreeState* st, OctreeParams P,
                                   const float4* __restrict__ vpos, const float4* __restrict__ vnrm, float4* vldir,
-                                  const float4* __restrict__ vdE, DevCounters* cnt, int cap, int robust, int all) {
-  int count = min(cnt->nee_count, cap);
+                                  const int* __restrict__ lit, DevCounters* cnt, int cap, int robust, int all) {
+  int count = min(all ? cnt->nee_count : cnt->lit_count, cap);
   int depth = st->depth;
   int queries = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
-    if (!all) {
-      float4 de = vdE[i];
-      if (!(fmaxf(de.x, fmaxf(de.y, de.z)) > 0.0f)) {
-        vldir[i].w = -2.0f;
-        continue;
-      }
-    }
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
+    const int i = all ? t : lit[t];
     float4 v = vpos[i], nn = vnrm[i];
     float p[3] = {v.x, v.y, v.z};
     float q[3] = {nn.x, nn.y, nn.z};
@@ -211,7 +205,7 @@ cudaError_t launch_oct_insert_nee(neb_ctx* c, const IterSlot& sl, cudaStream_t s
 
 cudaError_t launch_oct_density_nee(neb_ctx* c, const IterSlot& sl, cudaStream_t st) {
   k_oct_density_nee<<<capped_blocks(c->cap_nee, 256, 152 * 8), 256, 0, st>>>(c->oct_nodes, c->oct_state, c->oct, sl.nv.pos, sl.nv.nrm, sl.nv.ldir,
-                                             sl.nv.dE, sl.cnt, c->cap_nee, c->cfg.density_mode == 0,
+                                             sl.nv.lit, sl.cnt, c->cap_nee, c->cfg.density_mode == 0,
                                              c->cfg.density_all);
   return cudaGetLastError();
 }

@@ -150,6 +150,7 @@ __global__ void k_begin(DevCounters* cnt) {
   cnt->ph_count[0] = 0;
   cnt->ph_count[1] = 0;
   cnt->merge_count = 0;
+  cnt->lit_count = 0;
 }
 
 __global__ void k_camera(IterParams ip, CameraParams cam, CamRay* q, DevCounters* cnt) {
@@ -299,7 +300,7 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
       nv.wo[nid] = make_float4(-d.x, -d.y, -d.z, __int_as_float(pixel));
       nv.tau[nid] = make_float4(tau.x, tau.y, tau.z, g_y);
       nv.err[nid] = make_float4(err.x, err.y, err.z, ldist);
-      nv.ldir[nid] = make_float4(ldir.x, ldir.y, ldir.z, 0.0f);
+      nv.ldir[nid] = make_float4(ldir.x, ldir.y, ldir.z, -2.0f);  // rho: not evaluated (yet)
       nv.dE[nid] = make_float4(dE.x, dE.y, dE.z, nee_p_lp);
       if (slot_map) slot_map[(size_t)pixel * (ip.D - 1) + (k - 1)] = nid;
     }
@@ -336,19 +337,20 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_nee(SceneView s, IterParams ip, NeeStore nv, DevCounters* cnt,
                                                   double* accum, double* split, void* __restrict__ phq, int packed) {
-  const int count = min(cnt->nee_count, ip.cap_nee);
+  // both the NEE contribution and the photon need dE != 0: the kernel walks
+  // the list of vertices whose shadow ray reached the light
+  const int count = min(cnt->lit_count, ip.cap_nee);
   const int stride = gridDim.x * blockDim.x;
   const int P = ip.W * ip.H;
   const float pir2 = kPi * ip.r * ip.r;
   for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
-    const int i = base + threadIdx.x;
+    const int t = base + threadIdx.x;
+    const int i = t < count ? nv.lit[t] : 0;
     bool emit = false;
     PhotonRay ph;
     uint32_t nphot = 0;
-    // both the NEE contribution and the photon need dE != 0: a vertex whose
-    // shadow ray was blocked is skipped after reading dE alone
-    const float4 de = i < count ? nv.dE[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (i < count && maxc(xyz(de)) > 0.0f) {
+    const float4 de = t < count ? nv.dE[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (t < count && maxc(xyz(de)) > 0.0f) {
       float4 pp = nv.pos[i], nn = nv.nrm[i], ww = nv.wo[i], tt = nv.tau[i], ee = nv.err[i], ld = nv.ldir[i];
       int bits = __float_as_int(nn.w);
       int mat = bits & NV_MAT_MASK, k = (bits >> NV_K_SHIFT) & 63, vflags = (bits >> NV_FLAG_SHIFT) & 7;

@@ -353,7 +353,8 @@ __global__ void __launch_bounds__(kGroupThreads) k_cam_group_scatter(const CamRa
 }
 
 // Shadow rays (any hit with tmax = (1 - 1e-4) dist from the offset origin);
-// an occluded NEE vertex gets dE = 0.
+// an occluded NEE vertex gets dE = 0, the others are appended to the lit
+// list that passes 2-3 walk.
 __global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, NeeStore nv,
                                                                 const ShadowRay* __restrict__ srays, int cap,
                                                                 int* __restrict__ fetch, DevCounters* cnt) {
@@ -364,8 +365,11 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, Nee
   float tmax = 0.0f;
   int stack[64];
   uint32_t visits = 0, ptests = 0, rays = 0;
+  const bool no_geometry = s.nt + s.ns == 0;
   while (true) {
     int nr = fetch_rays(ray, fetch, count);
+    bool lit0 = false;
+    int lit0_id = 0;
     if (ray == kIdle && nr >= 0) {
       float4 so = __ldg(&srays[nr].o), sd = __ldg(&srays[nr].d);
       nr = __float_as_int(sd.w);
@@ -373,7 +377,15 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, Nee
       tmax = so.w;
       walk_init(w);
       ++rays;
-      if (s.nt + s.ns == 0) nr = kIdle;
+      if (no_geometry) {  // nothing can block it
+        lit0 = true;
+        lit0_id = nr;
+        nr = kIdle;
+      }
+    }
+    if (no_geometry) {
+      int slot = warp_append(&cnt->lit_count, lit0, cap, &cnt->status);
+      if (slot >= 0) nv.lit[slot] = lit0_id;
     }
     ray = nr;
     if (__all_sync(0xffffffffu, ray == kDone)) break;
@@ -381,6 +393,8 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, Nee
       if (ray >= 0 && w.node >= 0 && w.npend <= 1) inner_step4(s, r, tmax, w, stack, &cnt->status, visits);
       bool ready = ray < 0 || w.npend >= 2 || w.node < 0;
       if (__all_sync(0xffffffffu, ready)) {
+        bool lit = false;
+        int lit_id = 0;
         if (ray >= 0) {
           bool hit = false;
           for (int q = 0; q < w.npend; ++q) {
@@ -389,9 +403,16 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, Nee
             hit |= t > 0.0f && t < tmax;
           }
           w.npend = 0;
-          if (hit) nv.dE[ray] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          if (hit) {
+            nv.dE[ray] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          } else if (w.node < 0) {
+            lit = true;
+            lit_id = ray;
+          }
           if (hit || w.node < 0) ray = kIdle;
         }
+        int slot = warp_append(&cnt->lit_count, lit, cap, &cnt->status);
+        if (slot >= 0) nv.lit[slot] = lit_id;
         if (__all_sync(0xffffffffu, ray < 0)) break;
       }
     }
