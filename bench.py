@@ -175,10 +175,13 @@ def load_peaks():
 # sources hash to the value recorded with the capture, else null.
 TRAFFIC_SOURCES = ("paper_1909_00573_gb300/csrc/neb_trace.cu", "paper_1909_00573_gb300/csrc/neb_device.cuh",
                    "paper_1909_00573_gb300/csrc/neb_types.h")
-NCU_TRAFFIC = {
-    "trace_camera": {"bytes_per_launch": 73466496,
-                     "sources_sha256": "8566ef0625fed9f3f4754768a24f8cac270cd6a28a6bd32f44e896627ccfb5bd",
-                     "profile": "profiles/k_trace_closest_large_city.md"},
+NCU_TRAFFIC = {  # (workload, stage): DRAM bytes per launch from one ncu capture of these sources
+    ("large_city", "trace_camera"): {"bytes_per_launch": 73495270,
+                                     "sources_sha256": "ab4cbfcc29040f0c331378de51baf66992c9c7b15a22a1b40c7644bb853364a0",
+                                     "profile": "profiles/k_trace_closest_large_city.md"},
+    ("large_city", "shadow"): {"bytes_per_launch": 275990000,
+                               "sources_sha256": "ab4cbfcc29040f0c331378de51baf66992c9c7b15a22a1b40c7644bb853364a0",
+                               "profile": "profiles/k_trace_shadow_large_city.md"},
 }
 
 
@@ -190,8 +193,8 @@ def sources_sha256():
     return h.hexdigest()
 
 
-def measured_traffic(stage):
-    e = NCU_TRAFFIC.get(stage)
+def measured_traffic(workload, stage):
+    e = NCU_TRAFFIC.get((workload, stage))
     if not e or e["bytes_per_launch"] is None or e["sources_sha256"] != sources_sha256():
         return None, None
     return e["bytes_per_launch"], e["profile"]
@@ -210,7 +213,7 @@ def stage_bytes(stage, d, P, iters):
     elif stage == "trace_photon":
         rec = 40 * d["photon_hits"]
     elif stage == "shadow":
-        rec = 32 * d["shadow_rays"] + 16 * d["shadow_rays"]      # ray record read, dE cleared when occluded
+        rec = 32 * d["shadow_rays"] + 4 * d["photons"]           # ray record read, lit-list entries (about one per photon)
     elif stage == "extend":
         return (72 * d["camera_rays"] + 64 * max(d["camera_rays"] - P * iters, 0) + 112 * d["nee_vertices"] +
                 48 * d["random_hits"]), None
@@ -560,7 +563,7 @@ def main():
         per_launch = byt / dom_launches
         avg_ms = dom_ms / dom_launches
         achieved = per_launch / (avg_ms / 1000.0) / 1e9
-        traffic, traffic_src = measured_traffic(dom)
+        traffic, traffic_src = measured_traffic(args.workload, dom)
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src, "peak_kind": peak_kind,
                 "bytes_per_launch": per_launch, "avg_launch_ms": avg_ms,

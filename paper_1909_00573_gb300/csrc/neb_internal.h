@@ -70,7 +70,8 @@ struct NeeStore {
   float4* tau;   // rgb, w: g_y = cos_y / (dist^2 p_l)
   float4* err;   // hit point error bound, w: ldist
   float4* ldir;  // direction to the light point, w: rho after the density pass (-2 where not evaluated)
-  float4* dE;    // irradiance rgb (zero if back-facing or occluded), w: the light point's light-photon pdf
+  float4* dE;    // unoccluded irradiance rgb (zero if back-facing; read only for vertices of the lit list),
+                 // w: the light point's light-photon pdf
   int* lit;      // ids of the vertices whose shadow ray reached the light (DevCounters::lit_count of them)
 };
 enum { NV_DELTA = 1, NV_MERGEABLE = 2, NV_SHADOW = 4 };

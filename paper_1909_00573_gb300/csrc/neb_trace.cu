@@ -352,9 +352,9 @@ __global__ void __launch_bounds__(kGroupThreads) k_cam_group_scatter(const CamRa
   }
 }
 
-// Shadow rays (any hit with tmax = (1 - 1e-4) dist from the offset origin);
-// an occluded NEE vertex gets dE = 0, the others are appended to the lit
-// list that passes 2-3 walk.
+// Shadow rays (any hit with tmax = (1 - 1e-4) dist from the offset origin):
+// the NEE vertices whose ray reaches the light are appended to the lit list,
+// the only record of visibility that passes 2-3 read.
 __global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, NeeStore nv,
                                                                 const ShadowRay* __restrict__ srays, int cap,
                                                                 int* __restrict__ fetch, DevCounters* cnt) {
@@ -403,9 +403,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, Nee
             hit |= t > 0.0f && t < tmax;
           }
           w.npend = 0;
-          if (hit) {
-            nv.dE[ray] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-          } else if (w.node < 0) {
+          if (!hit && w.node < 0) {
             lit = true;
             lit_id = ray;
           }
