@@ -127,6 +127,18 @@ int neb_build_bvh(neb_ctx* ctx);
  * the last iteration, so work enqueued on it afterwards sees every result. */
 int neb_iterate(neb_ctx* ctx, int n_iterations);
 
+/* Progressive display: enqueues n_iterations iterations like neb_iterate and,
+ * after each, the image of all iterations so far (as neb_resolve) copied into
+ * rgb_host [H][W][3] float, each copy overwriting the previous one.  The
+ * copies follow each iteration's passes 2-3 on the context's second stream,
+ * so they do not hold back the next iteration's pass 1 (reading the image
+ * through neb_resolve after every neb_iterate call would).  Asynchronous:
+ * rgb_host must stay valid and unread until the context stream has been
+ * synchronised (it waits for the last copy before the call returns); pinned
+ * host memory keeps the copies asynchronous, pageable memory makes each copy
+ * wait.  NEB_ERR_ARG for a null buffer or a context without scene and BVH. */
+int neb_iterate_read(neb_ctx* ctx, int n_iterations, float* rgb_host);
+
 /* Batched jobs: n_iterations iterations of each of the n contexts, enqueued
  * round-robin (iteration t of every job before iteration t + 1 of any) so
  * the jobs' kernels overlap on the GPU.  The contexts must be distinct and on

@@ -113,7 +113,7 @@ extern "C" int neb_job_device_bytes(const neb_config* cfg, int n_tri, int n_sph,
             (cfg->octree_mode == 1 ? nee_rows * sizeof(int) : 0));
   b += 2 * k.cap_ph * sizeof(PhotonRay) + k.cap_cam * sizeof(int2) + k.cap_ph * sizeof(int2);
   b += k.cap_nee * (sizeof(MergeRec) + sizeof(int)) + 2 * ((size_t)k.table + 1) * sizeof(int);
-  b += scan_scratch_ints((size_t)k.table + 1) * sizeof(int) + k.P * 3 * sizeof(double);
+  b += scan_scratch_ints((size_t)k.table + 1) * sizeof(int) + k.P * 3 * (sizeof(double) + sizeof(float));
   b += cfg->keep_split ? k.P * 12 * sizeof(double) : 0;
   b += k.cap_nee * sizeof(ShadowRay) + group_counter_ints() * sizeof(int);
   const size_t nt = (size_t)n_tri, ns = (size_t)n_sph, nl = (size_t)n_lights, np = nt + ns;
@@ -175,6 +175,7 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
        dalloc(&c->bucket_count, (size_t)t + 1) == cudaSuccess &&
        dalloc(&c->bucket_start, (size_t)t + 1) == cudaSuccess &&
        dalloc(&c->scan_scratch.data, c->scan_scratch.n) == cudaSuccess && dalloc(&c->accum, P * 3) == cudaSuccess &&
+       dalloc(&c->frame, P * 3) == cudaSuccess &&
        (!cfg->keep_split || dalloc(&c->split, P * 12) == cudaSuccess);
   ok = ok && dalloc(&c->shadow_rays, c->cap_nee) == cudaSuccess &&
        dalloc(&c->group_counters, group_counter_ints()) == cudaSuccess;
@@ -183,6 +184,7 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
   for (int k = 0; k < 2 && ok; ++k)
     ok = cudaEventCreateWithFlags(&c->ev_pass1[k], cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&c->ev_pass23[k], cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&c->ev_frame, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     neb_destroy(c);
     return NEB_ERR_OOM;
@@ -213,7 +215,8 @@ extern "C" void neb_destroy(neb_ctx* c) {
   }
   cudaFree(c->phq[0]); cudaFree(c->phq[1]); cudaFree(c->hits); cudaFree(c->hits_ph); cudaFree(c->mrec);
   cudaFree(c->vert_bucket); cudaFree(c->bucket_count); cudaFree(c->bucket_start); cudaFree(c->scan_scratch.data);
-  cudaFree(c->accum); cudaFree(c->split); cudaFree(c->counters);
+  cudaFree(c->accum); cudaFree(c->frame); cudaFree(c->split); cudaFree(c->counters);
+  if (c->ev_frame) cudaEventDestroy(c->ev_frame);
   cudaFree(c->shadow_rays); cudaFree(c->group_counters);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
@@ -442,6 +445,28 @@ extern "C" int neb_iterate(neb_ctx* c, int n_iterations) {
     if (rc != NEB_OK) return rc;
   }
   return n_iterations > 0 ? join(c) : NEB_OK;
+}
+
+extern "C" int neb_iterate_read(neb_ctx* c, int n_iterations, float* rgb_host) {
+  if (!c || n_iterations < 0 || (n_iterations > 0 && !rgb_host)) return NEB_ERR_ARG;
+  if (!c->bvh_ready) return fail(c, NEB_ERR_ARG, "neb_iterate_read: call neb_scene_upload and neb_build_bvh first");
+  const size_t bytes = sizeof(float) * 3 * (size_t)c->P;
+  for (int i = 0; i < n_iterations; ++i) {
+    int rc = iterate_one(c);
+    if (rc != NEB_OK) return rc;
+    // the frame of this iteration follows its passes 2-3 on their stream, so
+    // pass 1 of the next iteration is not held back by it
+    cudaStream_t st2 = c->profiling ? c->stream : c->stream_b;
+    cudaError_t e = launch_resolve(c->accum, c->P, c->iteration, c->frame, st2);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rgb_host, c->frame, bytes, cudaMemcpyDeviceToHost, st2);
+    if (e != cudaSuccess) return fail(c, NEB_ERR_CUDA, "neb_iterate_read", e);
+  }
+  if (n_iterations > 0 && !c->profiling) {
+    cudaError_t e = cudaEventRecord(c->ev_frame, c->stream_b);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_frame, 0);
+    if (e != cudaSuccess) return fail(c, NEB_ERR_CUDA, "neb_iterate_read", e);
+  }
+  return NEB_OK;
 }
 
 extern "C" int neb_iterate_batch(neb_ctx* const* ctxs, int n, int n_iterations) {

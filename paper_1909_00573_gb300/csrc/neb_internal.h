@@ -181,6 +181,8 @@ struct neb_ctx {
   uint32_t table_size = 0;
   neb::Scratch scan_scratch;
   double* accum = nullptr;
+  float* frame = nullptr;             // resolved image staged for neb_iterate_read
+  cudaEvent_t ev_frame = nullptr;     // after the last frame copy of neb_iterate_read
   double* split = nullptr;
   neb::DevCounters* counters = nullptr;  // two sets, one per slot
   // passes 2-3 run on stream_b, overlapped with the next iteration's pass 1

@@ -27,7 +27,8 @@ EXPORTS = ["neb_create", "neb_destroy", "neb_last_error", "neb_scene_upload", "n
            "neb_octree_create", "neb_octree_destroy", "neb_octree_set_iteration", "neb_octree_insert",
            "neb_octree_density", "neb_octree_read", "neb_octree_load", "neb_count_neighbours",
            "neb_count_neighbours_noalloc", "neb_iterate_batch", "neb_job_device_bytes", "neb_get_tuning",
-           "neb_set_tuning", "neb_autotune", "neb_density_estimators", "neb_read_nee_vertices"]
+           "neb_set_tuning", "neb_autotune", "neb_density_estimators", "neb_read_nee_vertices",
+           "neb_iterate_read"]
 NOALLOC_MAX_POINTS = 1 << 18
 
 
@@ -91,6 +92,7 @@ def lib():
             "neb_scene_upload": ([vp, vp, vp, C.c_int, vp, vp, C.c_int, vp, C.c_int, vp], C.c_int),
             "neb_build_bvh": ([vp], C.c_int),
             "neb_iterate": ([vp, C.c_int], C.c_int),
+            "neb_iterate_read": ([vp, C.c_int, vp], C.c_int),
             "neb_resolve": ([vp, vp, C.c_int], C.c_int),
             "neb_read_accum": ([vp, vp], C.c_int),
             "neb_read_split": ([vp, vp], C.c_int),
@@ -186,6 +188,12 @@ class Context:
 
     def iterate(self, n=1):
         self._c(lib().neb_iterate(self.h, int(n)))
+
+    def iterate_read(self, n, rgb_host_ptr):
+        """n iterations, the running image copied to host memory at rgb_host_ptr
+        ([H][W][3] float32, preferably pinned) after each; asynchronous: read
+        the buffer only after synchronising the context stream."""
+        self._c(lib().neb_iterate_read(self.h, int(n), vp(rgb_host_ptr)))
 
     def read_nee_vertices(self):
         n = C.c_int(0)

@@ -439,6 +439,35 @@ def test_density_only_where_used_changes_no_result(neb, name, lp):
     assert a0.sum() > 0
 
 
+def test_iterate_read_frames_equal_resolve(neb):
+    """neb_iterate_read leaves in host memory the image of all iterations so
+    far after every call, equal to neb_resolve on the same context and (with
+    the deterministic octree) to a context that ran neb_iterate, up to the
+    order of the FP64 atomic additions."""
+    import torch
+    from paper_1909_00573_gb300 import scenes
+    s, rc = scenes.workload("tiny_room")
+    rc.octree_mode = 1
+    frame = torch.empty((rc.height, rc.width, 3), dtype=torch.float32).pin_memory()
+    a = neb.Context(neb.make_config(rc))
+    b = neb.Context(neb.make_config(rc))
+    for ctx in (a, b):
+        ctx.scene_upload(s)
+        ctx.build_bvh()
+    for n in (1, 3):
+        a.iterate_read(n, frame.data_ptr())
+        b.iterate(n)
+        torch.cuda.synchronize()
+        got = frame.numpy().copy()
+        ra, rb = a.resolve(), b.resolve()
+        assert np.array_equal(got, ra)
+        np.testing.assert_allclose(ra, rb, rtol=1e-5, atol=1e-6 * float(np.abs(rb).max()))
+        assert a.stats()["iterations"] == b.stats()["iterations"]
+    assert got.sum() > 0
+    a.close()
+    b.close()
+
+
 def test_packed_photon_records_error(neb, oracle):
     """Photon queue records packed to 48 bytes (FP16 flux mantissas, 16-bit
     octahedral direction) against 64-byte FP32 records and the oracle, on the
