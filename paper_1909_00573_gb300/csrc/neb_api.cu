@@ -252,12 +252,91 @@ static float3 hcross(float3 a, float3 b) {
 }
 static float3 hsub(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
 
+// Floats as ints that order like the floats (for atomicMin / atomicMax).
+__host__ __device__ static inline int ordered_int(float f) {
+  int i;
+  memcpy(&i, &f, sizeof(i));
+  return i >= 0 ? i : i ^ 0x7fffffff;
+}
+static float ordered_float(int i) {
+  int j = i >= 0 ? i : i ^ 0x7fffffff;
+  float f;
+  memcpy(&f, &j, sizeof(f));
+  return f;
+}
+
+namespace neb {
+__global__ void k_bounds_init(int* b) {
+  for (int k = 0; k < 3; ++k) {
+    b[k] = 0x7fffffff;
+    b[3 + k] = (int)0x80000000;
+  }
+}
+
+// Caller triangles [nt][3][3] + materials -> the v0 / v1 / v2 float4 arrays
+// (material index in v0.w), and the bounds of all vertices (ordered ints).
+__global__ void k_pack_triangles(const float* __restrict__ tri, const uint32_t* __restrict__ mat, int nt,
+                                 float4* v0, float4* v1, float4* v2, int* bounds) {
+  float lo[3] = {3.402823466e+38f, 3.402823466e+38f, 3.402823466e+38f};
+  float hi[3] = {-3.402823466e+38f, -3.402823466e+38f, -3.402823466e+38f};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += gridDim.x * blockDim.x) {
+    const float* t = tri + 9 * (size_t)i;
+    float v[9];
+    for (int k = 0; k < 9; ++k) v[k] = t[k];
+    v0[i] = make_float4(v[0], v[1], v[2], __int_as_float((int)mat[i]));
+    v1[i] = make_float4(v[3], v[4], v[5], 0.0f);
+    v2[i] = make_float4(v[6], v[7], v[8], 0.0f);
+    for (int q = 0; q < 3; ++q)
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = fminf(lo[k], v[3 * q + k]);
+        hi[k] = fmaxf(hi[k], v[3 * q + k]);
+      }
+  }
+  for (int k = 0; k < 3; ++k)
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+      hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+    }
+  if ((threadIdx.x & 31) == 0)
+    for (int k = 0; k < 3; ++k) {
+      atomicMin(bounds + k, ordered_int(lo[k]));
+      atomicMax(bounds + 3 + k, ordered_int(hi[k]));
+    }
+}
+
+__global__ void k_mark_lights(const int* __restrict__ light_prim, int nl, int* prim_light) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += gridDim.x * blockDim.x)
+    prim_light[light_prim[i]] = i;
+}
+
+static void launch_pack_triangles(const float* tri, const uint32_t* mat, int nt, float4* v0, float4* v1, float4* v2,
+                                  int* bounds, cudaStream_t st) {
+  k_bounds_init<<<1, 1, 0, st>>>(bounds);
+  int blocks = (nt + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_pack_triangles<<<blocks, 256, 0, st>>>(tri, mat, nt, v0, v1, v2, bounds);
+}
+
+static void launch_mark_lights(const int* light_prim, int nl, int* prim_light, cudaStream_t st) {
+  int blocks = (nl + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_mark_lights<<<blocks, 256, 0, st>>>(light_prim, nl, prim_light);
+}
+}  // namespace neb
+
 extern "C" int neb_scene_upload(neb_ctx* c, const float* tri, const uint32_t* tri_mat, int nt, const float* sph,
                                 const uint32_t* sph_mat, int ns, const float* mats, int nm, const float* cam) {
   if (!c) return NEB_ERR_ARG;
   if (nt < 0 || ns < 0 || nm < 1 || !mats || !cam || (nt > 0 && (!tri || !tri_mat)) ||
       (ns > 0 && (!sph || !sph_mat)) || nt + ns < 1)
     return fail(c, NEB_ERR_ARG, "neb_scene_upload: bad arguments");
+  // per-material mean emission; the material check and the light list take
+  // one pass over the primitives' material indices
+  std::vector<double> mat_le(nm);
+  for (int m = 0; m < nm; ++m) {
+    const float* e = mats + 12 * (size_t)m + 4;
+    mat_le[m] = ((double)e[0] + (double)e[1] + (double)e[2]) / 3.0;
+  }
   for (int i = 0; i < nt; ++i)
     if (tri_mat[i] >= (uint32_t)nm) return fail(c, NEB_ERR_ARG, "neb_scene_upload: triangle material out of range");
   for (int i = 0; i < ns; ++i)
@@ -267,15 +346,9 @@ extern "C" int neb_scene_upload(neb_ctx* c, const float* tri, const uint32_t* tr
   c->nt = nt;
   c->ns = ns;
   c->nm = nm;
-  // ---- host-side repacking into the device layouts
-  std::vector<float4> v0(nt), v1(nt), v2(nt), sp(ns), mt(3 * (size_t)nm);
+  // ---- host-side repacking of the small arrays (triangles are repacked on the device)
+  std::vector<float4> sp(ns), mt(3 * (size_t)nm);
   std::vector<int> smat(ns);
-  for (int i = 0; i < nt; ++i) {
-    const float* t = tri + 9 * (size_t)i;
-    v0[i] = make_float4(t[0], t[1], t[2], i2f((int)tri_mat[i]));
-    v1[i] = make_float4(t[3], t[4], t[5], 0.0f);
-    v2[i] = make_float4(t[6], t[7], t[8], 0.0f);
-  }
   for (int i = 0; i < ns; ++i) {
     sp[i] = make_float4(sph[4 * i], sph[4 * i + 1], sph[4 * i + 2], sph[4 * i + 3]);
     smat[i] = (int)sph_mat[i];
@@ -288,14 +361,13 @@ extern "C" int neb_scene_upload(neb_ctx* c, const float* tri, const uint32_t* tr
   }
   // ---- light list: emissive triangles in index order, then emissive spheres
   int np = nt + ns;
-  std::vector<int> prim_light(np, -1), light_prim;
+  std::vector<int> light_prim;
   std::vector<double> power;
   std::vector<float> inv_area;
   const double PI = 3.14159265358979323846;
   for (int p = 0; p < np; ++p) {
     int m = p < nt ? (int)tri_mat[p] : (int)sph_mat[p - nt];
-    const float* e = mats + 12 * (size_t)m + 4;
-    double le = ((double)e[0] + (double)e[1] + (double)e[2]) / 3.0;
+    double le = mat_le[m];
     if (le <= 0.0) continue;
     if (p < nt) {
       const float* t = tri + 9 * (size_t)p;
@@ -310,7 +382,6 @@ extern "C" int neb_scene_upload(neb_ctx* c, const float* tri, const uint32_t* tr
       power.push_back(4.0 * PI * PI * R * R * le);
       inv_area.push_back((float)(1.0 / (2.0 * PI * R * R)));
     }
-    prim_light[p] = (int)light_prim.size();
     light_prim.push_back(p);
   }
   int nl = (int)light_prim.size();
@@ -340,14 +411,8 @@ extern "C" int neb_scene_upload(neb_ctx* c, const float* tri, const uint32_t* tr
     while (!large.empty()) { aprob[large.back()] = 1.0f; large.pop_back(); }
     while (!small.empty()) { aprob[small.back()] = 1.0f; small.pop_back(); }
   }
-  // scene bounds
+  // scene bounds: spheres here, triangle vertices on the device (merged below)
   for (int k = 0; k < 3; ++k) { c->bmin[k] = 3.402823466e+38f; c->bmax[k] = -3.402823466e+38f; }
-  for (size_t i = 0; i < (size_t)nt * 3; ++i)
-    for (int k = 0; k < 3; ++k) {
-      float v = tri[i * 3 + k];
-      if (v < c->bmin[k]) c->bmin[k] = v;
-      if (v > c->bmax[k]) c->bmax[k] = v;
-    }
   for (int i = 0; i < ns; ++i)
     for (int k = 0; k < 3; ++k) {
       float ce = sph[4 * (size_t)i + k], r = sph[4 * (size_t)i + 3];
@@ -373,26 +438,41 @@ extern "C" int neb_scene_upload(neb_ctx* c, const float* tri, const uint32_t* tr
             dalloc(&c->prim_light, np) == cudaSuccess && dalloc(&c->light_prim, nl) == cudaSuccess &&
             dalloc(&c->light_psel, nl) == cudaSuccess && dalloc(&c->light_inv_area, nl) == cudaSuccess &&
             dalloc(&c->alias_prob, nl) == cudaSuccess && dalloc(&c->alias_idx, nl) == cudaSuccess;
-  c->oct = octree_params(c->bmin, c->bmax, c->cfg.octree_capacity, c->cfg.split_factor);
-  c->oct_cap = c->oct.capacity;
+  c->oct_cap = octree_params(c->bmin, c->bmax, c->cfg.octree_capacity, c->cfg.split_factor).capacity;
   ok = ok && dalloc(&c->oct_nodes, (size_t)c->oct_cap) == cudaSuccess && dalloc(&c->oct_state, 1) == cudaSuccess;
+  // the caller's triangle arrays, copied as they are and repacked on the device
+  float* d_tri = nullptr;
+  uint32_t* d_tmat = nullptr;
+  int* d_bounds = nullptr;
+  ok = ok && cudaMallocAsync(&d_tri, sizeof(float) * 9 * (size_t)(nt > 0 ? nt : 1), st) == cudaSuccess &&
+       cudaMallocAsync(&d_tmat, sizeof(uint32_t) * (size_t)(nt > 0 ? nt : 1), st) == cudaSuccess &&
+       cudaMallocAsync(&d_bounds, sizeof(int) * 6, st) == cudaSuccess;
   if (!ok) {
+    cudaFreeAsync(d_tri, st); cudaFreeAsync(d_tmat, st); cudaFreeAsync(d_bounds, st);
+    cudaStreamSynchronize(st);
+    cudaGetLastError();
     free_scene(c);
     return fail(c, NEB_ERR_OOM, "neb_scene_upload: device allocation failed");
   }
+  int hb[6];
   if (nt) {
-    cudaMemcpyAsync(c->tv0, v0.data(), sizeof(float4) * nt, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(c->tv1, v1.data(), sizeof(float4) * nt, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(c->tv2, v2.data(), sizeof(float4) * nt, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_tri, tri, sizeof(float) * 9 * (size_t)nt, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_tmat, tri_mat, sizeof(uint32_t) * (size_t)nt, cudaMemcpyHostToDevice, st);
+    launch_pack_triangles(d_tri, d_tmat, nt, c->tv0, c->tv1, c->tv2, d_bounds, st);
+    cudaMemcpyAsync(hb, d_bounds, sizeof(hb), cudaMemcpyDeviceToHost, st);
   }
+  cudaMemsetAsync(c->prim_light, 0xff, sizeof(int) * (size_t)np, st);  // -1: not a light
+  cudaFreeAsync(d_tri, st);
+  cudaFreeAsync(d_tmat, st);
+  cudaFreeAsync(d_bounds, st);
   if (ns) {
     cudaMemcpyAsync(c->sph, sp.data(), sizeof(float4) * ns, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(c->sph_mat, smat.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st);
   }
   cudaMemcpyAsync(c->mats, mt.data(), sizeof(float4) * 3 * nm, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(c->prim_light, prim_light.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st);
   if (nl) {
     cudaMemcpyAsync(c->light_prim, light_prim.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, st);
+    launch_mark_lights(c->light_prim, nl, c->prim_light, st);
     cudaMemcpyAsync(c->light_psel, psel.data(), sizeof(float) * nl, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(c->light_inv_area, inv_area.data(), sizeof(float) * nl, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(c->alias_prob, aprob.data(), sizeof(float) * nl, cudaMemcpyHostToDevice, st);
@@ -407,6 +487,13 @@ extern "C" int neb_scene_upload(neb_ctx* c, const float* tri, const uint32_t* tr
   c->launches = 0;
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(c, NEB_ERR_CUDA, "neb_scene_upload", e);
+  if (nt) {
+    for (int k = 0; k < 3; ++k) {
+      c->bmin[k] = fminf(c->bmin[k], ordered_float(hb[k]));
+      c->bmax[k] = fmaxf(c->bmax[k], ordered_float(hb[3 + k]));
+    }
+  }
+  c->oct = octree_params(c->bmin, c->bmax, c->cfg.octree_capacity, c->cfg.split_factor);
   c->scene_ready = true;
   return NEB_OK;
 }
