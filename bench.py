@@ -586,7 +586,9 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx2.scene_upload(hs)
+        t_up = time.perf_counter()
         ctx2.build_bvh()
+        t_bvh = time.perf_counter()
         ctx2.iterate_read(args.steps, img.data_ptr())   # every iteration's image copied to pinned host memory
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
@@ -594,6 +596,7 @@ def main():
         ctx2.close()
         e2e = {"value": job_value(world, P, args.steps, t_e2e), "unit": METRIC,
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(img.numel() * 4),
+               "upload_ms": 1000 * (t_up - t0), "bvh_ms": 1000 * (t_bvh - t_up),
                "note": "scene upload + BVH build once per job (h2d amortised over the steps); after every "
                        "iteration its image is resolved and copied to pinned host memory (neb_iterate_read, "
                        "asynchronous: the copies overlap the next iteration)"}
