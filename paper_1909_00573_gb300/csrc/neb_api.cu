@@ -59,12 +59,14 @@ static void free_scene(neb_ctx* c) {
   cudaFree(c->tv0); cudaFree(c->tv1); cudaFree(c->tv2); cudaFree(c->sph); cudaFree(c->mats); cudaFree(c->sph_mat);
   cudaFree(c->prim_light); cudaFree(c->light_prim); cudaFree(c->alias_idx); cudaFree(c->light_psel);
   cudaFree(c->light_inv_area); cudaFree(c->alias_prob); cudaFree(c->nodes);
+  cudaFree(c->node_parent); cudaFree(c->prim_owner);
   cudaFree(c->oct_nodes);
   cudaFree(c->oct_state);
   c->tv0 = c->tv1 = c->tv2 = c->sph = c->mats = nullptr;
   c->sph_mat = c->prim_light = c->light_prim = c->alias_idx = nullptr;
   c->light_psel = c->light_inv_area = c->alias_prob = nullptr;
   c->nodes = nullptr;
+  c->node_parent = c->prim_owner = nullptr;
   c->oct_nodes = nullptr;
   c->oct_state = nullptr;
   c->scene_ready = c->bvh_ready = false;
@@ -109,18 +111,18 @@ extern "C" int neb_job_device_bytes(const neb_config* cfg, int n_tri, int n_sph,
   const size_t D = (size_t)cfg->max_depth, nee_rows = k.P * (D > 1 ? D - 1 : 1);
   uint64_t b = 0;
   b += 3 * k.P * sizeof(CamRay) + 2 * sizeof(DevCounters);
-  b += 2 * (7 * k.cap_nee * sizeof(float4) + k.cap_nee * sizeof(int) + k.cap_rh * sizeof(RHEvent) +
+  b += 2 * (7 * k.cap_nee * sizeof(float4) + 2 * k.cap_nee * sizeof(int) + k.cap_rh * sizeof(RHEvent) +
             (cfg->octree_mode == 1 ? nee_rows * sizeof(int) : 0));
   b += 2 * k.cap_ph * sizeof(PhotonRay) + k.cap_cam * sizeof(int2) + k.cap_ph * sizeof(int2);
   b += k.cap_nee * (sizeof(MergeRec) + sizeof(int)) + 2 * ((size_t)k.table + 1) * sizeof(int);
   b += scan_scratch_ints((size_t)k.table + 1) * sizeof(int) + k.P * 3 * (sizeof(double) + sizeof(float));
   b += cfg->keep_split ? k.P * 12 * sizeof(double) : 0;
-  b += k.cap_nee * sizeof(ShadowRay) + group_counter_ints() * sizeof(int);
+  b += 2 * k.cap_nee * (sizeof(ShadowRay) + sizeof(int)) + group_counter_ints() * sizeof(int);
   const size_t nt = (size_t)n_tri, ns = (size_t)n_sph, nl = (size_t)n_lights, np = nt + ns;
   b += 3 * nt * sizeof(float4) + ns * (sizeof(float4) + sizeof(int)) + 3 * (size_t)n_mat * sizeof(float4);
   b += np * sizeof(int) + nl * (2 * sizeof(int) + 3 * sizeof(float));
   b += (1 + (((size_t)cfg->octree_capacity + 7) & ~(size_t)7)) * sizeof(int) + sizeof(OctreeState);
-  b += (np > 1 ? np - 1 : 1) * sizeof(BVH4Node);
+  b += (np > 1 ? np - 1 : 1) * (sizeof(BVH4Node) + sizeof(int)) + np * sizeof(int);
   *out = b;
   return NEB_OK;
 }
@@ -166,6 +168,7 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
          dalloc(&sl.nv.wo, c->cap_nee) == cudaSuccess && dalloc(&sl.nv.tau, c->cap_nee) == cudaSuccess &&
          dalloc(&sl.nv.err, c->cap_nee) == cudaSuccess && dalloc(&sl.nv.ldir, c->cap_nee) == cudaSuccess &&
          dalloc(&sl.nv.dE, c->cap_nee) == cudaSuccess && dalloc(&sl.nv.lit, c->cap_nee) == cudaSuccess &&
+         dalloc(&sl.nv.prim, c->cap_nee) == cudaSuccess &&
          dalloc(&sl.rh, c->cap_rh) == cudaSuccess &&
          (cfg->octree_mode != 1 || dalloc(&sl.slot_map, P * (D > 1 ? D - 1 : 1)) == cudaSuccess);
   }
@@ -177,7 +180,8 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
        dalloc(&c->scan_scratch.data, c->scan_scratch.n) == cudaSuccess && dalloc(&c->accum, P * 3) == cudaSuccess &&
        dalloc(&c->frame, P * 3) == cudaSuccess &&
        (!cfg->keep_split || dalloc(&c->split, P * 12) == cudaSuccess);
-  ok = ok && dalloc(&c->shadow_rays, c->cap_nee) == cudaSuccess &&
+  ok = ok && dalloc(&c->shadow_rays, c->cap_nee) == cudaSuccess && dalloc(&c->shadow_start, c->cap_nee) == cudaSuccess &&
+       dalloc(&c->shadow_rays_b, c->cap_nee) == cudaSuccess && dalloc(&c->shadow_start_b, c->cap_nee) == cudaSuccess &&
        dalloc(&c->group_counters, group_counter_ints()) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&c->stream_b, cudaStreamNonBlocking) == cudaSuccess &&
        cudaStreamCreateWithFlags(&c->stream_cap, cudaStreamNonBlocking) == cudaSuccess;
@@ -211,13 +215,14 @@ extern "C" void neb_destroy(neb_ctx* c) {
   if (c->stream_b) cudaStreamSynchronize(c->stream_b);
   for (IterSlot& sl : c->slots) {
     cudaFree(sl.nv.pos); cudaFree(sl.nv.nrm); cudaFree(sl.nv.wo); cudaFree(sl.nv.tau); cudaFree(sl.nv.err);
-    cudaFree(sl.nv.ldir); cudaFree(sl.nv.dE); cudaFree(sl.nv.lit); cudaFree(sl.rh); cudaFree(sl.slot_map);
+    cudaFree(sl.nv.ldir); cudaFree(sl.nv.dE); cudaFree(sl.nv.lit); cudaFree(sl.nv.prim); cudaFree(sl.rh); cudaFree(sl.slot_map);
   }
   cudaFree(c->phq[0]); cudaFree(c->phq[1]); cudaFree(c->hits); cudaFree(c->hits_ph); cudaFree(c->mrec);
   cudaFree(c->vert_bucket); cudaFree(c->bucket_count); cudaFree(c->bucket_start); cudaFree(c->scan_scratch.data);
   cudaFree(c->accum); cudaFree(c->frame); cudaFree(c->split); cudaFree(c->counters);
   if (c->ev_frame) cudaEventDestroy(c->ev_frame);
-  cudaFree(c->shadow_rays); cudaFree(c->group_counters);
+  cudaFree(c->shadow_rays); cudaFree(c->shadow_start); cudaFree(c->shadow_rays_b); cudaFree(c->shadow_start_b);
+  cudaFree(c->group_counters);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
   for (int k = 0; k < 2; ++k) {

@@ -401,8 +401,9 @@ static cudaError_t ploc_build(const SceneView& s, int n, const int* sorted_prim,
 // the largest surface area until it has four children or only leaves.  The
 // children that stay inner become the next level's work; siblings get
 // consecutive node indices.
+// parent / owner (or nullptr): parent node of each new node, node holding each primitive leaf
 __global__ void k_collapse4(const BVHNode* __restrict__ bin, const int2* __restrict__ work, int n_work,
-                            BVH4Node* out, int2* next_work, int* counters) {
+                            BVH4Node* out, int2* next_work, int* counters, int* parent, int* owner) {
   for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < n_work; w += gridDim.x * blockDim.x) {
     int2 it = work[w];
     BVHNode b = bin[it.x];
@@ -447,9 +448,11 @@ __global__ void k_collapse4(const BVHNode* __restrict__ bin, const int2* __restr
         if (ref[i] >= 0) {
           R[i] = base + j;
           next_work[wb + j] = make_int2(ref[i], base + j);
+          if (parent) parent[base + j] = it.y;
           ++j;
         } else {
           R[i] = ref[i];
+          if (owner) owner[~ref[i]] = it.y;
         }
       } else {
         L[0][i] = L[1][i] = L[2][i] = 0.0f;
@@ -470,7 +473,8 @@ __global__ void k_collapse4(const BVHNode* __restrict__ bin, const int2* __restr
   }
 }
 
-static cudaError_t collapse4(const BVHNode* bin, int n_bin, BVH4Node* out, cudaStream_t st, int* n_out) {
+static cudaError_t collapse4(const BVHNode* bin, int n_bin, BVH4Node* out, cudaStream_t st, int* n_out, int* parent,
+                             int* owner) {
   int2 *w0 = nullptr, *w1 = nullptr;
   int* cnt = nullptr;
   cudaError_t e = cudaSuccess;
@@ -488,7 +492,7 @@ static cudaError_t collapse4(const BVHNode* bin, int n_bin, BVH4Node* out, cudaS
   while (n_work > 0) {
     int blocks = (n_work + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    k_collapse4<<<blocks, 256, 0, st>>>(bin, w0, n_work, out, w1, cnt);
+    k_collapse4<<<blocks, 256, 0, st>>>(bin, w0, n_work, out, w1, cnt, parent, owner);
     cudaMemcpyAsync(h, cnt, 8, cudaMemcpyDeviceToHost, st);
     cudaMemsetAsync(cnt + 1, 0, 4, st);
     e = cudaStreamSynchronize(st);
@@ -504,18 +508,33 @@ static cudaError_t collapse4(const BVHNode* bin, int n_bin, BVH4Node* out, cudaS
 cudaError_t build_bvh(neb_ctx* c) {
   int n = c->nt + c->ns;
   if (c->nodes) { cudaFree(c->nodes); c->nodes = nullptr; }
+  if (c->node_parent) { cudaFree(c->node_parent); c->node_parent = nullptr; }
+  if (c->prim_owner) { cudaFree(c->prim_owner); c->prim_owner = nullptr; }
   if (n == 0) return cudaSuccess;
-  return build_bvh4(scene_view(c), n, c->cfg.bvh_builder, c->stream, &c->nodes, &c->n_nodes4);
+  return build_bvh4(scene_view(c), n, c->cfg.bvh_builder, c->stream, &c->nodes, &c->n_nodes4, &c->node_parent,
+                    &c->prim_owner);
 }
 
-cudaError_t build_bvh4(const SceneView& s, int n, int builder, cudaStream_t st, BVH4Node** nodes_out, int* n4_out) {
+cudaError_t build_bvh4(const SceneView& s, int n, int builder, cudaStream_t st, BVH4Node** nodes_out, int* n4_out,
+                       int** parent_out, int** owner_out) {
   BVH4Node* nodes = nullptr;
   cudaError_t e = cudaMalloc(&nodes, sizeof(BVH4Node) * (size_t)(n > 1 ? n - 1 : 1));
   if (e != cudaSuccess) return e;
   *nodes_out = nodes;
   *n4_out = 1;
+  int *parent = nullptr, *owner = nullptr;
+  if (parent_out && owner_out) {
+    e = cudaMalloc(&parent, sizeof(int) * (size_t)(n > 1 ? n - 1 : 1));
+    if (e != cudaSuccess) return e;
+    *parent_out = parent;
+    e = cudaMalloc(&owner, sizeof(int) * (size_t)n);
+    if (e != cudaSuccess) return e;
+    *owner_out = owner;
+    cudaMemsetAsync(parent, 0xff, sizeof(int), st);  // the root has no parent
+  }
   if (n == 1) {
     k_single_leaf<<<1, 1, 0, st>>>(s, nodes);
+    if (owner) cudaMemsetAsync(owner, 0, sizeof(int), st);
     return cudaGetLastError();
   }
   // the binary tree (LBVH or PLOC) is built first and collapsed into the 4-wide one
@@ -569,7 +588,7 @@ cudaError_t build_bvh4(const SceneView& s, int n, int builder, cudaStream_t st, 
     }
     if (e == cudaSuccess) e = cudaGetLastError();
     int n4 = 0;
-    if (e == cudaSuccess) e = collapse4(bin, n - 1, nodes, st, &n4);
+    if (e == cudaSuccess) e = collapse4(bin, n - 1, nodes, st, &n4, parent, owner);
     *n4_out = n4;
   } else {
     e = cudaErrorMemoryAllocation;

@@ -73,6 +73,7 @@ struct NeeStore {
   float4* dE;    // unoccluded irradiance rgb (zero if back-facing; read only for vertices of the lit list),
                  // w: the light point's light-photon pdf
   int* lit;      // ids of the vertices whose shadow ray reached the light (DevCounters::lit_count of them)
+  int* prim;     // primitive the vertex lies on
 };
 enum { NV_DELTA = 1, NV_MERGEABLE = 2, NV_SHADOW = 4 };
 enum { NV_MAT_MASK = (1 << 20) - 1, NV_K_SHIFT = 20, NV_FLAG_SHIFT = 26 };
@@ -86,6 +87,7 @@ struct DevCounters {
   int ph_count[2];
   int merge_count;
   int lit_count;
+  int shadow_count_b;  // shadow rays left for the second walk (no blocker near the origin)
   uint32_t status;
   unsigned long long camera_rays, nee_vertices, shadow_rays, photons, photon_hits;
   unsigned long long merge_tests, merges, random_hits, octree_inserts, octree_queries;
@@ -154,6 +156,8 @@ struct neb_ctx {
 
   // BVH (4-wide)
   neb::BVH4Node* nodes = nullptr;
+  int* node_parent = nullptr;  // parent of each 4-wide node, -1 at the root
+  int* prim_owner = nullptr;   // 4-wide node holding each primitive as a leaf child
   int n_nodes4 = 0;
   bool bvh_ready = false;
 
@@ -171,6 +175,9 @@ struct neb_ctx {
   int2* hits = nullptr;     // closest hits of the camera ray queue (pass 1)
   int2* hits_ph = nullptr;  // closest hits of the photon ray queue (pass 3)
   neb::ShadowRay* shadow_rays = nullptr;  // shadow rays grouped by light
+  int* shadow_start = nullptr;            // per shadow ray: the subtree walked first (near its origin)
+  neb::ShadowRay* shadow_rays_b = nullptr;  // rays the first walk did not settle, for the second
+  int* shadow_start_b = nullptr;
   int* group_counters = nullptr;  // ray grouping of pass 1: group counts, then cursors
   neb_tuning tune{1, 3, 2, 2, 8};  // launch settings (neb_set_tuning / neb_autotune)
   neb::MergeRec* mrec = nullptr;
@@ -222,7 +229,10 @@ cudaError_t build_bvh(neb_ctx* c);
 // 4-wide BVH over the n primitives of view s (triangles, then spheres; a
 // sphere of radius 0 is a point) into a new device array *nodes_out;
 // builder 0 PLOC, 1 Karras.  Synchronises st.
-cudaError_t build_bvh4(const SceneView& s, int n, int builder, cudaStream_t st, BVH4Node** nodes_out, int* n4_out);
+// parent_out / owner_out (or nullptr): the parent of every 4-wide node (-1 at
+// the root) and the node holding each primitive as a leaf child, allocated here
+cudaError_t build_bvh4(const SceneView& s, int n, int builder, cudaStream_t st, BVH4Node** nodes_out, int* n4_out,
+                       int** parent_out = nullptr, int** owner_out = nullptr);
 cudaError_t launch_trace_debug(const SceneView& s, const float* d_rays, int n, int* d_prim, float* d_t,
                                uint32_t* d_status, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* d_ctr, int n, uint2 key, uint32_t* d_out, cudaStream_t st);

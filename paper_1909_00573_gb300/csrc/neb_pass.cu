@@ -151,6 +151,7 @@ __global__ void k_begin(DevCounters* cnt) {
   cnt->ph_count[1] = 0;
   cnt->merge_count = 0;
   cnt->lit_count = 0;
+  cnt->shadow_count_b = 0;
 }
 
 __global__ void k_camera(IterParams ip, CameraParams cam, CamRay* q, DevCounters* cnt) {
@@ -203,6 +204,7 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
     float ldist = 0.0f, g_y = 0.0f;
     bool shadow = false;
     float nee_p_lp = 0.0f;
+    int hit_prim = -1;
     if (valid) {
       ry = in[i];
       rays = 1;
@@ -212,6 +214,7 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
       RayPre r = make_ray(xyz(ry.o), d);
       int2 hh = hits[i];
       int prim = hh.x;
+      hit_prim = prim;
       float t = __int_as_float(hh.y);
       if (prim >= 0) {
         hit_point(s, r, prim, t, p, err, n);
@@ -296,6 +299,7 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
       const int kmerge = ip.n_lp > 0 ? ip.D - 1 : ip.D - 2;
       int vflags = (delta ? NV_DELTA : 0) | ((!delta && k <= kmerge) ? NV_MERGEABLE : 0) | (shadow ? NV_SHADOW : 0);
       nv.pos[nid] = make_float4(p.x, p.y, p.z, Cfac);
+      nv.prim[nid] = hit_prim;
       nv.nrm[nid] = make_float4(n.x, n.y, n.z, __int_as_float(mat | (k << NV_K_SHIFT) | (vflags << NV_FLAG_SHIFT)));
       nv.wo[nid] = make_float4(-d.x, -d.y, -d.z, __int_as_float(pixel));
       nv.tau[nid] = make_float4(tau.x, tau.y, tau.z, g_y);
@@ -879,7 +883,7 @@ static long long enqueue_pass1(neb_ctx* c, int iteration, cudaStream_t st, Stage
   tm.end();
   tm.begin(STAGE_SHADOW);
   launch_trace_shadow(c, sl, st);
-  launches += 1;
+  launches += 2;
   tm.end();
   return launches;
 }

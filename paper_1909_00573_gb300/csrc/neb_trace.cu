@@ -16,7 +16,8 @@ namespace neb {
 
 constexpr int kTraceThreads = 256;
 constexpr int kRefill = 8;     // refill when at least this many lanes are idle
-constexpr int kSteps = 24;     // node steps between refill checks
+constexpr int kSteps = 24;     // node steps between refill checks (closest hit)
+constexpr int kShadowSteps = 10;  // the same for the any-hit walk
 constexpr int kIdle = -1, kDone = -2;
 
 // Traversal state.  Both walks run over the 4-wide BVH.  Closest-hit walks
@@ -31,6 +32,7 @@ struct Walk {
   float best_t;
   int npend;
   int pend[5];
+  int start, skip;  // any hit: the subtree walked first, and the subtree the second walk leaves out
 };
 
 __device__ __forceinline__ void walk_init(Walk& w) {
@@ -39,12 +41,14 @@ __device__ __forceinline__ void walk_init(Walk& w) {
   w.best = -1;
   w.best_t = FLT_MAX;
   w.npend = 0;
+  w.start = 0;
+  w.skip = -1;
 }
 
 // One inner-node step of the any-hit walk over the 4-wide tree: leaf children
 // whose box is hit are queued (at most four, so a walk steps with at most one
 // queued primitive), the first hit inner child is visited next and the others
-// are pushed.
+// are pushed; the child w.skip (a subtree already walked) is left out.
 __device__ __forceinline__ void inner_step4(const SceneView& s, const RayPre& r, float tbound, Walk& w, int* stack,
                                            uint32_t* status, uint32_t& visits) {
   Node4Oct n = load_node4_oct(s.nodes, w.node, r.oct);
@@ -53,7 +57,7 @@ __device__ __forceinline__ void inner_step4(const SceneView& s, const RayPre& r,
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     int ref = comp4i(n.ch, c);
-    if (ref == kEmptyChild) continue;
+    if (ref == kEmptyChild || ref == w.skip) continue;
     float tn;
     if (!child_hit(n, c, r, tbound, tn)) continue;
     if (ref < 0) {
@@ -292,9 +296,16 @@ __global__ void __launch_bounds__(kGroupThreads) k_shadow_count(NeeStore nv, con
   flush_counts(h, counts);
 }
 
+// Levels above the node that holds the origin's primitive: the subtree there
+// is walked first.
+constexpr int kShadowLift = 3;
+
 __global__ void __launch_bounds__(kGroupThreads) k_shadow_scatter(NeeStore nv, const DevCounters* cnt, int cap,
                                                                   GroupSpec g, int* __restrict__ cursors,
-                                                                  ShadowRay* __restrict__ rays) {
+                                                                  ShadowRay* __restrict__ rays,
+                                                                  const int* __restrict__ parent,
+                                                                  const int* __restrict__ owner,
+                                                                  int* __restrict__ start, int n_nodes) {
   __shared__ int h[kGroups];
   clear_hist(h);
   __syncthreads();
@@ -315,6 +326,9 @@ __global__ void __launch_bounds__(kGroupThreads) k_shadow_scatter(NeeStore nv, c
     sr.o = make_float4(o.x, o.y, o.z, ee.w * (1.0f - 1e-4f));
     sr.d = make_float4(ldir.x, ldir.y, ldir.z, __int_as_float(i));
     rays[slot] = sr;
+    int nd = __ldg(owner + nv.prim[i]);
+    for (int l = 0; l < kShadowLift && nd > 0 && nd < n_nodes; ++l) nd = __ldg(parent + nd);
+    start[slot] = nd > 0 && nd < n_nodes ? nd : 0;
   }
 }
 
@@ -354,11 +368,23 @@ __global__ void __launch_bounds__(kGroupThreads) k_cam_group_scatter(const CamRa
 
 // Shadow rays (any hit with tmax = (1 - 1e-4) dist from the offset origin):
 // the NEE vertices whose ray reaches the light are appended to the lit list,
-// the only record of visibility that passes 2-3 read.
+// the only record of visibility that passes 2-3 read.  Most shadow rays are
+// blocked, often by geometry next to their origin (the far side of the same
+// building), so there are two walks.  Phase 0 walks each ray through the
+// subtree a few levels above the node that holds its origin's primitive;
+// rays with no blocker there (and a subtree short of the whole tree) are
+// appended to a second queue.  Phase 1 walks those from the root, leaving
+// that subtree out.  Every leaf is tested once at most and the answer is that
+// of one walk from the root; splitting the walks keeps walks of similar
+// length together in a warp.
 __global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, NeeStore nv,
-                                                                const ShadowRay* __restrict__ srays, int cap,
-                                                                int* __restrict__ fetch, DevCounters* cnt) {
-  const int count = min(cnt->shadow_count, cap);
+                                                                const ShadowRay* __restrict__ srays,
+                                                                const int* __restrict__ sstart,
+                                                                const int* __restrict__ count_ptr, int cap,
+                                                                int* __restrict__ fetch, DevCounters* cnt, int phase,
+                                                                ShadowRay* __restrict__ rays_b,
+                                                                int* __restrict__ start_b) {
+  const int count = min(*count_ptr, cap);
   int ray = kIdle;  // NEE id of the lane's shadow ray
   RayPre r;
   Walk w;
@@ -372,11 +398,15 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, Nee
     int lit0_id = 0;
     if (ray == kIdle && nr >= 0) {
       float4 so = __ldg(&srays[nr].o), sd = __ldg(&srays[nr].d);
+      const int first = __ldg(sstart + nr);
       nr = __float_as_int(sd.w);
       r = make_ray(xyz(so), xyz(sd));
       tmax = so.w;
       walk_init(w);
-      ++rays;
+      w.start = first;
+      w.node = phase == 0 ? first : 0;
+      w.skip = phase == 0 ? -1 : first;
+      if (phase == 0) ++rays;
       if (no_geometry) {  // nothing can block it
         lit0 = true;
         lit0_id = nr;
@@ -389,12 +419,12 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, Nee
     }
     ray = nr;
     if (__all_sync(0xffffffffu, ray == kDone)) break;
-    for (int step = 0; step < kSteps; ++step) {
+    for (int step = 0; step < kShadowSteps; ++step) {
       if (ray >= 0 && w.node >= 0 && w.npend <= 1) inner_step4(s, r, tmax, w, stack, &cnt->status, visits);
       bool ready = ray < 0 || w.npend >= 2 || w.node < 0;
       if (__all_sync(0xffffffffu, ready)) {
-        bool lit = false;
-        int lit_id = 0;
+        bool lit = false, defer = false;
+        int id = 0;
         if (ray >= 0) {
           bool hit = false;
           for (int q = 0; q < w.npend; ++q) {
@@ -404,13 +434,24 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, Nee
           }
           w.npend = 0;
           if (!hit && w.node < 0) {
-            lit = true;
-            lit_id = ray;
+            id = ray;
+            if (phase == 0 && w.start > 0) defer = true;  // the rest of the tree is still to walk
+            else lit = true;
           }
           if (hit || w.node < 0) ray = kIdle;
         }
         int slot = warp_append(&cnt->lit_count, lit, cap, &cnt->status);
-        if (slot >= 0) nv.lit[slot] = lit_id;
+        if (slot >= 0) nv.lit[slot] = id;
+        if (phase == 0) {
+          int b = warp_append(&cnt->shadow_count_b, defer, cap, &cnt->status);
+          if (b >= 0) {
+            ShadowRay sr;
+            sr.o = make_float4(r.o.x, r.o.y, r.o.z, tmax);
+            sr.d = make_float4(r.d.x, r.d.y, r.d.z, __int_as_float(id));
+            rays_b[b] = sr;
+            start_b[b] = w.start;
+          }
+        }
         if (__all_sync(0xffffffffu, ray < 0)) break;
       }
     }
@@ -473,16 +514,24 @@ cudaError_t launch_group_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st)
   k_shadow_count<<<group_blocks(c->cap_nee), kGroupThreads, 0, st>>>(sl.nv, sl.cnt, c->cap_nee, g, counts);
   k_group_scan<<<1, kScanThreads, 0, st>>>(counts, cursors, &sl.cnt->shadow_count);
   k_shadow_scatter<<<group_blocks(c->cap_nee), kGroupThreads, 0, st>>>(sl.nv, sl.cnt, c->cap_nee, g, cursors,
-                                                             c->shadow_rays);
+                                                             c->shadow_rays, c->node_parent, c->prim_owner,
+                                                             c->shadow_start, c->n_nodes4);
   return cudaGetLastError();
 }
 
 cudaError_t launch_trace_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st) {
   static const int shadow_blocks = trace_blocks(k_trace_shadow);
-  int* fetch = &sl.cnt->fetch[1];
+  const int blocks = capped_blocks(c->cap_nee, kTraceThreads, shadow_blocks);
+  int* fetch = &sl.cnt->fetch[1];   // phase 0
+  int* fetch_b = &sl.cnt->fetch[3];  // phase 1
   cudaMemsetAsync(fetch, 0, sizeof(int), st);
-  k_trace_shadow<<<capped_blocks(c->cap_nee, kTraceThreads, shadow_blocks), kTraceThreads, 0, st>>>(scene_view(c), sl.nv, c->shadow_rays, c->cap_nee, fetch,
-                                                           sl.cnt);
+  cudaMemsetAsync(fetch_b, 0, sizeof(int), st);
+  k_trace_shadow<<<blocks, kTraceThreads, 0, st>>>(scene_view(c), sl.nv, c->shadow_rays, c->shadow_start,
+                                                   &sl.cnt->shadow_count, c->cap_nee, fetch, sl.cnt, 0,
+                                                   c->shadow_rays_b, c->shadow_start_b);
+  k_trace_shadow<<<blocks, kTraceThreads, 0, st>>>(scene_view(c), sl.nv, c->shadow_rays_b, c->shadow_start_b,
+                                                   &sl.cnt->shadow_count_b, c->cap_nee, fetch_b, sl.cnt, 1,
+                                                   nullptr, nullptr);
   return cudaGetLastError();
 }
 
