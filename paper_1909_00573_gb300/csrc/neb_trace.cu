@@ -32,7 +32,7 @@ struct Walk {
   float best_t;
   int npend;
   int pend[5];
-  int start, skip;  // any hit: the subtree walked first, and the subtree the second walk leaves out
+  int start, skip;  // any hit: the subtree walked first, and the subtree the second walk leaves out (0: none)
 };
 
 __device__ __forceinline__ void walk_init(Walk& w) {
@@ -42,13 +42,15 @@ __device__ __forceinline__ void walk_init(Walk& w) {
   w.best_t = FLT_MAX;
   w.npend = 0;
   w.start = 0;
-  w.skip = -1;
+  w.skip = 0;
 }
 
 // One inner-node step of the any-hit walk over the 4-wide tree: leaf children
 // whose box is hit are queued (at most four, so a walk steps with at most one
 // queued primitive), the first hit inner child is visited next and the others
-// are pushed; the child w.skip (a subtree already walked) is left out.
+// are pushed; the inner child w.skip (a subtree already walked) is left out.
+// Leaf links are negative and the root, 0, is no node's child, so w.skip = 0
+// leaves nothing out.
 __device__ __forceinline__ void inner_step4(const SceneView& s, const RayPre& r, float tbound, Walk& w, int* stack,
                                            uint32_t* status, uint32_t& visits) {
   Node4Oct n = load_node4_oct(s.nodes, w.node, r.oct);
@@ -405,7 +407,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, Nee
       walk_init(w);
       w.start = first;
       w.node = phase == 0 ? first : 0;
-      w.skip = phase == 0 ? -1 : first;
+      w.skip = phase == 0 ? 0 : first;
       if (phase == 0) ++rays;
       if (no_geometry) {  // nothing can block it
         lit0 = true;

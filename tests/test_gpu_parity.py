@@ -316,6 +316,27 @@ def test_bvh_axis_aligned_and_tiny_direction_rays(neb, oracle):
     assert np.all(gp[op >= 0] >= 0)
 
 
+@pytest.mark.parametrize("first", [True, False])
+def test_shadow_of_primitive_zero(neb, oracle, first):
+    """A single blocking triangle between a sphere light and a plane, stored
+    as primitive 0 (its leaf link is ~0 = -1) or last: the NEE image of
+    direct light (D = 2) matches the oracle pixel by pixel, umbra included."""
+    from paper_1909_00573_gb300 import scenes
+    base = scenes.plane_under_sphere()
+    blocker = np.array([[[-0.25, 0.5, -0.15], [0.25, 0.5, -0.15], [0.0, 0.5, 0.35]]], np.float32)
+    tri = np.concatenate([blocker, base.tri] if first else [base.tri, blocker], 0)
+    s = scenes.Scene(tri, np.zeros(len(tri)), base.sph, base.sph_mat, base.mats, base.cam, "blocked_plane")
+    rc = scenes.RenderConfig(64, 64, 2, 0.01, 1 << 14, 4, 2, strategy_mask=2)
+    ctx = neb.render(s, rc)
+    g = ctx.read_split()[1].sum(-1)
+    st = ctx.stats()
+    ctx.close()
+    o = oracle.render(s, rc)["split"][1].sum(-1)
+    assert st["status"] & ~neb.STATUS_OCTREE_FULL == 0
+    assert (o == 0).mean() > 0.02 and (o > 0).mean() > 0.5          # an umbra in view, and lit plane
+    assert _compare(g, o).mean() >= 0.999
+
+
 def test_neighbour_counts_equal_brute_force(neb, oracle):
     rng = np.random.default_rng(51)
     pts = rng.uniform(0, 1, (30000, 3)).astype(np.float32)
