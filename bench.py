@@ -176,11 +176,11 @@ def load_peaks():
 TRAFFIC_SOURCES = ("paper_1909_00573_gb300/csrc/neb_trace.cu", "paper_1909_00573_gb300/csrc/neb_device.cuh",
                    "paper_1909_00573_gb300/csrc/neb_types.h")
 NCU_TRAFFIC = {  # (workload, stage): DRAM bytes per launch from one ncu capture of these sources
-    ("large_city", "trace_camera"): {"bytes_per_launch": 73495270,
-                                     "sources_sha256": "ab4cbfcc29040f0c331378de51baf66992c9c7b15a22a1b40c7644bb853364a0",
+    ("large_city", "trace_camera"): {"bytes_per_launch": 73650278,
+                                     "sources_sha256": "4497dc8395ad32fa6586cd93ea5daf31dd12467338fa5499b5ba0f0546465864",
                                      "profile": "profiles/k_trace_closest_large_city.md"},
-    ("large_city", "shadow"): {"bytes_per_launch": 275990000,
-                               "sources_sha256": "ab4cbfcc29040f0c331378de51baf66992c9c7b15a22a1b40c7644bb853364a0",
+    ("large_city", "shadow"): {"bytes_per_launch": 217700608,   # mean of the two launches of an iteration
+                               "sources_sha256": "4497dc8395ad32fa6586cd93ea5daf31dd12467338fa5499b5ba0f0546465864",
                                "profile": "profiles/k_trace_shadow_large_city.md"},
 }
 
