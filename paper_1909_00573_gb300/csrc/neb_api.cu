@@ -59,14 +59,14 @@ static void free_scene(neb_ctx* c) {
   cudaFree(c->tv0); cudaFree(c->tv1); cudaFree(c->tv2); cudaFree(c->sph); cudaFree(c->mats); cudaFree(c->sph_mat);
   cudaFree(c->prim_light); cudaFree(c->light_prim); cudaFree(c->alias_idx); cudaFree(c->light_psel);
   cudaFree(c->light_inv_area); cudaFree(c->alias_prob); cudaFree(c->nodes);
-  cudaFree(c->node_parent); cudaFree(c->prim_owner);
+  cudaFree(c->prim_start);
   cudaFree(c->oct_nodes);
   cudaFree(c->oct_state);
   c->tv0 = c->tv1 = c->tv2 = c->sph = c->mats = nullptr;
   c->sph_mat = c->prim_light = c->light_prim = c->alias_idx = nullptr;
   c->light_psel = c->light_inv_area = c->alias_prob = nullptr;
   c->nodes = nullptr;
-  c->node_parent = c->prim_owner = nullptr;
+  c->prim_start = nullptr;
   c->oct_nodes = nullptr;
   c->oct_state = nullptr;
   c->scene_ready = c->bvh_ready = false;
@@ -122,7 +122,7 @@ extern "C" int neb_job_device_bytes(const neb_config* cfg, int n_tri, int n_sph,
   b += 3 * nt * sizeof(float4) + ns * (sizeof(float4) + sizeof(int)) + 3 * (size_t)n_mat * sizeof(float4);
   b += np * sizeof(int) + nl * (2 * sizeof(int) + 3 * sizeof(float));
   b += (1 + (((size_t)cfg->octree_capacity + 7) & ~(size_t)7)) * sizeof(int) + sizeof(OctreeState);
-  b += (np > 1 ? np - 1 : 1) * (sizeof(BVH4Node) + sizeof(int)) + np * sizeof(int);
+  b += (np > 1 ? np - 1 : 1) * sizeof(BVH4Node) + np * sizeof(int);
   *out = b;
   return NEB_OK;
 }

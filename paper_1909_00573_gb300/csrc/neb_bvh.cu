@@ -505,14 +505,31 @@ static cudaError_t collapse4(const BVHNode* bin, int n_bin, BVH4Node* out, cudaS
   return e;
 }
 
+__global__ void k_lift(int* node_of_prim, const int* __restrict__ parent, int n, int n_nodes, int lift) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    int nd = node_of_prim[p];
+    for (int l = 0; l < lift && nd > 0 && nd < n_nodes; ++l) nd = parent[nd];
+    node_of_prim[p] = nd > 0 && nd < n_nodes ? nd : 0;
+  }
+}
+
 cudaError_t build_bvh(neb_ctx* c) {
   int n = c->nt + c->ns;
   if (c->nodes) { cudaFree(c->nodes); c->nodes = nullptr; }
-  if (c->node_parent) { cudaFree(c->node_parent); c->node_parent = nullptr; }
-  if (c->prim_owner) { cudaFree(c->prim_owner); c->prim_owner = nullptr; }
+  if (c->prim_start) { cudaFree(c->prim_start); c->prim_start = nullptr; }
   if (n == 0) return cudaSuccess;
-  return build_bvh4(scene_view(c), n, c->cfg.bvh_builder, c->stream, &c->nodes, &c->n_nodes4, &c->node_parent,
-                    &c->prim_owner);
+  int* parent = nullptr;
+  cudaError_t e = build_bvh4(scene_view(c), n, c->cfg.bvh_builder, c->stream, &c->nodes, &c->n_nodes4, &parent,
+                             &c->prim_start);
+  if (e == cudaSuccess) {
+    // each primitive's leaf node, lifted in place to the subtree shadow walks start in
+    int blocks = (n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_lift<<<blocks, 256, 0, c->stream>>>(c->prim_start, parent, n, c->n_nodes4, kShadowLift);
+    e = cudaStreamSynchronize(c->stream);
+  }
+  cudaFree(parent);
+  return e;
 }
 
 cudaError_t build_bvh4(const SceneView& s, int n, int builder, cudaStream_t st, BVH4Node** nodes_out, int* n4_out,

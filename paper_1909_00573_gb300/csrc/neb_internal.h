@@ -156,8 +156,7 @@ struct neb_ctx {
 
   // BVH (4-wide)
   neb::BVH4Node* nodes = nullptr;
-  int* node_parent = nullptr;  // parent of each 4-wide node, -1 at the root
-  int* prim_owner = nullptr;   // 4-wide node holding each primitive as a leaf child
+  int* prim_start = nullptr;   // per primitive: the node kShadowLift levels above its leaf's node
   int n_nodes4 = 0;
   bool bvh_ready = false;
 
@@ -229,6 +228,9 @@ cudaError_t build_bvh(neb_ctx* c);
 // 4-wide BVH over the n primitives of view s (triangles, then spheres; a
 // sphere of radius 0 is a point) into a new device array *nodes_out;
 // builder 0 PLOC, 1 Karras.  Synchronises st.
+// Shadow walks start in the subtree this many levels above the node that
+// holds the origin's primitive (then walk the rest of the tree if needed).
+constexpr int kShadowLift = 3;
 // parent_out / owner_out (or nullptr): the parent of every 4-wide node (-1 at
 // the root) and the node holding each primitive as a leaf child, allocated here
 cudaError_t build_bvh4(const SceneView& s, int n, int builder, cudaStream_t st, BVH4Node** nodes_out, int* n4_out,

@@ -298,16 +298,14 @@ __global__ void __launch_bounds__(kGroupThreads) k_shadow_count(NeeStore nv, con
   flush_counts(h, counts);
 }
 
-// Levels above the node that holds the origin's primitive: the subtree there
-// is walked first.
-constexpr int kShadowLift = 3;
-
+// Each shadow ray also gets the subtree its walk starts in: the one
+// kShadowLift levels above the node that holds its origin's primitive
+// (precomputed per primitive when the tree is built).
 __global__ void __launch_bounds__(kGroupThreads) k_shadow_scatter(NeeStore nv, const DevCounters* cnt, int cap,
                                                                   GroupSpec g, int* __restrict__ cursors,
                                                                   ShadowRay* __restrict__ rays,
-                                                                  const int* __restrict__ parent,
-                                                                  const int* __restrict__ owner,
-                                                                  int* __restrict__ start, int n_nodes) {
+                                                                  const int* __restrict__ prim_start,
+                                                                  int* __restrict__ start) {
   __shared__ int h[kGroups];
   clear_hist(h);
   __syncthreads();
@@ -328,9 +326,7 @@ __global__ void __launch_bounds__(kGroupThreads) k_shadow_scatter(NeeStore nv, c
     sr.o = make_float4(o.x, o.y, o.z, ee.w * (1.0f - 1e-4f));
     sr.d = make_float4(ldir.x, ldir.y, ldir.z, __int_as_float(i));
     rays[slot] = sr;
-    int nd = __ldg(owner + nv.prim[i]);
-    for (int l = 0; l < kShadowLift && nd > 0 && nd < n_nodes; ++l) nd = __ldg(parent + nd);
-    start[slot] = nd > 0 && nd < n_nodes ? nd : 0;
+    start[slot] = __ldg(prim_start + nv.prim[i]);
   }
 }
 
@@ -516,8 +512,7 @@ cudaError_t launch_group_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st)
   k_shadow_count<<<group_blocks(c->cap_nee), kGroupThreads, 0, st>>>(sl.nv, sl.cnt, c->cap_nee, g, counts);
   k_group_scan<<<1, kScanThreads, 0, st>>>(counts, cursors, &sl.cnt->shadow_count);
   k_shadow_scatter<<<group_blocks(c->cap_nee), kGroupThreads, 0, st>>>(sl.nv, sl.cnt, c->cap_nee, g, cursors,
-                                                             c->shadow_rays, c->node_parent, c->prim_owner,
-                                                             c->shadow_start, c->n_nodes4);
+                                                             c->shadow_rays, c->prim_start, c->shadow_start);
   return cudaGetLastError();
 }
 
