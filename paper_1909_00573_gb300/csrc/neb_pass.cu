@@ -156,7 +156,12 @@ __global__ void k_begin(DevCounters* cnt) {
 
 __global__ void k_camera(IterParams ip, CameraParams cam, CamRay* q, DevCounters* cnt) {
   int P = ip.W * ip.H;
-  for (int pixel = blockIdx.x * blockDim.x + threadIdx.x; pixel < P; pixel += gridDim.x * blockDim.x) {
+  const bool tiled = (ip.W & 7) == 0 && (ip.H & 3) == 0;
+  const int tiles_x = ip.W >> 3;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < P; j += gridDim.x * blockDim.x) {
+    // queue order: 8 x 4 pixel tiles, one per warp, when the image is made of them
+    const int t = j >> 5, w = j & 31;
+    const int pixel = tiled ? ((t / tiles_x) * 4 + (w >> 3)) * ip.W + (t % tiles_x) * 8 + (w & 7) : j;
     uint4 rb = rng_block(ip.key, ip.iteration, pixel, 0, 0);
     float ju = u01(rb.x), jv = u01(rb.y);
     int px = pixel % ip.W, py = pixel / ip.W;
@@ -171,7 +176,7 @@ __global__ void k_camera(IterParams ip, CameraParams cam, CamRay* q, DevCounters
     r.d = make_float4(d.x, d.y, d.z, 1.0f);
     r.tau = make_float4(1.0f, 1.0f, 1.0f, 0.0f);
     r.mis = make_float4(0.0f, 0.0f, __int_as_float(-1), __int_as_float(RAY_FROM_CAMERA));
-    q[pixel] = r;
+    q[j] = r;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     cnt->cam_count[0] = P;
