@@ -346,6 +346,13 @@ __global__ void k_ploc_compact(int n, const int* __restrict__ nn, const int* __r
   }
 }
 
+// merges and survivors of a round: the last entries of the two exclusive scans plus their flags
+__global__ void k_ploc_tail(const int* mrank, const int* mflag, const int* kpos, const int* kflag, int count,
+                            int* out) {
+  out[0] = mrank[count - 1] + mflag[count - 1];
+  out[1] = kpos[count - 1] + kflag[count - 1];
+}
+
 static cudaError_t ploc_build(const SceneView& s, int n, const int* sorted_prim, BVHNode* nodes, Scratch& sc,
                               cudaStream_t st) {
   int *cid[2] = {nullptr, nullptr}, *nn = nullptr, *mflag = nullptr, *kflag = nullptr, *mrank = nullptr,
@@ -358,6 +365,8 @@ static cudaError_t ploc_build(const SceneView& s, int n, const int* sorted_prim,
             cudaMalloc(&nn, 4ull * n) == cudaSuccess && cudaMalloc(&mflag, 4ull * n) == cudaSuccess &&
             cudaMalloc(&kflag, 4ull * n) == cudaSuccess && cudaMalloc(&mrank, 4ull * n) == cudaSuccess &&
             cudaMalloc(&kpos, 4ull * n) == cudaSuccess && cudaMalloc(&tail, 16) == cudaSuccess;
+  int* h = nullptr;  // pinned: the per-round readback is one small asynchronous copy
+  ok = ok && cudaMallocHost(&h, 2 * sizeof(int)) == cudaSuccess;
   if (!ok) e = cudaErrorMemoryAllocation;
   if (ok) {
     int gb = (n + 255) / 256;
@@ -372,16 +381,13 @@ static cudaError_t ploc_build(const SceneView& s, int n, const int* sorted_prim,
       k_ploc_flags<<<fb, 256, 0, st>>>(count, nn, mflag, kflag);
       scan_exclusive(mflag, mrank, count, sc, st);
       scan_exclusive(kflag, kpos, count, sc, st);
-      int h[4];
-      cudaMemcpyAsync(&h[0], mrank + count - 1, 4, cudaMemcpyDeviceToHost, st);
-      cudaMemcpyAsync(&h[1], mflag + count - 1, 4, cudaMemcpyDeviceToHost, st);
-      cudaMemcpyAsync(&h[2], kpos + count - 1, 4, cudaMemcpyDeviceToHost, st);
-      cudaMemcpyAsync(&h[3], kflag + count - 1, 4, cudaMemcpyDeviceToHost, st);
+      k_ploc_tail<<<1, 1, 0, st>>>(mrank, mflag, kpos, kflag, count, tail);
+      cudaMemcpyAsync(h, tail, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
       k_ploc_compact<<<fb, 256, 0, st>>>(count, nn, cid[cur], blo[cur], bhi[cur], mrank, kpos, base, nodes,
                                          cid[1 - cur], blo[1 - cur], bhi[1 - cur]);
       e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) break;
-      int merges = h[0] + h[1], next = h[2] + h[3];
+      int merges = h[0], next = h[1];
       if (merges <= 0 || next >= count) { e = cudaErrorUnknown; break; }  // no progress: cannot happen
       base -= merges;
       count = next;
@@ -392,6 +398,7 @@ static cudaError_t ploc_build(const SceneView& s, int n, const int* sorted_prim,
   }
   cudaFree(cid[0]); cudaFree(cid[1]); cudaFree(blo[0]); cudaFree(blo[1]); cudaFree(bhi[0]); cudaFree(bhi[1]);
   cudaFree(nn); cudaFree(mflag); cudaFree(kflag); cudaFree(mrank); cudaFree(kpos); cudaFree(tail);
+  cudaFreeHost(h);
   return e;
 }
 
@@ -488,7 +495,13 @@ static cudaError_t collapse4(const BVHNode* bin, int n_bin, BVH4Node* out, cudaS
   cudaMemcpyAsync(w0, &root, 8, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(cnt, init, 8, cudaMemcpyHostToDevice, st);
   int n_work = 1;
-  int h[2] = {1, 0};
+  int* h = nullptr;  // pinned: one small asynchronous readback per level
+  if (cudaMallocHost(&h, 2 * sizeof(int)) != cudaSuccess) {
+    cudaFree(w0); cudaFree(w1); cudaFree(cnt);
+    return cudaErrorMemoryAllocation;
+  }
+  h[0] = 1;
+  h[1] = 0;
   while (n_work > 0) {
     int blocks = (n_work + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
@@ -502,6 +515,7 @@ static cudaError_t collapse4(const BVHNode* bin, int n_bin, BVH4Node* out, cudaS
   }
   *n_out = h[0];
   cudaFree(w0); cudaFree(w1); cudaFree(cnt);
+  cudaFreeHost(h);
   return e;
 }
 
