@@ -21,7 +21,7 @@ constexpr int kShadowSteps = 10;  // the same for the any-hit walk
 constexpr int kIdle = -1, kDone = -2;
 
 // Traversal state.  Both walks run over the 4-wide BVH.  Closest-hit walks
-// test a leaf primitive as soon as its box is hit.  Shadow (any-hit) walks
+// test the leaf primitives of a node right after its box tests.  Shadow (any-hit) walks
 // queue leaf primitives, and the warp tests its queued primitives together
 // once every lane has two queued or nothing left to walk, so the long
 // triangle test runs with most lanes active ("while-while" with speculative
