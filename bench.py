@@ -514,6 +514,7 @@ def main():
     t_b0 = time.perf_counter()
     ctx.build_bvh()
     bvh_build_ms = (time.perf_counter() - t_b0) * 1000.0
+    bvh_cost = ctx.bvh_cost()
     if args.autotune > 0:
         ctx.autotune(args.autotune)
     tuning = ctx.tuning().as_dict()
@@ -618,6 +619,7 @@ def main():
                 "counters_per_step": {k: (v / args.steps if not isinstance(v, list) else [x / args.steps for x in v])
                                       for k, v in d.items() if k not in ("iterations",)},
                 "status": s1["status"], "bvh_build_ms": bvh_build_ms,
+                "bvh_sah": {"node_visits": bvh_cost[0], "prim_tests": bvh_cost[1]},
                 "bvh": "PLOC" if args.bvh == 0 else "LBVH", "tuning": tuning,
                 "tuning_source": "autotuned" if args.autotune > 0 else "defaults"}
         print(json.dumps(line))

@@ -120,6 +120,13 @@ int neb_scene_upload(neb_ctx* ctx, const float* tri, const uint32_t* tri_mat, in
  * opened first) that all walks use.  Leaves hold one primitive. */
 int neb_build_bvh(neb_ctx* ctx);
 
+/* Quality of the built tree by the surface area heuristic (MacDonald and
+ * Booth): out[0] = expected 4-wide node visits (root included) and out[1] =
+ * expected primitive tests of a ray through the scene box, for rays uniform
+ * in space and direction, with no early exit.  Synchronises the context
+ * stream.  NEB_ERR_ARG before neb_build_bvh. */
+int neb_bvh_cost(neb_ctx* ctx, double* out);
+
 /* Enqueues n_iterations NEB iterations (asynchronous).  Iteration indices
  * continue from the previous call (1-based).  Passes 2-3 of an iteration run
  * on a second stream owned by the context and overlap pass 1 of the next

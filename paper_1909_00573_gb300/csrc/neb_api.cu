@@ -512,6 +512,17 @@ extern "C" int neb_build_bvh(neb_ctx* c) {
   return NEB_OK;
 }
 
+extern "C" int neb_bvh_cost(neb_ctx* c, double* out) {
+  if (!c || !out) return NEB_ERR_ARG;
+  if (!c->bvh_ready) return fail(c, NEB_ERR_ARG, "neb_bvh_cost: no BVH");
+  double s[3] = {0.0, 0.0, 0.0};
+  cudaError_t e = bvh_area_sums(c, s);
+  if (e != cudaSuccess) return fail(c, NEB_ERR_CUDA, "neb_bvh_cost", e);
+  out[0] = s[2] > 0.0 ? 1.0 + s[0] / s[2] : 0.0;
+  out[1] = s[2] > 0.0 ? s[1] / s[2] : 0.0;
+  return NEB_OK;
+}
+
 // Passes 2-3 of an iteration overlap pass 1 of the next one (two streams, two
 // buffer slots); stage timing keeps everything on one stream.
 static int iterate_one(neb_ctx* c) {

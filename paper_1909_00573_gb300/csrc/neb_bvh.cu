@@ -519,6 +519,58 @@ static cudaError_t collapse4(const BVHNode* bin, int n_bin, BVH4Node* out, cudaS
   return e;
 }
 
+// Surface-area sums of a 4-wide tree: out[0] += area of every inner child box,
+// out[1] += area of every leaf box, out[2] = area of the root's children's
+// union (one thread).  Over the root area they are the expected node visits
+// (besides the root) and primitive tests of a ray that meets the scene box,
+// for rays uniform in space and direction (MacDonald and Booth's surface area
+// heuristic).
+__device__ __forceinline__ float box_area(float lx, float hx, float ly, float hy, float lz, float hz) {
+  float dx = fmaxf(hx - lx, 0.0f), dy = fmaxf(hy - ly, 0.0f), dz = fmaxf(hz - lz, 0.0f);
+  return 2.0f * (dx * dy + dy * dz + dz * dx);
+}
+
+__global__ void k_bvh4_area(const BVH4Node* __restrict__ nodes, int n4, double* out) {
+  double inner = 0.0, leaf = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gridDim.x * blockDim.x) {
+    const BVH4Node nd = nodes[i];
+    for (int c = 0; c < 4; ++c) {
+      int ref = comp4i(nd.ch, c);
+      if (ref == kEmptyChild) continue;
+      double a = box_area(comp4(nd.lox, c), comp4(nd.hix, c), comp4(nd.loy, c), comp4(nd.hiy, c),
+                          comp4(nd.loz, c), comp4(nd.hiz, c));
+      if (ref >= 0) inner += a;
+      else leaf += a;
+    }
+  }
+  atomicAdd(out, inner);
+  atomicAdd(out + 1, leaf);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const BVH4Node r = nodes[0];
+    float lo[3] = {3.4e38f, 3.4e38f, 3.4e38f}, hi[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
+    for (int c = 0; c < 4; ++c) {
+      if (comp4i(r.ch, c) == kEmptyChild) continue;
+      lo[0] = fminf(lo[0], comp4(r.lox, c)); hi[0] = fmaxf(hi[0], comp4(r.hix, c));
+      lo[1] = fminf(lo[1], comp4(r.loy, c)); hi[1] = fmaxf(hi[1], comp4(r.hiy, c));
+      lo[2] = fminf(lo[2], comp4(r.loz, c)); hi[2] = fmaxf(hi[2], comp4(r.hiz, c));
+    }
+    out[2] = box_area(lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]);
+  }
+}
+
+cudaError_t bvh_area_sums(const neb_ctx* c, double out[3]) {
+  double* d = nullptr;
+  cudaError_t e = cudaMallocAsync(&d, 3 * sizeof(double), c->stream);
+  if (e != cudaSuccess) return e;
+  cudaMemsetAsync(d, 0, 3 * sizeof(double), c->stream);
+  int blocks = (c->n_nodes4 + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_bvh4_area<<<blocks > 0 ? blocks : 1, 256, 0, c->stream>>>(c->nodes, c->n_nodes4, d);
+  cudaMemcpyAsync(out, d, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  cudaFreeAsync(d, c->stream);
+  return cudaStreamSynchronize(c->stream);
+}
+
 __global__ void k_lift(int* node_of_prim, const int* __restrict__ parent, int n, int n_nodes, int lift) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     int nd = node_of_prim[p];

@@ -233,6 +233,8 @@ cudaError_t build_bvh(neb_ctx* c);
 constexpr int kShadowLift = 3;
 // parent_out / owner_out (or nullptr): the parent of every 4-wide node (-1 at
 // the root) and the node holding each primitive as a leaf child, allocated here
+// surface-area sums of the context's 4-wide tree: inner child boxes, leaf boxes, root box
+cudaError_t bvh_area_sums(const neb_ctx* c, double out[3]);
 cudaError_t build_bvh4(const SceneView& s, int n, int builder, cudaStream_t st, BVH4Node** nodes_out, int* n4_out,
                        int** parent_out = nullptr, int** owner_out = nullptr);
 cudaError_t launch_trace_debug(const SceneView& s, const float* d_rays, int n, int* d_prim, float* d_t,

@@ -28,7 +28,7 @@ EXPORTS = ["neb_create", "neb_destroy", "neb_last_error", "neb_scene_upload", "n
            "neb_octree_density", "neb_octree_read", "neb_octree_load", "neb_count_neighbours",
            "neb_count_neighbours_noalloc", "neb_iterate_batch", "neb_job_device_bytes", "neb_get_tuning",
            "neb_set_tuning", "neb_autotune", "neb_density_estimators", "neb_read_nee_vertices",
-           "neb_iterate_read"]
+           "neb_iterate_read", "neb_bvh_cost"]
 NOALLOC_MAX_POINTS = 1 << 18
 
 
@@ -93,6 +93,7 @@ def lib():
             "neb_build_bvh": ([vp], C.c_int),
             "neb_iterate": ([vp, C.c_int], C.c_int),
             "neb_iterate_read": ([vp, C.c_int, vp], C.c_int),
+            "neb_bvh_cost": ([vp, vp], C.c_int),
             "neb_resolve": ([vp, vp, C.c_int], C.c_int),
             "neb_read_accum": ([vp, vp], C.c_int),
             "neb_read_split": ([vp, vp], C.c_int),
@@ -188,6 +189,12 @@ class Context:
 
     def iterate(self, n=1):
         self._c(lib().neb_iterate(self.h, int(n)))
+
+    def bvh_cost(self):
+        """(expected node visits, expected primitive tests) of the built tree by the surface area heuristic."""
+        out = np.zeros(2, np.float64)
+        self._c(lib().neb_bvh_cost(self.h, _p(out)))
+        return float(out[0]), float(out[1])
 
     def iterate_read(self, n, rgb_host_ptr):
         """n iterations, the running image copied to host memory at rgb_host_ptr

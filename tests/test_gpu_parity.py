@@ -337,6 +337,35 @@ def test_shadow_of_primitive_zero(neb, oracle, first):
     assert _compare(g, o).mean() >= 0.999
 
 
+def test_bvh_cost_closed_forms(neb):
+    """Surface-area cost of the built tree: one triangle is one leaf under the
+    root (one node visit, one primitive test per ray through its box); for two
+    triangles far apart the expected tests are the sum of their boxes' areas
+    over the root box's area."""
+    from paper_1909_00573_gb300 import scenes
+
+    def area(lo, hi):
+        d = np.maximum(hi - lo, 0.0)
+        return 2.0 * (d[0] * d[1] + d[1] * d[2] + d[2] * d[0])
+
+    t1 = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0.5]], np.float32)
+    t2 = t1 + np.array([10, 3, 7], np.float32)
+    rc = scenes.RenderConfig(8, 8, 4, 0.01, 1024, 4, 1)
+    for tris in ([t1], [t1, t2]):
+        tri = np.stack(tris)
+        s = scenes.Scene(tri, np.zeros(len(tri)), np.zeros((0, 4)), np.zeros(0),
+                         scenes.material(0, (0.5,) * 3)[None], np.zeros(10))
+        ctx = neb.Context(neb.make_config(rc))
+        ctx.scene_upload(s)
+        ctx.build_bvh()
+        nodes, prims = ctx.bvh_cost()
+        ctx.close()
+        boxes = [(t.min(0).astype(np.float64), t.max(0).astype(np.float64)) for t in tris]
+        root = area(np.min([b[0] for b in boxes], 0), np.max([b[1] for b in boxes], 0))
+        assert nodes == pytest.approx(1.0)
+        assert prims == pytest.approx(sum(area(*b) for b in boxes) / root, rel=1e-6)
+
+
 def test_neighbour_counts_equal_brute_force(neb, oracle):
     rng = np.random.default_rng(51)
     pts = rng.uniform(0, 1, (30000, 3)).astype(np.float32)
