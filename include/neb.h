@@ -111,8 +111,9 @@ int neb_scene_upload(neb_ctx* ctx, const float* tri, const uint32_t* tri_mat, in
                      const float* sph, const uint32_t* sph_mat, int ns,
                      const float* mats, int nm, const float* cam);
 
-/* Builds the BVH on the device: 30-bit Morton codes of primitive centroids
- * (one scale for all axes), stable 4-bit LSD radix sort, then either PLOC
+/* Builds the BVH on the device: Morton codes of primitive centroids on a 2^21
+ * grid per axis (one scale for all axes), ordered by their top 62 bits with
+ * two stable 4-bit LSD radix sorts (low key, then high key), then either PLOC
  * (Meister and Bittner 2018: rounds of mutual nearest-neighbour merges by
  * union surface area within +-16 positions of the Morton order; default) or
  * the Karras (HPG 2012) hierarchy with bottom-up bounds; the binary tree is

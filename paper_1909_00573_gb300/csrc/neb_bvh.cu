@@ -68,7 +68,17 @@ __device__ __forceinline__ uint32_t expand_bits(uint32_t v) {
   return v;
 }
 
-__global__ void k_morton(SceneView s, int n, const int* cb, uint32_t* keys, int* vals) {
+// Morton code of the centroid on a 2^21 grid per axis (63 bits), as two
+// sort keys: hi = the top 30 bits (the code of the top 10 bits of each
+// coordinate), lo = the next 32 bits.  Sorting by lo and then, stably, by hi
+// orders by the 62-bit prefix: small, dense objects (a torus of 20,000
+// triangles inside one 1/1024 cell of a city) keep a spatial order instead of
+// the order of their primitive indices.
+__device__ __forceinline__ uint32_t expand_bits11(uint32_t v) {  // 11 bits -> every third of 31
+  return expand_bits(v & 1023u) | (((v >> 10) & 1u) << 30);
+}
+
+__global__ void k_morton(SceneView s, int n, const int* cb, uint32_t* keys_hi, uint32_t* keys_lo, int* vals) {
   float3 lo = f3(ordered_to_float(cb[0]), ordered_to_float(cb[1]), ordered_to_float(cb[2]));
   float3 hi = f3(ordered_to_float(cb[3]), ordered_to_float(cb[4]), ordered_to_float(cb[5]));
   // one scale for all axes: Morton cells stay cubes in world space, so flat
@@ -77,6 +87,7 @@ __global__ void k_morton(SceneView s, int n, const int* cb, uint32_t* keys, int*
   float3 ext = sub(hi, lo);
   float e = fmaxf(ext.x, fmaxf(ext.y, ext.z));
   float inv = e > 0.0f ? 1.0f / e : 0.0f;
+  const float g = 2097152.0f;  // 2^21
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     float3 a, b;
     prim_bounds(s, p, a, b);
@@ -84,12 +95,20 @@ __global__ void k_morton(SceneView s, int n, const int* cb, uint32_t* keys, int*
     float x = (c.x - lo.x) * inv;
     float y = (c.y - lo.y) * inv;
     float z = (c.z - lo.z) * inv;
-    uint32_t ix = (uint32_t)fminf(fmaxf(x * 1024.0f, 0.0f), 1023.0f);
-    uint32_t iy = (uint32_t)fminf(fmaxf(y * 1024.0f, 0.0f), 1023.0f);
-    uint32_t iz = (uint32_t)fminf(fmaxf(z * 1024.0f, 0.0f), 1023.0f);
-    keys[p] = (expand_bits(ix) << 2) | (expand_bits(iy) << 1) | expand_bits(iz);
+    uint32_t ix = (uint32_t)fminf(fmaxf(x * g, 0.0f), g - 1.0f);
+    uint32_t iy = (uint32_t)fminf(fmaxf(y * g, 0.0f), g - 1.0f);
+    uint32_t iz = (uint32_t)fminf(fmaxf(z * g, 0.0f), g - 1.0f);
+    keys_hi[p] = (expand_bits(ix >> 11) << 2) | (expand_bits(iy >> 11) << 1) | expand_bits(iz >> 11);
+    uint64_t m33 = ((uint64_t)expand_bits11(ix & 2047u) << 2) | ((uint64_t)expand_bits11(iy & 2047u) << 1) |
+                   (uint64_t)expand_bits11(iz & 2047u);
+    keys_lo[p] = (uint32_t)(m33 >> 1);
     vals[p] = p;
   }
+}
+
+__global__ void k_gather_keys(const uint32_t* __restrict__ keys, const int* __restrict__ order, int n,
+                              uint32_t* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = keys[order[i]];
 }
 
 // ---- stable LSD radix sort, 4-bit digits, one element per thread ----------------
@@ -626,7 +645,7 @@ cudaError_t build_bvh4(const SceneView& s, int n, int builder, cudaStream_t st, 
   if (e != cudaSuccess) return e;
   int nblocks = (n + kSortThreads - 1) / kSortThreads;
   size_t hist_n = (size_t)16 * nblocks;
-  uint32_t *k0 = nullptr, *k1 = nullptr;
+  uint32_t *k0 = nullptr, *k1 = nullptr, *khi = nullptr;
   int *v0 = nullptr, *v1 = nullptr, *hist = nullptr, *offs = nullptr, *cb = nullptr;
   int2* child = nullptr;
   int *pint = nullptr, *pleaf = nullptr, *flags = nullptr;
@@ -634,6 +653,7 @@ cudaError_t build_bvh4(const SceneView& s, int n, int builder, cudaStream_t st, 
   Scratch sc;
   sc.n = scan_scratch_ints(hist_n);
   bool ok = cudaMalloc(&k0, 4ull * n) == cudaSuccess && cudaMalloc(&k1, 4ull * n) == cudaSuccess &&
+            cudaMalloc(&khi, 4ull * n) == cudaSuccess &&
             cudaMalloc(&v0, 4ull * n) == cudaSuccess && cudaMalloc(&v1, 4ull * n) == cudaSuccess &&
             cudaMalloc(&hist, 4ull * hist_n) == cudaSuccess && cudaMalloc(&offs, 4ull * hist_n) == cudaSuccess &&
             cudaMalloc(&cb, 4ull * 6) == cudaSuccess && cudaMalloc(&child, 8ull * (n - 1)) == cudaSuccess &&
@@ -647,14 +667,19 @@ cudaError_t build_bvh4(const SceneView& s, int n, int builder, cudaStream_t st, 
     int gb = (n + 255) / 256;
     if (gb > 152 * 16) gb = 152 * 16;
     k_centroid_bounds<<<gb, 256, 0, st>>>(s, n, cb);
-    k_morton<<<gb, 256, 0, st>>>(s, n, cb, k0, v0);
-    for (int shift = 0; shift < 30; shift += 4) {
-      k_digit_hist<<<nblocks, kSortThreads, 0, st>>>(k0, n, shift, nblocks, hist);
-      scan_exclusive(hist, offs, hist_n, sc, st);
-      k_digit_scatter<<<nblocks, kSortThreads, 0, st>>>(k0, v0, n, shift, nblocks, offs, k1, v1);
-      uint32_t* tk = k0; k0 = k1; k1 = tk;
-      int* tv = v0; v0 = v1; v1 = tv;
-    }
+    k_morton<<<gb, 256, 0, st>>>(s, n, cb, khi, k0, v0);
+    auto sort32 = [&](int bits) {  // stable LSD passes over (k0, v0); an even count leaves them in k0, v0
+      for (int shift = 0; shift < bits; shift += 4) {
+        k_digit_hist<<<nblocks, kSortThreads, 0, st>>>(k0, n, shift, nblocks, hist);
+        scan_exclusive(hist, offs, hist_n, sc, st);
+        k_digit_scatter<<<nblocks, kSortThreads, 0, st>>>(k0, v0, n, shift, nblocks, offs, k1, v1);
+        uint32_t* tk = k0; k0 = k1; k1 = tk;
+        int* tv = v0; v0 = v1; v1 = tv;
+      }
+    };
+    sort32(32);                                              // by the low 32 bits
+    k_gather_keys<<<gb, 256, 0, st>>>(khi, v0, n, k0);        // the high keys in that order
+    sort32(30);                                              // stably by the high 30 bits
     if (builder == 1) {
       cudaMemsetAsync(pint, 0xff, 4ull * (n - 1), st);
       cudaMemsetAsync(flags, 0, 4ull * (n - 1), st);
@@ -676,7 +701,7 @@ cudaError_t build_bvh4(const SceneView& s, int n, int builder, cudaStream_t st, 
   } else {
     e = cudaErrorMemoryAllocation;
   }
-  cudaFree(k0); cudaFree(k1); cudaFree(v0); cudaFree(v1); cudaFree(hist); cudaFree(offs); cudaFree(cb);
+  cudaFree(k0); cudaFree(k1); cudaFree(khi); cudaFree(v0); cudaFree(v1); cudaFree(hist); cudaFree(offs); cudaFree(cb);
   cudaFree(child); cudaFree(pint); cudaFree(pleaf); cudaFree(flags); cudaFree(boxes); cudaFree(sc.data);
   cudaStreamSynchronize(st);
   cudaFree(bin);
