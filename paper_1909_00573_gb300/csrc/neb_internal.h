@@ -277,6 +277,7 @@ cudaError_t launch_trace_closest(neb_ctx* c, const float4* recs, const int* coun
 // groups the slot's shadow rays into c->shadow_rays, then walks them
 cudaError_t launch_group_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st);
 cudaError_t launch_trace_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st);
+int shadow_walk_launches(const neb_ctx* c);  // kernels launch_trace_shadow enqueues
 // regroups the camera queue q (count at count_ptr) into out (same count)
 cudaError_t launch_group_camera(neb_ctx* c, const CamRay* q, const int* count_ptr, CamRay* out, cudaStream_t st);
 

@@ -888,7 +888,7 @@ static long long enqueue_pass1(neb_ctx* c, int iteration, cudaStream_t st, Stage
   tm.end();
   tm.begin(STAGE_SHADOW);
   launch_trace_shadow(c, sl, st);
-  launches += 2;
+  launches += shadow_walk_launches(c);
   tm.end();
   return launches;
 }

@@ -374,7 +374,8 @@ __global__ void __launch_bounds__(kGroupThreads) k_cam_group_scatter(const CamRa
 // appended to a second queue.  Phase 1 walks those from the root, leaving
 // that subtree out.  Every leaf is tested once at most and the answer is that
 // of one walk from the root; splitting the walks keeps walks of similar
-// length together in a warp.
+// length together in a warp.  Phase 2 is the single walk from the root, used
+// for small trees, where the second launch would cost more than it saves.
 __global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, NeeStore nv,
                                                                 const ShadowRay* __restrict__ srays,
                                                                 const int* __restrict__ sstart,
@@ -401,10 +402,10 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, Nee
       r = make_ray(xyz(so), xyz(sd));
       tmax = so.w;
       walk_init(w);
-      w.start = first;
+      w.start = phase == 2 ? 0 : first;
       w.node = phase == 0 ? first : 0;
-      w.skip = phase == 0 ? 0 : first;
-      if (phase == 0) ++rays;
+      w.skip = phase == 1 ? first : 0;
+      if (phase != 1) ++rays;
       if (no_geometry) {  // nothing can block it
         lit0 = true;
         lit0_id = nr;
@@ -516,12 +517,23 @@ cudaError_t launch_group_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st)
   return cudaGetLastError();
 }
 
+// Trees of fewer nodes are walked from the root in one launch.
+constexpr int kLocalFirstMinNodes = 8192;
+
+int shadow_walk_launches(const neb_ctx* c) { return c->n_nodes4 >= kLocalFirstMinNodes ? 2 : 1; }
+
 cudaError_t launch_trace_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st) {
   static const int shadow_blocks = trace_blocks(k_trace_shadow);
   const int blocks = capped_blocks(c->cap_nee, kTraceThreads, shadow_blocks);
-  int* fetch = &sl.cnt->fetch[1];   // phase 0
+  int* fetch = &sl.cnt->fetch[1];   // phase 0 (or the single walk)
   int* fetch_b = &sl.cnt->fetch[3];  // phase 1
   cudaMemsetAsync(fetch, 0, sizeof(int), st);
+  if (shadow_walk_launches(c) == 1) {
+    k_trace_shadow<<<blocks, kTraceThreads, 0, st>>>(scene_view(c), sl.nv, c->shadow_rays, c->shadow_start,
+                                                     &sl.cnt->shadow_count, c->cap_nee, fetch, sl.cnt, 2, nullptr,
+                                                     nullptr);
+    return cudaGetLastError();
+  }
   cudaMemsetAsync(fetch_b, 0, sizeof(int), st);
   k_trace_shadow<<<blocks, kTraceThreads, 0, st>>>(scene_view(c), sl.nv, c->shadow_rays, c->shadow_start,
                                                    &sl.cnt->shadow_count, c->cap_nee, fetch, sl.cnt, 0,

@@ -316,15 +316,19 @@ def test_bvh_axis_aligned_and_tiny_direction_rays(neb, oracle):
     assert np.all(gp[op >= 0] >= 0)
 
 
+@pytest.mark.parametrize("tiles", [20, 120])
 @pytest.mark.parametrize("first", [True, False])
-def test_shadow_of_primitive_zero(neb, oracle, first):
+def test_shadow_of_primitive_zero(neb, oracle, first, tiles):
     """A single blocking triangle between a sphere light and a plane, stored
     as primitive 0 (its leaf link is ~0 = -1) or last: the NEE image of
-    direct light (D = 2) matches the oracle pixel by pixel, umbra included."""
+    direct light (D = 2) matches the oracle pixel by pixel, umbra included.
+    The plane of 20 x 20 tiles gives a small tree (one shadow walk from the
+    root), 120 x 120 a tree large enough for the near-origin walk first."""
     from paper_1909_00573_gb300 import scenes
     base = scenes.plane_under_sphere()
     blocker = np.array([[[-0.25, 0.5, -0.15], [0.25, 0.5, -0.15], [0.0, 0.5, 0.35]]], np.float32)
-    tri = np.concatenate([blocker, base.tri] if first else [base.tri, blocker], 0)
+    plane = scenes.ground_tiles(-50.0, -50.0, 50.0, 50.0, tiles).astype(np.float32)
+    tri = np.concatenate([blocker, plane] if first else [plane, blocker], 0)
     s = scenes.Scene(tri, np.zeros(len(tri)), base.sph, base.sph_mat, base.mats, base.cam, "blocked_plane")
     rc = scenes.RenderConfig(64, 64, 2, 0.01, 1 << 14, 4, 2, strategy_mask=2)
     ctx = neb.render(s, rc)
