@@ -176,11 +176,11 @@ def load_peaks():
 TRAFFIC_SOURCES = ("paper_1909_00573_gb300/csrc/neb_trace.cu", "paper_1909_00573_gb300/csrc/neb_device.cuh",
                    "paper_1909_00573_gb300/csrc/neb_types.h")
 NCU_TRAFFIC = {  # (workload, stage): DRAM bytes per launch from one ncu capture of these sources
-    ("large_city", "trace_camera"): {"bytes_per_launch": 73612185,
-                                     "sources_sha256": "ed2caf3427351663b3807b3a6f3f19367c608f938ab03b3b766c46a08b7725d6",
+    ("large_city", "trace_camera"): {"bytes_per_launch": 73595264,
+                                     "sources_sha256": "afee030ef903c525ac56b45f607fb4fabde1e33e6e4f75029c1adb627efe2e76",
                                      "profile": "profiles/k_trace_closest_large_city.md"},
-    ("large_city", "shadow"): {"bytes_per_launch": 217710336,   # mean of the two launches of an iteration
-                               "sources_sha256": "ed2caf3427351663b3807b3a6f3f19367c608f938ab03b3b766c46a08b7725d6",
+    ("large_city", "shadow"): {"bytes_per_launch": 217656448,   # mean of the two launches of an iteration
+                               "sources_sha256": "afee030ef903c525ac56b45f607fb4fabde1e33e6e4f75029c1adb627efe2e76",
                                "profile": "profiles/k_trace_shadow_large_city.md"},
 }
 
