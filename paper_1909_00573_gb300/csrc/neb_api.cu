@@ -183,6 +183,10 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
   ok = ok && dalloc(&c->shadow_rays, c->cap_nee) == cudaSuccess && dalloc(&c->shadow_start, c->cap_nee) == cudaSuccess &&
        dalloc(&c->shadow_rays_b, c->cap_nee) == cudaSuccess && dalloc(&c->shadow_start_b, c->cap_nee) == cudaSuccess &&
        dalloc(&c->group_counters, group_counter_ints()) == cudaSuccess;
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  ok = ok && cudaStreamCreateWithPriority(&c->stream_hi, cudaStreamNonBlocking, prio_hi) == cudaSuccess &&
+       cudaEventCreateWithFlags(&c->ev_caller, cudaEventDisableTiming) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&c->stream_b, cudaStreamNonBlocking) == cudaSuccess &&
        cudaStreamCreateWithFlags(&c->stream_cap, cudaStreamNonBlocking) == cudaSuccess;
   for (int k = 0; k < 2 && ok; ++k)
@@ -213,6 +217,7 @@ extern "C" void neb_destroy(neb_ctx* c) {
   free_scene(c);
   cudaFree(c->camq[0]); cudaFree(c->camq[1]); cudaFree(c->camq_grouped);
   if (c->stream_b) cudaStreamSynchronize(c->stream_b);
+  if (c->stream_hi) cudaStreamSynchronize(c->stream_hi);
   for (IterSlot& sl : c->slots) {
     cudaFree(sl.nv.pos); cudaFree(sl.nv.nrm); cudaFree(sl.nv.wo); cudaFree(sl.nv.tau); cudaFree(sl.nv.err);
     cudaFree(sl.nv.ldir); cudaFree(sl.nv.dE); cudaFree(sl.nv.lit); cudaFree(sl.nv.prim); cudaFree(sl.rh); cudaFree(sl.slot_map);
@@ -234,6 +239,8 @@ extern "C" void neb_destroy(neb_ctx* c) {
     if (c->graph_pass23[k]) cudaGraphExecDestroy(c->graph_pass23[k]);
   }
   if (c->stream_b) cudaStreamDestroy(c->stream_b);
+  if (c->stream_hi) cudaStreamDestroy(c->stream_hi);
+  if (c->ev_caller) cudaEventDestroy(c->ev_caller);
   if (c->stream_cap) cudaStreamDestroy(c->stream_cap);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;

@@ -194,6 +194,8 @@ struct neb_ctx {
   // passes 2-3 run on stream_b, overlapped with the next iteration's pass 1
   // on `stream`; ev_pass1[s] / ev_pass23[s] mark the end of each half for slot s
   cudaStream_t stream_b = nullptr;
+  cudaStream_t stream_hi = nullptr;   // pass 1 of the overlapped schedule, at the device's highest priority
+  cudaEvent_t ev_caller = nullptr;    // work the caller enqueued before an iteration
   cudaEvent_t ev_pass1[2] = {nullptr, nullptr}, ev_pass23[2] = {nullptr, nullptr};
   // overlapped iterations launch each half as a CUDA graph, recorded on
   // stream_cap every iteration and applied to the slot's executable graph

@@ -995,10 +995,14 @@ cudaError_t run_iteration(neb_ctx* c, int iteration, bool overlap) {
     tm.collect();
     return e;
   }
-  // Pass 1 on the caller's stream, passes 2-3 on stream_b.  Slot reuse: pass 1
-  // of this iteration waits for passes 2-3 of iteration - 2.
+  // Pass 1 on stream_hi (the device's highest stream priority, so its blocks
+  // are scheduled ahead of the overlapped passes 2-3), passes 2-3 on stream_b.
+  // Slot reuse: pass 1 of this iteration waits for passes 2-3 of iteration - 2.
   const int slot = iteration & 1;
-  cudaStream_t st = c->stream, st2 = c->stream_b;
+  cudaStream_t st = c->stream_hi, st2 = c->stream_b;
+  // pass 1 follows whatever the caller enqueued on its stream before this iteration
+  cudaEventRecord(c->ev_caller, c->stream);
+  cudaStreamWaitEvent(st, c->ev_caller, 0);
   // one half as a graph, or enqueued directly if graphs are off or the
   // recording fails (then they stay off for this context)
   auto half = [&](cudaGraphExec_t& exec, cudaStream_t to, auto enqueue) {
