@@ -129,10 +129,12 @@ int neb_build_bvh(neb_ctx* ctx);
 int neb_bvh_cost(neb_ctx* ctx, double* out);
 
 /* Enqueues n_iterations NEB iterations (asynchronous).  Iteration indices
- * continue from the previous call (1-based).  Passes 2-3 of an iteration run
- * on a second stream owned by the context and overlap pass 1 of the next
- * iteration; before the call returns, the context stream is made to wait for
- * the last iteration, so work enqueued on it afterwards sees every result. */
+ * continue from the previous call (1-based).  The iterations run on two
+ * streams owned by the context, after the work already enqueued on the
+ * context stream: pass 1 on a high-priority stream, passes 2-3 of an
+ * iteration on a second one, overlapping pass 1 of the next iteration; before
+ * the call returns, the context stream is made to wait for the last
+ * iteration, so work enqueued on it afterwards sees every result. */
 int neb_iterate(neb_ctx* ctx, int n_iterations);
 
 /* Progressive display: enqueues n_iterations iterations like neb_iterate and,
