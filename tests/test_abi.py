@@ -52,6 +52,8 @@ def test_argument_errors_without_gpu(libneb):
     cfg = neb.Config(8, 8, 4, 0.01, 64, 4, 0, 0, 0, 7, 0, 5)       # unknown BVH builder
     assert L.neb_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
     assert L.neb_iterate(None, 1) == -1
+    assert L.neb_iterate_read(None, 1, None) == -1
+    assert L.neb_bvh_cost(None, None) == -1
     assert L.neb_philox(None, -1, None, None) == -1
 
 
