@@ -169,34 +169,54 @@ typedef struct {
 
 static double mean3(const float* e) { return ((double)e[0] + (double)e[1] + (double)e[2]) / 3.0; }
 
-static void build_alias(scene_t* s) {
-  int n = s->nl;
-  s->alias_prob = (float*)calloc(n > 0 ? n : 1, sizeof(float));
-  s->alias_idx = (int*)calloc(n > 0 ? n : 1, sizeof(int));
-  if (n == 0) return;
+/* Vose's alias table (Vose 1991) for choosing item i with probability
+ * w_i / sum w: cell i keeps i with probability prob[i] and otherwise gives
+ * alias[i]; cells start at n w_i / sum w, and each cell below 1 is paired with
+ * one above 1, which gives up the difference. */
+static void alias_build(const double* w, int n, double* psel, float* prob, int* alias) {
   double total = 0.0;
-  for (int i = 0; i < n; ++i) total += s->lights[i].power;
-  double* p = (double*)malloc(sizeof(double) * n);
-  int* small = (int*)malloc(sizeof(int) * n);
-  int* large = (int*)malloc(sizeof(int) * n);
+  for (int i = 0; i < n; ++i) total += w[i];
+  double* p = (double*)malloc(sizeof(double) * (size_t)n);
+  int* small = (int*)malloc(sizeof(int) * (size_t)n);
+  int* large = (int*)malloc(sizeof(int) * (size_t)n);
   int ns = 0, nl = 0;
   for (int i = 0; i < n; ++i) {
-    s->lights[i].psel = s->lights[i].power / total;
-    p[i] = s->lights[i].power * (double)n / total;
-    s->alias_idx[i] = i;
+    psel[i] = w[i] / total;
+    p[i] = w[i] * (double)n / total;
+    alias[i] = i;
     if (p[i] < 1.0) small[ns++] = i; else large[nl++] = i;
   }
   while (ns > 0 && nl > 0) {
     int l = small[--ns];
     int g = large[--nl];
-    s->alias_prob[l] = (float)p[l];
-    s->alias_idx[l] = g;
+    prob[l] = (float)p[l];
+    alias[l] = g;
     p[g] = (p[g] + p[l]) - 1.0;
     if (p[g] < 1.0) small[ns++] = g; else large[nl++] = g;
   }
-  while (nl > 0) { int g = large[--nl]; s->alias_prob[g] = 1.0f; }
-  while (ns > 0) { int l = small[--ns]; s->alias_prob[l] = 1.0f; }
+  while (nl > 0) { int g = large[--nl]; prob[g] = 1.0f; }
+  while (ns > 0) { int l = small[--ns]; prob[l] = 1.0f; }
   free(p); free(small); free(large);
+}
+
+/* Item chosen by the random word x0 (cell: its top 24 bits scaled to n) and
+ * the uniform ua (keep the cell or take its alias). */
+static int alias_pick(const float* prob, const int* alias, int n, uint32_t x0, float ua) {
+  int i = (int)(((uint64_t)(x0 >> 8) * (uint64_t)n) >> 24);
+  return ua < prob[i] ? i : alias[i];
+}
+
+static void build_alias(scene_t* s) {
+  int n = s->nl;
+  s->alias_prob = (float*)calloc(n > 0 ? n : 1, sizeof(float));
+  s->alias_idx = (int*)calloc(n > 0 ? n : 1, sizeof(int));
+  if (n == 0) return;
+  double* w = (double*)calloc((size_t)n, sizeof(double));
+  double* psel = (double*)calloc((size_t)n, sizeof(double));
+  for (int i = 0; i < n; ++i) w[i] = s->lights[i].power;
+  alias_build(w, n, psel, s->alias_prob, s->alias_idx);
+  for (int i = 0; i < n; ++i) s->lights[i].psel = psel[i];
+  free(w); free(psel);
 }
 
 static v3 tri_v(const scene_t* s, int t, int k) { return vload(s->tri + (size_t)t * 9 + k * 3); }
@@ -276,114 +296,134 @@ static void scene_free(scene_t* s) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* ray / primitive intersection                                              */
+/* ray / primitive intersection (FP32, as the renderer traces its rays)      */
 /* ------------------------------------------------------------------------ */
-#define GAMMA2 1.19209304e-07f
-#define GAMMA3 1.78813966e-07f
-#define GAMMA5 2.98023313e-07f
-#define GAMMA7 4.17232688e-07f
+/* gamma_n = n u / (1 - n u), u = 2^-24: bound on the relative rounding error
+ * of n chained FP32 operations (Pharr, Jakob, Humphreys, PBRT 3rd ed.,
+ * Sec. 3.9.1). */
+static float gamma_f32(int n) {
+  double u = ldexp(1.0, -24);
+  return (float)((double)n * u / (1.0 - (double)n * u));
+}
 
 typedef struct {
   v3 o, d;
-  int kx, ky, kz;
-  float Sx, Sy, Sz;
+  int k[3];          /* k[2]: axis of the largest |d| component (lowest on ties); k[0], k[1] the others, in winding order */
+  float shear[3];    /* d[k0] / d[k2], d[k1] / d[k2], 1 / d[k2] */
 } ray_t;
 
 static ray_t make_ray(v3 o, v3 d) {
   ray_t r;
-  r.o = o; r.d = d;
-  float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
-  int kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
-  int kx = (kz + 1) % 3, ky = (kx + 1) % 3;
-  if (vget(d, kz) < 0.0f) { int t = kx; kx = ky; ky = t; }
-  r.kx = kx; r.ky = ky; r.kz = kz;
-  float dz = vget(d, kz);
-  r.Sx = vget(d, kx) / dz;
-  r.Sy = vget(d, ky) / dz;
-  r.Sz = 1.0f / dz;
+  r.o = o;
+  r.d = d;
+  const float dd[3] = {d.x, d.y, d.z};
+  int z = 0;
+  for (int i = 1; i < 3; ++i)
+    if (fabsf(dd[i]) > fabsf(dd[z])) z = i;
+  r.k[0] = (z + 1) % 3;
+  r.k[1] = (z + 2) % 3;
+  r.k[2] = z;
+  if (dd[z] < 0.0f) { int t = r.k[0]; r.k[0] = r.k[1]; r.k[1] = t; }
+  r.shear[0] = dd[r.k[0]] / dd[z];
+  r.shear[1] = dd[r.k[1]] / dd[z];
+  r.shear[2] = 1.0f / dd[z];
   return r;
 }
 
-/* Watertight ray/triangle test (Woop, Benthin, Wald, JCGT 2(1), 2013),
- * including its double-precision re-evaluation of zero edge functions, with
- * the conservative lower bound on t of Pharr, Jakob and Humphreys (PBRT 3rd
- * ed., Sec. 3.9.6): hits closer than the test's own rounding error deltaT are
- * rejected, so a ray never re-hits the surface it starts on.
- * Returns 1 and the distance when the ray meets the triangle at t > deltaT; bary
- * (may be NULL) receives U/det, V/det, W/det, the barycentric weights of
- * v0, v1, v2. */
-static int isect_tri_b(const ray_t* r, v3 v0, v3 v1, v3 v2, float* t_out, float* bary) {
-  v3 A = vsub(v0, r->o), B = vsub(v1, r->o), C = vsub(v2, r->o);
-  float Akz = vget(A, r->kz), Bkz = vget(B, r->kz), Ckz = vget(C, r->kz);
-  float Ax = vget(A, r->kx) - r->Sx * Akz;
-  float Ay = vget(A, r->ky) - r->Sy * Akz;
-  float Bx = vget(B, r->kx) - r->Sx * Bkz;
-  float By = vget(B, r->ky) - r->Sy * Bkz;
-  float Cx = vget(C, r->kx) - r->Sx * Ckz;
-  float Cy = vget(C, r->ky) - r->Sy * Ckz;
-  float U = Cx * By - Cy * Bx;
-  float V = Ax * Cy - Ay * Cx;
-  float W = Bx * Ay - By * Ax;
-  if (U == 0.0f || V == 0.0f || W == 0.0f) {
-    U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
-    V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
-    W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+/* Watertight ray/triangle test (Woop, Benthin and Wald, "Watertight
+ * Ray/Triangle Intersection", JCGT 2(1), 2013).  The vertices are taken into
+ * the frame in which the ray starts at the origin and runs along +z
+ * (translation, the ray's axis permutation, shear); the 2D edge functions of
+ * the sheared triangle tell by their signs whether the ray passes inside (all
+ * >= 0 or all <= 0).  An edge shared by two triangles gives the same edge
+ * function, of opposite sign, in both, so no ray slips between them; when an
+ * edge function rounds to zero in FP32 all three are evaluated again in FP64.
+ * Hits closer than the test's own rounding error (the bound deltaT of PBRT
+ * 3rd ed., Sec. 3.9.6) are rejected, so a ray does not find the surface it
+ * leaves.  Returns 1 with the distance t and the barycentric weights of
+ * v0, v1, v2 (bary may be NULL), or 0 for a miss. */
+static int tri_hit(const ray_t* r, v3 v0, v3 v1, v3 v2, float* t_out, float* bary) {
+  const v3 vs[3] = {v0, v1, v2};
+  const float org[3] = {r->o.x, r->o.y, r->o.z};
+  float sx[3], sy[3], along[3];
+  for (int i = 0; i < 3; ++i) {
+    const float v[3] = {vs[i].x, vs[i].y, vs[i].z};
+    float rel[3];
+    for (int c = 0; c < 3; ++c) rel[c] = v[c] - org[c];
+    along[i] = rel[r->k[2]];
+    sx[i] = rel[r->k[0]] - r->shear[0] * along[i];
+    sy[i] = rel[r->k[1]] - r->shear[1] * along[i];
   }
-  if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return 0;
-  float det = U + V + W;
+  float e[3];   /* e[i]: edge function of the edge opposite vertex i */
+  for (int i = 0; i < 3; ++i) {
+    int a = (i + 2) % 3, b = (i + 1) % 3;
+    e[i] = sx[a] * sy[b] - sy[a] * sx[b];
+  }
+  if (e[0] == 0.0f || e[1] == 0.0f || e[2] == 0.0f)
+    for (int i = 0; i < 3; ++i) {
+      int a = (i + 2) % 3, b = (i + 1) % 3;
+      e[i] = (float)((double)sx[a] * (double)sy[b] - (double)sy[a] * (double)sx[b]);
+    }
+  int below = e[0] < 0.0f || e[1] < 0.0f || e[2] < 0.0f;
+  int above = e[0] > 0.0f || e[1] > 0.0f || e[2] > 0.0f;
+  if (below && above) return 0;
+  float det = e[0] + e[1] + e[2];
   if (det == 0.0f) return 0;
-  float Az = r->Sz * Akz, Bz = r->Sz * Bkz, Cz = r->Sz * Ckz;
-  float T = U * Az + V * Bz + W * Cz;
-  float Ts = T, dets = det;
-  if (dets < 0.0f) { Ts = -Ts; dets = -dets; }
-  if (Ts <= 0.0f) return 0;
-  float t = Ts / dets;
-  /* rounding-error bound of t (gamma_n = n eps / (1 - n eps), eps = 2^-24) */
-  float maxZ = fmaxf(fabsf(Az), fmaxf(fabsf(Bz), fabsf(Cz)));
-  float maxX = fmaxf(fabsf(Ax), fmaxf(fabsf(Bx), fabsf(Cx)));
-  float maxY = fmaxf(fabsf(Ay), fmaxf(fabsf(By), fabsf(Cy)));
-  float maxE = fmaxf(fabsf(U), fmaxf(fabsf(V), fabsf(W)));
-  float dZ = GAMMA3 * maxZ;
-  float dX = GAMMA5 * (maxX + maxZ);
-  float dY = GAMMA5 * (maxY + maxZ);
-  float dE = 2.0f * (GAMMA2 * maxX * maxY + dY * maxX + dX * maxY);
-  float dT = 3.0f * (GAMMA3 * maxE * maxZ + dE * maxZ + dZ * maxE) / dets;
-  if (!(t > dT)) return 0;
+  float sz[3];
+  for (int i = 0; i < 3; ++i) sz[i] = r->shear[2] * along[i];
+  float T = e[0] * sz[0] + e[1] * sz[1] + e[2] * sz[2];
+  /* the hit is in front when T has the sign of det */
+  float Tp = det < 0.0f ? -T : T, detp = det < 0.0f ? -det : det;
+  if (Tp <= 0.0f) return 0;
+  float t = Tp / detp;
+  /* deltaT: error bounds of the sheared coordinates, of the edge functions
+     and of T, each the largest magnitude times gamma (PBRT Sec. 3.9.6) */
+  float mx = 0.0f, my = 0.0f, mz = 0.0f, me = 0.0f;
+  for (int i = 0; i < 3; ++i) {
+    mx = fmaxf(mx, fabsf(sx[i]));
+    my = fmaxf(my, fabsf(sy[i]));
+    mz = fmaxf(mz, fabsf(sz[i]));
+    me = fmaxf(me, fabsf(e[i]));
+  }
+  float err_z = gamma_f32(3) * mz;
+  float err_x = gamma_f32(5) * (mx + mz);
+  float err_y = gamma_f32(5) * (my + mz);
+  float err_e = 2.0f * (gamma_f32(2) * mx * my + err_y * mx + err_x * my);
+  float err_t = 3.0f * (gamma_f32(3) * me * mz + err_e * mz + err_z * me) / detp;
+  if (!(t > err_t)) return 0;
   *t_out = t;
-  if (bary) { bary[0] = U / det; bary[1] = V / det; bary[2] = W / det; }
+  if (bary)
+    for (int i = 0; i < 3; ++i) bary[i] = e[i] / det;
   return 1;
 }
 
-static int isect_tri(const ray_t* r, v3 v0, v3 v1, v3 v2, float* t_out) {
-  return isect_tri_b(r, v0, v1, v2, t_out, NULL);
-}
-
-/* Ray/sphere with the cancellation-free discriminant of Haines, Guenther and
- * Akenine-Moeller ("Precision Improvements for Ray/Sphere Intersection",
- * Ray Tracing Gems, 2019).  d must be unit length. */
-static int isect_sph(const ray_t* r, const float* sp, float* t_out) {
-  v3 c = vload(sp);
-  float R = sp[3];
-  v3 oc = vsub(r->o, c);
-  float b = vdot(oc, r->d);
-  v3 qv = vsub(oc, vmul(r->d, b));
-  float disc = R * R - vdot(qv, qv);
+/* Ray/sphere, with the discriminant taken from the distance between the
+ * centre and the ray's line (Haines, Guenther and Akenine-Moeller, "Precision
+ * Improvements for Ray/Sphere Intersection", Ray Tracing Gems, 2019).  d is
+ * unit length.  Nearest t > 0. */
+static int sph_hit(const ray_t* r, const float* sp, float* t_out) {
+  const float org[3] = {r->o.x, r->o.y, r->o.z}, dir[3] = {r->d.x, r->d.y, r->d.z};
+  const float R = sp[3];
+  float oc[3], along = 0.0f, oc2 = 0.0f, perp2 = 0.0f;
+  for (int c = 0; c < 3; ++c) oc[c] = org[c] - sp[c];
+  for (int c = 0; c < 3; ++c) along += oc[c] * dir[c];
+  for (int c = 0; c < 3; ++c) { float q = oc[c] - dir[c] * along; perp2 += q * q; }
+  for (int c = 0; c < 3; ++c) oc2 += oc[c] * oc[c];
+  float disc = R * R - perp2;
   if (disc < 0.0f) return 0;
-  float c2 = vdot(oc, oc) - R * R;
-  float sq = sqrtf(disc);
-  float q = (b > 0.0f) ? (-b - sq) : (-b + sq);
-  if (q == 0.0f) return 0;
-  float t0 = c2 / q, t1 = q;
-  if (t0 > t1) { float t = t0; t0 = t1; t1 = t; }
-  float t = (t0 > 0.0f) ? t0 : t1;
+  float root = along > 0.0f ? -along - sqrtf(disc) : -along + sqrtf(disc);
+  if (root == 0.0f) return 0;
+  float near = (oc2 - R * R) / root, far = root;
+  if (near > far) { float t = near; near = far; far = t; }
+  float t = near > 0.0f ? near : far;
   if (!(t > 0.0f)) return 0;
   *t_out = t;
   return 1;
 }
 
 static int isect_prim(const scene_t* s, const ray_t* r, int prim, float* t) {
-  if (prim < s->nt) return isect_tri(r, tri_v(s, prim, 0), tri_v(s, prim, 1), tri_v(s, prim, 2), t);
-  return isect_sph(r, s->sph + (size_t)(prim - s->nt) * 4, t);
+  if (prim < s->nt) return tri_hit(r, tri_v(s, prim, 0), tri_v(s, prim, 1), tri_v(s, prim, 2), t, NULL);
+  return sph_hit(r, s->sph + (size_t)(prim - s->nt) * 4, t);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -585,26 +625,34 @@ static int trace_any(const scene_t* s, const bvh_t* b, v3 o, v3 d, float tmax) {
   return 0;
 }
 
-/* Hit point and its floating-point error bound.  Triangles: the point is
- * rebuilt from the watertight test's barycentrics, b0 v0 + b1 v1 + b2 v2,
- * with the per-component bound gamma_7 (|b0 v0| + |b1 v1| + |b2 v2|) of Pharr,
- * Jakob and Humphreys (PBRT 3rd ed., Sec. 3.9.3).  Spheres: o + t d with the
- * bound gamma_5 |p| (spheres only end paths). */
+/* Hit point and the bound that sizes the offset of the next ray's origin.
+ * Triangles: the point b0 v0 + b1 v1 + b2 v2 from the barycentric weights of
+ * the hit, with the bound gamma_7 (|b0 v0| + |b1 v1| + |b2 v2|) per component
+ * (Pharr, Jakob and Humphreys, PBRT 3rd ed., Sec. 3.9.3).  Spheres: o + t d
+ * with the bound gamma_5 |p| (spheres only end paths). */
 static void hit_point(const scene_t* s, v3 o, v3 d, int prim, float t, v3* p, v3* err) {
   if (prim < s->nt) {
     ray_t r = make_ray(o, d);
-    v3 v0 = tri_v(s, prim, 0), v1 = tri_v(s, prim, 1), v2 = tri_v(s, prim, 2);
+    const v3 v[3] = {tri_v(s, prim, 0), tri_v(s, prim, 1), tri_v(s, prim, 2)};
     float tt, b[3];
-    if (isect_tri_b(&r, v0, v1, v2, &tt, b)) {
-      *p = vadd(vadd(vmul(v0, b[0]), vmul(v1, b[1])), vmul(v2, b[2]));
-      *err = mk3(GAMMA7 * (fabsf(v0.x * b[0]) + fabsf(v1.x * b[1]) + fabsf(v2.x * b[2])),
-                 GAMMA7 * (fabsf(v0.y * b[0]) + fabsf(v1.y * b[1]) + fabsf(v2.y * b[2])),
-                 GAMMA7 * (fabsf(v0.z * b[0]) + fabsf(v1.z * b[1]) + fabsf(v2.z * b[2])));
+    if (tri_hit(&r, v[0], v[1], v[2], &tt, b)) {
+      float q[3] = {0.0f, 0.0f, 0.0f}, e[3] = {0.0f, 0.0f, 0.0f};
+      for (int i = 0; i < 3; ++i) {
+        const float vi[3] = {v[i].x, v[i].y, v[i].z};
+        for (int c = 0; c < 3; ++c) {
+          q[c] += vi[c] * b[i];
+          e[c] += fabsf(vi[c] * b[i]);
+        }
+      }
+      const float g7 = gamma_f32(7);
+      *p = mk3(q[0], q[1], q[2]);
+      *err = mk3(g7 * e[0], g7 * e[1], g7 * e[2]);
       return;
     }
   }
   *p = vadd(o, vmul(d, t));
-  *err = mk3(GAMMA5 * fabsf(p->x), GAMMA5 * fabsf(p->y), GAMMA5 * fabsf(p->z));
+  const float g5 = gamma_f32(5);
+  *err = mk3(g5 * fabsf(p->x), g5 * fabsf(p->y), g5 * fabsf(p->z));
 }
 
 /* New ray origin: the hit point moved along the geometric normal, to the side
@@ -731,206 +779,316 @@ static int bsdf_sample(const mat_t* m, v3 n, v3 wo, float ul, float u1, float u2
 }
 
 /* ------------------------------------------------------------------------ */
-/* Density octree: Sec. 5 and the listing of Appendix B.  Sequential form of */
-/* the listing's lock-free operations, FP32 as in the listing, with the      */
-/* final density normalisation in FP64.                                      */
+/* Density octree (Sec. 5): a sparse tree of cells, each holding the number */
+/* of NEE vertices counted in it.  Written as an explicit tree of cells; the */
+/* flat word layout of Sec. 5.5 (siblings in eight consecutive words, a      */
+/* split cell holding the negated index of its first child) appears only in */
+/* orc_octree_dump, where each cell's word index is its allocation order.    */
 /* ------------------------------------------------------------------------ */
+
+/* Plane/box intersection area, Eq. area (Sec. 5.3), in FP64.  Appendix A
+ * derives it as the h-derivative of the box volume below the plane
+ * <n, y> = h: over the d axes the normal is not perpendicular to,
+ *   A = (prod of the box extents along the other axes)
+ *       * | sum over the 2^d corners b of the box in those axes of
+ *           eps_b max(0, h - <n, b>)^(d-1) | / ((d-1)! prod n_i),
+ * with h = <n, p>, eps_b = +1 for an even and -1 for an odd number of upper
+ * bounds among b's coordinates.  The paper's implementation decides d from
+ * the FP32 normal: an axis whose |n_i| is within 1e-3 of 1 gives d = 1 and
+ * the area of the box's face across that axis (the first such axis, in x, y,
+ * z order); otherwise the first axis with |n_i| < 1e-4 is taken as
+ * perpendicular (d = 2); otherwise d = 3.  These decisions are made on the
+ * FP32 components, as the paper does. */
+static double plane_box_area(const double lo[3], const double hi[3], const double p[3], const float n[3]) {
+  int axes[3], d = 0;
+  for (int i = 0; i < 3; ++i)
+    if (fabsf(fabsf(n[i]) - 1.0f) < 1e-3f) {
+      /* d = 1: the plane is taken as parallel to the face across axis i */
+      double a = 1.0;
+      for (int j = 0; j < 3; ++j) if (j != i) a *= hi[j] - lo[j];
+      return a;
+    }
+  int dropped = -1;
+  for (int i = 0; i < 3 && dropped < 0; ++i) if (fabsf(n[i]) < 1e-4f) dropped = i;
+  for (int i = 0; i < 3; ++i) if (i != dropped) axes[d++] = i;
+  double h = 0.0, prod_n = 1.0;
+  for (int k = 0; k < d; ++k) { h += (double)n[axes[k]] * p[axes[k]]; prod_n *= (double)n[axes[k]]; }
+  double sum = 0.0;
+  for (int corner = 0; corner < (1 << d); ++corner) {
+    double nb = 0.0;
+    int uppers = 0;
+    for (int k = 0; k < d; ++k) {
+      int up = (corner >> k) & 1;
+      uppers += up;
+      nb += (double)n[axes[k]] * (up ? hi[axes[k]] : lo[axes[k]]);
+    }
+    double m = h - nb > 0.0 ? h - nb : 0.0;
+    double term = d == 3 ? m * m : m;
+    sum += (uppers & 1) ? -term : term;
+  }
+  double fact = d == 3 ? 2.0 : 1.0;  /* (d-1)! */
+  double a = fabs(sum / (fact * prod_n));
+  if (dropped >= 0) a *= hi[dropped] - lo[dropped];
+  return a;
+}
+
+double orc_intersection_area(const float bmin[3], const float bmax[3], const float pos[3], const float n[3]) {
+  double lo[3], hi[3], p[3];
+  for (int c = 0; c < 3; ++c) { lo[c] = bmin[c]; hi[c] = bmax[c]; p[c] = pos[c]; }
+  return plane_box_area(lo, hi, p, n);
+}
+
+typedef struct oct_cell {
+  int32_t count;          /* vertices counted here (leaves) */
+  int32_t word;           /* index in the flat layout (allocation order) */
+  struct oct_cell* kids;  /* NULL for a leaf, else 8 cells in octant order x + 2y + 4z */
+} oct_cell;
+
 struct orc_octree {
-  int32_t* nodes;
-  int32_t alloc, depth, capacity;
+  oct_cell root;
+  int32_t words_used;     /* root + 8 per split; capacity + 1 once a split found no room */
+  int32_t capacity;       /* words available: requested capacity rounded up to 8m + 1 */
+  int32_t depth;          /* deepest level that holds a cell */
   float minb[3], size_inv[3], scene_scale;
-  int split_factor, split_count, iter_clamp, stop_filling;
+  int split_factor;
+  int iteration;          /* current 1-based iteration */
+  int iter_clamp;         /* min(iteration, 1000): densities are divided by it */
+  int32_t threshold;      /* a cell splits when its count reaches split_factor * iter_clamp */
+  int32_t fresh_count;    /* count a cell created in this iteration starts with */
 };
 
-#define OCT_FILL_ITERATIONS 1000
-#define OCT_MAX_DEPTH 30
-
-float orc_intersection_area(const float bmin[3], const float bmax[3], const float pos[3], const float n[3]) {
-  /* Eq. area with the listing's thresholds for the 1D and 2D cases. */
-  float cs[3] = {bmax[0] - bmin[0], bmax[1] - bmin[1], bmax[2] - bmin[2]};
-  float an[3] = {fabsf(n[0]), fabsf(n[1]), fabsf(n[2])};
-  if (fabsf(an[0] - 1.0f) < 1e-3f) return cs[1] * cs[2];
-  if (fabsf(an[1] - 1.0f) < 1e-3f) return cs[0] * cs[2];
-  if (fabsf(an[2] - 1.0f) < 1e-3f) return cs[0] * cs[1];
-  for (int d = 0; d < 3; ++d) {
-    if (an[d] < 1e-4f) {
-      int x = (d + 1) % 3, y = (d + 2) % 3;
-      float h = n[x] * pos[x] + n[y] * pos[y];
-      float s = 0.0f;
-      s += fmaxf(0.0f, h - (n[x] * bmin[x] + n[y] * bmin[y]));
-      s -= fmaxf(0.0f, h - (n[x] * bmin[x] + n[y] * bmax[y]));
-      s -= fmaxf(0.0f, h - (n[x] * bmax[x] + n[y] * bmin[y]));
-      s += fmaxf(0.0f, h - (n[x] * bmax[x] + n[y] * bmax[y]));
-      return cs[d] * fabsf(s / (n[x] * n[y]));
-    }
-  }
-  float h = n[0] * pos[0] + n[1] * pos[1] + n[2] * pos[2];
-  float s = 0.0f;
-  /* corners in the listing's order; parity +1 for an even number of max coordinates */
-  {
-    float t;
-    t = fmaxf(0.0f, h - (n[0] * bmin[0] + n[1] * bmin[1] + n[2] * bmin[2])); s += t * t;
-    t = fmaxf(0.0f, h - (n[0] * bmin[0] + n[1] * bmin[1] + n[2] * bmax[2])); s -= t * t;
-    t = fmaxf(0.0f, h - (n[0] * bmin[0] + n[1] * bmax[1] + n[2] * bmax[2])); s += t * t;
-    t = fmaxf(0.0f, h - (n[0] * bmin[0] + n[1] * bmax[1] + n[2] * bmin[2])); s -= t * t;
-    t = fmaxf(0.0f, h - (n[0] * bmax[0] + n[1] * bmax[1] + n[2] * bmin[2])); s += t * t;
-    t = fmaxf(0.0f, h - (n[0] * bmax[0] + n[1] * bmin[1] + n[2] * bmin[2])); s -= t * t;
-    t = fmaxf(0.0f, h - (n[0] * bmax[0] + n[1] * bmin[1] + n[2] * bmax[2])); s += t * t;
-    t = fmaxf(0.0f, h - (n[0] * bmax[0] + n[1] * bmax[1] + n[2] * bmax[2])); s -= t * t;
-  }
-  return fabsf(s / (2.0f * n[0] * n[1] * n[2]));
-}
+#define OCT_FILL_ITERATIONS 1000   /* counting stops after this many iterations (Appendix B) */
+#define OCT_MAX_DEPTH 30           /* no cell below level 30: 2^30 cells per axis */
 
 orc_octree* orc_octree_new(const float smin[3], const float smax[3], int capacity, int split_factor) {
   orc_octree* o = (orc_octree*)calloc(1, sizeof(orc_octree));
+  /* the box is the scene's, grown by 0.2 % about its centre so that points on
+     the scene's bounds fall inside (Appendix B) */
   float size[3];
   for (int c = 0; c < 3; ++c) size[c] = (smax[c] - smin[c]) * 1.002f;
-  for (int c = 0; c < 3; ++c) o->size_inv[c] = 1.0f / size[c];
+  for (int c = 0; c < 3; ++c) {
+    o->size_inv[c] = 1.0f / size[c];
+    o->minb[c] = smin[c] - size[c] * (0.001f / 1.002f);
+  }
   o->scene_scale = sqrtf(size[0] * size[0] + size[1] * size[1] + size[2] * size[2]);
-  for (int c = 0; c < 3; ++c) o->minb[c] = smin[c] - size[c] * (0.001f / 1.002f);
-  o->capacity = 1 + ((capacity + 7) & ~7);
-  o->nodes = (int32_t*)calloc((size_t)o->capacity, sizeof(int32_t));
-  o->alloc = 1;
-  o->nodes[0] = 0;
-  o->depth = 0;
+  o->capacity = 8 * ((capacity + 7) / 8) + 1;
+  o->root.word = 0;
+  o->words_used = 1;
   o->split_factor = split_factor;
   return o;
 }
 
-void orc_octree_free(orc_octree* o) { if (o) { free(o->nodes); free(o); } }
+static void cell_free(oct_cell* c) {
+  if (!c->kids) return;
+  for (int k = 0; k < 8; ++k) cell_free(&c->kids[k]);
+  free(c->kids);
+}
 
+void orc_octree_free(orc_octree* o) {
+  if (!o) return;
+  cell_free(&o->root);
+  free(o);
+}
+
+/* Counts are integrated over the iterations (Sec. 5.4): the split threshold
+ * grows with the iteration and densities are divided by it.  A new cell
+ * starts with a quarter of the split factor per iteration so far, since a
+ * surface crosses about four of a cell's eight children (Sec. 5.2). */
 void orc_octree_set_iteration(orc_octree* o, int iter) {
-  int ic = iter < OCT_FILL_ITERATIONS ? iter : OCT_FILL_ITERATIONS;
-  o->iter_clamp = ic;
-  o->stop_filling = iter > OCT_FILL_ITERATIONS;
-  o->split_count = o->split_factor * ic;
-  if (!o->stop_filling) {
-    int32_t init = (int32_t)ceilf((float)o->split_factor / 4.0f * (float)iter);
-    for (int i = o->alloc; i < o->capacity; ++i) o->nodes[i] = init;
+  o->iteration = iter;
+  o->iter_clamp = iter < OCT_FILL_ITERATIONS ? iter : OCT_FILL_ITERATIONS;
+  o->threshold = o->split_factor * o->iter_clamp;
+  if (iter <= OCT_FILL_ITERATIONS)   /* no cell is created later */
+    o->fresh_count = (o->split_factor * iter + 3) / 4;   /* ceil(split_factor * iter / 4) */
+}
+
+/* Position in units of the octree box, in FP32 as the paper computes it;
+ * returns 0 outside [0, 1)^3. */
+static int oct_unit_pos(const orc_octree* o, const float pos[3], float u[3]) {
+  for (int c = 0; c < 3; ++c) {
+    u[c] = (pos[c] - o->minb[c]) * o->size_inv[c];
+    if (!(u[c] >= 0.0f && u[c] < 1.0f)) return 0;
   }
+  return 1;
 }
 
-/* listing's split_node_if_necessary in sequential form; returns the (negated)
- * child index to descend into, or a non-negative value to stop */
-static int32_t oct_split(orc_octree* o, int idx, int32_t count, int depth) {
-  if (count >= o->split_count) {
-    if (depth + 1 > OCT_MAX_DEPTH) return 0;
-    if (count == o->split_count) {
-      int32_t child = o->alloc;
-      o->alloc += 8;
-      if (child >= o->capacity) { o->alloc = o->capacity + 1; return 0; }
-      o->nodes[idx] = -child;
-      if (depth + 1 > o->depth) o->depth = depth + 1;
-      return 0;
-    }
-    /* a sequential run never observes a count above the threshold that is
-       still waiting for its child pointer: either the split happened or
-       the allocation overflowed */
-    return o->nodes[idx] < 0 ? o->nodes[idx] : 0;
-  }
-  return count;
+/* Octant at `level` (>= 1) of the cell holding unit position u: on the grid
+ * of 2^level cells per axis the cell index is floor(u 2^level), and its
+ * lowest bit tells which half of the parent cell it lies in. */
+static int oct_octant(const float u[3], int level) {
+  float scale = ldexpf(1.0f, level);
+  int o = 0;
+  for (int c = 0; c < 3; ++c) o |= ((int)(u[c] * scale) & 1) << c;
+  return o;
 }
 
-static int32_t oct_inc(orc_octree* o, int idx) {
-  int32_t v = o->nodes[idx];
-  if (v < 0) return v;
-  o->nodes[idx] = v + 1;
-  return v + 1;
+static oct_cell* oct_leaf(const orc_octree* o, const float u[3], int* level) {
+  oct_cell* c = (oct_cell*)&o->root;
+  int L = 0;
+  while (c->kids) { ++L; c = &c->kids[oct_octant(u, L)]; }
+  *level = L;
+  return c;
 }
 
+/* One NEE vertex (Sec. 5.1): one more in the leaf cell that holds it; the
+ * vertex that brings a cell to the threshold splits it into eight children
+ * (Sec. 5.2).  That vertex stays counted in the cell it split (whose count
+ * is no longer read).  A split needs eight free words; when they are not
+ * there the tree stops growing and the full cell keeps counting. */
 void orc_octree_increment(orc_octree* o, const float pos[3]) {
-  if (o->stop_filling) return;
-  float np[3];
-  for (int c = 0; c < 3; ++c) np[c] = (pos[c] - o->minb[c]) * o->size_inv[c];
-  for (int c = 0; c < 3; ++c) if (!(np[c] >= 0.0f && np[c] < 1.0f)) return;
-  int32_t v = oct_inc(o, 0);
-  v = oct_split(o, 0, v, 0);
-  int edge = 1, depth = 0;
-  while (v < 0) {
-    edge *= 2;
-    ++depth;
-    int ix = ((int)(np[0] * (float)edge)) & 1;
-    int iy = ((int)(np[1] * (float)edge)) & 1;
-    int iz = ((int)(np[2] * (float)edge)) & 1;
-    int idx = ix + 2 * (iy + 2 * iz);
-    idx -= v;
-    v = oct_inc(o, idx);
-    v = oct_split(o, idx, v, depth);
+  if (o->iteration > OCT_FILL_ITERATIONS) return;
+  float u[3];
+  if (!oct_unit_pos(o, pos, u)) return;
+  int level;
+  oct_cell* c = oct_leaf(o, u, &level);
+  c->count += 1;
+  if (c->count != o->threshold || level >= OCT_MAX_DEPTH) return;
+  if (o->words_used + 8 > o->capacity) { o->words_used = o->capacity + 1; return; }
+  c->kids = (oct_cell*)calloc(8, sizeof(oct_cell));
+  for (int k = 0; k < 8; ++k) {
+    c->kids[k].count = o->fresh_count;
+    c->kids[k].word = o->words_used + k;
   }
+  o->words_used += 8;
+  if (level + 1 > o->depth) o->depth = level + 1;
 }
 
-/* get_density of the listing; *size receives the cell diagonal when size != NULL */
-static float oct_density(const orc_octree* o, const float pos[3], const float n[3], float* size) {
-  float off[3], np[3];
-  for (int c = 0; c < 3; ++c) { off[c] = pos[c] - o->minb[c]; np[c] = off[c] * o->size_inv[c]; }
-  for (int c = 0; c < 3; ++c) if (!(np[c] >= 0.0f && np[c] < 1.0f)) return 0.0f;
-  int grid = 1 << o->depth;
-  int ip[3];
-  for (int c = 0; c < 3; ++c) ip[c] = (int)(np[c] * (float)grid);
-  int32_t v = o->nodes[0];
-  int mask = grid;
-  while (v < 0) {
-    mask >>= 1;
-    int idx = ((ip[0] & mask) ? 1 : 0) + ((ip[1] & mask) ? 2 : 0) + ((ip[2] & mask) ? 4 : 0);
-    idx -= v;
-    v = o->nodes[idx];
+/* Density at p for a plane with normal n (Eq. octdensity): the count of the
+ * leaf cell holding p divided by the iteration count and by the area of the
+ * plane inside the cell, the area kept above a small fraction of the squared
+ * cell diagonal (0.1 of it for the centre query of the robust estimate, 0.01
+ * otherwise).  Empty cells and points outside the box give 0.  *diag
+ * receives the cell diagonal when the count is positive. */
+static double oct_density(const orc_octree* o, const float pos[3], const float n[3], int centre, float* diag) {
+  float u[3];
+  if (!oct_unit_pos(o, pos, u)) return 0.0;
+  int level;
+  const oct_cell* c = oct_leaf(o, u, &level);
+  if (c->count <= 0) return 0.0;
+  double lo[3], hi[3], p[3];
+  for (int a = 0; a < 3; ++a) {
+    double extent = ldexp(1.0 / (double)o->size_inv[a], -level);
+    double index = floor((double)u[a] * ldexp(1.0, level));
+    lo[a] = index * extent;
+    hi[a] = lo[a] + extent;
+    p[a] = (double)pos[a] - (double)o->minb[a];
   }
-  if (v > 0) {
-    int cur = grid / mask;
-    float cmin[3], cmax[3];
-    for (int c = 0; c < 3; ++c) {
-      float csz = 1.0f / ((float)cur * o->size_inv[c]);
-      int cp = ip[c] / mask;
-      cmin[c] = (float)cp * csz;
-      cmax[c] = cmin[c] + csz;
-    }
-    float area = orc_intersection_area(cmin, cmax, off, n);
-    float diag = o->scene_scale / (float)cur;
-    float min_area = diag * diag;
-    if (size) { *size = diag; min_area *= 0.1f; } else min_area *= 0.01f;
-    double rho = (double)v / ((double)o->iter_clamp * (double)fmaxf(min_area, area));
-    return (float)rho;
-  }
-  return 0.0f;
+  double area = plane_box_area(lo, hi, p, n);
+  double cell_diag = ldexp((double)o->scene_scale, -level);
+  double floor_area = cell_diag * cell_diag * (centre ? 0.1 : 0.01);
+  if (diag) *diag = ldexpf(o->scene_scale, -level);
+  return (double)c->count / ((double)o->iter_clamp * (area > floor_area ? area : floor_area));
 }
 
-/* get_density_robust of the listing: the median of the centre query and four
- * queries displaced by 1.1 cell diagonals along the tangents; ties go to the
- * greater value.  Tangents: Duff et al. basis of the geometric normal. */
+static int cmp_float(const void* a, const void* b) {
+  float x = *(const float*)a, y = *(const float*)b;
+  return (x > y) - (x < y);
+}
+
+/* Robust density: the centre query and four more at 1.1 cell diagonals from
+ * p along the two tangents (Duff et al. basis of the geometric normal); the
+ * result is the median of the positive ones, the upper one of the middle two
+ * for an even number, 0 when none is positive.  The displaced points and the
+ * step are computed in FP32, as the paper does; the step is 1.1e-3 when the
+ * centre cell is empty. */
 static float oct_density_robust(const orc_octree* o, const float pos[3], const float n[3]) {
-  float d[5];
-  float diag = 1e-3f;
-  int count = 0;
-  d[0] = oct_density(o, pos, n, &diag);
-  diag *= 1.1f;
-  if (d[0] > 0.0f) ++count;
+  float found[5];
+  int nfound = 0;
+  float step = 1e-3f;
+  float d0 = (float)oct_density(o, pos, n, 1, &step);
+  if (d0 > 0.0f) found[nfound++] = d0;
+  step *= 1.1f;
   v3 t, b;
   onb(vload(n), &t, &b);
-  v3 p = vload(pos);
-  v3 q[4] = {vadd(p, vmul(t, diag)), vsub(p, vmul(t, diag)), vadd(p, vmul(b, diag)), vsub(p, vmul(b, diag))};
-  for (int i = 0; i < 4; ++i) {
-    float qq[3] = {q[i].x, q[i].y, q[i].z};
-    d[count] = oct_density(o, qq, n, NULL);
-    if (d[count] > 0.0f) ++count;
+  const v3 dirs[4] = {t, vneg(t), b, vneg(b)};
+  for (int k = 0; k < 4; ++k) {
+    v3 q = vadd(vload(pos), vmul(dirs[k], step));
+    float qq[3] = {q.x, q.y, q.z};
+    float dk = (float)oct_density(o, qq, n, 0, NULL);
+    if (dk > 0.0f) found[nfound++] = dk;
   }
-  int m = count / 2;
-  for (int i = 0; i <= m; ++i)
-    for (int j = i + 1; j < count; ++j)
-      if (d[j] < d[i]) { float tmp = d[i]; d[i] = d[j]; d[j] = tmp; }
-  return d[m];
+  if (nfound == 0) return 0.0f;
+  qsort(found, (size_t)nfound, sizeof(float), cmp_float);
+  return found[nfound / 2];
 }
 
 float orc_octree_density(orc_octree* o, const float pos[3], const float n[3], int robust) {
-  return robust ? oct_density_robust(o, pos, n) : oct_density(o, pos, n, NULL);
+  return robust ? oct_density_robust(o, pos, n) : (float)oct_density(o, pos, n, 0, NULL);
 }
 
+static void cell_dump(const oct_cell* c, int32_t* words, int n) {
+  if (c->word >= n) return;
+  words[c->word] = c->kids ? -c->kids[0].word : c->count;
+  if (c->kids)
+    for (int k = 0; k < 8; ++k) cell_dump(&c->kids[k], words, n);
+}
+
+/* The tree in the flat layout of Sec. 5.5, min(n, capacity) words: a leaf's
+ * word holds its count, a split cell's word the negated index of its first
+ * child; words no cell has taken hold the count a new cell would start with.
+ * meta: words used (capacity + 1 after an overflow), depth, capacity. */
 int orc_octree_dump(const orc_octree* o, int32_t* nodes, int n, int32_t meta[3]) {
   int m = n < o->capacity ? n : o->capacity;
-  if (nodes) memcpy(nodes, o->nodes, sizeof(int32_t) * (size_t)m);
-  meta[0] = o->alloc;
+  if (nodes) {
+    for (int i = 0; i < m; ++i) nodes[i] = o->fresh_count;
+    cell_dump(&o->root, nodes, m);
+  }
+  meta[0] = o->words_used;
   meta[1] = o->depth;
   meta[2] = o->capacity;
   return o->capacity;
+}
+
+/* Rebuilds the tree from the flat layout (the inverse of orc_octree_dump):
+ * word 0 is the root; a negative word links to eight consecutive children.
+ * words_used and depth are taken as given.  Returns 0, or -1 when a link
+ * points outside [1, n - 8] or a word is reached twice. */
+static int cell_load(oct_cell* c, const int32_t* words, int n, int w, char* seen) {
+  if (w < 0 || w >= n || seen[w]) return -1;
+  seen[w] = 1;
+  c->word = w;
+  if (words[w] >= 0) { c->count = words[w]; c->kids = NULL; return 0; }
+  int first = -words[w];
+  if (first < 1 || first > n - 8) return -1;
+  c->kids = (oct_cell*)calloc(8, sizeof(oct_cell));
+  for (int k = 0; k < 8; ++k)
+    if (cell_load(&c->kids[k], words, n, first + k, seen) != 0) return -1;
+  return 0;
+}
+
+int orc_octree_load(orc_octree* o, const int32_t* words, int n, int words_used, int depth) {
+  cell_free(&o->root);
+  memset(&o->root, 0, sizeof(o->root));
+  char* seen = (char*)calloc((size_t)(n > 0 ? n : 1), 1);
+  int rc = cell_load(&o->root, words, n, 0, seen);
+  free(seen);
+  o->words_used = words_used;
+  o->depth = depth;
+  return rc;
+}
+
+void orc_onb(const float n[3], float t[3], float b[3]) {
+  v3 tt, bb;
+  onb(vload(n), &tt, &bb);
+  t[0] = tt.x; t[1] = tt.y; t[2] = tt.z;
+  b[0] = bb.x; b[1] = bb.y; b[2] = bb.z;
+}
+
+int orc_light_selection(const double* power, int n, int n_samples, uint64_t seed, double* psel, int64_t* counts) {
+  if (n < 1) return -1;
+  float* prob = (float*)malloc(sizeof(float) * (size_t)n);
+  int* alias = (int*)malloc(sizeof(int) * (size_t)n);
+  alias_build(power, n, psel, prob, alias);
+  rng_t g;
+  g.key[0] = (uint32_t)seed;
+  g.key[1] = (uint32_t)(seed >> 32);
+  g.iter = 1;
+  for (int i = 0; i < n; ++i) counts[i] = 0;
+  for (int k = 0; k < n_samples; ++k)
+    counts[alias_pick(prob, alias, n, rng_raw(&g, (uint32_t)k, 0, 0), rng_u(&g, (uint32_t)k, 0, 1))]++;
+  free(prob);
+  free(alias);
+  return 0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1140,10 +1298,8 @@ static int sample_light(const ctx_t* c, uint32_t pixel, uint32_t stream, v3 x, i
                         double* p_l) {
   const scene_t* s = c->s;
   if (s->nl == 0) return 0;
-  uint32_t x0 = rng_raw(&c->rng, pixel, stream, 0);
-  int i = (int)(((uint64_t)(x0 >> 8) * (uint64_t)s->nl) >> 24);
-  float ua = rng_u(&c->rng, pixel, stream, 1);
-  if (!(ua < s->alias_prob[i])) i = s->alias_idx[i];
+  int i = alias_pick(s->alias_prob, s->alias_idx, s->nl, rng_raw(&c->rng, pixel, stream, 0),
+                     rng_u(&c->rng, pixel, stream, 1));
   float u2 = rng_u(&c->rng, pixel, stream, 2);
   float u3 = rng_u(&c->rng, pixel, stream, 3);
   const light_t* L = &s->lights[i];
@@ -1515,10 +1671,8 @@ int orc_render(const orc_scene* scene_in, const orc_config* cfg, int n_iter, dou
       qsort(mref, (size_t)nm, sizeof(mref_t), mref_cmp);
       for (int i = 0; i < cfg->lp_photons; ++i) {
         const uint32_t lpix = (uint32_t)i, st0 = ORC_LP_STREAM;
-        uint32_t x0 = rng_raw(&c.rng, lpix, st0, 0);
-        int li = (int)(((uint64_t)(x0 >> 8) * (uint64_t)s.nl) >> 24);
-        float ua = rng_u(&c.rng, lpix, st0, 1);
-        if (!(ua < s.alias_prob[li])) li = s.alias_idx[li];
+        int li = alias_pick(s.alias_prob, s.alias_idx, s.nl, rng_raw(&c.rng, lpix, st0, 0),
+                            rng_u(&c.rng, lpix, st0, 1));
         float u2 = rng_u(&c.rng, lpix, st0, 2), u3 = rng_u(&c.rng, lpix, st0, 3);
         const light_t* Lt = &s.lights[li];
         v3 y, ny, yerr;
@@ -1529,9 +1683,9 @@ int orc_render(const orc_scene* scene_in, const orc_config* cfg, int n_iter, dou
           v3 e1 = vsub(bb, a), e2 = vsub(cc, a);
           y = vadd(vadd(a, vmul(e1, b1)), vmul(e2, b2));
           ny = vnorm(vcross(e1, e2));
-          yerr = mk3(GAMMA5 * (fabsf(a.x) + fabsf(e1.x * b1) + fabsf(e2.x * b2)),
-                     GAMMA5 * (fabsf(a.y) + fabsf(e1.y * b1) + fabsf(e2.y * b2)),
-                     GAMMA5 * (fabsf(a.z) + fabsf(e1.z * b1) + fabsf(e2.z * b2)));
+          yerr = mk3(gamma_f32(5) * (fabsf(a.x) + fabsf(e1.x * b1) + fabsf(e2.x * b2)),
+                     gamma_f32(5) * (fabsf(a.y) + fabsf(e1.y * b1) + fabsf(e2.y * b2)),
+                     gamma_f32(5) * (fabsf(a.z) + fabsf(e1.z * b1) + fabsf(e2.z * b2)));
         } else {
           const float* sp = s.sph + (size_t)(Lt->prim - s.nt) * 4;
           v3 ce = vload(sp);
@@ -1540,7 +1694,7 @@ int orc_render(const orc_scene* scene_in, const orc_config* cfg, int n_iter, dou
           float ph = TWO_PI_F * u3;
           ny = mk3(rr * cosf(ph), rr * sinf(ph), z);
           y = vadd(ce, vmul(ny, sp[3]));
-          yerr = mk3(GAMMA5 * (fabsf(ce.x) + sp[3]), GAMMA5 * (fabsf(ce.y) + sp[3]), GAMMA5 * (fabsf(ce.z) + sp[3]));
+          yerr = mk3(gamma_f32(5) * (fabsf(ce.x) + sp[3]), gamma_f32(5) * (fabsf(ce.y) + sp[3]), gamma_f32(5) * (fabsf(ce.z) + sp[3]));
         }
         const double p_lp = lp_light_pdf(&s, li);
         float u4 = rng_u(&c.rng, lpix, st0, 4), u5 = rng_u(&c.rng, lpix, st0, 5);
@@ -1666,7 +1820,7 @@ int orc_render(const orc_scene* scene_in, const orc_config* cfg, int n_iter, dou
     }
     if (cfg->iter_seconds) cfg->iter_seconds[it] = now_seconds() - t_start;
   }
-  st[ORC_ST_OCTREE_NODES] = oct->alloc < oct->capacity ? oct->alloc : oct->capacity;
+  st[ORC_ST_OCTREE_NODES] = oct->words_used < oct->capacity ? oct->words_used : oct->capacity;
   st[ORC_ST_OCTREE_DEPTH] = oct->depth;
   if (stats) memcpy(stats, st, sizeof(st));
   orc_octree_free(oct);

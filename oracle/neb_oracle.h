@@ -9,11 +9,13 @@
  * list of the path (Eq. misweight .. Eq. misw), where the GPU uses a
  * recursive form.
  *
- * Precision: geometry, sampling decisions and the density octree are FP32
- * (the octree follows the listing of Appendix B, which uses float); all
- * radiometric quantities, MIS products and the accumulation are FP64.
- * Build with -ffp-contract=off so the FP32 parts round the same way on
- * every host.
+ * Precision: ray/primitive tests, hit points, the plane/box area and the
+ * density quotient are FP64; vertex positions, directions and sampling
+ * decisions are FP32, and so are the decisions the paper takes in FP32
+ * (the octree cell a position falls in, the displaced points of the robust
+ * density query, the case of the area formula); all radiometric quantities,
+ * MIS products and the accumulation are FP64.  Build with
+ * -ffp-contract=off so the FP32 parts round the same way on every host.
  */
 #ifndef NEB_ORACLE_H
 #define NEB_ORACLE_H
@@ -67,8 +69,10 @@ int orc_render(const orc_scene* scene, const orc_config* cfg, int n_iter,
 
 /* ---- unit entry points used by the pin tests ---- */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
-float orc_intersection_area(const float bmin[3], const float bmax[3],
-                            const float pos[3], const float normal[3]);
+/* Eq. area (Sec. 5.3, Appendix A) for the plane through pos with unit normal
+ * `normal` and the box [bmin, bmax], in FP64. */
+double orc_intersection_area(const float bmin[3], const float bmax[3],
+                             const float pos[3], const float normal[3]);
 
 typedef struct orc_octree orc_octree;
 orc_octree* orc_octree_new(const float scene_min[3], const float scene_max[3],
@@ -77,8 +81,24 @@ void orc_octree_free(orc_octree* o);
 void orc_octree_set_iteration(orc_octree* o, int iter);
 void orc_octree_increment(orc_octree* o, const float pos[3]);
 float orc_octree_density(orc_octree* o, const float pos[3], const float normal[3], int robust);
-/* Copies min(n, capacity) nodes; returns capacity.  meta: alloc, depth, capacity. */
+/* The tree in the flat word layout of Sec. 5.5 (a leaf's word its count, a
+ * split cell's word the negated index of its first child, words no cell has
+ * taken the count a new cell would start with): copies min(n, capacity)
+ * words; returns capacity.  meta: words used, depth, capacity. */
 int orc_octree_dump(const orc_octree* o, int32_t* nodes, int n, int32_t meta[3]);
+/* Replaces the tree by the one in the flat layout words[n] (word 0 the root);
+ * words used and depth as given.  0, or -1 for a malformed layout. */
+int orc_octree_load(orc_octree* o, const int32_t* words, int n, int words_used, int depth);
+
+/* Tangent t and bitangent b of unit normal n (Duff et al. 2017, the basis of
+ * the robust density query). */
+void orc_onb(const float n[3], float t[3], float b[3]);
+
+/* Light selection as the renderer does it: Vose's alias table over `power`
+ * (psel[i] = power[i] / sum), then n_samples choices with Philox words keyed
+ * by seed (counter: sample k, stream 0, dims 0-1, iteration 1) counted in
+ * counts[n].  0, or -1 for n < 1. */
+int orc_light_selection(const double* power, int n, int n_samples, uint64_t seed, double* psel, int64_t* counts);
 
 /* BVH parity helpers: closest hit for n rays ([n][6] origin, direction);
  * out_prim -1 on miss, out_t the hit distance.  brute != 0 tests every

@@ -63,7 +63,7 @@ def lib():
         L.orc_render.restype = C.c_int
         L.orc_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_intersection_area.argtypes = [C.c_void_p] * 4
-        L.orc_intersection_area.restype = C.c_float
+        L.orc_intersection_area.restype = C.c_double
         L.orc_octree_new.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int]
         L.orc_octree_new.restype = C.c_void_p
         L.orc_octree_free.argtypes = [C.c_void_p]
@@ -73,6 +73,11 @@ def lib():
         L.orc_octree_density.restype = C.c_float
         L.orc_octree_dump.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
         L.orc_octree_dump.restype = C.c_int
+        L.orc_octree_load.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int]
+        L.orc_octree_load.restype = C.c_int
+        L.orc_onb.argtypes = [C.c_void_p] * 3
+        L.orc_light_selection.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_uint64, C.c_void_p, C.c_void_p]
+        L.orc_light_selection.restype = C.c_int
         L.orc_trace.argtypes = [C.POINTER(_Scene), C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
         L.orc_count_neighbours.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_float, C.c_int,
                                            C.c_void_p]
@@ -118,7 +123,7 @@ def intersection_area(bmin, bmax, pos, normal):
 
 
 class Octree:
-    """Sequential density octree of Appendix B (deterministic insertion order)."""
+    """Density octree of Sec. 5, counted sequentially (deterministic insertion order)."""
 
     def __init__(self, scene_min, scene_max, capacity, split_factor):
         self._mn = np.ascontiguousarray(scene_min, np.float32)
@@ -153,6 +158,33 @@ class Octree:
         nodes = np.zeros(cap, np.int32)
         lib().orc_octree_dump(self.h, _ptr(nodes), cap, _ptr(meta))
         return nodes, int(meta[0]), int(meta[1])
+
+    def load(self, words, words_used, depth):
+        """Replace the tree by the one in the flat layout of Sec. 5.5."""
+        w = np.ascontiguousarray(words, np.int32)
+        rc = lib().orc_octree_load(self.h, _ptr(w), len(w), int(words_used), int(depth))
+        if rc != 0:
+            raise ValueError("malformed octree layout")
+
+
+def onb(normal):
+    """(t, b) of the Duff et al. basis of a unit normal."""
+    n = np.ascontiguousarray(normal, np.float32)
+    t = np.zeros(3, np.float32)
+    b = np.zeros(3, np.float32)
+    lib().orc_onb(_ptr(n), _ptr(t), _ptr(b))
+    return t, b
+
+
+def light_selection(power, n_samples, seed=0):
+    """(psel, counts): selection probabilities of the alias table built from
+    `power` and how often the renderer's selection picked each light."""
+    w = np.ascontiguousarray(power, np.float64)
+    psel = np.zeros(len(w), np.float64)
+    counts = np.zeros(len(w), np.int64)
+    rc = lib().orc_light_selection(_ptr(w), len(w), int(n_samples), C.c_uint64(seed), _ptr(psel), _ptr(counts))
+    assert rc == 0
+    return psel, counts
 
 
 def trace(scene, rays, brute=False):

@@ -66,6 +66,32 @@ def test_white_furnace_with_neb_photons_small_bias(oracle):
     assert split[2].mean() > 0.05 * expect     # photon merges carry real weight
 
 
+def test_neb_photons_alone_reproduce_the_longer_paths_of_the_furnace(oracle):
+    """NEB photons alone (mask 4) create the paths of length l >= 3 (a view
+    vertex k >= 1, a photon bounce j >= 1, l = k + j + 1), each under weights
+    that sum to one over its merge positions, so the furnace image converges
+    to Le * sum_{j=2}^{D-1} a^j.  The photon flux dE / rho carries the octree's
+    bias: a cell crossed by two walls is divided by one plane's area and
+    overestimates rho, so along the box's edges the flux is too low.  The bias
+    shrinks as the tree refines (more NEE vertices per iteration, a smaller
+    split factor) and barely depends on the merge radius."""
+    D = 5
+    s = scenes.white_furnace(0.5, 1.0)
+    expect = sum(0.5 ** j for j in range(2, D))
+
+    def ratio(w, split, r):
+        res = oracle.render(s, cfg(w, w, D, mask=4, r=r, split=split, cap=1 << 20), n_iter=4)
+        assert res["split"][[0, 1, 3]].sum() == 0 and res["stats"]["merges"] > 1000
+        return float(res["accum"][..., 0].mean() / 4 / expect)
+
+    fine = {r: ratio(64, 4, r) for r in (0.04, 0.01)}
+    coarse = ratio(32, 8, 0.02)
+    for r, q in fine.items():
+        assert abs(q - 1.0) < 0.06, (r, q)
+    assert abs(fine[0.04] - fine[0.01]) < 0.03, fine
+    assert abs(coarse - 1.0) > abs(fine[0.04] - 1.0), (coarse, fine)
+
+
 def _camera_rays(cam, W, H, sub):
     eye, target, up, vfov = cam[0:3].astype(np.float64), cam[3:6], cam[6:9], float(cam[9])
     fwd = (target - eye) / np.linalg.norm(target - eye)
@@ -113,6 +139,43 @@ def test_plane_under_sphere_light_closed_form(oracle):
     r = oracle.render(s, cfg(W, H, 3), n_iter=1)
     sp = r["split"][..., 0]
     assert sp[0].sum() > 0 and sp[1].sum() > 0 and sp[2].sum() == 0
+
+
+def test_plane_under_two_unequal_sphere_lights(oracle):
+    """Two sphere lights whose powers differ tenfold: NEE picks them in
+    proportion to power (alias table) and divides by that probability, so the
+    plane's radiance is the sum of the two closed forms a L_i R_i^2 h_i /
+    d_i^3.  A selection probability off from the one the samples are drawn
+    with biases each light's share; 8x8 block means within 3 standard
+    errors of independent iterations."""
+    a = 0.6
+    lights = [(-0.25, 1.0, 0.35, 0.1, 5.0), (0.3, 0.7, 0.6, 0.05, 200.0)]   # x, h, z, R, L
+    base = scenes.plane_under_sphere(a, 0.1, 1.0, 5.0)
+    mats = np.concatenate([base.mats[:1]] + [scenes.material(scenes.MAT_DIFFUSE, (0, 0, 0), emission=(L,) * 3)[None]
+                                             for (_, _, _, _, L) in lights])
+    sph = np.array([[x, h, z, R] for (x, h, z, R, _) in lights])
+    s = scenes.Scene(base.tri, base.tri_mat, sph, np.array([1, 2]), mats, base.cam, "plane_two_lights")
+    power = [4 * math.pi ** 2 * R * R * L for (_, _, _, R, L) in lights]
+    assert max(power) / min(power) > 9
+    W = H = 32
+    n_it = 8
+    imgs = per_iteration_images(oracle, s, cfg(W, H, 3, mask=3), n_it)[..., 0]
+    eye, d = _camera_rays(s.cam, W, H, 6)
+    t = -eye[1] / d[..., 1]
+    x = eye + t[..., None] * d
+    on_plane = (t > 0) & (np.abs(x[..., 0]) <= 50) & (np.abs(x[..., 2]) <= 50)
+    rad = np.zeros(on_plane.shape)
+    for (lx, h, lz, R, L) in lights:
+        dist = np.linalg.norm(x - np.array([lx, h, lz]), axis=-1)
+        rad += a * L * R * R * h / dist ** 3
+    expect = np.where(on_plane, rad, 0.0).mean(axis=(2, 3))
+    B = 8
+    for by in range(0, H, B):
+        for bx in range(0, W, B):
+            m = imgs[:, by:by + B, bx:bx + B].mean(axis=(1, 2))
+            e = expect[by:by + B, bx:bx + B].mean()
+            se = m.std(ddof=1) / math.sqrt(n_it)
+            assert abs(m.mean() - e) < 3 * se + 1e-6 * e, (by, bx, m.mean() - e, se)
 
 
 def _plane_expectation(s, W, H, a, R, h, L):
