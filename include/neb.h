@@ -59,7 +59,7 @@ typedef struct {
   int max_depth;         /* D: maximum path length in segments, 1 <= D <= 64 */
   float merge_radius;    /* r of the uniform kernel 1/(pi r^2) (Sec. 3.2) */
   int octree_capacity;   /* nodes; rounded up to 8n+1 (Appendix B initialize) */
-  int split_factor;      /* SPLIT_FACTOR of Appendix B (paper: 4) */
+  int split_factor;      /* split factor of the density octree, >= 2: a cell splits at split_factor * iteration vertices (paper: 4, Sec. 5.5) */
   uint64_t seed;         /* Philox4x32-10 key */
   int octree_mode;       /* 0 concurrent lock-free inserts, 1 sequential in (pixel, k) order */
   int density_mode;      /* 0 robust median of five (get_density_robust), 1 single query */
@@ -232,33 +232,56 @@ int neb_trace_closest(neb_ctx* ctx, const float* rays, int n, int32_t* out_prim,
 /* Philox4x32-10 on the device: n counters [n][4] under one key -> [n][4]. */
 int neb_philox(const uint32_t* ctr, int n, const uint32_t key[2], uint32_t* out);
 
-/* Plane/box intersection area of Eq. area with the listing's 1D/2D
- * thresholds (Appendix B intersection_area), evaluated on the device for n
- * cases: boxes [n][6] (min, max), positions [n][3], normals [n][3]. */
-int neb_plane_box_area(const float* boxes, const float* pos, const float* nrm, int n, float* out);
+/* Area of the plane through a point with a unit normal inside an
+ * axis-aligned box (Eq. area, Sec. 5.3 and Appendix A), evaluated in FP64
+ * on the device for n cases, as the density query evaluates it: boxes [n][6]
+ * (min, max), points [n][3], normals [n][3] (host arrays, copied); out [n]
+ * (host).  A normal component within 1e-3 of +-1 gives the face area across
+ * that axis; otherwise a component below 1e-4 is taken as zero (the
+ * thresholds of the paper's implementation).  NEB_ERR_ARG for n < 0 or a
+ * missing array, NEB_ERR_NO_DEVICE / NEB_ERR_OOM / NEB_ERR_CUDA. */
+int neb_plane_box_area(const float* boxes, const float* pos, const float* nrm, int n, double* out);
 
-/* Stand-alone density octree (Sec. 5, Appendix B) on the device. */
+/* Stand-alone density octree (Sec. 5) on the device: one int32 word per
+ * cell, siblings in consecutive words, a word >= 0 a count and < 0 the
+ * negated index of the cell's first child (Sec. 5.5); word 0 is the root.
+ * The octree box is the scene box grown by 0.2 % about its centre; the word
+ * pool holds `capacity` rounded up to 8m + 1 words.  split_factor >= 2. */
 typedef struct neb_octree neb_octree;
 int neb_octree_create(const float scene_min[3], const float scene_max[3], int capacity,
                       int split_factor, void* cuda_stream, neb_octree** out);
 void neb_octree_destroy(neb_octree* o);
-/* set_iteration of the listing: scales, threshold, re-arm of unused nodes */
+/* Starts iteration iter >= 1 (Sec. 5.4): split threshold split_factor *
+ * min(iter, 1000), densities divided by min(iter, 1000), every free word
+ * set to the count a new cell starts with, ceil(split_factor * iter / 4);
+ * after iteration 1000 inserts are ignored. */
 int neb_octree_set_iteration(neb_octree* o, int iter);
-/* Inserts n positions [n][3]: mode 0 concurrent (one thread per position,
- * lock-free CAS counting and splitting with a bounded spin), mode 1 one
- * device thread in array order (identical to the sequential listing). */
+/* Counts n positions [n][3] (Sec. 5.1-5.2): each adds one to the leaf cell
+ * holding it, and the position that brings a cell to the threshold splits
+ * it (eight new cells from the pool; no room: the pool is marked exhausted
+ * and cells keep counting).  mode 0: concurrent, one thread per position,
+ * compare-and-swap counts, positions that count past the threshold while the
+ * split is published wait for it (bounded) and count again in the child;
+ * mode 1: one device thread in array order (deterministic).  Positions
+ * outside the octree box are ignored. */
 int neb_octree_insert(neb_octree* o, const float* pos, int n, int mode);
-/* get_density (robust = 0) or get_density_robust (robust = 1), FP64
- * normalisation, for n positions / geometric normals [n][3]. */
+/* Density (Eq. octdensity) at n positions with geometric normals [n][3]:
+ * robust = 0 one query, count / (iterations * max(floor, A)) with A the
+ * plane's area in the leaf cell (FP64) and floor 0.01 of the squared cell
+ * diagonal; robust = 1 the median of that query (floor 0.1) and four more
+ * displaced by 1.1 cell diagonals along the tangents of the Duff et al.
+ * basis, the upper of the middle two for an even count.  0 for an empty
+ * cell or a position outside the box. */
 int neb_octree_density(neb_octree* o, const float* pos, const float* nrm, int n, int robust, float* out);
 /* Copies the node array (capacity entries) and meta = {alloc, depth, capacity, status}. */
 int neb_octree_read(neb_octree* o, int32_t* nodes, int n_nodes, int32_t meta[4]);
 /* Restores a node array and its allocation state, e.g. one read back by
  * neb_octree_read, to resume a density estimate (the octree integrates over
  * iterations, Sec. 5.4).  nodes: n_nodes host entries, 1 <= n_nodes <=
- * capacity, copied before return; entries past n_nodes become 0.  alloc in
- * [1, capacity + 1] (capacity + 1: allocation overflowed), depth in
- * [0, 30]; the status word is cleared.  NEB_ERR_ARG for values out of range.
+ * capacity, copied before return; entries past n_nodes become 0.  alloc:
+ * the words in use, 1 + 8m <= capacity, or capacity + 1 when the pool was
+ * exhausted; depth in [0, 30]; the status word is cleared.  NEB_ERR_ARG for
+ * values out of range.
  * Node values are taken as given: a non-negative counter above the split
  * threshold with no child (a state inserts never leave) makes concurrent
  * inserts through it wait out their bounded spin, drop the position and

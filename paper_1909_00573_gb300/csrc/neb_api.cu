@@ -74,7 +74,7 @@ static void free_scene(neb_ctx* c) {
 
 static bool config_ok(const neb_config* cfg) {
   return cfg->width >= 1 && cfg->height >= 1 && cfg->max_depth >= 1 && cfg->max_depth <= kMaxDepth &&
-         cfg->merge_radius > 0.0f && cfg->octree_capacity >= 1 && cfg->split_factor >= 1 &&
+         cfg->merge_radius > 0.0f && cfg->octree_capacity >= 1 && cfg->split_factor >= 2 &&
          (cfg->octree_mode == 0 || cfg->octree_mode == 1) && (cfg->density_mode == 0 || cfg->density_mode == 1) &&
          !(cfg->strategy_mask & ~15u) && cfg->lp_photons >= 0 && cfg->lp_photons <= (1 << 26) &&
          (cfg->bvh_builder == 0 || cfg->bvh_builder == 1) &&
@@ -868,19 +868,22 @@ extern "C" int neb_philox(const uint32_t* ctr, int n, const uint32_t key[2], uin
   return e == cudaSuccess ? NEB_OK : NEB_ERR_CUDA;
 }
 
-extern "C" int neb_plane_box_area(const float* boxes, const float* pos, const float* nrm, int n, float* out) {
+extern "C" int neb_plane_box_area(const float* boxes, const float* pos, const float* nrm, int n, double* out) {
   if (n < 0 || (n > 0 && (!boxes || !pos || !nrm || !out))) return NEB_ERR_ARG;
   if (n == 0) return NEB_OK;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return NEB_ERR_NO_DEVICE;
   float* d = nullptr;
-  if (cudaMalloc(&d, sizeof(float) * 13 * (size_t)n) != cudaSuccess) return NEB_ERR_OOM;
+  double* dout = nullptr;
+  if (cudaMalloc(&d, sizeof(float) * 12 * (size_t)n) != cudaSuccess) return NEB_ERR_OOM;
+  if (cudaMalloc(&dout, sizeof(double) * (size_t)n) != cudaSuccess) { cudaFree(d); return NEB_ERR_OOM; }
   cudaMemcpy(d, boxes, sizeof(float) * 6 * (size_t)n, cudaMemcpyHostToDevice);
   cudaMemcpy(d + 6 * (size_t)n, pos, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice);
   cudaMemcpy(d + 9 * (size_t)n, nrm, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice);
-  launch_area(d, d + 6 * (size_t)n, d + 9 * (size_t)n, n, d + 12 * (size_t)n, 0);
-  cudaError_t e = cudaMemcpy(out, d + 12 * (size_t)n, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost);
+  launch_area(d, d + 6 * (size_t)n, d + 9 * (size_t)n, n, dout, 0);
+  cudaError_t e = cudaMemcpy(out, dout, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost);
   cudaFree(d);
+  cudaFree(dout);
   return e == cudaSuccess ? NEB_OK : NEB_ERR_CUDA;
 }
 

@@ -742,17 +742,17 @@ cudaError_t launch_philox(const uint32_t* d_ctr, int n, uint2 key, uint32_t* d_o
 }
 
 __global__ void k_area(const float* __restrict__ boxes, const float* __restrict__ pos, const float* __restrict__ nrm,
-                       int n, float* out) {
+                       int n, double* out) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    float lo[3] = {boxes[6 * i], boxes[6 * i + 1], boxes[6 * i + 2]};
-    float hi[3] = {boxes[6 * i + 3], boxes[6 * i + 4], boxes[6 * i + 5]};
-    float p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
-    float q[3] = {nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]};
-    out[i] = intersection_area(lo, hi, p, q);
+    const double lo[3] = {boxes[6 * i], boxes[6 * i + 1], boxes[6 * i + 2]};
+    const double hi[3] = {boxes[6 * i + 3], boxes[6 * i + 4], boxes[6 * i + 5]};
+    const double p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+    const float q[3] = {nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]};
+    out[i] = plane_box_area64(lo, hi, p, q);
   }
 }
 
-cudaError_t launch_area(const float* d_boxes, const float* d_pos, const float* d_nrm, int n, float* d_out,
+cudaError_t launch_area(const float* d_boxes, const float* d_pos, const float* d_nrm, int n, double* d_out,
                         cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_area<<<(n + 255) / 256, 256, 0, st>>>(d_boxes, d_pos, d_nrm, n, d_out);

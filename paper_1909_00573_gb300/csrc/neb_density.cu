@@ -159,7 +159,7 @@ using namespace neb;
 extern "C" int neb_density_estimators(const float* pos, const float* nrm, int n, const float scene_min[3],
                                       const float scene_max[3], int octree_capacity, int split_factor, float radius,
                                       int k, float* rho, double* ms) {
-  if (!pos || !nrm || !scene_min || !scene_max || !rho || n < 1 || octree_capacity < 1 || split_factor < 1 ||
+  if (!pos || !nrm || !scene_min || !scene_max || !rho || n < 1 || octree_capacity < 1 || split_factor < 2 ||
       !(radius > 0.0f) || k < 2 || k > kMaxK)
     return NEB_ERR_ARG;
   int ndev = 0;

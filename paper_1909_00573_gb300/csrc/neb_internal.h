@@ -242,7 +242,7 @@ cudaError_t build_bvh4(const SceneView& s, int n, int builder, cudaStream_t st, 
 cudaError_t launch_trace_debug(const SceneView& s, const float* d_rays, int n, int* d_prim, float* d_t,
                                uint32_t* d_status, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* d_ctr, int n, uint2 key, uint32_t* d_out, cudaStream_t st);
-cudaError_t launch_area(const float* d_boxes, const float* d_pos, const float* d_nrm, int n, float* d_out,
+cudaError_t launch_area(const float* d_boxes, const float* d_pos, const float* d_nrm, int n, double* d_out,
                         cudaStream_t st);
 
 // neb_grid.cu

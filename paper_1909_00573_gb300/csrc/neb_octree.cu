@@ -1,5 +1,5 @@
-// neb_octree.cu -- density octree kernels (Sec. 5, Appendix B) and the
-// stand-alone octree entry points of the C ABI.
+// neb_octree.cu -- density octree kernels (Sec. 5) and the stand-alone
+// octree entry points of the C ABI.
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -9,16 +9,21 @@
 
 namespace neb {
 
-// initialize() of the listing: scene box enlarged by 1.002 around its
-// minimum corner, capacity rounded up to 8n + 1.
+// The octree box is the scene box grown by 0.2 % about its centre, so that
+// points on the scene's bounds fall inside (Appendix B does the same); the
+// pool holds the requested number of words rounded up to 8m + 1 (the root and
+// m groups of eight children).
 OctreeParams octree_params(const float smin[3], const float smax[3], int capacity, int split_factor) {
   OctreeParams P;
-  float size[3];
-  for (int c = 0; c < 3; ++c) size[c] = (smax[c] - smin[c]) * 1.002f;
-  for (int c = 0; c < 3; ++c) P.size_inv[c] = 1.0f / size[c];
-  P.scene_scale = sqrtf(size[0] * size[0] + size[1] * size[1] + size[2] * size[2]);
-  for (int c = 0; c < 3; ++c) P.minb[c] = smin[c] - size[c] * (0.001f / 1.002f);
-  P.capacity = 1 + ((capacity + 7) & ~7);
+  float edge[3];
+  for (int c = 0; c < 3; ++c) {
+    edge[c] = (smax[c] - smin[c]) * 1.002f;
+    P.size_inv[c] = 1.0f / edge[c];
+    P.box_extent[c] = 1.0 / (double)P.size_inv[c];
+    P.minb[c] = smin[c] - edge[c] * (0.001f / 1.002f);
+  }
+  P.scene_scale = sqrtf(edge[0] * edge[0] + edge[1] * edge[1] + edge[2] * edge[2]);
+  P.capacity = 8 * ((capacity + 7) / 8) + 1;
   P.split_count = split_factor;
   P.iter_clamp = 1;
   P.stop_filling = 0;
@@ -26,17 +31,21 @@ OctreeParams octree_params(const float smin[3], const float smax[3], int capacit
   return P;
 }
 
-// set_iteration() of the listing (the re-arm of unused nodes is the kernel below)
+// Counts are integrated over the iterations (Sec. 5.4): the split threshold
+// grows with the iteration (up to 1000, after which counting stops) and
+// densities are divided by it.  A new cell starts with a quarter of the
+// split factor per iteration so far, since a surface crosses about four of a
+// cell's eight children (Sec. 5.2).  The re-arm kernel below writes that
+// count into every free word of the pool.
 void octree_set_iteration_params(OctreeParams& P, int split_factor, int iter) {
-  int ic = iter < kFillIterations ? iter : kFillIterations;
+  const int ic = iter < kFillIterations ? iter : kFillIterations;
   P.iter_clamp = ic;
   P.stop_filling = iter > kFillIterations;
   P.split_count = split_factor * ic;
-  P.init_value = (int)ceilf((float)split_factor / 4.0f * (float)iter);
+  P.init_value = (split_factor * ic + 3) / 4;  // ceil(split_factor * iter / 4) while counting
 }
 
-// every node in [alloc, capacity) starts at ceil(SPLIT/4 * iter): a surface
-// meets about four of the eight children of a split cell (Sec. 5.2)
+// every free word [alloc, capacity) gets the count a new cell starts with
 __global__ void k_oct_rearm(int* nodes, const OctreeState* st, OctreeParams P) {
   if (P.stop_filling) return;
   int a = *((const volatile int*)&st->alloc);
@@ -63,7 +72,7 @@ __global__ void k_oct_insert_points(int* nodes, OctreeState* st, OctreeParams P,
   }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     float p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
-    oct_insert_atomic(nodes, st, P, p, spin_limit, false);
+    oct_insert(nodes, st, P, p, spin_limit);
   }
 }
 
@@ -76,15 +85,13 @@ __global__ void k_oct_insert_points_seq(int* nodes, OctreeState* st, OctreeParam
   }
 }
 
-__global__ void k_oct_density_points(const int* __restrict__ nodes, const OctreeState* st, OctreeParams P,
-                                     const float* __restrict__ pos, const float* __restrict__ nrm, int n, int robust,
-                                     float* out) {
-  int depth = st->depth;
+__global__ void k_oct_density_points(const int* __restrict__ nodes, OctreeParams P, const float* __restrict__ pos,
+                                     const float* __restrict__ nrm, int n, int robust, float* out) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     float p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
     float q[3] = {nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]};
     int nq = 0;
-    out[i] = robust ? oct_density_robust(nodes, P, depth, p, q, &nq) : oct_density(nodes, P, depth, p, q, nullptr);
+    out[i] = robust ? oct_density_robust(nodes, P, p, q, &nq) : oct_density(nodes, P, p, q);
   }
 }
 
@@ -115,7 +122,7 @@ __global__ void k_oct_insert_nee(int* nodes, OctreeState* st, OctreeParams P, co
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
       float4 v = vpos[i];
       float p[3] = {v.x, v.y, v.z};
-      oct_insert_atomic(nodes, st, P, p, spin_limit, false);
+      oct_insert(nodes, st, P, p, spin_limit);
       ++done;
     }
   }
@@ -146,7 +153,6 @@ __global__ void k_oct_density_nee(const int* __restrict__ nodes, const OctreeSta
                                   const float4* __restrict__ vpos, const float4* __restrict__ vnrm, float4* vldir,
                                   const int* __restrict__ lit, DevCounters* cnt, int cap, int robust, int all) {
   int count = min(all ? cnt->nee_count : cnt->lit_count, cap);
-  int depth = st->depth;
   int queries = 0;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
     const int i = all ? t : lit[t];
@@ -155,9 +161,9 @@ __global__ void k_oct_density_nee(const int* __restrict__ nodes, const OctreeSta
     float q[3] = {nn.x, nn.y, nn.z};
     float rho;
     if (robust) {
-      rho = oct_density_robust(nodes, P, depth, p, q, &queries);
+      rho = oct_density_robust(nodes, P, p, q, &queries);
     } else {
-      rho = oct_density(nodes, P, depth, p, q, nullptr);
+      rho = oct_density(nodes, P, p, q);
       ++queries;
     }
     vldir[i].w = rho;
@@ -189,7 +195,8 @@ cudaError_t launch_oct_density_points(const int* nodes, const OctreeState* st, c
                                       const float* d_pos, const float* d_nrm, int n, int robust, float* d_out,
                                       cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_oct_density_points<<<blocks_for(n, 256), 256, 0, s>>>(nodes, st, P, d_pos, d_nrm, n, robust, d_out);
+  (void)st;
+  k_oct_density_points<<<blocks_for(n, 256), 256, 0, s>>>(nodes, P, d_pos, d_nrm, n, robust, d_out);
   return cudaGetLastError();
 }
 
@@ -226,7 +233,7 @@ struct neb_octree {
 
 extern "C" int neb_octree_create(const float scene_min[3], const float scene_max[3], int capacity, int split_factor,
                                  void* cuda_stream, neb_octree** out) {
-  if (!scene_min || !scene_max || !out || capacity < 1 || split_factor < 1) return NEB_ERR_ARG;
+  if (!scene_min || !scene_max || !out || capacity < 1 || split_factor < 2) return NEB_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return NEB_ERR_NO_DEVICE;
   neb_octree* o = new (std::nothrow) neb_octree();
@@ -300,8 +307,10 @@ extern "C" int neb_octree_density(neb_octree* o, const float* pos, const float* 
 }
 
 extern "C" int neb_octree_load(neb_octree* o, const int32_t* nodes, int n_nodes, int alloc, int depth) {
+  // words in use are the root plus whole groups of eight, or capacity + 1
+  // once the pool has been exhausted
   if (!o || !nodes || n_nodes < 1 || n_nodes > o->P.capacity || alloc < 1 || alloc > o->P.capacity + 1 ||
-      depth < 0 || depth > neb::kOctMaxDepth)
+      ((alloc - 1) % 8 != 0 && alloc != o->P.capacity + 1) || depth < 0 || depth > neb::kOctMaxDepth)
     return NEB_ERR_ARG;
   neb::OctreeState s{alloc, depth, 0u, 0};
   cudaMemsetAsync(o->nodes, 0, sizeof(int) * (size_t)o->P.capacity, o->stream);

@@ -1,368 +1,364 @@
-// neb_octree.cuh -- device side of the density octree (Sec. 5 and the
-// listing of Appendix B): plane/box area (Eq. area), count-and-split insert
-// (lock-free, and sequential for the deterministic mode), and the density
-// query with its robust median-of-five variant.
+// neb_octree.cuh -- device side of the density octree (Sec. 5): the area of
+// a plane inside a cell (Eq. area), counting a vertex with splits of full
+// cells (lock-free, or in insertion order on one thread for the deterministic
+// mode), and the density query (Eq. octdensity) with its robust
+// median-of-five form.
+//
+// Memory layout (Sec. 5.5): one int32 word per cell, the eight children of a
+// cell in consecutive words; a word >= 0 is a count, a word < 0 is the
+// negated index of the cell's first child.  Word 0 is the root.
+//
+// Addressing: a position is turned once into its cell on the finest grid the
+// tree can reach (2^30 cells per axis of the octree box); the child taken at
+// level L is then read from bit 30 - L of each of the three coordinates.  On
+// a grid of 2^L cells the cell index of unit coordinate u is floor(u 2^L),
+// and scaling by a power of two is exact in FP32, so this is the same cell
+// for every level as computing floor(u 2^L) level by level.
 #pragma once
 #include "neb_device.cuh"
 
 namespace neb {
 
-// Eq. area with the listing's 1D (|n_d| within 1e-3 of 1) and 2D (|n_d| <
-// 1e-4) cases; corners enter the alternating sum in the listing's order.
-__host__ __device__ __forceinline__ float intersection_area(const float bmin[3], const float bmax[3],
-                                                            const float pos[3], const float n[3]) {
-  float cs[3] = {bmax[0] - bmin[0], bmax[1] - bmin[1], bmax[2] - bmin[2]};
-  float an[3] = {fabsf(n[0]), fabsf(n[1]), fabsf(n[2])};
-  if (fabsf(an[0] - 1.0f) < 1e-3f) return cs[1] * cs[2];
-  if (fabsf(an[1] - 1.0f) < 1e-3f) return cs[0] * cs[2];
-  if (fabsf(an[2] - 1.0f) < 1e-3f) return cs[0] * cs[1];
-  for (int d = 0; d < 3; ++d) {
-    if (an[d] < 1e-4f) {
-      int x = d == 2 ? 0 : d + 1;
-      int y = x == 2 ? 0 : x + 1;
-      float h = n[x] * pos[x] + n[y] * pos[y];
-      float s = 0.0f;
-      s += fmaxf(0.0f, h - (n[x] * bmin[x] + n[y] * bmin[y]));
-      s -= fmaxf(0.0f, h - (n[x] * bmin[x] + n[y] * bmax[y]));
-      s -= fmaxf(0.0f, h - (n[x] * bmax[x] + n[y] * bmin[y]));
-      s += fmaxf(0.0f, h - (n[x] * bmax[x] + n[y] * bmax[y]));
-      return cs[d] * fabsf(s / (n[x] * n[y]));
+constexpr int kOctKeyBits = kOctMaxDepth;  // 30: levels 1..30 below the root
+
+// ---- Eq. area ----------------------------------------------------------------
+// Area of the plane through p with unit normal n inside the box [lo, hi]
+// (Eq. area, Sec. 5.3; Appendix A obtains it as the derivative of the box
+// volume below the plane).  FP64, in a frame where every axis is mirrored so
+// that the normal component m_i = |n_i| is non-negative: the corner lowest
+// along the normal becomes the origin of the alternating corner sum, with
+// a_i = m_i (p_i - that corner's coordinate) and w_i = m_i (hi_i - lo_i), and
+// the corner whose upper-bound set is c contributes
+// (-1)^|c| max(0, sum_i (a_i - [i in c] w_i))^(d-1), the sum being divided by
+// (d-1)! prod m_i.  Mirroring changes the sign of both the corner parity and
+// the product of the components, so the quotient is unchanged.  The number of
+// axes d follows the FP32 normal as the paper's implementation decides it: a
+// component within 1e-3 of +-1 leaves the face across that axis (d = 1), else
+// the first component below 1e-4 is dropped and its extent multiplies the
+// length found in the other two (d = 2), else d = 3.
+__device__ __forceinline__ double plane_box_area64(const double lo[3], const double hi[3], const double p[3],
+                                                   const float n[3]) {
+  const float m[3] = {fabsf(n[0]), fabsf(n[1]), fabsf(n[2])};
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    if (fabsf(m[i] - 1.0f) < 1e-3f) {
+      const int j = i == 2 ? 0 : i + 1, k = j == 2 ? 0 : j + 1;
+      return (hi[j] - lo[j]) * (hi[k] - lo[k]);
     }
+  const int drop = m[0] < 1e-4f ? 0 : (m[1] < 1e-4f ? 1 : (m[2] < 1e-4f ? 2 : -1));
+  double a[3] = {0.0, 0.0, 0.0}, w[3] = {0.0, 0.0, 0.0}, mprod = 1.0;
+  int d = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (i == drop) continue;
+    const double mi = (double)m[i];
+    a[d] = mi * (n[i] >= 0.0f ? p[i] - lo[i] : hi[i] - p[i]);
+    w[d] = mi * (hi[i] - lo[i]);
+    mprod *= mi;
+    ++d;
   }
-  float h = n[0] * pos[0] + n[1] * pos[1] + n[2] * pos[2];
-  float s = 0.0f, t;
-  t = fmaxf(0.0f, h - (n[0] * bmin[0] + n[1] * bmin[1] + n[2] * bmin[2])); s += t * t;
-  t = fmaxf(0.0f, h - (n[0] * bmin[0] + n[1] * bmin[1] + n[2] * bmax[2])); s -= t * t;
-  t = fmaxf(0.0f, h - (n[0] * bmin[0] + n[1] * bmax[1] + n[2] * bmax[2])); s += t * t;
-  t = fmaxf(0.0f, h - (n[0] * bmin[0] + n[1] * bmax[1] + n[2] * bmin[2])); s -= t * t;
-  t = fmaxf(0.0f, h - (n[0] * bmax[0] + n[1] * bmax[1] + n[2] * bmin[2])); s += t * t;
-  t = fmaxf(0.0f, h - (n[0] * bmax[0] + n[1] * bmin[1] + n[2] * bmin[2])); s -= t * t;
-  t = fmaxf(0.0f, h - (n[0] * bmax[0] + n[1] * bmin[1] + n[2] * bmax[2])); s += t * t;
-  t = fmaxf(0.0f, h - (n[0] * bmax[0] + n[1] * bmax[1] + n[2] * bmax[2])); s -= t * t;
-  return fabsf(s / (2.0f * n[0] * n[1] * n[2]));
+  const double top = a[0] + a[1] + a[2];
+  double sum = 0.0;
+  if (d == 3) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const double x = top - ((c & 1) ? w[0] : 0.0) - ((c & 2) ? w[1] : 0.0) - ((c & 4) ? w[2] : 0.0);
+      const double g = x > 0.0 ? x * x : 0.0;
+      sum += (__popc(c) & 1) ? -g : g;
+    }
+    return fabs(sum) / (2.0 * mprod);
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double x = top - ((c & 1) ? w[0] : 0.0) - ((c & 2) ? w[1] : 0.0);
+    const double g = x > 0.0 ? x : 0.0;
+    sum += (__popc(c) & 1) ? -g : g;
+  }
+  return (hi[drop] - lo[drop]) * fabs(sum) / mprod;
 }
 
-__device__ __forceinline__ bool oct_norm_pos(const OctreeParams& P, const float pos[3], float np[3]) {
-  for (int c = 0; c < 3; ++c) np[c] = (pos[c] - P.minb[c]) * P.size_inv[c];
-  for (int c = 0; c < 3; ++c)
-    if (!(np[c] >= 0.0f && np[c] < 1.0f)) return false;
+// ---- addressing --------------------------------------------------------------
+struct OctKey {
+  unsigned x, y, z;  // cell on the 2^30 grid of the octree box
+};
+
+// Key of a position; false outside the box.  The box-relative position is
+// computed in FP32 (no contraction), as the paper computes it, so that every
+// cell decision matches an FP32 evaluation of its formula.
+__device__ __forceinline__ bool oct_key(const OctreeParams& P, float px, float py, float pz, OctKey& k) {
+  const float u0 = __fmul_rn(__fsub_rn(px, P.minb[0]), P.size_inv[0]);
+  const float u1 = __fmul_rn(__fsub_rn(py, P.minb[1]), P.size_inv[1]);
+  const float u2 = __fmul_rn(__fsub_rn(pz, P.minb[2]), P.size_inv[2]);
+  if (!(u0 >= 0.0f && u0 < 1.0f && u1 >= 0.0f && u1 < 1.0f && u2 >= 0.0f && u2 < 1.0f)) return false;
+  const float g = (float)(1u << kOctKeyBits);
+  k.x = (unsigned)__fmul_rn(u0, g);
+  k.y = (unsigned)__fmul_rn(u1, g);
+  k.z = (unsigned)__fmul_rn(u2, g);
   return true;
 }
 
-// ---- insert ---------------------------------------------------------------
-// Sequential form (one device thread): identical to the listing run by one
-// CPU thread.
-__device__ __forceinline__ int oct_split_seq(int* nodes, OctreeState* st, const OctreeParams& P, int idx, int count,
-                                             int depth) {
-  if (count >= P.split_count) {
-    if (depth + 1 > kOctMaxDepth) return 0;
-    if (count == P.split_count) {
-      int child = st->alloc;
-      st->alloc += 8;
-      if (child >= P.capacity) {
-        st->alloc = P.capacity + 1;
-        st->status |= NEB_STATUS_OCTREE_FULL;
-        return 0;
-      }
-      nodes[idx] = -child;
-      if (depth + 1 > st->depth) st->depth = depth + 1;
-      return 0;
-    }
-    return nodes[idx] < 0 ? nodes[idx] : 0;
+// Child slot (0..7, x + 2y + 4z) taken at level L >= 1 on the way to key k.
+__device__ __forceinline__ int oct_octant(const OctKey& k, int L) {
+  const int s = kOctKeyBits - L;
+  return (int)(((k.x >> s) & 1u) | (((k.y >> s) & 1u) << 1) | (((k.z >> s) & 1u) << 2));
+}
+
+// First level at which the paths to keys a and b part (kOctKeyBits + 1 when
+// they end in the same finest cell).
+__device__ __forceinline__ int oct_parting_level(const OctKey& a, const OctKey& b) {
+  const unsigned diff = (a.x ^ b.x) | (a.y ^ b.y) | (a.z ^ b.z);
+  return diff ? kOctKeyBits - (31 - __clz(diff)) : kOctKeyBits + 1;
+}
+
+// Leaf on the path of key k, found read-only from word `word` (value v) at
+// `level`: returns the leaf's word; level and v are updated to the leaf's.
+__device__ __forceinline__ int oct_descend(const int* __restrict__ nodes, const OctKey& k, int word, int& level,
+                                           int& v) {
+  while (v < 0) {
+    ++level;
+    word = -v + oct_octant(k, level);
+    v = __ldg(nodes + word);
   }
-  return count;
+  return word;
+}
+
+// ---- counting ------------------------------------------------------------------
+// A vertex that counted past the threshold of a cell waits for the vertex
+// that reached the threshold to publish the cell's child link.  The wait is
+// bounded: when it runs out the status bit is set and the vertex stays
+// counted in the cell.  Returns the link (< 0), or 0 when no link will come
+// (the word pool is exhausted) or the wait ran out.
+__device__ __forceinline__ int oct_wait_for_link(const int* word, OctreeState* st, const OctreeParams& P,
+                                                 int spin_limit) {
+  for (int i = 0; i < spin_limit; ++i) {
+    const int v = *((const volatile int*)word);
+    if (v < 0) return v;
+    if (*((const volatile int*)&st->alloc) > P.capacity) return 0;
+    __nanosleep(64);
+  }
+  atomicOr(&st->status, NEB_STATUS_SPIN_TIMEOUT);
+  return 0;
+}
+
+// Counts one vertex with key k (Sec. 5.1): the count of the leaf cell on its
+// path goes up by one.  The vertex that brings a cell to the split threshold
+// splits it (Sec. 5.2): it takes the next eight words of the pool, which
+// already hold the count a new cell starts with (the re-arm kernel writes it
+// into every free word), and publishes the negated index of the first in
+// place of the count.  That vertex stays counted in the cell it split.
+// Concurrent form: the increment is a compare-and-swap that fails when the
+// word changed, and a vertex that counted past the threshold before the link
+// appeared is counted again in the child once the link is published.
+// Sequential form (one thread, the deterministic mode): plain loads and
+// stores.  With no eight words left the pool is marked exhausted (alloc >
+// capacity, status bit) and the cell keeps counting; splits stop at level 30.
+template <bool kSequential>
+__device__ __forceinline__ void oct_count(int* nodes, OctreeState* st, const OctreeParams& P, const OctKey& k,
+                                          int spin_limit) {
+  // Plain reads are enough on the way down: a link never changes once
+  // published, and a stale count only makes the compare-and-swap fail and
+  // return the word's current value.
+  int word = 0, level = 0;
+  int v = nodes[0];
+  while (true) {
+    if (v < 0) {
+      ++level;
+      word = -v + oct_octant(k, level);
+      v = nodes[word];
+      continue;
+    }
+    if (kSequential) {
+      nodes[word] = v + 1;
+    } else {
+      const int seen = atomicCAS(nodes + word, v, v + 1);
+      if (seen != v) {  // changed under us: a newer count, or now a link
+        v = seen;
+        continue;
+      }
+    }
+    const int now = v + 1;
+    if (now < P.split_count || level >= kOctMaxDepth) return;
+    if (now == P.split_count) {
+      const int first = kSequential ? st->alloc : atomicAdd(&st->alloc, 8);
+      if (first + 8 > P.capacity) {
+        if (kSequential) {
+          st->alloc = P.capacity + 1;
+          st->status |= NEB_STATUS_OCTREE_FULL;
+        } else {
+          atomicExch(&st->alloc, P.capacity + 1);
+          atomicOr(&st->status, NEB_STATUS_OCTREE_FULL);
+        }
+        return;
+      }
+      if (kSequential) {
+        st->alloc = first + 8;
+        nodes[word] = -first;
+        if (level + 1 > st->depth) st->depth = level + 1;
+      } else {
+        atomicExch(nodes + word, -first);
+        atomicMax(&st->depth, level + 1);
+      }
+      return;
+    }
+    // Past the threshold: only a cell that could not split (the pool is
+    // exhausted) is seen so by a lone thread; concurrently, another vertex may
+    // be splitting this cell.
+    if (kSequential) return;
+    v = oct_wait_for_link(nodes + word, st, P, spin_limit);
+    if (v >= 0) return;
+  }
+}
+
+// Leaf word of a position once no cell can split any more (the pool was
+// exhausted before this launch): a read-only descent; -1 outside the box.
+__device__ __forceinline__ int oct_frozen_leaf(const int* nodes, const OctreeParams& P, const float pos[3]) {
+  if (P.stop_filling) return -1;
+  OctKey k;
+  if (!oct_key(P, pos[0], pos[1], pos[2], k)) return -1;
+  int level = 0, v = nodes[0];
+  int word = 0;
+  while (v < 0) {
+    ++level;
+    word = -v + oct_octant(k, level);
+    v = nodes[word];
+  }
+  return word;
+}
+
+__device__ __forceinline__ void oct_insert(int* nodes, OctreeState* st, const OctreeParams& P, const float pos[3],
+                                           int spin_limit) {
+  if (P.stop_filling) return;
+  OctKey k;
+  if (oct_key(P, pos[0], pos[1], pos[2], k)) oct_count<false>(nodes, st, P, k, spin_limit);
 }
 
 __device__ __forceinline__ void oct_insert_seq(int* nodes, OctreeState* st, const OctreeParams& P,
                                                const float pos[3]) {
   if (P.stop_filling) return;
-  float np[3];
-  if (!oct_norm_pos(P, pos, np)) return;
-  int v = nodes[0];
-  if (v >= 0) nodes[0] = ++v;
-  v = oct_split_seq(nodes, st, P, 0, v, 0);
-  int edge = 1, depth = 0;
-  while (v < 0) {
-    edge *= 2;
-    ++depth;
-    int ix = ((int)(np[0] * (float)edge)) & 1;
-    int iy = ((int)(np[1] * (float)edge)) & 1;
-    int iz = ((int)(np[2] * (float)edge)) & 1;
-    int idx = ix + 2 * (iy + 2 * iz) - v;
-    v = nodes[idx];
-    if (v >= 0) nodes[idx] = ++v;
-    v = oct_split_seq(nodes, st, P, idx, v, depth);
-  }
+  OctKey k;
+  if (oct_key(P, pos[0], pos[1], pos[2], k)) oct_count<true>(nodes, st, P, k, 0);
 }
 
-// Lock-free form: CAS increment of a non-negative counter
-// (increment_if_positive), one thread per split (the one that reaches the
-// threshold exactly), the others wait for the child pointer with a bounded
-// spin and then count in the child.  A spin that runs out sets
-// NEB_STATUS_SPIN_TIMEOUT and drops the insert; it never traps.
-__device__ __forceinline__ int oct_inc_atomic(int* nodes, int idx, bool frozen) {
-  // A plain (cacheable) first read is enough: a child pointer never changes
-  // once published, and a stale counter only makes the CAS below fail and
-  // return the current value.
-  int old = nodes[idx];
-  // frozen: the allocation overflowed before this kernel started, so no
-  // counter can turn into a child pointer any more and a plain atomic add is
-  // the same increment without CAS retries on crowded leaves
-  if (frozen && old >= 0) return atomicAdd(nodes + idx, 1) + 1;
-  while (true) {
-    if (old < 0) return old;
-    int prev = atomicCAS(nodes + idx, old, old + 1);
-    if (prev == old) return old + 1;
-    old = prev;
+// ---- density -------------------------------------------------------------------
+// Density of a leaf with count c > 0 at `level` on the path of key k, for the
+// plane through pos with normal n (Eq. octdensity): c over the number of
+// iterations and over the plane's area in the cell, the area held above a
+// fraction of the squared cell diagonal (0.1 of it for the centre query of
+// the robust estimate, 0.01 otherwise).  The cell box and the point are
+// taken relative to the octree box's lower corner, in FP64, and the quotient
+// is rounded to FP32.
+__device__ __forceinline__ float oct_leaf_density(const OctreeParams& P, int c, int level, const OctKey& k,
+                                                  const float pos[3], const float n[3], bool centre) {
+  const int s = kOctKeyBits - level;
+  const unsigned cell[3] = {k.x >> s, k.y >> s, k.z >> s};
+  double lo[3], hi[3], p[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double extent = ldexp(P.box_extent[a], -level);
+    lo[a] = (double)cell[a] * extent;
+    hi[a] = lo[a] + extent;
+    p[a] = (double)pos[a] - (double)P.minb[a];
   }
+  const double area = plane_box_area64(lo, hi, p, n);
+  const double diag = ldexp((double)P.scene_scale, -level);
+  const double floor_area = diag * diag * (centre ? 0.1 : 0.01);
+  return (float)((double)c / ((double)P.iter_clamp * (area > floor_area ? area : floor_area)));
 }
 
-__device__ __forceinline__ int oct_split_atomic(int* nodes, OctreeState* st, const OctreeParams& P, int idx,
-                                                int count, int depth, int spin_limit) {
-  if (count >= P.split_count) {
-    if (depth + 1 > kOctMaxDepth) return 0;
-    if (count == P.split_count) {
-      int child = atomicAdd(&st->alloc, 8);
-      if (child >= P.capacity) {
-        atomicExch(&st->alloc, P.capacity + 1);
-        atomicOr(&st->status, NEB_STATUS_OCTREE_FULL);
-        return 0;
-      }
-      atomicExch(nodes + idx, -child);
-      atomicMax(&st->depth, depth + 1);
-      return 0;
-    }
-    for (int it = 0; it < spin_limit; ++it) {
-      int c = *((volatile int*)(nodes + idx));
-      if (c < 0) return c;
-      if (*((volatile int*)&st->alloc) > P.capacity) return 0;
-      __nanosleep(64);
-    }
-    atomicOr(&st->status, NEB_STATUS_SPIN_TIMEOUT);
-    return 0;
-  }
-  return count;
+// Single density query; 0 for an empty cell or a point outside the box.
+__device__ __forceinline__ float oct_density(const int* __restrict__ nodes, const OctreeParams& P, const float pos[3],
+                                             const float n[3]) {
+  OctKey k;
+  if (!oct_key(P, pos[0], pos[1], pos[2], k)) return 0.0f;
+  int level = 0, v = __ldg(nodes);
+  oct_descend(nodes, k, 0, level, v);
+  return v > 0 ? oct_leaf_density(P, v, level, k, pos, n, false) : 0.0f;
 }
 
-__device__ __forceinline__ void oct_insert_atomic(int* nodes, OctreeState* st, const OctreeParams& P,
-                                                  const float pos[3], int spin_limit, bool frozen) {
-  if (P.stop_filling) return;
-  float np[3];
-  if (!oct_norm_pos(P, pos, np)) return;
-  int v = oct_inc_atomic(nodes, 0, frozen);
-  v = oct_split_atomic(nodes, st, P, 0, v, 0, spin_limit);
-  int edge = 1, depth = 0;
-  while (v < 0) {
-    edge *= 2;
-    ++depth;
-    int ix = ((int)(np[0] * (float)edge)) & 1;
-    int iy = ((int)(np[1] * (float)edge)) & 1;
-    int iz = ((int)(np[2] * (float)edge)) & 1;
-    int idx = ix + 2 * (iy + 2 * iz) - v;
-    v = oct_inc_atomic(nodes, idx, frozen);
-    v = oct_split_atomic(nodes, st, P, idx, v, depth, spin_limit);
-  }
-}
-
-// Leaf reached by a position once the octree can no longer split (allocation
-// overflowed): a read-only descent; -1 for positions outside the box.
-__device__ __forceinline__ int oct_frozen_leaf(const int* nodes, const OctreeParams& P, const float pos[3]) {
-  if (P.stop_filling) return -1;
-  float np[3];
-  if (!oct_norm_pos(P, pos, np)) return -1;
-  int idx = 0;
-  int v = nodes[0];
-  int edge = 1;
-  while (v < 0) {
-    edge *= 2;
-    int ix = ((int)(np[0] * (float)edge)) & 1;
-    int iy = ((int)(np[1] * (float)edge)) & 1;
-    int iz = ((int)(np[2] * (float)edge)) & 1;
-    idx = ix + 2 * (iy + 2 * iz) - v;
-    v = nodes[idx];
-  }
-  return idx;
-}
-
-// ---- query -----------------------------------------------------------------
-// get_density of the listing with the final normalisation in FP64:
-// rho = c / (min(iter, 1000) * max(minArea, A)).  *size receives the cell
-// diagonal when non-null (robust centre query: minArea uses 0.1 instead of 0.01).
-__device__ __forceinline__ float oct_density(const int* __restrict__ nodes, const OctreeParams& P, int depth,
-                                             const float pos[3], const float n[3], float* size) {
-  float off[3], np[3];
-  for (int c = 0; c < 3; ++c) {
-    off[c] = pos[c] - P.minb[c];
-    np[c] = off[c] * P.size_inv[c];
-  }
-  for (int c = 0; c < 3; ++c)
-    if (!(np[c] >= 0.0f && np[c] < 1.0f)) return 0.0f;
-  int grid = 1 << depth;
-  int ip[3];
-  for (int c = 0; c < 3; ++c) ip[c] = (int)(np[c] * (float)grid);
-  int v = __ldg(nodes);
-  int mask = grid;
-  while (v < 0) {
-    mask >>= 1;
-    int idx = ((ip[0] & mask) ? 1 : 0) + ((ip[1] & mask) ? 2 : 0) + ((ip[2] & mask) ? 4 : 0);
-    idx -= v;
-    v = __ldg(nodes + idx);
-  }
-  if (v > 0) {
-    int cur = grid / mask;
-    float cmin[3], cmax[3];
-    for (int c = 0; c < 3; ++c) {
-      float csz = 1.0f / ((float)cur * P.size_inv[c]);
-      int cp = ip[c] / mask;
-      cmin[c] = (float)cp * csz;
-      cmax[c] = cmin[c] + csz;
-    }
-    float area = intersection_area(cmin, cmax, off, n);
-    float diag = P.scene_scale / (float)cur;
-    float min_area = diag * diag;
-    if (size) { *size = diag; min_area *= 0.1f; } else min_area *= 0.01f;
-    double rho = (double)v / ((double)P.iter_clamp * (double)fmaxf(min_area, area));
-    return (float)rho;
-  }
-  return 0.0f;
-}
-
-// Cell of the leaf (v, mask) reached by a query with integer position ip,
-// offset position off and normal n: returns the count v (0 when empty) and
-// the area denominator max(minArea, A) of get_density's quotient.
-__device__ __forceinline__ int oct_leaf_terms(const OctreeParams& P, int grid, int mask, int v, const int ip[3],
-                                              const float off[3], const float n[3], float* size, float& denom) {
-  denom = 1.0f;
-  if (v <= 0) return 0;
-  int cur = grid / mask;
-  float cmin[3], cmax[3];
-  for (int c = 0; c < 3; ++c) {
-    float csz = 1.0f / ((float)cur * P.size_inv[c]);
-    int cp = ip[c] / mask;
-    cmin[c] = (float)cp * csz;
-    cmax[c] = cmin[c] + csz;
-  }
-  float area = intersection_area(cmin, cmax, off, n);
-  float diag = P.scene_scale / (float)cur;
-  float min_area = diag * diag;
-  if (size) { *size = diag; min_area *= 0.1f; } else min_area *= 0.01f;
-  denom = fmaxf(min_area, area);
-  return v;
-}
-
-// The listing's quotient with its normalisation in FP64, rounded to FP32.
-__device__ __forceinline__ float oct_rho(int v, int iter_clamp, float denom) {
-  if (v <= 0) return 0.0f;
-  return (float)((double)v / ((double)iter_clamp * (double)denom));
-}
-
-// get_density_robust of the listing: median of the centre query and four
-// queries displaced by 1.1 cell diagonals along the tangents of the Duff et
-// al. basis of the geometric normal; ties go to the greater value.  A
-// displaced query walks the same nodes as the centre one down to the first
-// level where its cell coordinates differ, so it resumes from the centre's
-// recorded path there instead of at the root (same nodes, same result).
-__device__ __forceinline__ float oct_density_robust(const int* __restrict__ nodes, const OctreeParams& P, int depth,
+// Robust density: the centre query and four queries at 1.1 cell diagonals
+// from the point along the two tangents of the Duff et al. basis of the
+// geometric normal; the result is the median of the positive ones, the upper
+// of the middle two for an even number, 0 when none is positive.  The step
+// and the displaced points are FP32 (no contraction), as the paper computes
+// them; the step is 1.1e-3 when the centre cell is empty.  A displaced query
+// runs through the same words as the centre query down to the level where
+// their paths part, so it resumes from the centre's path there.
+__device__ __forceinline__ float oct_density_robust(const int* __restrict__ nodes, const OctreeParams& P,
                                                     const float pos[3], const float n[3], int* queries) {
-  int cv[5] = {0, 0, 0, 0, 0};     // leaf counts of the five queries
-  float cd[5] = {1, 1, 1, 1, 1};   // their area denominators
-  float diag = 1e-3f;
-  const int grid = 1 << depth;
-  // centre query with its path: vs[L] = node value at level L
-  int vs[kOctMaxDepth + 2];
-  int ipc[3];
-  int Lc = -1;
-  {
-    float off[3], np[3];
-    bool in = true;
-    for (int c = 0; c < 3; ++c) {
-      off[c] = pos[c] - P.minb[c];
-      np[c] = off[c] * P.size_inv[c];
-      in = in && (np[c] >= 0.0f && np[c] < 1.0f);
+  float found[5];
+  int nfound = 0;
+  float step = 1e-3f;
+  // centre query, remembering the word value at every level of its path
+  int path[kOctMaxDepth + 1];
+  OctKey kc;
+  int centre_level = -1;
+  if (oct_key(P, pos[0], pos[1], pos[2], kc)) {
+    int level = 0, v = __ldg(nodes);
+    path[0] = v;
+    while (v < 0) {
+      ++level;
+      v = __ldg(nodes + (-v + oct_octant(kc, level)));
+      path[level] = v;
     }
-    if (in) {
-      for (int c = 0; c < 3; ++c) ipc[c] = (int)(np[c] * (float)grid);
-      int v = __ldg(nodes);
-      int mask = grid;
-      int L = 0;
-      vs[0] = v;
-      while (v < 0) {
-        mask >>= 1;
-        int idx = ((ipc[0] & mask) ? 1 : 0) + ((ipc[1] & mask) ? 2 : 0) + ((ipc[2] & mask) ? 4 : 0);
-        idx -= v;
-        v = __ldg(nodes + idx);
-        vs[++L] = v;
-      }
-      Lc = L;
-      cv[0] = oct_leaf_terms(P, grid, mask, v, ipc, off, n, &diag, cd[0]);
+    centre_level = level;
+    if (v > 0) {
+      found[nfound++] = oct_leaf_density(P, v, level, kc, pos, n, true);
+      step = ldexpf(P.scene_scale, -level);
     }
   }
-  diag *= 1.1f;
+  step = __fmul_rn(step, 1.1f);
   float3 t, b;
   onb(f3(n[0], n[1], n[2]), t, b);
-  float3 p = f3(pos[0], pos[1], pos[2]);
-  float3 q[4] = {add(p, mul(t, diag)), sub(p, mul(t, diag)), add(p, mul(b, diag)), sub(p, mul(b, diag))};
-  // The four displaced walks are independent: they step down together, so
-  // each step issues up to four loads at once instead of one chain at a time.
-  int v4[4], m4[4], ip4[4][3];
+  const float dx[4] = {t.x, -t.x, b.x, -b.x}, dy[4] = {t.y, -t.y, b.y, -b.y}, dz[4] = {t.z, -t.z, b.z, -b.z};
+  // the four displaced walks step down together: each step issues up to four
+  // independent loads instead of one chain at a time
+  float q[4][3];
+  OctKey kq[4];
+  int vq[4], lq[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    float qq[3] = {q[i].x, q[i].y, q[i].z};
-    bool in = true;
-    for (int c = 0; c < 3; ++c) {
-      float np = (qq[c] - P.minb[c]) * P.size_inv[c];
-      in = in && (np >= 0.0f && np < 1.0f);
-      ip4[i][c] = in ? (int)(np * (float)grid) : 0;
-    }
-    v4[i] = 0;  // outside the scene box: no walk, count 0
-    m4[i] = grid;
-    if (in) {
-      if (Lc >= 0) {
-        unsigned diff = (unsigned)((ip4[i][0] ^ ipc[0]) | (ip4[i][1] ^ ipc[1]) | (ip4[i][2] ^ ipc[2]));
-        // first level whose octant differs: mask (grid >> L) equals the top differing bit
-        int Ld = diff ? depth - (31 - __clz(diff)) : depth + 1;
-        int L = Ld - 1 < Lc ? Ld - 1 : Lc;
-        v4[i] = vs[L];
-        m4[i] = grid >> L;
+    q[i][0] = __fadd_rn(pos[0], __fmul_rn(dx[i], step));
+    q[i][1] = __fadd_rn(pos[1], __fmul_rn(dy[i], step));
+    q[i][2] = __fadd_rn(pos[2], __fmul_rn(dz[i], step));
+    vq[i] = 0;  // outside the box: no walk, nothing found
+    lq[i] = 0;
+    if (oct_key(P, q[i][0], q[i][1], q[i][2], kq[i])) {
+      if (centre_level >= 0) {
+        const int part = oct_parting_level(kc, kq[i]);
+        lq[i] = part - 1 < centre_level ? part - 1 : centre_level;
+        vq[i] = path[lq[i]];
       } else {
-        v4[i] = __ldg(nodes);
+        vq[i] = __ldg(nodes);
       }
     }
   }
-  while (v4[0] < 0 || v4[1] < 0 || v4[2] < 0 || v4[3] < 0) {
+  while (vq[0] < 0 || vq[1] < 0 || vq[2] < 0 || vq[3] < 0) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      if (v4[i] < 0) {
-        m4[i] >>= 1;
-        int mk = m4[i];
-        int idx = ((ip4[i][0] & mk) ? 1 : 0) + ((ip4[i][1] & mk) ? 2 : 0) + ((ip4[i][2] & mk) ? 4 : 0);
-        v4[i] = __ldg(nodes + (idx - v4[i]));
+    for (int i = 0; i < 4; ++i)
+      if (vq[i] < 0) {
+        ++lq[i];
+        vq[i] = __ldg(nodes + (-vq[i] + oct_octant(kq[i], lq[i])));
       }
-    }
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    if (v4[i] > 0) {
-      float qq[3] = {q[i].x, q[i].y, q[i].z};
-      float off[3];
-      for (int c = 0; c < 3; ++c) off[c] = qq[c] - P.minb[c];
-      cv[i + 1] = oct_leaf_terms(P, grid, m4[i], v4[i], ip4[i], off, n, nullptr, cd[i + 1]);
+  for (int i = 0; i < 4; ++i)
+    if (vq[i] > 0) {
+      const float r = oct_leaf_density(P, vq[i], lq[i], kq[i], q[i], n, false);
+      if (r > 0.0f) found[nfound++] = r;
     }
-  }
   *queries += 5;
-  // Median of the positive results, ties to the greater: the listing's partial
-  // selection sort over the FP64 quotients rounded to FP32.
-  float d[5];
-  int count = 0;
-#pragma unroll
-  for (int i = 0; i < 5; ++i)
-    if (cv[i] > 0) d[count++] = oct_rho(cv[i], P.iter_clamp, cd[i]);
-  if (count == 0) return 0.0f;
-  const int m = count / 2;
-  for (int i = 0; i <= m; ++i)
-    for (int j = i + 1; j < count; ++j)
-      if (d[j] < d[i]) { float tmp = d[i]; d[i] = d[j]; d[j] = tmp; }
-  return d[m];
+  if (nfound == 0) return 0.0f;
+  // insertion sort of at most five values, then the upper median
+  for (int i = 1; i < nfound; ++i) {
+    const float x = found[i];
+    int j = i - 1;
+    while (j >= 0 && found[j] > x) {
+      found[j + 1] = found[j];
+      --j;
+    }
+    found[j + 1] = x;
+  }
+  return found[nfound / 2];
 }
 
 }  // namespace neb

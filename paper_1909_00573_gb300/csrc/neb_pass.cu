@@ -499,8 +499,7 @@ __global__ void __launch_bounds__(kThreads) k_emission(SceneView s, IterParams i
           const float4 nn = nv.nrm[prev];
           const float pp[3] = {xp4.x, xp4.y, xp4.z}, qq[3] = {nn.x, nn.y, nn.z};
           int queries = 0;
-          rho = robust ? oct_density_robust(oct_nodes, oct, oct_state->depth, pp, qq, &queries)
-                       : oct_density(oct_nodes, oct, oct_state->depth, pp, qq, nullptr);
+          rho = robust ? oct_density_robust(oct_nodes, oct, pp, qq, &queries) : oct_density(oct_nodes, oct, pp, qq);
         }
       } else {
         continue;  // the NEE store overflowed; the event cannot be weighted
@@ -589,8 +588,8 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
             const int li = __float_as_int(ph.mis.y);
             const float p_l = light_pdf(s, li, yl, hp);
             float pp[3] = {hp.x, hp.y, hp.z}, nn[3] = {hn.x, hn.y, hn.z};
-            const float rho = robust ? oct_density_robust(oct_nodes, oct, oct_state->depth, pp, nn, &queries)
-                                     : (++queries, oct_density(oct_nodes, oct, oct_state->depth, pp, nn, nullptr));
+            const float rho = robust ? oct_density_robust(oct_nodes, oct, pp, nn, &queries)
+                                     : (++queries, oct_density(oct_nodes, oct, pp, nn));
             if (p_l > 0.0f) {
               const float R = cos_y * kInvPi * cos_hit / d2;
               const float num = (float)ip.n_lp * pir2 * (p_lp / p_l) * R;

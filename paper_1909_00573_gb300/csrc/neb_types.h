@@ -29,14 +29,19 @@ struct __align__(16) BVH4Node {
 };
 constexpr int kEmptyChild = (int)0x80000000;
 
-// Octree globals of Appendix B (initialize / set_iteration), device resident.
+// Density-octree parameters, passed to the kernels by value (Sec. 5): the
+// octree box (the scene box grown by 0.2 %), the word pool's size, and the
+// quantities that change with the iteration.
 struct OctreeParams {
-  float minb[3], size_inv[3], scene_scale;
-  int capacity;
-  int split_count;   // SPLIT_FACTOR * min(iter, 1000)
-  int iter_clamp;
-  int stop_filling;
-  int init_value;    // ceil(SPLIT_FACTOR / 4 * iter)
+  float minb[3];        // lower corner of the octree box
+  float size_inv[3];    // 1 / edge length of the box, per axis (FP32)
+  double box_extent[3]; // 1 / size_inv, the edge lengths the cell boxes are cut from (FP64)
+  float scene_scale;    // length of the box diagonal
+  int capacity;         // words in the pool, 8m + 1
+  int split_count;      // a cell splits when its count reaches split_factor * min(iter, 1000)
+  int iter_clamp;       // min(iter, 1000): densities are divided by it
+  int stop_filling;     // iter > 1000: counting stops
+  int init_value;       // count of a new cell: ceil(split_factor * iter / 4)
 };
 
 struct OctreeState {  // device memory

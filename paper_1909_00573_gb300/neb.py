@@ -284,7 +284,7 @@ def plane_box_area(boxes, pos, nrm):
     b = np.ascontiguousarray(boxes, np.float32).reshape(-1, 6)
     p = np.ascontiguousarray(pos, np.float32).reshape(-1, 3)
     n = np.ascontiguousarray(nrm, np.float32).reshape(-1, 3)
-    out = np.zeros(len(b), np.float32)
+    out = np.zeros(len(b), np.float64)
     _check(lib().neb_plane_box_area(_p(b), _p(p), _p(n), len(b), _p(out)))
     return out
 

@@ -1,13 +1,15 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle on
 the same seeded inputs.
 
-Tolerances: integer / index work (Philox, octree nodes, neighbour counts,
-closest-hit primitive ids) is compared bit-exactly; FP32 arithmetic that both
-sides perform in the same order without contraction (plane/box area, octree
-density, hit distances) is compared bit-exactly too; per-path radiometric
-contributions (FP32 on the GPU, FP64 in the oracle) within 1e-4 relative on at
-least 99.9 % of paths, the rest only where a discrete decision flips (grazing
-hit, merge radius, octree cell boundary)."""
+Tolerances: integer / index work (Philox, octree words, neighbour counts,
+closest-hit primitive ids) is compared bit-exactly, and so are the FP32 hit
+distances of the watertight test (both sides run the published algorithm's
+FP32 operations in its order, without contraction); the plane/box area is
+FP64 on both sides, each in its own arrangement of Eq. area, and agrees to
+1e-9 relative; densities (an FP64 quotient rounded to FP32) agree to 2 ulp;
+per-path radiometric contributions (FP32 on the GPU, FP64 in the oracle)
+within 1e-4 relative on at least 99.9 % of paths, the rest only where a
+discrete decision flips (grazing hit, merge radius, octree cell boundary)."""
 import os
 
 import numpy as np
@@ -42,7 +44,10 @@ def test_philox_device_equals_oracle(neb, oracle):
         assert g[i].tolist() == oracle.philox4x32_10(ctr[i], key).tolist()
 
 
-def test_plane_box_area_bit_exact(neb, oracle):
+def test_plane_box_area_equals_oracle(neb, oracle):
+    """Eq. area in FP64 on both sides (the kernel in a mirrored frame, the
+    oracle as the plain corner sum), including the 1D and 2D cases the FP32
+    normal selects and points outside the box."""
     rng = np.random.default_rng(12)
     n = 4000
     lo = rng.uniform(-2, 2, (n, 3)).astype(np.float32)
@@ -51,11 +56,13 @@ def test_plane_box_area_bit_exact(neb, oracle):
     nrm = rng.normal(size=(n, 3))
     nrm[: n // 4, 0] = 0.0                      # the 2D cases
     nrm[n // 4: n // 2] = [0.0004, 0.9999999, 0.0002]   # the 1D cases
+    nrm[n // 2: n // 2 + 200, 1] = 1.5e-4       # just above the 2D threshold
     nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
     nrm = nrm.astype(np.float32)
     g = neb.plane_box_area(np.concatenate([lo, hi], 1), pos, nrm)
-    o = np.array([oracle.intersection_area(lo[i], hi[i], pos[i], nrm[i]) for i in range(n)], np.float32)
-    assert np.array_equal(g.view(np.int32), o.view(np.int32))
+    o = np.array([oracle.intersection_area(lo[i], hi[i], pos[i], nrm[i]) for i in range(n)])
+    face = np.prod(hi.astype(np.float64) - lo, axis=1) ** (2 / 3)
+    assert np.all(np.abs(g - o) <= 1e-9 * np.abs(o) + 1e-12 * face)
 
 
 # --------------------------------------------------------------------------
@@ -73,7 +80,9 @@ def _octree_inputs(seed, n_iter=3, n=6000):
 
 
 @pytest.mark.parametrize("split", [4, 8])
-def test_octree_sequential_bit_exact(neb, oracle, split):
+def test_octree_sequential_equals_oracle(neb, oracle, split):
+    """Deterministic mode: the device's word array equals the oracle's tree
+    written in the flat layout, word for word, after every iteration."""
     its = _octree_inputs(13 + split)
     g = neb.Octree([0, 0, 0], [1, 1, 1], 1 << 14, split)
     o = oracle.Octree([0, 0, 0], [1, 1, 1], 1 << 14, split)
@@ -95,7 +104,9 @@ def test_octree_sequential_bit_exact(neb, oracle, split):
     for robust in (False, True):
         gr = g.density(q, nq, robust)
         orr = o.density(q, nq, robust)
-        assert np.array_equal(gr.view(np.int32), orr.view(np.int32)), robust
+        # FP64 quotients from two arrangements of Eq. area, rounded to FP32
+        assert np.all(np.abs(gr - orr) <= 2.4e-7 * np.abs(orr)), robust
+        assert np.mean(gr == orr) >= 0.995, robust
 
 
 def test_octree_concurrent_conserves_counts(neb):
@@ -410,9 +421,9 @@ def test_tiny_room_per_path_parity(neb, oracle):
     for k in range(3):
         ok = _compare(gsplit[k].sum(-1), osplit[k].sum(-1))
         assert ok.mean() >= 0.995, (k, ok.mean())
-    # the density at every NEE vertex: the octree arithmetic is bit-exact for
-    # identical positions; here positions differ in the last bits (device
-    # sinf/cosf in direction sampling), which moves the plane/box area slightly
+    # the density at every NEE vertex: equal to 2 ulp for identical positions;
+    # here positions differ in the last bits (device sinf/cosf in direction
+    # sampling), which moves the plane/box area slightly
     both = (grho >= 0) & (orho >= 0)
     assert ((grho >= 0) != (orho >= 0)).mean() < 1e-3
     rel = np.abs(grho[both] - orho[both]) / np.maximum(np.abs(orho[both]), 1e-30)
