@@ -1468,6 +1468,11 @@ int orc_render(const orc_scene* scene_in, const orc_config* cfg, int n_iter, dou
   if (pe > P) pe = P;
   int np = pe - pb > 0 ? pe - pb : 0;
   orc_octree* oct = orc_octree_new(s.bmin, s.bmax, cfg->octree_capacity, cfg->split_factor);
+  double* before = NULL;   /* the sums before the current iteration, for iter_images */
+  if (cfg->iter_images) {
+    before = (double*)malloc(sizeof(double) * (size_t)P * 3);
+    memcpy(before, accum, sizeof(double) * (size_t)P * 3);
+  }
   cv_t* paths = (cv_t*)calloc((size_t)np * (D + 1), sizeof(cv_t));
   int* plen = (int*)calloc((size_t)(np > 0 ? np : 1), sizeof(int));
   rh_t* rh = (rh_t*)calloc((size_t)np * D + 1, sizeof(rh_t));
@@ -1819,7 +1824,15 @@ int orc_render(const orc_scene* scene_in, const orc_config* cfg, int n_iter, dou
       }
     }
     if (cfg->iter_seconds) cfg->iter_seconds[it] = now_seconds() - t_start;
+    if (cfg->iter_images) {
+      double* img = cfg->iter_images + (size_t)it * (size_t)P * 3;
+      for (size_t j = 0; j < (size_t)P * 3; ++j) {
+        img[j] = accum[j] - before[j];
+        before[j] = accum[j];
+      }
+    }
   }
+  free(before);
   st[ORC_ST_OCTREE_NODES] = oct->words_used < oct->capacity ? oct->words_used : oct->capacity;
   st[ORC_ST_OCTREE_DEPTH] = oct->depth;
   if (stats) memcpy(stats, st, sizeof(st));

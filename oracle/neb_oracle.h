@@ -49,6 +49,7 @@ typedef struct {
   int pixel_begin, pixel_end; /* camera paths traced: [begin, end) (row-major), end<=0: all */
   double* iter_seconds;       /* optional [n_iter]: wall time of each iteration (BVH build excluded) */
   int lp_photons;             /* conventional light photons per iteration (n_LP, Sec. 6.1; strategy bit 8) */
+  double* iter_images;        /* optional [n_iter][H*W*3]: each iteration's own contributions */
 } orc_config;
 
 /* stats[] slots filled by orc_render (summed over iterations) */

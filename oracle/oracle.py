@@ -47,7 +47,7 @@ class _Config(C.Structure):
                 ("merge_radius", C.c_float), ("octree_capacity", C.c_int), ("split_factor", C.c_int),
                 ("seed", C.c_uint64), ("density_mode", C.c_int), ("strategy_mask", C.c_uint32),
                 ("first_iteration", C.c_int), ("pixel_begin", C.c_int), ("pixel_end", C.c_int),
-                ("iter_seconds", C.c_void_p), ("lp_photons", C.c_int)]
+                ("iter_seconds", C.c_void_p), ("lp_photons", C.c_int), ("iter_images", C.c_void_p)]
 
 
 _lib = None
@@ -242,18 +242,21 @@ def mis_weights_lp(verts, light, merge_radius, rho, n_lp, mask=15):
     return w[:2 * len(V) - 1]
 
 
-def render(scene, cfg, n_iter=None, first_iteration=1, pixel_range=None, want_split=True, want_rho=False):
+def render(scene, cfg, n_iter=None, first_iteration=1, pixel_range=None, want_split=True, want_rho=False,
+           want_iterations=False):
     """Run the oracle.  Returns dict with accum [H,W,3] (sum over iterations),
     split [4,H,W,3] of the last iteration (random hits, NEE, NEB photon merges,
-    light-photon merges), rho [H*W, D-1] and stats."""
+    light-photon merges), rho [H*W, D-1], stats and, with want_iterations,
+    iterations [n_iter,H,W,3] (each iteration's own image)."""
     n_iter = cfg.iterations if n_iter is None else n_iter
     s, keep = _scene_struct(scene)
     pb, pe = (0, 0) if pixel_range is None else pixel_range
     iter_sec = np.zeros(max(int(n_iter), 1), np.float64)
+    P = cfg.width * cfg.height
+    iters = np.zeros((max(int(n_iter), 1), P, 3), np.float64) if want_iterations else None
     c = _Config(cfg.width, cfg.height, cfg.max_depth, cfg.merge_radius, cfg.octree_capacity, cfg.split_factor,
                 cfg.seed, cfg.density_mode, cfg.strategy_mask, first_iteration, pb, pe, _ptr(iter_sec),
-                getattr(cfg, "lp_photons", 0))
-    P = cfg.width * cfg.height
+                getattr(cfg, "lp_photons", 0), _ptr(iters))
     accum = np.zeros((P, 3), np.float64)
     split = np.zeros((4, P, 3), np.float64) if want_split else None
     rho = np.zeros((P, max(cfg.max_depth - 1, 1)), np.float32) if want_rho else None
@@ -268,6 +271,8 @@ def render(scene, cfg, n_iter=None, first_iteration=1, pixel_range=None, want_sp
         out["split"] = split.reshape(4, cfg.height, cfg.width, 3)
     if want_rho:
         out["rho"] = rho
+    if want_iterations:
+        out["iterations"] = iters[:n_iter].reshape(n_iter, cfg.height, cfg.width, 3)
     return out
 
 
