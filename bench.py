@@ -1,11 +1,14 @@
 #!/usr/bin/env python
 """Benchmark of the NEB iteration on one or more GB300s.
 
-Workload: the large-city scene (400 x 400 seeded boxes, ~1.95M triangles, a
-glass torus of extent diag/1000, 16 sphere lights), 1280 x 720 camera paths
-per iteration, maximum path length 10, merge radius 1e-3 of the torus extent,
-4M-node density octree, split factor 4.  A step is one NEB iteration (all
-passes) over the 921,600 paths of one image.
+Workload (default): the many-lights scene, the largest single-GPU
+configuration: the large-city geometry (400 x 400 seeded boxes, ~1.95M
+triangles, a glass torus of extent diag/1000) with 65,536 sphere lights chosen
+through a power alias table and a rough-conductor roof patch, 1920 x 1080
+camera paths per iteration, maximum path length 10, merge radius 1e-3 of the
+torus extent, 4M-word density octree, split factor 4.  A step is one NEB
+iteration (all passes) over the 2,073,600 paths of one image.
+--workload large_city: the same city with 16 lights at 1280 x 720.
 
 Prints one JSON line (rank 0).  value = camera paths per second over all GPUs
 (Mpaths/s) with the scene resident in HBM; e2e = the same metric through the
@@ -31,7 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Mpaths/s"
-WORKLOAD = "large_city"
+WORKLOAD = "many_lights"
 
 
 def parse():
@@ -59,6 +62,9 @@ def parse():
                     help="NEB+LP (Sec. 6.1): conventional light photons per iteration in addition to NEB photons")
     ap.add_argument("--autotune", type=int, default=0,
                     help="run the autotuner (this many iterations per candidate) before the warm-up")
+    ap.add_argument("--live-octree-cap", type=int, default=1 << 27,
+                    help="word pool of the second measurement, large enough that the octree never fills "
+                         "(0: skip it)")
     return ap.parse_args()
 
 
@@ -169,20 +175,16 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
-# stage's kernel, from one ncu capture of the full workload (profiles/ holds
-# the summary and the command).  It is reported only while the kernel's
-# sources hash to the value recorded with the capture, else null.
+# Counters of a stage's kernel from ncu captures of these sources (profiles/
+# holds the summaries and the commands): DRAM traffic (dram__bytes_read.sum +
+# dram__bytes_write.sum) per launch at the full workload, and from the full
+# capture of a smaller image of the same scene the lane efficiency
+# (smsp__thread_inst_executed_per_inst_executed / 32) and the issue-active
+# fraction (sm__inst_issued ... per active cycle).  Reported only while the
+# kernel's sources hash to the value recorded with the capture, else null.
 TRAFFIC_SOURCES = ("paper_1909_00573_gb300/csrc/neb_trace.cu", "paper_1909_00573_gb300/csrc/neb_device.cuh",
                    "paper_1909_00573_gb300/csrc/neb_types.h")
-NCU_TRAFFIC = {  # (workload, stage): DRAM bytes per launch from one ncu capture of these sources
-    ("large_city", "trace_camera"): {"bytes_per_launch": 73595264,
-                                     "sources_sha256": "afee030ef903c525ac56b45f607fb4fabde1e33e6e4f75029c1adb627efe2e76",
-                                     "profile": "profiles/k_trace_closest_large_city.md"},
-    ("large_city", "shadow"): {"bytes_per_launch": 217656448,   # mean of the two launches of an iteration
-                               "sources_sha256": "afee030ef903c525ac56b45f607fb4fabde1e33e6e4f75029c1adb627efe2e76",
-                               "profile": "profiles/k_trace_shadow_large_city.md"},
-}
+NCU_COUNTERS = {}  # (workload, stage): {"bytes_per_launch", "lane_efficiency", "issue_active", "sources_sha256", "profile"}
 
 
 def sources_sha256():
@@ -193,11 +195,12 @@ def sources_sha256():
     return h.hexdigest()
 
 
-def measured_traffic(workload, stage):
-    e = NCU_TRAFFIC.get((workload, stage))
-    if not e or e["bytes_per_launch"] is None or e["sources_sha256"] != sources_sha256():
-        return None, None
-    return e["bytes_per_launch"], e["profile"]
+def measured_counters(workload, stage):
+    """The stored ncu counters of (workload, stage), or None when the sources changed since."""
+    e = NCU_COUNTERS.get((workload, stage))
+    if not e or e["sources_sha256"] != sources_sha256():
+        return None
+    return e
 
 
 def stage_bytes(stage, d, P, iters):
@@ -564,14 +567,69 @@ def main():
         per_launch = byt / dom_launches
         avg_ms = dom_ms / dom_launches
         achieved = per_launch / (avg_ms / 1000.0) / 1e9
-        traffic, traffic_src = measured_traffic(args.workload, dom)
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src, "peak_kind": peak_kind,
-                "bytes_per_launch": per_launch, "avg_launch_ms": avg_ms,
+        cnt = measured_counters(args.workload, dom)
+        traffic = cnt["bytes_per_launch"] if cnt else None
+        roof = {"bound": cnt["bound"] if cnt else "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "peak_kind": peak_kind, "bytes_per_launch": per_launch, "avg_launch_ms": avg_ms,
                 "achieved_without_traversal": (None if byt_nt is None else
-                                               (byt_nt / dom_launches) / (avg_ms / 1000.0) / 1e9)}
+                                               (byt_nt / dom_launches) / (avg_ms / 1000.0) / 1e9),
+                "dram_frac": (None if traffic is None else traffic / (avg_ms / 1000.0) / 1e9 / peak),
+                "lane_efficiency": cnt["lane_efficiency"] if cnt else None,
+                "issue_active": cnt["issue_active"] if cnt else None,
+                "headroom": (None if not cnt else cnt["lane_efficiency"] * cnt["issue_active"]),
+                "counters_source": cnt["profile"] if cnt else None}
     total_stage_ms = sum(v[0] for v in stages.values())
     ctx.close()
+
+    # ---- the octree from a fresh start, in contexts created after every
+    # kernel has been loaded: (a) the workload's word pool, iterations timed
+    # one by one up to the warm-up count, and the iteration at which the pool
+    # fills (from then on no cell splits, inserts count in their leaf: the
+    # regime of the timed steps above); (b) a pool the tree does not fill
+    # before the end of the timed steps, whose timed steps run the splitting
+    # inserts (compare-and-swap counts)
+    def fresh_run(capacity, timed_steps):
+        rcx = scenes.workload(args.workload)[1]
+        rcx.width, rcx.height, rcx.seed = rc.width, rc.height, rc.seed
+        rcx.strategy_mask, rcx.lp_photons = rc.strategy_mask, rc.lp_photons
+        rcx.octree_capacity = capacity
+        cx = neb.Context(neb.make_config(rcx, bvh_builder=args.bvh), stream.cuda_stream)
+        cx.scene_upload(scene)
+        cx.build_bvh()
+        per_it, full_at = [], None
+        for i in range(max(args.warmup, 1)):
+            w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            w0.record(stream)
+            cx.iterate(1)
+            w1.record(stream)
+            torch.cuda.synchronize()
+            per_it.append(w0.elapsed_time(w1))
+            if full_at is None and cx.stats(check=False)["status"] & neb.STATUS_OCTREE_FULL:
+                full_at = i + 1
+        out = {"capacity_words": capacity, "ms_per_iteration_from_the_first": per_it,
+               "full_at_iteration": full_at}
+        if timed_steps > 0:
+            l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0.record(stream)
+            cx.iterate(timed_steps)
+            l1.record(stream)
+            torch.cuda.synchronize()
+            ms_t = l0.elapsed_time(l1)
+            out.update({"timed_steps_ms_per_step": ms_t / timed_steps,
+                        "timed_steps_value": job_value(1, P, timed_steps, ms_t / 1000.0)})
+        st = cx.stats(check=False)
+        if full_at is None and st["status"] & neb.STATUS_OCTREE_FULL:
+            out["full_during_timed_steps"] = True
+        out.update({"words_used": st["octree_nodes"], "depth": st["octree_depth"]})
+        cx.close()
+        return out
+
+    octree = {"timed_regime": "frozen (pool full: inserts count in their leaf, no splits)"
+              if (s0["status"] & neb.STATUS_OCTREE_FULL) else "live (cells still split)",
+              "fill": fresh_run(rc.octree_capacity, 0)}
+    if args.live_octree_cap > 0:
+        octree["live"] = fresh_run(args.live_octree_cap, args.steps)
 
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
@@ -618,7 +676,7 @@ def main():
                 "rates": rates(d, world, ms),
                 "counters_per_step": {k: (v / args.steps if not isinstance(v, list) else [x / args.steps for x in v])
                                       for k, v in d.items() if k not in ("iterations",)},
-                "status": s1["status"], "bvh_build_ms": bvh_build_ms,
+                "status": s1["status"], "octree": octree, "bvh_build_ms": bvh_build_ms,
                 "bvh_sah": {"node_visits": bvh_cost[0], "prim_tests": bvh_cost[1]},
                 "bvh": "PLOC" if args.bvh == 0 else "LBVH", "tuning": tuning,
                 "tuning_source": "autotuned" if args.autotune > 0 else "defaults"}

@@ -71,19 +71,21 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
 
 def test_secondary_rates_and_traffic_lookup(monkeypatch):
-    """Rates are whole-job counts per second; a DRAM-traffic figure is used
-    only for its workload and stage, and only while the traversal sources
-    hash to those it was captured from."""
+    """Rates are whole-job counts per second; stored ncu counters are used
+    only for their workload and stage, and only while the traversal sources
+    hash to those they were captured from."""
     import bench
     d = {"camera_rays": 4e6, "shadow_rays": 3e6, "photon_hits": 1e6, "merge_tests": 2e6, "merges": 5e4,
          "octree_inserts": 3e6, "octree_queries": 1e5}
     r = bench.rates(d, 2, 1000.0)                      # two ranks, one second
     assert r["Mrays_per_s"] == 16.0 and r["Mmerges_per_s"] == 0.1 and r["Moctree_inserts_per_s"] == 6.0
     assert bench.rates(d, 1, 0.0) is None
-    key = ("large_city", "trace_camera")
-    entry = dict(bench.NCU_TRAFFIC[key])
-    monkeypatch.setitem(bench.NCU_TRAFFIC, key, dict(entry, sources_sha256=bench.sources_sha256()))
-    assert bench.measured_traffic("large_city", "trace_camera") == (entry["bytes_per_launch"], entry["profile"])
-    assert bench.measured_traffic("many_lights", "trace_camera") == (None, None)
-    monkeypatch.setitem(bench.NCU_TRAFFIC, key, dict(entry, sources_sha256="0" * 64))
-    assert bench.measured_traffic("large_city", "trace_camera") == (None, None)
+    key = ("many_lights", "trace_camera")
+    entry = {"bound": "issue", "bytes_per_launch": 1.0e8, "lane_efficiency": 0.4, "issue_active": 0.6,
+             "profile": "profiles/x.md", "sources_sha256": bench.sources_sha256()}
+    monkeypatch.setitem(bench.NCU_COUNTERS, key, entry)
+    assert bench.measured_counters("many_lights", "trace_camera") == entry
+    assert bench.measured_counters("large_city", "trace_camera") is None
+    assert bench.measured_counters("many_lights", "shadow") is None
+    monkeypatch.setitem(bench.NCU_COUNTERS, key, dict(entry, sources_sha256="0" * 64))
+    assert bench.measured_counters("many_lights", "trace_camera") is None
