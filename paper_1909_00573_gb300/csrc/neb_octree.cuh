@@ -15,6 +15,8 @@
 // and scaling by a power of two is exact in FP32, so this is the same cell
 // for every level as computing floor(u 2^L) level by level.
 #pragma once
+#include <climits>
+
 #include "neb_device.cuh"
 
 namespace neb {
@@ -140,73 +142,131 @@ __device__ __forceinline__ int oct_wait_for_link(const int* word, OctreeState* s
   return 0;
 }
 
-// Counts one vertex with key k (Sec. 5.1): the count of the leaf cell on its
-// path goes up by one.  The vertex that brings a cell to the split threshold
-// splits it (Sec. 5.2): it takes the next eight words of the pool, which
-// already hold the count a new cell starts with (the re-arm kernel writes it
-// into every free word), and publishes the negated index of the first in
-// place of the count.  That vertex stays counted in the cell it split.
-// Concurrent form: the increment is a compare-and-swap that fails when the
-// word changed, and a vertex that counted past the threshold before the link
-// appeared is counted again in the child once the link is published.
-// Sequential form (one thread, the deterministic mode): plain loads and
-// stores.  With no eight words left the pool is marked exhausted (alloc >
-// capacity, status bit) and the cell keeps counting; splits stop at level 30.
+// The vertex that brought the cell in `word` (at `level`) to the split
+// threshold gives it eight children (Sec. 5.2): it takes the next eight words
+// of the pool, which already hold the count a new cell starts with (the
+// re-arm kernel writes it into every free word), and publishes the negated
+// index of the first in place of the count; it stays counted in the cell it
+// split.  With no eight words left the pool is marked exhausted (alloc >
+// capacity, status bit) and the cell keeps counting.
 template <bool kSequential>
+__device__ __forceinline__ void oct_split(int* nodes, OctreeState* st, const OctreeParams& P, int word, int level) {
+  const int first = kSequential ? st->alloc : atomicAdd(&st->alloc, 8);
+  if (first + 8 > P.capacity) {
+    if (kSequential) {
+      st->alloc = P.capacity + 1;
+      st->status |= NEB_STATUS_OCTREE_FULL;
+    } else {
+      atomicExch(&st->alloc, P.capacity + 1);
+      atomicOr(&st->status, NEB_STATUS_OCTREE_FULL);
+    }
+    return;
+  }
+  if (kSequential) {
+    st->alloc = first + 8;
+    nodes[word] = -first;
+    if (level + 1 > st->depth) st->depth = level + 1;
+  } else {
+    atomicExch(nodes + word, -first);
+    atomicMax(&st->depth, level + 1);
+  }
+}
+
+// Counts one vertex with key k (Sec. 5.1) on one thread, in insertion order
+// (the deterministic mode): the count of the leaf cell on its path goes up by
+// one; reaching the threshold splits the cell.  Splits stop at level 30.
+__device__ __forceinline__ void oct_count_seq(int* nodes, OctreeState* st, const OctreeParams& P, const OctKey& k) {
+  int word = 0, level = 0;
+  int v = nodes[0];
+  while (v < 0) {
+    ++level;
+    word = -v + oct_octant(k, level);
+    v = nodes[word];
+  }
+  nodes[word] = v + 1;
+  if (v + 1 == P.split_count && level < kOctMaxDepth) oct_split<true>(nodes, st, P, word, level);
+}
+
+// The same, concurrently (one thread per vertex).  Lanes of a warp that reach
+// the same cell together add their vertices with one compare-and-swap by the
+// lowest of them, taking no more than the cell still holds below the split
+// threshold; the lane whose vertex lands on the threshold splits the cell.
+// A vertex that finds a cell at or past the threshold is not counted there
+// (that count would be overwritten by the link): it waits for the link and
+// counts in the child.  When no link comes (the pool is exhausted, or the
+// bounded wait ran out, which sets the status bit) it counts in the cell
+// past the threshold.  Each vertex is counted exactly once; a cell that splits
+// holds exactly the threshold when its link replaces the count.  Plain reads
+// are enough on the way down: a link never changes once published, and a
+// stale count only makes the compare-and-swap fail and return the word's
+// current value.
 __device__ __forceinline__ void oct_count(int* nodes, OctreeState* st, const OctreeParams& P, const OctKey& k,
                                           int spin_limit) {
-  // Plain reads are enough on the way down: a link never changes once
-  // published, and a stale count only makes the compare-and-swap fail and
-  // return the word's current value.
+  const int lane = threadIdx.x & 31;
   int word = 0, level = 0;
+  bool past = false;  // counting past the threshold of this cell is allowed
   int v = nodes[0];
   while (true) {
     if (v < 0) {
       ++level;
       word = -v + oct_octant(k, level);
       v = nodes[word];
+      past = false;
       continue;
     }
-    if (kSequential) {
-      nodes[word] = v + 1;
-    } else {
-      const int seen = atomicCAS(nodes + word, v, v + 1);
-      if (seen != v) {  // changed under us: a newer count, or now a link
-        v = seen;
-        continue;
+    const int limit = (past || level >= kOctMaxDepth) ? INT_MAX : P.split_count;
+    if (v >= limit) {
+      v = oct_wait_for_link(nodes + word, st, P, spin_limit);
+      if (v >= 0) {
+        past = true;
+        v = nodes[word];
+      }
+      continue;
+    }
+    // one compare-and-swap per group of lanes at the same cell
+    const unsigned grp = __match_any_sync(__activemask(), word);
+    const int leader = __ffs(grp) - 1;
+    const int n = __popc(grp), rank = __popc(grp & ((1u << lane) - 1u));
+    int base = 0, got = 0;
+    if (lane == leader) {
+      int cur = v;
+      while (true) {
+        if (cur < 0 || cur >= limit) {  // now a link, or full: nobody counts here
+          base = cur;
+          break;
+        }
+        const int take = min(n, limit - cur);
+        const int seen = atomicCAS(nodes + word, cur, cur + take);
+        if (seen == cur) {
+          base = cur;
+          got = take;
+          break;
+        }
+        cur = seen;
       }
     }
-    const int now = v + 1;
-    if (now < P.split_count || level >= kOctMaxDepth) return;
-    if (now == P.split_count) {
-      const int first = kSequential ? st->alloc : atomicAdd(&st->alloc, 8);
-      if (first + 8 > P.capacity) {
-        if (kSequential) {
-          st->alloc = P.capacity + 1;
-          st->status |= NEB_STATUS_OCTREE_FULL;
-        } else {
-          atomicExch(&st->alloc, P.capacity + 1);
-          atomicOr(&st->status, NEB_STATUS_OCTREE_FULL);
-        }
-        return;
-      }
-      if (kSequential) {
-        st->alloc = first + 8;
-        nodes[word] = -first;
-        if (level + 1 > st->depth) st->depth = level + 1;
-      } else {
-        atomicExch(nodes + word, -first);
-        atomicMax(&st->depth, level + 1);
-      }
+    base = __shfl_sync(grp, base, leader);
+    got = __shfl_sync(grp, got, leader);
+    if (rank < got) {
+      if (limit == P.split_count && base + rank + 1 == limit) oct_split<false>(nodes, st, P, word, level);
       return;
     }
-    // Past the threshold: only a cell that could not split (the pool is
-    // exhausted) is seen so by a lone thread; concurrently, another vertex may
-    // be splitting this cell.
-    if (kSequential) return;
-    v = oct_wait_for_link(nodes + word, st, P, spin_limit);
-    if (v >= 0) return;
+    v = got > 0 ? base + got : base;  // the word as the group left it
   }
+}
+
+__device__ __forceinline__ void oct_insert(int* nodes, OctreeState* st, const OctreeParams& P, const float pos[3],
+                                           int spin_limit) {
+  if (P.stop_filling) return;
+  OctKey k;
+  if (oct_key(P, pos[0], pos[1], pos[2], k)) oct_count(nodes, st, P, k, spin_limit);
+}
+
+__device__ __forceinline__ void oct_insert_seq(int* nodes, OctreeState* st, const OctreeParams& P,
+                                               const float pos[3]) {
+  if (P.stop_filling) return;
+  OctKey k;
+  if (oct_key(P, pos[0], pos[1], pos[2], k)) oct_count_seq(nodes, st, P, k);
 }
 
 // Leaf word of a position once no cell can split any more (the pool was
@@ -223,20 +283,6 @@ __device__ __forceinline__ int oct_frozen_leaf(const int* nodes, const OctreePar
     v = nodes[word];
   }
   return word;
-}
-
-__device__ __forceinline__ void oct_insert(int* nodes, OctreeState* st, const OctreeParams& P, const float pos[3],
-                                           int spin_limit) {
-  if (P.stop_filling) return;
-  OctKey k;
-  if (oct_key(P, pos[0], pos[1], pos[2], k)) oct_count<false>(nodes, st, P, k, spin_limit);
-}
-
-__device__ __forceinline__ void oct_insert_seq(int* nodes, OctreeState* st, const OctreeParams& P,
-                                               const float pos[3]) {
-  if (P.stop_filling) return;
-  OctKey k;
-  if (oct_key(P, pos[0], pos[1], pos[2], k)) oct_count<true>(nodes, st, P, k, 0);
 }
 
 // ---- density -------------------------------------------------------------------
