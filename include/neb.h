@@ -306,7 +306,9 @@ int neb_density_estimators(const float* pos, const float* nrm, int n, const floa
 
 /* Merge candidate search through the device hashed grid (cell size 2r, the
  * structure used by the photon merge): for each query, the number of points
- * with |p - q|^2 <= r^2 evaluated in FP32. */
+ * with |p - q|^2 <= r^2 evaluated in FP32.  Grid cells are held within
+ * +-2^30 per axis; far points share the boundary cell and counts stay exact
+ * (slower when many points lie beyond it). */
 int neb_count_neighbours(const float* pts, int n, const float* queries, int m, float r, int32_t* out);
 
 /* The same neighbour count for callers that cannot allocate device memory:
@@ -316,7 +318,8 @@ int neb_count_neighbours(const float* pts, int n, const float* queries, int m, f
  * has no counterpart; this is a library service.
  *
  * d_pts [n][3], d_queries [m][3] and d_out [m] are DEVICE pointers owned by
- * the caller; cuda_stream is a cudaStream_t (NULL: the default stream).  The
+ * the caller; cuda_stream is a cudaStream_t of the current device (NULL: the
+ * default stream; a stream of another device returns NEB_ERR_ARG).  The
  * call only enqueues work (memset + kernels) on that stream and returns;
  * synchronise before reading d_out.  It allocates nothing: its scratch is a
  * fixed ~9 MiB array inside the library image (held by every GPU that loads
@@ -324,6 +327,9 @@ int neb_count_neighbours(const float* pts, int n, const float* queries, int m, f
  * NEB_NOALLOC_MAX_POINTS (larger n returns NEB_ERR_ARG; m is unlimited).
  * The first call on each device looks up the array's device address with
  * cudaGetSymbolAddress; make that first call before any stream capture.
+ * The library keeps that address for the rest of the process: after a
+ * cudaDeviceReset of the device it is stale, so do not call this entry point
+ * on a device that has been reset.
  * Every call on a device shares the one array: calls whose work overlaps on
  * the GPU (other streams, other host threads) race and corrupt each other's
  * results; serialise them.  Results equal those of neb_count_neighbours. */

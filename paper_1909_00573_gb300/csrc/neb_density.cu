@@ -30,7 +30,7 @@ __global__ void k_naive_rho(const float4* __restrict__ sorted, const int* __rest
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     float3 p = f3(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]);
     float gx = (p.x - gmin.x) * cell_inv, gy = (p.y - gmin.y) * cell_inv, gz = (p.z - gmin.z) * cell_inv;
-    int cx = (int)floorf(gx), cy = (int)floorf(gy), cz = (int)floorf(gz);
+    int cx = grid_cell_index(gx), cy = grid_cell_index(gy), cz = grid_cell_index(gz);
     int ox = (gx - (float)cx >= 0.5f) ? 1 : -1, oy = (gy - (float)cy >= 0.5f) ? 1 : -1,
         oz = (gz - (float)cz >= 0.5f) ? 1 : -1;
     uint32_t bk[8];

@@ -267,6 +267,14 @@ __device__ __forceinline__ float3 oct_decode16(uint32_t v) {
 // et al., "Optimized Spatial Hashing for Collision Detection of Deformable
 // Objects", VMV 2003).  The merge grid, its builder and the stand-alone point
 // grids all use this one function.
+// Cell index of grid coordinate g (position / cell size): floor(g), held
+// within +-2^30 so that far points or a tiny cell cannot overflow the
+// integer; points beyond that all share the boundary cell, and since every
+// candidate is checked by its distance, counts stay exact.
+__device__ __forceinline__ int grid_cell_index(float g) {
+  return (int)fminf(fmaxf(floorf(g), -1073741824.0f), 1073741824.0f);
+}
+
 __device__ __forceinline__ uint32_t grid_hash(int x, int y, int z, uint32_t mask) {
   return (((uint32_t)x * 73856093u) ^ ((uint32_t)y * 19349663u) ^ ((uint32_t)z * 83492791u)) & mask;
 }

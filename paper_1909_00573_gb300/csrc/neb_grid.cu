@@ -97,9 +97,9 @@ cudaError_t scan_exclusive(const int* d_in, int* d_out, size_t n, Scratch& scrat
 
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t point_bucket(float3 p, float3 gmin, float cell_inv, uint32_t mask) {
-  int cx = (int)floorf((p.x - gmin.x) * cell_inv);
-  int cy = (int)floorf((p.y - gmin.y) * cell_inv);
-  int cz = (int)floorf((p.z - gmin.z) * cell_inv);
+  int cx = grid_cell_index((p.x - gmin.x) * cell_inv);
+  int cy = grid_cell_index((p.y - gmin.y) * cell_inv);
+  int cz = grid_cell_index((p.z - gmin.z) * cell_inv);
   return grid_hash(cx, cy, cz, mask);
 }
 
@@ -167,7 +167,7 @@ __global__ void k_pts_query(const float4* __restrict__ sorted, const int* __rest
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
     float3 hp = f3(q[3 * i], q[3 * i + 1], q[3 * i + 2]);
     float gx = (hp.x - gmin.x) * cell_inv, gy = (hp.y - gmin.y) * cell_inv, gz = (hp.z - gmin.z) * cell_inv;
-    int cx = (int)floorf(gx), cy = (int)floorf(gy), cz = (int)floorf(gz);
+    int cx = grid_cell_index(gx), cy = grid_cell_index(gy), cz = grid_cell_index(gz);
     int ox = (gx - (float)cx >= 0.5f) ? 1 : -1, oy = (gy - (float)cy >= 0.5f) ? 1 : -1,
         oz = (gz - (float)cz >= 0.5f) ? 1 : -1;
     uint32_t bk[8];
@@ -286,10 +286,15 @@ extern "C" int neb_count_neighbours_noalloc(const float* d_pts, int n, const flo
     return NEB_ERR_ARG;
   if (n > NEB_NOALLOC_MAX_POINTS) return NEB_ERR_ARG;
   if (m == 0) return NEB_OK;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (st) {  // the scratch address is the current device's: the stream must be on it
+    int dev = 0, sdev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaStreamGetDevice(st, &sdev) != cudaSuccess) return NEB_ERR_CUDA;
+    if (sdev != dev) return NEB_ERR_ARG;
+  }
   unsigned char* base = nullptr;
   int rc = noalloc_scratch(&base);
   if (rc != NEB_OK) return rc;
-  cudaStream_t st = (cudaStream_t)cuda_stream;
   int* counts = reinterpret_cast<int*>(base + kNaCountsOff);
   int* starts = reinterpret_cast<int*>(base + kNaStartsOff);
   int* vb = reinterpret_cast<int*>(base + kNaBucketOff);

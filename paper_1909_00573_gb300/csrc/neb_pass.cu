@@ -680,7 +680,7 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
     if (want_merge) {
       float gx = (m_p.x - ip.gmin.x) * ip.cell_inv, gy = (m_p.y - ip.gmin.y) * ip.cell_inv,
             gz = (m_p.z - ip.gmin.z) * ip.cell_inv;
-      int cx = (int)floorf(gx), cy = (int)floorf(gy), cz = (int)floorf(gz);
+      int cx = grid_cell_index(gx), cy = grid_cell_index(gy), cz = grid_cell_index(gz);
       int ox = (gx - (float)cx >= 0.5f) ? 1 : -1, oy = (gy - (float)cy >= 0.5f) ? 1 : -1,
           oz = (gz - (float)cz >= 0.5f) ? 1 : -1;
       uint32_t bk[8];

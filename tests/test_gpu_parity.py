@@ -62,7 +62,12 @@ def test_plane_box_area_equals_oracle(neb, oracle):
     g = neb.plane_box_area(np.concatenate([lo, hi], 1), pos, nrm)
     o = np.array([oracle.intersection_area(lo[i], hi[i], pos[i], nrm[i]) for i in range(n)])
     face = np.prod(hi.astype(np.float64) - lo, axis=1) ** (2 / 3)
-    assert np.all(np.abs(g - o) <= 1e-9 * np.abs(o) + 1e-12 * face)
+    # Where the plane misses the box the area is 0 and both sides return the
+    # rounding noise of the corner sum, about 1e-16 of the face area divided by the
+    # product of the normal components the sum uses.
+    m = np.abs(nrm.astype(np.float64))
+    cancel = face / np.prod(np.where(m >= 1e-4, m, 1.0), axis=1)
+    assert np.all(np.abs(g - o) <= 1e-9 * np.abs(o) + 1e-14 * cancel)
 
 
 # --------------------------------------------------------------------------
@@ -390,6 +395,20 @@ def test_neighbour_counts_equal_brute_force(neb, oracle):
         o = oracle.count_neighbours(pts, q, r, brute=True)
         assert np.array_equal(g, o)
     assert neb.count_neighbours(np.zeros((0, 3), np.float32), q[:5], 0.1).tolist() == [0] * 5
+
+
+def test_neighbour_counts_far_from_the_origin_with_a_tiny_radius(neb, oracle):
+    """Coordinates near 5e6 with r = 1e-3 put the grid cells beyond 2^30 per
+    axis: they are held at the boundary cell, and the counts (here the
+    multiplicity of each lattice point, all other points being 0.5 or more
+    away) still equal brute force."""
+    rng = np.random.default_rng(52)
+    lattice = (5.0e6 + 0.5 * rng.integers(0, 40, (300, 3))).astype(np.float32)
+    pts = np.repeat(lattice, rng.integers(1, 5, len(lattice)), axis=0)
+    q = np.concatenate([lattice, -lattice[:50]]).astype(np.float32)
+    g = neb.count_neighbours(pts, q, 1e-3)
+    o = oracle.count_neighbours(pts, q, 1e-3, brute=True)
+    assert np.array_equal(g, o) and g[:300].min() >= 1 and g[300:].max() == 0
 
 
 # --------------------------------------------------------------------------

@@ -37,3 +37,33 @@ def test_noalloc_matches_allocating_entry_point_twice():
     with pytest.raises(neb.NebError):
         neb.count_neighbours_noalloc(d_pts.data_ptr(), neb.NOALLOC_MAX_POINTS + 1, d_q.data_ptr(), 10, 0.01,
                                      d_out.data_ptr(), stream.cuda_stream)
+
+
+def test_noalloc_far_coordinates_and_stream_of_another_device():
+    """Coordinates near 5e6 with r = 1e-3 (grid cells beyond 2^30 per axis,
+    held at the boundary cell) give the allocating entry point's counts; a
+    stream that does not belong to the current device is refused."""
+    torch = pytest.importorskip("torch")
+    from paper_1909_00573_gb300 import build
+    build.build()
+    from paper_1909_00573_gb300 import neb
+    rng = np.random.default_rng(72)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    lattice = (5.0e6 + 0.5 * rng.integers(0, 40, (300, 3))).astype(np.float32)
+    pts = np.repeat(lattice, rng.integers(1, 5, len(lattice)), axis=0)
+    q = lattice.copy()
+    ref = neb.count_neighbours(pts, q, 1e-3)
+    d_pts = torch.from_numpy(pts).to(dev)
+    d_q = torch.from_numpy(q).to(dev)
+    for _ in range(2):
+        d_out = torch.full((len(q),), -7, dtype=torch.int32, device=dev)
+        neb.count_neighbours_noalloc(d_pts.data_ptr(), len(pts), d_q.data_ptr(), len(q), 1e-3, d_out.data_ptr(),
+                                     stream.cuda_stream)
+        torch.cuda.synchronize()
+        assert np.array_equal(d_out.cpu().numpy(), ref)
+    if torch.cuda.device_count() > 1:
+        other = torch.cuda.Stream(device=torch.device("cuda", 1))
+        with pytest.raises(neb.NebError):
+            neb.count_neighbours_noalloc(d_pts.data_ptr(), len(pts), d_q.data_ptr(), len(q), 1e-3,
+                                         d_out.data_ptr(), other.cuda_stream)
