@@ -54,7 +54,8 @@ def parse():
                     help="batched-jobs measurement: N heterogeneous jobs, batched vs sequential per-job launches")
     ap.add_argument("--mem-budget-gb", type=float, default=150.0, help="admission cap of the batched jobs")
     ap.add_argument("--serve", type=int, default=0,
-                    help="served progressive rendering: R requests with Poisson arrivals, vs sequential per-job")
+                    help="served progressive rendering: R requests with Poisson arrivals, each to a relative-RMSE "
+                         "target, vs sequential per-job launches")
     ap.add_argument("--rate", type=float, default=200.0, help="mean request arrival rate (per second) for --serve")
     ap.add_argument("--ablation", action="store_true",
                     help="density estimators of Sec. 5 (octree, naive, k nearest) on one iteration's NEE vertices")
@@ -373,23 +374,30 @@ def run_batch(args):
 
 def run_serve(args):
     """Served progressive rendering: args.serve requests drawn from the
-    batched-jobs mix, Poisson arrivals at args.rate per second, targets of 16
-    to 256 iterations (log-uniform), admission capped at --mem-budget-gb.
-    The same requests are served by continuous batching and by sequential
-    per-job launches in arrival order."""
+    batched-jobs mix, Poisson arrivals at args.rate per second, each asking
+    for a relative RMSE that a pilot run (16 iterations of the same job at
+    128 x 128, outside the timed region) predicts it reaches after 16 to 256
+    iterations (log-uniform); a job retires when its two-half error estimate
+    (checked every 4 iterations) reaches the target, or at 256 iterations.
+    Admission capped at --mem-budget-gb.  The same requests are served by
+    continuous batching and by sequential per-job launches in arrival order."""
     os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     rank, world, local = dist_env()
+    import numpy as np
     import torch
     torch.cuda.set_device(local)
     from paper_1909_00573_gb300 import build as B
     B.build()
     from paper_1909_00573_gb300 import scenes, serve
     budget = args.mem_budget_gb * 1e9
+    t_p = time.perf_counter()
+    reqs = serve.poisson_requests(scenes.batch_jobs(args.serve, seed=rank), args.rate, seed=rank,
+                                  pilot=serve.pilot_rmse)
+    pilot_s = time.perf_counter() - t_p
     out = {}
     clocks = ClockSampler(local)
     clocks.start()
     for mode in ("served", "sequential"):
-        reqs = serve.poisson_requests(scenes.batch_jobs(args.serve, seed=rank), args.rate, seed=rank)
         t0 = time.perf_counter()
         if mode == "served":
             res, rounds, rejected = serve.run_served(reqs, budget, max_jobs=64)
@@ -401,14 +409,20 @@ def run_serve(args):
         if mode == "served":
             out[mode]["rounds"] = len(rounds)
             out[mode]["max_resident"] = max(n for _, _, n in rounds)
+            out[mode]["mean_resident"] = float(np.mean([n for _, _, n in rounds]))
     clk = clocks.stop()
     sv, sq = out["served"], out["sequential"]
+    targets = [r.target_rmse for r in reqs]
     line = {"metric": METRIC, "value": sv["mpaths_per_s"], "unit": METRIC, "n_gpus": 1, "steps": sv["rounds"],
             "warmup": 0, "ms_per_step": sv["iteration_latency_ms"]["p50"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"served progressive rendering: {args.serve} requests from the batched-jobs mix, "
-                                   f"Poisson arrivals at {args.rate:g}/s, 16..256 iterations each, admission cap "
-                                   f"{args.mem_budget_gb:g} GB, at most 64 resident jobs"},
+                                   f"Poisson arrivals at {args.rate:g}/s, each to a relative-RMSE target "
+                                   f"(two-half estimate; 16..256 iterations by its pilot), admission cap "
+                                   f"{args.mem_budget_gb:g} GB, at most 64 resident jobs",
+                       "target_rmse": {"min": float(min(targets)), "median": float(np.median(targets)),
+                                       "max": float(max(targets))},
+                       "pilot_s": pilot_s},
             "served": sv, "sequential_per_job": sq,
             "throughput_ratio": sv["mpaths_per_s"] / sq["mpaths_per_s"],
             "time_to_target_mean_ratio": sq["time_to_target_s"]["mean"] / sv["time_to_target_s"]["mean"],

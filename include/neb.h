@@ -194,8 +194,24 @@ int neb_autotune(neb_ctx* ctx, int iterations_per_candidate, neb_tuning* chosen)
  * memory (written on the context stream), zero for host memory (synchronises). */
 int neb_resolve(neb_ctx* ctx, float* rgb_out, int out_is_device);
 
+/* Waits until everything enqueued on the context so far (iterations,
+ * resolves, copies) has finished; other contexts' work is not waited for.
+ * NEB_ERR_CUDA on a device error. */
+int neb_synchronize(neb_ctx* ctx);
+
 /* Raw FP64 sums [H][W][3] (host memory; synchronises). */
 int neb_read_accum(neb_ctx* ctx, double* out);
+
+/* Relative RMSE of the progressive image, estimated from its own samples:
+ * contributions of even and odd iterations are summed apart, and with m_e,
+ * m_o their per-pixel means (luminance, the sum of the channels) over the
+ * n_e, n_o iterations of each parity, the variance of the mean of all n
+ * iterations is Var(m_e - m_o) n_e n_o / n^2.  *rel_rmse = sqrt(sum over
+ * pixels of that variance / sum of the squared mean).  It measures the
+ * noise, not the bias of the consistent estimator (Sec. 3.2, Sec. 5).
+ * Needs at least two iterations (else NEB_ERR_ARG); synchronises the context
+ * stream. */
+int neb_error_estimate(neb_ctx* ctx, double* rel_rmse);
 
 /* Last iteration's contributions split by strategy [4][H][W][3] (0 random hit,
  * 1 NEE, 2 NEB photon merge, 3 light-photon merge); requires cfg.keep_split.

@@ -115,7 +115,7 @@ extern "C" int neb_job_device_bytes(const neb_config* cfg, int n_tri, int n_sph,
             (cfg->octree_mode == 1 ? nee_rows * sizeof(int) : 0));
   b += 2 * k.cap_ph * sizeof(PhotonRay) + k.cap_cam * sizeof(int2) + k.cap_ph * sizeof(int2);
   b += k.cap_nee * (sizeof(MergeRec) + sizeof(int)) + 2 * ((size_t)k.table + 1) * sizeof(int);
-  b += scan_scratch_ints((size_t)k.table + 1) * sizeof(int) + k.P * 3 * (sizeof(double) + sizeof(float));
+  b += scan_scratch_ints((size_t)k.table + 1) * sizeof(int) + k.P * 3 * (2 * sizeof(double) + sizeof(float));
   b += cfg->keep_split ? k.P * 12 * sizeof(double) : 0;
   b += 2 * k.cap_nee * (sizeof(ShadowRay) + sizeof(int)) + group_counter_ints() * sizeof(int);
   const size_t nt = (size_t)n_tri, ns = (size_t)n_sph, nl = (size_t)n_lights, np = nt + ns;
@@ -177,7 +177,7 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
        dalloc(&c->mrec, c->cap_nee) == cudaSuccess && dalloc(&c->vert_bucket, c->cap_nee) == cudaSuccess &&
        dalloc(&c->bucket_count, (size_t)t + 1) == cudaSuccess &&
        dalloc(&c->bucket_start, (size_t)t + 1) == cudaSuccess &&
-       dalloc(&c->scan_scratch.data, c->scan_scratch.n) == cudaSuccess && dalloc(&c->accum, P * 3) == cudaSuccess &&
+       dalloc(&c->scan_scratch.data, c->scan_scratch.n) == cudaSuccess && dalloc(&c->accum, P * 6) == cudaSuccess &&
        dalloc(&c->frame, P * 3) == cudaSuccess &&
        (!cfg->keep_split || dalloc(&c->split, P * 12) == cudaSuccess);
   ok = ok && dalloc(&c->shadow_rays, c->cap_nee) == cudaSuccess && dalloc(&c->shadow_start, c->cap_nee) == cudaSuccess &&
@@ -198,7 +198,7 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
     return NEB_ERR_OOM;
   }
   cudaMemsetAsync(c->bucket_count, 0, sizeof(int) * ((size_t)t + 1), c->stream);
-  cudaMemsetAsync(c->accum, 0, sizeof(double) * P * 3, c->stream);
+  cudaMemsetAsync(c->accum, 0, sizeof(double) * P * 6, c->stream);
   cudaMemsetAsync(c->counters, 0, 2 * sizeof(DevCounters), c->stream);
   cudaMemsetAsync(c->group_counters, 0, sizeof(int) * group_counter_ints(), c->stream);
   if (c->split) cudaMemsetAsync(c->split, 0, sizeof(double) * P * 12, c->stream);
@@ -493,7 +493,7 @@ extern "C" int neb_scene_upload(neb_ctx* c, const float* tri, const uint32_t* tr
   OctreeState s0{1, 0, 0, 0};
   cudaMemsetAsync(c->oct_nodes, 0, sizeof(int) * (size_t)c->oct_cap, st);
   cudaMemcpyAsync(c->oct_state, &s0, sizeof(s0), cudaMemcpyHostToDevice, st);
-  cudaMemsetAsync(c->accum, 0, sizeof(double) * 3 * (size_t)c->P, st);
+  cudaMemsetAsync(c->accum, 0, sizeof(double) * 6 * (size_t)c->P, st);
   cudaMemsetAsync(c->counters, 0, 2 * sizeof(DevCounters), st);
   c->iteration = 0;
   c->launches = 0;
@@ -694,10 +694,39 @@ extern "C" int neb_resolve(neb_ctx* c, float* rgb_out, int out_is_device) {
   return e == cudaSuccess ? NEB_OK : fail(c, NEB_ERR_CUDA, "neb_resolve", e);
 }
 
+extern "C" int neb_synchronize(neb_ctx* c) {
+  if (!c) return NEB_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? NEB_OK : fail(c, NEB_ERR_CUDA, "neb_synchronize", e);
+}
+
+extern "C" int neb_error_estimate(neb_ctx* c, double* rel_rmse) {
+  if (!c || !rel_rmse) return NEB_ERR_ARG;
+  const int n = c->iteration, n_odd = (n + 1) / 2, n_even = n / 2;
+  if (n_even < 1) return fail(c, NEB_ERR_ARG, "neb_error_estimate: needs at least two iterations");
+  double* d = nullptr;
+  cudaError_t e = cudaMallocAsync(&d, 2 * sizeof(double), c->stream);
+  if (e != cudaSuccess) return fail(c, NEB_ERR_OOM, "neb_error_estimate", e);
+  launch_error_sums(c->accum, c->P, n_even, n_odd, d, c->stream);
+  double h[2] = {0.0, 0.0};
+  cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+  cudaFreeAsync(d, c->stream);
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(c, NEB_ERR_CUDA, "neb_error_estimate", e);
+  const double var_of_mean = h[0] * (double)n_even * (double)n_odd / ((double)n * (double)n);
+  *rel_rmse = h[1] > 0.0 ? sqrt(var_of_mean / h[1]) : 0.0;
+  return NEB_OK;
+}
+
 extern "C" int neb_read_accum(neb_ctx* c, double* out) {
   if (!c || !out) return NEB_ERR_ARG;
-  cudaMemcpyAsync(out, c->accum, sizeof(double) * 3 * (size_t)c->P, cudaMemcpyDeviceToHost, c->stream);
-  cudaError_t e = cudaStreamSynchronize(c->stream);
+  double* d = nullptr;
+  cudaError_t e = cudaMallocAsync(&d, sizeof(double) * 3 * (size_t)c->P, c->stream);
+  if (e != cudaSuccess) return fail(c, NEB_ERR_OOM, "neb_read_accum", e);
+  launch_sum_halves(c->accum, c->P, d, c->stream);
+  cudaMemcpyAsync(out, d, sizeof(double) * 3 * (size_t)c->P, cudaMemcpyDeviceToHost, c->stream);
+  cudaFreeAsync(d, c->stream);
+  e = cudaStreamSynchronize(c->stream);
   return e == cudaSuccess ? NEB_OK : fail(c, NEB_ERR_CUDA, "neb_read_accum", e);
 }
 

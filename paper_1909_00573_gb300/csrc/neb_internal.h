@@ -186,7 +186,7 @@ struct neb_ctx {
   int cap_cam = 0, cap_nee = 0, cap_rh = 0, cap_ph = 0;
   uint32_t table_size = 0;
   neb::Scratch scan_scratch;
-  double* accum = nullptr;
+  double* accum = nullptr;  // FP64 sums: [2][P][3], even iterations then odd iterations
   float* frame = nullptr;             // resolved image staged for neb_iterate_read
   cudaEvent_t ev_frame = nullptr;     // after the last frame copy of neb_iterate_read
   double* split = nullptr;
@@ -287,6 +287,8 @@ cudaError_t launch_group_camera(neb_ctx* c, const CamRay* q, const int* count_pt
 // overlap: passes 2-3 go to stream_b (ordered by the slot events), else all on c->stream
 cudaError_t run_iteration(neb_ctx* c, int iteration, bool overlap);
 cudaError_t launch_resolve(const double* accum, int P, int iterations, float* out, cudaStream_t st);
+cudaError_t launch_sum_halves(const double* accum, int P, double* out, cudaStream_t st);
+cudaError_t launch_error_sums(const double* accum, int P, int n_even, int n_odd, double* out, cudaStream_t st);
 cudaError_t launch_read_rho(neb_ctx* c, float* d_out);
 
 }  // namespace neb

@@ -769,8 +769,54 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
 __global__ void k_reset_photon_slot(DevCounters* cnt, int slot) { cnt->ph_count[slot] = 0; }
 __global__ void k_reset_cam_slot(DevCounters* cnt, int slot) { cnt->cam_count[slot] = 0; }
 
+// image = (sum of the even-iteration half + sum of the odd-iteration half) / iterations
 __global__ void k_resolve(const double* __restrict__ accum, int n, double inv, float* out) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = (float)(accum[i] * inv);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = (float)((accum[i] + accum[n + i]) * inv);
+}
+
+// the FP64 sums over all iterations: the two halves added
+__global__ void k_sum_halves(const double* __restrict__ accum, int n, double* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = accum[i] + accum[n + i];
+}
+
+// Two-half error estimate of the progressive image: with m_e and m_o the
+// per-pixel means of the n_e even and n_o odd iterations (luminance, the sum
+// of the three channels), the variance of the mean of all n iterations is
+// Var(m_e - m_o) n_e n_o / n^2.  The block sums of (m_e - m_o)^2 and of the
+// squared mean are added into out[0] and out[1].
+__global__ void k_error_sums(const double* __restrict__ accum, int P, int n_even, int n_odd, double* out) {
+  __shared__ double s_num[8], s_den[8];
+  const double ie = 1.0 / n_even, io = 1.0 / n_odd, in = 1.0 / (n_even + n_odd);
+  double num = 0.0, den = 0.0;
+  const size_t half = 3 * (size_t)P;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+    const double* e = accum + 3 * (size_t)i;
+    const double* o = e + half;
+    const double le = e[0] + e[1] + e[2], lo = o[0] + o[1] + o[2];
+    const double d = le * ie - lo * io, m = (le + lo) * in;
+    num += d * d;
+    den += m * m;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    num += __shfl_down_sync(0xffffffffu, num, off);
+    den += __shfl_down_sync(0xffffffffu, den, off);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    s_num[w] = num;
+    s_den[w] = den;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += s_num[k];
+      b += s_den[k];
+    }
+    atomicAdd(out, a);
+    atomicAdd(out + 1, b);
+  }
 }
 
 __global__ void k_fill(float* out, size_t n, float v) {
@@ -903,6 +949,9 @@ static long long enqueue_pass23(neb_ctx* c, int iteration, cudaStream_t st2, Sta
   IterSlot& sl = c->slots[iteration & 1];
   DevCounters* cnt = sl.cnt;
   double* split = c->cfg.keep_split ? c->split : nullptr;
+  // iterations of each parity add to their own half of the FP64 sums (the
+  // two halves give the error estimate; the image is their sum)
+  double* accum = c->accum + (size_t)(iteration & 1) * 3 * (size_t)c->P;
   long long launches = 0;
   octree_set_iteration_params(c->oct, c->cfg.split_factor, iteration);
   tm.begin(STAGE_INSERT);
@@ -915,7 +964,7 @@ static long long enqueue_pass23(neb_ctx* c, int iteration, cudaStream_t st2, Sta
   launch_oct_density_nee(c, sl, st2);
   tm.end();
   tm.begin(STAGE_NEE);
-  k_nee<<<capped_blocks(c->cap_nee, kThreads, B), kThreads, 0, st2>>>(s, ip, sl.nv, cnt, c->accum, split, c->phq[0],
+  k_nee<<<capped_blocks(c->cap_nee, kThreads, B), kThreads, 0, st2>>>(s, ip, sl.nv, cnt, accum, split, c->phq[0],
                                                                         c->cfg.photon_records);
   if (ip.n_lp > 0 && c->D >= 2) {
     k_lp_emit<<<capped_blocks(ip.n_lp, kThreads, B), kThreads, 0, st2>>>(s, ip, cnt, c->phq[0], c->cfg.photon_records);
@@ -933,7 +982,7 @@ static long long enqueue_pass23(neb_ctx* c, int iteration, cudaStream_t st2, Sta
     tm.end();
   }
   tm.begin(STAGE_EMISSION);
-  k_emission<<<capped_blocks(c->cap_rh, kThreads, B), kThreads, 0, st2>>>(s, ip, sl.nv, sl.rh, cnt, c->accum, split,
+  k_emission<<<capped_blocks(c->cap_rh, kThreads, B), kThreads, 0, st2>>>(s, ip, sl.nv, sl.rh, cnt, accum, split,
                                                                            c->oct_nodes, c->oct_state, c->oct,
                                                                            c->cfg.density_mode == 0);
   launches += 1;
@@ -948,7 +997,7 @@ static long long enqueue_pass23(neb_ctx* c, int iteration, cudaStream_t st2, Sta
       tm.end();
       tm.begin(STAGE_PHOTON);
       k_photon<<<capped_blocks(c->cap_ph, kThreads, B), kThreads, 0, st2>>>(s, ip, j, c->phq[in], in, c->phq[out], out, c->cfg.photon_records, sl.nv, c->mrec, c->bucket_start, cnt,
-                                        c->accum, split, c->hits_ph, c->oct_nodes, c->oct_state, c->oct,
+                                        accum, split, c->hits_ph, c->oct_nodes, c->oct_state, c->oct,
                                         c->cfg.density_mode == 0);
       launches += 3;
       tm.end();
@@ -1024,6 +1073,18 @@ cudaError_t run_iteration(neb_ctx* c, int iteration, bool overlap) {
   half(c->graph_pass23[slot], st2, [&](cudaStream_t cs) { return enqueue_pass23(c, iteration, cs, tm); });
   cudaEventRecord(c->ev_pass23[slot], st2);
   c->launches += launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_halves(const double* accum, int P, double* out, cudaStream_t st) {
+  const int n = 3 * P;
+  k_sum_halves<<<(n + 255) / 256, 256, 0, st>>>(accum, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_error_sums(const double* accum, int P, int n_even, int n_odd, double* out, cudaStream_t st) {
+  cudaMemsetAsync(out, 0, 2 * sizeof(double), st);
+  k_error_sums<<<capped_blocks(P, 256, 152 * 4), 256, 0, st>>>(accum, P, n_even, n_odd, out);
   return cudaGetLastError();
 }
 

@@ -28,7 +28,7 @@ EXPORTS = ["neb_create", "neb_destroy", "neb_last_error", "neb_scene_upload", "n
            "neb_octree_density", "neb_octree_read", "neb_octree_load", "neb_count_neighbours",
            "neb_count_neighbours_noalloc", "neb_iterate_batch", "neb_job_device_bytes", "neb_get_tuning",
            "neb_set_tuning", "neb_autotune", "neb_density_estimators", "neb_read_nee_vertices",
-           "neb_iterate_read", "neb_bvh_cost"]
+           "neb_iterate_read", "neb_bvh_cost", "neb_error_estimate", "neb_synchronize"]
 NOALLOC_MAX_POINTS = 1 << 18
 
 
@@ -96,6 +96,8 @@ def lib():
             "neb_bvh_cost": ([vp, vp], C.c_int),
             "neb_resolve": ([vp, vp, C.c_int], C.c_int),
             "neb_read_accum": ([vp, vp], C.c_int),
+            "neb_error_estimate": ([vp, vp], C.c_int),
+            "neb_synchronize": ([vp], C.c_int),
             "neb_read_split": ([vp, vp], C.c_int),
             "neb_read_nee_rho": ([vp, vp], C.c_int),
             "neb_get_stats": ([vp, C.POINTER(Stats)], C.c_int),
@@ -235,6 +237,16 @@ class Context:
         out = np.zeros((self.cfg.height, self.cfg.width, 3), np.float64)
         self._c(lib().neb_read_accum(self.h, _p(out)))
         return out
+
+    def synchronize(self):
+        """Wait for this context's enqueued work only."""
+        self._c(lib().neb_synchronize(self.h))
+
+    def error_estimate(self):
+        """Relative RMSE of the current image from its even and odd iterations (needs two or more)."""
+        out = np.zeros(1, np.float64)
+        self._c(lib().neb_error_estimate(self.h, _p(out)))
+        return float(out[0])
 
     def read_split(self):
         out = np.zeros((4, self.cfg.height, self.cfg.width, 3), np.float64)
