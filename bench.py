@@ -185,7 +185,22 @@ def load_peaks():
 # kernel's sources hash to the value recorded with the capture, else null.
 TRAFFIC_SOURCES = ("paper_1909_00573_gb300/csrc/neb_trace.cu", "paper_1909_00573_gb300/csrc/neb_device.cuh",
                    "paper_1909_00573_gb300/csrc/neb_types.h")
-NCU_COUNTERS = {}  # (workload, stage): {"bytes_per_launch", "lane_efficiency", "issue_active", "sources_sha256", "profile"}
+NCU_COUNTERS = {  # (workload, stage): counters of the stage's kernel, captured from these sources
+    ("many_lights", "trace_camera"): {
+        "bound": "issue",              # instruction issue on dependent chains and divergence, not DRAM
+        "bytes_per_launch": 161979000,  # mean DRAM read + write of the 10 camera launches of an iteration
+        "lane_efficiency": 12.96 / 32,  # smsp__thread_inst_executed_per_inst_executed, 960 x 540 capture
+        "issue_active": 0.700,          # smsp__issue_active, 960 x 540 capture
+        "sources_sha256": "f9925dd2b99f08e16dbe9f24a5a78c9fba6e333602523df34a41a43af2672582",
+        "profile": "profiles/k_trace_closest_many_lights.md"},
+    ("large_city", "trace_camera"): {
+        "bound": "issue",
+        "bytes_per_launch": 73500000,   # mean DRAM read + write of the 10 camera launches of an iteration
+        "lane_efficiency": None,        # no full capture of the current sources on this scene
+        "issue_active": None,
+        "sources_sha256": "f9925dd2b99f08e16dbe9f24a5a78c9fba6e333602523df34a41a43af2672582",
+        "profile": "profiles/k_trace_closest_large_city.md"},
+}
 
 
 def sources_sha256():
@@ -591,7 +606,9 @@ def main():
                 "dram_frac": (None if traffic is None else traffic / (avg_ms / 1000.0) / 1e9 / peak),
                 "lane_efficiency": cnt["lane_efficiency"] if cnt else None,
                 "issue_active": cnt["issue_active"] if cnt else None,
-                "headroom": (None if not cnt else cnt["lane_efficiency"] * cnt["issue_active"]),
+                "headroom": (cnt["lane_efficiency"] * cnt["issue_active"]
+                             if cnt and cnt["lane_efficiency"] is not None and cnt["issue_active"] is not None
+                             else None),
                 "counters_source": cnt["profile"] if cnt else None}
     total_stage_ms = sum(v[0] for v in stages.values())
     ctx.close()
