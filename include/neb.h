@@ -58,11 +58,11 @@ typedef struct {
   int width, height;     /* image size; one camera path per pixel per iteration */
   int max_depth;         /* D: maximum path length in segments, 1 <= D <= 64 */
   float merge_radius;    /* r of the uniform kernel 1/(pi r^2) (Sec. 3.2) */
-  int octree_capacity;   /* nodes; rounded up to 8n+1 (Appendix B initialize) */
+  int octree_capacity;   /* words of the density octree's pool; rounded up to 8m + 1 (the root and groups of eight children, Sec. 5.5) */
   int split_factor;      /* split factor of the density octree, >= 2: a cell splits at split_factor * iteration vertices (paper: 4, Sec. 5.5) */
   uint64_t seed;         /* Philox4x32-10 key */
   int octree_mode;       /* 0 concurrent lock-free inserts, 1 sequential in (pixel, k) order */
-  int density_mode;      /* 0 robust median of five (get_density_robust), 1 single query */
+  int density_mode;      /* 0 robust: median of five queries (the centre and four displaced along the tangents), 1 single query */
   uint32_t strategy_mask;/* bit 0 random hit (e), bit 1 NEE (E), bit 2 NEB photon merge (P),
                             bit 3 conventional light-photon merge (LP, with lp_photons > 0) */
   int keep_split;        /* nonzero: keep the last iteration's contributions split by strategy */
@@ -105,8 +105,9 @@ const char* neb_last_error(const neb_ctx* ctx);
 /* Copies the scene to the device (SoA triangles as float4 v0, v1, v2; spheres;
  * materials), builds the light list (emissive triangles in index order, then
  * spheres) with power-proportional selection through an alias table (Vose
- * 1991), and derives the octree box from the scene bounds (Appendix B
- * initialize: enlarged by 1.002).  Resets the accumulation. */
+ * 1991), and derives the octree box from the scene bounds (grown by 0.2 %
+ * about their centre, as the paper's implementation does).  Resets the
+ * accumulation. */
 int neb_scene_upload(neb_ctx* ctx, const float* tri, const uint32_t* tri_mat, int nt,
                      const float* sph, const uint32_t* sph_mat, int ns,
                      const float* mats, int nm, const float* cam);
@@ -308,8 +309,8 @@ int neb_octree_load(neb_octree* o, const int32_t* nodes, int n_nodes, int alloc,
  * geometric normals [n][3] (host) taken as the NEE vertices of one
  * iteration; every estimate is made at each of the points and written to
  * rho[3][n]: (0) the density octree as the pass uses it (concurrent insert,
- * get_density_robust; scene box, capacity and split factor as in
- * neb_octree_create); (1) the naive estimator: points within `radius` of
+ * the robust median-of-five query; scene box, capacity and split factor as
+ * in neb_octree_create); (1) the naive estimator: points within `radius` of
  * the point, itself included, / (pi radius^2), through a hashed grid;
  * (2) the k-nearest-neighbour estimator (k - 1) / (pi d_k^2), d_k the
  * distance to the k-th nearest other point (2 <= k <= 16; 0 with fewer than k

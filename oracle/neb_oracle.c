@@ -9,8 +9,8 @@
  *   pass 1  trace view paths; every vertex at which NEE is attempted is an
  *           NEE vertex, stored and counted in the density octree (Sec. 3.1,
  *           Sec. 5.1); random hits of emitters are stored (Sec. 3.1).
- *   pass 2  (a) density rho at every NEE vertex (Eq. octdensity, Appendix B
- *           get_density_robust); (b) NEE contribution L_E (Sec. 3.2);
+ *   pass 2  (a) density rho at every NEE vertex (Eq. octdensity, the robust
+ *           median of five queries); (b) NEE contribution L_E (Sec. 3.2);
  *           (c) photon Phi = dE / rho (Eq. flux) walked from the NEE vertex,
  *           merged at view vertices found by a range search around each
  *           photon hit (Sec. 3.2, uniform kernel 1/(pi r^2)).

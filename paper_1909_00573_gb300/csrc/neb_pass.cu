@@ -938,8 +938,8 @@ static long long enqueue_pass1(neb_ctx* c, int iteration, cudaStream_t st, Stage
   return launches;
 }
 
-// Passes 2-3 of `iteration` on stream st: octree set_iteration (Appendix B:
-// host-side scalars, device re-arm), inserts of the iteration's NEE vertices,
+// Passes 2-3 of `iteration` on stream st: the octree's iteration start (Sec.
+// 5.4: host-side scalars, device re-arm of the free words), inserts of the iteration's NEE vertices,
 // densities, NEE contributions and photon emission; then the deferred random
 // hits, photon walks and merges.
 static long long enqueue_pass23(neb_ctx* c, int iteration, cudaStream_t st2, StageTimer& tm) {

@@ -30,7 +30,7 @@ def test_philox_known_answers(oracle):
 
 
 # --------------------------------------------------------------------------
-# plane/box intersection area (Eq. area, Appendix A and the listing)
+# plane/box intersection area (Eq. area, Sec. 5.3 and Appendix A)
 # --------------------------------------------------------------------------
 def exact_area(bmin, bmax, p, n):
     """Area of {x in box : n.x = n.p} by clipping: plane/edge crossings,
@@ -135,8 +135,8 @@ def test_area_is_unchanged_by_mirroring_the_axes(oracle):
         assert a1 == pytest.approx(a0, rel=1e-9, abs=1e-12)
 
 
-def test_area_near_listing_thresholds_is_bounded(oracle):
-    """The listing switches to the 1D / 2D formulas when a component is within
+def test_area_near_the_implementation_thresholds_is_bounded(oracle):
+    """The paper's implementation switches to the 1D / 2D formulas when a component is within
     1e-3 of 1 or below 1e-4; the error there stays small (documented reading)."""
     rng = np.random.default_rng(2)
     for _ in range(500):

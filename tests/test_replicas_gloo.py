@@ -85,7 +85,7 @@ def test_secondary_rates_and_traffic_lookup(monkeypatch):
              "profile": "profiles/x.md", "sources_sha256": bench.sources_sha256()}
     monkeypatch.setitem(bench.NCU_COUNTERS, key, entry)
     assert bench.measured_counters("many_lights", "trace_camera") == entry
-    assert bench.measured_counters("large_city", "trace_camera") is None
+    assert bench.measured_counters("tiny_room", "trace_camera") is None
     assert bench.measured_counters("many_lights", "shadow") is None
     monkeypatch.setitem(bench.NCU_COUNTERS, key, dict(entry, sources_sha256="0" * 64))
     assert bench.measured_counters("many_lights", "trace_camera") is None
