@@ -61,6 +61,8 @@ def parse():
                     help="density estimators of Sec. 5 (octree, naive, k nearest) on one iteration's NEE vertices")
     ap.add_argument("--lp-photons", type=int, default=0,
                     help="NEB+LP (Sec. 6.1): conventional light photons per iteration in addition to NEB photons")
+    ap.add_argument("--merge-mode", type=int, default=0, choices=[0, 1, 2],
+                    help="photon merge: 0 dense hits per cell, sparse per hit (default); 1 per hit; 2 per cell")
     ap.add_argument("--autotune", type=int, default=0,
                     help="run the autotuner (this many iterations per candidate) before the warm-up")
     ap.add_argument("--live-octree-cap", type=int, default=1 << 27,
@@ -325,6 +327,8 @@ def run_batch(args):
     B.build()
     from paper_1909_00573_gb300 import neb, scenes
     jobs = scenes.batch_jobs(args.batch, seed=rank, iterations=args.steps)
+    for _, rc in jobs:
+        rc.merge_mode = args.merge_mode
     budget = args.mem_budget_gb * 1e9
     admitted, resident, rejected = [], 0, 0
     for s, rc in jobs:
@@ -406,8 +410,10 @@ def run_serve(args):
     from paper_1909_00573_gb300 import scenes, serve
     budget = args.mem_budget_gb * 1e9
     t_p = time.perf_counter()
-    reqs = serve.poisson_requests(scenes.batch_jobs(args.serve, seed=rank), args.rate, seed=rank,
-                                  pilot=serve.pilot_rmse)
+    jobs = scenes.batch_jobs(args.serve, seed=rank)
+    for _, rc in jobs:
+        rc.merge_mode = args.merge_mode
+    reqs = serve.poisson_requests(jobs, args.rate, seed=rank, pilot=serve.pilot_rmse)
     pilot_s = time.perf_counter() - t_p
     out = {}
     clocks = ClockSampler(local)
@@ -534,6 +540,7 @@ def main():
         rc.strategy_mask |= 8
         rc.lp_photons = args.lp_photons
     rc.seed = replica_seed(rank)        # replicas render independent sample streams
+    rc.merge_mode = args.merge_mode
     P = rc.width * rc.height
     # a dedicated (non-default) stream: the library's kernels and the timing
     # events must be ordered on the same stream
@@ -623,7 +630,7 @@ def main():
     def fresh_run(capacity, timed_steps):
         rcx = scenes.workload(args.workload)[1]
         rcx.width, rcx.height, rcx.seed = rc.width, rc.height, rc.seed
-        rcx.strategy_mask, rcx.lp_photons = rc.strategy_mask, rc.lp_photons
+        rcx.strategy_mask, rcx.lp_photons, rcx.merge_mode = rc.strategy_mask, rc.lp_photons, rc.merge_mode
         rcx.octree_capacity = capacity
         cx = neb.Context(neb.make_config(rcx, bvh_builder=args.bvh), stream.cuda_stream)
         cx.scene_upload(scene)

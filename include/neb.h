@@ -77,6 +77,17 @@ typedef struct {
                             shadow ray reached the light, for w_E and Phi = dE / rho, and the vertex
                             before each random light hit, for w_e); 1: at every NEE vertex.  The
                             image is the same either way; 1 only fills neb_read_nee_rho */
+  int merge_mode;        /* how photon hits are merged with the view vertices within r (Sec. 3.2).
+                            Per hit: the hit searches the grid of view vertices as it is made.
+                            Per cell: the photon walks stage their hits, and after the last walk
+                            the staged hits of each grid cell are merged together, their points in
+                            shared memory, each view vertex summing its merges before one FP64
+                            addition.  0 (default): hits with more than 64 view vertices in their
+                            cells per cell, the others per hit; 1: every hit per hit; 2: every hit
+                            per cell.  Hits that find the staging list full merge per hit.  All
+                            modes find the same pairs with the same terms; the sums differ only in
+                            rounding (per cell, a vertex's merges of one cell add in FP32 first) */
+  int merge_hits;        /* staging capacity of modes 0 and 2 in hits per iteration; 0: 2 W H (D - 1) */
 } neb_config;
 
 typedef struct {
@@ -91,6 +102,7 @@ typedef struct {
   int32_t octree_nodes, octree_depth;
   uint32_t status;                         /* NEB_STATUS_* bits, sticky */
   int32_t pad;
+  int64_t merge_hits_staged;               /* photon hits merged per cell (merge_mode 0 and 2) */
 } neb_stats;
 
 typedef struct neb_ctx neb_ctx;

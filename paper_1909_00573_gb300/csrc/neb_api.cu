@@ -80,13 +80,14 @@ static bool config_ok(const neb_config* cfg) {
          (cfg->bvh_builder == 0 || cfg->bvh_builder == 1) &&
          (cfg->photon_records == 0 || cfg->photon_records == 1) &&
          (cfg->density_all == 0 || cfg->density_all == 1) &&
+         cfg->merge_mode >= 0 && cfg->merge_mode <= 2 && cfg->merge_hits >= 0 &&
          (long long)cfg->width * cfg->height <= (1ll << 28);
 }
 
 // Queue capacities and hash-table size of a configuration (neb_create).
 struct Capacities {
-  size_t P, cap_cam, cap_nee, cap_rh, cap_ph;
-  uint32_t table;
+  size_t P, cap_cam, cap_nee, cap_rh, cap_ph, cap_mh;
+  uint32_t table, ptable;
 };
 static Capacities capacities(const neb_config* cfg) {
   Capacities k;
@@ -98,6 +99,12 @@ static Capacities capacities(const neb_config* cfg) {
   k.cap_ph = k.cap_nee;
   k.table = 1024;
   while (k.table < (uint32_t)k.cap_nee) k.table <<= 1;
+  // staged photon hits of the per-cell merge (none when every hit merges on
+  // its own); the photon table has a bucket per four staged hits
+  const size_t mh = cfg->merge_hits > 0 ? (size_t)cfg->merge_hits : 2 * k.cap_ph;
+  k.cap_mh = cfg->merge_mode != 1 ? (mh < ((size_t)1 << 30) ? mh : ((size_t)1 << 30)) : 0;
+  k.ptable = 1024;
+  while (k.ptable < k.table && (size_t)k.ptable * 4 < k.cap_mh) k.ptable <<= 1;
   return k;
 }
 
@@ -118,6 +125,8 @@ extern "C" int neb_job_device_bytes(const neb_config* cfg, int n_tri, int n_sph,
   b += scan_scratch_ints((size_t)k.table + 1) * sizeof(int) + k.P * 3 * (2 * sizeof(double) + sizeof(float));
   b += cfg->keep_split ? k.P * 12 * sizeof(double) : 0;
   b += 2 * k.cap_nee * (sizeof(ShadowRay) + sizeof(int)) + group_counter_ints() * sizeof(int);
+  b += k.cap_mh * (sizeof(MergeHit) + sizeof(int) + sizeof(int2)) +
+       (k.cap_mh ? 2 * ((size_t)k.ptable + 1) * sizeof(int) : 0);
   const size_t nt = (size_t)n_tri, ns = (size_t)n_sph, nl = (size_t)n_lights, np = nt + ns;
   b += 3 * nt * sizeof(float4) + ns * (sizeof(float4) + sizeof(int)) + 3 * (size_t)n_mat * sizeof(float4);
   b += np * sizeof(int) + nl * (2 * sizeof(int) + 3 * sizeof(float));
@@ -155,6 +164,8 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
   c->cap_nee = (int)k.cap_nee;
   c->cap_rh = (int)k.cap_rh;
   c->cap_ph = (int)k.cap_ph;
+  c->cap_mh = (int)k.cap_mh;
+  c->ptable_size = k.ptable;
   uint32_t t = k.table;
   c->table_size = t;
   c->scan_scratch.n = scan_scratch_ints((size_t)t + 1);
@@ -183,6 +194,11 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
   ok = ok && dalloc(&c->shadow_rays, c->cap_nee) == cudaSuccess && dalloc(&c->shadow_start, c->cap_nee) == cudaSuccess &&
        dalloc(&c->shadow_rays_b, c->cap_nee) == cudaSuccess && dalloc(&c->shadow_start_b, c->cap_nee) == cudaSuccess &&
        dalloc(&c->group_counters, group_counter_ints()) == cudaSuccess;
+  if (ok && c->cap_mh > 0)
+    ok = dalloc(&c->mh, (size_t)c->cap_mh) == cudaSuccess && dalloc(&c->mh_sorted, (size_t)c->cap_mh) == cudaSuccess &&
+         dalloc(&c->mh_tile, (size_t)c->cap_mh) == cudaSuccess &&
+         dalloc(&c->pb_count, (size_t)c->ptable_size + 1) == cudaSuccess &&
+         dalloc(&c->pb_start, (size_t)c->ptable_size + 1) == cudaSuccess;
   int prio_lo = 0, prio_hi = 0;
   cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   ok = ok && cudaStreamCreateWithPriority(&c->stream_hi, cudaStreamNonBlocking, prio_hi) == cudaSuccess &&
@@ -198,6 +214,7 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
     return NEB_ERR_OOM;
   }
   cudaMemsetAsync(c->bucket_count, 0, sizeof(int) * ((size_t)t + 1), c->stream);
+  if (c->pb_count) cudaMemsetAsync(c->pb_count, 0, sizeof(int) * ((size_t)c->ptable_size + 1), c->stream);
   cudaMemsetAsync(c->accum, 0, sizeof(double) * P * 6, c->stream);
   cudaMemsetAsync(c->counters, 0, 2 * sizeof(DevCounters), c->stream);
   cudaMemsetAsync(c->group_counters, 0, sizeof(int) * group_counter_ints(), c->stream);
@@ -228,6 +245,7 @@ extern "C" void neb_destroy(neb_ctx* c) {
   if (c->ev_frame) cudaEventDestroy(c->ev_frame);
   cudaFree(c->shadow_rays); cudaFree(c->shadow_start); cudaFree(c->shadow_rays_b); cudaFree(c->shadow_start_b);
   cudaFree(c->group_counters);
+  cudaFree(c->mh); cudaFree(c->mh_sorted); cudaFree(c->mh_tile); cudaFree(c->pb_count); cudaFree(c->pb_start);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
   for (int k = 0; k < 2; ++k) {
@@ -799,6 +817,7 @@ extern "C" int neb_get_stats(neb_ctx* c, neb_stats* out) {
   h.octree_queries += h1.octree_queries;
   h.node_visits += h1.node_visits;
   h.prim_tests += h1.prim_tests;
+  h.merge_hits_staged += h1.merge_hits_staged;
   for (int i = 0; i < 3; ++i) {
     h.visits_by[i] += h1.visits_by[i];
     h.ptests_by[i] += h1.ptests_by[i];
@@ -825,6 +844,7 @@ extern "C" int neb_get_stats(neb_ctx* c, neb_stats* out) {
   out->octree_nodes = os.alloc < c->oct_cap ? os.alloc : c->oct_cap;
   out->octree_depth = os.depth;
   out->status = h.status | os.status;
+  out->merge_hits_staged = (int64_t)h.merge_hits_staged;
   if (out->status & NEB_STATUS_SPIN_TIMEOUT) return fail(c, NEB_ERR_DEVICE_TIMEOUT, "octree insert spin timed out");
   if (out->status & (NEB_STATUS_QUEUE_OVERFLOW | NEB_STATUS_STACK_OVERFLOW))
     return fail(c, NEB_ERR_QUEUE_OVERFLOW, "device queue or traversal stack overflowed");
@@ -834,7 +854,7 @@ extern "C" int neb_get_stats(neb_ctx* c, neb_stats* out) {
 static const char* kStageNames[STAGE_COUNT] = {"rearm",      "camera",   "trace_camera", "extend",
                                                "shadow",     "octree_insert", "density", "nee_emit",
                                                "grid_build", "emission", "trace_photon", "photon",
-                                               "group"};
+                                               "group",      "merge"};
 
 extern "C" int neb_set_profiling(neb_ctx* c, int enable) {
   if (!c) return NEB_ERR_ARG;

@@ -62,6 +62,16 @@ struct __align__(16) MergeRec {
   float4 pos;  // xyz, w: NEE id (int bits)
 };
 
+// Photon hit staged for the per-cell merge (48 bytes): everything the merge
+// of this hit with a view vertex x_k reads, with the hit's 1 / w written as
+// c0 (1 + c1' pdfF + c2' pdfC Cfac) and c0 folded into the flux (c0 = 1 for
+// NEB photons, so their terms are the ones the per-hit merge computes).
+struct __align__(16) MergeHit {
+  float4 key;  // hit point xyz, w: kmax | (channel - 2) << 8 (int bits)
+  float4 dir;  // -photon direction (towards where it came from), w: c1'
+  float4 phi;  // flux / c0 (rgb), w: c2'
+};
+
 // NEE vertex store, structure of arrays (one float4 per field).
 struct NeeStore {
   float4* pos;   // xyz, w: Cfac_k = C'_k cos_prev / (pdf_fwd |cos_k|)
@@ -94,6 +104,12 @@ struct DevCounters {
   unsigned long long node_visits, prim_tests;
   unsigned long long visits_by[3], ptests_by[3];  // camera, shadow, photon traversal
   int fetch[4];                                   // dynamic-fetch counters of the traversal kernels
+  int mh_count;                                   // photon hits staged for the per-cell merge
+  int mh_tiles;                                   // full tiles of staged hits (of one bucket)
+  int mh_small;                                   // partial tiles (the rest of a bucket)
+  int mh_next, mh_next_small;                     // dynamic fetch of the tiles
+  int pad_;
+  unsigned long long merge_hits_staged;           // hits merged through the per-cell merge
 };
 
 // Buffers that pass 1 of an iteration fills and passes 2 and 3 read.  There
@@ -123,10 +139,13 @@ struct IterParams {
   float3 gmin;          // hashed grid origin
   float cell_inv;       // 1 / (2 r)
   uint32_t table_mask;  // hash table size - 1
+  int cap_mh;           // staged photon hits per iteration (0: every hit merges on its own)
+  int stage_min;        // a hit is staged when more view vertices than this lie in its cells
 };
 
 enum { STAGE_REARM = 0, STAGE_CAMERA, STAGE_TRACE_CAM, STAGE_EXTEND, STAGE_SHADOW, STAGE_INSERT, STAGE_DENSITY,
-       STAGE_NEE, STAGE_GRID, STAGE_EMISSION, STAGE_TRACE_PHOTON, STAGE_PHOTON, STAGE_GROUP, STAGE_COUNT };
+       STAGE_NEE, STAGE_GRID, STAGE_EMISSION, STAGE_TRACE_PHOTON, STAGE_PHOTON, STAGE_GROUP, STAGE_MERGE,
+       STAGE_COUNT };
 // timed stage intervals per iteration: 5 D + 5 for max depth D (up to D = 64)
 constexpr int kMaxStageRecords = 5 * kMaxDepth + 8;
 
@@ -185,6 +204,15 @@ struct neb_ctx {
   int* bucket_start = nullptr;
   int cap_cam = 0, cap_nee = 0, cap_rh = 0, cap_ph = 0;
   uint32_t table_size = 0;
+  // per-cell merge: staged photon hits, their order by bucket of the photon
+  // table, the tiles, and the photon table's counts and starts
+  neb::MergeHit* mh = nullptr;
+  int* mh_sorted = nullptr;
+  int2* mh_tile = nullptr;
+  int* pb_count = nullptr;
+  int* pb_start = nullptr;
+  int cap_mh = 0;
+  uint32_t ptable_size = 0;
   neb::Scratch scan_scratch;
   double* accum = nullptr;  // FP64 sums: [2][P][3], even iterations then odd iterations
   float* frame = nullptr;             // resolved image staged for neb_iterate_read
@@ -259,6 +287,13 @@ cudaError_t count_neighbours_device(const float* d_pts, int n, const float* d_q,
 // order.
 cudaError_t build_point_grid(const float* d_pts, int n, float cell, float3 gmin, uint32_t table, int* bucket_count,
                              int* bucket_start, int* vert_bucket, float4* sorted, Scratch& sc, cudaStream_t st);
+
+// neb_merge.cu
+// Per-cell merge of the photon hits staged during the photon walks: orders
+// them by cell, then merges every cell's hits with the view vertices around
+// it.  Returns the number of kernels enqueued through *launches.
+cudaError_t merge_staged(neb_ctx* c, const IterParams& ip, const IterSlot& sl, double* accum, double* split,
+                         cudaStream_t st, long long* launches);
 
 // neb_octree.cu
 OctreeParams octree_params(const float smin[3], const float smax[3], int capacity, int split_factor);

@@ -34,6 +34,9 @@ constexpr int kThreads = 256;
 constexpr int PH_J_SHIFT = 8, PH_J_MASK = 63;
 constexpr int PH_LP = 1 << 14, PH_FIRST = 1 << 15;
 constexpr uint32_t kLpStream = 0x40000000u;  // Philox stream of light photon i: + hit index
+// Merge mode 0: a photon hit with more view vertices than this in the grid
+// cells around it is staged for the per-cell merge; sparser hits merge at once.
+constexpr int kStageCandidates = 64;
 
 // ---- photon queue records: PhotonRay (64 bytes) or PackedPhoton (48 bytes)
 union Half2Bits {
@@ -91,24 +94,6 @@ static int grid_blocks(const neb_ctx* c) {
   return sms * c->tune.shade_blocks_per_sm;
 }
 
-__device__ __forceinline__ void warp_count(unsigned long long* dst, uint32_t v) {
-  uint32_t s = __reduce_add_sync(0xffffffffu, v);
-  if ((threadIdx.x & 31) == 0 && s) atomicAdd(dst, (unsigned long long)s);
-}
-
-__device__ __forceinline__ void add_pixel(double* accum, double* split, int which, int pixel, float3 L, int P) {
-  double* a = accum + (size_t)pixel * 3;
-  atomicAdd(a, (double)L.x);
-  atomicAdd(a + 1, (double)L.y);
-  atomicAdd(a + 2, (double)L.z);
-  if (split) {
-    double* sp = split + ((size_t)which * P + pixel) * 3;
-    atomicAdd(sp, (double)L.x);
-    atomicAdd(sp + 1, (double)L.y);
-    atomicAdd(sp + 2, (double)L.z);
-  }
-}
-
 // NEE area pdf p_l of point y on light li seen from x (power-proportional
 // selection times uniform area on triangles / on the hemisphere of a sphere
 // that faces x).
@@ -152,6 +137,11 @@ __global__ void k_begin(DevCounters* cnt) {
   cnt->merge_count = 0;
   cnt->lit_count = 0;
   cnt->shadow_count_b = 0;
+  cnt->mh_count = 0;
+  cnt->mh_tiles = 0;
+  cnt->mh_small = 0;
+  cnt->mh_next = 0;
+  cnt->mh_next_small = 0;
 }
 
 __global__ void k_camera(IterParams ip, CameraParams cam, CamRay* q, DevCounters* cnt) {
@@ -537,7 +527,7 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
                                                      const int* __restrict__ bucket_start, DevCounters* cnt,
                                                      double* accum, double* split, const int2* __restrict__ hits,
                                                      const int* __restrict__ oct_nodes, const OctreeState* oct_state,
-                                                     OctreeParams oct, int robust) {
+                                                     OctreeParams oct, int robust, MergeHit* __restrict__ mh) {
   const int count = min(cnt->ph_count[in_slot], ip.cap_ph);
   const int stride = gridDim.x * blockDim.x;
   const int P = ip.W * ip.H;
@@ -701,6 +691,30 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
     } else {
 #pragma unroll
       for (int c = 0; c < 8; ++c) cb[c] = cl[c] = 0;
+    }
+    // A hit with many view vertices in its cells is staged for the per-cell
+    // merge that follows the last photon walk (if the list has room); the
+    // others merge here.
+    if (ip.cap_mh > 0) {
+      const bool dense = want_merge && nl > ip.stage_min;
+      const unsigned sm = __ballot_sync(0xffffffffu, dense);
+      if (sm) {
+        const int leader = __ffs(sm) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&cnt->mh_count, __popc(sm));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        const int slot = base + __popc(sm & ((1u << lane) - 1u));
+        if (dense && slot < ip.cap_mh) {
+          MergeHit h;
+          h.key = make_float4(m_p.x, m_p.y, m_p.z, __int_as_float((m_kmax & 0xff) | ((m_chan - 2) << 8)));
+          h.dir = make_float4(-m_d.x, -m_d.y, -m_d.z, m_c1 / m_c0);
+          h.phi = make_float4(m_phi.x / m_c0, m_phi.y / m_c0, m_phi.z / m_c0, m_c2 / m_c0);
+          mh[slot] = h;
+          nl = 0;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) cl[c] = 0;
+        }
+      }
     }
     int incl = nl;
 #pragma unroll
@@ -884,6 +898,8 @@ IterParams iter_params(const neb_ctx* c, int iteration) {
   ip.gmin = f3(c->bmin[0] - cs, c->bmin[1] - cs, c->bmin[2] - cs);
   ip.cell_inv = 1.0f / cs;
   ip.table_mask = c->table_size - 1;
+  ip.cap_mh = c->cap_mh;
+  ip.stage_min = c->cfg.merge_mode == 2 ? -1 : kStageCandidates;
   return ip;
 }
 
@@ -998,8 +1014,13 @@ static long long enqueue_pass23(neb_ctx* c, int iteration, cudaStream_t st2, Sta
       tm.begin(STAGE_PHOTON);
       k_photon<<<capped_blocks(c->cap_ph, kThreads, B), kThreads, 0, st2>>>(s, ip, j, c->phq[in], in, c->phq[out], out, c->cfg.photon_records, sl.nv, c->mrec, c->bucket_start, cnt,
                                         accum, split, c->hits_ph, c->oct_nodes, c->oct_state, c->oct,
-                                        c->cfg.density_mode == 0);
+                                        c->cfg.density_mode == 0, c->mh);
       launches += 3;
+      tm.end();
+    }
+    if (ip.cap_mh > 0) {
+      tm.begin(STAGE_MERGE);
+      merge_staged(c, ip, sl, accum, split, st2, &launches);
       tm.end();
     }
   }

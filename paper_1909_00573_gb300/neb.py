@@ -43,7 +43,8 @@ class Config(C.Structure):
                 ("octree_capacity", C.c_int), ("split_factor", C.c_int), ("seed", C.c_uint64),
                 ("octree_mode", C.c_int), ("density_mode", C.c_int), ("strategy_mask", C.c_uint32),
                 ("keep_split", C.c_int), ("bvh_builder", C.c_int), ("photon_records", C.c_int),
-                ("lp_photons", C.c_int), ("density_all", C.c_int)]
+                ("lp_photons", C.c_int), ("density_all", C.c_int), ("merge_mode", C.c_int),
+                ("merge_hits", C.c_int)]
 
 
 class Tuning(C.Structure):
@@ -62,7 +63,7 @@ class Stats(C.Structure):
                 ("prim_tests", C.c_int64), ("kernel_launches", C.c_int64),
                 ("stage_node_visits", C.c_int64 * 3), ("stage_prim_tests", C.c_int64 * 3),
                 ("octree_nodes", C.c_int32), ("octree_depth", C.c_int32),
-                ("status", C.c_uint32), ("pad", C.c_int32)]
+                ("status", C.c_uint32), ("pad", C.c_int32), ("merge_hits_staged", C.c_int64)]
 
     def as_dict(self):
         d = {}
@@ -143,13 +144,14 @@ def _check(rc, ctx=None):
 
 
 def make_config(rc, keep_split=False, octree_mode=None, density_mode=None, strategy_mask=None, bvh_builder=0,
-                photon_records=0):
+                photon_records=0, merge_mode=None, merge_hits=0):
     """neb_config from a scenes.RenderConfig."""
     return Config(rc.width, rc.height, rc.max_depth, rc.merge_radius, rc.octree_capacity, rc.split_factor,
                   rc.seed, rc.octree_mode if octree_mode is None else octree_mode,
                   rc.density_mode if density_mode is None else density_mode,
                   rc.strategy_mask if strategy_mask is None else strategy_mask, int(keep_split), int(bvh_builder),
-                  int(photon_records), int(getattr(rc, "lp_photons", 0)), int(getattr(rc, "density_all", 0)))
+                  int(photon_records), int(getattr(rc, "lp_photons", 0)), int(getattr(rc, "density_all", 0)),
+                  int(getattr(rc, "merge_mode", 0) if merge_mode is None else merge_mode), int(merge_hits))
 
 
 class Context:

@@ -96,6 +96,7 @@ class RenderConfig:
                                 # bit 3 conventional light-photon merge (LP, Sec. 6.1)
     lp_photons: int = 0         # light photons per iteration (n_LP) when bit 3 is set
     density_all: int = 0        # 1: evaluate rho at every NEE vertex, not only where a result uses it
+    merge_mode: int = 0         # photon merge: 0 dense hits per cell, sparse per hit; 1 per hit; 2 per cell
 
 
 class SplitMix64:

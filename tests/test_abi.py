@@ -71,7 +71,12 @@ def test_batch_and_admission_arguments_without_gpu(libneb):
     cfg = neb.make_config(rc)
     b = neb.job_device_bytes(cfg, s.n_tri, s.n_sph, len(s.mats), s.n_emitters)
     # two NEE slots of 112 B per vertex dominate: 2 x 921,600 x 9 x 112 B
-    assert 2 * 921600 * 9 * 112 < b < 6e9
+    assert 2 * 921600 * 9 * 112 < b < 7e9
+    # the staging list of the per-cell merge: 2 x 921,600 x 9 hits of 48 B, a
+    # 4-B order and an 8-B tile each, and two 4-B arrays per photon bucket
+    inline = neb.job_device_bytes(neb.make_config(rc, merge_mode=1), s.n_tri, s.n_sph, len(s.mats),
+                                  s.n_emitters)
+    assert b - inline == 2 * 921600 * 9 * 60 + 2 * 4 * ((1 << 22) + 1)
     split = neb.job_device_bytes(neb.make_config(rc, keep_split=True), s.n_tri, s.n_sph, len(s.mats),
                                  s.n_emitters)
     assert split - b == 921600 * 12 * 8                         # the FP64 per-strategy split (4 strategies)

@@ -455,18 +455,29 @@ def test_tiny_room_per_path_parity(neb, oracle):
         abs(st["nee_vertices"] - ref["stats"]["nee_vertices"]) <= 2
 
 
-def test_overlapped_iterations_equal_sequential(neb):
+def sums_close(a, b, merge_mode):
+    """FP64 sums of two runs of the same work: equal up to the order of the
+    FP64 atomic additions when every photon hit merges on its own (merge mode
+    1); with the per-cell merge (modes 0 and 2) each view vertex first sums
+    its merges of one tile in FP32, in an order that varies from run to run,
+    so the photon-merge part agrees to FP32 rounding of those partial sums."""
+    rtol, atol = (1e-12, 1e-12) if merge_mode == 1 else (1e-5, 1e-7)
+    np.testing.assert_allclose(a, b, rtol=rtol, atol=atol * float(np.abs(b).max()))
+
+
+@pytest.mark.parametrize("merge_mode", [1, 2])
+def test_overlapped_iterations_equal_sequential(neb, merge_mode):
     """Passes 2-3 of iteration i overlap pass 1 of iteration i + 1 on a second
     stream (two buffer slots).  With the deterministic octree, that schedule
     must give the same results as running every stage in order on one stream
     (stage timing forces the latter): identical densities and counters, and
-    FP64 sums equal up to the order of the atomic additions."""
+    FP64 sums equal up to the order of the additions."""
     from paper_1909_00573_gb300 import scenes
     s, rc = scenes.workload("tiny_room")
     rc.octree_mode = 1
     out = []
     for sequential in (False, True):
-        ctx = neb.Context(neb.make_config(rc, keep_split=True))
+        ctx = neb.Context(neb.make_config(rc, keep_split=True, merge_mode=merge_mode))
         ctx.scene_upload(s)
         ctx.build_bvh()
         ctx.set_profiling(sequential)
@@ -475,11 +486,15 @@ def test_overlapped_iterations_equal_sequential(neb):
         ctx.close()
     (r0, sp0, a0, st0), (r1, sp1, a1, st1) = out
     assert np.array_equal(r0, r1)
-    for key in ("camera_rays", "nee_vertices", "shadow_rays", "photons", "photon_hits", "merge_tests", "merges",
-                "random_hits", "octree_inserts", "octree_queries", "octree_nodes", "iterations"):
+    keys = ["camera_rays", "nee_vertices", "shadow_rays", "photons", "photon_hits", "merges", "random_hits",
+            "octree_inserts", "octree_queries", "octree_nodes", "iterations", "merge_hits_staged"]
+    if merge_mode == 1:
+        keys.append("merge_tests")          # per cell, the tests depend on how a cell's hits are tiled
+    for key in keys:
         assert st0[key] == st1[key], key
-    np.testing.assert_allclose(sp0, sp1, rtol=1e-12, atol=1e-12 * float(np.abs(sp1).max()))
-    np.testing.assert_allclose(a0, a1, rtol=1e-12, atol=1e-12 * float(np.abs(a1).max()))
+    assert (st0["merge_hits_staged"] > 0) == (merge_mode == 2)
+    sums_close(sp0, sp1, merge_mode)
+    sums_close(a0, a1, merge_mode)
     assert a0.sum() > 0
 
 
@@ -505,7 +520,9 @@ def test_density_only_where_used_changes_no_result(neb, name, lp):
     out = {}
     for every in (0, 1):
         rc.density_all = every
-        ctx = neb.Context(neb.make_config(rc, keep_split=True))
+        # every hit merges on its own: the sums then differ only in the order
+        # of the FP64 additions
+        ctx = neb.Context(neb.make_config(rc, keep_split=True, merge_mode=1))
         ctx.scene_upload(s)
         ctx.build_bvh()
         ctx.iterate(rc.iterations)

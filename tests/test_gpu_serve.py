@@ -94,7 +94,8 @@ def test_served_jobs_retire_at_their_rmse_target(mods):
         assert res.reached or res.iterations == 64
         ctx = neb.render(req.scene, req.rc, n_iter=res.iterations)
         solo = ctx.resolve()
-        assert ctx.error_estimate() == pytest.approx(res.rmse, rel=1e-9)
+        # the same samples; per-cell merge sums round differently from run to run
+        assert ctx.error_estimate() == pytest.approx(res.rmse, rel=1e-5)
         ctx.close()
         np.testing.assert_allclose(res.image, solo, rtol=1e-5, atol=1e-7 * float(np.abs(solo).max()))
     its = sorted(r.iterations for r in results)
