@@ -82,7 +82,7 @@ typedef struct {
                             Per cell: the photon walks stage their hits, and after the last walk
                             the staged hits of each grid cell are merged together, their points in
                             shared memory, each view vertex summing its merges before one FP64
-                            addition.  0 (default): hits with more than 64 view vertices in their
+                            addition.  0 (default): hits with more than 16 view vertices in their
                             cells per cell, the others per hit; 1: every hit per hit; 2: every hit
                             per cell.  Hits that find the staging list full merge per hit.  All
                             modes find the same pairs with the same terms; the sums differ only in

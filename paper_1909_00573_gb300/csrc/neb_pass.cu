@@ -36,7 +36,7 @@ constexpr int PH_LP = 1 << 14, PH_FIRST = 1 << 15;
 constexpr uint32_t kLpStream = 0x40000000u;  // Philox stream of light photon i: + hit index
 // Merge mode 0: a photon hit with more view vertices than this in the grid
 // cells around it is staged for the per-cell merge; sparser hits merge at once.
-constexpr int kStageCandidates = 64;
+constexpr int kStageCandidates = 16;
 
 // ---- photon queue records: PhotonRay (64 bytes) or PackedPhoton (48 bytes)
 union Half2Bits {

@@ -70,10 +70,8 @@ def test_per_cell_merge_equals_per_hit_merge(neb, name):
         assert 0 < staged <= 3 * cap                       # at most cap staged per iteration
     if name == "list_full":
         assert staged == 3 * cap                           # the rest merged per hit
-    elif name == "default_dense":
-        assert staged > 0.5 * st0["photon_hits"]           # most hits have many vertices around them
-    elif name == "default_sparse":
-        assert staged < 0.1 * st0["photon_hits"]
+    elif name.startswith("default"):
+        assert staged < st0["photon_hits"]
     else:
         assert staged > 3 * 2000
     # per strategy: random hits and NEE do not merge; the merge channels
@@ -85,3 +83,14 @@ def test_per_cell_merge_equals_per_hit_merge(neb, name):
     if CASES[name][4]:
         assert float(np.abs(sp1[3]).sum()) > 0
     np.testing.assert_allclose(a0, a1, rtol=2e-5, atol=1e-7 * float(np.abs(a1).max()))
+
+
+def test_default_mode_stages_the_dense_hits(neb):
+    """Merge mode 0 stages a hit when more than 16 view vertices lie in its
+    grid cells: with 16 times the pixels of the same room most hits are
+    staged, a larger share than at the smaller size."""
+    frac = {}
+    for name in ("default_sparse", "default_dense"):
+        st = _run(neb, name, 0)[2]
+        frac[name] = st["merge_hits_staged"] / st["photon_hits"]
+    assert frac["default_dense"] > 0.5 and frac["default_dense"] > frac["default_sparse"], frac
