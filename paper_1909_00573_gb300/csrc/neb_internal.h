@@ -108,7 +108,7 @@ struct DevCounters {
   int mh_tiles;                                   // full tiles of staged hits (of one bucket)
   int mh_small;                                   // partial tiles (the rest of a bucket)
   int mh_next, mh_next_small;                     // dynamic fetch of the tiles
-  int pad_;
+  int oct_deferred;                               // octree inserts deferred past an exhausted pool
   unsigned long long merge_hits_staged;           // hits merged through the per-cell merge
 };
 

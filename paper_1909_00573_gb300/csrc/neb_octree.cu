@@ -54,25 +54,63 @@ __global__ void k_oct_rearm(int* nodes, const OctreeState* st, OctreeParams P) {
     nodes[i] = P.init_value;
 }
 
+// Appends index i to a list when pred (warp-aggregated; all lanes call it).
+__device__ __forceinline__ void warp_push(int* list, int* count, bool pred, int i) {
+  const unsigned m = __ballot_sync(0xffffffffu, pred);
+  if (m == 0) return;
+  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = i;
+}
+
+// Counts one vertex per lane in its leaf once no cell can split any more:
+// a read-only descent, and lanes of a warp that land in the same leaf add
+// their count with one atomic (neighbouring paths share leaves; crowded
+// leaves would otherwise serialise thousands of single increments).  All
+// lanes call it; pos == nullptr for a lane without a vertex.
+__device__ __forceinline__ void oct_count_frozen(int* nodes, const OctreeParams& P, const float* pos) {
+  const int leaf = pos ? oct_frozen_leaf(nodes, P, pos) : -1;
+  const unsigned same = __match_any_sync(0xffffffffu, leaf);
+  if (leaf >= 0 && (int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(nodes + leaf, __popc(same));
+}
+
+// Concurrent inserts of n points; those that find the pool exhausted go to
+// the deferred list, counted by k_oct_count_deferred_points after this launch.
 __global__ void k_oct_insert_points(int* nodes, OctreeState* st, OctreeParams P, const float* __restrict__ pos, int n,
-                                    int spin_limit) {
+                                    int spin_limit, int* deferred, int* n_deferred) {
   const bool frozen = st->alloc > P.capacity;  // overflowed in an earlier launch
-  if (frozen) {
-    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
-      int i = base + threadIdx.x;
-      int leaf = -1;
-      if (i < n) {
-        float p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
-        leaf = oct_frozen_leaf(nodes, P, p);
-      }
-      unsigned same = __match_any_sync(0xffffffffu, leaf);
-      if (leaf >= 0 && (int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(nodes + leaf, __popc(same));
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int i = base + threadIdx.x;
+    float p[3] = {0.0f, 0.0f, 0.0f};
+    if (i < n) {
+      p[0] = pos[3 * i];
+      p[1] = pos[3 * i + 1];
+      p[2] = pos[3 * i + 2];
     }
-    return;
+    if (frozen) {
+      oct_count_frozen(nodes, P, i < n ? p : nullptr);
+      continue;
+    }
+    const bool later = i < n && !oct_insert<true>(nodes, st, P, p, spin_limit);
+    warp_push(deferred, n_deferred, later, i);
   }
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    float p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
-    oct_insert(nodes, st, P, p, spin_limit);
+}
+
+__global__ void k_oct_count_deferred_points(int* nodes, OctreeParams P, const float* __restrict__ pos,
+                                            const int* __restrict__ deferred, const int* n_deferred) {
+  const int n = *n_deferred;
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int i = base + threadIdx.x;
+    float p[3] = {0.0f, 0.0f, 0.0f};
+    if (i < n) {
+      const int j = deferred[i];
+      p[0] = pos[3 * j];
+      p[1] = pos[3 * j + 1];
+      p[2] = pos[3 * j + 2];
+    }
+    oct_count_frozen(nodes, P, i < n ? p : nullptr);
   }
 }
 
@@ -95,38 +133,53 @@ __global__ void k_oct_density_points(const int* __restrict__ nodes, OctreeParams
   }
 }
 
-// NEB pass: inserts of this iteration's NEE vertices
+// NEB pass: inserts of this iteration's NEE vertices.  Once the pool is
+// exhausted (in an earlier iteration, or during this launch for the vertices
+// that meet it, which go to the deferred list) no cell can split any more and
+// every insert only counts in its leaf.
 __global__ void k_oct_insert_nee(int* nodes, OctreeState* st, OctreeParams P, const float4* __restrict__ vpos,
-                                 DevCounters* cnt, int cap, int spin_limit) {
+                                 DevCounters* cnt, int cap, int spin_limit, int* deferred) {
   int count = min(cnt->nee_count, cap);
   const bool frozen = st->alloc > P.capacity;  // overflowed in an earlier iteration
   uint32_t done = 0;
-  if (frozen) {
-    // No cell can split any more: every insert only counts in its leaf.  Lanes
-    // of a warp that land in the same leaf add their count with one atomic
-    // (neighbouring paths share leaves; crowded leaves would otherwise
-    // serialise thousands of single increments).
-    for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
-      int i = base + threadIdx.x;
-      int leaf = -1;
-      if (i < count) {
-        float4 v = vpos[i];
-        float p[3] = {v.x, v.y, v.z};
-        leaf = oct_frozen_leaf(nodes, P, p);
-        ++done;
-      }
-      unsigned same = __match_any_sync(0xffffffffu, leaf);
-      if (leaf >= 0 && (int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(nodes + leaf, __popc(same));
+  for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
+    const int i = base + threadIdx.x;
+    float p[3] = {0.0f, 0.0f, 0.0f};
+    if (i < count) {
+      const float4 v = vpos[i];
+      p[0] = v.x;
+      p[1] = v.y;
+      p[2] = v.z;
     }
-  } else {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
-      float4 v = vpos[i];
-      float p[3] = {v.x, v.y, v.z};
-      oct_insert(nodes, st, P, p, spin_limit);
-      ++done;
+    if (frozen) {
+      oct_count_frozen(nodes, P, i < count ? p : nullptr);
+      done += i < count;
+      continue;
     }
+    const bool later = i < count && !oct_insert<true>(nodes, st, P, p, spin_limit);
+    done += i < count && !later;
+    warp_push(deferred, &cnt->oct_deferred, later, i);
   }
   if (done) atomicAdd(&cnt->octree_inserts, (unsigned long long)done);
+}
+
+// The vertices that met the exhausted pool during k_oct_insert_nee, counted
+// in their leaves now that every link of that launch is published.
+__global__ void k_oct_count_deferred_nee(int* nodes, OctreeParams P, const float4* __restrict__ vpos,
+                                         DevCounters* cnt, const int* __restrict__ deferred) {
+  const int n = cnt->oct_deferred;
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int i = base + threadIdx.x;
+    float p[3] = {0.0f, 0.0f, 0.0f};
+    if (i < n) {
+      const float4 v = vpos[deferred[i]];
+      p[0] = v.x;
+      p[1] = v.y;
+      p[2] = v.z;
+    }
+    oct_count_frozen(nodes, P, i < n ? p : nullptr);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && n) atomicAdd(&cnt->octree_inserts, (unsigned long long)n);
 }
 
 // deterministic mode: one thread inserts in (pixel, k) order
@@ -184,11 +237,19 @@ cudaError_t launch_oct_rearm(int* nodes, const OctreeState* st, const OctreePara
 cudaError_t launch_oct_insert_points(int* nodes, OctreeState* st, const OctreeParams& P, const float* d_pos, int n,
                                      int mode, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  if (mode == 1)
+  if (mode == 1) {
     k_oct_insert_points_seq<<<1, 1, 0, s>>>(nodes, st, P, d_pos, n);
-  else
-    k_oct_insert_points<<<blocks_for(n, 256), 256, 0, s>>>(nodes, st, P, d_pos, n, kSpinLimit);
-  return cudaGetLastError();
+    return cudaGetLastError();
+  }
+  int* deferred = nullptr;  // the deferred list, then its length
+  cudaError_t e = cudaMallocAsync(&deferred, sizeof(int) * ((size_t)n + 1), s);
+  if (e != cudaSuccess) return e;
+  cudaMemsetAsync(deferred + n, 0, sizeof(int), s);
+  k_oct_insert_points<<<blocks_for(n, 256), 256, 0, s>>>(nodes, st, P, d_pos, n, kSpinLimit, deferred, deferred + n);
+  k_oct_count_deferred_points<<<blocks_for(n, 256), 256, 0, s>>>(nodes, P, d_pos, deferred, deferred + n);
+  e = cudaGetLastError();
+  cudaFreeAsync(deferred, s);
+  return e;
 }
 
 cudaError_t launch_oct_density_points(const int* nodes, const OctreeState* st, const OctreeParams& P,
@@ -204,9 +265,14 @@ cudaError_t launch_oct_insert_nee(neb_ctx* c, const IterSlot& sl, cudaStream_t s
   if (c->cfg.octree_mode == 1)
     k_oct_insert_nee_seq<<<1, 1, 0, st>>>(c->oct_nodes, c->oct_state, c->oct, sl.nv.pos, sl.slot_map,
                                           c->P * (c->D - 1), sl.cnt);
-  else
-    k_oct_insert_nee<<<capped_blocks(c->cap_nee, 256, 152 * 8), 256, 0, st>>>(c->oct_nodes, c->oct_state, c->oct, sl.nv.pos, sl.cnt, c->cap_nee,
-                                              kSpinLimit);
+  else {
+    // the deferred list borrows the grid's per-vertex bucket array, which the
+    // grid build of this iteration writes afresh after the density pass
+    const int B = capped_blocks(c->cap_nee, 256, 152 * 8);
+    k_oct_insert_nee<<<B, 256, 0, st>>>(c->oct_nodes, c->oct_state, c->oct, sl.nv.pos, sl.cnt, c->cap_nee, kSpinLimit,
+                                        c->vert_bucket);
+    k_oct_count_deferred_nee<<<B, 256, 0, st>>>(c->oct_nodes, c->oct, sl.nv.pos, sl.cnt, c->vert_bucket);
+  }
   return cudaGetLastError();
 }
 

@@ -151,6 +151,18 @@ __device__ __forceinline__ int oct_wait_for_link(const int* word, OctreeState* s
 // capacity, status bit) and the cell keeps counting.
 template <bool kSequential>
 __device__ __forceinline__ void oct_split(int* nodes, OctreeState* st, const OctreeParams& P, int word, int level) {
+  if (!kSequential) {
+    // Once the pool is used up no cell can split: the many cells that still
+    // reach their threshold then take no atomic on the two pool words (one
+    // marks the pool exhausted, so vertices waiting for a link stop waiting).
+    const int a = *((const volatile int*)&st->alloc);
+    if (a + 8 > P.capacity) {
+      if (a <= P.capacity) atomicMax(&st->alloc, P.capacity + 1);
+      if (!(*((const volatile uint32_t*)&st->status) & NEB_STATUS_OCTREE_FULL))
+        atomicOr(&st->status, NEB_STATUS_OCTREE_FULL);
+      return;
+    }
+  }
   const int first = kSequential ? st->alloc : atomicAdd(&st->alloc, 8);
   if (first + 8 > P.capacity) {
     if (kSequential) {
@@ -200,8 +212,17 @@ __device__ __forceinline__ void oct_count_seq(int* nodes, OctreeState* st, const
 // are enough on the way down: a link never changes once published, and a
 // stale count only makes the compare-and-swap fail and return the word's
 // current value.
-__device__ __forceinline__ void oct_count(int* nodes, OctreeState* st, const OctreeParams& P, const OctKey& k,
+//
+// kDefer: a vertex that finds the pool exhausted before it is counted returns
+// false instead, and the caller counts it after the launch, when every link
+// of the launch is published and the tree can no longer change (a read-only
+// descent and an add): once the pool runs out, most vertices meet full cells
+// and would otherwise all count past the threshold through contended
+// compare-and-swaps.  Returns true when the vertex was counted.
+template <bool kDefer>
+__device__ __forceinline__ bool oct_count(int* nodes, OctreeState* st, const OctreeParams& P, const OctKey& k,
                                           int spin_limit) {
+  if (kDefer && *((const volatile int*)&st->alloc) > P.capacity) return false;
   const int lane = threadIdx.x & 31;
   int word = 0, level = 0;
   bool past = false;  // counting past the threshold of this cell is allowed
@@ -218,6 +239,7 @@ __device__ __forceinline__ void oct_count(int* nodes, OctreeState* st, const Oct
     if (v >= limit) {
       v = oct_wait_for_link(nodes + word, st, P, spin_limit);
       if (v >= 0) {
+        if (kDefer && *((const volatile int*)&st->alloc) > P.capacity) return false;
         past = true;
         v = nodes[word];
       }
@@ -249,17 +271,20 @@ __device__ __forceinline__ void oct_count(int* nodes, OctreeState* st, const Oct
     got = __shfl_sync(grp, got, leader);
     if (rank < got) {
       if (limit == P.split_count && base + rank + 1 == limit) oct_split<false>(nodes, st, P, word, level);
-      return;
+      return true;
     }
     v = got > 0 ? base + got : base;  // the word as the group left it
   }
 }
 
-__device__ __forceinline__ void oct_insert(int* nodes, OctreeState* st, const OctreeParams& P, const float pos[3],
+// Concurrent insert of one vertex; false when it was deferred (kDefer).
+template <bool kDefer>
+__device__ __forceinline__ bool oct_insert(int* nodes, OctreeState* st, const OctreeParams& P, const float pos[3],
                                            int spin_limit) {
-  if (P.stop_filling) return;
+  if (P.stop_filling) return true;
   OctKey k;
-  if (oct_key(P, pos[0], pos[1], pos[2], k)) oct_count(nodes, st, P, k, spin_limit);
+  if (oct_key(P, pos[0], pos[1], pos[2], k)) return oct_count<kDefer>(nodes, st, P, k, spin_limit);
+  return true;
 }
 
 __device__ __forceinline__ void oct_insert_seq(int* nodes, OctreeState* st, const OctreeParams& P,

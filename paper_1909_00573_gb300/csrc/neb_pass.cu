@@ -142,6 +142,7 @@ __global__ void k_begin(DevCounters* cnt) {
   cnt->mh_small = 0;
   cnt->mh_next = 0;
   cnt->mh_next_small = 0;
+  cnt->oct_deferred = 0;
 }
 
 __global__ void k_camera(IterParams ip, CameraParams cam, CamRay* q, DevCounters* cnt) {
@@ -974,7 +975,7 @@ static long long enqueue_pass23(neb_ctx* c, int iteration, cudaStream_t st2, Sta
   if (split) cudaMemsetAsync(c->split, 0, sizeof(double) * 12 * (size_t)c->P, st2);
   launch_oct_rearm(c->oct_nodes, c->oct_state, c->oct, st2);
   launch_oct_insert_nee(c, sl, st2);
-  launches += 2;
+  launches += c->cfg.octree_mode == 1 ? 2 : 3;
   tm.end();
   tm.begin(STAGE_DENSITY);
   launch_oct_density_nee(c, sl, st2);

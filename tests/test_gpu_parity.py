@@ -139,6 +139,32 @@ def test_octree_concurrent_conserves_counts(neb):
         assert a1 > a0
 
 
+def test_octree_concurrent_conserves_counts_when_the_pool_runs_out(neb):
+    """The pool runs out during the first launch: vertices that meet it count
+    in their leaves after the launch, when every split of the launch is
+    published, and still every insert is accounted for, in that launch and
+    in the next ones (the tree frozen from the start of the launch)."""
+    its = _octree_inputs(23, n_iter=3, n=40000)
+    split = 4
+    g = neb.Octree([0, 0, 0], [1, 1, 1], 2048, split)
+    for i, pts in enumerate(its, start=1):
+        g.set_iteration(i)
+        before, a0, _, _ = g.read()
+        g.insert(pts, mode=0)
+        after, a1, depth, status = g.read()
+        assert status & neb.STATUS_SPIN_TIMEOUT == 0 and status & neb.STATUS_OCTREE_FULL
+        T = split * i
+        total = 0
+        for idx in range(len(after)):
+            b, a = int(before[idx]), int(after[idx])
+            if b < 0:
+                continue           # split in an earlier launch
+            if idx >= a0 and a >= 0 and b == a:
+                continue           # a free word
+            total += (a - b) if a >= 0 else (T - b)
+        assert total == len(pts), (i, total)
+
+
 def test_octree_load_round_trip(neb):
     """A node array read back and loaded into a fresh octree (checkpoint and
     resume) gives the same densities and continues counting identically."""
