@@ -24,6 +24,7 @@
 
 #include <cfloat>
 
+#include "neb_accum.cuh"
 #include "neb_device.cuh"
 #include "neb_internal.h"
 

@@ -20,6 +20,7 @@
 #include <cfloat>
 #include <cstdio>
 
+#include "neb_accum.cuh"
 #include "neb_device.cuh"
 #include "neb_internal.h"
 #include "neb_octree.cuh"
