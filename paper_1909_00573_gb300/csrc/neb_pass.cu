@@ -202,12 +202,39 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
     bool shadow = false;
     float nee_p_lp = 0.0f;
     int hit_prim = -1;
+    // NEE light choice and the light's data: they depend only on the pixel
+    // and k, so these loads go out first and overlap those of the hit
+    const bool want_nee = k <= ip.D - 1 && s.nl > 0;
+    int lidx = 0, lprim = 0;
+    float u2 = 0.0f, u3 = 0.0f, l_pa = 0.0f;
+    float4 la0 = make_float4(0, 0, 0, 0), la1 = la0, la2 = la0;  // light triangle, or la0: light sphere
+    float3 l_emit = f3(0, 0, 0);
     if (valid) {
       ry = in[i];
       rays = 1;
       d = xyz(ry.d);
       pixel = __float_as_int(ry.o.w);
       flags = __float_as_int(ry.mis.w);
+      if (want_nee) {
+        uint4 rb = rng_block(ip.key, ip.iteration, pixel, 256u * k, 0);
+        lidx = (int)(((uint64_t)(rb.x >> 8) * (uint64_t)s.nl) >> 24);
+        if (!(u01(rb.y) < __ldg(s.alias_prob + lidx))) lidx = __ldg(s.alias_idx + lidx);
+        u2 = u01(rb.z);
+        u3 = u01(rb.w);
+        lprim = __ldg(s.light_prim + lidx);
+        l_pa = __ldg(s.light_psel + lidx) * __ldg(s.light_inv_area + lidx);
+        int lmat;
+        if (lprim < s.nt) {
+          la0 = __ldg(s.tv0 + lprim);
+          la1 = __ldg(s.tv1 + lprim);
+          la2 = __ldg(s.tv2 + lprim);
+          lmat = __float_as_int(la0.w);
+        } else {
+          la0 = __ldg(s.sph + (lprim - s.nt));
+          lmat = __ldg(&s.sph_mat[lprim - s.nt]);
+        }
+        l_emit = xyz(__ldg(s.mats + 3 * lmat + 1));
+      }
       RayPre r = make_ray(xyz(ry.o), d);
       int2 hh = hits[i];
       int prim = hh.x;
@@ -239,34 +266,31 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
         if (!mat_black(m)) {
           alive = k < ip.D;
           Cfac = (flags & RAY_FROM_CAMERA) ? 0.0f : ry.mis.x * ry.tau.w / (ry.d.w * cos_k);
-          if (k <= ip.D - 1 && s.nl > 0) {
+          if (want_nee) {
             store_nee = true;
             nee_new = 1;
-            uint4 rb = rng_block(ip.key, ip.iteration, pixel, 256u * k, 0);
-            int lidx = (int)(((uint64_t)(rb.x >> 8) * (uint64_t)s.nl) >> 24);
-            if (!(u01(rb.y) < __ldg(s.alias_prob + lidx))) lidx = __ldg(s.alias_idx + lidx);
-            float u2 = u01(rb.z), u3 = u01(rb.w);
-            int lprim = __ldg(s.light_prim + lidx);
             float3 y, ny;
+            float p_l;
             if (lprim < s.nt) {
               float b1 = u2, b2 = u3;
               if (b1 + b2 > 1.0f) { b1 = 1.0f - b1; b2 = 1.0f - b2; }
-              float3 a0 = xyz(__ldg(s.tv0 + lprim)), a1 = xyz(__ldg(s.tv1 + lprim)), a2 = xyz(__ldg(s.tv2 + lprim));
+              float3 a0 = xyz(la0), a1 = xyz(la1), a2 = xyz(la2);
               float3 e1 = sub(a1, a0), e2 = sub(a2, a0);
               y = add(add(a0, mul(e1, b1)), mul(e2, b2));
               ny = normalize(cross(e1, e2));
+              p_l = l_pa;
             } else {
-              float4 sp = __ldg(s.sph + (lprim - s.nt));
-              float3 ce = xyz(sp);
+              float3 ce = xyz(la0);
               float3 w = normalize(sub(p, ce));
               float z = u2;
               float rr = sqrtf(fmaxf(0.0f, 1.0f - z * z));
               float phi = kTwoPi * u3;
               float3 dir = from_local(w, rr * cosf(phi), rr * sinf(phi), z);
-              y = add(ce, mul(dir, sp.w));
+              y = add(ce, mul(dir, la0.w));
               ny = dir;
+              // the sampled hemisphere faces x: the pdf of light_pdf
+              p_l = dot(sub(y, ce), sub(p, ce)) > 0.0f ? l_pa : 0.0f;
             }
-            float p_l = light_pdf(s, lidx, y, p);
             float3 dd = sub(y, p);
             float dist2 = dot(dd, dd);
             float dist = sqrtf(dist2);
@@ -276,11 +300,10 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
             if (cos_y > 0.0f && p_l > 0.0f) {
               float cos_x = fabsf(dot(n, ldir));
               float g = cos_x * cos_y / (dist2 * p_l);
-              Mat lm = load_mat(s.mats, prim_mat(s, lprim));
-              dE = mul(lm.emission, g);
+              dE = mul(l_emit, g);
               g_y = cos_y / (dist2 * p_l);
               shadow = true;
-              nee_p_lp = lp_light_pdf(s, lidx);
+              nee_p_lp = lprim < s.nt ? l_pa : 0.5f * l_pa;  // the light-photon pdf of lp_light_pdf
             }
           }
         }
