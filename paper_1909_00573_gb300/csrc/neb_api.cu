@@ -97,8 +97,10 @@ static Capacities capacities(const neb_config* cfg) {
   k.cap_nee = k.P * (D > 1 ? D - 1 : 1);
   k.cap_rh = k.P * D;
   k.cap_ph = k.cap_nee;
+  // buckets of the view-vertex grid: one per NEE vertex, at most 2^22 (16 MB of
+  // counts and 16 MB of starts stay in L2; more vertices share buckets)
   k.table = 1024;
-  while (k.table < (uint32_t)k.cap_nee) k.table <<= 1;
+  while (k.table < (uint32_t)k.cap_nee && k.table < (1u << 22)) k.table <<= 1;
   // staged photon hits of the per-cell merge (none when every hit merges on
   // its own); the photon table has a bucket per four staged hits
   const size_t mh = cfg->merge_hits > 0 ? (size_t)cfg->merge_hits : 2 * k.cap_ph;
