@@ -127,6 +127,7 @@ extern "C" int neb_job_device_bytes(const neb_config* cfg, int n_tri, int n_sph,
   b += scan_scratch_ints((size_t)k.table + 1) * sizeof(int) + k.P * 3 * (2 * sizeof(double) + sizeof(float));
   b += cfg->keep_split ? k.P * 12 * sizeof(double) : 0;
   b += 2 * k.cap_nee * (sizeof(ShadowRay) + sizeof(int)) + group_counter_ints() * sizeof(int);
+  b += cfg->photon_records == 0 ? k.cap_ph * sizeof(PhotonRay) + group_counter_ints() * sizeof(int) : 0;
   b += k.cap_mh * (sizeof(MergeHit) + sizeof(int) + sizeof(int2)) +
        (k.cap_mh ? 2 * ((size_t)k.ptable + 1) * sizeof(int) : 0);
   const size_t nt = (size_t)n_tri, ns = (size_t)n_sph, nl = (size_t)n_lights, np = nt + ns;
@@ -196,6 +197,9 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
   ok = ok && dalloc(&c->shadow_rays, c->cap_nee) == cudaSuccess && dalloc(&c->shadow_start, c->cap_nee) == cudaSuccess &&
        dalloc(&c->shadow_rays_b, c->cap_nee) == cudaSuccess && dalloc(&c->shadow_start_b, c->cap_nee) == cudaSuccess &&
        dalloc(&c->group_counters, group_counter_ints()) == cudaSuccess;
+  if (ok && cfg->photon_records == 0)
+    ok = dalloc(&c->phq_grouped, (size_t)c->cap_ph) == cudaSuccess &&
+         dalloc(&c->ph_group_counters, group_counter_ints()) == cudaSuccess;
   if (ok && c->cap_mh > 0)
     ok = dalloc(&c->mh, (size_t)c->cap_mh) == cudaSuccess && dalloc(&c->mh_sorted, (size_t)c->cap_mh) == cudaSuccess &&
          dalloc(&c->mh_tile, (size_t)c->cap_mh) == cudaSuccess &&
@@ -217,6 +221,7 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
   }
   cudaMemsetAsync(c->bucket_count, 0, sizeof(int) * ((size_t)t + 1), c->stream);
   if (c->pb_count) cudaMemsetAsync(c->pb_count, 0, sizeof(int) * ((size_t)c->ptable_size + 1), c->stream);
+  if (c->ph_group_counters) cudaMemsetAsync(c->ph_group_counters, 0, sizeof(int) * group_counter_ints(), c->stream);
   cudaMemsetAsync(c->accum, 0, sizeof(double) * P * 6, c->stream);
   cudaMemsetAsync(c->counters, 0, 2 * sizeof(DevCounters), c->stream);
   cudaMemsetAsync(c->group_counters, 0, sizeof(int) * group_counter_ints(), c->stream);
@@ -247,6 +252,7 @@ extern "C" void neb_destroy(neb_ctx* c) {
   if (c->ev_frame) cudaEventDestroy(c->ev_frame);
   cudaFree(c->shadow_rays); cudaFree(c->shadow_start); cudaFree(c->shadow_rays_b); cudaFree(c->shadow_start_b);
   cudaFree(c->group_counters);
+  cudaFree(c->phq_grouped); cudaFree(c->ph_group_counters);
   cudaFree(c->mh); cudaFree(c->mh_sorted); cudaFree(c->mh_tile); cudaFree(c->pb_count); cudaFree(c->pb_start);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);

@@ -188,6 +188,8 @@ struct neb_ctx {
   // per-iteration buffers
   neb::CamRay* camq[2] = {nullptr, nullptr};
   neb::CamRay* camq_grouped = nullptr;  // bounce rays regrouped before tracing
+  neb::PhotonRay* phq_grouped = nullptr;  // photon rays regrouped before tracing (FP32 records only)
+  int* ph_group_counters = nullptr;       // their grouping counters (passes 2-3 run beside pass 1's grouping)
   neb::IterSlot slots[2];
   neb::PhotonRay* phq[2] = {nullptr, nullptr};
   int2* hits = nullptr;     // closest hits of the camera ray queue (pass 1)
@@ -317,6 +319,9 @@ cudaError_t launch_trace_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st)
 int shadow_walk_launches(const neb_ctx* c);  // kernels launch_trace_shadow enqueues
 // regroups the camera queue q (count at count_ptr) into out (same count)
 cudaError_t launch_group_camera(neb_ctx* c, const CamRay* q, const int* count_ptr, CamRay* out, cudaStream_t st);
+// the same for a queue of FP32 photon records, with the photon grouping counters
+cudaError_t launch_group_photons(neb_ctx* c, const PhotonRay* q, const int* count_ptr, PhotonRay* out,
+                                 cudaStream_t st);
 
 // neb_pass.cu
 // overlap: passes 2-3 go to stream_b (ordered by the slot events), else all on c->stream

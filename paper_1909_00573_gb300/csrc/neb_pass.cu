@@ -1032,12 +1032,22 @@ static long long enqueue_pass23(neb_ctx* c, int iteration, cudaStream_t st2, Sta
     for (int j = 1; j <= photon_launches; ++j) {
       int in = (j - 1) & 1, out = j & 1;
       k_reset_photon_slot<<<1, 1, 0, st2>>>(cnt, out);
+      const void* qin = c->phq[in];
+      if (c->phq_grouped) {
+        // photon rays regrouped by origin and direction cell, as the camera
+        // bounce rays are, so a warp's rays walk the same nodes
+        tm.begin(STAGE_GROUP);
+        launch_group_photons(c, static_cast<const PhotonRay*>(c->phq[in]), &cnt->ph_count[in], c->phq_grouped, st2);
+        launches += 3;
+        tm.end();
+        qin = c->phq_grouped;
+      }
       tm.begin(STAGE_TRACE_PHOTON);
-      launch_trace_closest(c, reinterpret_cast<const float4*>(c->phq[in]), &cnt->ph_count[in], c->cap_ph,
+      launch_trace_closest(c, reinterpret_cast<const float4*>(qin), &cnt->ph_count[in], c->cap_ph,
                            c->hits_ph, 2, cnt, st2, c->cfg.photon_records);
       tm.end();
       tm.begin(STAGE_PHOTON);
-      k_photon<<<capped_blocks(c->cap_ph, kThreads, B), kThreads, 0, st2>>>(s, ip, j, c->phq[in], in, c->phq[out], out, c->cfg.photon_records, sl.nv, c->mrec, c->bucket_start, cnt,
+      k_photon<<<capped_blocks(c->cap_ph, kThreads, B), kThreads, 0, st2>>>(s, ip, j, qin, in, c->phq[out], out, c->cfg.photon_records, sl.nv, c->mrec, c->bucket_start, cnt,
                                         accum, split, c->hits_ph, c->oct_nodes, c->oct_state, c->oct,
                                         c->cfg.density_mode == 0, c->mh);
       launches += 3;

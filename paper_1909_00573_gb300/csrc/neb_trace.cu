@@ -512,6 +512,23 @@ cudaError_t launch_group_camera(neb_ctx* c, const CamRay* q, const int* count_pt
   return cudaGetLastError();
 }
 
+// Photon records share the camera records' layout in their first two float4
+// (origin, direction), which is all the grouping reads; it moves whole
+// 64-byte records.
+static_assert(sizeof(PhotonRay) == sizeof(CamRay), "photon and camera records are both 64 bytes");
+cudaError_t launch_group_photons(neb_ctx* c, const PhotonRay* q, const int* count_ptr, PhotonRay* out,
+                                 cudaStream_t st) {
+  GroupSpec g = {scene_grid(c), c->tune.cam_origin_bits, c->tune.cam_dir_bits};
+  int* counts = c->ph_group_counters;
+  int* cursors = c->ph_group_counters + kGroups;
+  const CamRay* qc = reinterpret_cast<const CamRay*>(q);
+  CamRay* oc = reinterpret_cast<CamRay*>(out);
+  k_cam_group_count<<<group_blocks(c->cap_ph), kGroupThreads, 0, st>>>(qc, count_ptr, c->cap_ph, g, counts);
+  k_group_scan<<<1, kScanThreads, 0, st>>>(counts, cursors, nullptr);
+  k_cam_group_scatter<<<group_blocks(c->cap_ph), kGroupThreads, 0, st>>>(qc, count_ptr, c->cap_ph, g, cursors, oc);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_group_shadow(neb_ctx* c, const IterSlot& sl, cudaStream_t st) {
   GroupSpec g = {scene_grid(c), c->tune.shadow_origin_bits, c->tune.shadow_light_bits};
   int* counts = c->group_counters;
