@@ -25,4 +25,16 @@ __device__ __forceinline__ void add_pixel(double* accum, double* split, int whic
   }
 }
 
+// Occupancy of the merge grid's cells: one bit per value of a second hash of
+// the cell (independent of the bucket hash), set for every cell that holds a
+// mergeable view vertex.  A search skips a cell whose bit is clear: no vertex
+// lies in it, whatever other cells share its bucket.
+__device__ __forceinline__ uint32_t cell_bit_index(int x, int y, int z, uint32_t mask) {
+  return (((uint32_t)x * 0x9E3779B1u) ^ ((uint32_t)y * 0x85EBCA77u) ^ ((uint32_t)z * 0xC2B2AE3Du)) & mask;
+}
+__device__ __forceinline__ bool cell_occupied(const uint32_t* __restrict__ bits, uint32_t mask, int x, int y, int z) {
+  const uint32_t h = cell_bit_index(x, y, z, mask);
+  return (__ldg(bits + (h >> 5)) >> (h & 31u)) & 1u;
+}
+
 }  // namespace neb

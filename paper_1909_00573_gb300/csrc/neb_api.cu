@@ -123,7 +123,8 @@ extern "C" int neb_job_device_bytes(const neb_config* cfg, int n_tri, int n_sph,
   b += 2 * (7 * k.cap_nee * sizeof(float4) + 2 * k.cap_nee * sizeof(int) + k.cap_rh * sizeof(RHEvent) +
             (cfg->octree_mode == 1 ? nee_rows * sizeof(int) : 0));
   b += 2 * k.cap_ph * sizeof(PhotonRay) + k.cap_cam * sizeof(int2) + k.cap_ph * sizeof(int2);
-  b += k.cap_nee * (sizeof(MergeRec) + sizeof(int)) + 2 * ((size_t)k.table + 1) * sizeof(int);
+  b += k.cap_nee * (sizeof(MergeRec) + sizeof(int)) + 2 * ((size_t)k.table + 1) * sizeof(int) +
+       (size_t)k.table * sizeof(uint32_t);
   b += scan_scratch_ints((size_t)k.table + 1) * sizeof(int) + k.P * 3 * (2 * sizeof(double) + sizeof(float));
   b += cfg->keep_split ? k.P * 12 * sizeof(double) : 0;
   b += 2 * k.cap_nee * (sizeof(ShadowRay) + sizeof(int)) + group_counter_ints() * sizeof(int);
@@ -190,7 +191,7 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
        dalloc(&c->hits, (size_t)c->cap_cam) == cudaSuccess && dalloc(&c->hits_ph, (size_t)c->cap_ph) == cudaSuccess &&
        dalloc(&c->mrec, c->cap_nee) == cudaSuccess && dalloc(&c->vert_bucket, c->cap_nee) == cudaSuccess &&
        dalloc(&c->bucket_count, (size_t)t + 1) == cudaSuccess &&
-       dalloc(&c->bucket_start, (size_t)t + 1) == cudaSuccess &&
+       dalloc(&c->bucket_start, (size_t)t + 1) == cudaSuccess && dalloc(&c->cell_bits, (size_t)t) == cudaSuccess &&
        dalloc(&c->scan_scratch.data, c->scan_scratch.n) == cudaSuccess && dalloc(&c->accum, P * 6) == cudaSuccess &&
        dalloc(&c->frame, P * 3) == cudaSuccess &&
        (!cfg->keep_split || dalloc(&c->split, P * 12) == cudaSuccess);
@@ -247,7 +248,7 @@ extern "C" void neb_destroy(neb_ctx* c) {
     cudaFree(sl.nv.ldir); cudaFree(sl.nv.dE); cudaFree(sl.nv.lit); cudaFree(sl.nv.prim); cudaFree(sl.rh); cudaFree(sl.slot_map);
   }
   cudaFree(c->phq[0]); cudaFree(c->phq[1]); cudaFree(c->hits); cudaFree(c->hits_ph); cudaFree(c->mrec);
-  cudaFree(c->vert_bucket); cudaFree(c->bucket_count); cudaFree(c->bucket_start); cudaFree(c->scan_scratch.data);
+  cudaFree(c->vert_bucket); cudaFree(c->bucket_count); cudaFree(c->bucket_start); cudaFree(c->cell_bits); cudaFree(c->scan_scratch.data);
   cudaFree(c->accum); cudaFree(c->frame); cudaFree(c->split); cudaFree(c->counters);
   if (c->ev_frame) cudaEventDestroy(c->ev_frame);
   cudaFree(c->shadow_rays); cudaFree(c->shadow_start); cudaFree(c->shadow_rays_b); cudaFree(c->shadow_start_b);

@@ -4,6 +4,7 @@
 // buckets so that a photon's r-ball touches at most 8 cells.
 #include <cuda_runtime.h>
 
+#include "neb_accum.cuh"
 #include "neb_device.cuh"
 #include "neb_internal.h"
 
@@ -104,14 +105,21 @@ __device__ __forceinline__ uint32_t point_bucket(float3 p, float3 gmin, float ce
 }
 
 __global__ void k_grid_count(NeeStore nv, DevCounters* cnt, int cap, float3 gmin, float cell_inv, uint32_t mask,
-                             int* __restrict__ bucket_count, int* __restrict__ vert_bucket) {
+                             int* __restrict__ bucket_count, int* __restrict__ vert_bucket, uint32_t* cell_bits,
+                             uint32_t bits_mask) {
   int count = min(cnt->nee_count, cap);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
     int bits = __float_as_int(nv.nrm[i].w);
     int b = -1;
     if ((bits >> NV_FLAG_SHIFT) & NV_MERGEABLE) {
-      b = (int)point_bucket(xyz(nv.pos[i]), gmin, cell_inv, mask);
+      const float3 p = xyz(nv.pos[i]);
+      const int cx = grid_cell_index((p.x - gmin.x) * cell_inv), cy = grid_cell_index((p.y - gmin.y) * cell_inv),
+                cz = grid_cell_index((p.z - gmin.z) * cell_inv);
+      b = (int)grid_hash(cx, cy, cz, mask);
       atomicAdd(bucket_count + b, 1);
+      const uint32_t h = cell_bit_index(cx, cy, cz, bits_mask);
+      const uint32_t bit = 1u << (h & 31u);
+      if (!(cell_bits[h >> 5] & bit)) atomicOr(cell_bits + (h >> 5), bit);
     }
     vert_bucket[i] = b;
   }
@@ -133,8 +141,9 @@ __global__ void k_grid_scatter(NeeStore nv, DevCounters* cnt, int cap, const int
 
 cudaError_t grid_build(neb_ctx* c, const IterParams& ip, const IterSlot& sl, cudaStream_t st) {
   const int B = capped_blocks(c->cap_nee, 256, 152 * 8);
+  cudaMemsetAsync(c->cell_bits, 0, sizeof(uint32_t) * (size_t)c->table_size, st);
   k_grid_count<<<B, 256, 0, st>>>(sl.nv, sl.cnt, c->cap_nee, ip.gmin, ip.cell_inv, ip.table_mask, c->bucket_count,
-                                  c->vert_bucket);
+                                  c->vert_bucket, c->cell_bits, ip.cell_bits_mask);
   cudaError_t e = scan_exclusive(c->bucket_count, c->bucket_start, (size_t)c->table_size + 1, c->scan_scratch, st);
   if (e != cudaSuccess) return e;
   k_grid_scatter<<<B, 256, 0, st>>>(sl.nv, sl.cnt, c->cap_nee, c->vert_bucket, c->bucket_start, c->bucket_count,

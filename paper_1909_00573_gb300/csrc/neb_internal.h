@@ -139,6 +139,8 @@ struct IterParams {
   float3 gmin;          // hashed grid origin
   float cell_inv;       // 1 / (2 r)
   uint32_t table_mask;  // hash table size - 1
+  const uint32_t* cell_bits;  // occupancy bits of the grid's cells
+  uint32_t cell_bits_mask;    // number of bits - 1
   int cap_mh;           // staged photon hits per iteration (0: every hit merges on its own)
   int stage_min;        // a hit is staged when more view vertices than this lie in its cells
 };
@@ -204,6 +206,7 @@ struct neb_ctx {
   int* vert_bucket = nullptr;
   int* bucket_count = nullptr;
   int* bucket_start = nullptr;
+  uint32_t* cell_bits = nullptr;  // occupancy bits of the grid's cells, 32 per bucket
   int cap_cam = 0, cap_nee = 0, cap_rh = 0, cap_ph = 0;
   uint32_t table_size = 0;
   // per-cell merge: staged photon hits, their order by bucket of the photon

@@ -301,14 +301,17 @@ __device__ __forceinline__ void merge_group(const MergeArgs& a, const IterParams
     }
   }
   const int ncell = nc[0] * nc[1] * nc[2];
-  uint32_t b = 0x80000000u | (uint32_t)lane;  // distinct dummies for lanes without a cell
+  // lanes without an occupied cell hold distinct dummies
+  uint32_t b = 0x80000000u | (uint32_t)lane;
+  bool occ = false;
   if (lane < ncell) {
     const int ix = lane % nc[0], iy = (lane / nc[0]) % nc[1], iz = lane / (nc[0] * nc[1]);
-    b = grid_hash(c0[0] + ix, c0[1] + iy, c0[2] + iz, ip.table_mask);
+    occ = cell_occupied(ip.cell_bits, ip.cell_bits_mask, c0[0] + ix, c0[1] + iy, c0[2] + iz);
+    if (occ) b = grid_hash(c0[0] + ix, c0[1] + iy, c0[2] + iz, ip.table_mask);
   }
   // a bucket reached from two cells is walked once
   const unsigned same = __match_any_sync(kFull, b);
-  const bool own = lane < ncell && __ffs(same) - 1 == lane;
+  const bool own = occ && __ffs(same) - 1 == lane;
   int start = 0, len = 0;
   if (own) {
     start = __ldg(a.bucket_start + b);

@@ -699,18 +699,25 @@ __global__ void __launch_bounds__(kThreads) k_photon(SceneView s, IterParams ip,
       int ox = (gx - (float)cx >= 0.5f) ? 1 : -1, oy = (gy - (float)cy >= 0.5f) ? 1 : -1,
           oz = (gz - (float)cz >= 0.5f) ? 1 : -1;
       uint32_t bk[8];
+      bool occ[8];  // the cell holds a mergeable vertex (its occupancy bit)
 #pragma unroll
-      for (int c = 0; c < 8; ++c)
-        bk[c] = grid_hash(cx + ((c & 1) ? ox : 0), cy + ((c & 2) ? oy : 0), cz + ((c & 4) ? oz : 0),
-                          ip.table_mask);
+      for (int c = 0; c < 8; ++c) {
+        const int x = cx + ((c & 1) ? ox : 0), y = cy + ((c & 2) ? oy : 0), z = cz + ((c & 4) ? oz : 0);
+        bk[c] = grid_hash(x, y, z, ip.table_mask);
+        occ[c] = cell_occupied(ip.cell_bits, ip.cell_bits_mask, x, y, z);
+      }
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         bool dup = false;
 #pragma unroll
-        for (int c2 = 0; c2 < c; ++c2) dup |= bk[c2] == bk[c];
-        int b0 = __ldg(bucket_start + bk[c]), b1 = __ldg(bucket_start + bk[c] + 1);
+        for (int c2 = 0; c2 < c; ++c2) dup |= occ[c2] && bk[c2] == bk[c];
+        int b0 = 0, b1 = 0;
+        if (occ[c] && !dup) {
+          b0 = __ldg(bucket_start + bk[c]);
+          b1 = __ldg(bucket_start + bk[c] + 1);
+        }
         cb[c] = b0;
-        cl[c] = dup ? 0 : b1 - b0;
+        cl[c] = b1 - b0;
         nl += cl[c];
       }
     } else {
@@ -923,6 +930,8 @@ IterParams iter_params(const neb_ctx* c, int iteration) {
   ip.gmin = f3(c->bmin[0] - cs, c->bmin[1] - cs, c->bmin[2] - cs);
   ip.cell_inv = 1.0f / cs;
   ip.table_mask = c->table_size - 1;
+  ip.cell_bits = c->cell_bits;
+  ip.cell_bits_mask = 32u * c->table_size - 1u;
   ip.cap_mh = c->cap_mh;
   ip.stage_min = c->cfg.merge_mode == 2 ? -1 : kStageCandidates;
   return ip;
