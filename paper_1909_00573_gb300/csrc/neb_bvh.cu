@@ -372,20 +372,36 @@ __global__ void k_ploc_tail(const int* mrank, const int* mflag, const int* kpos,
   out[1] = kpos[count - 1] + kflag[count - 1];
 }
 
+// A build's temporaries are stream-ordered allocations on its stream (no
+// device-wide synchronisation on free), and its per-round readbacks go to one
+// pinned word pair per host thread, allocated once.
+template <typename T>
+static bool talloc(T** p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  return cudaMallocAsync(reinterpret_cast<void**>(p), bytes, st) == cudaSuccess;
+}
+template <typename T>
+static void tfree(T* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+static int* readback_words() {
+  thread_local int* h = nullptr;
+  if (!h && cudaMallocHost(&h, 2 * sizeof(int)) != cudaSuccess) h = nullptr;
+  return h;
+}
+
 static cudaError_t ploc_build(const SceneView& s, int n, const int* sorted_prim, BVHNode* nodes, Scratch& sc,
                               cudaStream_t st) {
   int *cid[2] = {nullptr, nullptr}, *nn = nullptr, *mflag = nullptr, *kflag = nullptr, *mrank = nullptr,
       *kpos = nullptr, *tail = nullptr;
   float4 *blo[2] = {nullptr, nullptr}, *bhi[2] = {nullptr, nullptr};
   cudaError_t e = cudaSuccess;
-  bool ok = cudaMalloc(&cid[0], 4ull * n) == cudaSuccess && cudaMalloc(&cid[1], 4ull * n) == cudaSuccess &&
-            cudaMalloc(&blo[0], 16ull * n) == cudaSuccess && cudaMalloc(&blo[1], 16ull * n) == cudaSuccess &&
-            cudaMalloc(&bhi[0], 16ull * n) == cudaSuccess && cudaMalloc(&bhi[1], 16ull * n) == cudaSuccess &&
-            cudaMalloc(&nn, 4ull * n) == cudaSuccess && cudaMalloc(&mflag, 4ull * n) == cudaSuccess &&
-            cudaMalloc(&kflag, 4ull * n) == cudaSuccess && cudaMalloc(&mrank, 4ull * n) == cudaSuccess &&
-            cudaMalloc(&kpos, 4ull * n) == cudaSuccess && cudaMalloc(&tail, 16) == cudaSuccess;
-  int* h = nullptr;  // pinned: the per-round readback is one small asynchronous copy
-  ok = ok && cudaMallocHost(&h, 2 * sizeof(int)) == cudaSuccess;
+  bool ok = talloc(&cid[0], 4ull * n, st) && talloc(&cid[1], 4ull * n, st) && talloc(&blo[0], 16ull * n, st) &&
+            talloc(&blo[1], 16ull * n, st) && talloc(&bhi[0], 16ull * n, st) && talloc(&bhi[1], 16ull * n, st) &&
+            talloc(&nn, 4ull * n, st) && talloc(&mflag, 4ull * n, st) && talloc(&kflag, 4ull * n, st) &&
+            talloc(&mrank, 4ull * n, st) && talloc(&kpos, 4ull * n, st) && talloc(&tail, 16, st);
+  int* h = readback_words();  // pinned: the per-round readback is one small asynchronous copy
+  ok = ok && h;
   if (!ok) e = cudaErrorMemoryAllocation;
   if (ok) {
     int gb = (n + 255) / 256;
@@ -415,9 +431,8 @@ static cudaError_t ploc_build(const SceneView& s, int n, const int* sorted_prim,
     }
     if (e == cudaSuccess && base != -1) e = cudaErrorUnknown;
   }
-  cudaFree(cid[0]); cudaFree(cid[1]); cudaFree(blo[0]); cudaFree(blo[1]); cudaFree(bhi[0]); cudaFree(bhi[1]);
-  cudaFree(nn); cudaFree(mflag); cudaFree(kflag); cudaFree(mrank); cudaFree(kpos); cudaFree(tail);
-  cudaFreeHost(h);
+  tfree(cid[0], st); tfree(cid[1], st); tfree(blo[0], st); tfree(blo[1], st); tfree(bhi[0], st); tfree(bhi[1], st);
+  tfree(nn, st); tfree(mflag, st); tfree(kflag, st); tfree(mrank, st); tfree(kpos, st); tfree(tail, st);
   return e;
 }
 
@@ -504,9 +519,8 @@ static cudaError_t collapse4(const BVHNode* bin, int n_bin, BVH4Node* out, cudaS
   int2 *w0 = nullptr, *w1 = nullptr;
   int* cnt = nullptr;
   cudaError_t e = cudaSuccess;
-  if (cudaMalloc(&w0, 8ull * (n_bin + 1)) != cudaSuccess || cudaMalloc(&w1, 8ull * (n_bin + 1)) != cudaSuccess ||
-      cudaMalloc(&cnt, 8) != cudaSuccess) {
-    cudaFree(w0); cudaFree(w1); cudaFree(cnt);
+  if (!talloc(&w0, 8ull * (n_bin + 1), st) || !talloc(&w1, 8ull * (n_bin + 1), st) || !talloc(&cnt, 8, st)) {
+    tfree(w0, st); tfree(w1, st); tfree(cnt, st);
     return cudaErrorMemoryAllocation;
   }
   int2 root = make_int2(0, 0);
@@ -514,9 +528,9 @@ static cudaError_t collapse4(const BVHNode* bin, int n_bin, BVH4Node* out, cudaS
   cudaMemcpyAsync(w0, &root, 8, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(cnt, init, 8, cudaMemcpyHostToDevice, st);
   int n_work = 1;
-  int* h = nullptr;  // pinned: one small asynchronous readback per level
-  if (cudaMallocHost(&h, 2 * sizeof(int)) != cudaSuccess) {
-    cudaFree(w0); cudaFree(w1); cudaFree(cnt);
+  int* h = readback_words();  // pinned: one small asynchronous readback per level
+  if (!h) {
+    tfree(w0, st); tfree(w1, st); tfree(cnt, st);
     return cudaErrorMemoryAllocation;
   }
   h[0] = 1;
@@ -533,8 +547,7 @@ static cudaError_t collapse4(const BVHNode* bin, int n_bin, BVH4Node* out, cudaS
     int2* t = w0; w0 = w1; w1 = t;
   }
   *n_out = h[0];
-  cudaFree(w0); cudaFree(w1); cudaFree(cnt);
-  cudaFreeHost(h);
+  tfree(w0, st); tfree(w1, st); tfree(cnt, st);
   return e;
 }
 
@@ -641,8 +654,7 @@ cudaError_t build_bvh4(const SceneView& s, int n, int builder, cudaStream_t st, 
   }
   // the binary tree (LBVH or PLOC) is built first and collapsed into the 4-wide one
   BVHNode* bin = nullptr;
-  e = cudaMalloc(&bin, sizeof(BVHNode) * (size_t)(n - 1));
-  if (e != cudaSuccess) return e;
+  if (!talloc(&bin, sizeof(BVHNode) * (size_t)(n - 1), st)) return cudaErrorMemoryAllocation;
   int nblocks = (n + kSortThreads - 1) / kSortThreads;
   size_t hist_n = (size_t)16 * nblocks;
   uint32_t *k0 = nullptr, *k1 = nullptr, *khi = nullptr;
@@ -652,15 +664,11 @@ cudaError_t build_bvh4(const SceneView& s, int n, int builder, cudaStream_t st, 
   Box6* boxes = nullptr;
   Scratch sc;
   sc.n = scan_scratch_ints(hist_n);
-  bool ok = cudaMalloc(&k0, 4ull * n) == cudaSuccess && cudaMalloc(&k1, 4ull * n) == cudaSuccess &&
-            cudaMalloc(&khi, 4ull * n) == cudaSuccess &&
-            cudaMalloc(&v0, 4ull * n) == cudaSuccess && cudaMalloc(&v1, 4ull * n) == cudaSuccess &&
-            cudaMalloc(&hist, 4ull * hist_n) == cudaSuccess && cudaMalloc(&offs, 4ull * hist_n) == cudaSuccess &&
-            cudaMalloc(&cb, 4ull * 6) == cudaSuccess && cudaMalloc(&child, 8ull * (n - 1)) == cudaSuccess &&
-            cudaMalloc(&pint, 4ull * (n - 1)) == cudaSuccess && cudaMalloc(&pleaf, 4ull * n) == cudaSuccess &&
-            cudaMalloc(&flags, 4ull * (n - 1)) == cudaSuccess &&
-            cudaMalloc(&boxes, sizeof(Box6) * (size_t)(n - 1)) == cudaSuccess &&
-            cudaMalloc(&sc.data, 4ull * sc.n) == cudaSuccess;
+  bool ok = talloc(&k0, 4ull * n, st) && talloc(&k1, 4ull * n, st) && talloc(&khi, 4ull * n, st) &&
+            talloc(&v0, 4ull * n, st) && talloc(&v1, 4ull * n, st) && talloc(&hist, 4ull * hist_n, st) &&
+            talloc(&offs, 4ull * hist_n, st) && talloc(&cb, 4ull * 6, st) && talloc(&child, 8ull * (n - 1), st) &&
+            talloc(&pint, 4ull * (n - 1), st) && talloc(&pleaf, 4ull * n, st) && talloc(&flags, 4ull * (n - 1), st) &&
+            talloc(&boxes, sizeof(Box6) * (size_t)(n - 1), st) && talloc(&sc.data, 4ull * sc.n, st);
   if (ok) {
     int init[6] = {0x7fffffff, 0x7fffffff, 0x7fffffff, (int)0x80000000, (int)0x80000000, (int)0x80000000};
     cudaMemcpyAsync(cb, init, sizeof(init), cudaMemcpyHostToDevice, st);
@@ -690,9 +698,9 @@ cudaError_t build_bvh4(const SceneView& s, int n, int builder, cudaStream_t st, 
     } else {
       Scratch sc2;
       sc2.n = scan_scratch_ints(n);
-      e = cudaMalloc(&sc2.data, 4ull * sc2.n);
+      e = talloc(&sc2.data, 4ull * sc2.n, st) ? cudaSuccess : cudaErrorMemoryAllocation;
       if (e == cudaSuccess) e = ploc_build(s, n, v0, bin, sc2, st);
-      cudaFree(sc2.data);
+      tfree(sc2.data, st);
     }
     if (e == cudaSuccess) e = cudaGetLastError();
     int n4 = 0;
@@ -701,10 +709,11 @@ cudaError_t build_bvh4(const SceneView& s, int n, int builder, cudaStream_t st, 
   } else {
     e = cudaErrorMemoryAllocation;
   }
-  cudaFree(k0); cudaFree(k1); cudaFree(khi); cudaFree(v0); cudaFree(v1); cudaFree(hist); cudaFree(offs); cudaFree(cb);
-  cudaFree(child); cudaFree(pint); cudaFree(pleaf); cudaFree(flags); cudaFree(boxes); cudaFree(sc.data);
+  tfree(k0, st); tfree(k1, st); tfree(khi, st); tfree(v0, st); tfree(v1, st); tfree(hist, st); tfree(offs, st);
+  tfree(cb, st); tfree(child, st); tfree(pint, st); tfree(pleaf, st); tfree(flags, st); tfree(boxes, st);
+  tfree(sc.data, st);
+  tfree(bin, st);
   cudaStreamSynchronize(st);
-  cudaFree(bin);
   return e;
 }
 
