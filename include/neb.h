@@ -190,6 +190,9 @@ typedef struct {
   int cam_origin_bits, cam_dir_bits;         /* each in [0, 4] */
   int shadow_origin_bits, shadow_light_bits; /* each in [0, 4] */
   int shade_blocks_per_sm;                   /* [1, 32] */
+  int photon_grouping;                       /* 0 or 1: regroup photon rays before each photon walk (only
+                                                where the context holds a queue for it: FP32 photon
+                                                records and a photon queue of at least 2^20 rays) */
 } neb_tuning;
 int neb_get_tuning(const neb_ctx* ctx, neb_tuning* out);
 /* NEB_ERR_ARG for values out of range; applies from the next iteration. */

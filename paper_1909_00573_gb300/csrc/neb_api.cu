@@ -84,6 +84,10 @@ static bool config_ok(const neb_config* cfg) {
          (long long)cfg->width * cfg->height <= (1ll << 28);
 }
 
+static bool photon_grouping(const neb_config* cfg, size_t cap_ph) {
+  return cfg->photon_records == 0 && cap_ph >= ((size_t)1 << 20);
+}
+
 // Queue capacities and hash-table size of a configuration (neb_create).
 struct Capacities {
   size_t P, cap_cam, cap_nee, cap_rh, cap_ph, cap_mh;
@@ -128,7 +132,7 @@ extern "C" int neb_job_device_bytes(const neb_config* cfg, int n_tri, int n_sph,
   b += scan_scratch_ints((size_t)k.table + 1) * sizeof(int) + k.P * 3 * (2 * sizeof(double) + sizeof(float));
   b += cfg->keep_split ? k.P * 12 * sizeof(double) : 0;
   b += 2 * k.cap_nee * (sizeof(ShadowRay) + sizeof(int)) + group_counter_ints() * sizeof(int);
-  b += cfg->photon_records == 0 ? k.cap_ph * sizeof(PhotonRay) + group_counter_ints() * sizeof(int) : 0;
+  b += photon_grouping(cfg, k.cap_ph) ? k.cap_ph * sizeof(PhotonRay) + group_counter_ints() * sizeof(int) : 0;
   b += k.cap_mh * (sizeof(MergeHit) + sizeof(int) + sizeof(int2)) +
        (k.cap_mh ? 2 * ((size_t)k.ptable + 1) * sizeof(int) : 0);
   const size_t nt = (size_t)n_tri, ns = (size_t)n_sph, nl = (size_t)n_lights, np = nt + ns;
@@ -198,7 +202,10 @@ extern "C" int neb_create(const neb_config* cfg, void* cuda_stream, neb_ctx** ou
   ok = ok && dalloc(&c->shadow_rays, c->cap_nee) == cudaSuccess && dalloc(&c->shadow_start, c->cap_nee) == cudaSuccess &&
        dalloc(&c->shadow_rays_b, c->cap_nee) == cudaSuccess && dalloc(&c->shadow_start_b, c->cap_nee) == cudaSuccess &&
        dalloc(&c->group_counters, group_counter_ints()) == cudaSuccess;
-  if (ok && cfg->photon_records == 0)
+  // photon rays are regrouped before each walk when the queue can be large
+  // (for small jobs the three extra launches per bounce cost more than the
+  // walk gains); FP32 records only
+  if (ok && photon_grouping(cfg, (size_t)c->cap_ph))
     ok = dalloc(&c->phq_grouped, (size_t)c->cap_ph) == cudaSuccess &&
          dalloc(&c->ph_group_counters, group_counter_ints()) == cudaSuccess;
   if (ok && c->cap_mh > 0)
@@ -635,7 +642,8 @@ static bool tuning_ok(const neb_tuning* t) {
   auto in = [](int v, int lo, int hi) { return v >= lo && v <= hi; };
   return in(t->cam_origin_bits, 0, 4) && in(t->cam_dir_bits, 0, 4) && in(t->shadow_origin_bits, 0, 4) &&
          in(t->shadow_light_bits, 0, 4) && 3 * (t->cam_origin_bits + t->cam_dir_bits) <= 12 &&
-         3 * (t->shadow_origin_bits + t->shadow_light_bits) <= 12 && in(t->shade_blocks_per_sm, 1, 32);
+         3 * (t->shadow_origin_bits + t->shadow_light_bits) <= 12 && in(t->shade_blocks_per_sm, 1, 32) &&
+         in(t->photon_grouping, 0, 1);
 }
 
 extern "C" int neb_get_tuning(const neb_ctx* c, neb_tuning* out) {

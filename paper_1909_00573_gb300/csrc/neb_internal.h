@@ -201,7 +201,7 @@ struct neb_ctx {
   neb::ShadowRay* shadow_rays_b = nullptr;  // rays the first walk did not settle, for the second
   int* shadow_start_b = nullptr;
   int* group_counters = nullptr;  // ray grouping of pass 1: group counts, then cursors
-  neb_tuning tune{1, 3, 2, 2, 8};  // launch settings (neb_set_tuning / neb_autotune)
+  neb_tuning tune{1, 3, 2, 2, 8, 1};  // launch settings (neb_set_tuning / neb_autotune)
   neb::MergeRec* mrec = nullptr;
   int* vert_bucket = nullptr;
   int* bucket_count = nullptr;

@@ -1042,7 +1042,7 @@ static long long enqueue_pass23(neb_ctx* c, int iteration, cudaStream_t st2, Sta
       int in = (j - 1) & 1, out = j & 1;
       k_reset_photon_slot<<<1, 1, 0, st2>>>(cnt, out);
       const void* qin = c->phq[in];
-      if (c->phq_grouped) {
+      if (c->phq_grouped && c->tune.photon_grouping) {
         // photon rays regrouped by origin and direction cell, as the camera
         // bounce rays are, so a warp's rays walk the same nodes
         tm.begin(STAGE_GROUP);

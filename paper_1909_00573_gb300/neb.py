@@ -49,7 +49,7 @@ class Config(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("cam_origin_bits", C.c_int), ("cam_dir_bits", C.c_int), ("shadow_origin_bits", C.c_int),
-                ("shadow_light_bits", C.c_int), ("shade_blocks_per_sm", C.c_int)]
+                ("shadow_light_bits", C.c_int), ("shade_blocks_per_sm", C.c_int), ("photon_grouping", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -115,3 +115,31 @@ def test_tuning_changes_no_result(neb):
     assert ctx.tuning().as_dict() == t.as_dict()
     assert 3 * (t.cam_origin_bits + t.cam_dir_bits) <= 12 and 1 <= t.shade_blocks_per_sm <= 32
     ctx.close()
+
+
+def test_photon_regrouping_changes_no_result(neb):
+    """Photon rays regrouped before each walk (a launch setting, on where the
+    photon queue holds at least 2^20 rays): the same photons, hits and merges
+    as without, and the FP64 sums equal up to the order of the additions
+    (every hit merged on its own).  A 400 x 400 room: 1.12 M photon slots."""
+    from paper_1909_00573_gb300 import scenes
+    s = scenes.tiny_room()
+    rc = scenes.RenderConfig(400, 400, 8, 0.01, 1 << 20, 8, 2, seed=5, octree_mode=1)
+    out = []
+    for grouping in (1, 0):
+        ctx = _start(neb, s, rc, merge_mode=1)
+        t = ctx.tuning()
+        assert t.photon_grouping == 1                     # on by default
+        t.photon_grouping = grouping
+        ctx.set_tuning(t)
+        ctx.iterate(rc.iterations)
+        out.append((ctx.read_nee_rho(), ctx.read_accum(), ctx.stats()))
+        ctx.close()
+    (r1, a1, st1), (r0, a0, st0) = out
+    assert np.array_equal(r1, r0)
+    for key in ("photons", "photon_hits", "merges", "merge_tests", "camera_rays"):
+        assert st1[key] == st0[key], key
+    assert st1["kernel_launches"] > st0["kernel_launches"]   # the regrouping launches ran
+    _close(a1, a0, 1)
+    assert a0.sum() > 0
+
