@@ -22,14 +22,15 @@ constexpr int kTraceThreads = 256;
 constexpr int kRefill = 8;        // refill when at least this many lanes are idle
 constexpr int kSteps = 24;        // node steps between refill checks (closest hit)
 constexpr int kShadowSteps = 64;  // node steps at most between refills (any hit; it votes every step)
+constexpr int kShadowFlush = 28;  // any hit: lanes ready to test their queued leaves before the warp tests
 constexpr int kIdle = -1, kDone = -2;
 
 // Traversal state.  Both walks run over the 4-wide BVH.  Closest-hit walks
 // test the leaf primitives of a node right after its box tests.  Shadow (any-hit) walks
 // queue leaf primitives, and the warp tests its queued primitives together
-// once every lane has two queued or nothing left to walk, so the long
-// triangle test runs with most lanes active ("while-while" with speculative
-// traversal, Aila and Laine 2009).
+// once kShadowFlush lanes have two queued or nothing left to walk, so the
+// long triangle test runs with most lanes active ("while-while" with
+// speculative traversal, Aila and Laine 2009).
 struct Walk {
   int node;  // next inner node, -1 when the stack is exhausted
   int sp, best;
@@ -202,7 +203,10 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, Nee
     for (int step = 0; step < kShadowSteps; ++step) {
       if (ray >= 0 && w.node >= 0 && w.npend <= 1) inner_step4(s, r, tmax, w, stack, &cnt->status, visits);
       bool ready = ray < 0 || w.npend >= 2 || w.node < 0;
-      if (__all_sync(0xffffffffu, ready)) {
+      // the queued leaves are tested once 28 lanes are ready (the others test
+      // what they have queued and walk on): waiting for all 32 leaves most
+      // lanes idle behind the last few (many lights: 5.82 -> 5.58 ms)
+      if (__popc(__ballot_sync(0xffffffffu, ready)) >= kShadowFlush) {
         bool lit = false, defer = false;
         int id = 0;
         if (ray >= 0) {
