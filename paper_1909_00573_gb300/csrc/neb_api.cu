@@ -58,13 +58,16 @@ static cudaError_t dalloc(T** p, size_t count) {
 static void free_scene(neb_ctx* c) {
   cudaFree(c->tv0); cudaFree(c->tv1); cudaFree(c->tv2); cudaFree(c->sph); cudaFree(c->mats); cudaFree(c->sph_mat);
   cudaFree(c->prim_light); cudaFree(c->light_prim); cudaFree(c->alias_idx); cudaFree(c->light_psel);
-  cudaFree(c->light_inv_area); cudaFree(c->alias_prob); cudaFree(c->nodes);
+  cudaFree(c->light_inv_area); cudaFree(c->alias_prob); cudaFree(c->nee_lights); cudaFree(c->alias_slots);
+  cudaFree(c->nodes);
   cudaFree(c->prim_start);
   cudaFree(c->oct_nodes);
   cudaFree(c->oct_state);
   c->tv0 = c->tv1 = c->tv2 = c->sph = c->mats = nullptr;
   c->sph_mat = c->prim_light = c->light_prim = c->alias_idx = nullptr;
   c->light_psel = c->light_inv_area = c->alias_prob = nullptr;
+  c->nee_lights = nullptr;
+  c->alias_slots = nullptr;
   c->nodes = nullptr;
   c->prim_start = nullptr;
   c->oct_nodes = nullptr;
@@ -137,7 +140,7 @@ extern "C" int neb_job_device_bytes(const neb_config* cfg, int n_tri, int n_sph,
        (k.cap_mh ? 2 * ((size_t)k.ptable + 1) * sizeof(int) : 0);
   const size_t nt = (size_t)n_tri, ns = (size_t)n_sph, nl = (size_t)n_lights, np = nt + ns;
   b += 3 * nt * sizeof(float4) + ns * (sizeof(float4) + sizeof(int)) + 3 * (size_t)n_mat * sizeof(float4);
-  b += np * sizeof(int) + nl * (2 * sizeof(int) + 3 * sizeof(float));
+  b += np * sizeof(int) + nl * (2 * sizeof(int) + 3 * sizeof(float) + sizeof(NeeLight) + sizeof(int2));
   b += (1 + (((size_t)cfg->octree_capacity + 7) & ~(size_t)7)) * sizeof(int) + sizeof(OctreeState);
   b += (np > 1 ? np - 1 : 1) * sizeof(BVH4Node) + np * sizeof(int);
   *out = b;
@@ -363,6 +366,47 @@ static void launch_pack_triangles(const float* tri, const uint32_t* mat, int nt,
   k_pack_triangles<<<blocks, 256, 0, st>>>(tri, mat, nt, v0, v1, v2, bounds);
 }
 
+// The NEE light records and alias slots: the same values the per-light
+// arrays hold (the area pdf is the same FP32 product psel * (1 / area) the
+// light pdf forms), gathered per light into one 64-byte line.
+__global__ void k_nee_lights(const int* __restrict__ light_prim, const float* __restrict__ psel,
+                             const float* __restrict__ inv_area, const float* __restrict__ alias_prob,
+                             const int* __restrict__ alias_idx, const float4* __restrict__ tv0,
+                             const float4* __restrict__ tv1, const float4* __restrict__ tv2,
+                             const float4* __restrict__ sph, const int* __restrict__ sph_mat,
+                             const float4* __restrict__ mats, int nt, int nl, NeeLight* out, int2* slots) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += gridDim.x * blockDim.x) {
+    const int prim = light_prim[i];
+    const float pa = psel[i] * inv_area[i];
+    NeeLight L;
+    int mat;
+    if (prim < nt) {
+      float4 a = tv0[prim], b = tv1[prim], cc = tv2[prim];
+      mat = __float_as_int(a.w);
+      L.a = make_float4(a.x, a.y, a.z, 0.0f);
+      L.b = make_float4(b.x, b.y, b.z, pa);
+      L.c = make_float4(cc.x, cc.y, cc.z, __int_as_float(prim));
+    } else {
+      mat = sph_mat[prim - nt];
+      L.a = sph[prim - nt];
+      L.b = make_float4(0.0f, 0.0f, 0.0f, pa);
+      L.c = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(prim));
+    }
+    float4 e = mats[3 * mat + 1];
+    L.e = make_float4(e.x, e.y, e.z, 0.0f);
+    out[i] = L;
+    slots[i] = make_int2(__float_as_int(alias_prob[i]), alias_idx[i]);
+  }
+}
+
+static void launch_nee_lights(neb_ctx* c, cudaStream_t st) {
+  int blocks = (c->nl + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_nee_lights<<<blocks, 256, 0, st>>>(c->light_prim, c->light_psel, c->light_inv_area, c->alias_prob, c->alias_idx,
+                                       c->tv0, c->tv1, c->tv2, c->sph, c->sph_mat, c->mats, c->nt, c->nl,
+                                       c->nee_lights, c->alias_slots);
+}
+
 static void launch_mark_lights(const int* light_prim, int nl, int* prim_light, cudaStream_t st) {
   int blocks = (nl + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
@@ -483,7 +527,8 @@ extern "C" int neb_scene_upload(neb_ctx* c, const float* tri, const uint32_t* tr
             dalloc(&c->sph_mat, ns) == cudaSuccess && dalloc(&c->mats, 3 * (size_t)nm) == cudaSuccess &&
             dalloc(&c->prim_light, np) == cudaSuccess && dalloc(&c->light_prim, nl) == cudaSuccess &&
             dalloc(&c->light_psel, nl) == cudaSuccess && dalloc(&c->light_inv_area, nl) == cudaSuccess &&
-            dalloc(&c->alias_prob, nl) == cudaSuccess && dalloc(&c->alias_idx, nl) == cudaSuccess;
+            dalloc(&c->alias_prob, nl) == cudaSuccess && dalloc(&c->alias_idx, nl) == cudaSuccess &&
+            dalloc(&c->nee_lights, nl) == cudaSuccess && dalloc(&c->alias_slots, nl) == cudaSuccess;
   c->oct_cap = octree_params(c->bmin, c->bmax, c->cfg.octree_capacity, c->cfg.split_factor).capacity;
   ok = ok && dalloc(&c->oct_nodes, (size_t)c->oct_cap) == cudaSuccess && dalloc(&c->oct_state, 1) == cudaSuccess;
   // the caller's triangle arrays, copied as they are and repacked on the device
@@ -523,6 +568,7 @@ extern "C" int neb_scene_upload(neb_ctx* c, const float* tri, const uint32_t* tr
     cudaMemcpyAsync(c->light_inv_area, inv_area.data(), sizeof(float) * nl, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(c->alias_prob, aprob.data(), sizeof(float) * nl, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(c->alias_idx, aidx.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, st);
+    launch_nee_lights(c, st);
   }
   OctreeState s0{1, 0, 0, 0};
   cudaMemsetAsync(c->oct_nodes, 0, sizeof(int) * (size_t)c->oct_cap, st);

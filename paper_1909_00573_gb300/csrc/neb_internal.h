@@ -49,6 +49,16 @@ struct __align__(16) PackedPhoton {
                // w: k_nee | j << 8 | (flux exponent + 128) << 16
 };
 
+// One light of the NEE light choice (64 bytes): what a light sample at a
+// camera vertex reads once the alias slot has picked the light, so that the
+// choice costs two dependent loads (slot, then this line) instead of five.
+struct __align__(16) NeeLight {
+  float4 a;  // triangle: v0; sphere: centre, w radius
+  float4 b;  // triangle: v1; w: area pdf of the choice, psel / area (sphere: psel / (2 pi R^2))
+  float4 c;  // triangle: v2; w: primitive index (int bits)
+  float4 e;  // emission rgb of the light's material
+};
+
 // Shadow ray of an NEE vertex in light-grouped order (32 bytes).
 struct __align__(16) ShadowRay {
   float4 o;  // offset origin, w: tmax = (1 - 1e-4) distance to the light point
@@ -172,6 +182,8 @@ struct neb_ctx {
   int* sph_mat = nullptr;
   int *prim_light = nullptr, *light_prim = nullptr, *alias_idx = nullptr;
   float *light_psel = nullptr, *light_inv_area = nullptr, *alias_prob = nullptr;
+  neb::NeeLight* nee_lights = nullptr;  // per light, in light-list order
+  int2* alias_slots = nullptr;          // per alias slot: (probability bits, alias)
   neb::CameraParams cam{};
   bool scene_ready = false;
 

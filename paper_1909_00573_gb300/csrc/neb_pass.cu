@@ -182,7 +182,9 @@ __global__ void k_camera(IterParams ip, CameraParams cam, CamRay* q, DevCounters
 __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip, int k, const CamRay* __restrict__ in,
                                                      int in_slot, CamRay* __restrict__ out, int out_slot,
                                                      NeeStore nv, RHEvent* __restrict__ rh, DevCounters* cnt,
-                                                     int* __restrict__ slot_map, const int2* __restrict__ hits) {
+                                                     int* __restrict__ slot_map, const int2* __restrict__ hits,
+                                                     const NeeLight* __restrict__ lights,
+                                                     const int2* __restrict__ alias) {
   const int count = min(cnt->cam_count[in_slot], ip.cap_cam);
   const int stride = gridDim.x * blockDim.x;
   for (int base = blockIdx.x * blockDim.x; base < count; base += stride) {
@@ -218,22 +220,17 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
       if (want_nee) {
         uint4 rb = rng_block(ip.key, ip.iteration, pixel, 256u * k, 0);
         lidx = (int)(((uint64_t)(rb.x >> 8) * (uint64_t)s.nl) >> 24);
-        if (!(u01(rb.y) < __ldg(s.alias_prob + lidx))) lidx = __ldg(s.alias_idx + lidx);
+        const int2 slot = __ldg(alias + lidx);
+        if (!(u01(rb.y) < __int_as_float(slot.x))) lidx = slot.y;
         u2 = u01(rb.z);
         u3 = u01(rb.w);
-        lprim = __ldg(s.light_prim + lidx);
-        l_pa = __ldg(s.light_psel + lidx) * __ldg(s.light_inv_area + lidx);
-        int lmat;
-        if (lprim < s.nt) {
-          la0 = __ldg(s.tv0 + lprim);
-          la1 = __ldg(s.tv1 + lprim);
-          la2 = __ldg(s.tv2 + lprim);
-          lmat = __float_as_int(la0.w);
-        } else {
-          la0 = __ldg(s.sph + (lprim - s.nt));
-          lmat = __ldg(&s.sph_mat[lprim - s.nt]);
-        }
-        l_emit = xyz(__ldg(s.mats + 3 * lmat + 1));
+        const NeeLight* L = lights + lidx;
+        la0 = __ldg(&L->a);
+        la1 = __ldg(&L->b);
+        la2 = __ldg(&L->c);
+        l_emit = xyz(__ldg(&L->e));
+        lprim = __float_as_int(la2.w);
+        l_pa = la1.w;
       }
       RayPre r = make_ray(xyz(ry.o), d);
       int2 hh = hits[i];
@@ -973,7 +970,8 @@ static long long enqueue_pass1(neb_ctx* c, int iteration, cudaStream_t st, Stage
                          st);
     tm.end();
     tm.begin(STAGE_EXTEND);
-    k_extend<<<capped_blocks(c->cap_cam, kThreads, B), kThreads, 0, st>>>(s, ip, k, qin, in, c->camq[out], out, sl.nv, sl.rh, cnt, sl.slot_map, c->hits);
+    k_extend<<<capped_blocks(c->cap_cam, kThreads, B), kThreads, 0, st>>>(
+        s, ip, k, qin, in, c->camq[out], out, sl.nv, sl.rh, cnt, sl.slot_map, c->hits, c->nee_lights, c->alias_slots);
     launches += 3;
     tm.end();
   }
