@@ -256,12 +256,13 @@ __global__ void k_single_leaf(SceneView s, BVH4Node* nodes) {
   float3 lo, hi;
   prim_bounds(s, 0, lo, hi);
   BVH4Node nd;
-  nd.lox = make_float4(lo.x, 0, 0, 0);
-  nd.hix = make_float4(hi.x, 0, 0, 0);
-  nd.loy = make_float4(lo.y, 0, 0, 0);
-  nd.hiy = make_float4(hi.y, 0, 0, 0);
-  nd.loz = make_float4(lo.z, 0, 0, 0);
-  nd.hiz = make_float4(hi.z, 0, 0, 0);
+  const float I = INFINITY;
+  nd.lox = make_float4(lo.x, I, I, I);
+  nd.hix = make_float4(hi.x, -I, -I, -I);
+  nd.loy = make_float4(lo.y, I, I, I);
+  nd.hiy = make_float4(hi.y, -I, -I, -I);
+  nd.loz = make_float4(lo.z, I, I, I);
+  nd.hiz = make_float4(hi.z, -I, -I, -I);
   nd.ch = make_int4(~0, kEmptyChild, kEmptyChild, kEmptyChild);
   nd.pad = make_float4(0, 0, 0, 0);
   nodes[0] = nd;
@@ -496,8 +497,10 @@ __global__ void k_collapse4(const BVHNode* __restrict__ bin, const int2* __restr
           if (owner) owner[~ref[i]] = it.y;
         }
       } else {
-        L[0][i] = L[1][i] = L[2][i] = 0.0f;
-        H[0][i] = H[1][i] = H[2][i] = 0.0f;
+        // an empty slot holds the inverted infinite box, which every slab
+        // test misses (entry +inf, exit -inf whatever the ray's octant)
+        L[0][i] = L[1][i] = L[2][i] = INFINITY;
+        H[0][i] = H[1][i] = H[2][i] = -INFINITY;
         R[i] = kEmptyChild;
       }
     }

@@ -456,16 +456,51 @@ __device__ __forceinline__ Node4Oct load_node4_oct(const BVH4Node* __restrict__ 
 __device__ __forceinline__ float comp4(float4 v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w)); }
 __device__ __forceinline__ int comp4i(int4 v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w)); }
 
-// Slab test of child c: entry = max(0, entry planes), exit = min(tmax, exit
-// planes widened by 1 + 2 gamma_3); NaN distances drop out of fmaxf / fminf.
-__device__ __forceinline__ bool child_hit(const Node4Oct& n, int c, const RayPre& r, float tmax, float& tnear) {
-  float t0 = fmaxf(fmaxf((comp4(n.nx, c) - r.o.x) * r.inv.x, (comp4(n.ny, c) - r.o.y) * r.inv.y),
-                   fmaxf((comp4(n.nz, c) - r.o.z) * r.inv.z, 0.0f));
-  float t1 = fminf(fminf((comp4(n.fx, c) - r.o.x) * r.inv.x, (comp4(n.fy, c) - r.o.y) * r.inv.y),
-                   (comp4(n.fz, c) - r.o.z) * r.inv.z) * 1.0000004f;
-  t1 = fminf(t1, tmax);
-  tnear = t0;
-  return t0 <= t1;
+// Three-input FP32 minimum and maximum (sm_100 and later); NaN inputs drop
+// out as they do from nested fminf / fmaxf.
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
+// Slab distances (plane - o) * inv of two children on one axis, with one
+// packed FP32x2 add and one packed multiply: each half rounds like the scalar
+// subtract and multiply (plane + (-o) is plane - o exactly).
+__device__ __forceinline__ float2 slab2(float a, float b, float no, float inv) {
+  return __fmul2_rn(__fadd2_rn(make_float2(a, b), make_float2(no, no)), make_float2(inv, inv));
+}
+
+// Slab tests of the four children: entry = max(0, entry planes), exit =
+// min(tmax, exit planes widened by 1 + 2 gamma_3); NaN distances drop out of
+// the minimum and maximum.  Returns the mask of children whose box is hit
+// before tmax and their entry distances.
+__device__ __forceinline__ uint32_t child_hits4(const Node4Oct& n, const RayPre& r, float tmax, float (&tn)[4]) {
+  const float nox = -r.o.x, noy = -r.o.y, noz = -r.o.z;
+  const float2 nx01 = slab2(n.nx.x, n.nx.y, nox, r.inv.x), nx23 = slab2(n.nx.z, n.nx.w, nox, r.inv.x);
+  const float2 ny01 = slab2(n.ny.x, n.ny.y, noy, r.inv.y), ny23 = slab2(n.ny.z, n.ny.w, noy, r.inv.y);
+  const float2 nz01 = slab2(n.nz.x, n.nz.y, noz, r.inv.z), nz23 = slab2(n.nz.z, n.nz.w, noz, r.inv.z);
+  const float2 fx01 = slab2(n.fx.x, n.fx.y, nox, r.inv.x), fx23 = slab2(n.fx.z, n.fx.w, nox, r.inv.x);
+  const float2 fy01 = slab2(n.fy.x, n.fy.y, noy, r.inv.y), fy23 = slab2(n.fy.z, n.fy.w, noy, r.inv.y);
+  const float2 fz01 = slab2(n.fz.x, n.fz.y, noz, r.inv.z), fz23 = slab2(n.fz.z, n.fz.w, noz, r.inv.z);
+  const float ex[4] = {nx01.x, nx01.y, nx23.x, nx23.y}, ey[4] = {ny01.x, ny01.y, ny23.x, ny23.y},
+              ez[4] = {nz01.x, nz01.y, nz23.x, nz23.y};
+  const float gx[4] = {fx01.x, fx01.y, fx23.x, fx23.y}, gy[4] = {fy01.x, fy01.y, fy23.x, fy23.y},
+              gz[4] = {fz01.x, fz01.y, fz23.x, fz23.y};
+  uint32_t m = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float t0 = fmaxf(fmax3(ex[c], ey[c], ez[c]), 0.0f);
+    const float t1 = fminf(fmin3(gx[c], gy[c], gz[c]) * 1.0000004f, tmax);
+    tn[c] = t0;
+    if (t0 <= t1) m |= 1u << c;
+  }
+  return m;
 }
 
 // Sort key of a hit inner child: its entry distance (>= 0, so the float bits
@@ -493,22 +528,23 @@ __device__ __forceinline__ bool closest_step4(const SceneView& s, const RayPre& 
   ++visits;
   uint32_t k0 = kNoKey, k1 = kNoKey, k2 = kNoKey, k3 = kNoKey;
   int leaves = 0;
+  float tn[4];
+  const uint32_t hit = child_hits4(n, r, best_t, tn);
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     int ref = comp4i(n.ch, c);
-    if (ref == kEmptyChild) continue;
-    float tn;
-    if (!child_hit(n, c, r, best_t, tn)) continue;
+    if (!(hit & (1u << c))) continue;  // empty slots hold boxes no ray hits
     if (ref < 0) {
       leaves |= 1 << c;
     } else {
-      uint32_t k = child_key(tn, c);
+      uint32_t k = child_key(tn[c], c);
       if (c == 0) k0 = k;
       else if (c == 1) k1 = k;
       else if (c == 2) k2 = k;
       else k3 = k;
     }
   }
+  const float bt = best_t;
   while (leaves) {
     int c = __ffs(leaves) - 1;
     leaves &= leaves - 1;
@@ -520,11 +556,14 @@ __device__ __forceinline__ bool closest_step4(const SceneView& s, const RayPre& 
       best = p;
     }
   }
-  // a child entered beyond a closer hit found here holds no closer hit
-  if (k0 != kNoKey && key_dist(k0) > best_t) k0 = kNoKey;
-  if (k1 != kNoKey && key_dist(k1) > best_t) k1 = kNoKey;
-  if (k2 != kNoKey && key_dist(k2) > best_t) k2 = kNoKey;
-  if (k3 != kNoKey && key_dist(k3) > best_t) k3 = kNoKey;
+  // a child entered beyond a closer hit found here holds no closer hit (the
+  // box tests already dropped the children entered beyond the earlier one)
+  if (best_t < bt) {
+    if (k0 != kNoKey && key_dist(k0) > best_t) k0 = kNoKey;
+    if (k1 != kNoKey && key_dist(k1) > best_t) k1 = kNoKey;
+    if (k2 != kNoKey && key_dist(k2) > best_t) k2 = kNoKey;
+    if (k3 != kNoKey && key_dist(k3) > best_t) k3 = kNoKey;
+  }
   key_swap(k0, k1);
   key_swap(k2, k3);
   key_swap(k0, k2);

@@ -61,12 +61,12 @@ __device__ __forceinline__ void inner_step4(const SceneView& s, const RayPre& r,
   Node4Oct n = load_node4_oct(s.nodes, w.node, r.oct);
   ++visits;
   int next = -1;
+  float tn[4];
+  const uint32_t hit = child_hits4(n, r, tbound, tn);
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     int ref = comp4i(n.ch, c);
-    if (ref == kEmptyChild || ref == w.skip) continue;
-    float tn;
-    if (!child_hit(n, c, r, tbound, tn)) continue;
+    if (ref == w.skip || !(hit & (1u << c))) continue;  // empty slots hold boxes no ray hits
     if (ref < 0) {
       w.pend[w.npend++] = ~ref;
     } else if (next < 0) {
@@ -107,7 +107,7 @@ __device__ __forceinline__ int fetch_rays(int cur, int* fetch, int count, int re
 // float4 1: CamRay and PhotonRay).  hits[i] = (prim, t bits), prim -1 on a miss.
 // packed: records are PackedPhoton (48 bytes, direction in the octahedral
 // word) instead of 64-byte records with the direction in float4 1.
-__global__ void __launch_bounds__(kTraceThreads) k_trace_closest(SceneView s, const float4* __restrict__ recs,
+__global__ void __launch_bounds__(kTraceThreads, 4) k_trace_closest(SceneView s, const float4* __restrict__ recs,
                                                                  const int* __restrict__ count_ptr, int cap,
                                                                  int* __restrict__ fetch, int2* __restrict__ hits,
                                                                  DevCounters* cnt, int which, int packed) {
