@@ -190,17 +190,17 @@ TRAFFIC_SOURCES = ("paper_1909_00573_gb300/csrc/neb_trace.cu", "paper_1909_00573
 NCU_COUNTERS = {  # (workload, stage): counters of the stage's kernel, captured from these sources
     ("many_lights", "trace_camera"): {
         "bound": "issue",              # instruction issue on dependent chains and divergence, not DRAM
-        "bytes_per_launch": 161478963,  # mean DRAM read + write of the 10 camera launches of an iteration
-        "lane_efficiency": 12.18 / 32,  # smsp__thread_inst_executed_per_inst_executed, 960 x 540 capture
-        "issue_active": 0.689,          # smsp__issue_active, 960 x 540 capture
-        "sources_sha256": "b2c09f40d46936b21ab9a6dfa5ee62244a644dc94386ee6071bd1c95373e9c10",
+        "bytes_per_launch": 161644518,  # mean DRAM read + write of the 10 camera launches of an iteration
+        "lane_efficiency": 12.06 / 32,  # smsp__thread_inst_executed_per_inst_executed, 960 x 540 capture
+        "issue_active": 0.688,          # smsp__issue_active, 960 x 540 capture
+        "sources_sha256": "44e3203109cfef4c8680dfca0c9edc99f29c05d7d751e6f138eed3cedede8818",
         "profile": "profiles/k_trace_closest_many_lights.md"},
     ("large_city", "trace_camera"): {
         "bound": "issue",
-        "bytes_per_launch": 73624217,   # mean DRAM read + write of the 10 camera launches of an iteration
-        "lane_efficiency": 10.82 / 32,  # smsp__thread_inst_executed_per_inst_executed, 640 x 360 capture
-        "issue_active": 0.621,          # smsp__issue_active, 640 x 360 capture
-        "sources_sha256": "b2c09f40d46936b21ab9a6dfa5ee62244a644dc94386ee6071bd1c95373e9c10",
+        "bytes_per_launch": 73705164,   # mean DRAM read + write of the 10 camera launches of an iteration
+        "lane_efficiency": 10.79 / 32,  # smsp__thread_inst_executed_per_inst_executed, 640 x 360 capture
+        "issue_active": 0.618,          # smsp__issue_active, 640 x 360 capture
+        "sources_sha256": "44e3203109cfef4c8680dfca0c9edc99f29c05d7d751e6f138eed3cedede8818",
         "profile": "profiles/k_trace_closest_large_city.md"},
 }
 

@@ -6,6 +6,7 @@
 // implementation of the same formulas.  Where a fused multiply-add is
 // wanted it is written explicitly (__fmaf_rn).
 #pragma once
+#include <cfloat>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -456,6 +457,15 @@ __device__ __forceinline__ Node4Oct load_node4_oct(const BVH4Node* __restrict__ 
 __device__ __forceinline__ float comp4(float4 v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w)); }
 __device__ __forceinline__ int comp4i(int4 v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w)); }
 
+// Walks take only rays with a finite origin and direction.  The slab test
+// drops NaN distances, so a ray with a NaN component would enter every child
+// slot, the empty ones (inverted infinite boxes) included; such a ray hits
+// nothing and is settled before its walk, as a walk of it would settle it.
+__device__ __forceinline__ bool ray_finite(float3 o, float3 d) {
+  return fabsf(o.x) <= FLT_MAX && fabsf(o.y) <= FLT_MAX && fabsf(o.z) <= FLT_MAX && fabsf(d.x) <= FLT_MAX &&
+         fabsf(d.y) <= FLT_MAX && fabsf(d.z) <= FLT_MAX;
+}
+
 // Three-input FP32 minimum and maximum (sm_100 and later); NaN inputs drop
 // out as they do from nested fminf / fmaxf.
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
@@ -610,7 +620,7 @@ __device__ __forceinline__ int trace_closest(const SceneView& s, const RayPre& r
                                              uint32_t* status, uint32_t& visits, uint32_t& ptests) {
   int best = -1;
   float best_t = tmax;
-  if (s.nt + s.ns == 0) { t_out = tmax; return -1; }
+  if (s.nt + s.ns == 0 || !ray_finite(r.o, r.d)) { t_out = tmax; return -1; }
   int stack[64];
   float stack_t[64];
   int sp = 0, node = 0;

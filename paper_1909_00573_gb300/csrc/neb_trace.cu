@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_trace_closest(SceneView s,
       float3 d = packed ? oct_decode16(__ldg(reinterpret_cast<const uint4*>(rec + 2)).x) : xyz(__ldg(rec + 1));
       r = make_ray(xyz(o), d);
       walk_init(w);
-      if (s.nt + s.ns == 0) {
+      if (s.nt + s.ns == 0 || !ray_finite(r.o, r.d)) {  // a miss without a walk
         hits[nr] = make_int2(-1, __float_as_int(FLT_MAX));
         nr = kIdle;
       }
@@ -188,13 +188,13 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_shadow(SceneView s, Nee
       w.node = phase == 0 ? first : 0;
       w.skip = phase == 1 ? first : 0;
       if (phase != 1) ++rays;
-      if (no_geometry) {  // nothing can block it
+      if (no_geometry || !ray_finite(r.o, r.d)) {  // nothing can block it
         lit0 = true;
         lit0_id = nr;
         nr = kIdle;
       }
     }
-    if (no_geometry) {
+    if (__any_sync(0xffffffffu, lit0)) {
       int slot = warp_append(&cnt->lit_count, lit0, cap, &cnt->status);
       if (slot >= 0) nv.lit[slot] = lit0_id;
     }

@@ -283,6 +283,56 @@ def test_bvh_closest_hit_equals_oracle(neb, oracle, name, builder):
     assert (gp >= 0).mean() > 0.3
 
 
+@pytest.mark.parametrize("n_tri", [1, 2, 5, 7])
+def test_bvh_empty_child_slots_and_degenerate_rays(neb, oracle, n_tri):
+    """Trees of one to seven triangles leave empty child slots in their 4-wide
+    nodes; an empty slot holds the inverted infinite box, which no finite ray
+    enters whatever its octant, zero direction components included.  Rays
+    through the origin (where a zero box would sit) and along the axes must
+    hit what the oracle hits.  Rays with a NaN or infinite origin or
+    direction component hit nothing: they are settled before their walk."""
+    from paper_1909_00573_gb300 import scenes
+    rng = np.random.default_rng(11 + n_tri)
+    c = rng.uniform(0.2, 1.0, (n_tri, 1, 3)) * rng.choice([-1.0, 1.0], (n_tri, 1, 3))
+    tri = (c + rng.uniform(-0.15, 0.15, (n_tri, 3, 3))).astype(np.float32)
+    s = scenes.Scene(tri, np.zeros(n_tri), np.zeros((0, 4)), np.zeros(0),
+                     scenes.material(0, (0.5,) * 3)[None], np.zeros(10))
+    n = 4000
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    through0 = np.concatenate([-2.0 * d, d], 1)                    # origins on lines through (0, 0, 0)
+    aim = tri[rng.integers(0, n_tri, n)].mean(axis=1)
+    o = aim + rng.uniform(1.0, 2.0, (n, 1)) * rng.normal(size=(n, 3))
+    da = aim - o
+    da /= np.linalg.norm(da, axis=1, keepdims=True)
+    aimed = np.concatenate([o, da], 1)                               # rays at triangle centroids
+    axes = np.zeros((12, 6))
+    for k in range(6):                                               # along +-x, +-y, +-z through 0
+        axes[2 * k, k // 2] = (-2.0 if k % 2 == 0 else 2.0)
+        axes[2 * k, 3 + k // 2] = (1.0 if k % 2 == 0 else -1.0)
+        axes[2 * k + 1, 3 + k // 2] = axes[2 * k, 3 + k // 2]        # from the origin itself
+    rays = np.concatenate([through0, aimed, axes]).astype(np.float32)
+    rc = scenes.RenderConfig(8, 8, 4, 0.01, 1024, 4, 1)
+    ctx = neb.Context(neb.make_config(rc))
+    ctx.scene_upload(s)
+    ctx.build_bvh()
+    gp, gt = ctx.trace_closest(rays)
+    assert ctx.stats()["status"] == 0
+    op, ot = oracle.trace(s, rays)
+    same = gp == op
+    assert same.mean() >= 0.999, same.mean()
+    hit = same & (gp >= 0)
+    assert np.array_equal(gt[hit].view(np.int32), ot[hit].view(np.int32))
+    assert (gp[n:2 * n] >= 0).mean() > 0.9                          # the aimed rays hit
+    bad = np.repeat(rays[n:n + 8], 6, axis=0)
+    for k in range(6):                                               # one non-finite component each
+        bad[k::6, k] = np.nan if k % 2 == 0 else np.inf
+    bad[3::6, 3] = -np.inf
+    bp, bt = ctx.trace_closest(bad)
+    ctx.close()
+    assert (bp == -1).all()
+
+
 def test_bvh_far_origin_rays_hit_their_targets(neb, oracle):
     """The slab test must stay conservative for origins far from the boxes
     (large |o|, small boxes): with the camera 15 units from a scene of extent
