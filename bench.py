@@ -310,6 +310,26 @@ def config_dict(rc, scene):
             "l2": "inputs larger than L2 (scene + BVH + per-iteration records > 129 MB)"}
 
 
+def admission_waves(sizes, budget):
+    """Jobs in order into waves whose summed device bytes fit the budget: a
+    job that does not fit the current wave starts the next one; a job larger
+    than the budget alone is rejected.  Returns ([[job index, ...], ...],
+    number rejected)."""
+    waves, wave, resident, rejected = [], [], 0, 0
+    for i, b in enumerate(sizes):
+        if b > budget:
+            rejected += 1
+            continue
+        if wave and resident + b > budget:
+            waves.append(wave)
+            wave, resident = [], 0
+        wave.append(i)
+        resident += b
+    if wave:
+        waves.append(wave)
+    return waves, rejected
+
+
 def run_batch(args):
     """Batched jobs: a seeded mix of heterogeneous jobs (rooms and cities of
     ~1.3k to ~500k triangles, 128^2 to 1024^2 pixels, 1 to 64 lights).  Jobs
@@ -333,19 +353,10 @@ def run_batch(args):
     for _, rc in jobs:
         rc.merge_mode = args.merge_mode
     budget = args.mem_budget_gb * 1e9
-    waves, wave, resident, rejected = [], [], 0, 0
-    for s, rc in jobs:
-        b = neb.job_device_bytes(neb.make_config(rc), s.n_tri, s.n_sph, len(s.mats), s.n_emitters)
-        if b > budget:
-            rejected += 1                             # does not fit even alone
-            continue
-        if resident + b > budget:
-            waves.append((wave, resident))
-            wave, resident = [], 0
-        wave.append((s, rc))
-        resident += b
-    if wave:
-        waves.append((wave, resident))
+    sizes = [neb.job_device_bytes(neb.make_config(rc), s.n_tri, s.n_sph, len(s.mats), s.n_emitters)
+             for s, rc in jobs]
+    plan, rejected = admission_waves(sizes, budget)
+    waves = [([jobs[i] for i in w], sum(sizes[i] for i in w)) for w in plan]
     admitted = [j for w, _ in waves for j in w]
     paths = sum(rc.width * rc.height for _, rc in admitted)
     t_seq = t_batch = setup_s = 0.0

@@ -89,3 +89,16 @@ def test_secondary_rates_and_traffic_lookup(monkeypatch):
     assert bench.measured_counters("many_lights", "shadow") is None
     monkeypatch.setitem(bench.NCU_COUNTERS, key, dict(entry, sources_sha256="0" * 64))
     assert bench.measured_counters("many_lights", "trace_camera") is None
+
+
+def test_batch_admission_waves():
+    """The batched-jobs benchmark runs every job: jobs go in order into waves
+    whose summed device bytes fit the budget, a job that does not fit starts
+    the next wave, and only a job larger than the budget alone is rejected."""
+    import bench
+    waves, rejected = bench.admission_waves([40, 50, 20, 70, 10, 120, 30], 100)
+    assert rejected == 1                                   # the 120-byte job
+    assert waves == [[0, 1], [2, 3, 4], [6]]
+    assert all(sum([40, 50, 20, 70, 10, 120, 30][i] for i in w) <= 100 for w in waves)
+    assert bench.admission_waves([], 100) == ([], 0)
+    assert bench.admission_waves([100, 100], 100) == ([[0], [1]], 0)   # a wave may be exactly full
