@@ -204,8 +204,9 @@ __global__ void __launch_bounds__(kThreads) k_extend(SceneView s, IterParams ip,
     bool shadow = false;
     float nee_p_lp = 0.0f;
     int hit_prim = -1;
-    // NEE light choice and the light's data: they depend only on the pixel
-    // and k, so these loads go out first and overlap those of the hit
+    // NEE light choice (its alias slot, then the chosen light's record): it
+    // depends only on the pixel and k, so these loads go out first and
+    // overlap those of the hit
     const bool want_nee = k <= ip.D - 1 && s.nl > 0;
     int lidx = 0, lprim = 0;
     float u2 = 0.0f, u3 = 0.0f, l_pa = 0.0f;
